@@ -1,0 +1,146 @@
+"""Plant plausible mistakes in copies of the oracle and confirm that the pin
+checks notice each one (CPU only; the real oracle is never modified)."""
+import importlib.util
+import os
+
+import numpy as np
+import pytest
+
+from tests import pins
+
+ORACLE_FILE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                           "oracle", "magpie_oracle.py")
+
+
+def fresh_oracle():
+    spec = importlib.util.spec_from_file_location("oracle_copy", ORACLE_FILE)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def m_restrict_sum(O):
+    O.restrict = lambda a: a[0::2, 0::2] + a[1::2, 0::2] + a[0::2, 1::2] + a[1::2, 1::2]
+
+
+def m_prolong_scaled(O):
+    orig = O.prolong
+    O.prolong = lambda b: 0.25 * orig(b)
+
+
+def m_fft_sign(O):
+    O.fft2 = lambda x: np.fft.ifft2(x) * x.shape[0] * x.shape[1]
+    O.ifft2 = lambda x: np.fft.fft2(x) / (x.shape[0] * x.shape[1])
+
+
+def m_fft_unnormalised_inverse(O):
+    O.ifft2 = lambda x: np.fft.ifft2(x) * x.shape[0] * x.shape[1]
+
+
+def m_no_sqrt(O):
+    def rew(zk, Q, dk, prev_phase=None):
+        psi = O.fft2(Q * zk)
+        return O.ifft2(dk * np.exp(1j * np.angle(psi)))
+    O.revised_exit_wave = rew
+
+
+def m_gradient_no_conj(O):
+    O.gradient_k = lambda zk, Q, dk: Q * (Q * zk - O.revised_exit_wave(zk, Q, dk))
+
+
+def m_wr_no_conj(O):
+    def cw(Q):
+        a2 = np.abs(Q) ** 2
+        QH = O.restrict(Q)
+        S = O.restrict(a2)
+        Wz = O.safe_div(a2, O.prolong(S))
+        WR = O.prolong(QH) * O.safe_div(Wz, np.conj(Q))
+        Wu = O.safe_div(np.abs(QH) ** 2, S)
+        return QH, Wz, WR, Wu
+    O.coarse_weights = cw
+
+
+def m_wz_unnormalised(O):
+    orig = O.coarse_weights
+
+    def cw(Q):
+        QH, Wz, WR, Wu = orig(Q)
+        return QH, np.abs(Q) ** 2, WR, Wu
+    O.coarse_weights = cw
+
+
+def m_uh_unweighted(O):
+    def magps(zk, Q, Rk, u, levels):
+        if levels == 1:
+            return O.proximal_step(zk, Q, Rk, u)
+        QH, Wz, WR, Wu = O.coarse_weights(Q)
+        zH = O.restrict(Wz * zk)
+        RH = O.restrict(WR * Rk)
+        eH = magps(zH, QH, RH, O.restrict(u), levels - 1) - zH
+        return O.proximal_step(zk + O.prolong(eH), Q, Rk, u)
+    O.magps = magps
+
+
+def m_post_smooth_from_z(O):
+    def magps(zk, Q, Rk, u, levels):
+        if levels == 1:
+            return O.proximal_step(zk, Q, Rk, u)
+        QH, Wz, WR, Wu = O.coarse_weights(Q)
+        zH = O.restrict(Wz * zk)
+        RH = O.restrict(WR * Rk)
+        eH = magps(zH, QH, RH, Wu * O.restrict(u), levels - 1) - zH
+        return O.proximal_step(zk, Q, Rk, u) + O.prolong(eH)
+    O.magps = magps
+
+
+def m_minibatch_count_average(O):
+    def step(z, Q, positions, d, u, levels, batch):
+        m = Q.shape[0]
+        num = np.zeros(z.shape, dtype=np.complex128)
+        den = np.zeros(z.shape)
+        for k in batch:
+            r, c = positions[k]
+            zk = z[r:r + m, c:c + m]
+            Rk = O.revised_exit_wave(zk, Q, d[k])
+            num[r:r + m, c:c + m] += O.magps(zk, Q, Rk, u, levels) - zk
+            den[r:r + m, c:c + m] += 1.0
+        out = np.array(z, dtype=np.complex128)
+        lit = den > 0
+        out[lit] += num[lit] / den[lit]
+        return out
+    O.minibatch_step = step
+
+
+def m_regulariser_amplitude(O):
+    O.rpie_regulariser = lambda Q, alpha: alpha * (np.abs(Q).max() - np.abs(Q))
+
+
+def m_extract_transposed(O):
+    O.extract = lambda z, pos, m: z[int(pos[1]):int(pos[1]) + m, int(pos[0]):int(pos[0]) + m].copy()
+
+
+def m_objective_no_half(O):
+    orig = O.objective_k
+    O.objective_k = lambda zk, Q, dk: 2.0 * orig(zk, Q, dk)
+
+
+MUTATIONS = [m_restrict_sum, m_prolong_scaled, m_fft_sign, m_fft_unnormalised_inverse,
+             m_no_sqrt, m_gradient_no_conj, m_wr_no_conj, m_wz_unnormalised,
+             m_uh_unweighted, m_post_smooth_from_z, m_minibatch_count_average,
+             m_regulariser_amplitude, m_extract_transposed, m_objective_no_half]
+
+FAST_CHECKS = [c for c in pins.ALL_CHECKS if c is not pins.check_recovery]
+
+
+@pytest.mark.parametrize("mutate", MUTATIONS, ids=lambda f: f.__name__[2:])
+def test_planted_mistake_is_caught(mutate):
+    O = fresh_oracle()
+    mutate(O)
+    failed = []
+    for check in FAST_CHECKS:
+        try:
+            with np.errstate(all="ignore"):
+                check(O)
+        except (AssertionError, ValueError, IndexError, ZeroDivisionError, FloatingPointError):
+            failed.append(check.__name__)
+    assert failed, f"no pin caught {mutate.__name__}"
