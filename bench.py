@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Throughput of the MAGPIE sweep on GB300: patterns/s per sweep.
+
+One step = one sweep (one iteration of Algorithm MAGPIE) over all windows of
+the n=512, m=128, 900-window, 3-level, minibatch-64 Poisson workload, with
+its inputs resident in HBM.  L2 is flushed (a 256 MiB write) before every
+timed sweep, outside the timed interval; each sweep is timed with CUDA
+events on the library's stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Several GPUs run independent replicas (the sweep itself runs on one GPU):
+rank r uses cuda:LOCAL_RANK, the value is all ranks' patterns over the
+slowest rank's time.  `--impl reference` times the FP64 CPU oracle on this
+host's cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2504_10118_gb300 import synth  # noqa: E402
+
+FP32_LANES_PER_SM = 128
+SMS = 152
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "window_kernel_m128_mid.txt")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_2504_10118_gb300", "csrc", "magpie.cu")
+
+
+def flops_per_window(m: int) -> float:
+    """Algorithmic flops of one window: two 2-D FFTs at the nominal 5 M log2 M
+    each, plus 43 M for the exit wave, projection, residual and V-cycle."""
+    M = m * m
+    return 10.0 * M * math.log2(M) + 43.0 * M
+
+
+def hbm_bytes_per_window(m: int) -> float:
+    """Compulsory HBM bytes of one window: its float32 amplitudes."""
+    return 4.0 * m * m
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return p, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def measured_traffic():
+    """DRAM bytes per launch of the window kernel from the committed ncu
+    summary, or None when the kernel source changed since it was taken."""
+    try:
+        lines = open(TRAFFIC_FILE).read().splitlines()
+    except OSError:
+        return None
+    kv = {}
+    for ln in lines:
+        if ":" in ln:
+            k, v = ln.split(":", 1)
+            kv[k.strip()] = v.strip()
+    src = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
+    if kv.get("source_sha256") != src or "dram_bytes_per_launch" not in kv:
+        return None
+    return float(kv["dram_bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi samples of one GPU while the benchmark runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-i", device_id, "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in out.splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power),
+                "window": "warm-up and timed sweeps"}
+
+
+def gpu_uuid(dev) -> str:
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [x for x in vis.split(",") if x]
+        return ids[dev.index] if dev.index < len(ids) else str(dev.index)
+
+
+def make_data(w, dev, magpie):
+    """Object, probe, positions and noisy intensities of workload w on dev.
+    Noise-free intensities come from the library's forward model."""
+    import torch
+    z_true, Q, pos = synth.make_problem(w)
+    Qt = torch.from_numpy(Q.astype(np.complex64)).to(dev)
+    post = torch.from_numpy(pos).to(dev)
+    clean = magpie.magpie_forward_intensities(torch.from_numpy(z_true.astype(np.complex64)).to(dev), Qt, post, w.m)
+    d = synth.poisson_noise(clean.cpu().numpy(), w.photons).astype(np.float32)
+    return z_true, Qt, post, torch.from_numpy(d).to(dev), d
+
+
+def oracle_windows_per_second(w, budget_s: float, min_s: float = 10.0):
+    """FP64 oracle on this host: minibatch steps of workload w until at least
+    min_s seconds have passed (bounded by budget_s); returns (windows/s,
+    windows, seconds)."""
+    from oracle import magpie_oracle as O
+    z_true, Q, pos = synth.make_problem(w)
+    clean = O.forward_intensities(z_true, Q, pos)
+    d = synth.poisson_noise(clean, w.photons)
+    u = O.rpie_regulariser(Q, w.alpha)
+    z = np.ones((w.n, w.n), dtype=np.complex128)
+    order = synth.make_order(w.n_pos, 0)
+    done, t0 = 0, time.perf_counter()
+    s = 0
+    while True:
+        batch = order[s:s + w.minibatch]
+        if len(batch) == 0:
+            s = 0
+            continue
+        z = O.minibatch_step(z, Q, pos, d, u, w.levels, batch)
+        done += len(batch)
+        s += w.minibatch
+        el = time.perf_counter() - t0
+        if el >= min_s or el >= budget_s:
+            return done / el, done, el
+
+
+def run_reference(args, w):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import magpie_oracle as O
+    z_true, Q, pos = synth.make_problem(w)
+    clean = O.forward_intensities(z_true, Q, pos)
+    d = synth.poisson_noise(clean, w.photons)
+    u = O.rpie_regulariser(Q, w.alpha)
+    z = np.ones((w.n, w.n), dtype=np.complex128)
+    per_step = 2 * w.minibatch  # a bounded sample: two minibatches per step
+    order = synth.make_order(w.n_pos, 0)
+
+    def step(i):
+        nonlocal z
+        for b in range(2):
+            s = ((2 * i + b) * w.minibatch) % w.n_pos
+            z = O.minibatch_step(z, Q, pos, d, u, w.levels, order[s:s + w.minibatch])
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step(args.warmup + i)
+    el = time.perf_counter() - t0
+    value = per_step * args.steps / el
+    line = {
+        "impl": "reference", "metric": "patterns/s per sweep", "value": value, "unit": "patterns/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(w),
+        "cpu_baseline": {"value": value, "unit": "patterns/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} windows (two minibatches) of the workload per step, "
+                                   f"FP64 NumPy oracle, {os.cpu_count()} host cores present, 1 used"},
+        "e2e": {"value": value, "unit": "patterns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_of(w):
+    return {"workload": w.name, "n": w.n, "m": w.m, "n_pos": w.n_pos, "levels": w.levels,
+            "minibatch": w.minibatch, "alpha": w.alpha, "photons_per_pattern": w.photons,
+            "parallelism": "replicas", "l2": "flushed (256 MiB write) before every timed sweep"}
+
+
+def run_ours(args, w):
+    import torch
+    from paper_2504_10118_gb300 import magpie
+
+    rank, world, local = dist_env()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    if rank == 0:
+        magpie.build()
+    if pg:
+        pg.barrier()
+    magpie.lib()
+
+    z_true, Qt, post, dt, d_host = make_data(w, dev, magpie)
+    z = torch.ones((w.n, w.n), dtype=torch.complex64, device=dev)
+    ctx = magpie.magpie_create(magpie.magpie_params_of(w.n, w.n, w.m, w.n_pos, w.levels, w.minibatch, w.alpha),
+                               z, Qt, post, dt)
+    orders = torch.from_numpy(np.stack([synth.make_order(w.n_pos, s)
+                                        for s in range(args.warmup + args.steps)])).to(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(gpu_uuid(dev))
+
+    for s in range(args.warmup):
+        magpie.magpie_sweep(ctx, orders[s])
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        flush.zero_()
+        ev0[s].record(stream)
+        magpie.magpie_sweep(ctx, orders[args.warmup + s])
+        ev1[s].record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if pg:
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    total_ms = float(t.item())
+
+    # dominant kernel: the per-window kernel, timed with events captured in
+    # the sweep graph over the same kind of sweeps
+    prof_sweeps = min(args.steps, 20)
+    wk_ms, ap_ms, launches = 0.0, 0.0, 0
+    for s in range(prof_sweeps):
+        flush.zero_()
+        a, b, n = magpie.magpie_profile_sweep(ctx, orders[args.warmup + s])
+        wk_ms += a
+        ap_ms += b
+        launches += n
+    windows = prof_sweeps * w.n_pos
+    pk, src = peaks()
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    alu_peak = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
+    achieved_tf = windows * flops_per_window(w.m) / (wk_ms * 1e-3) / 1e12
+    achieved_gbs = windows * hbm_bytes_per_window(w.m) / (wk_ms * 1e-3) / 1e9
+    traffic = measured_traffic()
+
+    # end to end through the host-buffer call: order + intensities in, object out
+    order_h = [torch.from_numpy(synth.make_order(w.n_pos, 1000 + s)).pin_memory() for s in range(args.steps)]
+    d_pin = torch.from_numpy(d_host).pin_memory()
+    z_out = torch.empty((w.n, w.n), dtype=torch.complex64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        magpie.magpie_sweep_host(ctx, order_h[s], d_pin, z_out)
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if pg:
+        pg.all_reduce(e2e_t, op=pg.ReduceOp.MAX)
+    e2e_s = float(e2e_t.item())
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, nwin, el = oracle_windows_per_second(w, budget_s=30.0)
+        cpu = {"value": v, "unit": "patterns/s", "cores": 1, "kind": "oracle",
+               "sample": f"{nwin} windows in minibatch steps of the same workload, {el:.1f} s, "
+                         f"FP64 NumPy oracle on 1 of {os.cpu_count()} host cores"}
+    ctx.close()
+    if rank == 0:
+        value = world * args.steps * w.n_pos / (total_ms * 1e-3)
+        line = {
+            "metric": "patterns/s per sweep", "value": value, "unit": "patterns/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded object, probe, raster and Poisson noise)",
+            "config": config_of(w),
+            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
+                         "frac": achieved_tf / alu_peak, "traffic": traffic,
+                         "kernel": f"window_kernel<{w.m}, step>",
+                         "avg_launch_ms": wk_ms / max(launches, 1),
+                         "peak_source": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
+                                        f"(SM max clock, {src})",
+                         "hbm_view": {"achieved": achieved_gbs, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+                                      "frac": achieved_gbs / pk.get("hbm_gbs", 6800.0)},
+                         "apply_kernel_ms_per_sweep": ap_ms / prof_sweeps,
+                         "window_kernel_ms_per_sweep": wk_ms / prof_sweeps},
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * args.steps * w.n_pos / e2e_s, "unit": "patterns/s",
+                    "h2d_bytes_per_step": 4 * w.n_pos + 4 * w.n_pos * w.m * w.m,
+                    "d2h_bytes_per_step": 8 * w.n * w.n,
+                    "call": "magpie_sweep_host (order and intensities in, object out, pinned buffers)"},
+            "gpu_launches": 2 * math.ceil(w.n_pos / w.minibatch) * args.steps,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(synth.WORKLOADS), default="mid")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    w = synth.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+    return run_ours(args, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

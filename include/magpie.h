@@ -1,0 +1,192 @@
+/*
+ * magpie.h -- C ABI of the GB300 (sm_103a) MAGPIE sweep library.
+ *
+ * MAGPIE (Multilevel-Adaptive-Guided Ptychographic Iterative Engine) solves
+ *     min_z  Phi(z) = 1/2 sum_k || Q . P_k z - R_k(P_k z) ||^2      (Eq. exit_misfit)
+ * for an object z (n_rows x n_cols, complex) from N diffraction patterns
+ * d_k = |F(Q . P_k z*)|^2 (Section 2.1), with a known probe Q (m x m,
+ * complex) and scan windows P_k (m x m sub-arrays of z whose top-left corner
+ * is positions[k] = (row, col)).  F is the unnormalised 2-D DFT,
+ * (Fx)[p,q] = sum_{a,b} x[a,b] exp(-2 pi i (pa + qb)/m), F^{-1} = F^* / m^2.
+ *
+ * One sweep visits the windows in a caller-supplied permutation (Algorithm
+ * MAGPIE), in consecutive minibatches of B windows.  For every window of a
+ * minibatch, from the same z: the exit wave Q . z_k, its FFT, the Fourier
+ * modulus projection onto sqrt(d_k), the inverse FFT (the revised exit wave
+ * R_k of Definition "Revised Exit Wave", with theta(0) := 0), and the MAGPS
+ * V-cycle of Algorithm MAGPS with the weights of Eq. (def_weights) and the
+ * rPIE regulariser u = alpha (max|Q|^2 - |Q|^2) (Section 2.1).  The
+ * increments Delta_k are combined as
+ *     z <- z + sum_k P_k^T (w . Delta_k) / sum_k P_k^T w,   w = u + |Q|^2,
+ * on pixels where the denominator is positive; for one level this is the
+ * exact minimiser of the proximal surrogate of Eq. (proximal_point_method)
+ * summed over the minibatch, and for B = 1 it is Algorithm MAGPIE itself.
+ *
+ * Data types and layouts (all row-major, no padding):
+ *   complex   : two float32, real then imaginary (C99 float _Complex,
+ *               cuComplex, torch.complex64)
+ *   object    : complex [n_rows][n_cols]
+ *   probe     : complex [m][m]
+ *   positions : int32 [n_pos][2] = (row, col) of the window's top-left pixel,
+ *               0 <= row <= n_rows - m, 0 <= col <= n_cols - m
+ *   intensities : float32 [n_pos][m][m], DFT order (zero frequency at [0][0],
+ *               no FFT shift), non-negative
+ *   order / idx : int32 permutation of, or subset of, 0 .. n_pos-1
+ *
+ * Streams: every call is ordered on the CUDA stream given at creation (a
+ * cudaStream_t passed as void*, 0 = the legacy default stream) and returns
+ * without waiting for the GPU, except where stated ("synchronous").
+ *
+ * Errors: every int-returning call returns MAGPIE_OK (0) or a negative code;
+ * magpie_strerror() names a code and magpie_last_error() gives the message of
+ * the calling thread's most recent failure.  No C++ exception crosses the
+ * ABI.  A failed call leaves the context usable unless it returned
+ * MAGPIE_ECUDA, after which only magpie_destroy() is meaningful.
+ */
+#ifndef MAGPIE_H
+#define MAGPIE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MAGPIE_OK 0
+#define MAGPIE_EINVAL (-1)      /* an argument is out of range or NULL          */
+#define MAGPIE_ECUDA (-2)       /* a CUDA runtime call or kernel launch failed  */
+#define MAGPIE_ENOMEM (-3)      /* device memory allocation failed              */
+#define MAGPIE_EUNSUPPORTED (-4)/* a valid size this build has no kernel for    */
+#define MAGPIE_EINDEX (-5)      /* a device-side window index was out of range  */
+
+typedef struct magpie_ctx magpie_ctx;
+
+typedef struct {
+  int32_t n_rows, n_cols; /* object size; both >= m                               */
+  int32_t m;              /* probe / window side: 8, 16, 32, 64 or 128             */
+  int32_t n_pos;          /* N >= 1                                                 */
+  int32_t levels;         /* grids including the finest, 1 <= levels <= log2(m)+1;
+                             1 is rPIE, L is MAGPIE_{L-1} of Section 5.1            */
+  int32_t minibatch;      /* B, 1 <= B <= min(n_pos, 4096)                          */
+  float alpha;            /* rPIE constant, finite and >= 0 (Section 2.1)           */
+} magpie_params;
+
+/*
+ * Create a reconstruction context (Algorithm MAGPIE's inputs z^(0), Q,
+ * {d_k}, u).  All pointers are DEVICE pointers owned by the caller.
+ *   object      : complex [n_rows][n_cols], read and updated in place by the
+ *                 sweep calls; must stay allocated while the context lives.
+ *   probe       : complex [m][m]; copied at creation (and by
+ *                 magpie_set_probe), not kept.
+ *   positions   : int32 [n_pos][2]; copied and range-checked at creation
+ *                 (this copies them to the host once: synchronous).
+ *   intensities : float32 [n_pos][m][m]; read once at creation, when the
+ *                 context stores the amplitudes sqrt(d_k) in its own buffer.
+ *   stream      : cudaStream_t (as void*) on which every call is ordered.
+ * The context owns its workspaces: amplitudes (4 N m^2 bytes), the per-level
+ * probe factors, the minibatch increment buffer (8 B m^2 bytes) and small
+ * per-window arrays.  Returns MAGPIE_EINVAL for bad sizes, NULL pointers or
+ * out-of-range positions, MAGPIE_EUNSUPPORTED for an m without a kernel.
+ */
+int magpie_create(magpie_ctx** out, const magpie_params* params, void* object,
+                  const void* probe, const int32_t* positions,
+                  const float* intensities, void* stream);
+
+/* Release every resource of the context (after finishing its stream work). */
+void magpie_destroy(magpie_ctx* ctx);
+
+/*
+ * One minibatch step: the windows idx[0..count-1] (DEVICE int32 array) are
+ * processed from the current object and their increments applied (the
+ * combination rule at the top of this file).  1 <= count <= minibatch.
+ * Indices outside [0, n_pos) are skipped on the device and reported as
+ * MAGPIE_EINDEX by the next synchronous call.
+ */
+int magpie_step(magpie_ctx* ctx, const int32_t* idx, int32_t count);
+
+/*
+ * One sweep (one iteration of Algorithm MAGPIE): ceil(N / B) minibatch steps
+ * over consecutive slices of order[0..n_pos-1] (DEVICE int32 permutation),
+ * the last slice possibly shorter.  The order is copied to the context
+ * first, so the caller may reuse its buffer once the stream reaches the
+ * call.  The steps replay a CUDA graph captured on the first call.
+ */
+int magpie_sweep(magpie_ctx* ctx, const int32_t* order);
+
+/*
+ * One sweep exactly as magpie_sweep, for measurement: the same kernels are
+ * launched one by one (not from the graph) with a CUDA event recorded on the
+ * context's stream before and after each of them.  Synchronous:
+ * writes the summed durations of the per-window kernel (*window_ms) and of the
+ * object-update kernel (*apply_ms) over the sweep, and the number of
+ * minibatch steps (*launches, one launch of each kernel per step), to HOST
+ * pointers (each may be NULL).
+ */
+int magpie_profile_sweep(magpie_ctx* ctx, const int32_t* order, double* window_ms, double* apply_ms,
+                         int32_t* launches);
+
+/*
+ * Phi(z) of Eq. (exit_misfit) at the current object over all N windows,
+ * accumulated in float64 (per window in float32 partial sums of at most a few
+ * dozen terms).  Synchronous: writes *phi (HOST pointer).
+ */
+int magpie_objective(magpie_ctx* ctx, double* phi);
+
+/*
+ * The stopping criterion of Section 5, (1/(N m)) sum_k || grad Phi_k(z_k) ||_2
+ * with grad Phi_k = conj(Q)(Q z_k - R_k(z_k)) (Eq. misfit_derivative), at
+ * the current object over all N windows.  Synchronous: writes *value (HOST).
+ */
+int magpie_stop_metric(magpie_ctx* ctx, double* value);
+
+/*
+ * Re-read the probe from `probe` (DEVICE complex [m][m]) and recompute the
+ * regulariser and the per-level factors (Eq. def_weights); `probe` may be
+ * the pointer given at creation after the caller changed its contents.
+ */
+int magpie_set_probe(magpie_ctx* ctx, const void* probe);
+
+/*
+ * Per-window values of the last pass over each window (from a sweep, a
+ * step or an objective/stop-metric evaluation): phi_k = Phi_k(z_k) and
+ * gnorm_k = || grad Phi_k(z_k) ||_2 at the object the window saw.
+ * Synchronous: writes HOST arrays phi[n_pos] and gnorm[n_pos] (either may
+ * be NULL).
+ */
+int magpie_window_values(magpie_ctx* ctx, double* phi, double* gnorm);
+
+/*
+ * End-to-end sweep from host memory: copies order (HOST int32[n_pos]) and,
+ * if `intensities` (HOST float32 [n_pos][m][m]) is not NULL, a new data set
+ * to the device, runs one sweep, and if `object_out` (HOST complex
+ * [n_rows][n_cols]) is not NULL copies the object back.  Synchronous.  Host
+ * buffers should be page-locked for full copy bandwidth.
+ */
+int magpie_sweep_host(magpie_ctx* ctx, const int32_t* order, const float* intensities,
+                      void* object_out);
+
+/*
+ * Forward model of Section 2.1 without noise, d_k = |F(Q . P_k z)|^2 for
+ * k = 0..n_pos-1, no context needed.  DEVICE pointers: object complex
+ * [n_rows][n_cols], probe complex [m][m], positions int32 [n_pos][2],
+ * out float32 [n_pos][m][m].  Same size limits and checks as magpie_create
+ * (positions are copied to the host for the range check: synchronous).
+ */
+int magpie_forward_intensities(const void* object, int32_t n_rows, int32_t n_cols,
+                               const void* probe, int32_t m, const int32_t* positions,
+                               int32_t n_pos, float* out, void* stream);
+
+/* Static name of an error code; never NULL. */
+const char* magpie_strerror(int code);
+
+/* Message of the calling thread's most recent failed call ("" if none). */
+const char* magpie_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int magpie_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MAGPIE_H */

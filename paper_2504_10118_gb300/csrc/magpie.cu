@@ -1,0 +1,1124 @@
+// magpie.cu -- MAGPIE sweep on one GB300 (sm_103a): kernels and the C ABI.
+//
+// Per minibatch step, one thread block per scan window k runs, entirely in
+// shared memory and registers:
+//   pass A  gather z_k, exit wave Q . z_k, column FFTs          (Section 2.1)
+//   pass B  row FFTs, Fourier modulus projection onto sqrt(d_k),
+//           inverse row FFTs                                    (Definition REW)
+//   pass C  inverse column FFTs -> R_k, then g = conj(Q)(R_k - Q z_k)
+//   pass D  the MAGPS V-cycle (Algorithm MAGPS) in residual form
+// and writes its increment w . Delta_k (w = u + |Q|^2) to a per-window
+// buffer.  A second kernel then updates every object pixel by the ordered
+// sum over the minibatch, z += sum_k w.Delta_k / sum_k w, so no atomics are
+// used and results are bitwise reproducible.
+//
+// Residual form of Algorithm MAGPS.  With the weights of Eq. (def_weights),
+// W_R . Q = (I_H^h Q_H) . W_z, so by Lemma (commutative) the coarse residual
+// R_H - Q_H z_H equals I_h^H(W_R . (R - Q z)).  Writing g^l = conj(Q^l)(R^l -
+// Q^l z^l) and w^l = u^l + |Q^l|^2 one level at a time gives
+//   g^{l+1} = W_u^l . I_h^H g^l,            (W_u^l = |Q^{l+1}|^2 / I_h^H|Q^l|^2)
+//   e^{L-1} = g^{L-1} / w^{L-1}             (coarsest proximal step)
+//   e^l     = g^l / w^l + (u^l / w^l) . I_H^h e^{l+1}   (post-smoothing)
+//   w^0 . Delta = g^0 + u^0 . I_H^h e^1,
+// where e^l is the increment of level l.  Every per-level factor is real and
+// depends on the probe only; they are computed once in float64 (Eq.
+// def_weights with the division rule: a quotient whose denominator is at most
+// 1e-30 is 0, and where w^l vanishes the step passes the coarse increment
+// through unchanged, as the proximal factor conj(Q^l)/w^l is then 0).
+//
+// FFTs: an m-point line is split over G lanes of one warp holding E = m/G
+// points each (m = E G, four-step Cooley-Tukey): an E-point DFT in registers,
+// twiddles w_m^{g k1}, an exchange through the line's own shared-memory
+// storage (XOR-swizzled so that both sides of the exchange are free of bank
+// conflicts), and G-point DFTs in registers.  The inverse transform consumes
+// the forward transform's output distribution directly (the four steps in
+// reverse), so each 2-D transform needs one smem round trip per direction.
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "magpie.h"
+
+namespace {
+
+constexpr int kVersion = 10000;  // 1.0.0
+constexpr int kMaxMinibatch = 4096;  // the update kernel keeps the minibatch's corners in smem
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return f2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return f2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return f2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return f2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+__device__ __forceinline__ float2 cmul_cj(float2 a, float2 b) {
+  return f2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+// a * w (forward) or a * conj(w) (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 twmul(float2 a, float2 w) {
+  return INV ? f2(a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y) : cmul(a, w);
+}
+
+// cos and sin of 2 pi r / 16 (exact decimal expansions of cos(pi/8),
+// cos(pi/4), sin(pi/8)); indices are compile-time after unrolling.
+__host__ __device__ constexpr float cos16(int r) {
+  return r == 0 ? 1.0f : r == 1 ? 0.92387953251128675613f : r == 2 ? 0.70710678118654752440f
+       : r == 3 ? 0.38268343236508977173f : r == 4 ? 0.0f : r == 5 ? -0.38268343236508977173f
+       : r == 6 ? -0.70710678118654752440f : r == 7 ? -0.92387953251128675613f : r == 8 ? -1.0f
+       : r == 9 ? -0.92387953251128675613f : r == 10 ? -0.70710678118654752440f
+       : r == 11 ? -0.38268343236508977173f : r == 12 ? 0.0f : r == 13 ? 0.38268343236508977173f
+       : r == 14 ? 0.70710678118654752440f : 0.92387953251128675613f;
+}
+__host__ __device__ constexpr float sin16(int r) { return cos16((r + 12) & 15); }
+
+// a * exp(-2 pi i r / 16) (forward) or exp(+2 pi i r / 16) (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 rot16(float2 a, int r) {
+  r &= 15;
+  if (r == 0) return a;
+  if (r == 8) return f2(-a.x, -a.y);
+  if (r == 4) return INV ? f2(-a.y, a.x) : f2(a.y, -a.x);
+  if (r == 12) return INV ? f2(a.y, -a.x) : f2(-a.y, a.x);
+  const float c = cos16(r);
+  const float s = INV ? sin16(r) : -sin16(r);
+  return f2(a.x * c - a.y * s, a.x * s + a.y * c);
+}
+
+template <int N>
+__host__ __device__ constexpr int bitrev(int k) {
+  int r = 0;
+  for (int b = 1; b < N; b <<= 1) {
+    r = (r << 1) | (k & 1);
+    k >>= 1;
+  }
+  return r;
+}
+
+// In-register N-point DFT (N <= 16): radix-2 decimation in frequency, then
+// the bit-reversal permutation (register renaming only).  Unnormalised.
+template <int N, bool INV>
+__device__ __forceinline__ void dft_reg(float2 (&a)[N]) {
+#pragma unroll
+  for (int len = N; len >= 2; len >>= 1) {
+    const int half = len >> 1;
+#pragma unroll
+    for (int s = 0; s < N; s += len) {
+#pragma unroll
+      for (int j = 0; j < half; ++j) {
+        const float2 u = a[s + j];
+        const float2 v = a[s + j + half];
+        a[s + j] = cadd(u, v);
+        a[s + j + half] = rot16<INV>(csub(u, v), j * (16 / len));
+      }
+    }
+  }
+  float2 b[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) b[k] = a[bitrev<N>(k)];
+#pragma unroll
+  for (int k = 0; k < N; ++k) a[k] = b[k];
+}
+
+// ------------------------------------------------------ per-size geometry
+template <int MS> struct Cfg;
+template <> struct Cfg<8> { static constexpr int E = 4, G = 2; };
+template <> struct Cfg<16> { static constexpr int E = 4, G = 4; };
+template <> struct Cfg<32> { static constexpr int E = 8, G = 4; };
+template <> struct Cfg<64> { static constexpr int E = 8, G = 8; };
+template <> struct Cfg<128> { static constexpr int E = 16, G = 8; };
+
+template <int MS> struct Geo {
+  static constexpr int E = Cfg<MS>::E;
+  static constexpr int G = Cfg<MS>::G;
+  static_assert(E * G == MS && G <= E && G <= 32, "line split");
+  static constexpr int M = MS * MS;
+  static constexpr int LANES = MS * G;  // lanes that one pass over all lines needs
+  static constexpr int T = LANES < 32 ? 32 : (LANES > 512 ? 512 : LANES);
+  static constexpr int LPT = (LANES + T - 1) / T;  // line rounds per pass
+  static constexpr int PAD = (32 / G) % 16;       // row pitch pad (complex)
+  static constexpr int SP = MS + PAD;
+  // dynamic shared memory in float2 units: S, twiddles, level scratch
+  static constexpr int LVL = (MS / 4) * (MS / 4) * 2;
+  static constexpr size_t SMEM = sizeof(float2) * (size_t(MS) * SP + MS + LVL) + sizeof(double) * 64;
+};
+
+// Forward (INV=false) m-point transform of one line whose lanes hold the
+// input x[e] = line[g + G e].  On return x[j G + k2] = X[g + G j + E k2].
+// `base`/`stride` address the line's MS slots in shared memory (used as the
+// exchange buffer); `tw[t]` = exp(-2 pi i t / MS).
+template <int MS, bool INV>
+__device__ __forceinline__ void line_fwd(float2 (&x)[Cfg<MS>::E], int g, bool act, float2* base,
+                                         int stride, const float2* tw) {
+  constexpr int E = Cfg<MS>::E, G = Cfg<MS>::G;
+  dft_reg<E, INV>(x);
+#pragma unroll
+  for (int k1 = 1; k1 < E; ++k1) x[k1] = twmul<INV>(x[k1], tw[(g * k1) & (MS - 1)]);
+  if constexpr (G > 1) {
+#pragma unroll
+    for (int k1 = 0; k1 < E; ++k1)
+      if (act) base[(k1 * G + (g ^ (k1 & (G - 1)))) * stride] = x[k1];
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < E / G; ++j) {
+      const int k1 = g + G * j;
+      float2 v[G];
+#pragma unroll
+      for (int gp = 0; gp < G; ++gp) v[gp] = act ? base[(k1 * G + (gp ^ g)) * stride] : f2(0.f, 0.f);
+      dft_reg<G, INV>(v);
+#pragma unroll
+      for (int k2 = 0; k2 < G; ++k2) x[j * G + k2] = v[k2];
+    }
+    __syncwarp();
+  }
+}
+
+// Unnormalised inverse of line_fwd: input in line_fwd's output distribution,
+// output x[e] = sum_k X[k] exp(+2 pi i k (g + G e) / MS).
+template <int MS>
+__device__ __forceinline__ void line_inv(float2 (&x)[Cfg<MS>::E], int g, bool act, float2* base,
+                                         int stride, const float2* tw) {
+  constexpr int E = Cfg<MS>::E, G = Cfg<MS>::G;
+  if constexpr (G > 1) {
+#pragma unroll
+    for (int j = 0; j < E / G; ++j) {
+      const int k1 = g + G * j;
+      float2 v[G];
+#pragma unroll
+      for (int k2 = 0; k2 < G; ++k2) v[k2] = x[j * G + k2];
+      dft_reg<G, true>(v);
+#pragma unroll
+      for (int gp = 0; gp < G; ++gp) {
+        const float2 t = gp ? twmul<true>(v[gp], tw[(gp * k1) & (MS - 1)]) : v[0];
+        if (act) base[(k1 * G + (gp ^ g)) * stride] = t;
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k1 = 0; k1 < E; ++k1)
+      x[k1] = act ? base[(k1 * G + (g ^ (k1 & (G - 1)))) * stride] : f2(0.f, 0.f);
+    __syncwarp();
+  }
+  dft_reg<E, true>(x);
+}
+
+// Offset of level-l (l >= 1) factor arrays in the float pyramid buffer:
+// [u^0: M][w^0: M] then per level l = 1.. : [W_u^{l-1}][1/w^l][u^l/w^l],
+// each (MS >> l)^2 floats.
+__host__ __device__ __forceinline__ int lvl_off(int MS, int l) {
+  int off = 2 * MS * MS;
+  for (int j = 1; j < l; ++j) off += 3 * (MS >> j) * (MS >> j);
+  return off;
+}
+__host__ __device__ __forceinline__ int pyr_size(int MS, int L) { return lvl_off(MS, L); }
+
+enum Mode { kStep = 0, kEval = 1, kSim = 2 };
+
+struct StepArgs {
+  const float2* z;    // object [n_rows][n_cols]
+  int n_rows, n_cols;
+  const float2* Q;    // probe [MS][MS]
+  const float2* tw;   // exp(-2 pi i t / MS), t < MS
+  const float* amp;   // amplitudes sqrt(d) [n_pos][MS][MS]
+  float* out_int;     // forward intensities [n_pos][MS][MS] (kSim)
+  const int32_t* pos; // [n_pos][2]
+  const int32_t* idx; // window of each block
+  int n_pos;
+  float2* contrib;    // [blocks][MS][MS] increments w . Delta
+  const float* pyr;   // per-level factors
+  int levels;
+  double* phi_pos;    // per-window Phi_k
+  double* gn_pos;     // per-window ||grad Phi_k||
+  int* err;           // bit 0: window index out of range
+};
+
+__device__ __forceinline__ double block_sum(double v, double* red, int tid, int nthreads) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (tid == 0)
+    for (int i = 0; i < nthreads / 32; ++i) r += red[i];
+  __syncthreads();
+  return r;
+}
+
+// V-cycle pass of one window: S holds g^0; blocks of 2^TT x 2^TT level-0
+// pixels are handled in registers, levels coarser than TT (if any) in the
+// smem scratch `lvl` by all threads.
+template <int MS, int TT>
+__device__ __forceinline__ void vcycle(const float2* S, float2* lvl, const float* pyr, int L,
+                                       float2* out, int tid) {
+  constexpr int BS = 1 << TT, NBS = MS >> TT, T = Geo<MS>::T, SP = Geo<MS>::SP;
+  const bool deep = (L - 1) > TT;
+  const float* u0 = pyr;
+  const float* wu1 = pyr + lvl_off(MS, 1);
+  const float* iw1 = wu1 + (MS / 2) * (MS / 2);
+  const float* rr1 = iw1 + (MS / 2) * (MS / 2);
+  const float* wu2 = pyr + lvl_off(MS, 2);
+  const float* iwT = pyr + lvl_off(MS, TT) + (MS >> TT) * (MS >> TT);
+
+  auto restrict_block = [&](int br, int bc, float2 (&g0)[BS][BS], float2 (&g1)[BS / 2][BS / 2]) -> float2 {
+#pragma unroll
+    for (int a = 0; a < BS; ++a)
+#pragma unroll
+      for (int b = 0; b < BS; ++b) g0[a][b] = S[(BS * br + a) * SP + BS * bc + b];
+#pragma unroll
+    for (int a = 0; a < BS / 2; ++a)
+#pragma unroll
+      for (int b = 0; b < BS / 2; ++b) {
+        const int r1 = (BS / 2) * br + a, c1 = (BS / 2) * bc + b;
+        const float s = 0.25f * __ldg(&wu1[r1 * (MS / 2) + c1]);
+        const float2 sum = cadd(cadd(g0[2 * a][2 * b], g0[2 * a][2 * b + 1]),
+                                cadd(g0[2 * a + 1][2 * b], g0[2 * a + 1][2 * b + 1]));
+        g1[a][b] = cscale(sum, s);
+      }
+    if constexpr (TT == 1) {
+      return g1[0][0];
+    } else {
+      const float s = 0.25f * __ldg(&wu2[br * (MS / 4) + bc]);
+      return cscale(cadd(cadd(g1[0][0], g1[0][1]), cadd(g1[1][0], g1[1][1])), s);
+    }
+  };
+
+  if (deep) {
+    // phase 1: level-TT values of every block
+    for (int blk = tid; blk < NBS * NBS; blk += T) {
+      float2 g0[BS][BS], g1[BS / 2][BS / 2];
+      lvl[blk] = restrict_block(blk / NBS, blk % NBS, g0, g1);
+    }
+    __syncthreads();
+    // phase 2: levels TT .. L-1 in shared memory, level l at lvl + off(l)
+    auto off = [](int l) {
+      int o = 0;
+      for (int j = TT; j < l; ++j) o += (MS >> j) * (MS >> j);
+      return o;
+    };
+    for (int l = TT; l < L - 1; ++l) {
+      const int s = MS >> l, sc = s >> 1;
+      const float2* fine = lvl + off(l);
+      float2* coarse = lvl + off(l + 1);
+      const float* wu = pyr + lvl_off(MS, l + 1);
+      for (int i = tid; i < sc * sc; i += T) {
+        const int r = i / sc, c = i - (i / sc) * sc;
+        const float2 sum = cadd(cadd(fine[(2 * r) * s + 2 * c], fine[(2 * r) * s + 2 * c + 1]),
+                                cadd(fine[(2 * r + 1) * s + 2 * c], fine[(2 * r + 1) * s + 2 * c + 1]));
+        coarse[i] = cscale(sum, 0.25f * __ldg(&wu[i]));
+      }
+      __syncthreads();
+    }
+    {
+      const int l = L - 1, s = MS >> l;
+      float2* a = lvl + off(l);
+      const float* iw = pyr + lvl_off(MS, l) + s * s;
+      for (int i = tid; i < s * s; i += T) a[i] = cscale(a[i], __ldg(&iw[i]));
+      __syncthreads();
+    }
+    for (int l = L - 2; l >= TT; --l) {
+      const int s = MS >> l, sc = s >> 1;
+      float2* a = lvl + off(l);
+      const float2* p = lvl + off(l + 1);
+      const float* iw = pyr + lvl_off(MS, l) + s * s;
+      const float* rr = iw + s * s;
+      for (int i = tid; i < s * s; i += T) {
+        const int r = i / s, c = i - (i / s) * s;
+        const float2 pe = p[(r >> 1) * sc + (c >> 1)];
+        const float2 v = cscale(a[i], __ldg(&iw[i]));
+        const float q = __ldg(&rr[i]);
+        a[i] = f2(v.x + q * pe.x, v.y + q * pe.y);
+      }
+      __syncthreads();
+    }
+  }
+  // phase 3: up-pass inside each block and the increments w . Delta
+  for (int blk = tid; blk < NBS * NBS; blk += T) {
+    const int br = blk / NBS, bc = blk - (blk / NBS) * NBS;
+    float2 g0[BS][BS], g1[BS / 2][BS / 2];
+    const float2 gT = restrict_block(br, bc, g0, g1);
+    const float2 eT = deep ? lvl[blk] : cscale(gT, __ldg(&iwT[blk]));
+    float2 e1[BS / 2][BS / 2];
+    if constexpr (TT == 1) {
+      e1[0][0] = eT;
+    } else {
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          const int o = (2 * br + a) * (MS / 2) + 2 * bc + b;
+          const float2 v = cscale(g1[a][b], __ldg(&iw1[o]));
+          const float q = __ldg(&rr1[o]);
+          e1[a][b] = f2(v.x + q * eT.x, v.y + q * eT.y);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < BS; ++a)
+#pragma unroll
+      for (int b = 0; b < BS; ++b) {
+        const int o = (BS * br + a) * MS + BS * bc + b;
+        const float u = __ldg(&u0[o]);
+        const float2 ep = e1[a >> 1][b >> 1];
+        out[o] = f2(g0[a][b].x + u * ep.x, g0[a][b].y + u * ep.y);
+      }
+  }
+}
+
+// One thread block per window.  Launch with Geo<MS>::T threads and
+// Geo<MS>::SMEM bytes of dynamic shared memory.
+template <int MS, int MODE>
+__global__ void __launch_bounds__(Geo<MS>::T) window_kernel(StepArgs A) {
+  using Gm = Geo<MS>;
+  constexpr int E = Gm::E, G = Gm::G, T = Gm::T, SP = Gm::SP, M = Gm::M;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* S = reinterpret_cast<float2*>(smem_raw);
+  float2* tws = S + MS * SP;
+  float2* lvl = tws + MS;
+  double* red = reinterpret_cast<double*>(lvl + Gm::LVL);
+
+  const int tid = threadIdx.x;
+  const int k = A.idx[blockIdx.x];
+  if ((unsigned)k >= (unsigned)A.n_pos) {
+    if (tid == 0) atomicOr(A.err, 1);
+    return;  // uniform across the block
+  }
+  const int pr = A.pos[2 * k], pc = A.pos[2 * k + 1];
+  const float2* zk = A.z + (size_t)pr * A.n_cols + pc;
+  for (int i = tid; i < MS; i += T) tws[i] = A.tw[i];
+  __syncthreads();
+
+  // ---- pass A: exit wave and column FFTs
+#pragma unroll
+  for (int it = 0; it < Gm::LPT; ++it) {
+    const int ln = it * T + tid;
+    const bool act = ln < Gm::LANES;
+    const int c = act ? ln / G : 0, g = ln % G;
+    float2 x[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int r = g + G * e;
+      x[e] = act ? cmul(__ldg(&A.Q[r * MS + c]), __ldg(&zk[(size_t)r * A.n_cols + c])) : f2(0.f, 0.f);
+    }
+    line_fwd<MS, false>(x, g, act, S + c, SP, tws);
+#pragma unroll
+    for (int j = 0; j < E / G; ++j)
+#pragma unroll
+      for (int k2 = 0; k2 < G; ++k2)
+        if (act) S[(g + G * j + E * k2) * SP + c] = x[j * G + k2];
+  }
+  __syncthreads();
+
+  // ---- pass B: row FFTs, modulus projection, inverse row FFTs
+  float res = 0.f;
+  const float* ampk = A.amp + (size_t)k * M;
+#pragma unroll
+  for (int it = 0; it < Gm::LPT; ++it) {
+    const int ln = it * T + tid;
+    const bool act = ln < Gm::LANES;
+    const int kr = act ? ln / G : 0, g = ln % G;
+    float2* row = S + kr * SP;
+    float2 x[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = act ? row[g + G * e] : f2(0.f, 0.f);
+    __syncwarp();
+    line_fwd<MS, false>(x, g, act, row, 1, tws);
+    if constexpr (MODE == kSim) {
+      float* outk = A.out_int + (size_t)k * M + kr * MS;
+#pragma unroll
+      for (int j = 0; j < E / G; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < G; ++k2) {
+          const float2 P = x[j * G + k2];
+          if (act) outk[g + G * j + E * k2] = P.x * P.x + P.y * P.y;
+        }
+    } else {
+      constexpr float inv_m = 1.0f / float(M);
+#pragma unroll
+      for (int j = 0; j < E / G; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < G; ++k2) {
+          const float a = act ? __ldg(&ampk[kr * MS + g + G * j + E * k2]) : 0.f;
+          const float2 P = x[j * G + k2];
+          const float p2 = P.x * P.x + P.y * P.y;
+          float mag;
+          float2 Pp;
+          if (p2 > 0.f) {
+            const float rs = rsqrtf(p2);
+            mag = p2 * rs;
+            const float s = a * rs * inv_m;
+            Pp = f2(P.x * s, P.y * s);
+          } else {
+            mag = 0.f;
+            Pp = f2(a * inv_m, 0.f);
+          }
+          const float dlt = mag - a;
+          res += dlt * dlt;
+          x[j * G + k2] = Pp;
+        }
+      line_inv<MS>(x, g, act, row, 1, tws);
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (act) row[g + G * e] = x[e];
+    }
+  }
+  if constexpr (MODE == kSim) return;
+  __syncthreads();
+
+  // ---- pass C: inverse column FFTs, R_k, g = conj(Q)(R_k - Q z_k)
+  float gn2 = 0.f;
+  float2* out = A.contrib + (size_t)blockIdx.x * M;
+  const bool direct = (MODE == kStep) && A.levels == 1;
+#pragma unroll
+  for (int it = 0; it < Gm::LPT; ++it) {
+    const int ln = it * T + tid;
+    const bool act = ln < Gm::LANES;
+    const int c = act ? ln / G : 0, g = ln % G;
+    float2 x[E];
+#pragma unroll
+    for (int j = 0; j < E / G; ++j)
+#pragma unroll
+      for (int k2 = 0; k2 < G; ++k2) x[j * G + k2] = act ? S[(g + G * j + E * k2) * SP + c] : f2(0.f, 0.f);
+    __syncwarp();
+    line_inv<MS>(x, g, act, S + c, SP, tws);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int r = g + G * e;
+      if (act) {
+        const float2 q = __ldg(&A.Q[r * MS + c]);
+        const float2 zz = __ldg(&zk[(size_t)r * A.n_cols + c]);
+        const float2 rho = csub(x[e], cmul(q, zz));
+        const float2 gg = cmul_cj(q, rho);
+        gn2 += gg.x * gg.x + gg.y * gg.y;
+        if (direct)
+          out[r * MS + c] = gg;
+        else
+          S[r * SP + c] = gg;
+      }
+    }
+  }
+
+  // per-window objective and gradient norm (float64 across the block)
+  const double rs = block_sum((double)res, red, tid, T);
+  const double gs = block_sum((double)gn2, red, tid, T);
+  if (tid == 0) {
+    A.phi_pos[k] = rs / (2.0 * (double)M);
+    A.gn_pos[k] = sqrt(gs);
+  }
+  if (MODE != kStep || direct) return;
+
+  // ---- pass D: MAGPS V-cycle (levels >= 2); block_sum synchronised S
+  if (A.levels == 2)
+    vcycle<MS, 1>(S, lvl, A.pyr, A.levels, out, tid);
+  else
+    vcycle<MS, 2>(S, lvl, A.pyr, A.levels, out, tid);
+}
+
+// z += sum_b contrib_b / sum_b w0 over the windows covering each pixel, in
+// minibatch order (bitwise reproducible).
+__global__ void apply_kernel(float2* z, int n_rows, int n_cols, const int32_t* pos, const int32_t* idx,
+                             int count, int n_pos, const float2* contrib, const float* w0, int MS) {
+  extern __shared__ int2 bp[];
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    const int k = idx[i];
+    bp[i] = ((unsigned)k < (unsigned)n_pos) ? make_int2(pos[2 * k], pos[2 * k + 1])
+                                            : make_int2(-(1 << 30), -(1 << 30));
+  }
+  __syncthreads();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_rows * n_cols) return;
+  const int r = p / n_cols, c = p - (p / n_cols) * n_cols;
+  float nx = 0.f, ny = 0.f, d = 0.f;
+  for (int b = 0; b < count; ++b) {
+    const int dr = r - bp[b].x, dc = c - bp[b].y;
+    if ((unsigned)dr < (unsigned)MS && (unsigned)dc < (unsigned)MS) {
+      const int o = dr * MS + dc;
+      const float2 v = contrib[(size_t)b * MS * MS + o];
+      nx += v.x;
+      ny += v.y;
+      d += __ldg(&w0[o]);
+    }
+  }
+  if (d > 0.f) {
+    float2 zz = z[p];
+    zz.x += nx / d;
+    zz.y += ny / d;
+    z[p] = zz;
+  }
+}
+
+__global__ void sqrt_kernel(const float* d, float* a, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    a[i] = sqrtf(fmaxf(d[i], 0.f));
+}
+
+// Per-level probe factors in float64 (Eq. def_weights and the rPIE
+// regulariser), one block.  scratch: complex levels of Q and real levels of
+// u, each laid out level after level.
+__global__ void __launch_bounds__(1024) pyramid_kernel(const float2* Q, int MS, int L, float alpha, double2* qs, double* us,
+                               float* pyr) {
+  __shared__ double red[32];
+  const int tid = threadIdx.x, T = blockDim.x;
+  const int M = MS * MS;
+  constexpr double kTiny = 1e-30;
+  double mx = 0.0;
+  for (int i = tid; i < M; i += T) {
+    const float2 q = Q[i];
+    qs[i] = make_double2(q.x, q.y);
+    mx = fmax(mx, (double)q.x * q.x + (double)q.y * q.y);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  if ((tid & 31) == 0) red[tid >> 5] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0.0;
+    for (int i = 0; i < T / 32; ++i) m = fmax(m, red[i]);
+    red[0] = m;
+  }
+  __syncthreads();
+  mx = red[0];
+  for (int i = tid; i < M; i += T) {
+    const double a2 = qs[i].x * qs[i].x + qs[i].y * qs[i].y;
+    const double u = (double)alpha * (mx - a2);
+    us[i] = u;
+    pyr[i] = (float)u;
+    pyr[M + i] = (float)(u + a2);
+  }
+  __syncthreads();
+  int qoff = 0;
+  for (int l = 1; l < L; ++l) {
+    const int sf = MS >> (l - 1), s = MS >> l;
+    const int noff = qoff + sf * sf;
+    float* wu = pyr + lvl_off(MS, l);
+    float* iw = wu + s * s;
+    float* rr = iw + s * s;
+    for (int i = tid; i < s * s; i += T) {
+      const int r = i / s, c = i % s;
+      double2 qm = make_double2(0.0, 0.0);
+      double sa = 0.0, um = 0.0;
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+          const int o = qoff + (2 * r + a) * sf + 2 * c + b;
+          qm.x += qs[o].x;
+          qm.y += qs[o].y;
+          sa += qs[o].x * qs[o].x + qs[o].y * qs[o].y;
+          um += us[o];
+        }
+      qm.x *= 0.25;
+      qm.y *= 0.25;
+      sa *= 0.25;
+      um *= 0.25;
+      const double qh2 = qm.x * qm.x + qm.y * qm.y;
+      const double w_u = sa > kTiny ? qh2 / sa : 0.0;
+      const double uh = w_u * um;
+      const double wh = uh + qh2;
+      qs[noff + i] = qm;
+      us[noff + i] = uh;
+      wu[i] = (float)w_u;
+      iw[i] = wh > kTiny ? (float)(1.0 / wh) : 0.f;
+      rr[i] = wh > kTiny ? (float)(uh / wh) : 1.f;
+    }
+    qoff = noff;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(1024) reduce_kernel(const double* phi, const double* gn, int n, double* out) {
+  __shared__ double red[32];
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    a += phi[i];
+    b += gn[i];
+  }
+  const int T = blockDim.x, tid = threadIdx.x;
+  for (int pass = 0; pass < 2; ++pass) {
+    double v = pass ? b : a;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+      double r = 0.0;
+      for (int i = 0; i < T / 32; ++i) r += red[i];
+      out[pass] = r;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void iota_kernel(int32_t* a, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = i;
+}
+
+// ------------------------------------------------------------- host side
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                      \
+  do {                                                                                      \
+    cudaError_t e_ = (expr);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail(e_ == cudaErrorMemoryAllocation ? MAGPIE_ENOMEM : MAGPIE_ECUDA,           \
+                  std::string(#expr) + ": " + cudaGetErrorString(e_));                      \
+  } while (0)
+
+bool supported_m(int m) { return m == 8 || m == 16 || m == 32 || m == 64 || m == 128; }
+
+int ilog2(int v) {
+  int r = 0;
+  while ((1 << r) < v) ++r;
+  return r;
+}
+
+template <int MS, int MODE>
+cudaError_t launch_window(const StepArgs& a, int blocks, cudaStream_t st) {
+  window_kernel<MS, MODE><<<blocks, Geo<MS>::T, Geo<MS>::SMEM, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_window_m(int MS, const StepArgs& a, int blocks, cudaStream_t st) {
+  switch (MS) {
+    case 8: return launch_window<8, MODE>(a, blocks, st);
+    case 16: return launch_window<16, MODE>(a, blocks, st);
+    case 32: return launch_window<32, MODE>(a, blocks, st);
+    case 64: return launch_window<64, MODE>(a, blocks, st);
+    case 128: return launch_window<128, MODE>(a, blocks, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Opt the window kernels of one size into their dynamic shared memory; done
+// before any launch (and so outside stream capture).
+template <int MS>
+cudaError_t prepare_size() {
+  const int bytes = (int)Geo<MS>::SMEM;
+  cudaError_t e = cudaFuncSetAttribute(window_kernel<MS, kStep>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(window_kernel<MS, kEval>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(window_kernel<MS, kSim>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
+}
+
+cudaError_t prepare_kernels(int MS) {
+  switch (MS) {
+    case 8: return prepare_size<8>();
+    case 16: return prepare_size<16>();
+    case 32: return prepare_size<32>();
+    case 64: return prepare_size<64>();
+    case 128: return prepare_size<128>();
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int check_positions(const int32_t* host_pos, int n_pos, int n_rows, int n_cols, int m) {
+  for (int k = 0; k < n_pos; ++k) {
+    const int r = host_pos[2 * k], c = host_pos[2 * k + 1];
+    if (r < 0 || c < 0 || r > n_rows - m || c > n_cols - m)
+      return fail(MAGPIE_EINVAL, "position " + std::to_string(k) + " = (" + std::to_string(r) + ", " +
+                                     std::to_string(c) + ") puts the window outside the object");
+  }
+  return MAGPIE_OK;
+}
+
+}  // namespace
+
+struct magpie_ctx {
+  magpie_params p{};
+  int M = 0;
+  float2* z = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  float2* Q = nullptr;
+  float2* tw = nullptr;
+  float* amp = nullptr;
+  float* stage = nullptr;  // host-sweep intensity staging
+  int32_t* pos = nullptr;
+  float* pyr = nullptr;
+  double2* pyr_q = nullptr;
+  double* pyr_u = nullptr;
+  float2* contrib = nullptr;
+  double* phi_pos = nullptr;
+  double* gn_pos = nullptr;
+  int32_t* iota = nullptr;
+  int32_t* order = nullptr;
+  double* sums = nullptr;
+  int* err = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<cudaEvent_t> events;  // 4 per minibatch step (magpie_profile_sweep)
+};
+
+namespace {
+
+StepArgs make_args(magpie_ctx* c, const int32_t* idx) {
+  StepArgs a{};
+  a.z = c->z;
+  a.n_rows = c->p.n_rows;
+  a.n_cols = c->p.n_cols;
+  a.Q = c->Q;
+  a.tw = c->tw;
+  a.amp = c->amp;
+  a.out_int = nullptr;
+  a.pos = c->pos;
+  a.idx = idx;
+  a.n_pos = c->p.n_pos;
+  a.contrib = c->contrib;
+  a.pyr = c->pyr;
+  a.levels = c->p.levels;
+  a.phi_pos = c->phi_pos;
+  a.gn_pos = c->gn_pos;
+  a.err = c->err;
+  return a;
+}
+
+// ev (optional): four events recorded before/after the window kernel and
+// before/after the apply kernel.
+int enqueue_step(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st, const cudaEvent_t* ev = nullptr) {
+  StepArgs a = make_args(c, idx);
+  if (ev) CUDA_TRY(cudaEventRecord(ev[0], st));
+  CUDA_TRY(launch_window_m<kStep>(c->p.m, a, count, st));
+  if (ev) CUDA_TRY(cudaEventRecord(ev[1], st));
+  const int n = c->p.n_rows * c->p.n_cols;
+  const int T = 256;
+  if (ev) CUDA_TRY(cudaEventRecord(ev[2], st));
+  apply_kernel<<<(n + T - 1) / T, T, sizeof(int2) * count, st>>>(c->z, c->p.n_rows, c->p.n_cols, c->pos, idx,
+                                                                  count, c->p.n_pos, c->contrib, c->pyr + c->M,
+                                                                  c->p.m);
+  CUDA_TRY(cudaGetLastError());
+  if (ev) CUDA_TRY(cudaEventRecord(ev[3], st));
+  return MAGPIE_OK;
+}
+
+int build_pyramid(magpie_ctx* c, const void* probe) {
+  CUDA_TRY(cudaMemcpyAsync(c->Q, probe, sizeof(float2) * c->M, cudaMemcpyDeviceToDevice, c->stream));
+  pyramid_kernel<<<1, 1024, 0, c->stream>>>(c->Q, c->p.m, c->p.levels, c->p.alpha, c->pyr_q, c->pyr_u, c->pyr);
+  CUDA_TRY(cudaGetLastError());
+  return MAGPIE_OK;
+}
+
+int read_err(magpie_ctx* c) {
+  int h = 0;
+  CUDA_TRY(cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (h) {
+    CUDA_TRY(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+    return fail(MAGPIE_EINDEX, "a window index passed to a step or sweep was outside [0, n_pos)");
+  }
+  return MAGPIE_OK;
+}
+
+int evaluate(magpie_ctx* c, double* phi, double* stop) {
+  StepArgs a = make_args(c, c->iota);
+  CUDA_TRY(launch_window_m<kEval>(c->p.m, a, c->p.n_pos, c->stream));
+  reduce_kernel<<<1, 1024, 0, c->stream>>>(c->phi_pos, c->gn_pos, c->p.n_pos, c->sums);
+  CUDA_TRY(cudaGetLastError());
+  double h[2];
+  CUDA_TRY(cudaMemcpyAsync(h, c->sums, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  int rc = read_err(c);
+  if (rc) return rc;
+  if (phi) *phi = h[0];
+  if (stop) *stop = h[1] / ((double)c->p.n_pos * (double)c->p.m);
+  return MAGPIE_OK;
+}
+
+int n_steps(const magpie_ctx* c) { return (c->p.n_pos + c->p.minibatch - 1) / c->p.minibatch; }
+
+// Replays (capturing it on first use) the graph of one sweep over the
+// permutation already in c->order.
+int launch_sweep(magpie_ctx* c) {
+  const int N = c->p.n_pos, B = c->p.minibatch;
+  if (!c->graph) {
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = MAGPIE_OK;
+    for (int s = 0; s < N && rc == MAGPIE_OK; s += B)
+      rc = enqueue_step(c, c->order + s, N - s < B ? N - s : B, c->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    CUDA_TRY(e);
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    CUDA_TRY(e);
+  }
+  CUDA_TRY(cudaGraphLaunch(c->graph, c->stream));
+  return MAGPIE_OK;
+}
+
+int validate(const magpie_params* p) {
+  if (!p) return fail(MAGPIE_EINVAL, "params is NULL");
+  if (p->m < 1 || (p->m & (p->m - 1)))
+    return fail(MAGPIE_EINVAL, "m = " + std::to_string(p->m) + " is not a power of two");
+  if (!supported_m(p->m))
+    return fail(MAGPIE_EUNSUPPORTED, "no kernel for m = " + std::to_string(p->m) + " (8..128)");
+  if (p->n_rows < p->m || p->n_cols < p->m) return fail(MAGPIE_EINVAL, "object smaller than the window");
+  if ((long long)p->n_rows * p->n_cols > (1LL << 30)) return fail(MAGPIE_EINVAL, "object larger than 2^30 pixels");
+  if (p->n_pos < 1) return fail(MAGPIE_EINVAL, "n_pos < 1");
+  if (p->levels < 1 || p->levels > ilog2(p->m) + 1)
+    return fail(MAGPIE_EINVAL, "levels must lie in [1, log2(m) + 1]");
+  if (p->minibatch < 1 || p->minibatch > p->n_pos || p->minibatch > kMaxMinibatch)
+    return fail(MAGPIE_EINVAL, "minibatch must lie in [1, min(n_pos, 4096)]");
+  if (!(p->alpha >= 0.f) || !std::isfinite(p->alpha)) return fail(MAGPIE_EINVAL, "alpha must be finite and >= 0");
+  return MAGPIE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int magpie_version(void) { return kVersion; }
+
+const char* magpie_strerror(int code) {
+  switch (code) {
+    case MAGPIE_OK: return "success";
+    case MAGPIE_EINVAL: return "invalid argument";
+    case MAGPIE_ECUDA: return "CUDA error";
+    case MAGPIE_ENOMEM: return "out of device memory";
+    case MAGPIE_EUNSUPPORTED: return "unsupported size";
+    case MAGPIE_EINDEX: return "window index out of range";
+    default: return "unknown error";
+  }
+}
+
+const char* magpie_last_error(void) { return g_last_error.c_str(); }
+
+void magpie_destroy(magpie_ctx* c) {
+  if (!c) return;
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (auto e : c->events)
+    if (e) cudaEventDestroy(e);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  void* bufs[] = {c->Q, c->tw, c->amp, c->stage, c->pos, c->pyr, c->pyr_q, c->pyr_u, c->contrib,
+                  c->phi_pos, c->gn_pos, c->iota, c->order, c->sums, c->err};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  delete c;
+}
+
+int magpie_create(magpie_ctx** out, const magpie_params* params, void* object, const void* probe,
+                  const int32_t* positions, const float* intensities, void* stream) {
+  if (!out) return fail(MAGPIE_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate(params);
+  if (rc) return rc;
+  if (!object || !probe || !positions || !intensities) return fail(MAGPIE_EINVAL, "a data pointer is NULL");
+  const magpie_params& p = *params;
+  std::vector<int32_t> hpos(2 * (size_t)p.n_pos);
+  cudaStream_t st = (cudaStream_t)stream;
+  CUDA_TRY(cudaMemcpyAsync(hpos.data(), positions, sizeof(int32_t) * hpos.size(), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  rc = check_positions(hpos.data(), p.n_pos, p.n_rows, p.n_cols, p.m);
+  if (rc) return rc;
+
+  magpie_ctx* c = new magpie_ctx();
+  c->p = p;
+  c->M = p.m * p.m;
+  c->z = (float2*)object;
+  c->stream = st;
+  const size_t M = c->M, N = p.n_pos;
+  auto alloc = [&](void** ptr, size_t bytes) -> int {
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+      magpie_destroy(c);
+      return fail(e == cudaErrorMemoryAllocation ? MAGPIE_ENOMEM : MAGPIE_ECUDA,
+                  std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    return MAGPIE_OK;
+  };
+  if ((rc = alloc((void**)&c->Q, sizeof(float2) * M)) || (rc = alloc((void**)&c->tw, sizeof(float2) * p.m)) ||
+      (rc = alloc((void**)&c->amp, sizeof(float) * M * N)) || (rc = alloc((void**)&c->pos, sizeof(int32_t) * 2 * N)) ||
+      (rc = alloc((void**)&c->pyr, sizeof(float) * pyr_size(p.m, p.levels))) ||
+      (rc = alloc((void**)&c->pyr_q, sizeof(double2) * 2 * M)) || (rc = alloc((void**)&c->pyr_u, sizeof(double) * 2 * M)) ||
+      (rc = alloc((void**)&c->contrib, sizeof(float2) * M * p.minibatch)) ||
+      (rc = alloc((void**)&c->phi_pos, sizeof(double) * N)) || (rc = alloc((void**)&c->gn_pos, sizeof(double) * N)) ||
+      (rc = alloc((void**)&c->iota, sizeof(int32_t) * N)) || (rc = alloc((void**)&c->order, sizeof(int32_t) * N)) ||
+      (rc = alloc((void**)&c->sums, sizeof(double) * 2)) || (rc = alloc((void**)&c->err, sizeof(int))))
+    return rc;
+
+  auto cleanup_fail = [&](int code) {
+    magpie_destroy(c);
+    return code;
+  };
+#define CTX_TRY(expr)                                                                          \
+  do {                                                                                         \
+    cudaError_t e_ = (expr);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return cleanup_fail(fail(MAGPIE_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_))); \
+  } while (0)
+  CTX_TRY(prepare_kernels(p.m));
+  CTX_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  std::vector<float2> htw(p.m);
+  for (int t = 0; t < p.m; ++t) {
+    const double ang = -2.0 * 3.14159265358979323846 * (double)t / (double)p.m;
+    htw[t] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+  }
+  CTX_TRY(cudaMemcpyAsync(c->tw, htw.data(), sizeof(float2) * p.m, cudaMemcpyHostToDevice, st));
+  CTX_TRY(cudaMemcpyAsync(c->pos, positions, sizeof(int32_t) * 2 * N, cudaMemcpyDeviceToDevice, st));
+  CTX_TRY(cudaMemsetAsync(c->err, 0, sizeof(int), st));
+  CTX_TRY(cudaMemsetAsync(c->phi_pos, 0, sizeof(double) * N, st));
+  CTX_TRY(cudaMemsetAsync(c->gn_pos, 0, sizeof(double) * N, st));
+  iota_kernel<<<(int)((N + 255) / 256), 256, 0, st>>>(c->iota, (int)N);
+  CTX_TRY(cudaGetLastError());
+  sqrt_kernel<<<1024, 256, 0, st>>>(intensities, c->amp, M * N);
+  CTX_TRY(cudaGetLastError());
+  rc = build_pyramid(c, probe);
+  if (rc) return cleanup_fail(rc);
+  CTX_TRY(cudaStreamSynchronize(st));
+#undef CTX_TRY
+  *out = c;
+  return MAGPIE_OK;
+}
+
+int magpie_set_probe(magpie_ctx* c, const void* probe) {
+  if (!c || !probe) return fail(MAGPIE_EINVAL, "NULL argument");
+  return build_pyramid(c, probe);
+}
+
+int magpie_step(magpie_ctx* c, const int32_t* idx, int32_t count) {
+  if (!c || !idx) return fail(MAGPIE_EINVAL, "NULL argument");
+  if (count < 1 || count > c->p.minibatch) return fail(MAGPIE_EINVAL, "count must lie in [1, minibatch]");
+  return enqueue_step(c, idx, count, c->stream);
+}
+
+int magpie_sweep(magpie_ctx* c, const int32_t* order) {
+  if (!c || !order) return fail(MAGPIE_EINVAL, "NULL argument");
+  CUDA_TRY(cudaMemcpyAsync(c->order, order, sizeof(int32_t) * c->p.n_pos, cudaMemcpyDeviceToDevice, c->stream));
+  return launch_sweep(c);
+}
+
+int magpie_profile_sweep(magpie_ctx* c, const int32_t* order, double* window_ms, double* apply_ms,
+                         int32_t* launches) {
+  if (!c || !order) return fail(MAGPIE_EINVAL, "NULL argument");
+  CUDA_TRY(cudaMemcpyAsync(c->order, order, sizeof(int32_t) * c->p.n_pos, cudaMemcpyDeviceToDevice, c->stream));
+  if (c->events.empty()) {
+    c->events.resize(4 * (size_t)n_steps(c), nullptr);
+    for (auto& e : c->events) CUDA_TRY(cudaEventCreate(&e));
+  }
+  const int N = c->p.n_pos, B = c->p.minibatch;
+  for (int s = 0, i = 0; s < N; s += B, ++i) {
+    int rc = enqueue_step(c, c->order + s, N - s < B ? N - s : B, c->stream, &c->events[4 * (size_t)i]);
+    if (rc) return rc;
+  }
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  double wsum = 0.0, asum = 0.0;
+  for (int i = 0; i < n_steps(c); ++i) {
+    float a = 0.f, b = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&a, c->events[4 * i], c->events[4 * i + 1]));
+    CUDA_TRY(cudaEventElapsedTime(&b, c->events[4 * i + 2], c->events[4 * i + 3]));
+    wsum += a;
+    asum += b;
+  }
+  if (window_ms) *window_ms = wsum;
+  if (apply_ms) *apply_ms = asum;
+  if (launches) *launches = n_steps(c);
+  return read_err(c);
+}
+
+int magpie_objective(magpie_ctx* c, double* phi) {
+  if (!c || !phi) return fail(MAGPIE_EINVAL, "NULL argument");
+  return evaluate(c, phi, nullptr);
+}
+
+int magpie_stop_metric(magpie_ctx* c, double* value) {
+  if (!c || !value) return fail(MAGPIE_EINVAL, "NULL argument");
+  return evaluate(c, nullptr, value);
+}
+
+int magpie_window_values(magpie_ctx* c, double* phi, double* gnorm) {
+  if (!c) return fail(MAGPIE_EINVAL, "NULL argument");
+  const size_t N = c->p.n_pos;
+  if (phi) CUDA_TRY(cudaMemcpyAsync(phi, c->phi_pos, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream));
+  if (gnorm) CUDA_TRY(cudaMemcpyAsync(gnorm, c->gn_pos, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream));
+  return read_err(c);
+}
+
+int magpie_sweep_host(magpie_ctx* c, const int32_t* order, const float* intensities, void* object_out) {
+  if (!c || !order) return fail(MAGPIE_EINVAL, "NULL argument");
+  const size_t N = c->p.n_pos, M = c->M;
+  if (intensities) {
+    if (!c->stage) CUDA_TRY(cudaMalloc((void**)&c->stage, sizeof(float) * N * M));
+    CUDA_TRY(cudaMemcpyAsync(c->stage, intensities, sizeof(float) * N * M, cudaMemcpyHostToDevice, c->stream));
+    sqrt_kernel<<<1024, 256, 0, c->stream>>>(c->stage, c->amp, N * M);
+    CUDA_TRY(cudaGetLastError());
+  }
+  CUDA_TRY(cudaMemcpyAsync(c->order, order, sizeof(int32_t) * N, cudaMemcpyHostToDevice, c->stream));
+  int rc = launch_sweep(c);
+  if (rc) return rc;
+  if (object_out)
+    CUDA_TRY(cudaMemcpyAsync(object_out, c->z, sizeof(float2) * (size_t)c->p.n_rows * c->p.n_cols,
+                             cudaMemcpyDeviceToHost, c->stream));
+  return read_err(c);
+}
+
+int magpie_forward_intensities(const void* object, int32_t n_rows, int32_t n_cols, const void* probe, int32_t m,
+                               const int32_t* positions, int32_t n_pos, float* out, void* stream) {
+  magpie_params p{};
+  p.n_rows = n_rows;
+  p.n_cols = n_cols;
+  p.m = m;
+  p.n_pos = n_pos;
+  p.levels = 1;
+  p.minibatch = 1;
+  p.alpha = 0.f;
+  int rc = validate(&p);
+  if (rc) return rc;
+  if (!object || !probe || !positions || !out) return fail(MAGPIE_EINVAL, "a data pointer is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int32_t> hpos(2 * (size_t)n_pos);
+  CUDA_TRY(cudaMemcpyAsync(hpos.data(), positions, sizeof(int32_t) * hpos.size(), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  rc = check_positions(hpos.data(), n_pos, n_rows, n_cols, m);
+  if (rc) return rc;
+  CUDA_TRY(prepare_kernels(m));
+  float2* tw = nullptr;
+  int32_t* iota = nullptr;
+  CUDA_TRY(cudaMalloc((void**)&tw, sizeof(float2) * m));
+  cudaError_t e = cudaMalloc((void**)&iota, sizeof(int32_t) * n_pos);
+  if (e != cudaSuccess) {
+    cudaFree(tw);
+    CUDA_TRY(e);
+  }
+  std::vector<float2> htw(m);
+  for (int t = 0; t < m; ++t) {
+    const double ang = -2.0 * 3.14159265358979323846 * (double)t / (double)m;
+    htw[t] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+  }
+  StepArgs a{};
+  a.z = (const float2*)object;
+  a.n_rows = n_rows;
+  a.n_cols = n_cols;
+  a.Q = (const float2*)probe;
+  a.tw = tw;
+  a.out_int = out;
+  a.pos = positions;
+  a.idx = iota;
+  a.n_pos = n_pos;
+  a.levels = 1;
+  e = cudaMemcpyAsync(tw, htw.data(), sizeof(float2) * m, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    iota_kernel<<<(n_pos + 255) / 256, 256, 0, st>>>(iota, n_pos);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = launch_window_m<kSim>(m, a, n_pos, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(tw);
+  cudaFree(iota);
+  CUDA_TRY(e);
+  return MAGPIE_OK;
+}
+
+}  // extern "C"

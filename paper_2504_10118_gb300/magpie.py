@@ -1,0 +1,227 @@
+"""ctypes binding of the MAGPIE sweep library (include/magpie.h).
+
+Argument marshalling only: every function forwards to the C function of the
+same name in the in-tree shared library, passing raw device pointers of
+torch tensors and the current CUDA stream.  There is no Python or CPU
+implementation behind these calls; when the library has not been built the
+first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+BUILD_DIR = os.path.join(HERE, "_build")
+LIB_PATH = os.path.join(BUILD_DIR, "libmagpie.so")
+SOURCES = [os.path.join(HERE, "csrc", "magpie.cu")]
+HEADER = os.path.join(ROOT, "include", "magpie.h")
+NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
+              "-Xcompiler", "-fPIC", "-shared"]
+
+OK, EINVAL, ECUDA, ENOMEM, EUNSUPPORTED, EINDEX = 0, -1, -2, -3, -4, -5
+
+
+class MagpieError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"{message} (code {code})")
+        self.code = code
+
+
+class magpie_params(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int32), ("n_cols", ctypes.c_int32), ("m", ctypes.c_int32),
+                ("n_pos", ctypes.c_int32), ("levels", ctypes.c_int32), ("minibatch", ctypes.c_int32),
+                ("alpha", ctypes.c_float)]
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the library for sm_103a into the package's _build/ folder."""
+    newest = max(os.path.getmtime(p) for p in SOURCES + [HEADER])
+    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
+        return LIB_PATH
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    tmp = LIB_PATH + ".tmp"
+    cmd = ["nvcc", *NVCC_FLAGS, "-I", os.path.join(ROOT, "include"), "-o", tmp, *SOURCES]
+    if verbose:
+        print(" ".join(cmd))
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"MAGPIE CUDA library not built ({LIB_PATH} missing); "
+                               "run paper_2504_10118_gb300.magpie.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, f32p = ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)
+        dp = ctypes.POINTER(ctypes.c_double)
+        sig = {
+            "magpie_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(magpie_params), vp, vp, vp, vp, vp]),
+            "magpie_destroy": (None, [vp]),
+            "magpie_step": (ctypes.c_int, [vp, vp, i32]),
+            "magpie_sweep": (ctypes.c_int, [vp, vp]),
+            "magpie_objective": (ctypes.c_int, [vp, dp]),
+            "magpie_profile_sweep": (ctypes.c_int, [vp, vp, dp, dp, ctypes.POINTER(i32)]),
+            "magpie_stop_metric": (ctypes.c_int, [vp, dp]),
+            "magpie_set_probe": (ctypes.c_int, [vp, vp]),
+            "magpie_window_values": (ctypes.c_int, [vp, vp, vp]),
+            "magpie_sweep_host": (ctypes.c_int, [vp, vp, vp, vp]),
+            "magpie_forward_intensities": (ctypes.c_int, [vp, i32, i32, vp, i32, vp, i32, vp, vp]),
+            "magpie_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+            "magpie_last_error": (ctypes.c_char_p, []),
+            "magpie_version": (ctypes.c_int, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int) -> None:
+    if rc != OK:
+        L = lib()
+        raise MagpieError(rc, f"{L.magpie_strerror(rc).decode()}: {L.magpie_last_error().decode()}")
+
+
+def _dev(t: torch.Tensor, dtype: torch.dtype, numel: int, name: str) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() != numel:
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor of {numel} elements")
+    return t.data_ptr()
+
+
+def _host(t: torch.Tensor, dtype: torch.dtype, numel: int, name: str) -> int:
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"{name} must be a host tensor")
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() != numel:
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor of {numel} elements")
+    return t.data_ptr()
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def magpie_params_of(n_rows, n_cols, m, n_pos, levels, minibatch, alpha) -> magpie_params:
+    return magpie_params(int(n_rows), int(n_cols), int(m), int(n_pos), int(levels), int(minibatch), float(alpha))
+
+
+class Context:
+    """Owns a magpie_ctx and keeps the caller's tensors alive with it."""
+
+    def __init__(self, params: magpie_params, obj, probe, positions, intensities):
+        self.params = params
+        n, m, N = params.n_rows * params.n_cols, params.m, params.n_pos
+        self._keep = (obj, probe, positions, intensities)
+        h = ctypes.c_void_p()
+        _check(lib().magpie_create(ctypes.byref(h), ctypes.byref(params),
+                                   _dev(obj, torch.complex64, n, "object"),
+                                   _dev(probe, torch.complex64, m * m, "probe"),
+                                   _dev(positions, torch.int32, 2 * N, "positions"),
+                                   _dev(intensities, torch.float32, N * m * m, "intensities"),
+                                   _stream()))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().magpie_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def magpie_create(params: magpie_params, obj, probe, positions, intensities) -> Context:
+    return Context(params, obj, probe, positions, intensities)
+
+
+def magpie_destroy(ctx: Context) -> None:
+    ctx.close()
+
+
+def magpie_step(ctx: Context, idx: torch.Tensor) -> None:
+    _check(lib().magpie_step(ctx.handle, _dev(idx, torch.int32, idx.numel(), "idx"), idx.numel()))
+
+
+def magpie_sweep(ctx: Context, order: torch.Tensor) -> None:
+    _check(lib().magpie_sweep(ctx.handle, _dev(order, torch.int32, ctx.params.n_pos, "order")))
+
+
+def magpie_profile_sweep(ctx: Context, order: torch.Tensor):
+    """(window-kernel ms, apply-kernel ms, steps) of one sweep timed with events."""
+    a, b, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    _check(lib().magpie_profile_sweep(ctx.handle, _dev(order, torch.int32, ctx.params.n_pos, "order"),
+                                      ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)))
+    return a.value, b.value, n.value
+
+
+def magpie_objective(ctx: Context) -> float:
+    v = ctypes.c_double()
+    _check(lib().magpie_objective(ctx.handle, ctypes.byref(v)))
+    return v.value
+
+
+def magpie_stop_metric(ctx: Context) -> float:
+    v = ctypes.c_double()
+    _check(lib().magpie_stop_metric(ctx.handle, ctypes.byref(v)))
+    return v.value
+
+
+def magpie_set_probe(ctx: Context, probe: torch.Tensor) -> None:
+    _check(lib().magpie_set_probe(ctx.handle, _dev(probe, torch.complex64, ctx.params.m ** 2, "probe")))
+
+
+def magpie_window_values(ctx: Context):
+    N = ctx.params.n_pos
+    phi = torch.empty(N, dtype=torch.float64)
+    gn = torch.empty(N, dtype=torch.float64)
+    _check(lib().magpie_window_values(ctx.handle, phi.data_ptr(), gn.data_ptr()))
+    return phi, gn
+
+
+def magpie_sweep_host(ctx: Context, order: torch.Tensor, intensities=None, object_out=None) -> None:
+    p = ctx.params
+    o = _host(order, torch.int32, p.n_pos, "order")
+    d = None if intensities is None else _host(intensities, torch.float32, p.n_pos * p.m * p.m, "intensities")
+    z = None if object_out is None else _host(object_out, torch.complex64, p.n_rows * p.n_cols, "object_out")
+    _check(lib().magpie_sweep_host(ctx.handle, o, d, z))
+
+
+def magpie_forward_intensities(obj, probe, positions, m: int) -> torch.Tensor:
+    n_rows, n_cols = obj.shape
+    N = positions.shape[0]
+    out = torch.empty((N, m, m), dtype=torch.float32, device=obj.device)
+    _check(lib().magpie_forward_intensities(_dev(obj, torch.complex64, n_rows * n_cols, "object"),
+                                            n_rows, n_cols, _dev(probe, torch.complex64, m * m, "probe"), m,
+                                            _dev(positions, torch.int32, 2 * N, "positions"), N,
+                                            out.data_ptr(), _stream()))
+    return out
+
+
+def magpie_strerror(code: int) -> str:
+    return lib().magpie_strerror(code).decode()
+
+
+def magpie_last_error() -> str:
+    return lib().magpie_last_error().decode()
+
+
+def magpie_version() -> int:
+    return lib().magpie_version()

@@ -1,0 +1,90 @@
+"""The C ABI library builds, loads and exports every declared symbol; its
+argument checks run without a GPU (CPU)."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+from paper_2504_10118_gb300 import magpie
+
+needs_nvcc = pytest.mark.skipif(shutil.which("nvcc") is None, reason="nvcc not available")
+
+
+@pytest.fixture(scope="module")
+def L():
+    if shutil.which("nvcc") is not None:
+        magpie.build()
+    if not os.path.exists(magpie.LIB_PATH):
+        pytest.skip("library not built and nvcc not available")
+    return magpie.lib()
+
+
+def declared_functions():
+    text = open(magpie.HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(magpie_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for n in ["magpie_create", "magpie_destroy", "magpie_step", "magpie_sweep", "magpie_objective",
+              "magpie_stop_metric", "magpie_set_probe", "magpie_forward_intensities", "magpie_sweep_host"]:
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_error_strings_and_version(L):
+    assert L.magpie_version() == 10000
+    for code in (0, -1, -2, -3, -4, -5):
+        assert L.magpie_strerror(code)
+    assert L.magpie_strerror(-99) == b"unknown error"
+
+
+def _create(L, **kw):
+    p = dict(n_rows=128, n_cols=128, m=32, n_pos=64, levels=2, minibatch=16, alpha=0.1)
+    p.update(kw)
+    h = ctypes.c_void_p()
+    params = magpie.magpie_params(p["n_rows"], p["n_cols"], p["m"], p["n_pos"], p["levels"],
+                                  p["minibatch"], p["alpha"])
+    # dummy non-NULL pointers: argument checks fail before any of them is used
+    dummy = ctypes.c_void_p(0x1000)
+    rc = L.magpie_create(ctypes.byref(h), ctypes.byref(params), dummy, dummy, dummy, dummy, None)
+    return rc, h
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(m=12), magpie.EINVAL),
+    (dict(m=256), magpie.EUNSUPPORTED),
+    (dict(m=4), magpie.EUNSUPPORTED),
+    (dict(levels=0), magpie.EINVAL),
+    (dict(levels=7), magpie.EINVAL),
+    (dict(minibatch=0), magpie.EINVAL),
+    (dict(minibatch=65), magpie.EINVAL),
+    (dict(n_pos=0, minibatch=1), magpie.EINVAL),
+    (dict(n_rows=16), magpie.EINVAL),
+    (dict(alpha=-1.0), magpie.EINVAL),
+    (dict(alpha=float("nan")), magpie.EINVAL),
+    (dict(alpha=float("inf")), magpie.EINVAL),
+])
+def test_create_rejects_bad_arguments_without_a_gpu(L, kw, code):
+    rc, h = _create(L, **kw)
+    assert rc == code
+    assert not h.value
+    assert L.magpie_last_error()
+
+
+def test_null_arguments(L):
+    assert L.magpie_step(None, None, 1) == magpie.EINVAL
+    assert L.magpie_sweep(None, None) == magpie.EINVAL
+    v = ctypes.c_double()
+    assert L.magpie_objective(None, ctypes.byref(v)) == magpie.EINVAL
+    assert L.magpie_stop_metric(None, ctypes.byref(v)) == magpie.EINVAL
+    rc = L.magpie_create(None, None, None, None, None, None, None)
+    assert rc == magpie.EINVAL
+    L.magpie_destroy(None)
