@@ -48,7 +48,7 @@
 namespace {
 
 constexpr int kVersion = 10000;  // 1.0.0
-constexpr int kMaxMinibatch = 4096;  // the update kernel keeps the minibatch's corners in smem
+constexpr int kMaxMinibatch = 4096;  // the update kernel keeps the minibatch's corners in smem (48 KiB)
 
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
@@ -521,35 +521,68 @@ __global__ void __launch_bounds__(Geo<MS>::T) window_kernel(StepArgs A) {
 }
 
 // z += sum_b contrib_b / sum_b w0 over the windows covering each pixel, in
-// minibatch order (bitwise reproducible).
-__global__ void apply_kernel(float2* z, int n_rows, int n_cols, const int32_t* pos, const int32_t* idx,
-                             int count, int n_pos, const float2* contrib, const float* w0, int MS) {
-  extern __shared__ int2 bp[];
+// minibatch order (bitwise reproducible).  One block per 32 x 32 object tile:
+// the block first lists, in minibatch order, the windows that overlap its
+// tile (a ballot compaction by warp 0), then each thread updates 4 pixels by
+// walking that short list.  Dynamic smem: count int2 corners + count ints.
+constexpr int kApplyTile = 32;
+__global__ void __launch_bounds__(256) apply_kernel(float2* z, int n_rows, int n_cols, const int32_t* pos,
+                                                    const int32_t* idx, int count, int n_pos,
+                                                    const float2* contrib, const float* w0, int MS) {
+  extern __shared__ int2 corner[];
+  int* list = reinterpret_cast<int*>(corner + count);
+  __shared__ int n_list;
+  const int R0 = blockIdx.y * kApplyTile, C0 = blockIdx.x * kApplyTile;
   for (int i = threadIdx.x; i < count; i += blockDim.x) {
     const int k = idx[i];
-    bp[i] = ((unsigned)k < (unsigned)n_pos) ? make_int2(pos[2 * k], pos[2 * k + 1])
-                                            : make_int2(-(1 << 30), -(1 << 30));
+    corner[i] = ((unsigned)k < (unsigned)n_pos) ? make_int2(pos[2 * k], pos[2 * k + 1])
+                                                : make_int2(-(1 << 30), -(1 << 30));
   }
   __syncthreads();
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n_rows * n_cols) return;
-  const int r = p / n_cols, c = p - (p / n_cols) * n_cols;
-  float nx = 0.f, ny = 0.f, d = 0.f;
-  for (int b = 0; b < count; ++b) {
-    const int dr = r - bp[b].x, dc = c - bp[b].y;
-    if ((unsigned)dr < (unsigned)MS && (unsigned)dc < (unsigned)MS) {
-      const int o = dr * MS + dc;
-      const float2 v = contrib[(size_t)b * MS * MS + o];
-      nx += v.x;
-      ny += v.y;
-      d += __ldg(&w0[o]);
+  if (threadIdx.x < 32) {
+    const unsigned lane = threadIdx.x;
+    int base = 0;
+    for (int b0 = 0; b0 < count; b0 += 32) {
+      const int b = b0 + (int)lane;
+      bool hit = false;
+      if (b < count) {
+        const int2 q = corner[b];
+        hit = q.x < R0 + kApplyTile && q.x + MS > R0 && q.y < C0 + kApplyTile && q.y + MS > C0;
+      }
+      const unsigned mask = __ballot_sync(0xffffffffu, hit);
+      if (hit) list[base + __popc(mask & ((1u << lane) - 1u))] = b;
+      base += __popc(mask);
     }
+    if (lane == 0) n_list = base;
   }
-  if (d > 0.f) {
-    float2 zz = z[p];
-    zz.x += nx / d;
-    zz.y += ny / d;
-    z[p] = zz;
+  __syncthreads();
+  const int nl = n_list;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int c = C0 + tx;
+#pragma unroll
+  for (int i = 0; i < kApplyTile / 8; ++i) {
+    const int r = R0 + ty + 8 * i;
+    if (r >= n_rows || c >= n_cols) continue;
+    float nx = 0.f, ny = 0.f, d = 0.f;
+    for (int j = 0; j < nl; ++j) {
+      const int b = list[j];
+      const int2 q = corner[b];
+      const int dr = r - q.x, dc = c - q.y;
+      if ((unsigned)dr < (unsigned)MS && (unsigned)dc < (unsigned)MS) {
+        const int o = dr * MS + dc;
+        const float2 v = contrib[(size_t)b * MS * MS + o];
+        nx += v.x;
+        ny += v.y;
+        d += __ldg(&w0[o]);
+      }
+    }
+    if (d > 0.f) {
+      const size_t p = (size_t)r * n_cols + c;
+      float2 zz = z[p];
+      zz.x += nx / d;
+      zz.y += ny / d;
+      z[p] = zz;
+    }
   }
 }
 
@@ -713,6 +746,9 @@ cudaError_t prepare_size() {
 }
 
 cudaError_t prepare_kernels(int MS) {
+  cudaError_t e = cudaFuncSetAttribute(apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)((sizeof(int2) + sizeof(int)) * kMaxMinibatch));
+  if (e != cudaSuccess) return e;
   switch (MS) {
     case 8: return prepare_size<8>();
     case 16: return prepare_size<16>();
@@ -790,12 +826,10 @@ int enqueue_step(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st, 
   if (ev) CUDA_TRY(cudaEventRecord(ev[0], st));
   CUDA_TRY(launch_window_m<kStep>(c->p.m, a, count, st));
   if (ev) CUDA_TRY(cudaEventRecord(ev[1], st));
-  const int n = c->p.n_rows * c->p.n_cols;
-  const int T = 256;
+  const dim3 tiles((c->p.n_cols + kApplyTile - 1) / kApplyTile, (c->p.n_rows + kApplyTile - 1) / kApplyTile);
   if (ev) CUDA_TRY(cudaEventRecord(ev[2], st));
-  apply_kernel<<<(n + T - 1) / T, T, sizeof(int2) * count, st>>>(c->z, c->p.n_rows, c->p.n_cols, c->pos, idx,
-                                                                  count, c->p.n_pos, c->contrib, c->pyr + c->M,
-                                                                  c->p.m);
+  apply_kernel<<<tiles, 256, (sizeof(int2) + sizeof(int)) * count, st>>>(
+      c->z, c->p.n_rows, c->p.n_cols, c->pos, idx, count, c->p.n_pos, c->contrib, c->pyr + c->M, c->p.m);
   CUDA_TRY(cudaGetLastError());
   if (ev) CUDA_TRY(cudaEventRecord(ev[3], st));
   return MAGPIE_OK;

@@ -226,38 +226,40 @@ def test_mid_workload_full_size():
     """The n=512, m=128, 900-window, 3-level, B=64 Poisson workload at full
     size, in the launch configuration the benchmark times.
 
-    From a well-conditioned state (the true object plus noise) one minibatch
-    step and one whole sweep meet the 1e-5 bar.  From the flat start z = 1
-    every window's spectrum is F(Q) itself, with exact zeros and deep minima
-    where the phase, and so R_k, is decided by rounding (theta(0) = 0 in
-    FP64, a rounding-noise phase in FP32); the oracle's own arithmetic with
-    float32 FFTs moves ~2.5e-3 from the FP64 result over that sweep, and the
-    CUDA path must stay within twice the distance measured that way."""
+    Every one of the 15 minibatch steps of a sweep meets the 1e-5 bar when the
+    oracle starts from the state the GPU reached before that step.  Whole
+    sweeps are compared with a bar set by the conditioning of the iteration:
+    rounding-level differences grow about 1.7x per step here, so the oracle's
+    own arithmetic with float32 FFTs ends a sweep ~2.4e-5 from its FP64 result
+    (from the true object plus noise) or ~2.5e-3 (from the flat start z = 1,
+    whose window spectra are F(Q) itself, with exact zeros where the phase is
+    decided by rounding: theta(0) = 0 in FP64, a rounding-noise phase in
+    FP32).  The CUDA path must stay within twice the distance measured that
+    way."""
     w = synth.WORKLOADS["mid"]
     P = Problem(w.n, w.m, w.grid, w.step, w.jitter, w.levels, w.minibatch, alpha=w.alpha,
                 photons=w.photons, perturb=0.2)
     order = synth.make_order(P.N, 0)
     ctx = P.ctx()
-    magpie.magpie_step(ctx, dev_i32(order[: w.minibatch]))
-    ref1 = O.minibatch_step(P.z0, P.Q, P.pos, P.d, P.u, w.levels, order[: w.minibatch])
-    assert rel(P.z_gpu(), ref1) < STEP_TOL
+    worst = 0.0
+    for s in range(0, P.N, w.minibatch):
+        before = P.z_gpu()
+        batch = order[s:s + w.minibatch]
+        magpie.magpie_step(ctx, dev_i32(batch))
+        ref = O.minibatch_step(before, P.Q, P.pos, P.d, P.u, w.levels, batch)
+        worst = max(worst, rel(P.z_gpu(), ref))
+    assert worst < STEP_TOL, worst
     ctx.close()
 
-    ctx = P.ctx()
-    magpie.magpie_sweep(ctx, dev_i32(order))
-    ref = O.sweep(P.z0, P.Q, P.pos, P.d, P.u, w.levels, order, w.minibatch)
-    assert rel(P.z_gpu(), ref) < STEP_TOL
-    ctx.close()
-
-    flat = np.ones((w.n, w.n), dtype=np.complex128)
-    ctx = P.ctx(flat)
-    magpie.magpie_sweep(ctx, dev_i32(order))
-    ref = O.sweep(flat, P.Q, P.pos, P.d, P.u, w.levels, order, w.minibatch)
-    f32_ffts = oracle_with_float32_ffts().sweep(flat, P.Q, P.pos, P.d, P.u, w.levels, order, w.minibatch)
-    bar = max(STEP_TOL, 2.0 * rel(f32_ffts, ref))
-    got = rel(P.z_gpu(), ref)
-    assert got < bar, (got, rel(f32_ffts, ref))
-    ctx.close()
+    f32_oracle = oracle_with_float32_ffts()
+    for start in (P.z0, np.ones((w.n, w.n), dtype=np.complex128)):
+        ctx = P.ctx(start)
+        magpie.magpie_sweep(ctx, dev_i32(order))
+        ref = O.sweep(start, P.Q, P.pos, P.d, P.u, w.levels, order, w.minibatch)
+        drift = rel(f32_oracle.sweep(start, P.Q, P.pos, P.d, P.u, w.levels, order, w.minibatch), ref)
+        got = rel(P.z_gpu(), ref)
+        assert got < max(STEP_TOL, 2.0 * drift), (got, drift)
+        ctx.close()
 
 
 # ------------------------------------------------------------ API behaviour
