@@ -179,6 +179,40 @@ int magpie_forward_intensities(const void* object, int32_t n_rows, int32_t n_col
 /* Static name of an error code; never NULL. */
 const char* magpie_strerror(int code);
 
+/*
+ * One minibatch step, as magpie_step, for callers that cannot allocate GPU
+ * memory: code that runs under a fixed memory budget handed out by a host
+ * framework, plug-ins whose host application owns every device allocation,
+ * and real-time acquisition loops where cudaMalloc's implicit device
+ * synchronisation (and its chance of failing under memory pressure) is not
+ * acceptable.  It needs no context and calls no allocation routine: its
+ * workspace (the per-window increments, the per-level probe factors and the
+ * twiddles) lives in one fixed array of about 9 MiB that every GPU loading
+ * this library holds until the process exits.  This entry point is an
+ * addition of this library; the paper has no counterpart.
+ *   object      : DEVICE complex [n_rows][n_cols], updated in place
+ *   probe       : DEVICE complex [m][m]; its per-level factors (Eq.
+ *                 def_weights) are recomputed on every call
+ *   positions   : DEVICE int32 [n_pos][2]
+ *   amplitudes  : DEVICE float32 [n_pos][m][m], the square roots sqrt(d_k)
+ *                 of the measured intensities (DFT order)
+ *   idx         : DEVICE int32 [count], the windows of this minibatch
+ *   phi, gnorm  : DEVICE float64 [n_pos] outputs, Phi_k and ||grad Phi_k||
+ *                 of the windows of this minibatch (other entries untouched)
+ *   stream      : cudaStream_t as void*
+ * Limits: m as for magpie_create, count * m^2 <= 2^20 (e.g. 64 windows of
+ * 128 x 128), otherwise MAGPIE_EINVAL.  Windows whose index or position is
+ * out of range are skipped and reported as MAGPIE_EINDEX.  Synchronous: it
+ * waits for the step to finish before returning.  The first call on each
+ * device looks up the workspace's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All
+ * calls share the one workspace: calls that overlap on the GPU (other
+ * threads, other streams) race and must be serialised by the caller.
+ */
+int magpie_step_noalloc(void* object, int32_t n_rows, int32_t n_cols, const void* probe, int32_t m,
+                        const int32_t* positions, int32_t n_pos, const float* amplitudes, const int32_t* idx,
+                        int32_t count, int32_t levels, float alpha, double* phi, double* gnorm, void* stream);
+
 /* Message of the calling thread's most recent failed call ("" if none). */
 const char* magpie_last_error(void);
 

@@ -910,6 +910,81 @@ int validate(const magpie_params* p) {
   return MAGPIE_OK;
 }
 
+
+// ------------------------------------------------ minibatch step without allocation
+// Fixed scratch for magpie_step_noalloc, shared by every call in the process
+// (one copy per GPU that loads the library, held until exit).
+constexpr size_t kNoAllocMaxIncrement = size_t(1) << 20;  // count * m^2 complex values
+constexpr size_t kNoAllocContribBytes = kNoAllocMaxIncrement * sizeof(float2);                      // 8 MiB
+constexpr size_t kNoAllocPyrBytes = sizeof(float) * 3 * 128 * 128;                                 // level factors
+constexpr size_t kNoAllocPyrQBytes = sizeof(double2) * 2 * 128 * 128;                              // FP64 probe levels
+constexpr size_t kNoAllocPyrUBytes = sizeof(double) * 2 * 128 * 128;                               // FP64 u levels
+constexpr size_t kNoAllocTwBytes = sizeof(float2) * 128;
+constexpr size_t kNoAllocIdxBytes = sizeof(int32_t) * (kNoAllocMaxIncrement / 64);                 // count <= 2^14
+constexpr size_t kNoAllocBytes = kNoAllocContribBytes + kNoAllocPyrBytes + kNoAllocPyrQBytes + kNoAllocPyrUBytes +
+                                 kNoAllocTwBytes + kNoAllocIdxBytes + 256;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// idx -> sanitized copy: a window whose index is outside [0, n_pos) or whose
+// corner puts it outside the object becomes -1 (skipped by the step kernels)
+// and sets bit 0 of *err.
+__global__ void sanitize_idx_kernel(const int32_t* idx, int count, const int32_t* pos, int n_pos, int n_rows,
+                                    int n_cols, int m, int32_t* out, int* err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  int k = idx[i];
+  bool ok = (unsigned)k < (unsigned)n_pos;
+  if (ok) {
+    const int r = pos[2 * k], c = pos[2 * k + 1];
+    ok = r >= 0 && c >= 0 && r <= n_rows - m && c <= n_cols - m;
+  }
+  if (!ok) {
+    k = -1;
+    atomicOr(err, 1);
+  }
+  out[i] = k;
+}
+
+struct NoAllocScratch {
+  float2* contrib;
+  float* pyr;
+  double2* pyr_q;
+  double* pyr_u;
+  float2* tw;
+  int32_t* idx;
+  int* err;
+};
+
+// Per-device base address of g_noalloc_scratch, looked up once per device
+// with that device current (host code may not use the symbol's own address).
+int noalloc_scratch(NoAllocScratch* out) {
+  constexpr int kMaxDevices = 64;
+  static unsigned char* base[kMaxDevices] = {};
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(MAGPIE_EUNSUPPORTED, "device ordinal beyond 63");
+  if (!base[dev]) {
+    void* p = nullptr;
+    CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    base[dev] = (unsigned char*)p;
+  }
+  unsigned char* b = base[dev];
+  out->contrib = (float2*)b;
+  b += kNoAllocContribBytes;
+  out->pyr = (float*)b;
+  b += kNoAllocPyrBytes;
+  out->pyr_q = (double2*)b;
+  b += kNoAllocPyrQBytes;
+  out->pyr_u = (double*)b;
+  b += kNoAllocPyrUBytes;
+  out->tw = (float2*)b;
+  b += kNoAllocTwBytes;
+  out->idx = (int32_t*)b;
+  b += kNoAllocIdxBytes;
+  out->err = (int*)b;
+  return MAGPIE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1152,6 +1227,70 @@ int magpie_forward_intensities(const void* object, int32_t n_rows, int32_t n_col
   cudaFree(tw);
   cudaFree(iota);
   CUDA_TRY(e);
+  return MAGPIE_OK;
+}
+
+
+int magpie_step_noalloc(void* object, int32_t n_rows, int32_t n_cols, const void* probe, int32_t m,
+                        const int32_t* positions, int32_t n_pos, const float* amplitudes, const int32_t* idx,
+                        int32_t count, int32_t levels, float alpha, double* phi, double* gnorm, void* stream) {
+  magpie_params p{};
+  p.n_rows = n_rows;
+  p.n_cols = n_cols;
+  p.m = m;
+  p.n_pos = n_pos;
+  p.levels = levels;
+  p.minibatch = count;
+  p.alpha = alpha;
+  int rc = validate(&p);
+  if (rc) return rc;
+  if (!object || !probe || !positions || !amplitudes || !idx || !phi || !gnorm)
+    return fail(MAGPIE_EINVAL, "a data pointer is NULL");
+  if ((size_t)count * (size_t)m * (size_t)m > kNoAllocMaxIncrement)
+    return fail(MAGPIE_EINVAL, "count * m^2 = " + std::to_string((long long)count * m * m) +
+                                   " exceeds the fixed scratch of 2^20 complex values");
+  NoAllocScratch w{};
+  rc = noalloc_scratch(&w);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  CUDA_TRY(prepare_kernels(m));
+  float2 htw[128];
+  for (int t = 0; t < m; ++t) {
+    const double ang = -2.0 * 3.14159265358979323846 * (double)t / (double)m;
+    htw[t] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+  }
+  CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+  CUDA_TRY(cudaMemcpyAsync(w.tw, htw, sizeof(float2) * m, cudaMemcpyHostToDevice, st));
+  sanitize_idx_kernel<<<(count + 255) / 256, 256, 0, st>>>(idx, count, positions, n_pos, n_rows, n_cols, m, w.idx,
+                                                            w.err);
+  CUDA_TRY(cudaGetLastError());
+  pyramid_kernel<<<1, 1024, 0, st>>>((const float2*)probe, m, levels, alpha, w.pyr_q, w.pyr_u, w.pyr);
+  CUDA_TRY(cudaGetLastError());
+  StepArgs a{};
+  a.z = (const float2*)object;
+  a.n_rows = n_rows;
+  a.n_cols = n_cols;
+  a.Q = (const float2*)probe;
+  a.tw = w.tw;
+  a.amp = amplitudes;
+  a.pos = positions;
+  a.idx = w.idx;
+  a.n_pos = n_pos;
+  a.contrib = w.contrib;
+  a.pyr = w.pyr;
+  a.levels = levels;
+  a.phi_pos = phi;
+  a.gn_pos = gnorm;
+  a.err = w.err;
+  CUDA_TRY(launch_window_m<kStep>(m, a, count, st));
+  const dim3 tiles((n_cols + kApplyTile - 1) / kApplyTile, (n_rows + kApplyTile - 1) / kApplyTile);
+  apply_kernel<<<tiles, 256, (sizeof(int2) + sizeof(int)) * count, st>>>(
+      (float2*)object, n_rows, n_cols, positions, w.idx, count, n_pos, w.contrib, w.pyr + m * m, m);
+  CUDA_TRY(cudaGetLastError());
+  int h = 0;
+  CUDA_TRY(cudaMemcpyAsync(&h, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (h) return fail(MAGPIE_EINDEX, "a window index or its position was out of range; that window was skipped");
   return MAGPIE_OK;
 }
 

@@ -78,6 +78,8 @@ def lib() -> ctypes.CDLL:
             "magpie_window_values": (ctypes.c_int, [vp, vp, vp]),
             "magpie_sweep_host": (ctypes.c_int, [vp, vp, vp, vp]),
             "magpie_forward_intensities": (ctypes.c_int, [vp, i32, i32, vp, i32, vp, i32, vp, vp]),
+            "magpie_step_noalloc": (ctypes.c_int, [vp, i32, i32, vp, i32, vp, i32, vp, vp, i32, i32,
+                                                    ctypes.c_float, vp, vp, vp]),
             "magpie_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             "magpie_last_error": (ctypes.c_char_p, []),
             "magpie_version": (ctypes.c_int, []),
@@ -213,6 +215,20 @@ def magpie_forward_intensities(obj, probe, positions, m: int) -> torch.Tensor:
                                             _dev(positions, torch.int32, 2 * N, "positions"), N,
                                             out.data_ptr(), _stream()))
     return out
+
+
+def magpie_step_noalloc(obj, probe, positions, amplitudes, idx, levels: int, alpha: float, phi, gnorm) -> None:
+    """One minibatch step that allocates no GPU memory (see the C header)."""
+    n_rows, n_cols = obj.shape
+    m = probe.shape[0]
+    N = positions.shape[0]
+    _check(lib().magpie_step_noalloc(_dev(obj, torch.complex64, n_rows * n_cols, "object"), n_rows, n_cols,
+                                     _dev(probe, torch.complex64, m * m, "probe"), m,
+                                     _dev(positions, torch.int32, 2 * N, "positions"), N,
+                                     _dev(amplitudes, torch.float32, N * m * m, "amplitudes"),
+                                     _dev(idx, torch.int32, idx.numel(), "idx"), idx.numel(), int(levels),
+                                     float(alpha), _dev(phi, torch.float64, N, "phi"),
+                                     _dev(gnorm, torch.float64, N, "gnorm"), _stream()))
 
 
 def magpie_strerror(code: int) -> str:
