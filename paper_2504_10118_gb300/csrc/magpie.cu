@@ -34,6 +34,7 @@
 // the forward transform's output distribution directly (the four steps in
 // reverse), so each 2-D transform needs one smem round trip per direction.
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -46,6 +47,8 @@
 #include "magpie.h"
 
 namespace {
+
+namespace cg = cooperative_groups;
 
 constexpr int kVersion = 10000;  // 1.0.0
 constexpr int kMaxMinibatch = 4096;  // the update kernel keeps the minibatch's corners in smem (48 KiB)
@@ -129,35 +132,77 @@ __device__ __forceinline__ void dft_reg(float2 (&a)[N]) {
 }
 
 // ------------------------------------------------------ per-size geometry
+// An MS x MS window is handled by a cluster of CL thread blocks.  Block q owns
+// a slab of SLAB = MS / CL lines: rows q*SLAB.. of the row-slab buffer X and
+// columns q*SLAB.. of the column-slab buffer Y.  An MS-point line is split
+// over G lanes of one warp holding E = MS / G points each; SLAB is a multiple
+// of E and of G, so every cross-slab store below targets a compile-time rank.
 template <int MS> struct Cfg;
-template <> struct Cfg<8> { static constexpr int E = 4, G = 2; };
-template <> struct Cfg<16> { static constexpr int E = 4, G = 4; };
-template <> struct Cfg<32> { static constexpr int E = 8, G = 4; };
-template <> struct Cfg<64> { static constexpr int E = 8, G = 8; };
-template <> struct Cfg<128> { static constexpr int E = 16, G = 8; };
+template <> struct Cfg<8> { static constexpr int E = 4, G = 2, CL = 1; };
+template <> struct Cfg<16> { static constexpr int E = 4, G = 4, CL = 1; };
+template <> struct Cfg<32> { static constexpr int E = 8, G = 4, CL = 1; };
+template <> struct Cfg<64> { static constexpr int E = 8, G = 8, CL = 2; };
+template <> struct Cfg<128> { static constexpr int E = 16, G = 8, CL = 4; };
 
 template <int MS> struct Geo {
-  static constexpr int E = Cfg<MS>::E;
-  static constexpr int G = Cfg<MS>::G;
+  static constexpr int E = Cfg<MS>::E, G = Cfg<MS>::G, CL = Cfg<MS>::CL;
   static_assert(E * G == MS && G <= E && G <= 32, "line split");
+  static constexpr int SLAB = MS / CL;
+  static_assert(CL == 1 || (SLAB % E == 0 && SLAB % G == 0 && SLAB >= 8), "slab split");
   static constexpr int M = MS * MS;
-  static constexpr int LANES = MS * G;  // lanes that one pass over all lines needs
-  static constexpr int T = LANES < 32 ? 32 : (LANES > 512 ? 512 : LANES);
-  static constexpr int LPT = (LANES + T - 1) / T;  // line rounds per pass
-  static constexpr int PAD = (32 / G) % 16;       // row pitch pad (complex)
-  static constexpr int SP = MS + PAD;
-  // dynamic shared memory in float2 units: S, twiddles, level scratch
-  static constexpr int LVL = (MS / 4) * (MS / 4) * 2;
-  static constexpr size_t SMEM = sizeof(float2) * (size_t(MS) * SP + MS + LVL) + sizeof(double) * 64;
+  static constexpr int LANES = SLAB * G;  // one lane group per line of the slab
+  static constexpr int T = LANES < 32 ? 32 : LANES;
+  static_assert(T <= 1024 && T % 32 == 0, "block size");
+  static constexpr int XN = SLAB * MS;  // complex entries of X and of Y
+  static constexpr int LVL = (MS / 4) * (SLAB / 4) * 2 + 4 * CL * CL + 32;
+  // resident blocks per SM the register budget is sized for (two 4-block
+  // windows' worth of slabs share an SM for m = 128)
+  static constexpr int MIN_BLOCKS = T >= 256 ? 2 : 1;
+  static constexpr size_t SMEM = sizeof(float2) * (2 * size_t(XN) + MS + LVL) + sizeof(double) * 64;
 };
 
-// Forward (INV=false) m-point transform of one line whose lanes hold the
+// XOR swizzle of the column index by the row index, within rows of width W:
+// with it, 8 consecutive rows of one column, 4 consecutive rows of 8
+// consecutive columns, and the transposed exchange reads all hit distinct
+// bank pairs (for both warp halves of an 8-byte access).
+template <int W>
+__device__ __forceinline__ int swz(int r) {
+  return ((((r & 1) << 3) | (((r >> 1) & 3) << 1))) & (W - 1);
+}
+// X: [SLAB][MS], Y: [MS][SLAB], both row-major with the swizzle.
+template <int MS>
+__device__ __forceinline__ int xi(int rho, int c) {
+  return rho * MS + (c ^ swz<MS>(rho));
+}
+template <int MS>
+__device__ __forceinline__ int yi(int r, int gam) {
+  constexpr int S = Geo<MS>::SLAB;
+  return r * S + (gam ^ swz<S>(r));
+}
+
+// Barrier over the window's blocks; with CL = 1 an ordinary block barrier.
+template <int CL>
+__device__ __forceinline__ void window_sync() {
+  if constexpr (CL > 1)
+    cg::this_cluster().sync();
+  else
+    __syncthreads();
+}
+// The same shared-memory object in block `rank` of the window's cluster.
+template <int CL, typename P>
+__device__ __forceinline__ P* peer(P* p, int rank) {
+  if constexpr (CL > 1)
+    return cg::this_cluster().map_shared_rank(p, rank);
+  else
+    return p;
+}
+
+// Forward (INV=false) MS-point transform of one line whose lanes hold the
 // input x[e] = line[g + G e].  On return x[j G + k2] = X[g + G j + E k2].
-// `base`/`stride` address the line's MS slots in shared memory (used as the
-// exchange buffer); `tw[t]` = exp(-2 pi i t / MS).
-template <int MS, bool INV>
-__device__ __forceinline__ void line_fwd(float2 (&x)[Cfg<MS>::E], int g, bool act, float2* base,
-                                         int stride, const float2* tw) {
+// slot(s) addresses the line's MS slots in shared memory (the exchange
+// buffer); tw[t] = exp(-2 pi i t / MS).
+template <int MS, bool INV, class Slot>
+__device__ __forceinline__ void line_fwd(float2 (&x)[Cfg<MS>::E], int g, bool act, Slot slot, const float2* tw) {
   constexpr int E = Cfg<MS>::E, G = Cfg<MS>::G;
   dft_reg<E, INV>(x);
 #pragma unroll
@@ -165,14 +210,14 @@ __device__ __forceinline__ void line_fwd(float2 (&x)[Cfg<MS>::E], int g, bool ac
   if constexpr (G > 1) {
 #pragma unroll
     for (int k1 = 0; k1 < E; ++k1)
-      if (act) base[(k1 * G + (g ^ (k1 & (G - 1)))) * stride] = x[k1];
+      if (act) slot(k1 * G + (g ^ (k1 & (G - 1)))) = x[k1];
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < E / G; ++j) {
       const int k1 = g + G * j;
       float2 v[G];
 #pragma unroll
-      for (int gp = 0; gp < G; ++gp) v[gp] = act ? base[(k1 * G + (gp ^ g)) * stride] : f2(0.f, 0.f);
+      for (int gp = 0; gp < G; ++gp) v[gp] = act ? slot(k1 * G + (gp ^ g)) : f2(0.f, 0.f);
       dft_reg<G, INV>(v);
 #pragma unroll
       for (int k2 = 0; k2 < G; ++k2) x[j * G + k2] = v[k2];
@@ -183,9 +228,8 @@ __device__ __forceinline__ void line_fwd(float2 (&x)[Cfg<MS>::E], int g, bool ac
 
 // Unnormalised inverse of line_fwd: input in line_fwd's output distribution,
 // output x[e] = sum_k X[k] exp(+2 pi i k (g + G e) / MS).
-template <int MS>
-__device__ __forceinline__ void line_inv(float2 (&x)[Cfg<MS>::E], int g, bool act, float2* base,
-                                         int stride, const float2* tw) {
+template <int MS, class Slot>
+__device__ __forceinline__ void line_inv(float2 (&x)[Cfg<MS>::E], int g, bool act, Slot slot, const float2* tw) {
   constexpr int E = Cfg<MS>::E, G = Cfg<MS>::G;
   if constexpr (G > 1) {
 #pragma unroll
@@ -198,13 +242,12 @@ __device__ __forceinline__ void line_inv(float2 (&x)[Cfg<MS>::E], int g, bool ac
 #pragma unroll
       for (int gp = 0; gp < G; ++gp) {
         const float2 t = gp ? twmul<true>(v[gp], tw[(gp * k1) & (MS - 1)]) : v[0];
-        if (act) base[(k1 * G + (gp ^ g)) * stride] = t;
+        if (act) slot(k1 * G + (gp ^ g)) = t;
       }
     }
     __syncwarp();
 #pragma unroll
-    for (int k1 = 0; k1 < E; ++k1)
-      x[k1] = act ? base[(k1 * G + (g ^ (k1 & (G - 1)))) * stride] : f2(0.f, 0.f);
+    for (int k1 = 0; k1 < E; ++k1) x[k1] = act ? slot(k1 * G + (g ^ (k1 & (G - 1)))) : f2(0.f, 0.f);
     __syncwarp();
   }
   dft_reg<E, true>(x);
@@ -230,9 +273,9 @@ struct StepArgs {
   const float* amp;   // amplitudes sqrt(d) [n_pos][MS][MS]
   float* out_int;     // forward intensities [n_pos][MS][MS] (kSim)
   const int32_t* pos; // [n_pos][2]
-  const int32_t* idx; // window of each block
+  const int32_t* idx; // window of each cluster
   int n_pos;
-  float2* contrib;    // [blocks][MS][MS] increments w . Delta
+  float2* contrib;    // [windows][MS][MS] increments w . Delta
   const float* pyr;   // per-level factors
   int levels;
   double* phi_pos;    // per-window Phi_k
@@ -252,183 +295,274 @@ __device__ __forceinline__ double block_sum(double v, double* red, int tid, int 
   return r;
 }
 
-// V-cycle pass of one window: S holds g^0; blocks of 2^TT x 2^TT level-0
-// pixels are handled in registers, levels coarser than TT (if any) in the
-// smem scratch `lvl` by all threads.
+__device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
+  return f2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+
+// MAGPS V-cycle of one window in residual form, on this block's column slab
+// Y (g^0 for MS rows x SLAB columns).  Lane gamma of a warp owns column
+// gamma of a strip of 2^TT rows; the 2x2 restrictions pair columns by warp
+// shuffles.  Levels coarser than TT are kept in `lvl` (local levels up to
+// log2(SLAB); coarser ones span the cluster and are finished by block 0).
 template <int MS, int TT>
-__device__ __forceinline__ void vcycle(const float2* S, float2* lvl, const float* pyr, int L,
-                                       float2* out, int tid) {
-  constexpr int BS = 1 << TT, NBS = MS >> TT, T = Geo<MS>::T, SP = Geo<MS>::SP;
+__device__ __forceinline__ void vcycle(const float2* Y, float2* lvl, const float* pyr, int L, int q, float2* out,
+                                       int tid) {
+  using Gm = Geo<MS>;
+  constexpr int SLAB = Gm::SLAB, T = Gm::T, CL = Gm::CL, H = 1 << TT, NS = MS / H, SPAR = T / SLAB;
+  constexpr int LLOC = (SLAB >= 32) ? 5 : (SLAB == 16 ? 4 : 3);  // log2(SLAB)
+  static_assert((1 << LLOC) == SLAB, "slab levels");
+  const int gam = tid % SLAB, s0 = tid / SLAB;
+  const int cgl = q * SLAB + gam;  // column in the window
   const bool deep = (L - 1) > TT;
   const float* u0 = pyr;
   const float* wu1 = pyr + lvl_off(MS, 1);
   const float* iw1 = wu1 + (MS / 2) * (MS / 2);
   const float* rr1 = iw1 + (MS / 2) * (MS / 2);
-  const float* wu2 = pyr + lvl_off(MS, 2);
-  const float* iwT = pyr + lvl_off(MS, TT) + (MS >> TT) * (MS >> TT);
+  // offsets of the slab's level arrays (levels TT .. LLOC) in lvl
+  auto off = [](int l) {
+    int o = 0;
+    for (int j = TT; j < l; ++j) o += (MS >> j) * (SLAB >> j);
+    return o;
+  };
 
-  auto restrict_block = [&](int br, int bc, float2 (&g0)[BS][BS], float2 (&g1)[BS / 2][BS / 2]) -> float2 {
+  // g at level TT of the 2^TT x 2^TT bin of column cgl in strip s (the same
+  // value in all 2^TT lanes of the bin); g0 and g1 keep the finer levels.
+  auto strip = [&](int s, bool ok, float2 (&g0)[H], float2 (&g1)[H / 2]) -> float2 {
+    const int R0 = s * H;
 #pragma unroll
-    for (int a = 0; a < BS; ++a)
+    for (int a = 0; a < H; ++a) g0[a] = ok ? Y[yi<MS>(R0 + a, gam)] : f2(0.f, 0.f);
 #pragma unroll
-      for (int b = 0; b < BS; ++b) g0[a][b] = S[(BS * br + a) * SP + BS * bc + b];
-#pragma unroll
-    for (int a = 0; a < BS / 2; ++a)
-#pragma unroll
-      for (int b = 0; b < BS / 2; ++b) {
-        const int r1 = (BS / 2) * br + a, c1 = (BS / 2) * bc + b;
-        const float s = 0.25f * __ldg(&wu1[r1 * (MS / 2) + c1]);
-        const float2 sum = cadd(cadd(g0[2 * a][2 * b], g0[2 * a][2 * b + 1]),
-                                cadd(g0[2 * a + 1][2 * b], g0[2 * a + 1][2 * b + 1]));
-        g1[a][b] = cscale(sum, s);
-      }
+    for (int a = 0; a < H / 2; ++a) {
+      float2 v = cadd(g0[2 * a], g0[2 * a + 1]);
+      v = cadd(v, shfl_xor2(v, 1));
+      const float w = ok ? __ldg(&wu1[(R0 / 2 + a) * (MS / 2) + (cgl >> 1)]) : 0.f;
+      g1[a] = cscale(v, 0.25f * w);
+    }
     if constexpr (TT == 1) {
-      return g1[0][0];
+      return g1[0];
     } else {
-      const float s = 0.25f * __ldg(&wu2[br * (MS / 4) + bc]);
-      return cscale(cadd(cadd(g1[0][0], g1[0][1]), cadd(g1[1][0], g1[1][1])), s);
+      float2 v = cadd(g1[0], g1[1]);
+      v = cadd(v, shfl_xor2(v, 2));
+      const float w = ok ? __ldg(&pyr[lvl_off(MS, 2) + (R0 / 4) * (MS / 4) + (cgl >> 2)]) : 0.f;
+      return cscale(v, 0.25f * w);
     }
   };
 
   if (deep) {
-    // phase 1: level-TT values of every block
-    for (int blk = tid; blk < NBS * NBS; blk += T) {
-      float2 g0[BS][BS], g1[BS / 2][BS / 2];
-      lvl[blk] = restrict_block(blk / NBS, blk % NBS, g0, g1);
+    // phase 1: level-TT values of every strip bin
+    for (int base = 0; base < NS; base += SPAR) {
+      const int s = base + s0;
+      const bool ok = s < NS;
+      float2 g0[H], g1[H / 2];
+      const float2 gT = strip(s, ok, g0, g1);
+      if (ok && (gam & (H - 1)) == 0) lvl[off(TT) + s * (SLAB >> TT) + (gam >> TT)] = gT;
     }
     __syncthreads();
-    // phase 2: levels TT .. L-1 in shared memory, level l at lvl + off(l)
-    auto off = [](int l) {
-      int o = 0;
-      for (int j = TT; j < l; ++j) o += (MS >> j) * (MS >> j);
-      return o;
-    };
-    for (int l = TT; l < L - 1; ++l) {
-      const int s = MS >> l, sc = s >> 1;
+    // phase 2: restrictions inside the slab, levels TT+1 .. min(L-1, LLOC)
+    const int ltop = (L - 1) < LLOC ? (L - 1) : LLOC;
+    for (int l = TT; l < ltop; ++l) {
+      const int rows = MS >> (l + 1), cols = SLAB >> (l + 1), fc = SLAB >> l;
       const float2* fine = lvl + off(l);
       float2* coarse = lvl + off(l + 1);
       const float* wu = pyr + lvl_off(MS, l + 1);
-      for (int i = tid; i < sc * sc; i += T) {
-        const int r = i / sc, c = i - (i / sc) * sc;
-        const float2 sum = cadd(cadd(fine[(2 * r) * s + 2 * c], fine[(2 * r) * s + 2 * c + 1]),
-                                cadd(fine[(2 * r + 1) * s + 2 * c], fine[(2 * r + 1) * s + 2 * c + 1]));
-        coarse[i] = cscale(sum, 0.25f * __ldg(&wu[i]));
+      for (int i = tid; i < rows * cols; i += T) {
+        const int r = i / cols, c = i - (i / cols) * cols;
+        const float2 sm = cadd(cadd(fine[(2 * r) * fc + 2 * c], fine[(2 * r) * fc + 2 * c + 1]),
+                               cadd(fine[(2 * r + 1) * fc + 2 * c], fine[(2 * r + 1) * fc + 2 * c + 1]));
+        coarse[i] = cscale(sm, 0.25f * __ldg(&wu[r * (MS >> (l + 1)) + q * cols + c]));
       }
       __syncthreads();
     }
-    {
-      const int l = L - 1, s = MS >> l;
+    if (L - 1 <= LLOC) {
+      // coarsest level inside the slab
+      const int l = L - 1, rows = MS >> l, cols = SLAB >> l;
       float2* a = lvl + off(l);
-      const float* iw = pyr + lvl_off(MS, l) + s * s;
-      for (int i = tid; i < s * s; i += T) a[i] = cscale(a[i], __ldg(&iw[i]));
+      const float* iw = pyr + lvl_off(MS, l) + (MS >> l) * (MS >> l);
+      for (int i = tid; i < rows * cols; i += T) {
+        const int r = i / cols, c = i - (i / cols) * cols;
+        a[i] = cscale(a[i], __ldg(&iw[r * (MS >> l) + q * cols + c]));
+      }
       __syncthreads();
+    } else {
+      if constexpr (CL > 1) {
+        // levels LLOC .. L-1 span the cluster: block 0 gathers the CL x CL
+        // level-LLOC values (column qq from block qq), runs the coarse
+        // levels, and sends back level-LLOC increments.
+        window_sync<CL>();
+        if (q == 0 && tid == 0) {
+          float2* gl = lvl + off(LLOC + 1);  // global arrays of levels LLOC.. in block 0
+          auto goff = [](int i) {  // offset of level LLOC + i
+            int o = 0;
+            for (int l = LLOC; l < LLOC + i; ++l) o += (MS >> l) * (MS >> l);
+            return o;
+          };
+          for (int qq = 0; qq < CL; ++qq) {
+            const float2* src = peer<CL>(lvl, qq) + off(LLOC);
+            for (int i = 0; i < CL; ++i) gl[i * CL + qq] = src[i];
+          }
+          for (int l = LLOC; l < L - 1; ++l) {
+            const int n = MS >> (l + 1), nf = MS >> l;
+            const float2* fine = gl + goff(l - LLOC);
+            float2* coarse = gl + goff(l - LLOC + 1);
+            const float* wu = pyr + lvl_off(MS, l + 1);
+            for (int i = 0; i < n * n; ++i) {
+              const int r = i / n, c = i % n;
+              const float2 sm = cadd(cadd(fine[(2 * r) * nf + 2 * c], fine[(2 * r) * nf + 2 * c + 1]),
+                                     cadd(fine[(2 * r + 1) * nf + 2 * c], fine[(2 * r + 1) * nf + 2 * c + 1]));
+              coarse[i] = cscale(sm, 0.25f * wu[i]);
+            }
+          }
+          {
+            const int l = L - 1, n = MS >> l;
+            float2* a = gl + goff(l - LLOC);
+            const float* iw = pyr + lvl_off(MS, l) + n * n;
+            for (int i = 0; i < n * n; ++i) a[i] = cscale(a[i], iw[i]);
+          }
+          for (int l = L - 2; l >= LLOC; --l) {
+            const int n = MS >> l, nc = n >> 1;
+            float2* a = gl + goff(l - LLOC);
+            const float2* pe = gl + goff(l - LLOC + 1);
+            const float* iw = pyr + lvl_off(MS, l) + n * n;
+            const float* rr = iw + n * n;
+            for (int i = 0; i < n * n; ++i) {
+              const int r = i / n, c = i % n;
+              const float2 p = pe[(r >> 1) * nc + (c >> 1)];
+              const float2 v = cscale(a[i], iw[i]);
+              a[i] = f2(v.x + rr[i] * p.x, v.y + rr[i] * p.y);
+            }
+          }
+          for (int qq = 0; qq < CL; ++qq) {
+            float2* dst = peer<CL>(lvl, qq) + off(LLOC);
+            for (int i = 0; i < CL; ++i) dst[i] = gl[i * CL + qq];
+          }
+        }
+        window_sync<CL>();
+      }
     }
-    for (int l = L - 2; l >= TT; --l) {
-      const int s = MS >> l, sc = s >> 1;
+    // up-pass inside the slab down to level TT
+    const int lstart = ((L - 1) < LLOC ? (L - 1) : LLOC) - 1;
+    for (int l = lstart; l >= TT; --l) {
+      const int rows = MS >> l, cols = SLAB >> l, cc = cols >> 1;
       float2* a = lvl + off(l);
-      const float2* p = lvl + off(l + 1);
-      const float* iw = pyr + lvl_off(MS, l) + s * s;
-      const float* rr = iw + s * s;
-      for (int i = tid; i < s * s; i += T) {
-        const int r = i / s, c = i - (i / s) * s;
-        const float2 pe = p[(r >> 1) * sc + (c >> 1)];
-        const float2 v = cscale(a[i], __ldg(&iw[i]));
-        const float q = __ldg(&rr[i]);
-        a[i] = f2(v.x + q * pe.x, v.y + q * pe.y);
+      const float2* pe = lvl + off(l + 1);
+      const float* iw = pyr + lvl_off(MS, l) + (MS >> l) * (MS >> l);
+      const float* rr = iw + (MS >> l) * (MS >> l);
+      for (int i = tid; i < rows * cols; i += T) {
+        const int r = i / cols, c = i - (i / cols) * cols;
+        const int o = r * (MS >> l) + q * cols + c;
+        const float2 p = pe[(r >> 1) * cc + (c >> 1)];
+        const float2 v = cscale(a[i], __ldg(&iw[o]));
+        const float w = __ldg(&rr[o]);
+        a[i] = f2(v.x + w * p.x, v.y + w * p.y);
       }
       __syncthreads();
     }
   }
-  // phase 3: up-pass inside each block and the increments w . Delta
-  for (int blk = tid; blk < NBS * NBS; blk += T) {
-    const int br = blk / NBS, bc = blk - (blk / NBS) * NBS;
-    float2 g0[BS][BS], g1[BS / 2][BS / 2];
-    const float2 gT = restrict_block(br, bc, g0, g1);
-    const float2 eT = deep ? lvl[blk] : cscale(gT, __ldg(&iwT[blk]));
-    float2 e1[BS / 2][BS / 2];
+  // phase 3: per strip, the up-pass to level 0 and the increments w . Delta
+  const float* iwT = pyr + lvl_off(MS, TT) + (MS >> TT) * (MS >> TT);
+  for (int base = 0; base < NS; base += SPAR) {
+    const int s = base + s0;
+    const bool ok = s < NS;
+    float2 g0[H], g1[H / 2];
+    const float2 gT = strip(s, ok, g0, g1);
+    const int R0 = s * H;
+    float2 eT = f2(0.f, 0.f);
+    if (ok) {
+      eT = deep ? lvl[off(TT) + s * (SLAB >> TT) + (gam >> TT)]
+                : cscale(gT, __ldg(&iwT[(R0 >> TT) * (MS >> TT) + (cgl >> TT)]));
+    }
+    float2 e1[H / 2];
     if constexpr (TT == 1) {
-      e1[0][0] = eT;
+      e1[0] = eT;
     } else {
 #pragma unroll
-      for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-          const int o = (2 * br + a) * (MS / 2) + 2 * bc + b;
-          const float2 v = cscale(g1[a][b], __ldg(&iw1[o]));
-          const float q = __ldg(&rr1[o]);
-          e1[a][b] = f2(v.x + q * eT.x, v.y + q * eT.y);
-        }
-    }
-#pragma unroll
-    for (int a = 0; a < BS; ++a)
-#pragma unroll
-      for (int b = 0; b < BS; ++b) {
-        const int o = (BS * br + a) * MS + BS * bc + b;
-        const float u = __ldg(&u0[o]);
-        const float2 ep = e1[a >> 1][b >> 1];
-        out[o] = f2(g0[a][b].x + u * ep.x, g0[a][b].y + u * ep.y);
+      for (int a = 0; a < 2; ++a) {
+        const int o = (R0 / 2 + a) * (MS / 2) + (cgl >> 1);
+        const float2 v = cscale(g1[a], ok ? __ldg(&iw1[o]) : 0.f);
+        const float w = ok ? __ldg(&rr1[o]) : 0.f;
+        e1[a] = f2(v.x + w * eT.x, v.y + w * eT.y);
       }
+    }
+    if (ok) {
+#pragma unroll
+      for (int a = 0; a < H; ++a) {
+        const int o = (R0 + a) * MS + cgl;
+        const float u = __ldg(&u0[o]);
+        out[o] = f2(g0[a].x + u * e1[a >> 1].x, g0[a].y + u * e1[a >> 1].y);
+      }
+    }
   }
 }
 
-// One thread block per window.  Launch with Geo<MS>::T threads and
-// Geo<MS>::SMEM bytes of dynamic shared memory.
+// One cluster of Geo<MS>::CL blocks per window (grid = windows * CL), each
+// with Geo<MS>::T threads and Geo<MS>::SMEM bytes of dynamic shared memory.
 template <int MS, int MODE>
-__global__ void __launch_bounds__(Geo<MS>::T) window_kernel(StepArgs A) {
+__global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel(StepArgs A) {
   using Gm = Geo<MS>;
-  constexpr int E = Gm::E, G = Gm::G, T = Gm::T, SP = Gm::SP, M = Gm::M;
+  constexpr int E = Gm::E, G = Gm::G, CL = Gm::CL, SLAB = Gm::SLAB, T = Gm::T, M = Gm::M;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* S = reinterpret_cast<float2*>(smem_raw);
-  float2* tws = S + MS * SP;
+  float2* X = reinterpret_cast<float2*>(smem_raw);
+  float2* Y = X + Gm::XN;
+  float2* tws = Y + Gm::XN;
   float2* lvl = tws + MS;
-  double* red = reinterpret_cast<double*>(lvl + Gm::LVL);
+  double* red = reinterpret_cast<double*>(lvl + Gm::LVL);  // [0,32) warp sums, [32,48) block partials
 
   const int tid = threadIdx.x;
-  const int k = A.idx[blockIdx.x];
+  int q = 0;
+  if constexpr (CL > 1) q = (int)cg::this_cluster().block_rank();
+  const int win = blockIdx.x / CL;
+  const int k = A.idx[win];
   if ((unsigned)k >= (unsigned)A.n_pos) {
-    if (tid == 0) atomicOr(A.err, 1);
-    return;  // uniform across the block
+    if (tid == 0 && q == 0) atomicOr(A.err, 1);
+    return;  // uniform across the cluster
   }
   const int pr = A.pos[2 * k], pc = A.pos[2 * k + 1];
   const float2* zk = A.z + (size_t)pr * A.n_cols + pc;
   for (int i = tid; i < MS; i += T) tws[i] = A.tw[i];
   __syncthreads();
 
-  // ---- pass A: exit wave and column FFTs
-#pragma unroll
-  for (int it = 0; it < Gm::LPT; ++it) {
-    const int ln = it * T + tid;
-    const bool act = ln < Gm::LANES;
-    const int c = act ? ln / G : 0, g = ln % G;
+  const bool act = tid < Gm::LANES;
+  const int lam = act ? tid / G : 0, g = tid % G;
+  const int line = q * SLAB + lam;  // column (passes A, C) or row (pass B) of this lane group
+
+  // ---- pass A: exit wave and column FFTs; results go to the row owners' X
+  {
     float2 x[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int r = g + G * e;
-      x[e] = act ? cmul(__ldg(&A.Q[r * MS + c]), __ldg(&zk[(size_t)r * A.n_cols + c])) : f2(0.f, 0.f);
+      x[e] = act ? cmul(__ldg(&A.Q[r * MS + line]), __ldg(&zk[(size_t)r * A.n_cols + line])) : f2(0.f, 0.f);
     }
-    line_fwd<MS, false>(x, g, act, S + c, SP, tws);
+    line_fwd<MS, false>(x, g, act, [&](int sl) -> float2& { return Y[yi<MS>(sl, lam)]; }, tws);
 #pragma unroll
     for (int j = 0; j < E / G; ++j)
 #pragma unroll
-      for (int k2 = 0; k2 < G; ++k2)
-        if (act) S[(g + G * j + E * k2) * SP + c] = x[j * G + k2];
+      for (int k2 = 0; k2 < G; ++k2) {
+        const int kr = g + G * j + E * k2;
+        float2* dst = peer<CL>(X, (E * k2) / SLAB);
+        if (act) dst[xi<MS>(kr % SLAB, line)] = x[j * G + k2];
+      }
   }
-  __syncthreads();
+  window_sync<CL>();
 
-  // ---- pass B: row FFTs, modulus projection, inverse row FFTs
+  // ---- pass B: row FFTs, modulus projection, inverse row FFTs; results go
+  // to the column owners' Y
   float res = 0.f;
-  const float* ampk = A.amp + (size_t)k * M;
-#pragma unroll
-  for (int it = 0; it < Gm::LPT; ++it) {
-    const int ln = it * T + tid;
-    const bool act = ln < Gm::LANES;
-    const int kr = act ? ln / G : 0, g = ln % G;
-    float2* row = S + kr * SP;
+  {
+    const int kr = line;
     float2 x[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) x[e] = act ? row[g + G * e] : f2(0.f, 0.f);
+    for (int e = 0; e < E; ++e) x[e] = act ? X[xi<MS>(lam, g + G * e)] : f2(0.f, 0.f);
+    float av[E];
+    if constexpr (MODE != kSim) {
+      const float* ampr = A.amp + (size_t)k * M + kr * MS;
+#pragma unroll
+      for (int j = 0; j < E / G; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < G; ++k2) av[j * G + k2] = act ? __ldg(&ampr[g + G * j + E * k2]) : 0.f;
+    }
     __syncwarp();
-    line_fwd<MS, false>(x, g, act, row, 1, tws);
+    line_fwd<MS, false>(x, g, act, [&](int sl) -> float2& { return X[xi<MS>(lam, sl)]; }, tws);
     if constexpr (MODE == kSim) {
       float* outk = A.out_int + (size_t)k * M + kr * MS;
 #pragma unroll
@@ -438,94 +572,101 @@ __global__ void __launch_bounds__(Geo<MS>::T) window_kernel(StepArgs A) {
           const float2 P = x[j * G + k2];
           if (act) outk[g + G * j + E * k2] = P.x * P.x + P.y * P.y;
         }
+      return;  // no block reads another block's memory after the barrier above
     } else {
       constexpr float inv_m = 1.0f / float(M);
 #pragma unroll
-      for (int j = 0; j < E / G; ++j)
-#pragma unroll
-        for (int k2 = 0; k2 < G; ++k2) {
-          const float a = act ? __ldg(&ampk[kr * MS + g + G * j + E * k2]) : 0.f;
-          const float2 P = x[j * G + k2];
-          const float p2 = P.x * P.x + P.y * P.y;
-          float mag;
-          float2 Pp;
-          if (p2 > 0.f) {
-            const float rs = rsqrtf(p2);
-            mag = p2 * rs;
-            const float s = a * rs * inv_m;
-            Pp = f2(P.x * s, P.y * s);
-          } else {
-            mag = 0.f;
-            Pp = f2(a * inv_m, 0.f);
-          }
-          const float dlt = mag - a;
-          res += dlt * dlt;
-          x[j * G + k2] = Pp;
+      for (int i = 0; i < E; ++i) {
+        const float a = av[i];
+        const float2 P = x[i];
+        const float p2 = P.x * P.x + P.y * P.y;
+        float mag;
+        float2 Pp;
+        if (p2 > 0.f) {
+          const float rs = rsqrtf(p2);
+          mag = p2 * rs;
+          const float sc = a * rs * inv_m;
+          Pp = f2(P.x * sc, P.y * sc);
+        } else {
+          mag = 0.f;
+          Pp = f2(a * inv_m, 0.f);
         }
-      line_inv<MS>(x, g, act, row, 1, tws);
+        const float dlt = mag - a;
+        res += dlt * dlt;
+        x[i] = Pp;
+      }
+      line_inv<MS>(x, g, act, [&](int sl) -> float2& { return X[xi<MS>(lam, sl)]; }, tws);
 #pragma unroll
-      for (int e = 0; e < E; ++e)
-        if (act) row[g + G * e] = x[e];
-    }
-  }
-  if constexpr (MODE == kSim) return;
-  __syncthreads();
-
-  // ---- pass C: inverse column FFTs, R_k, g = conj(Q)(R_k - Q z_k)
-  float gn2 = 0.f;
-  float2* out = A.contrib + (size_t)blockIdx.x * M;
-  const bool direct = (MODE == kStep) && A.levels == 1;
-#pragma unroll
-  for (int it = 0; it < Gm::LPT; ++it) {
-    const int ln = it * T + tid;
-    const bool act = ln < Gm::LANES;
-    const int c = act ? ln / G : 0, g = ln % G;
-    float2 x[E];
-#pragma unroll
-    for (int j = 0; j < E / G; ++j)
-#pragma unroll
-      for (int k2 = 0; k2 < G; ++k2) x[j * G + k2] = act ? S[(g + G * j + E * k2) * SP + c] : f2(0.f, 0.f);
-    __syncwarp();
-    line_inv<MS>(x, g, act, S + c, SP, tws);
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int r = g + G * e;
-      if (act) {
-        const float2 q = __ldg(&A.Q[r * MS + c]);
-        const float2 zz = __ldg(&zk[(size_t)r * A.n_cols + c]);
-        const float2 rho = csub(x[e], cmul(q, zz));
-        const float2 gg = cmul_cj(q, rho);
-        gn2 += gg.x * gg.x + gg.y * gg.y;
-        if (direct)
-          out[r * MS + c] = gg;
-        else
-          S[r * SP + c] = gg;
+      for (int e = 0; e < E; ++e) {
+        const int c = g + G * e;
+        float2* dst = peer<CL>(Y, (G * e) / SLAB);
+        if (act) dst[yi<MS>(kr, c % SLAB)] = x[e];
       }
     }
   }
+  if constexpr (MODE != kSim) {
+    const double rs = block_sum((double)res, red, tid, T);
+    if (tid == 0) peer<CL>(red, 0)[32 + q] = rs;
+    window_sync<CL>();
 
-  // per-window objective and gradient norm (float64 across the block)
-  const double rs = block_sum((double)res, red, tid, T);
-  const double gs = block_sum((double)gn2, red, tid, T);
-  if (tid == 0) {
-    A.phi_pos[k] = rs / (2.0 * (double)M);
-    A.gn_pos[k] = sqrt(gs);
+    // ---- pass C: inverse column FFTs, R_k, g = conj(Q)(R_k - Q z_k)
+    float gn2 = 0.f;
+    float2* out = A.contrib + (size_t)win * M;
+    const bool direct = (MODE == kStep) && A.levels == 1;
+    {
+      float2 x[E];
+#pragma unroll
+      for (int j = 0; j < E / G; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < G; ++k2) x[j * G + k2] = act ? Y[yi<MS>(g + G * j + E * k2, lam)] : f2(0.f, 0.f);
+      __syncwarp();
+      line_inv<MS>(x, g, act, [&](int sl) -> float2& { return Y[yi<MS>(sl, lam)]; }, tws);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int r = g + G * e;
+        if (act) {
+          const float2 qv = __ldg(&A.Q[r * MS + line]);
+          const float2 zz = __ldg(&zk[(size_t)r * A.n_cols + line]);
+          const float2 rho = csub(x[e], cmul(qv, zz));
+          const float2 gg = cmul_cj(qv, rho);
+          gn2 += gg.x * gg.x + gg.y * gg.y;
+          if (direct)
+            out[r * MS + line] = gg;
+          else
+            Y[yi<MS>(r, lam)] = gg;
+        }
+      }
+    }
+    const double gs = block_sum((double)gn2, red, tid, T);
+    if (tid == 0) peer<CL>(red, 0)[40 + q] = gs;
+    window_sync<CL>();
+    if (q == 0 && tid == 0) {
+      double a = 0.0, b = 0.0;
+      for (int i = 0; i < CL; ++i) {
+        a += red[32 + i];
+        b += red[40 + i];
+      }
+      A.phi_pos[k] = a / (2.0 * (double)M);
+      A.gn_pos[k] = sqrt(b);
+    }
+    if (MODE != kStep || direct) return;
+
+    // ---- pass D: MAGPS V-cycle (levels >= 2) on the column slab
+    if (A.levels == 2)
+      vcycle<MS, 1>(Y, lvl, A.pyr, A.levels, q, out, tid);
+    else
+      vcycle<MS, 2>(Y, lvl, A.pyr, A.levels, q, out, tid);
   }
-  if (MODE != kStep || direct) return;
-
-  // ---- pass D: MAGPS V-cycle (levels >= 2); block_sum synchronised S
-  if (A.levels == 2)
-    vcycle<MS, 1>(S, lvl, A.pyr, A.levels, out, tid);
-  else
-    vcycle<MS, 2>(S, lvl, A.pyr, A.levels, out, tid);
 }
 
 // z += sum_b contrib_b / sum_b w0 over the windows covering each pixel, in
-// minibatch order (bitwise reproducible).  One block per 32 x 32 object tile:
-// the block first lists, in minibatch order, the windows that overlap its
-// tile (a ballot compaction by warp 0), then each thread updates 4 pixels by
-// walking that short list.  Dynamic smem: count int2 corners + count ints.
-constexpr int kApplyTile = 32;
+// minibatch order (bitwise reproducible).  One block of 256 threads per
+// 16 x 16 object tile, one pixel per thread: the block first lists, in
+// minibatch order, the windows that overlap its tile (a ballot compaction by
+// warp 0); each thread then walks that short list four entries at a time with
+// predicated loads, so several increments are in flight per thread.
+// Dynamic smem: count int2 corners + count ints.
+constexpr int kApplyTile = 16;
 __global__ void __launch_bounds__(256) apply_kernel(float2* z, int n_rows, int n_cols, const int32_t* pos,
                                                     const int32_t* idx, int count, int n_pos,
                                                     const float2* contrib, const float* w0, int MS) {
@@ -557,32 +698,37 @@ __global__ void __launch_bounds__(256) apply_kernel(float2* z, int n_rows, int n
   }
   __syncthreads();
   const int nl = n_list;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int c = C0 + tx;
+  const int r = R0 + (threadIdx.x >> 4), c = C0 + (threadIdx.x & 15);
+  if (r >= n_rows || c >= n_cols) return;
+  const size_t M = (size_t)MS * MS;
+  float nx = 0.f, ny = 0.f, d = 0.f;
+  for (int j0 = 0; j0 < nl; j0 += 4) {
+    float2 v[4];
+    float wv[4];
 #pragma unroll
-  for (int i = 0; i < kApplyTile / 8; ++i) {
-    const int r = R0 + ty + 8 * i;
-    if (r >= n_rows || c >= n_cols) continue;
-    float nx = 0.f, ny = 0.f, d = 0.f;
-    for (int j = 0; j < nl; ++j) {
-      const int b = list[j];
+    for (int u = 0; u < 4; ++u) {
+      const int j = j0 + u;
+      const int b = j < nl ? list[j] : 0;
       const int2 q = corner[b];
       const int dr = r - q.x, dc = c - q.y;
-      if ((unsigned)dr < (unsigned)MS && (unsigned)dc < (unsigned)MS) {
-        const int o = dr * MS + dc;
-        const float2 v = contrib[(size_t)b * MS * MS + o];
-        nx += v.x;
-        ny += v.y;
-        d += __ldg(&w0[o]);
-      }
+      const bool in = j < nl && (unsigned)dr < (unsigned)MS && (unsigned)dc < (unsigned)MS;
+      const int o = in ? dr * MS + dc : 0;
+      v[u] = in ? contrib[(size_t)b * M + o] : make_float2(0.f, 0.f);
+      wv[u] = in ? __ldg(&w0[o]) : 0.f;
     }
-    if (d > 0.f) {
-      const size_t p = (size_t)r * n_cols + c;
-      float2 zz = z[p];
-      zz.x += nx / d;
-      zz.y += ny / d;
-      z[p] = zz;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      nx += v[u].x;
+      ny += v[u].y;
+      d += wv[u];
     }
+  }
+  if (d > 0.f) {
+    const size_t p = (size_t)r * n_cols + c;
+    float2 zz = z[p];
+    zz.x += nx / d;
+    zz.y += ny / d;
+    z[p] = zz;
   }
 }
 
@@ -715,8 +861,26 @@ int ilog2(int v) {
 }
 
 template <int MS, int MODE>
-cudaError_t launch_window(const StepArgs& a, int blocks, cudaStream_t st) {
-  window_kernel<MS, MODE><<<blocks, Geo<MS>::T, Geo<MS>::SMEM, st>>>(a);
+cudaError_t launch_window(const StepArgs& a, int windows, cudaStream_t st) {
+  using Gm = Geo<MS>;
+  if constexpr (Gm::CL == 1) {
+    window_kernel<MS, MODE><<<windows, Gm::T, Gm::SMEM, st>>>(a);
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)windows * Gm::CL, 1, 1);
+    cfg.blockDim = dim3(Gm::T, 1, 1);
+    cfg.dynamicSmemBytes = Gm::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = Gm::CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, window_kernel<MS, MODE>, a);
+    if (e != cudaSuccess) return e;
+  }
   return cudaGetLastError();
 }
 
