@@ -42,6 +42,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "magpie.h"
@@ -179,6 +180,13 @@ __device__ __forceinline__ int yi(int r, int gam) {
   constexpr int S = Geo<MS>::SLAB;
   return r * S + (gam ^ swz<S>(r));
 }
+
+// Programmatic dependent launch: let the next kernel in the stream start its
+// blocks (its own wait still covers all of this grid's memory), and wait for
+// the previous kernel's memory before touching what it wrote.  Both are
+// no-ops for launches without the programmatic-serialization attribute.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // Barrier over the window's blocks; with CL = 1 an ordinary block barrier.
 template <int CL>
@@ -508,9 +516,15 @@ __global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel
   double* red = reinterpret_cast<double*>(lvl + Gm::LVL);  // [0,32) warp sums, [32,48) block partials
 
   const int tid = threadIdx.x;
+  pdl_trigger();
   int q = 0;
   if constexpr (CL > 1) q = (int)cg::this_cluster().block_rank();
   const int win = blockIdx.x / CL;
+  // the twiddle table is written only by host copies, before any kernel of
+  // the library runs; everything else may come from the kernel just before
+  // (a window list, the object, the increments), so it is read after the wait
+  for (int i = tid; i < MS; i += T) tws[i] = A.tw[i];
+  pdl_wait();
   const int k = A.idx[win];
   if ((unsigned)k >= (unsigned)A.n_pos) {
     if (tid == 0 && q == 0) atomicOr(A.err, 1);
@@ -518,7 +532,6 @@ __global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel
   }
   const int pr = A.pos[2 * k], pc = A.pos[2 * k + 1];
   const float2* zk = A.z + (size_t)pr * A.n_cols + pc;
-  for (int i = tid; i < MS; i += T) tws[i] = A.tw[i];
   __syncthreads();
 
   const bool act = tid < Gm::LANES;
@@ -673,6 +686,8 @@ __global__ void __launch_bounds__(256) apply_kernel(float2* z, int n_rows, int n
   extern __shared__ int2 corner[];
   int* list = reinterpret_cast<int*>(corner + count);
   __shared__ int n_list;
+  pdl_trigger();
+  pdl_wait();  // window list, increments and object come from the kernels before
   const int R0 = blockIdx.y * kApplyTile, C0 = blockIdx.x * kApplyTile;
   for (int i = threadIdx.x; i < count; i += blockDim.x) {
     const int k = idx[i];
@@ -860,28 +875,47 @@ int ilog2(int v) {
   return r;
 }
 
+// Launch with the programmatic-stream-serialization attribute (and a cluster
+// dimension when cl > 1): the kernel may start while its predecessor in the
+// stream finishes; its pdl_wait() orders it after that predecessor's memory.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, int cl,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  int n = 0;
+  attr[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[n].val.programmaticStreamSerializationAllowed = 1;
+  ++n;
+  if (cl > 1) {
+    attr[n].id = cudaLaunchAttributeClusterDimension;
+    attr[n].val.clusterDim.x = cl;
+    attr[n].val.clusterDim.y = 1;
+    attr[n].val.clusterDim.z = 1;
+    ++n;
+  }
+  cfg.attrs = attr;
+  cfg.numAttrs = n;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
 template <int MS, int MODE>
 cudaError_t launch_window(const StepArgs& a, int windows, cudaStream_t st) {
   using Gm = Geo<MS>;
-  if constexpr (Gm::CL == 1) {
-    window_kernel<MS, MODE><<<windows, Gm::T, Gm::SMEM, st>>>(a);
-  } else {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)windows * Gm::CL, 1, 1);
-    cfg.blockDim = dim3(Gm::T, 1, 1);
-    cfg.dynamicSmemBytes = Gm::SMEM;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = Gm::CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, window_kernel<MS, MODE>, a);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaGetLastError();
+  return launch_pdl(window_kernel<MS, MODE>, dim3((unsigned)windows * Gm::CL), dim3(Gm::T), Gm::SMEM, st, Gm::CL, a);
+}
+
+cudaError_t launch_apply(float2* z, int n_rows, int n_cols, const int32_t* pos, const int32_t* idx, int count,
+                         int n_pos, const float2* contrib, const float* w0, int MS, cudaStream_t st) {
+  const dim3 tiles((n_cols + kApplyTile - 1) / kApplyTile, (n_rows + kApplyTile - 1) / kApplyTile);
+  return launch_pdl(apply_kernel, tiles, dim3(256), (sizeof(int2) + sizeof(int)) * count, st, 1, z, n_rows, n_cols,
+                    pos, idx, count, n_pos, contrib, w0, MS);
 }
 
 template <int MODE>
@@ -990,11 +1024,9 @@ int enqueue_step(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st, 
   if (ev) CUDA_TRY(cudaEventRecord(ev[0], st));
   CUDA_TRY(launch_window_m<kStep>(c->p.m, a, count, st));
   if (ev) CUDA_TRY(cudaEventRecord(ev[1], st));
-  const dim3 tiles((c->p.n_cols + kApplyTile - 1) / kApplyTile, (c->p.n_rows + kApplyTile - 1) / kApplyTile);
   if (ev) CUDA_TRY(cudaEventRecord(ev[2], st));
-  apply_kernel<<<tiles, 256, (sizeof(int2) + sizeof(int)) * count, st>>>(
-      c->z, c->p.n_rows, c->p.n_cols, c->pos, idx, count, c->p.n_pos, c->contrib, c->pyr + c->M, c->p.m);
-  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(launch_apply(c->z, c->p.n_rows, c->p.n_cols, c->pos, idx, count, c->p.n_pos, c->contrib, c->pyr + c->M,
+                        c->p.m, st));
   if (ev) CUDA_TRY(cudaEventRecord(ev[3], st));
   return MAGPIE_OK;
 }
@@ -1447,10 +1479,8 @@ int magpie_step_noalloc(void* object, int32_t n_rows, int32_t n_cols, const void
   a.gn_pos = gnorm;
   a.err = w.err;
   CUDA_TRY(launch_window_m<kStep>(m, a, count, st));
-  const dim3 tiles((n_cols + kApplyTile - 1) / kApplyTile, (n_rows + kApplyTile - 1) / kApplyTile);
-  apply_kernel<<<tiles, 256, (sizeof(int2) + sizeof(int)) * count, st>>>(
-      (float2*)object, n_rows, n_cols, positions, w.idx, count, n_pos, w.contrib, w.pyr + m * m, m);
-  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(launch_apply((float2*)object, n_rows, n_cols, positions, w.idx, count, n_pos, w.contrib, w.pyr + m * m, m,
+                        st));
   int h = 0;
   CUDA_TRY(cudaMemcpyAsync(&h, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
