@@ -57,6 +57,22 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def max_over_ranks(x: float, pg, device) -> float:
+    """The largest x over all ranks of the process group (x itself alone)."""
+    if pg is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, steps: int, n_pos: int, slowest_ms: float) -> float:
+    """patterns/s of all replicas together: every rank ran `steps` sweeps of
+    `n_pos` windows; the job took as long as its slowest rank."""
+    return world * steps * n_pos / (slowest_ms * 1e-3)
+
+
 def peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -271,11 +287,7 @@ def run_ours(args, w):
         pg.barrier()
     torch.cuda.synchronize()
     clk = clocks.stop()
-    total_ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if pg:
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)), pg, dev)
 
     # dominant kernel: the per-window kernel, timed with events captured in
     # the sweep graph over the same kind of sweeps
@@ -303,11 +315,7 @@ def run_ours(args, w):
     t0 = time.perf_counter()
     for s in range(args.steps):
         magpie.magpie_sweep_host(ctx, order_h[s], d_pin, z_out)
-    e2e_s = time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if pg:
-        pg.all_reduce(e2e_t, op=pg.ReduceOp.MAX)
-    e2e_s = float(e2e_t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, pg, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -317,7 +325,7 @@ def run_ours(args, w):
                          f"FP64 NumPy oracle on 1 of {os.cpu_count()} host cores"}
     ctx.close()
     if rank == 0:
-        value = world * args.steps * w.n_pos / (total_ms * 1e-3)
+        value = whole_job_value(world, args.steps, w.n_pos, total_ms)
         line = {
             "metric": "patterns/s per sweep", "value": value, "unit": "patterns/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -335,7 +343,7 @@ def run_ours(args, w):
                          "apply_kernel_ms_per_sweep": ap_ms / prof_sweeps,
                          "window_kernel_ms_per_sweep": wk_ms / prof_sweeps},
             "cpu_baseline": cpu,
-            "e2e": {"value": world * args.steps * w.n_pos / e2e_s, "unit": "patterns/s",
+            "e2e": {"value": whole_job_value(world, args.steps, w.n_pos, 1e3 * e2e_s), "unit": "patterns/s",
                     "h2d_bytes_per_step": 4 * w.n_pos + 4 * w.n_pos * w.m * w.m,
                     "d2h_bytes_per_step": 8 * w.n * w.n,
                     "call": "magpie_sweep_host (order and intensities in, object out, pinned buffers)"},

@@ -63,7 +63,7 @@ typedef struct magpie_ctx magpie_ctx;
 
 typedef struct {
   int32_t n_rows, n_cols; /* object size; both >= m                               */
-  int32_t m;              /* probe / window side: 8, 16, 32, 64 or 128             */
+  int32_t m;              /* probe / window side: 8, 16, 32, 64, 128 or 256        */
   int32_t n_pos;          /* N >= 1                                                 */
   int32_t levels;         /* grids including the finest, 1 <= levels <= log2(m)+1;
                              1 is rPIE, L is MAGPIE_{L-1} of Section 5.1            */
@@ -187,7 +187,7 @@ const char* magpie_strerror(int code);
  * synchronisation (and its chance of failing under memory pressure) is not
  * acceptable.  It needs no context and calls no allocation routine: its
  * workspace (the per-window increments, the per-level probe factors and the
- * twiddles) lives in one fixed array of about 9 MiB that every GPU loading
+ * twiddles) lives in one fixed array of about 9.5 MiB that every GPU loading
  * this library holds until the process exits.  This entry point is an
  * addition of this library; the paper has no counterpart.
  *   object      : DEVICE complex [n_rows][n_cols], updated in place
@@ -200,8 +200,8 @@ const char* magpie_strerror(int code);
  *   phi, gnorm  : DEVICE float64 [n_pos] outputs, Phi_k and ||grad Phi_k||
  *                 of the windows of this minibatch (other entries untouched)
  *   stream      : cudaStream_t as void*
- * Limits: m as for magpie_create, count * m^2 <= 2^20 (e.g. 64 windows of
- * 128 x 128), otherwise MAGPIE_EINVAL.  Windows whose index or position is
+ * Limits: m <= 128 (MAGPIE_EUNSUPPORTED otherwise), count * m^2 <= 2^20
+ * (e.g. 64 windows of 128 x 128), otherwise MAGPIE_EINVAL.  Windows whose index or position is
  * out of range are skipped and reported as MAGPIE_EINDEX.  Synchronous: it
  * waits for the step to finish before returning.  The first call on each
  * device looks up the workspace's device address (cudaGetSymbolAddress) with

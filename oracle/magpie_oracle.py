@@ -22,6 +22,13 @@ notes of the repository):
     <= 1e-30 is set to 0 (W_z, W_R, W_u^H and the proximal factor
     conj(Q) / (u + |Q|^2) at coarse levels, where the complex bin mean of Q
     can vanish).  -- parity unpinned
+  * Probe step (optional, off by default; the paper keeps Q fixed and names
+    blind ptychography as future work): the same surrogate minimised over Q
+    with the object fixed, by the symmetry of 1/2 || Q . z_k - R_k ||^2 in Q
+    and z_k: Q <- Q + sum_k conj(z_k)(R_k - Q z_k) / sum_k (u_Q,k + |z_k|^2),
+    u_Q,k = beta (max |z_k|^2 - |z_k|^2), all windows of the minibatch from the
+    same (z, Q).  -- parity pinned only as the exact minimiser of that
+    proximal surrogate and by full-batch monotone descent
   * Minibatch step: the paper updates one window at a time (Algorithm
     MAGPIE).  For a minibatch every window starts from the same z; the
     increments Delta_k are combined as z <- z + sum_k P_k^T (w . Delta_k) /
@@ -260,6 +267,32 @@ def minibatch_step(z, Q, positions, d, u, levels, batch):
     lit = den > 0
     out[lit] += num[lit] / den[lit]
     return out
+
+
+def probe_step(z, Q, positions, d, beta, batch):
+    """Probe update of one minibatch (module docstring, reading R2): every
+    window from the same (z, Q); returns the new probe."""
+    m = Q.shape[0]
+    num = np.zeros(Q.shape, dtype=np.complex128)
+    den = np.zeros(Q.shape, dtype=np.float64)
+    for k in batch:
+        zk = extract(z, positions[k], m)
+        Rk = revised_exit_wave(zk, Q, d[k])
+        a2 = np.abs(zk) ** 2
+        num += np.conj(zk) * (Rk - Q * zk)
+        den += beta * (a2.max() - a2) + a2
+    out = np.array(Q, dtype=np.complex128, copy=True)
+    lit = den > 0
+    out[lit] += num[lit] / den[lit]
+    return out
+
+
+def minibatch_step_with_probe(z, Q, positions, d, alpha, levels, batch, beta):
+    """Object and probe updated together from the same (z, Q): the object by
+    minibatch_step with u = u^rPIE(Q), the probe by probe_step."""
+    u = rpie_regulariser(Q, alpha)
+    return (minibatch_step(z, Q, positions, d, u, levels, batch),
+            probe_step(z, Q, positions, d, beta, batch))
 
 
 def sweep(z, Q, positions, d, u, levels, order, minibatch):

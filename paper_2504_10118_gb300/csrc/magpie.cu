@@ -53,6 +53,7 @@ namespace cg = cooperative_groups;
 
 constexpr int kVersion = 10000;  // 1.0.0
 constexpr int kMaxMinibatch = 4096;  // the update kernel keeps the minibatch's corners in smem (48 KiB)
+constexpr int kMaxCluster = 8;       // largest number of blocks per window
 
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
@@ -144,6 +145,7 @@ template <> struct Cfg<16> { static constexpr int E = 4, G = 4, CL = 1; };
 template <> struct Cfg<32> { static constexpr int E = 8, G = 4, CL = 1; };
 template <> struct Cfg<64> { static constexpr int E = 8, G = 8, CL = 2; };
 template <> struct Cfg<128> { static constexpr int E = 16, G = 8, CL = 4; };
+template <> struct Cfg<256> { static constexpr int E = 16, G = 16, CL = 8; };
 
 template <int MS> struct Geo {
   static constexpr int E = Cfg<MS>::E, G = Cfg<MS>::G, CL = Cfg<MS>::CL;
@@ -154,11 +156,11 @@ template <int MS> struct Geo {
   static constexpr int LANES = SLAB * G;  // one lane group per line of the slab
   static constexpr int T = LANES < 32 ? 32 : LANES;
   static_assert(T <= 1024 && T % 32 == 0, "block size");
-  static constexpr int XN = SLAB * MS;  // complex entries of X and of Y
+  static constexpr int XN = SLAB * MS;  // complex entries of each of X and Y
   static constexpr int LVL = (MS / 4) * (SLAB / 4) * 2 + 4 * CL * CL + 32;
   // resident blocks per SM the register budget is sized for (two 4-block
   // windows' worth of slabs share an SM for m = 128)
-  static constexpr int MIN_BLOCKS = T >= 256 ? 2 : 1;
+  static constexpr int MIN_BLOCKS = (T >= 256 && T < 512) ? 2 : 1;
   static constexpr size_t SMEM = sizeof(float2) * (2 * size_t(XN) + MS + LVL) + sizeof(double) * 64;
 };
 
@@ -187,6 +189,22 @@ __device__ __forceinline__ int yi(int r, int gam) {
 // no-ops for launches without the programmatic-serialization attribute.
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Split barrier over the window's blocks: arrive (releasing this thread's
+// earlier shared-memory writes, local and remote) ... independent work ...
+// wait (acquiring the other blocks' writes).  With CL = 1 the wait is an
+// ordinary block barrier.
+template <int CL>
+__device__ __forceinline__ void window_arrive() {
+  if constexpr (CL > 1) asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+template <int CL>
+__device__ __forceinline__ void window_wait() {
+  if constexpr (CL > 1)
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+  else
+    __syncthreads();
+}
 
 // Barrier over the window's blocks; with CL = 1 an ordinary block barrier.
 template <int CL>
@@ -288,6 +306,8 @@ struct StepArgs {
   int levels;
   double* phi_pos;    // per-window Phi_k
   double* gn_pos;     // per-window ||grad Phi_k||
+  double* part;       // [windows][CL][2] block partials of the two sums (CL > 1)
+  unsigned* cnt;      // [windows] blocks done, reset to 0 by the last one (CL > 1)
   int* err;           // bit 0: window index out of range
 };
 
@@ -509,11 +529,11 @@ __global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel
   using Gm = Geo<MS>;
   constexpr int E = Gm::E, G = Gm::G, CL = Gm::CL, SLAB = Gm::SLAB, T = Gm::T, M = Gm::M;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* X = reinterpret_cast<float2*>(smem_raw);
-  float2* Y = X + Gm::XN;
+  float2* X = reinterpret_cast<float2*>(smem_raw);  // row slab
+  float2* Y = X + Gm::XN;                            // column slab
   float2* tws = Y + Gm::XN;
   float2* lvl = tws + MS;
-  double* red = reinterpret_cast<double*>(lvl + Gm::LVL);  // [0,32) warp sums, [32,48) block partials
+  double* red = reinterpret_cast<double*>(lvl + Gm::LVL);  // block_sum scratch
 
   const int tid = threadIdx.x;
   pdl_trigger();
@@ -538,7 +558,8 @@ __global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel
   const int lam = act ? tid / G : 0, g = tid % G;
   const int line = q * SLAB + lam;  // column (passes A, C) or row (pass B) of this lane group
 
-  // ---- pass A: exit wave and column FFTs; results go to the row owners' X
+  // ---- pass A: exit wave Q z_k and column FFTs; results go to the row
+  // owners' X
   {
     float2 x[E];
 #pragma unroll
@@ -556,7 +577,17 @@ __global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel
         if (act) dst[xi<MS>(kr % SLAB, line)] = x[j * G + k2];
       }
   }
-  window_sync<CL>();
+  window_arrive<CL>();
+  // amplitudes of this block's rows, fetched while the other blocks finish
+  float av[E];
+  if constexpr (MODE != kSim) {
+    const float* ampr = A.amp + (size_t)k * M + line * MS;
+#pragma unroll
+    for (int j = 0; j < E / G; ++j)
+#pragma unroll
+      for (int k2 = 0; k2 < G; ++k2) av[j * G + k2] = act ? __ldg(&ampr[g + G * j + E * k2]) : 0.f;
+  }
+  window_wait<CL>();
 
   // ---- pass B: row FFTs, modulus projection, inverse row FFTs; results go
   // to the column owners' Y
@@ -566,14 +597,6 @@ __global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel
     float2 x[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) x[e] = act ? X[xi<MS>(lam, g + G * e)] : f2(0.f, 0.f);
-    float av[E];
-    if constexpr (MODE != kSim) {
-      const float* ampr = A.amp + (size_t)k * M + kr * MS;
-#pragma unroll
-      for (int j = 0; j < E / G; ++j)
-#pragma unroll
-        for (int k2 = 0; k2 < G; ++k2) av[j * G + k2] = act ? __ldg(&ampr[g + G * j + E * k2]) : 0.f;
-    }
     __syncwarp();
     line_fwd<MS, false>(x, g, act, [&](int sl) -> float2& { return X[xi<MS>(lam, sl)]; }, tws);
     if constexpr (MODE == kSim) {
@@ -618,14 +641,10 @@ __global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel
     }
   }
   if constexpr (MODE != kSim) {
-    const double rs = block_sum((double)res, red, tid, T);
-    if (tid == 0) peer<CL>(red, 0)[32 + q] = rs;
-    window_sync<CL>();
+    window_arrive<CL>();
+    window_wait<CL>();
 
-    // ---- pass C: inverse column FFTs, R_k, g = conj(Q)(R_k - Q z_k)
-    float gn2 = 0.f;
-    float2* out = A.contrib + (size_t)win * M;
-    const bool direct = (MODE == kStep) && A.levels == 1;
+    // ---- pass C: inverse column FFTs; R_k into Y
     {
       float2 x[E];
 #pragma unroll
@@ -635,32 +654,61 @@ __global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel
       __syncwarp();
       line_inv<MS>(x, g, act, [&](int sl) -> float2& { return Y[yi<MS>(sl, lam)]; }, tws);
 #pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int r = g + G * e;
-        if (act) {
-          const float2 qv = __ldg(&A.Q[r * MS + line]);
-          const float2 zz = __ldg(&zk[(size_t)r * A.n_cols + line]);
-          const float2 rho = csub(x[e], cmul(qv, zz));
-          const float2 gg = cmul_cj(qv, rho);
-          gn2 += gg.x * gg.x + gg.y * gg.y;
+      for (int e = 0; e < E; ++e)
+        if (act) Y[yi<MS>(g + G * e, lam)] = x[e];
+    }
+    __syncthreads();
+
+    // ---- g^0 = conj(Q)(R_k - Q z_k) over the slab, lane = column (row-coalesced
+    // probe and object loads); into Y, or straight to the increments for one
+    // level
+    float gn2 = 0.f;
+    float2* out = A.contrib + (size_t)win * M;
+    const bool direct = (MODE == kStep) && A.levels == 1;
+    {
+      constexpr int SPAR = T / SLAB;
+      const int gam = tid % SLAB, r0 = tid / SLAB;
+      const int cgl = q * SLAB + gam;
+      for (int r = r0; r < MS; r += SPAR) {
+        const int o = yi<MS>(r, gam);
+        const float2 qv = __ldg(&A.Q[r * MS + cgl]);
+        const float2 zz = __ldg(&zk[(size_t)r * A.n_cols + cgl]);
+        const float2 gg = cmul_cj(qv, csub(Y[o], cmul(qv, zz)));
+        gn2 += gg.x * gg.x + gg.y * gg.y;
+        if (MODE == kStep) {
           if (direct)
-            out[r * MS + line] = gg;
+            out[r * MS + cgl] = gg;
           else
-            Y[yi<MS>(r, lam)] = gg;
+            Y[o] = gg;
         }
       }
     }
+
+    // per-window Phi_k and ||grad Phi_k||: block sums in float64, combined in
+    // block order by the last block of the window to finish
+    const double rs = block_sum((double)res, red, tid, T);
     const double gs = block_sum((double)gn2, red, tid, T);
-    if (tid == 0) peer<CL>(red, 0)[40 + q] = gs;
-    window_sync<CL>();
-    if (q == 0 && tid == 0) {
-      double a = 0.0, b = 0.0;
-      for (int i = 0; i < CL; ++i) {
-        a += red[32 + i];
-        b += red[40 + i];
+    if (tid == 0) {
+      if constexpr (CL == 1) {
+        A.phi_pos[k] = rs / (2.0 * (double)M);
+        A.gn_pos[k] = sqrt(gs);
+      } else {
+        A.part[(size_t)(win * CL + q) * 2] = rs;
+        A.part[(size_t)(win * CL + q) * 2 + 1] = gs;
+        __threadfence();
+        const unsigned done = atomicAdd(&A.cnt[win], 1u);
+        if (done == CL - 1) {
+          __threadfence();
+          double a = 0.0, b = 0.0;
+          for (int i = 0; i < CL; ++i) {
+            a += __ldcg(&A.part[(size_t)(win * CL + i) * 2]);
+            b += __ldcg(&A.part[(size_t)(win * CL + i) * 2 + 1]);
+          }
+          A.phi_pos[k] = a / (2.0 * (double)M);
+          A.gn_pos[k] = sqrt(b);
+          A.cnt[win] = 0u;
+        }
       }
-      A.phi_pos[k] = a / (2.0 * (double)M);
-      A.gn_pos[k] = sqrt(b);
     }
     if (MODE != kStep || direct) return;
 
@@ -867,7 +915,7 @@ int fail(int code, const std::string& msg) {
                   std::string(#expr) + ": " + cudaGetErrorString(e_));                      \
   } while (0)
 
-bool supported_m(int m) { return m == 8 || m == 16 || m == 32 || m == 64 || m == 128; }
+bool supported_m(int m) { return m == 8 || m == 16 || m == 32 || m == 64 || m == 128 || m == 256; }
 
 int ilog2(int v) {
   int r = 0;
@@ -926,6 +974,7 @@ cudaError_t launch_window_m(int MS, const StepArgs& a, int blocks, cudaStream_t 
     case 32: return launch_window<32, MODE>(a, blocks, st);
     case 64: return launch_window<64, MODE>(a, blocks, st);
     case 128: return launch_window<128, MODE>(a, blocks, st);
+    case 256: return launch_window<256, MODE>(a, blocks, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -953,6 +1002,7 @@ cudaError_t prepare_kernels(int MS) {
     case 32: return prepare_size<32>();
     case 64: return prepare_size<64>();
     case 128: return prepare_size<128>();
+    case 256: return prepare_size<256>();
     default: return cudaErrorInvalidValue;
   }
 }
@@ -986,6 +1036,8 @@ struct magpie_ctx {
   float2* contrib = nullptr;
   double* phi_pos = nullptr;
   double* gn_pos = nullptr;
+  double* part = nullptr;     // [n_pos][kMaxCluster][2] per-block partial sums
+  unsigned* cnt = nullptr;    // [n_pos] blocks done per window slot
   int32_t* iota = nullptr;
   int32_t* order = nullptr;
   double* sums = nullptr;
@@ -1013,6 +1065,8 @@ StepArgs make_args(magpie_ctx* c, const int32_t* idx) {
   a.levels = c->p.levels;
   a.phi_pos = c->phi_pos;
   a.gn_pos = c->gn_pos;
+  a.part = c->part;
+  a.cnt = c->cnt;
   a.err = c->err;
   return a;
 }
@@ -1094,7 +1148,7 @@ int validate(const magpie_params* p) {
   if (p->m < 1 || (p->m & (p->m - 1)))
     return fail(MAGPIE_EINVAL, "m = " + std::to_string(p->m) + " is not a power of two");
   if (!supported_m(p->m))
-    return fail(MAGPIE_EUNSUPPORTED, "no kernel for m = " + std::to_string(p->m) + " (8..128)");
+    return fail(MAGPIE_EUNSUPPORTED, "no kernel for m = " + std::to_string(p->m) + " (8..256)");
   if (p->n_rows < p->m || p->n_cols < p->m) return fail(MAGPIE_EINVAL, "object smaller than the window");
   if ((long long)p->n_rows * p->n_cols > (1LL << 30)) return fail(MAGPIE_EINVAL, "object larger than 2^30 pixels");
   if (p->n_pos < 1) return fail(MAGPIE_EINVAL, "n_pos < 1");
@@ -1116,9 +1170,11 @@ constexpr size_t kNoAllocPyrBytes = sizeof(float) * 3 * 128 * 128;              
 constexpr size_t kNoAllocPyrQBytes = sizeof(double2) * 2 * 128 * 128;                              // FP64 probe levels
 constexpr size_t kNoAllocPyrUBytes = sizeof(double) * 2 * 128 * 128;                               // FP64 u levels
 constexpr size_t kNoAllocTwBytes = sizeof(float2) * 128;
-constexpr size_t kNoAllocIdxBytes = sizeof(int32_t) * (kNoAllocMaxIncrement / 64);                 // count <= 2^14
+constexpr size_t kNoAllocIdxBytes = sizeof(int32_t) * kMaxMinibatch;
+constexpr size_t kNoAllocPartBytes = sizeof(double) * 2 * kMaxCluster * kMaxMinibatch;              // 512 KiB
+constexpr size_t kNoAllocCntBytes = sizeof(unsigned) * kMaxMinibatch;
 constexpr size_t kNoAllocBytes = kNoAllocContribBytes + kNoAllocPyrBytes + kNoAllocPyrQBytes + kNoAllocPyrUBytes +
-                                 kNoAllocTwBytes + kNoAllocIdxBytes + 256;
+                                 kNoAllocTwBytes + kNoAllocIdxBytes + kNoAllocPartBytes + kNoAllocCntBytes + 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 // idx -> sanitized copy: a window whose index is outside [0, n_pos) or whose
@@ -1148,6 +1204,8 @@ struct NoAllocScratch {
   double* pyr_u;
   float2* tw;
   int32_t* idx;
+  double* part;
+  unsigned* cnt;
   int* err;
 };
 
@@ -1177,6 +1235,10 @@ int noalloc_scratch(NoAllocScratch* out) {
   b += kNoAllocTwBytes;
   out->idx = (int32_t*)b;
   b += kNoAllocIdxBytes;
+  out->part = (double*)b;
+  b += kNoAllocPartBytes;
+  out->cnt = (unsigned*)b;
+  b += kNoAllocCntBytes;
   out->err = (int*)b;
   return MAGPIE_OK;
 }
@@ -1208,7 +1270,7 @@ void magpie_destroy(magpie_ctx* c) {
     if (e) cudaEventDestroy(e);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   void* bufs[] = {c->Q, c->tw, c->amp, c->stage, c->pos, c->pyr, c->pyr_q, c->pyr_u, c->contrib,
-                  c->phi_pos, c->gn_pos, c->iota, c->order, c->sums, c->err};
+                  c->phi_pos, c->gn_pos, c->part, c->cnt, c->iota, c->order, c->sums, c->err};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete c;
@@ -1250,6 +1312,8 @@ int magpie_create(magpie_ctx** out, const magpie_params* params, void* object, c
       (rc = alloc((void**)&c->pyr_q, sizeof(double2) * 2 * M)) || (rc = alloc((void**)&c->pyr_u, sizeof(double) * 2 * M)) ||
       (rc = alloc((void**)&c->contrib, sizeof(float2) * M * p.minibatch)) ||
       (rc = alloc((void**)&c->phi_pos, sizeof(double) * N)) || (rc = alloc((void**)&c->gn_pos, sizeof(double) * N)) ||
+      (rc = alloc((void**)&c->part, sizeof(double) * 2 * kMaxCluster * N)) ||
+      (rc = alloc((void**)&c->cnt, sizeof(unsigned) * N)) ||
       (rc = alloc((void**)&c->iota, sizeof(int32_t) * N)) || (rc = alloc((void**)&c->order, sizeof(int32_t) * N)) ||
       (rc = alloc((void**)&c->sums, sizeof(double) * 2)) || (rc = alloc((void**)&c->err, sizeof(int))))
     return rc;
@@ -1276,6 +1340,7 @@ int magpie_create(magpie_ctx** out, const magpie_params* params, void* object, c
   CTX_TRY(cudaMemsetAsync(c->err, 0, sizeof(int), st));
   CTX_TRY(cudaMemsetAsync(c->phi_pos, 0, sizeof(double) * N, st));
   CTX_TRY(cudaMemsetAsync(c->gn_pos, 0, sizeof(double) * N, st));
+  CTX_TRY(cudaMemsetAsync(c->cnt, 0, sizeof(unsigned) * N, st));
   iota_kernel<<<(int)((N + 255) / 256), 256, 0, st>>>(c->iota, (int)N);
   CTX_TRY(cudaGetLastError());
   sqrt_kernel<<<1024, 256, 0, st>>>(intensities, c->amp, M * N);
@@ -1442,6 +1507,7 @@ int magpie_step_noalloc(void* object, int32_t n_rows, int32_t n_cols, const void
   if (rc) return rc;
   if (!object || !probe || !positions || !amplitudes || !idx || !phi || !gnorm)
     return fail(MAGPIE_EINVAL, "a data pointer is NULL");
+  if (m > 128) return fail(MAGPIE_EUNSUPPORTED, "the fixed workspace holds probe factors for m <= 128");
   if ((size_t)count * (size_t)m * (size_t)m > kNoAllocMaxIncrement)
     return fail(MAGPIE_EINVAL, "count * m^2 = " + std::to_string((long long)count * m * m) +
                                    " exceeds the fixed scratch of 2^20 complex values");
@@ -1456,6 +1522,7 @@ int magpie_step_noalloc(void* object, int32_t n_rows, int32_t n_cols, const void
     htw[t] = make_float2((float)std::cos(ang), (float)std::sin(ang));
   }
   CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+  CUDA_TRY(cudaMemsetAsync(w.cnt, 0, sizeof(unsigned) * count, st));
   CUDA_TRY(cudaMemcpyAsync(w.tw, htw, sizeof(float2) * m, cudaMemcpyHostToDevice, st));
   sanitize_idx_kernel<<<(count + 255) / 256, 256, 0, st>>>(idx, count, positions, n_pos, n_rows, n_cols, m, w.idx,
                                                             w.err);
@@ -1477,6 +1544,8 @@ int magpie_step_noalloc(void* object, int32_t n_rows, int32_t n_cols, const void
   a.levels = levels;
   a.phi_pos = phi;
   a.gn_pos = gnorm;
+  a.part = w.part;
+  a.cnt = w.cnt;
   a.err = w.err;
   CUDA_TRY(launch_window_m<kStep>(m, a, count, st));
   CUDA_TRY(launch_apply((float2*)object, n_rows, n_cols, positions, w.idx, count, n_pos, w.contrib, w.pyr + m * m, m,

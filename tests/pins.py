@@ -428,6 +428,37 @@ def check_recovery(O):
     assert last < 1e-6 < first, (first, last)
 
 
+def check_probe_step(O):
+    """Probe step (reading R2): it zeroes the gradient in Q of
+    sum_k [1/2 ||Q . z_k - R_k||^2 + 1/2 u_Q,k^T |Q - Q^(j)|^2] with R_k and
+    z_k from the current iterate, and a full-batch probe step never increases
+    Phi (majorization, with the roles of Q and z_k exchanged)."""
+    z_true, Q_true, pos, d = _small_problem(O, seed=19)
+    rng = np.random.default_rng(19)
+    z = z_true + 0.1 * _crand(rng, *z_true.shape)
+    Qj = Q_true * (1 + 0.2 * _crand(rng, *Q_true.shape))
+    m = Qj.shape[0]
+    beta = 0.3
+    batch = np.array([0, 3, 5, 6])
+    Qp = O.probe_step(z, Qj, pos, d, beta, batch)
+    grad = np.zeros(Qj.shape, dtype=np.complex128)
+    for k in batch:
+        zk = O.extract(z, pos[k], m)
+        Rk = O.revised_exit_wave(zk, Qj, d[k])
+        a2 = np.abs(zk) ** 2
+        uq = beta * (a2.max() - a2)
+        grad += np.conj(zk) * (Qp * zk - Rk) + uq * (Qp - Qj)
+    assert np.abs(grad).max() < 1e-10 * np.abs(Qj).max()
+    allk = np.arange(len(pos))
+    prev = O.objective(z, Qj, pos, d)
+    Qc = Qj
+    for it in range(5):
+        Qc = O.probe_step(z, Qc, pos, d, beta, allk)
+        cur = O.objective(z, Qc, pos, d)
+        assert cur <= prev * (1 + 1e-12)
+        prev = cur
+
+
 ALL_CHECKS = [
     check_dft_defining_sum, check_dft_parseval_inverse, check_dft_closed_forms,
     check_scan_adjoint, check_transfer_operators, check_objective_forms,
@@ -436,5 +467,5 @@ ALL_CHECKS = [
     check_weight_properties, check_coarse_step_closed_form,
     check_coarse_prox_is_argmin, check_auto_regularisation,
     check_consistency_bounds, check_residual_form, check_special_cases,
-    check_recovery,
+    check_probe_step, check_recovery,
 ]

@@ -60,7 +60,7 @@ def _create(L, **kw):
 
 @pytest.mark.parametrize("kw,code", [
     (dict(m=12), magpie.EINVAL),
-    (dict(m=256), magpie.EUNSUPPORTED),
+    (dict(m=512, n_rows=1024, n_cols=1024), magpie.EUNSUPPORTED),
     (dict(m=4), magpie.EUNSUPPORTED),
     (dict(levels=0), magpie.EINVAL),
     (dict(levels=7), magpie.EINVAL),

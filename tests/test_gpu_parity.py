@@ -68,7 +68,7 @@ def dev_i32(a):
 
 
 # ------------------------------------------------------------- forward model
-@pytest.mark.parametrize("m", [8, 16, 32, 64, 128])
+@pytest.mark.parametrize("m", [8, 16, 32, 64, 128, 256])
 def test_forward_intensities(m):
     n = 3 * m
     z = f32(synth.make_object(n))
@@ -94,6 +94,8 @@ STEP_CASES = [
     (192, 64, 6, 24, 2, 1, 9, 9), (192, 64, 6, 24, 2, 3, 9, 9), (192, 64, 6, 24, 2, 7, 9, 5),
     (256, 128, 5, 30, 2, 1, 6, 6), (256, 128, 5, 30, 2, 3, 6, 6), (256, 128, 5, 30, 2, 4, 6, 4),
     (256, 128, 5, 30, 2, 8, 25, 25),
+    (512, 256, 3, 100, 2, 1, 4, 4), (512, 256, 3, 100, 2, 4, 9, 9), (512, 256, 3, 100, 2, 6, 3, 3),
+    (512, 256, 3, 100, 2, 9, 9, 9),
 ]
 
 
