@@ -69,7 +69,22 @@ typedef struct {
                              1 is rPIE, L is MAGPIE_{L-1} of Section 5.1            */
   int32_t minibatch;      /* B, 1 <= B <= min(n_pos, 4096)                          */
   float alpha;            /* rPIE constant, finite and >= 0 (Section 2.1)           */
+  int32_t update_probe;   /* 0: the probe is known and fixed (the paper); 1: every
+                             minibatch step also moves the context's probe (below)  */
+  float beta;             /* probe regulariser when update_probe = 1, >= 0          */
 } magpie_params;
+
+/*
+ * Probe step (update_probe = 1; an extension: the paper keeps Q fixed and
+ * names blind ptychography as future work).  From the same (z, Q) as the
+ * object step, the surrogate 1/2 || Q . z_k - R_k ||^2, symmetric in Q and
+ * z_k, is minimised over Q with a proximal term:
+ *   Q <- Q + sum_k conj(z_k)(R_k - Q z_k) / sum_k (u_Q,k + |z_k|^2),
+ *   u_Q,k = beta (max |z_k|^2 - |z_k|^2),
+ * on probe pixels with a positive denominator; the regulariser and the
+ * per-level factors are then recomputed from the new probe.  The context
+ * keeps its own probe; magpie_get_probe copies it out.
+ */
 
 /*
  * Create a reconstruction context (Algorithm MAGPIE's inputs z^(0), Q,
@@ -124,6 +139,9 @@ int magpie_sweep(magpie_ctx* ctx, const int32_t* order);
  */
 int magpie_profile_sweep(magpie_ctx* ctx, const int32_t* order, double* window_ms, double* apply_ms,
                          int32_t* launches);
+
+/* Copy the context's current probe to `probe` (DEVICE complex [m][m]). */
+int magpie_get_probe(magpie_ctx* ctx, void* probe);
 
 /*
  * Phi(z) of Eq. (exit_misfit) at the current object over all N windows,
@@ -216,7 +234,7 @@ int magpie_step_noalloc(void* object, int32_t n_rows, int32_t n_cols, const void
 /* Message of the calling thread's most recent failed call ("" if none). */
 const char* magpie_last_error(void);
 
-/* Library version as major*10000 + minor*100 + patch. */
+/* Library version as major*10000 + minor*100 + patch (this is 1.1.0). */
 int magpie_version(void);
 
 #ifdef __cplusplus

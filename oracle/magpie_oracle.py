@@ -295,6 +295,13 @@ def minibatch_step_with_probe(z, Q, positions, d, alpha, levels, batch, beta):
             probe_step(z, Q, positions, d, beta, batch))
 
 
+def sweep_with_probe(z, Q, positions, d, alpha, levels, order, minibatch, beta):
+    """One iteration over all windows updating object and probe per minibatch."""
+    for s in range(0, len(order), minibatch):
+        z, Q = minibatch_step_with_probe(z, Q, positions, d, alpha, levels, order[s:s + minibatch], beta)
+    return z, Q
+
+
 def sweep(z, Q, positions, d, u, levels, order, minibatch):
     """One iteration over all windows: consecutive minibatches of `order`."""
     for s in range(0, len(order), minibatch):

@@ -51,7 +51,7 @@ namespace {
 
 namespace cg = cooperative_groups;
 
-constexpr int kVersion = 10000;  // 1.0.0
+constexpr int kVersion = 10100;  // 1.1.0
 constexpr int kMaxMinibatch = 4096;  // the update kernel keeps the minibatch's corners in smem (48 KiB)
 constexpr int kMaxCluster = 8;       // largest number of blocks per window
 
@@ -183,13 +183,6 @@ __device__ __forceinline__ int yi(int r, int gam) {
   return r * S + (gam ^ swz<S>(r));
 }
 
-// Programmatic dependent launch: let the next kernel in the stream start its
-// blocks (its own wait still covers all of this grid's memory), and wait for
-// the previous kernel's memory before touching what it wrote.  Both are
-// no-ops for launches without the programmatic-serialization attribute.
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
 // Split barrier over the window's blocks: arrive (releasing this thread's
 // earlier shared-memory writes, local and remote) ... independent work ...
 // wait (acquiring the other blocks' writes).  With CL = 1 the wait is an
@@ -304,10 +297,10 @@ struct StepArgs {
   float2* contrib;    // [windows][MS][MS] increments w . Delta
   const float* pyr;   // per-level factors
   int levels;
-  double* phi_pos;    // per-window Phi_k
-  double* gn_pos;     // per-window ||grad Phi_k||
-  double* part;       // [windows][CL][2] block partials of the two sums (CL > 1)
-  unsigned* cnt;      // [windows] blocks done, reset to 0 by the last one (CL > 1)
+  double* part;       // [windows][CL][2] block partials of the window's two sums
+  float2* pnum;       // probe step only: [windows][MS][MS] conj(z_k)(R_k - Q z_k)
+  float* pa2;         // probe step only: [windows][MS][MS] |z_k|^2
+  double* pmax;       // probe step only: [windows][CL] block maxima of |z_k|^2
   int* err;           // bit 0: window index out of range
 };
 
@@ -319,6 +312,18 @@ __device__ __forceinline__ double block_sum(double v, double* red, int tid, int 
   double r = 0.0;
   if (tid == 0)
     for (int i = 0; i < nthreads / 32; ++i) r += red[i];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ double block_max(double v, double* red, int tid, int nthreads) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (tid == 0)
+    for (int i = 0; i < nthreads / 32; ++i) r = fmax(r, red[i]);
   __syncthreads();
   return r;
 }
@@ -536,15 +541,10 @@ __global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel
   double* red = reinterpret_cast<double*>(lvl + Gm::LVL);  // block_sum scratch
 
   const int tid = threadIdx.x;
-  pdl_trigger();
   int q = 0;
   if constexpr (CL > 1) q = (int)cg::this_cluster().block_rank();
   const int win = blockIdx.x / CL;
-  // the twiddle table is written only by host copies, before any kernel of
-  // the library runs; everything else may come from the kernel just before
-  // (a window list, the object, the increments), so it is read after the wait
   for (int i = tid; i < MS; i += T) tws[i] = A.tw[i];
-  pdl_wait();
   const int k = A.idx[win];
   if ((unsigned)k >= (unsigned)A.n_pos) {
     if (tid == 0 && q == 0) atomicOr(A.err, 1);
@@ -558,15 +558,28 @@ __global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel
   const int lam = act ? tid / G : 0, g = tid % G;
   const int line = q * SLAB + lam;  // column (passes A, C) or row (pass B) of this lane group
 
-  // ---- pass A: exit wave Q z_k and column FFTs; results go to the row
-  // owners' X
+  // slab geometry of the row-coalesced passes: lane gam of a row of the
+  // block's column slab, rows r0, r0 + RSTEP, ...
+  constexpr int RSTEP = T / SLAB, RPT = MS / RSTEP;
+  const int gam = tid % SLAB, r0 = tid / SLAB;
+  const int cgl = q * SLAB + gam;
+
+  // ---- pass A: exit wave psi = Q z_k gathered row by row into Y, then the
+  // column FFTs; results go to the row owners' X
   {
+    float2 pv[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      const int r = r0 + RSTEP * i;
+      pv[i] = cmul(__ldg(&A.Q[r * MS + cgl]), __ldg(&zk[(size_t)r * A.n_cols + cgl]));
+    }
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) Y[yi<MS>(r0 + RSTEP * i, gam)] = pv[i];
+    __syncthreads();
     float2 x[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int r = g + G * e;
-      x[e] = act ? cmul(__ldg(&A.Q[r * MS + line]), __ldg(&zk[(size_t)r * A.n_cols + line])) : f2(0.f, 0.f);
-    }
+    for (int e = 0; e < E; ++e) x[e] = act ? Y[yi<MS>(g + G * e, lam)] : f2(0.f, 0.f);
+    __syncwarp();
     line_fwd<MS, false>(x, g, act, [&](int sl) -> float2& { return Y[yi<MS>(sl, lam)]; }, tws);
 #pragma unroll
     for (int j = 0; j < E / G; ++j)
@@ -642,7 +655,17 @@ __global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel
   }
   if constexpr (MODE != kSim) {
     window_arrive<CL>();
+    // the exit wave again, row by row, while the other blocks finish pass B;
+    // it is parked in X (free once every block of the window is past pass B)
+    float2 pv[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      const int r = r0 + RSTEP * i;
+      pv[i] = cmul(__ldg(&A.Q[r * MS + cgl]), __ldg(&zk[(size_t)r * A.n_cols + cgl]));
+    }
     window_wait<CL>();
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) X[yi<MS>(r0 + RSTEP * i, gam)] = pv[i];
 
     // ---- pass C: inverse column FFTs; R_k into Y
     {
@@ -659,23 +682,31 @@ __global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel
     }
     __syncthreads();
 
-    // ---- g^0 = conj(Q)(R_k - Q z_k) over the slab, lane = column (row-coalesced
-    // probe and object loads); into Y, or straight to the increments for one
-    // level
-    float gn2 = 0.f;
+    // ---- g^0 = conj(Q)(R_k - psi) over the slab, lane = column; into Y, or
+    // straight to the increments for one level
+    float gn2 = 0.f, amax = 0.f;
     float2* out = A.contrib + (size_t)win * M;
     const bool direct = (MODE == kStep) && A.levels == 1;
     {
-      constexpr int SPAR = T / SLAB;
-      const int gam = tid % SLAB, r0 = tid / SLAB;
-      const int cgl = q * SLAB + gam;
-      for (int r = r0; r < MS; r += SPAR) {
+      float2 qv[RPT];
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) qv[i] = __ldg(&A.Q[(r0 + RSTEP * i) * MS + cgl]);
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) {
+        const int r = r0 + RSTEP * i;
         const int o = yi<MS>(r, gam);
-        const float2 qv = __ldg(&A.Q[r * MS + cgl]);
-        const float2 zz = __ldg(&zk[(size_t)r * A.n_cols + cgl]);
-        const float2 gg = cmul_cj(qv, csub(Y[o], cmul(qv, zz)));
+        const float2 rho = csub(Y[o], X[o]);
+        const float2 gg = cmul_cj(qv[i], rho);
         gn2 += gg.x * gg.x + gg.y * gg.y;
         if (MODE == kStep) {
+          if (A.pnum) {
+            // the probe step's window terms (same R_k and z_k)
+            const float2 zz = __ldg(&zk[(size_t)r * A.n_cols + cgl]);
+            const float a2 = zz.x * zz.x + zz.y * zz.y;
+            A.pnum[(size_t)win * M + r * MS + cgl] = cmul_cj(zz, rho);
+            A.pa2[(size_t)win * M + r * MS + cgl] = a2;
+            amax = fmaxf(amax, a2);
+          }
           if (direct)
             out[r * MS + cgl] = gg;
           else
@@ -683,32 +714,18 @@ __global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel
         }
       }
     }
+    if (MODE == kStep && A.pnum) {
+      const double bm = block_max((double)amax, red, tid, T);
+      if (tid == 0) A.pmax[win * CL + q] = bm;
+    }
 
-    // per-window Phi_k and ||grad Phi_k||: block sums in float64, combined in
-    // block order by the last block of the window to finish
+    // block partials of the window's two sums (float64); the kernel that
+    // follows combines them in block order
     const double rs = block_sum((double)res, red, tid, T);
     const double gs = block_sum((double)gn2, red, tid, T);
     if (tid == 0) {
-      if constexpr (CL == 1) {
-        A.phi_pos[k] = rs / (2.0 * (double)M);
-        A.gn_pos[k] = sqrt(gs);
-      } else {
-        A.part[(size_t)(win * CL + q) * 2] = rs;
-        A.part[(size_t)(win * CL + q) * 2 + 1] = gs;
-        __threadfence();
-        const unsigned done = atomicAdd(&A.cnt[win], 1u);
-        if (done == CL - 1) {
-          __threadfence();
-          double a = 0.0, b = 0.0;
-          for (int i = 0; i < CL; ++i) {
-            a += __ldcg(&A.part[(size_t)(win * CL + i) * 2]);
-            b += __ldcg(&A.part[(size_t)(win * CL + i) * 2 + 1]);
-          }
-          A.phi_pos[k] = a / (2.0 * (double)M);
-          A.gn_pos[k] = sqrt(b);
-          A.cnt[win] = 0u;
-        }
-      }
+      A.part[(size_t)(win * CL + q) * 2] = rs;
+      A.part[(size_t)(win * CL + q) * 2 + 1] = gs;
     }
     if (MODE != kStep || direct) return;
 
@@ -730,12 +747,25 @@ __global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel
 constexpr int kApplyTile = 16;
 __global__ void __launch_bounds__(256) apply_kernel(float2* z, int n_rows, int n_cols, const int32_t* pos,
                                                     const int32_t* idx, int count, int n_pos,
-                                                    const float2* contrib, const float* w0, int MS) {
+                                                    const float2* contrib, const float* w0, int MS,
+                                                    const double* part, int CL, double* phi_pos, double* gn_pos) {
   extern __shared__ int2 corner[];
+  if (blockIdx.x == 0 && blockIdx.y == 0) {
+    // the window kernel's block partials -> Phi_k and ||grad Phi_k||, in block order
+    for (int b = threadIdx.x; b < count; b += blockDim.x) {
+      const int k = idx[b];
+      if ((unsigned)k >= (unsigned)n_pos) continue;
+      double a = 0.0, g = 0.0;
+      for (int q = 0; q < CL; ++q) {
+        a += part[(size_t)(b * CL + q) * 2];
+        g += part[(size_t)(b * CL + q) * 2 + 1];
+      }
+      phi_pos[k] = a / (2.0 * (double)MS * (double)MS);
+      gn_pos[k] = sqrt(g);
+    }
+  }
   int* list = reinterpret_cast<int*>(corner + count);
   __shared__ int n_list;
-  pdl_trigger();
-  pdl_wait();  // window list, increments and object come from the kernels before
   const int R0 = blockIdx.y * kApplyTile, C0 = blockIdx.x * kApplyTile;
   for (int i = threadIdx.x; i < count; i += blockDim.x) {
     const int k = idx[i];
@@ -801,83 +831,200 @@ __global__ void sqrt_kernel(const float* d, float* a, size_t n) {
 }
 
 // Per-level probe factors in float64 (Eq. def_weights and the rPIE
-// regulariser), one block.  scratch: complex levels of Q and real levels of
-// u, each laid out level after level.
-__global__ void __launch_bounds__(1024) pyramid_kernel(const float2* Q, int MS, int L, float alpha, double2* qs, double* us,
-                               float* pyr) {
-  __shared__ double red[32];
-  const int tid = threadIdx.x, T = blockDim.x;
-  const int M = MS * MS;
-  constexpr double kTiny = 1e-30;
+// regulariser), in three launches: max |Q|^2; the levels inside 16 x 16
+// tiles of the finest grid (one block per tile, levels in shared memory);
+// and the levels coarser than a tile (one block).  Each element's arithmetic
+// and summation order is the same in all three.
+constexpr double kTiny = 1e-30;  // division rule threshold
+
+__global__ void __launch_bounds__(256) probe_max_kernel(const float2* Q, int M, unsigned long long* mx_bits) {
+  __shared__ double red[8];
   double mx = 0.0;
-  for (int i = tid; i < M; i += T) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
     const float2 q = Q[i];
-    qs[i] = make_double2(q.x, q.y);
     mx = fmax(mx, (double)q.x * q.x + (double)q.y * q.y);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
-  if ((tid & 31) == 0) red[tid >> 5] = mx;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
-  if (tid == 0) {
-    double m = 0.0;
-    for (int i = 0; i < T / 32; ++i) m = fmax(m, red[i]);
-    red[0] = m;
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x / 32); ++i) mx = fmax(mx, red[i]);
+    // non-negative doubles order like their bit patterns
+    atomicMax(mx_bits, (unsigned long long)__double_as_longlong(mx));
   }
-  __syncthreads();
-  mx = red[0];
-  for (int i = tid; i < M; i += T) {
-    const double a2 = qs[i].x * qs[i].x + qs[i].y * qs[i].y;
+}
+
+// one coarsening of a 2x2 bin: Q_H, S = mean |Q|^2, W_u, u_H and the floats
+__device__ __forceinline__ void coarsen(const double2* q4, const double* u4, double2& qm, double& uh, float& wu,
+                                        float& iw, float& rr) {
+  qm = make_double2(0.0, 0.0);
+  double sa = 0.0, um = 0.0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    qm.x += q4[i].x;
+    qm.y += q4[i].y;
+    sa += q4[i].x * q4[i].x + q4[i].y * q4[i].y;
+    um += u4[i];
+  }
+  qm.x *= 0.25;
+  qm.y *= 0.25;
+  sa *= 0.25;
+  um *= 0.25;
+  const double qh2 = qm.x * qm.x + qm.y * qm.y;
+  const double w_u = sa > kTiny ? qh2 / sa : 0.0;
+  uh = w_u * um;
+  const double wh = uh + qh2;
+  wu = (float)w_u;
+  iw = wh > kTiny ? (float)(1.0 / wh) : 0.f;
+  rr = wh > kTiny ? (float)(uh / wh) : 1.f;
+}
+
+// One block of TS x TS threads per TS x TS tile of the finest grid
+// (TS = min(16, MS)): levels 0 .. min(L-1, log2 TS).  The tile's top level is
+// also written in float64 to qtop/utop when coarser levels remain.
+__global__ void __launch_bounds__(256) pyramid_tile_kernel(const float2* Q, int MS, int L, float alpha,
+                                                            const unsigned long long* mx_bits, double2* qtop,
+                                                            double* utop, float* pyr) {
+  __shared__ double2 qsh[2][256];
+  __shared__ double ush[2][256];
+  const int TS = MS < 16 ? MS : 16;
+  const int tx = threadIdx.x % TS, ty = threadIdx.x / TS;
+  const int R0 = blockIdx.y * TS, C0 = blockIdx.x * TS;
+  const int M = MS * MS;
+  const double mx = __longlong_as_double((long long)*mx_bits);
+  {
+    const int i = (R0 + ty) * MS + C0 + tx;
+    const float2 q = Q[i];
+    const double2 qd = make_double2(q.x, q.y);
+    const double a2 = qd.x * qd.x + qd.y * qd.y;
     const double u = (double)alpha * (mx - a2);
-    us[i] = u;
     pyr[i] = (float)u;
     pyr[M + i] = (float)(u + a2);
+    qsh[0][ty * TS + tx] = qd;
+    ush[0][ty * TS + tx] = u;
   }
   __syncthreads();
-  int qoff = 0;
-  for (int l = 1; l < L; ++l) {
+  int lt = 0;
+  while ((TS >> (lt + 1)) >= 1 && lt + 1 <= L - 1) {
+    const int l = lt + 1, ts = TS >> l, src = lt & 1, dst = l & 1;
+    if ((int)threadIdx.x < ts * ts) {
+      const int r = threadIdx.x / ts, c = threadIdx.x % ts;
+      double2 q4[4];
+      double u4[4];
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          q4[2 * a + b] = qsh[src][(2 * r + a) * (2 * ts) + 2 * c + b];
+          u4[2 * a + b] = ush[src][(2 * r + a) * (2 * ts) + 2 * c + b];
+        }
+      double2 qm;
+      double uh;
+      float wu, iw, rr;
+      coarsen(q4, u4, qm, uh, wu, iw, rr);
+      const int s = MS >> l;
+      const int o = ((R0 >> l) + r) * s + (C0 >> l) + c;
+      float* base = pyr + lvl_off(MS, l);
+      base[o] = wu;
+      base[s * s + o] = iw;
+      base[2 * s * s + o] = rr;
+      qsh[dst][r * ts + c] = qm;
+      ush[dst][r * ts + c] = uh;
+    }
+    __syncthreads();
+    lt = l;
+  }
+  if (lt < L - 1) {
+    // the tile's top level feeds the coarser levels
+    const int ts = TS >> lt, s = MS >> lt;
+    if ((int)threadIdx.x < ts * ts) {
+      const int r = threadIdx.x / ts, c = threadIdx.x % ts;
+      const int o = ((R0 >> lt) + r) * s + (C0 >> lt) + c;
+      qtop[o] = qsh[lt & 1][threadIdx.x];
+      utop[o] = ush[lt & 1][threadIdx.x];
+    }
+  }
+}
+
+// Levels coarser than a tile, from the level-`lt` float64 arrays (one block).
+__global__ void __launch_bounds__(256) pyramid_top_kernel(int MS, int L, int lt, double2* qtop, double* utop,
+                                                           float* pyr) {
+  int off = 0;  // level l's arrays at qtop + off (level lt at 0)
+  for (int l = lt + 1; l < L; ++l) {
     const int sf = MS >> (l - 1), s = MS >> l;
-    const int noff = qoff + sf * sf;
-    float* wu = pyr + lvl_off(MS, l);
-    float* iw = wu + s * s;
-    float* rr = iw + s * s;
-    for (int i = tid; i < s * s; i += T) {
+    const int noff = off + sf * sf;
+    for (int i = threadIdx.x; i < s * s; i += blockDim.x) {
       const int r = i / s, c = i % s;
-      double2 qm = make_double2(0.0, 0.0);
-      double sa = 0.0, um = 0.0;
+      double2 q4[4];
+      double u4[4];
       for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b) {
-          const int o = qoff + (2 * r + a) * sf + 2 * c + b;
-          qm.x += qs[o].x;
-          qm.y += qs[o].y;
-          sa += qs[o].x * qs[o].x + qs[o].y * qs[o].y;
-          um += us[o];
+          q4[2 * a + b] = qtop[off + (2 * r + a) * sf + 2 * c + b];
+          u4[2 * a + b] = utop[off + (2 * r + a) * sf + 2 * c + b];
         }
-      qm.x *= 0.25;
-      qm.y *= 0.25;
-      sa *= 0.25;
-      um *= 0.25;
-      const double qh2 = qm.x * qm.x + qm.y * qm.y;
-      const double w_u = sa > kTiny ? qh2 / sa : 0.0;
-      const double uh = w_u * um;
-      const double wh = uh + qh2;
-      qs[noff + i] = qm;
-      us[noff + i] = uh;
-      wu[i] = (float)w_u;
-      iw[i] = wh > kTiny ? (float)(1.0 / wh) : 0.f;
-      rr[i] = wh > kTiny ? (float)(uh / wh) : 1.f;
+      double2 qm;
+      double uh;
+      float wu, iw, rr;
+      coarsen(q4, u4, qm, uh, wu, iw, rr);
+      float* base = pyr + lvl_off(MS, l);
+      base[i] = wu;
+      base[s * s + i] = iw;
+      base[2 * s * s + i] = rr;
+      qtop[noff + i] = qm;
+      utop[noff + i] = uh;
     }
-    qoff = noff;
+    off = noff;
     __syncthreads();
   }
 }
 
-__global__ void __launch_bounds__(1024) reduce_kernel(const double* phi, const double* gn, int n, double* out) {
+// Probe step of one minibatch (simultaneous with the object step): every
+// probe pixel sums, in minibatch order, the windows' conj(z_k)(R_k - Q z_k)
+// and beta (max|z_k|^2 - |z_k|^2) + |z_k|^2, and moves by their ratio.
+__global__ void __launch_bounds__(256) probe_apply_kernel(float2* Q, int M, const int32_t* idx, int count, int n_pos,
+                                                          const float2* pnum, const float* pa2, const double* pmax,
+                                                          int CL, float beta) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= M) return;
+  float nx = 0.f, ny = 0.f, d = 0.f;
+  for (int b = 0; b < count; ++b) {
+    if ((unsigned)idx[b] >= (unsigned)n_pos) continue;
+    double mb = 0.0;
+    for (int q = 0; q < CL; ++q) mb = fmax(mb, pmax[b * CL + q]);
+    const float2 v = pnum[(size_t)b * M + p];
+    const float a2 = pa2[(size_t)b * M + p];
+    nx += v.x;
+    ny += v.y;
+    d += beta * ((float)mb - a2) + a2;
+  }
+  if (d > 0.f) {
+    float2 q = Q[p];
+    q.x += nx / d;
+    q.y += ny / d;
+    Q[p] = q;
+  }
+}
+
+// Objective and stopping metric of a full pass (window k in launch slot k):
+// per-window values from the block partials, then their sums, all in a fixed
+// order (one block).
+__global__ void __launch_bounds__(1024) reduce_kernel(const double* part, int CL, int MS, int n, double* phi_pos,
+                                                      double* gn_pos, double* out) {
   __shared__ double red[32];
   double a = 0.0, b = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    a += phi[i];
-    b += gn[i];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    double pk = 0.0, gk = 0.0;
+    for (int q = 0; q < CL; ++q) {
+      pk += part[(size_t)(k * CL + q) * 2];
+      gk += part[(size_t)(k * CL + q) * 2 + 1];
+    }
+    pk /= 2.0 * (double)MS * (double)MS;
+    gk = sqrt(gk);
+    phi_pos[k] = pk;
+    gn_pos[k] = gk;
+    a += pk;
+    b += gk;
   }
   const int T = blockDim.x, tid = threadIdx.x;
   for (int pass = 0; pass < 2; ++pass) {
@@ -923,22 +1070,17 @@ int ilog2(int v) {
   return r;
 }
 
-// Launch with the programmatic-stream-serialization attribute (and a cluster
-// dimension when cl > 1): the kernel may start while its predecessor in the
-// stream finishes; its pdl_wait() orders it after that predecessor's memory.
+// Launch with a cluster dimension when cl > 1.
 template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, int cl,
+cudaError_t launch_ex(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, int cl,
                        Args&&... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[2];
+  cudaLaunchAttribute attr[1];
   int n = 0;
-  attr[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[n].val.programmaticStreamSerializationAllowed = 1;
-  ++n;
   if (cl > 1) {
     attr[n].id = cudaLaunchAttributeClusterDimension;
     attr[n].val.clusterDim.x = cl;
@@ -956,14 +1098,35 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 template <int MS, int MODE>
 cudaError_t launch_window(const StepArgs& a, int windows, cudaStream_t st) {
   using Gm = Geo<MS>;
-  return launch_pdl(window_kernel<MS, MODE>, dim3((unsigned)windows * Gm::CL), dim3(Gm::T), Gm::SMEM, st, Gm::CL, a);
+  return launch_ex(window_kernel<MS, MODE>, dim3((unsigned)windows * Gm::CL), dim3(Gm::T), Gm::SMEM, st, Gm::CL, a);
+}
+
+// blocks per window of the window kernel for patch side m
+int cluster_of(int m) { return m >= 256 ? 8 : m == 128 ? 4 : m == 64 ? 2 : 1; }
+
+// The per-level probe factors of probe Q (float64 arithmetic) into pyr.
+// mx: one 8-byte scratch word; qtop/utop: float64 scratch of 2 MS^2 entries.
+cudaError_t enqueue_pyramid(const float2* Q, int MS, int L, float alpha, unsigned long long* mx, double2* qtop,
+                            double* utop, float* pyr, cudaStream_t st) {
+  const int M = MS * MS;
+  cudaError_t e = cudaMemsetAsync(mx, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  const int mb = (M + 255) / 256 < 64 ? (M + 255) / 256 : 64;
+  probe_max_kernel<<<mb, 256, 0, st>>>(Q, M, mx);
+  const int TS = MS < 16 ? MS : 16;
+  pyramid_tile_kernel<<<dim3(MS / TS, MS / TS), TS * TS, 0, st>>>(Q, MS, L, alpha, mx, qtop, utop, pyr);
+  int lt = 0;
+  while ((TS >> (lt + 1)) >= 1 && lt + 1 <= L - 1) ++lt;
+  if (lt < L - 1) pyramid_top_kernel<<<1, 256, 0, st>>>(MS, L, lt, qtop, utop, pyr);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_apply(float2* z, int n_rows, int n_cols, const int32_t* pos, const int32_t* idx, int count,
-                         int n_pos, const float2* contrib, const float* w0, int MS, cudaStream_t st) {
+                         int n_pos, const float2* contrib, const float* w0, int MS, const double* part,
+                         double* phi_pos, double* gn_pos, cudaStream_t st) {
   const dim3 tiles((n_cols + kApplyTile - 1) / kApplyTile, (n_rows + kApplyTile - 1) / kApplyTile);
-  return launch_pdl(apply_kernel, tiles, dim3(256), (sizeof(int2) + sizeof(int)) * count, st, 1, z, n_rows, n_cols,
-                    pos, idx, count, n_pos, contrib, w0, MS);
+  return launch_ex(apply_kernel, tiles, dim3(256), (sizeof(int2) + sizeof(int)) * count, st, 1, z, n_rows, n_cols,
+                   pos, idx, count, n_pos, contrib, w0, MS, part, cluster_of(MS), phi_pos, gn_pos);
 }
 
 template <int MODE>
@@ -1037,13 +1200,20 @@ struct magpie_ctx {
   double* phi_pos = nullptr;
   double* gn_pos = nullptr;
   double* part = nullptr;     // [n_pos][kMaxCluster][2] per-block partial sums
-  unsigned* cnt = nullptr;    // [n_pos] blocks done per window slot
+  unsigned long long* mx = nullptr;  // max |Q|^2 (bits of a double)
+  float2* pnum = nullptr;     // probe step: [minibatch][m][m]
+  float* pa2 = nullptr;       // probe step: [minibatch][m][m]
+  double* pmax = nullptr;     // probe step: [minibatch][kMaxCluster]
   int32_t* iota = nullptr;
   int32_t* order = nullptr;
   double* sums = nullptr;
   int* err = nullptr;
   cudaGraphExec_t graph = nullptr;
   std::vector<cudaEvent_t> events;  // 4 per minibatch step (magpie_profile_sweep)
+  // host sweeps: chunked uploads of the intensities on several copy streams
+  cudaStream_t copy_streams[4] = {};
+  cudaEvent_t copy_done[4] = {};
+  cudaEvent_t copy_start = nullptr;
 };
 
 namespace {
@@ -1063,10 +1233,10 @@ StepArgs make_args(magpie_ctx* c, const int32_t* idx) {
   a.contrib = c->contrib;
   a.pyr = c->pyr;
   a.levels = c->p.levels;
-  a.phi_pos = c->phi_pos;
-  a.gn_pos = c->gn_pos;
   a.part = c->part;
-  a.cnt = c->cnt;
+  a.pnum = c->pnum;
+  a.pa2 = c->pa2;
+  a.pmax = c->pmax;
   a.err = c->err;
   return a;
 }
@@ -1080,15 +1250,20 @@ int enqueue_step(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st, 
   if (ev) CUDA_TRY(cudaEventRecord(ev[1], st));
   if (ev) CUDA_TRY(cudaEventRecord(ev[2], st));
   CUDA_TRY(launch_apply(c->z, c->p.n_rows, c->p.n_cols, c->pos, idx, count, c->p.n_pos, c->contrib, c->pyr + c->M,
-                        c->p.m, st));
+                        c->p.m, c->part, c->phi_pos, c->gn_pos, st));
+  if (c->p.update_probe) {
+    probe_apply_kernel<<<(c->M + 255) / 256, 256, 0, st>>>(c->Q, c->M, idx, count, c->p.n_pos, c->pnum, c->pa2,
+                                                           c->pmax, cluster_of(c->p.m), c->p.beta);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(enqueue_pyramid(c->Q, c->p.m, c->p.levels, c->p.alpha, c->mx, c->pyr_q, c->pyr_u, c->pyr, st));
+  }
   if (ev) CUDA_TRY(cudaEventRecord(ev[3], st));
   return MAGPIE_OK;
 }
 
 int build_pyramid(magpie_ctx* c, const void* probe) {
   CUDA_TRY(cudaMemcpyAsync(c->Q, probe, sizeof(float2) * c->M, cudaMemcpyDeviceToDevice, c->stream));
-  pyramid_kernel<<<1, 1024, 0, c->stream>>>(c->Q, c->p.m, c->p.levels, c->p.alpha, c->pyr_q, c->pyr_u, c->pyr);
-  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(enqueue_pyramid(c->Q, c->p.m, c->p.levels, c->p.alpha, c->mx, c->pyr_q, c->pyr_u, c->pyr, c->stream));
   return MAGPIE_OK;
 }
 
@@ -1106,7 +1281,8 @@ int read_err(magpie_ctx* c) {
 int evaluate(magpie_ctx* c, double* phi, double* stop) {
   StepArgs a = make_args(c, c->iota);
   CUDA_TRY(launch_window_m<kEval>(c->p.m, a, c->p.n_pos, c->stream));
-  reduce_kernel<<<1, 1024, 0, c->stream>>>(c->phi_pos, c->gn_pos, c->p.n_pos, c->sums);
+  reduce_kernel<<<1, 1024, 0, c->stream>>>(c->part, cluster_of(c->p.m), c->p.m, c->p.n_pos, c->phi_pos, c->gn_pos,
+                                           c->sums);
   CUDA_TRY(cudaGetLastError());
   double h[2];
   CUDA_TRY(cudaMemcpyAsync(h, c->sums, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
@@ -1157,6 +1333,9 @@ int validate(const magpie_params* p) {
   if (p->minibatch < 1 || p->minibatch > p->n_pos || p->minibatch > kMaxMinibatch)
     return fail(MAGPIE_EINVAL, "minibatch must lie in [1, min(n_pos, 4096)]");
   if (!(p->alpha >= 0.f) || !std::isfinite(p->alpha)) return fail(MAGPIE_EINVAL, "alpha must be finite and >= 0");
+  if (p->update_probe != 0 && p->update_probe != 1) return fail(MAGPIE_EINVAL, "update_probe must be 0 or 1");
+  if (p->update_probe && (!(p->beta >= 0.f) || !std::isfinite(p->beta)))
+    return fail(MAGPIE_EINVAL, "beta must be finite and >= 0");
   return MAGPIE_OK;
 }
 
@@ -1172,9 +1351,8 @@ constexpr size_t kNoAllocPyrUBytes = sizeof(double) * 2 * 128 * 128;            
 constexpr size_t kNoAllocTwBytes = sizeof(float2) * 128;
 constexpr size_t kNoAllocIdxBytes = sizeof(int32_t) * kMaxMinibatch;
 constexpr size_t kNoAllocPartBytes = sizeof(double) * 2 * kMaxCluster * kMaxMinibatch;              // 512 KiB
-constexpr size_t kNoAllocCntBytes = sizeof(unsigned) * kMaxMinibatch;
 constexpr size_t kNoAllocBytes = kNoAllocContribBytes + kNoAllocPyrBytes + kNoAllocPyrQBytes + kNoAllocPyrUBytes +
-                                 kNoAllocTwBytes + kNoAllocIdxBytes + kNoAllocPartBytes + kNoAllocCntBytes + 256;
+                                 kNoAllocTwBytes + kNoAllocIdxBytes + kNoAllocPartBytes + 8 + 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 // idx -> sanitized copy: a window whose index is outside [0, n_pos) or whose
@@ -1205,7 +1383,7 @@ struct NoAllocScratch {
   float2* tw;
   int32_t* idx;
   double* part;
-  unsigned* cnt;
+  unsigned long long* mx;
   int* err;
 };
 
@@ -1237,8 +1415,8 @@ int noalloc_scratch(NoAllocScratch* out) {
   b += kNoAllocIdxBytes;
   out->part = (double*)b;
   b += kNoAllocPartBytes;
-  out->cnt = (unsigned*)b;
-  b += kNoAllocCntBytes;
+  out->mx = (unsigned long long*)b;
+  b += 8;
   out->err = (int*)b;
   return MAGPIE_OK;
 }
@@ -1266,11 +1444,16 @@ const char* magpie_last_error(void) { return g_last_error.c_str(); }
 void magpie_destroy(magpie_ctx* c) {
   if (!c) return;
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (int i = 0; i < 4; ++i) {
+    if (c->copy_streams[i]) cudaStreamDestroy(c->copy_streams[i]);
+    if (c->copy_done[i]) cudaEventDestroy(c->copy_done[i]);
+  }
+  if (c->copy_start) cudaEventDestroy(c->copy_start);
   for (auto e : c->events)
     if (e) cudaEventDestroy(e);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   void* bufs[] = {c->Q, c->tw, c->amp, c->stage, c->pos, c->pyr, c->pyr_q, c->pyr_u, c->contrib,
-                  c->phi_pos, c->gn_pos, c->part, c->cnt, c->iota, c->order, c->sums, c->err};
+                  c->phi_pos, c->gn_pos, c->part, c->mx, c->pnum, c->pa2, c->pmax, c->iota, c->order, c->sums, c->err};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete c;
@@ -1313,7 +1496,10 @@ int magpie_create(magpie_ctx** out, const magpie_params* params, void* object, c
       (rc = alloc((void**)&c->contrib, sizeof(float2) * M * p.minibatch)) ||
       (rc = alloc((void**)&c->phi_pos, sizeof(double) * N)) || (rc = alloc((void**)&c->gn_pos, sizeof(double) * N)) ||
       (rc = alloc((void**)&c->part, sizeof(double) * 2 * kMaxCluster * N)) ||
-      (rc = alloc((void**)&c->cnt, sizeof(unsigned) * N)) ||
+      (rc = alloc((void**)&c->mx, sizeof(unsigned long long))) ||
+      (p.update_probe && (rc = alloc((void**)&c->pnum, sizeof(float2) * M * p.minibatch))) ||
+      (p.update_probe && (rc = alloc((void**)&c->pa2, sizeof(float) * M * p.minibatch))) ||
+      (p.update_probe && (rc = alloc((void**)&c->pmax, sizeof(double) * kMaxCluster * p.minibatch))) ||
       (rc = alloc((void**)&c->iota, sizeof(int32_t) * N)) || (rc = alloc((void**)&c->order, sizeof(int32_t) * N)) ||
       (rc = alloc((void**)&c->sums, sizeof(double) * 2)) || (rc = alloc((void**)&c->err, sizeof(int))))
     return rc;
@@ -1340,7 +1526,6 @@ int magpie_create(magpie_ctx** out, const magpie_params* params, void* object, c
   CTX_TRY(cudaMemsetAsync(c->err, 0, sizeof(int), st));
   CTX_TRY(cudaMemsetAsync(c->phi_pos, 0, sizeof(double) * N, st));
   CTX_TRY(cudaMemsetAsync(c->gn_pos, 0, sizeof(double) * N, st));
-  CTX_TRY(cudaMemsetAsync(c->cnt, 0, sizeof(unsigned) * N, st));
   iota_kernel<<<(int)((N + 255) / 256), 256, 0, st>>>(c->iota, (int)N);
   CTX_TRY(cudaGetLastError());
   sqrt_kernel<<<1024, 256, 0, st>>>(intensities, c->amp, M * N);
@@ -1398,6 +1583,12 @@ int magpie_profile_sweep(magpie_ctx* c, const int32_t* order, double* window_ms,
   return read_err(c);
 }
 
+int magpie_get_probe(magpie_ctx* c, void* probe) {
+  if (!c || !probe) return fail(MAGPIE_EINVAL, "NULL argument");
+  CUDA_TRY(cudaMemcpyAsync(probe, c->Q, sizeof(float2) * c->M, cudaMemcpyDeviceToDevice, c->stream));
+  return MAGPIE_OK;
+}
+
 int magpie_objective(magpie_ctx* c, double* phi) {
   if (!c || !phi) return fail(MAGPIE_EINVAL, "NULL argument");
   return evaluate(c, phi, nullptr);
@@ -1420,10 +1611,31 @@ int magpie_sweep_host(magpie_ctx* c, const int32_t* order, const float* intensit
   if (!c || !order) return fail(MAGPIE_EINVAL, "NULL argument");
   const size_t N = c->p.n_pos, M = c->M;
   if (intensities) {
+    // four chunks on four copy streams (several copy engines), each chunk's
+    // square roots taken on its own stream as soon as it has landed
+    constexpr int kChunks = 4;
     if (!c->stage) CUDA_TRY(cudaMalloc((void**)&c->stage, sizeof(float) * N * M));
-    CUDA_TRY(cudaMemcpyAsync(c->stage, intensities, sizeof(float) * N * M, cudaMemcpyHostToDevice, c->stream));
-    sqrt_kernel<<<1024, 256, 0, c->stream>>>(c->stage, c->amp, N * M);
-    CUDA_TRY(cudaGetLastError());
+    if (!c->copy_start) {
+      CUDA_TRY(cudaEventCreateWithFlags(&c->copy_start, cudaEventDisableTiming));
+      for (int i = 0; i < kChunks; ++i) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&c->copy_streams[i], cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreateWithFlags(&c->copy_done[i], cudaEventDisableTiming));
+      }
+    }
+    CUDA_TRY(cudaEventRecord(c->copy_start, c->stream));
+    const size_t total = N * M, per = (total + kChunks - 1) / kChunks;
+    for (int i = 0; i < kChunks; ++i) {
+      const size_t b0 = i * per, n = b0 >= total ? 0 : (total - b0 < per ? total - b0 : per);
+      cudaStream_t cs = c->copy_streams[i];
+      CUDA_TRY(cudaStreamWaitEvent(cs, c->copy_start, 0));
+      if (n) {
+        CUDA_TRY(cudaMemcpyAsync(c->stage + b0, intensities + b0, sizeof(float) * n, cudaMemcpyHostToDevice, cs));
+        sqrt_kernel<<<256, 256, 0, cs>>>(c->stage + b0, c->amp + b0, n);
+        CUDA_TRY(cudaGetLastError());
+      }
+      CUDA_TRY(cudaEventRecord(c->copy_done[i], cs));
+      CUDA_TRY(cudaStreamWaitEvent(c->stream, c->copy_done[i], 0));
+    }
   }
   CUDA_TRY(cudaMemcpyAsync(c->order, order, sizeof(int32_t) * N, cudaMemcpyHostToDevice, c->stream));
   int rc = launch_sweep(c);
@@ -1522,13 +1734,11 @@ int magpie_step_noalloc(void* object, int32_t n_rows, int32_t n_cols, const void
     htw[t] = make_float2((float)std::cos(ang), (float)std::sin(ang));
   }
   CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int), st));
-  CUDA_TRY(cudaMemsetAsync(w.cnt, 0, sizeof(unsigned) * count, st));
   CUDA_TRY(cudaMemcpyAsync(w.tw, htw, sizeof(float2) * m, cudaMemcpyHostToDevice, st));
   sanitize_idx_kernel<<<(count + 255) / 256, 256, 0, st>>>(idx, count, positions, n_pos, n_rows, n_cols, m, w.idx,
                                                             w.err);
   CUDA_TRY(cudaGetLastError());
-  pyramid_kernel<<<1, 1024, 0, st>>>((const float2*)probe, m, levels, alpha, w.pyr_q, w.pyr_u, w.pyr);
-  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(enqueue_pyramid((const float2*)probe, m, levels, alpha, w.mx, w.pyr_q, w.pyr_u, w.pyr, st));
   StepArgs a{};
   a.z = (const float2*)object;
   a.n_rows = n_rows;
@@ -1542,14 +1752,11 @@ int magpie_step_noalloc(void* object, int32_t n_rows, int32_t n_cols, const void
   a.contrib = w.contrib;
   a.pyr = w.pyr;
   a.levels = levels;
-  a.phi_pos = phi;
-  a.gn_pos = gnorm;
   a.part = w.part;
-  a.cnt = w.cnt;
   a.err = w.err;
   CUDA_TRY(launch_window_m<kStep>(m, a, count, st));
   CUDA_TRY(launch_apply((float2*)object, n_rows, n_cols, positions, w.idx, count, n_pos, w.contrib, w.pyr + m * m, m,
-                        st));
+                        w.part, phi, gnorm, st));
   int h = 0;
   CUDA_TRY(cudaMemcpyAsync(&h, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));

@@ -35,7 +35,7 @@ class MagpieError(RuntimeError):
 class magpie_params(ctypes.Structure):
     _fields_ = [("n_rows", ctypes.c_int32), ("n_cols", ctypes.c_int32), ("m", ctypes.c_int32),
                 ("n_pos", ctypes.c_int32), ("levels", ctypes.c_int32), ("minibatch", ctypes.c_int32),
-                ("alpha", ctypes.c_float)]
+                ("alpha", ctypes.c_float), ("update_probe", ctypes.c_int32), ("beta", ctypes.c_float)]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -75,6 +75,7 @@ def lib() -> ctypes.CDLL:
             "magpie_profile_sweep": (ctypes.c_int, [vp, vp, dp, dp, ctypes.POINTER(i32)]),
             "magpie_stop_metric": (ctypes.c_int, [vp, dp]),
             "magpie_set_probe": (ctypes.c_int, [vp, vp]),
+            "magpie_get_probe": (ctypes.c_int, [vp, vp]),
             "magpie_window_values": (ctypes.c_int, [vp, vp, vp]),
             "magpie_sweep_host": (ctypes.c_int, [vp, vp, vp, vp]),
             "magpie_forward_intensities": (ctypes.c_int, [vp, i32, i32, vp, i32, vp, i32, vp, vp]),
@@ -118,8 +119,9 @@ def _stream() -> int:
     return torch.cuda.current_stream().cuda_stream
 
 
-def magpie_params_of(n_rows, n_cols, m, n_pos, levels, minibatch, alpha) -> magpie_params:
-    return magpie_params(int(n_rows), int(n_cols), int(m), int(n_pos), int(levels), int(minibatch), float(alpha))
+def magpie_params_of(n_rows, n_cols, m, n_pos, levels, minibatch, alpha, update_probe=0, beta=0.0) -> magpie_params:
+    return magpie_params(int(n_rows), int(n_cols), int(m), int(n_pos), int(levels), int(minibatch), float(alpha),
+                         int(update_probe), float(beta))
 
 
 class Context:
@@ -188,6 +190,13 @@ def magpie_stop_metric(ctx: Context) -> float:
 
 def magpie_set_probe(ctx: Context, probe: torch.Tensor) -> None:
     _check(lib().magpie_set_probe(ctx.handle, _dev(probe, torch.complex64, ctx.params.m ** 2, "probe")))
+
+
+def magpie_get_probe(ctx: Context) -> torch.Tensor:
+    m = ctx.params.m
+    out = torch.empty((m, m), dtype=torch.complex64, device=ctx._keep[0].device)
+    _check(lib().magpie_get_probe(ctx.handle, out.data_ptr()))
+    return out
 
 
 def magpie_window_values(ctx: Context):

@@ -40,18 +40,18 @@ def test_every_declared_symbol_is_exported(L):
 
 
 def test_error_strings_and_version(L):
-    assert L.magpie_version() == 10000
+    assert L.magpie_version() == 10100
     for code in (0, -1, -2, -3, -4, -5):
         assert L.magpie_strerror(code)
     assert L.magpie_strerror(-99) == b"unknown error"
 
 
 def _create(L, **kw):
-    p = dict(n_rows=128, n_cols=128, m=32, n_pos=64, levels=2, minibatch=16, alpha=0.1)
+    p = dict(n_rows=128, n_cols=128, m=32, n_pos=64, levels=2, minibatch=16, alpha=0.1, update_probe=0, beta=0.0)
     p.update(kw)
     h = ctypes.c_void_p()
     params = magpie.magpie_params(p["n_rows"], p["n_cols"], p["m"], p["n_pos"], p["levels"],
-                                  p["minibatch"], p["alpha"])
+                                  p["minibatch"], p["alpha"], p["update_probe"], p["beta"])
     # dummy non-NULL pointers: argument checks fail before any of them is used
     dummy = ctypes.c_void_p(0x1000)
     rc = L.magpie_create(ctypes.byref(h), ctypes.byref(params), dummy, dummy, dummy, dummy, None)
@@ -71,12 +71,37 @@ def _create(L, **kw):
     (dict(alpha=-1.0), magpie.EINVAL),
     (dict(alpha=float("nan")), magpie.EINVAL),
     (dict(alpha=float("inf")), magpie.EINVAL),
+    (dict(update_probe=2), magpie.EINVAL),
+    (dict(update_probe=1, beta=-0.5), magpie.EINVAL),
+    (dict(update_probe=1, beta=float("nan")), magpie.EINVAL),
 ])
 def test_create_rejects_bad_arguments_without_a_gpu(L, kw, code):
     rc, h = _create(L, **kw)
     assert rc == code
     assert not h.value
     assert L.magpie_last_error()
+
+
+def test_params_layout_matches_the_header():
+    text = open(magpie.HEADER).read()
+    body = text[text.index("typedef struct {"):text.index("} magpie_params;")]
+    fields = [f for f in re_fields(body)]
+    assert fields == [name for name, _ in magpie.magpie_params._fields_]
+    assert ctypes.sizeof(magpie.magpie_params) == 4 * len(fields)
+
+
+def re_fields(body):
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    out = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl or decl.startswith("typedef"):
+            decl = decl.replace("typedef struct {", "").strip()
+        if not decl:
+            continue
+        names = decl.split(None, 1)[1]
+        out += [n.strip() for n in names.split(",")]
+    return out
 
 
 def test_null_arguments(L):

@@ -50,11 +50,13 @@ class Problem:
         self.z0 = f32(z0)
         self.u = O.rpie_regulariser(self.Q, alpha)
 
-    def ctx(self, z=None):
+    def ctx(self, z=None, update_probe=0, beta=0.0, probe=None):
         dev = torch.device("cuda")
         self.zt = torch.from_numpy((self.z0 if z is None else z).astype(np.complex64)).to(dev)
-        p = magpie.magpie_params_of(self.n, self.n, self.m, self.N, self.levels, self.B, self.alpha)
-        return magpie.magpie_create(p, self.zt, torch.from_numpy(self.Q.astype(np.complex64)).to(dev),
+        p = magpie.magpie_params_of(self.n, self.n, self.m, self.N, self.levels, self.B, self.alpha,
+                                    update_probe, beta)
+        Q = self.Q if probe is None else probe
+        return magpie.magpie_create(p, self.zt, torch.from_numpy(Q.astype(np.complex64)).to(dev),
                                     torch.from_numpy(self.pos).to(dev),
                                     torch.from_numpy(self.d.astype(np.float32)).to(dev))
 
@@ -290,6 +292,52 @@ def test_set_probe():
     magpie.magpie_step(ctx, dev_i32(batch))
     ref = O.minibatch_step(P.z0, Q2, P.pos, P.d, O.rpie_regulariser(Q2, w.alpha), w.levels, batch)
     assert rel(P.z_gpu(), ref) < STEP_TOL
+    ctx.close()
+
+
+def probe_problem(L):
+    """The small workload with a probe that is 10% off the true one."""
+    P, w = tiny_problem()
+    P.levels = L
+    rng = np.random.default_rng(7)
+    Q0 = f32(P.Q * (1 + 0.1 * (rng.standard_normal(P.Q.shape) + 1j * rng.standard_normal(P.Q.shape))))
+    return P, w, Q0
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+def test_probe_step(L):
+    P, w, Q0 = probe_problem(L)
+    beta = 0.2
+    ctx = P.ctx(update_probe=1, beta=beta, probe=Q0)
+    batch = synth.make_order(P.N, 1)[: w.minibatch]
+    magpie.magpie_step(ctx, dev_i32(batch))
+    z_ref, Q_ref = O.minibatch_step_with_probe(P.z0, Q0, P.pos, P.d, w.alpha, L, batch, beta)
+    assert rel(P.z_gpu(), z_ref) < STEP_TOL
+    Q_gpu = magpie.magpie_get_probe(ctx).cpu().numpy().astype(np.complex128)
+    assert rel(Q_gpu, Q_ref) < STEP_TOL
+    ctx.close()
+
+
+def test_probe_sweep():
+    P, w, Q0 = probe_problem(2)
+    beta = 0.2
+    ctx = P.ctx(update_probe=1, beta=beta, probe=Q0)
+    order = synth.make_order(P.N, 2)
+    magpie.magpie_sweep(ctx, dev_i32(order))
+    z_ref, Q_ref = O.sweep_with_probe(P.z0, Q0, P.pos, P.d, w.alpha, 2, order, w.minibatch, beta)
+    assert rel(P.z_gpu(), z_ref) < STEP_TOL
+    assert rel(magpie.magpie_get_probe(ctx).cpu().numpy().astype(np.complex128), Q_ref) < STEP_TOL
+    # the objective evaluation uses the moved probe
+    phi = magpie.magpie_objective(ctx)
+    assert abs(phi - O.objective(z_ref, Q_ref, P.pos, P.d)) < 1e-4 * phi
+    ctx.close()
+
+
+def test_probe_fixed_by_default():
+    P, w = tiny_problem()
+    ctx = P.ctx()
+    magpie.magpie_sweep(ctx, dev_i32(synth.make_order(P.N, 0)))
+    assert np.array_equal(magpie.magpie_get_probe(ctx).cpu().numpy(), P.Q.astype(np.complex64))
     ctx.close()
 
 
