@@ -37,7 +37,8 @@ FP32_LANES_PER_SM = 128
 SMS = 152
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "window_kernel_m128_mid.txt")
-KERNEL_SOURCE = os.path.join(ROOT, "paper_2504_10118_gb300", "csrc", "magpie.cu")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2504_10118_gb300", "csrc", f)
+                  for f in ("fft_lines.cuh", "window_kernel.cuh")]
 
 
 def flops_per_window(m: int) -> float:
@@ -82,6 +83,15 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def kernel_source_hash() -> str:
+    """sha256 over the window kernel's source files (the ncu figures go stale
+    when it changes)."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
+
+
 def measured_traffic():
     """DRAM bytes per launch of the window kernel from the committed ncu
     summary, or None when the kernel source changed since it was taken."""
@@ -94,7 +104,7 @@ def measured_traffic():
         if ":" in ln:
             k, v = ln.split(":", 1)
             kv[k.strip()] = v.strip()
-    src = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
+    src = kernel_source_hash()
     if kv.get("source_sha256") != src or "dram_bytes_per_launch" not in kv:
         return None
     return float(kv["dram_bytes_per_launch"])

@@ -55,701 +55,26 @@ constexpr int kVersion = 10100;  // 1.1.0
 constexpr int kMaxMinibatch = 4096;  // the update kernel keeps the minibatch's corners in smem (48 KiB)
 constexpr int kMaxCluster = 8;       // largest number of blocks per window
 
-// ------------------------------------------------------------------ helpers
-__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return f2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return f2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return f2(a.x * s, a.y * s); }
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return f2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-// conj(a) * b
-__device__ __forceinline__ float2 cmul_cj(float2 a, float2 b) {
-  return f2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
-}
-// a * w (forward) or a * conj(w) (inverse)
-template <bool INV>
-__device__ __forceinline__ float2 twmul(float2 a, float2 w) {
-  return INV ? f2(a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y) : cmul(a, w);
-}
-
-// cos and sin of 2 pi r / 16 (exact decimal expansions of cos(pi/8),
-// cos(pi/4), sin(pi/8)); indices are compile-time after unrolling.
-__host__ __device__ constexpr float cos16(int r) {
-  return r == 0 ? 1.0f : r == 1 ? 0.92387953251128675613f : r == 2 ? 0.70710678118654752440f
-       : r == 3 ? 0.38268343236508977173f : r == 4 ? 0.0f : r == 5 ? -0.38268343236508977173f
-       : r == 6 ? -0.70710678118654752440f : r == 7 ? -0.92387953251128675613f : r == 8 ? -1.0f
-       : r == 9 ? -0.92387953251128675613f : r == 10 ? -0.70710678118654752440f
-       : r == 11 ? -0.38268343236508977173f : r == 12 ? 0.0f : r == 13 ? 0.38268343236508977173f
-       : r == 14 ? 0.70710678118654752440f : 0.92387953251128675613f;
-}
-__host__ __device__ constexpr float sin16(int r) { return cos16((r + 12) & 15); }
-
-// a * exp(-2 pi i r / 16) (forward) or exp(+2 pi i r / 16) (inverse)
-template <bool INV>
-__device__ __forceinline__ float2 rot16(float2 a, int r) {
-  r &= 15;
-  if (r == 0) return a;
-  if (r == 8) return f2(-a.x, -a.y);
-  if (r == 4) return INV ? f2(-a.y, a.x) : f2(a.y, -a.x);
-  if (r == 12) return INV ? f2(a.y, -a.x) : f2(-a.y, a.x);
-  const float c = cos16(r);
-  const float s = INV ? sin16(r) : -sin16(r);
-  return f2(a.x * c - a.y * s, a.x * s + a.y * c);
-}
-
-template <int N>
-__host__ __device__ constexpr int bitrev(int k) {
-  int r = 0;
-  for (int b = 1; b < N; b <<= 1) {
-    r = (r << 1) | (k & 1);
-    k >>= 1;
-  }
-  return r;
-}
-
-// In-register N-point DFT (N <= 16): radix-2 decimation in frequency, then
-// the bit-reversal permutation (register renaming only).  Unnormalised.
-template <int N, bool INV>
-__device__ __forceinline__ void dft_reg(float2 (&a)[N]) {
-#pragma unroll
-  for (int len = N; len >= 2; len >>= 1) {
-    const int half = len >> 1;
-#pragma unroll
-    for (int s = 0; s < N; s += len) {
-#pragma unroll
-      for (int j = 0; j < half; ++j) {
-        const float2 u = a[s + j];
-        const float2 v = a[s + j + half];
-        a[s + j] = cadd(u, v);
-        a[s + j + half] = rot16<INV>(csub(u, v), j * (16 / len));
-      }
-    }
-  }
-  float2 b[N];
-#pragma unroll
-  for (int k = 0; k < N; ++k) b[k] = a[bitrev<N>(k)];
-#pragma unroll
-  for (int k = 0; k < N; ++k) a[k] = b[k];
-}
-
-// ------------------------------------------------------ per-size geometry
-// An MS x MS window is handled by a cluster of CL thread blocks.  Block q owns
-// a slab of SLAB = MS / CL lines: rows q*SLAB.. of the row-slab buffer X and
-// columns q*SLAB.. of the column-slab buffer Y.  An MS-point line is split
-// over G lanes of one warp holding E = MS / G points each; SLAB is a multiple
-// of E and of G, so every cross-slab store below targets a compile-time rank.
-template <int MS> struct Cfg;
-template <> struct Cfg<8> { static constexpr int E = 4, G = 2, CL = 1; };
-template <> struct Cfg<16> { static constexpr int E = 4, G = 4, CL = 1; };
-template <> struct Cfg<32> { static constexpr int E = 8, G = 4, CL = 1; };
-template <> struct Cfg<64> { static constexpr int E = 8, G = 8, CL = 2; };
-template <> struct Cfg<128> { static constexpr int E = 16, G = 8, CL = 4; };
-template <> struct Cfg<256> { static constexpr int E = 16, G = 16, CL = 8; };
-
-template <int MS> struct Geo {
-  static constexpr int E = Cfg<MS>::E, G = Cfg<MS>::G, CL = Cfg<MS>::CL;
-  static_assert(E * G == MS && G <= E && G <= 32, "line split");
-  static constexpr int SLAB = MS / CL;
-  static_assert(CL == 1 || (SLAB % E == 0 && SLAB % G == 0 && SLAB >= 8), "slab split");
-  static constexpr int M = MS * MS;
-  static constexpr int LANES = SLAB * G;  // one lane group per line of the slab
-  static constexpr int T = LANES < 32 ? 32 : LANES;
-  static_assert(T <= 1024 && T % 32 == 0, "block size");
-  static constexpr int XN = SLAB * MS;  // complex entries of each of X and Y
-  static constexpr int LVL = (MS / 4) * (SLAB / 4) * 2 + 4 * CL * CL + 32;
-  // resident blocks per SM the register budget is sized for (two 4-block
-  // windows' worth of slabs share an SM for m = 128)
-  static constexpr int MIN_BLOCKS = (T >= 256 && T < 512) ? 2 : 1;
-  static constexpr size_t SMEM = sizeof(float2) * (2 * size_t(XN) + MS + LVL) + sizeof(double) * 64;
-};
-
-// XOR swizzle of the column index by the row index, within rows of width W:
-// with it, 8 consecutive rows of one column, 4 consecutive rows of 8
-// consecutive columns, and the transposed exchange reads all hit distinct
-// bank pairs (for both warp halves of an 8-byte access).
-template <int W>
-__device__ __forceinline__ int swz(int r) {
-  return ((((r & 1) << 3) | (((r >> 1) & 3) << 1))) & (W - 1);
-}
-// X: [SLAB][MS], Y: [MS][SLAB], both row-major with the swizzle.
-template <int MS>
-__device__ __forceinline__ int xi(int rho, int c) {
-  return rho * MS + (c ^ swz<MS>(rho));
-}
-template <int MS>
-__device__ __forceinline__ int yi(int r, int gam) {
-  constexpr int S = Geo<MS>::SLAB;
-  return r * S + (gam ^ swz<S>(r));
-}
-
-// Split barrier over the window's blocks: arrive (releasing this thread's
-// earlier shared-memory writes, local and remote) ... independent work ...
-// wait (acquiring the other blocks' writes).  With CL = 1 the wait is an
-// ordinary block barrier.
-template <int CL>
-__device__ __forceinline__ void window_arrive() {
-  if constexpr (CL > 1) asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-}
-template <int CL>
-__device__ __forceinline__ void window_wait() {
-  if constexpr (CL > 1)
-    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-  else
-    __syncthreads();
-}
-
-// Barrier over the window's blocks; with CL = 1 an ordinary block barrier.
-template <int CL>
-__device__ __forceinline__ void window_sync() {
-  if constexpr (CL > 1)
-    cg::this_cluster().sync();
-  else
-    __syncthreads();
-}
-// The same shared-memory object in block `rank` of the window's cluster.
-template <int CL, typename P>
-__device__ __forceinline__ P* peer(P* p, int rank) {
-  if constexpr (CL > 1)
-    return cg::this_cluster().map_shared_rank(p, rank);
-  else
-    return p;
-}
-
-// Forward (INV=false) MS-point transform of one line whose lanes hold the
-// input x[e] = line[g + G e].  On return x[j G + k2] = X[g + G j + E k2].
-// slot(s) addresses the line's MS slots in shared memory (the exchange
-// buffer); tw[t] = exp(-2 pi i t / MS).
-template <int MS, bool INV, class Slot>
-__device__ __forceinline__ void line_fwd(float2 (&x)[Cfg<MS>::E], int g, bool act, Slot slot, const float2* tw) {
-  constexpr int E = Cfg<MS>::E, G = Cfg<MS>::G;
-  dft_reg<E, INV>(x);
-#pragma unroll
-  for (int k1 = 1; k1 < E; ++k1) x[k1] = twmul<INV>(x[k1], tw[(g * k1) & (MS - 1)]);
-  if constexpr (G > 1) {
-#pragma unroll
-    for (int k1 = 0; k1 < E; ++k1)
-      if (act) slot(k1 * G + (g ^ (k1 & (G - 1)))) = x[k1];
-    __syncwarp();
-#pragma unroll
-    for (int j = 0; j < E / G; ++j) {
-      const int k1 = g + G * j;
-      float2 v[G];
-#pragma unroll
-      for (int gp = 0; gp < G; ++gp) v[gp] = act ? slot(k1 * G + (gp ^ g)) : f2(0.f, 0.f);
-      dft_reg<G, INV>(v);
-#pragma unroll
-      for (int k2 = 0; k2 < G; ++k2) x[j * G + k2] = v[k2];
-    }
-    __syncwarp();
-  }
-}
-
-// Unnormalised inverse of line_fwd: input in line_fwd's output distribution,
-// output x[e] = sum_k X[k] exp(+2 pi i k (g + G e) / MS).
-template <int MS, class Slot>
-__device__ __forceinline__ void line_inv(float2 (&x)[Cfg<MS>::E], int g, bool act, Slot slot, const float2* tw) {
-  constexpr int E = Cfg<MS>::E, G = Cfg<MS>::G;
-  if constexpr (G > 1) {
-#pragma unroll
-    for (int j = 0; j < E / G; ++j) {
-      const int k1 = g + G * j;
-      float2 v[G];
-#pragma unroll
-      for (int k2 = 0; k2 < G; ++k2) v[k2] = x[j * G + k2];
-      dft_reg<G, true>(v);
-#pragma unroll
-      for (int gp = 0; gp < G; ++gp) {
-        const float2 t = gp ? twmul<true>(v[gp], tw[(gp * k1) & (MS - 1)]) : v[0];
-        if (act) slot(k1 * G + (gp ^ g)) = t;
-      }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int k1 = 0; k1 < E; ++k1) x[k1] = act ? slot(k1 * G + (g ^ (k1 & (G - 1)))) : f2(0.f, 0.f);
-    __syncwarp();
-  }
-  dft_reg<E, true>(x);
-}
-
-// Offset of level-l (l >= 1) factor arrays in the float pyramid buffer:
-// [u^0: M][w^0: M] then per level l = 1.. : [W_u^{l-1}][1/w^l][u^l/w^l],
-// each (MS >> l)^2 floats.
-__host__ __device__ __forceinline__ int lvl_off(int MS, int l) {
-  int off = 2 * MS * MS;
-  for (int j = 1; j < l; ++j) off += 3 * (MS >> j) * (MS >> j);
-  return off;
-}
-__host__ __device__ __forceinline__ int pyr_size(int MS, int L) { return lvl_off(MS, L); }
-
-enum Mode { kStep = 0, kEval = 1, kSim = 2 };
-
-struct StepArgs {
-  const float2* z;    // object [n_rows][n_cols]
-  int n_rows, n_cols;
-  const float2* Q;    // probe [MS][MS]
-  const float2* tw;   // exp(-2 pi i t / MS), t < MS
-  const float* amp;   // amplitudes sqrt(d) [n_pos][MS][MS]
-  float* out_int;     // forward intensities [n_pos][MS][MS] (kSim)
-  const int32_t* pos; // [n_pos][2]
-  const int32_t* idx; // window of each cluster
-  int n_pos;
-  float2* contrib;    // [windows][MS][MS] increments w . Delta
-  const float* pyr;   // per-level factors
-  int levels;
-  double* part;       // [windows][CL][2] block partials of the window's two sums
-  float2* pnum;       // probe step only: [windows][MS][MS] conj(z_k)(R_k - Q z_k)
-  float* pa2;         // probe step only: [windows][MS][MS] |z_k|^2
-  double* pmax;       // probe step only: [windows][CL] block maxima of |z_k|^2
-  int* err;           // bit 0: window index out of range
-};
-
-__device__ __forceinline__ double block_sum(double v, double* red, int tid, int nthreads) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if ((tid & 31) == 0) red[tid >> 5] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (tid == 0)
-    for (int i = 0; i < nthreads / 32; ++i) r += red[i];
-  __syncthreads();
-  return r;
-}
-
-__device__ __forceinline__ double block_max(double v, double* red, int tid, int nthreads) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
-  if ((tid & 31) == 0) red[tid >> 5] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (tid == 0)
-    for (int i = 0; i < nthreads / 32; ++i) r = fmax(r, red[i]);
-  __syncthreads();
-  return r;
-}
-
-__device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
-  return f2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
-}
-
-// MAGPS V-cycle of one window in residual form, on this block's column slab
-// Y (g^0 for MS rows x SLAB columns).  Lane gamma of a warp owns column
-// gamma of a strip of 2^TT rows; the 2x2 restrictions pair columns by warp
-// shuffles.  Levels coarser than TT are kept in `lvl` (local levels up to
-// log2(SLAB); coarser ones span the cluster and are finished by block 0).
-template <int MS, int TT>
-__device__ __forceinline__ void vcycle(const float2* Y, float2* lvl, const float* pyr, int L, int q, float2* out,
-                                       int tid) {
-  using Gm = Geo<MS>;
-  constexpr int SLAB = Gm::SLAB, T = Gm::T, CL = Gm::CL, H = 1 << TT, NS = MS / H, SPAR = T / SLAB;
-  constexpr int LLOC = (SLAB >= 32) ? 5 : (SLAB == 16 ? 4 : 3);  // log2(SLAB)
-  static_assert((1 << LLOC) == SLAB, "slab levels");
-  const int gam = tid % SLAB, s0 = tid / SLAB;
-  const int cgl = q * SLAB + gam;  // column in the window
-  const bool deep = (L - 1) > TT;
-  const float* u0 = pyr;
-  const float* wu1 = pyr + lvl_off(MS, 1);
-  const float* iw1 = wu1 + (MS / 2) * (MS / 2);
-  const float* rr1 = iw1 + (MS / 2) * (MS / 2);
-  // offsets of the slab's level arrays (levels TT .. LLOC) in lvl
-  auto off = [](int l) {
-    int o = 0;
-    for (int j = TT; j < l; ++j) o += (MS >> j) * (SLAB >> j);
-    return o;
-  };
-
-  // g at level TT of the 2^TT x 2^TT bin of column cgl in strip s (the same
-  // value in all 2^TT lanes of the bin); g0 and g1 keep the finer levels.
-  auto strip = [&](int s, bool ok, float2 (&g0)[H], float2 (&g1)[H / 2]) -> float2 {
-    const int R0 = s * H;
-#pragma unroll
-    for (int a = 0; a < H; ++a) g0[a] = ok ? Y[yi<MS>(R0 + a, gam)] : f2(0.f, 0.f);
-#pragma unroll
-    for (int a = 0; a < H / 2; ++a) {
-      float2 v = cadd(g0[2 * a], g0[2 * a + 1]);
-      v = cadd(v, shfl_xor2(v, 1));
-      const float w = ok ? __ldg(&wu1[(R0 / 2 + a) * (MS / 2) + (cgl >> 1)]) : 0.f;
-      g1[a] = cscale(v, 0.25f * w);
-    }
-    if constexpr (TT == 1) {
-      return g1[0];
-    } else {
-      float2 v = cadd(g1[0], g1[1]);
-      v = cadd(v, shfl_xor2(v, 2));
-      const float w = ok ? __ldg(&pyr[lvl_off(MS, 2) + (R0 / 4) * (MS / 4) + (cgl >> 2)]) : 0.f;
-      return cscale(v, 0.25f * w);
-    }
-  };
-
-  if (deep) {
-    // phase 1: level-TT values of every strip bin
-    for (int base = 0; base < NS; base += SPAR) {
-      const int s = base + s0;
-      const bool ok = s < NS;
-      float2 g0[H], g1[H / 2];
-      const float2 gT = strip(s, ok, g0, g1);
-      if (ok && (gam & (H - 1)) == 0) lvl[off(TT) + s * (SLAB >> TT) + (gam >> TT)] = gT;
-    }
-    __syncthreads();
-    // phase 2: restrictions inside the slab, levels TT+1 .. min(L-1, LLOC)
-    const int ltop = (L - 1) < LLOC ? (L - 1) : LLOC;
-    for (int l = TT; l < ltop; ++l) {
-      const int rows = MS >> (l + 1), cols = SLAB >> (l + 1), fc = SLAB >> l;
-      const float2* fine = lvl + off(l);
-      float2* coarse = lvl + off(l + 1);
-      const float* wu = pyr + lvl_off(MS, l + 1);
-      for (int i = tid; i < rows * cols; i += T) {
-        const int r = i / cols, c = i - (i / cols) * cols;
-        const float2 sm = cadd(cadd(fine[(2 * r) * fc + 2 * c], fine[(2 * r) * fc + 2 * c + 1]),
-                               cadd(fine[(2 * r + 1) * fc + 2 * c], fine[(2 * r + 1) * fc + 2 * c + 1]));
-        coarse[i] = cscale(sm, 0.25f * __ldg(&wu[r * (MS >> (l + 1)) + q * cols + c]));
-      }
-      __syncthreads();
-    }
-    if (L - 1 <= LLOC) {
-      // coarsest level inside the slab
-      const int l = L - 1, rows = MS >> l, cols = SLAB >> l;
-      float2* a = lvl + off(l);
-      const float* iw = pyr + lvl_off(MS, l) + (MS >> l) * (MS >> l);
-      for (int i = tid; i < rows * cols; i += T) {
-        const int r = i / cols, c = i - (i / cols) * cols;
-        a[i] = cscale(a[i], __ldg(&iw[r * (MS >> l) + q * cols + c]));
-      }
-      __syncthreads();
-    } else {
-      if constexpr (CL > 1) {
-        // levels LLOC .. L-1 span the cluster: block 0 gathers the CL x CL
-        // level-LLOC values (column qq from block qq), runs the coarse
-        // levels, and sends back level-LLOC increments.
-        window_sync<CL>();
-        if (q == 0 && tid == 0) {
-          float2* gl = lvl + off(LLOC + 1);  // global arrays of levels LLOC.. in block 0
-          auto goff = [](int i) {  // offset of level LLOC + i
-            int o = 0;
-            for (int l = LLOC; l < LLOC + i; ++l) o += (MS >> l) * (MS >> l);
-            return o;
-          };
-          for (int qq = 0; qq < CL; ++qq) {
-            const float2* src = peer<CL>(lvl, qq) + off(LLOC);
-            for (int i = 0; i < CL; ++i) gl[i * CL + qq] = src[i];
-          }
-          for (int l = LLOC; l < L - 1; ++l) {
-            const int n = MS >> (l + 1), nf = MS >> l;
-            const float2* fine = gl + goff(l - LLOC);
-            float2* coarse = gl + goff(l - LLOC + 1);
-            const float* wu = pyr + lvl_off(MS, l + 1);
-            for (int i = 0; i < n * n; ++i) {
-              const int r = i / n, c = i % n;
-              const float2 sm = cadd(cadd(fine[(2 * r) * nf + 2 * c], fine[(2 * r) * nf + 2 * c + 1]),
-                                     cadd(fine[(2 * r + 1) * nf + 2 * c], fine[(2 * r + 1) * nf + 2 * c + 1]));
-              coarse[i] = cscale(sm, 0.25f * wu[i]);
-            }
-          }
-          {
-            const int l = L - 1, n = MS >> l;
-            float2* a = gl + goff(l - LLOC);
-            const float* iw = pyr + lvl_off(MS, l) + n * n;
-            for (int i = 0; i < n * n; ++i) a[i] = cscale(a[i], iw[i]);
-          }
-          for (int l = L - 2; l >= LLOC; --l) {
-            const int n = MS >> l, nc = n >> 1;
-            float2* a = gl + goff(l - LLOC);
-            const float2* pe = gl + goff(l - LLOC + 1);
-            const float* iw = pyr + lvl_off(MS, l) + n * n;
-            const float* rr = iw + n * n;
-            for (int i = 0; i < n * n; ++i) {
-              const int r = i / n, c = i % n;
-              const float2 p = pe[(r >> 1) * nc + (c >> 1)];
-              const float2 v = cscale(a[i], iw[i]);
-              a[i] = f2(v.x + rr[i] * p.x, v.y + rr[i] * p.y);
-            }
-          }
-          for (int qq = 0; qq < CL; ++qq) {
-            float2* dst = peer<CL>(lvl, qq) + off(LLOC);
-            for (int i = 0; i < CL; ++i) dst[i] = gl[i * CL + qq];
-          }
-        }
-        window_sync<CL>();
-      }
-    }
-    // up-pass inside the slab down to level TT
-    const int lstart = ((L - 1) < LLOC ? (L - 1) : LLOC) - 1;
-    for (int l = lstart; l >= TT; --l) {
-      const int rows = MS >> l, cols = SLAB >> l, cc = cols >> 1;
-      float2* a = lvl + off(l);
-      const float2* pe = lvl + off(l + 1);
-      const float* iw = pyr + lvl_off(MS, l) + (MS >> l) * (MS >> l);
-      const float* rr = iw + (MS >> l) * (MS >> l);
-      for (int i = tid; i < rows * cols; i += T) {
-        const int r = i / cols, c = i - (i / cols) * cols;
-        const int o = r * (MS >> l) + q * cols + c;
-        const float2 p = pe[(r >> 1) * cc + (c >> 1)];
-        const float2 v = cscale(a[i], __ldg(&iw[o]));
-        const float w = __ldg(&rr[o]);
-        a[i] = f2(v.x + w * p.x, v.y + w * p.y);
-      }
-      __syncthreads();
-    }
-  }
-  // phase 3: per strip, the up-pass to level 0 and the increments w . Delta
-  const float* iwT = pyr + lvl_off(MS, TT) + (MS >> TT) * (MS >> TT);
-  for (int base = 0; base < NS; base += SPAR) {
-    const int s = base + s0;
-    const bool ok = s < NS;
-    float2 g0[H], g1[H / 2];
-    const float2 gT = strip(s, ok, g0, g1);
-    const int R0 = s * H;
-    float2 eT = f2(0.f, 0.f);
-    if (ok) {
-      eT = deep ? lvl[off(TT) + s * (SLAB >> TT) + (gam >> TT)]
-                : cscale(gT, __ldg(&iwT[(R0 >> TT) * (MS >> TT) + (cgl >> TT)]));
-    }
-    float2 e1[H / 2];
-    if constexpr (TT == 1) {
-      e1[0] = eT;
-    } else {
-#pragma unroll
-      for (int a = 0; a < 2; ++a) {
-        const int o = (R0 / 2 + a) * (MS / 2) + (cgl >> 1);
-        const float2 v = cscale(g1[a], ok ? __ldg(&iw1[o]) : 0.f);
-        const float w = ok ? __ldg(&rr1[o]) : 0.f;
-        e1[a] = f2(v.x + w * eT.x, v.y + w * eT.y);
-      }
-    }
-    if (ok) {
-#pragma unroll
-      for (int a = 0; a < H; ++a) {
-        const int o = (R0 + a) * MS + cgl;
-        const float u = __ldg(&u0[o]);
-        out[o] = f2(g0[a].x + u * e1[a >> 1].x, g0[a].y + u * e1[a >> 1].y);
-      }
-    }
-  }
-}
-
-// One cluster of Geo<MS>::CL blocks per window (grid = windows * CL), each
-// with Geo<MS>::T threads and Geo<MS>::SMEM bytes of dynamic shared memory.
-template <int MS, int MODE>
-__global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel(StepArgs A) {
-  using Gm = Geo<MS>;
-  constexpr int E = Gm::E, G = Gm::G, CL = Gm::CL, SLAB = Gm::SLAB, T = Gm::T, M = Gm::M;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* X = reinterpret_cast<float2*>(smem_raw);  // row slab
-  float2* Y = X + Gm::XN;                            // column slab
-  float2* tws = Y + Gm::XN;
-  float2* lvl = tws + MS;
-  double* red = reinterpret_cast<double*>(lvl + Gm::LVL);  // block_sum scratch
-
-  const int tid = threadIdx.x;
-  int q = 0;
-  if constexpr (CL > 1) q = (int)cg::this_cluster().block_rank();
-  const int win = blockIdx.x / CL;
-  for (int i = tid; i < MS; i += T) tws[i] = A.tw[i];
-  const int k = A.idx[win];
-  if ((unsigned)k >= (unsigned)A.n_pos) {
-    if (tid == 0 && q == 0) atomicOr(A.err, 1);
-    return;  // uniform across the cluster
-  }
-  const int pr = A.pos[2 * k], pc = A.pos[2 * k + 1];
-  const float2* zk = A.z + (size_t)pr * A.n_cols + pc;
-  __syncthreads();
-
-  const bool act = tid < Gm::LANES;
-  const int lam = act ? tid / G : 0, g = tid % G;
-  const int line = q * SLAB + lam;  // column (passes A, C) or row (pass B) of this lane group
-
-  // slab geometry of the row-coalesced passes: lane gam of a row of the
-  // block's column slab, rows r0, r0 + RSTEP, ...
-  constexpr int RSTEP = T / SLAB, RPT = MS / RSTEP;
-  const int gam = tid % SLAB, r0 = tid / SLAB;
-  const int cgl = q * SLAB + gam;
-
-  // ---- pass A: exit wave psi = Q z_k gathered row by row into Y, then the
-  // column FFTs; results go to the row owners' X
-  {
-    float2 pv[RPT];
-#pragma unroll
-    for (int i = 0; i < RPT; ++i) {
-      const int r = r0 + RSTEP * i;
-      pv[i] = cmul(__ldg(&A.Q[r * MS + cgl]), __ldg(&zk[(size_t)r * A.n_cols + cgl]));
-    }
-#pragma unroll
-    for (int i = 0; i < RPT; ++i) Y[yi<MS>(r0 + RSTEP * i, gam)] = pv[i];
-    __syncthreads();
-    float2 x[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) x[e] = act ? Y[yi<MS>(g + G * e, lam)] : f2(0.f, 0.f);
-    __syncwarp();
-    line_fwd<MS, false>(x, g, act, [&](int sl) -> float2& { return Y[yi<MS>(sl, lam)]; }, tws);
-#pragma unroll
-    for (int j = 0; j < E / G; ++j)
-#pragma unroll
-      for (int k2 = 0; k2 < G; ++k2) {
-        const int kr = g + G * j + E * k2;
-        float2* dst = peer<CL>(X, (E * k2) / SLAB);
-        if (act) dst[xi<MS>(kr % SLAB, line)] = x[j * G + k2];
-      }
-  }
-  window_arrive<CL>();
-  // amplitudes of this block's rows, fetched while the other blocks finish
-  float av[E];
-  if constexpr (MODE != kSim) {
-    const float* ampr = A.amp + (size_t)k * M + line * MS;
-#pragma unroll
-    for (int j = 0; j < E / G; ++j)
-#pragma unroll
-      for (int k2 = 0; k2 < G; ++k2) av[j * G + k2] = act ? __ldg(&ampr[g + G * j + E * k2]) : 0.f;
-  }
-  window_wait<CL>();
-
-  // ---- pass B: row FFTs, modulus projection, inverse row FFTs; results go
-  // to the column owners' Y
-  float res = 0.f;
-  {
-    const int kr = line;
-    float2 x[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) x[e] = act ? X[xi<MS>(lam, g + G * e)] : f2(0.f, 0.f);
-    __syncwarp();
-    line_fwd<MS, false>(x, g, act, [&](int sl) -> float2& { return X[xi<MS>(lam, sl)]; }, tws);
-    if constexpr (MODE == kSim) {
-      float* outk = A.out_int + (size_t)k * M + kr * MS;
-#pragma unroll
-      for (int j = 0; j < E / G; ++j)
-#pragma unroll
-        for (int k2 = 0; k2 < G; ++k2) {
-          const float2 P = x[j * G + k2];
-          if (act) outk[g + G * j + E * k2] = P.x * P.x + P.y * P.y;
-        }
-      return;  // no block reads another block's memory after the barrier above
-    } else {
-      constexpr float inv_m = 1.0f / float(M);
-#pragma unroll
-      for (int i = 0; i < E; ++i) {
-        const float a = av[i];
-        const float2 P = x[i];
-        const float p2 = P.x * P.x + P.y * P.y;
-        float mag;
-        float2 Pp;
-        if (p2 > 0.f) {
-          const float rs = rsqrtf(p2);
-          mag = p2 * rs;
-          const float sc = a * rs * inv_m;
-          Pp = f2(P.x * sc, P.y * sc);
-        } else {
-          mag = 0.f;
-          Pp = f2(a * inv_m, 0.f);
-        }
-        const float dlt = mag - a;
-        res += dlt * dlt;
-        x[i] = Pp;
-      }
-      line_inv<MS>(x, g, act, [&](int sl) -> float2& { return X[xi<MS>(lam, sl)]; }, tws);
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int c = g + G * e;
-        float2* dst = peer<CL>(Y, (G * e) / SLAB);
-        if (act) dst[yi<MS>(kr, c % SLAB)] = x[e];
-      }
-    }
-  }
-  if constexpr (MODE != kSim) {
-    window_arrive<CL>();
-    // the exit wave again, row by row, while the other blocks finish pass B;
-    // it is parked in X (free once every block of the window is past pass B)
-    float2 pv[RPT];
-#pragma unroll
-    for (int i = 0; i < RPT; ++i) {
-      const int r = r0 + RSTEP * i;
-      pv[i] = cmul(__ldg(&A.Q[r * MS + cgl]), __ldg(&zk[(size_t)r * A.n_cols + cgl]));
-    }
-    window_wait<CL>();
-#pragma unroll
-    for (int i = 0; i < RPT; ++i) X[yi<MS>(r0 + RSTEP * i, gam)] = pv[i];
-
-    // ---- pass C: inverse column FFTs; R_k into Y
-    {
-      float2 x[E];
-#pragma unroll
-      for (int j = 0; j < E / G; ++j)
-#pragma unroll
-        for (int k2 = 0; k2 < G; ++k2) x[j * G + k2] = act ? Y[yi<MS>(g + G * j + E * k2, lam)] : f2(0.f, 0.f);
-      __syncwarp();
-      line_inv<MS>(x, g, act, [&](int sl) -> float2& { return Y[yi<MS>(sl, lam)]; }, tws);
-#pragma unroll
-      for (int e = 0; e < E; ++e)
-        if (act) Y[yi<MS>(g + G * e, lam)] = x[e];
-    }
-    __syncthreads();
-
-    // ---- g^0 = conj(Q)(R_k - psi) over the slab, lane = column; into Y, or
-    // straight to the increments for one level
-    float gn2 = 0.f, amax = 0.f;
-    float2* out = A.contrib + (size_t)win * M;
-    const bool direct = (MODE == kStep) && A.levels == 1;
-    {
-      float2 qv[RPT];
-#pragma unroll
-      for (int i = 0; i < RPT; ++i) qv[i] = __ldg(&A.Q[(r0 + RSTEP * i) * MS + cgl]);
-#pragma unroll
-      for (int i = 0; i < RPT; ++i) {
-        const int r = r0 + RSTEP * i;
-        const int o = yi<MS>(r, gam);
-        const float2 rho = csub(Y[o], X[o]);
-        const float2 gg = cmul_cj(qv[i], rho);
-        gn2 += gg.x * gg.x + gg.y * gg.y;
-        if (MODE == kStep) {
-          if (A.pnum) {
-            // the probe step's window terms (same R_k and z_k)
-            const float2 zz = __ldg(&zk[(size_t)r * A.n_cols + cgl]);
-            const float a2 = zz.x * zz.x + zz.y * zz.y;
-            A.pnum[(size_t)win * M + r * MS + cgl] = cmul_cj(zz, rho);
-            A.pa2[(size_t)win * M + r * MS + cgl] = a2;
-            amax = fmaxf(amax, a2);
-          }
-          if (direct)
-            out[r * MS + cgl] = gg;
-          else
-            Y[o] = gg;
-        }
-      }
-    }
-    if (MODE == kStep && A.pnum) {
-      const double bm = block_max((double)amax, red, tid, T);
-      if (tid == 0) A.pmax[win * CL + q] = bm;
-    }
-
-    // block partials of the window's two sums (float64); the kernel that
-    // follows combines them in block order
-    const double rs = block_sum((double)res, red, tid, T);
-    const double gs = block_sum((double)gn2, red, tid, T);
-    if (tid == 0) {
-      A.part[(size_t)(win * CL + q) * 2] = rs;
-      A.part[(size_t)(win * CL + q) * 2 + 1] = gs;
-    }
-    if (MODE != kStep || direct) return;
-
-    // ---- pass D: MAGPS V-cycle (levels >= 2) on the column slab
-    if (A.levels == 2)
-      vcycle<MS, 1>(Y, lvl, A.pyr, A.levels, q, out, tid);
-    else
-      vcycle<MS, 2>(Y, lvl, A.pyr, A.levels, q, out, tid);
-  }
-}
+#include "fft_lines.cuh"
+#include "window_kernel.cuh"
 
 // z += sum_b contrib_b / sum_b w0 over the windows covering each pixel, in
 // minibatch order (bitwise reproducible).  One block of 256 threads per
 // 16 x 16 object tile, one pixel per thread: the block first lists, in
-// minibatch order, the windows that overlap its tile (a ballot compaction by
-// warp 0); each thread then walks that short list four entries at a time with
-// predicated loads, so several increments are in flight per thread.
+// minibatch order, the windows that overlap its tile (corners as recorded by
+// the window kernel; a ballot compaction over all warps); each thread then
+// walks that short list four entries at a time with predicated loads, so
+// several increments are in flight per thread.  Block (0, 0) also turns the
+// window kernel's block partials into Phi_k and ||grad Phi_k||.
 // Dynamic smem: count int2 corners + count ints.
 constexpr int kApplyTile = 16;
-__global__ void __launch_bounds__(256) apply_kernel(float2* z, int n_rows, int n_cols, const int32_t* pos,
+__global__ void __launch_bounds__(256) apply_kernel(float2* z, int n_rows, int n_cols, const int2* corners,
                                                     const int32_t* idx, int count, int n_pos,
                                                     const float2* contrib, const float* w0, int MS,
                                                     const double* part, int CL, double* phi_pos, double* gn_pos) {
   extern __shared__ int2 corner[];
+  int* list = reinterpret_cast<int*>(corner + count);
+  __shared__ int warp_hits[8], n_list;
   if (blockIdx.x == 0 && blockIdx.y == 0) {
     // the window kernel's block partials -> Phi_k and ||grad Phi_k||, in block order
     for (int b = threadIdx.x; b < count; b += blockDim.x) {
@@ -764,31 +89,32 @@ __global__ void __launch_bounds__(256) apply_kernel(float2* z, int n_rows, int n
       gn_pos[k] = sqrt(g);
     }
   }
-  int* list = reinterpret_cast<int*>(corner + count);
-  __shared__ int n_list;
   const int R0 = blockIdx.y * kApplyTile, C0 = blockIdx.x * kApplyTile;
-  for (int i = threadIdx.x; i < count; i += blockDim.x) {
-    const int k = idx[i];
-    corner[i] = ((unsigned)k < (unsigned)n_pos) ? make_int2(pos[2 * k], pos[2 * k + 1])
-                                                : make_int2(-(1 << 30), -(1 << 30));
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const unsigned lane = threadIdx.x;
-    int base = 0;
-    for (int b0 = 0; b0 < count; b0 += 32) {
-      const int b = b0 + (int)lane;
-      bool hit = false;
-      if (b < count) {
-        const int2 q = corner[b];
-        hit = q.x < R0 + kApplyTile && q.x + MS > R0 && q.y < C0 + kApplyTile && q.y + MS > C0;
-      }
-      const unsigned mask = __ballot_sync(0xffffffffu, hit);
-      if (hit) list[base + __popc(mask & ((1u << lane) - 1u))] = b;
-      base += __popc(mask);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // windows meeting this tile, listed in minibatch order: every warp takes
+  // 32 consecutive windows per round, ballots, and the rounds are stitched
+  // together by per-warp counts
+  int base = 0;
+  for (int b0 = 0; b0 < count; b0 += 256) {
+    const int b = b0 + threadIdx.x;
+    bool hit = false;
+    if (b < count) {
+      const int2 q = corners[b];
+      corner[b] = q;
+      hit = q.x < R0 + kApplyTile && q.x + MS > R0 && q.y < C0 + kApplyTile && q.y + MS > C0;
     }
-    if (lane == 0) n_list = base;
+    const unsigned mask = __ballot_sync(0xffffffffu, hit);
+    if (lane == 0) warp_hits[wid] = __popc(mask);
+    __syncthreads();
+    int off = base;
+    for (int i = 0; i < wid; ++i) off += warp_hits[i];
+    if (hit) list[off + __popc(mask & ((1u << lane) - 1u))] = b;
+    int tot = 0;
+    for (int i = 0; i < 8; ++i) tot += warp_hits[i];
+    base += tot;
+    __syncthreads();
   }
+  if (threadIdx.x == 0) n_list = base;
   __syncthreads();
   const int nl = n_list;
   const int r = R0 + (threadIdx.x >> 4), c = C0 + (threadIdx.x & 15);
@@ -1121,12 +447,12 @@ cudaError_t enqueue_pyramid(const float2* Q, int MS, int L, float alpha, unsigne
   return cudaGetLastError();
 }
 
-cudaError_t launch_apply(float2* z, int n_rows, int n_cols, const int32_t* pos, const int32_t* idx, int count,
+cudaError_t launch_apply(float2* z, int n_rows, int n_cols, const int2* corners, const int32_t* idx, int count,
                          int n_pos, const float2* contrib, const float* w0, int MS, const double* part,
                          double* phi_pos, double* gn_pos, cudaStream_t st) {
   const dim3 tiles((n_cols + kApplyTile - 1) / kApplyTile, (n_rows + kApplyTile - 1) / kApplyTile);
   return launch_ex(apply_kernel, tiles, dim3(256), (sizeof(int2) + sizeof(int)) * count, st, 1, z, n_rows, n_cols,
-                   pos, idx, count, n_pos, contrib, w0, MS, part, cluster_of(MS), phi_pos, gn_pos);
+                   corners, idx, count, n_pos, contrib, w0, MS, part, cluster_of(MS), phi_pos, gn_pos);
 }
 
 template <int MODE>
@@ -1200,6 +526,7 @@ struct magpie_ctx {
   double* phi_pos = nullptr;
   double* gn_pos = nullptr;
   double* part = nullptr;     // [n_pos][kMaxCluster][2] per-block partial sums
+  int2* corner = nullptr;     // [minibatch] corners of a step's windows
   unsigned long long* mx = nullptr;  // max |Q|^2 (bits of a double)
   float2* pnum = nullptr;     // probe step: [minibatch][m][m]
   float* pa2 = nullptr;       // probe step: [minibatch][m][m]
@@ -1234,6 +561,7 @@ StepArgs make_args(magpie_ctx* c, const int32_t* idx) {
   a.pyr = c->pyr;
   a.levels = c->p.levels;
   a.part = c->part;
+  a.corner = c->corner;
   a.pnum = c->pnum;
   a.pa2 = c->pa2;
   a.pmax = c->pmax;
@@ -1249,8 +577,8 @@ int enqueue_step(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st, 
   CUDA_TRY(launch_window_m<kStep>(c->p.m, a, count, st));
   if (ev) CUDA_TRY(cudaEventRecord(ev[1], st));
   if (ev) CUDA_TRY(cudaEventRecord(ev[2], st));
-  CUDA_TRY(launch_apply(c->z, c->p.n_rows, c->p.n_cols, c->pos, idx, count, c->p.n_pos, c->contrib, c->pyr + c->M,
-                        c->p.m, c->part, c->phi_pos, c->gn_pos, st));
+  CUDA_TRY(launch_apply(c->z, c->p.n_rows, c->p.n_cols, c->corner, idx, count, c->p.n_pos, c->contrib,
+                        c->pyr + c->M, c->p.m, c->part, c->phi_pos, c->gn_pos, st));
   if (c->p.update_probe) {
     probe_apply_kernel<<<(c->M + 255) / 256, 256, 0, st>>>(c->Q, c->M, idx, count, c->p.n_pos, c->pnum, c->pa2,
                                                            c->pmax, cluster_of(c->p.m), c->p.beta);
@@ -1352,7 +680,7 @@ constexpr size_t kNoAllocTwBytes = sizeof(float2) * 128;
 constexpr size_t kNoAllocIdxBytes = sizeof(int32_t) * kMaxMinibatch;
 constexpr size_t kNoAllocPartBytes = sizeof(double) * 2 * kMaxCluster * kMaxMinibatch;              // 512 KiB
 constexpr size_t kNoAllocBytes = kNoAllocContribBytes + kNoAllocPyrBytes + kNoAllocPyrQBytes + kNoAllocPyrUBytes +
-                                 kNoAllocTwBytes + kNoAllocIdxBytes + kNoAllocPartBytes + 8 + 256;
+                                 kNoAllocTwBytes + kNoAllocIdxBytes + kNoAllocPartBytes + 8 + sizeof(int2) * kMaxMinibatch + 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 // idx -> sanitized copy: a window whose index is outside [0, n_pos) or whose
@@ -1384,6 +712,7 @@ struct NoAllocScratch {
   int32_t* idx;
   double* part;
   unsigned long long* mx;
+  int2* corner;
   int* err;
 };
 
@@ -1417,6 +746,8 @@ int noalloc_scratch(NoAllocScratch* out) {
   b += kNoAllocPartBytes;
   out->mx = (unsigned long long*)b;
   b += 8;
+  out->corner = (int2*)b;
+  b += sizeof(int2) * kMaxMinibatch;
   out->err = (int*)b;
   return MAGPIE_OK;
 }
@@ -1453,7 +784,7 @@ void magpie_destroy(magpie_ctx* c) {
     if (e) cudaEventDestroy(e);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   void* bufs[] = {c->Q, c->tw, c->amp, c->stage, c->pos, c->pyr, c->pyr_q, c->pyr_u, c->contrib,
-                  c->phi_pos, c->gn_pos, c->part, c->mx, c->pnum, c->pa2, c->pmax, c->iota, c->order, c->sums, c->err};
+                  c->phi_pos, c->gn_pos, c->part, c->corner, c->mx, c->pnum, c->pa2, c->pmax, c->iota, c->order, c->sums, c->err};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete c;
@@ -1497,6 +828,7 @@ int magpie_create(magpie_ctx** out, const magpie_params* params, void* object, c
       (rc = alloc((void**)&c->phi_pos, sizeof(double) * N)) || (rc = alloc((void**)&c->gn_pos, sizeof(double) * N)) ||
       (rc = alloc((void**)&c->part, sizeof(double) * 2 * kMaxCluster * N)) ||
       (rc = alloc((void**)&c->mx, sizeof(unsigned long long))) ||
+      (rc = alloc((void**)&c->corner, sizeof(int2) * p.minibatch)) ||
       (p.update_probe && (rc = alloc((void**)&c->pnum, sizeof(float2) * M * p.minibatch))) ||
       (p.update_probe && (rc = alloc((void**)&c->pa2, sizeof(float) * M * p.minibatch))) ||
       (p.update_probe && (rc = alloc((void**)&c->pmax, sizeof(double) * kMaxCluster * p.minibatch))) ||
@@ -1753,9 +1085,10 @@ int magpie_step_noalloc(void* object, int32_t n_rows, int32_t n_cols, const void
   a.pyr = w.pyr;
   a.levels = levels;
   a.part = w.part;
+  a.corner = w.corner;
   a.err = w.err;
   CUDA_TRY(launch_window_m<kStep>(m, a, count, st));
-  CUDA_TRY(launch_apply((float2*)object, n_rows, n_cols, positions, w.idx, count, n_pos, w.contrib, w.pyr + m * m, m,
+  CUDA_TRY(launch_apply((float2*)object, n_rows, n_cols, w.corner, w.idx, count, n_pos, w.contrib, w.pyr + m * m, m,
                         w.part, phi, gnorm, st));
   int h = 0;
   CUDA_TRY(cudaMemcpyAsync(&h, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));

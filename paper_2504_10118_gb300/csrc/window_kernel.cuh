@@ -1,0 +1,475 @@
+// window_kernel.cuh -- the per-window kernel of the MAGPIE sweep (gather,
+// 2-D FFT, modulus projection, inverse FFT, MAGPS V-cycle) and its level
+// factor layout.  Included by magpie.cu inside its anonymous namespace.
+#pragma once
+
+// Offset of level-l (l >= 1) factor arrays in the float pyramid buffer:
+// [u^0: M][w^0: M] then per level l = 1.. : [W_u^{l-1}][1/w^l][u^l/w^l],
+// each (MS >> l)^2 floats.
+__host__ __device__ __forceinline__ int lvl_off(int MS, int l) {
+  int off = 2 * MS * MS;
+  for (int j = 1; j < l; ++j) off += 3 * (MS >> j) * (MS >> j);
+  return off;
+}
+__host__ __device__ __forceinline__ int pyr_size(int MS, int L) { return lvl_off(MS, L); }
+
+enum Mode { kStep = 0, kEval = 1, kSim = 2 };
+
+struct StepArgs {
+  const float2* z;    // object [n_rows][n_cols]
+  int n_rows, n_cols;
+  const float2* Q;    // probe [MS][MS]
+  const float2* tw;   // exp(-2 pi i t / MS), t < MS
+  const float* amp;   // amplitudes sqrt(d) [n_pos][MS][MS]
+  float* out_int;     // forward intensities [n_pos][MS][MS] (kSim)
+  const int32_t* pos; // [n_pos][2]
+  const int32_t* idx; // window of each cluster
+  int n_pos;
+  float2* contrib;    // [windows][MS][MS] increments w . Delta
+  const float* pyr;   // per-level factors
+  int levels;
+  double* part;       // [windows][CL][2] block partials of the window's two sums
+  int2* corner;       // step: [windows] top-left corner of each window (far away if skipped)
+  float2* pnum;       // probe step only: [windows][MS][MS] conj(z_k)(R_k - Q z_k)
+  float* pa2;         // probe step only: [windows][MS][MS] |z_k|^2
+  double* pmax;       // probe step only: [windows][CL] block maxima of |z_k|^2
+  int* err;           // bit 0: window index out of range
+};
+
+__device__ __forceinline__ double block_sum(double v, double* red, int tid, int nthreads) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (tid == 0)
+    for (int i = 0; i < nthreads / 32; ++i) r += red[i];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ double block_max(double v, double* red, int tid, int nthreads) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (tid == 0)
+    for (int i = 0; i < nthreads / 32; ++i) r = fmax(r, red[i]);
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
+  return f2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+
+// MAGPS V-cycle of one window in residual form, on this block's column slab
+// Y (g^0 for MS rows x SLAB columns).  Lane gamma of a warp owns column
+// gamma of a strip of 2^TT rows; the 2x2 restrictions pair columns by warp
+// shuffles.  Levels coarser than TT are kept in `lvl` (local levels up to
+// log2(SLAB); coarser ones span the cluster and are finished by block 0).
+template <int MS, int TT>
+__device__ __forceinline__ void vcycle(const float2* Y, float2* lvl, const float* pyr, int L, int q, float2* out,
+                                       int tid) {
+  using Gm = Geo<MS>;
+  constexpr int SLAB = Gm::SLAB, T = Gm::T, CL = Gm::CL, H = 1 << TT, NS = MS / H, SPAR = T / SLAB;
+  constexpr int LLOC = (SLAB >= 32) ? 5 : (SLAB == 16 ? 4 : 3);  // log2(SLAB)
+  static_assert((1 << LLOC) == SLAB, "slab levels");
+  const int gam = tid % SLAB, s0 = tid / SLAB;
+  const int cgl = q * SLAB + gam;  // column in the window
+  const bool deep = (L - 1) > TT;
+  const float* u0 = pyr;
+  const float* wu1 = pyr + lvl_off(MS, 1);
+  const float* iw1 = wu1 + (MS / 2) * (MS / 2);
+  const float* rr1 = iw1 + (MS / 2) * (MS / 2);
+  // offsets of the slab's level arrays (levels TT .. LLOC) in lvl
+  auto off = [](int l) {
+    int o = 0;
+    for (int j = TT; j < l; ++j) o += (MS >> j) * (SLAB >> j);
+    return o;
+  };
+
+  // g at level TT of the 2^TT x 2^TT bin of column cgl in strip s (the same
+  // value in all 2^TT lanes of the bin); g0 and g1 keep the finer levels.
+  auto strip = [&](int s, bool ok, float2 (&g0)[H], float2 (&g1)[H / 2]) -> float2 {
+    const int R0 = s * H;
+#pragma unroll
+    for (int a = 0; a < H; ++a) g0[a] = ok ? Y[yi<MS>(R0 + a, gam)] : f2(0.f, 0.f);
+#pragma unroll
+    for (int a = 0; a < H / 2; ++a) {
+      float2 v = cadd(g0[2 * a], g0[2 * a + 1]);
+      v = cadd(v, shfl_xor2(v, 1));
+      const float w = ok ? __ldg(&wu1[(R0 / 2 + a) * (MS / 2) + (cgl >> 1)]) : 0.f;
+      g1[a] = cscale(v, 0.25f * w);
+    }
+    if constexpr (TT == 1) {
+      return g1[0];
+    } else {
+      float2 v = cadd(g1[0], g1[1]);
+      v = cadd(v, shfl_xor2(v, 2));
+      const float w = ok ? __ldg(&pyr[lvl_off(MS, 2) + (R0 / 4) * (MS / 4) + (cgl >> 2)]) : 0.f;
+      return cscale(v, 0.25f * w);
+    }
+  };
+
+  if (deep) {
+    // phase 1: level-TT values of every strip bin
+    for (int base = 0; base < NS; base += SPAR) {
+      const int s = base + s0;
+      const bool ok = s < NS;
+      float2 g0[H], g1[H / 2];
+      const float2 gT = strip(s, ok, g0, g1);
+      if (ok && (gam & (H - 1)) == 0) lvl[off(TT) + s * (SLAB >> TT) + (gam >> TT)] = gT;
+    }
+    __syncthreads();
+    // phase 2: restrictions inside the slab, levels TT+1 .. min(L-1, LLOC)
+    const int ltop = (L - 1) < LLOC ? (L - 1) : LLOC;
+    for (int l = TT; l < ltop; ++l) {
+      const int rows = MS >> (l + 1), cols = SLAB >> (l + 1), fc = SLAB >> l;
+      const float2* fine = lvl + off(l);
+      float2* coarse = lvl + off(l + 1);
+      const float* wu = pyr + lvl_off(MS, l + 1);
+      for (int i = tid; i < rows * cols; i += T) {
+        const int r = i / cols, c = i - (i / cols) * cols;
+        const float2 sm = cadd(cadd(fine[(2 * r) * fc + 2 * c], fine[(2 * r) * fc + 2 * c + 1]),
+                               cadd(fine[(2 * r + 1) * fc + 2 * c], fine[(2 * r + 1) * fc + 2 * c + 1]));
+        coarse[i] = cscale(sm, 0.25f * __ldg(&wu[r * (MS >> (l + 1)) + q * cols + c]));
+      }
+      __syncthreads();
+    }
+    if (L - 1 <= LLOC) {
+      // coarsest level inside the slab
+      const int l = L - 1, rows = MS >> l, cols = SLAB >> l;
+      float2* a = lvl + off(l);
+      const float* iw = pyr + lvl_off(MS, l) + (MS >> l) * (MS >> l);
+      for (int i = tid; i < rows * cols; i += T) {
+        const int r = i / cols, c = i - (i / cols) * cols;
+        a[i] = cscale(a[i], __ldg(&iw[r * (MS >> l) + q * cols + c]));
+      }
+      __syncthreads();
+    } else {
+      if constexpr (CL > 1) {
+        // levels LLOC .. L-1 span the cluster: block 0 gathers the CL x CL
+        // level-LLOC values (column qq from block qq), runs the coarse
+        // levels, and sends back level-LLOC increments.
+        window_sync<CL>();
+        if (q == 0 && tid == 0) {
+          float2* gl = lvl + off(LLOC + 1);  // global arrays of levels LLOC.. in block 0
+          auto goff = [](int i) {  // offset of level LLOC + i
+            int o = 0;
+            for (int l = LLOC; l < LLOC + i; ++l) o += (MS >> l) * (MS >> l);
+            return o;
+          };
+          for (int qq = 0; qq < CL; ++qq) {
+            const float2* src = peer<CL>(lvl, qq) + off(LLOC);
+            for (int i = 0; i < CL; ++i) gl[i * CL + qq] = src[i];
+          }
+          for (int l = LLOC; l < L - 1; ++l) {
+            const int n = MS >> (l + 1), nf = MS >> l;
+            const float2* fine = gl + goff(l - LLOC);
+            float2* coarse = gl + goff(l - LLOC + 1);
+            const float* wu = pyr + lvl_off(MS, l + 1);
+            for (int i = 0; i < n * n; ++i) {
+              const int r = i / n, c = i % n;
+              const float2 sm = cadd(cadd(fine[(2 * r) * nf + 2 * c], fine[(2 * r) * nf + 2 * c + 1]),
+                                     cadd(fine[(2 * r + 1) * nf + 2 * c], fine[(2 * r + 1) * nf + 2 * c + 1]));
+              coarse[i] = cscale(sm, 0.25f * wu[i]);
+            }
+          }
+          {
+            const int l = L - 1, n = MS >> l;
+            float2* a = gl + goff(l - LLOC);
+            const float* iw = pyr + lvl_off(MS, l) + n * n;
+            for (int i = 0; i < n * n; ++i) a[i] = cscale(a[i], iw[i]);
+          }
+          for (int l = L - 2; l >= LLOC; --l) {
+            const int n = MS >> l, nc = n >> 1;
+            float2* a = gl + goff(l - LLOC);
+            const float2* pe = gl + goff(l - LLOC + 1);
+            const float* iw = pyr + lvl_off(MS, l) + n * n;
+            const float* rr = iw + n * n;
+            for (int i = 0; i < n * n; ++i) {
+              const int r = i / n, c = i % n;
+              const float2 p = pe[(r >> 1) * nc + (c >> 1)];
+              const float2 v = cscale(a[i], iw[i]);
+              a[i] = f2(v.x + rr[i] * p.x, v.y + rr[i] * p.y);
+            }
+          }
+          for (int qq = 0; qq < CL; ++qq) {
+            float2* dst = peer<CL>(lvl, qq) + off(LLOC);
+            for (int i = 0; i < CL; ++i) dst[i] = gl[i * CL + qq];
+          }
+        }
+        window_sync<CL>();
+      }
+    }
+    // up-pass inside the slab down to level TT
+    const int lstart = ((L - 1) < LLOC ? (L - 1) : LLOC) - 1;
+    for (int l = lstart; l >= TT; --l) {
+      const int rows = MS >> l, cols = SLAB >> l, cc = cols >> 1;
+      float2* a = lvl + off(l);
+      const float2* pe = lvl + off(l + 1);
+      const float* iw = pyr + lvl_off(MS, l) + (MS >> l) * (MS >> l);
+      const float* rr = iw + (MS >> l) * (MS >> l);
+      for (int i = tid; i < rows * cols; i += T) {
+        const int r = i / cols, c = i - (i / cols) * cols;
+        const int o = r * (MS >> l) + q * cols + c;
+        const float2 p = pe[(r >> 1) * cc + (c >> 1)];
+        const float2 v = cscale(a[i], __ldg(&iw[o]));
+        const float w = __ldg(&rr[o]);
+        a[i] = f2(v.x + w * p.x, v.y + w * p.y);
+      }
+      __syncthreads();
+    }
+  }
+  // phase 3: per strip, the up-pass to level 0 and the increments w . Delta
+  const float* iwT = pyr + lvl_off(MS, TT) + (MS >> TT) * (MS >> TT);
+  for (int base = 0; base < NS; base += SPAR) {
+    const int s = base + s0;
+    const bool ok = s < NS;
+    float2 g0[H], g1[H / 2];
+    const float2 gT = strip(s, ok, g0, g1);
+    const int R0 = s * H;
+    float2 eT = f2(0.f, 0.f);
+    if (ok) {
+      eT = deep ? lvl[off(TT) + s * (SLAB >> TT) + (gam >> TT)]
+                : cscale(gT, __ldg(&iwT[(R0 >> TT) * (MS >> TT) + (cgl >> TT)]));
+    }
+    float2 e1[H / 2];
+    if constexpr (TT == 1) {
+      e1[0] = eT;
+    } else {
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const int o = (R0 / 2 + a) * (MS / 2) + (cgl >> 1);
+        const float2 v = cscale(g1[a], ok ? __ldg(&iw1[o]) : 0.f);
+        const float w = ok ? __ldg(&rr1[o]) : 0.f;
+        e1[a] = f2(v.x + w * eT.x, v.y + w * eT.y);
+      }
+    }
+    if (ok) {
+#pragma unroll
+      for (int a = 0; a < H; ++a) {
+        const int o = (R0 + a) * MS + cgl;
+        const float u = __ldg(&u0[o]);
+        out[o] = f2(g0[a].x + u * e1[a >> 1].x, g0[a].y + u * e1[a >> 1].y);
+      }
+    }
+  }
+}
+
+// One cluster of Geo<MS>::CL blocks per window (grid = windows * CL), each
+// with Geo<MS>::T threads and Geo<MS>::SMEM bytes of dynamic shared memory.
+template <int MS, int MODE>
+__global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel(StepArgs A) {
+  using Gm = Geo<MS>;
+  constexpr int E = Gm::E, G = Gm::G, CL = Gm::CL, SLAB = Gm::SLAB, T = Gm::T, M = Gm::M;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* X = reinterpret_cast<float2*>(smem_raw);  // row slab
+  float2* Y = X + Gm::XN;                            // column slab
+  float2* tws = Y + Gm::XN;
+  float2* lvl = tws + MS;
+  double* red = reinterpret_cast<double*>(lvl + Gm::LVL);  // block_sum scratch
+
+  const int tid = threadIdx.x;
+  int q = 0;
+  if constexpr (CL > 1) q = (int)cg::this_cluster().block_rank();
+  const int win = blockIdx.x / CL;
+  for (int i = tid; i < MS; i += T) tws[i] = A.tw[i];
+  const int k = A.idx[win];
+  if ((unsigned)k >= (unsigned)A.n_pos) {
+    if (tid == 0 && q == 0) {
+      atomicOr(A.err, 1);
+      if (MODE == kStep) A.corner[win] = make_int2(-(1 << 30), -(1 << 30));
+    }
+    return;  // uniform across the cluster
+  }
+  const int pr = A.pos[2 * k], pc = A.pos[2 * k + 1];
+  if (MODE == kStep && tid == 0 && q == 0) A.corner[win] = make_int2(pr, pc);
+  const float2* zk = A.z + (size_t)pr * A.n_cols + pc;
+  __syncthreads();
+
+  const bool act = tid < Gm::LANES;
+  const int lam = act ? tid / G : 0, g = tid % G;
+  const int line = q * SLAB + lam;  // column (passes A, C) or row (pass B) of this lane group
+
+  // slab geometry of the row-coalesced passes: lane gam of a row of the
+  // block's column slab, rows r0, r0 + RSTEP, ...
+  constexpr int RSTEP = T / SLAB, RPT = MS / RSTEP;
+  const int gam = tid % SLAB, r0 = tid / SLAB;
+  const int cgl = q * SLAB + gam;
+
+  // ---- pass A: exit wave psi = Q z_k gathered row by row into Y, then the
+  // column FFTs; results go to the row owners' X
+  {
+    float2 pv[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      const int r = r0 + RSTEP * i;
+      pv[i] = cmul(__ldg(&A.Q[r * MS + cgl]), __ldg(&zk[(size_t)r * A.n_cols + cgl]));
+    }
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) Y[yi<MS>(r0 + RSTEP * i, gam)] = pv[i];
+    __syncthreads();
+    float2 x[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = act ? Y[yi<MS>(g + G * e, lam)] : f2(0.f, 0.f);
+    __syncwarp();
+    line_fwd<MS, false>(x, g, act, [&](int sl) -> float2& { return Y[yi<MS>(sl, lam)]; }, tws);
+#pragma unroll
+    for (int j = 0; j < E / G; ++j)
+#pragma unroll
+      for (int k2 = 0; k2 < G; ++k2) {
+        const int kr = g + G * j + E * k2;
+        float2* dst = peer<CL>(X, (E * k2) / SLAB);
+        if (act) dst[xi<MS>(kr % SLAB, line)] = x[j * G + k2];
+      }
+  }
+  window_arrive<CL>();
+  // amplitudes of this block's rows, fetched while the other blocks finish
+  float av[E];
+  if constexpr (MODE != kSim) {
+    const float* ampr = A.amp + (size_t)k * M + line * MS;
+#pragma unroll
+    for (int j = 0; j < E / G; ++j)
+#pragma unroll
+      for (int k2 = 0; k2 < G; ++k2) av[j * G + k2] = act ? __ldg(&ampr[g + G * j + E * k2]) : 0.f;
+  }
+  window_wait<CL>();
+
+  // ---- pass B: row FFTs, modulus projection, inverse row FFTs; results go
+  // to the column owners' Y
+  float res = 0.f;
+  {
+    const int kr = line;
+    float2 x[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = act ? X[xi<MS>(lam, g + G * e)] : f2(0.f, 0.f);
+    __syncwarp();
+    line_fwd<MS, false>(x, g, act, [&](int sl) -> float2& { return X[xi<MS>(lam, sl)]; }, tws);
+    if constexpr (MODE == kSim) {
+      float* outk = A.out_int + (size_t)k * M + kr * MS;
+#pragma unroll
+      for (int j = 0; j < E / G; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < G; ++k2) {
+          const float2 P = x[j * G + k2];
+          if (act) outk[g + G * j + E * k2] = P.x * P.x + P.y * P.y;
+        }
+      return;  // no block reads another block's memory after the barrier above
+    } else {
+      constexpr float inv_m = 1.0f / float(M);
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const float a = av[i];
+        const float2 P = x[i];
+        const float p2 = P.x * P.x + P.y * P.y;
+        float mag;
+        float2 Pp;
+        if (p2 > 0.f) {
+          const float rs = rsqrtf(p2);
+          mag = p2 * rs;
+          const float sc = a * rs * inv_m;
+          Pp = f2(P.x * sc, P.y * sc);
+        } else {
+          mag = 0.f;
+          Pp = f2(a * inv_m, 0.f);
+        }
+        const float dlt = mag - a;
+        res += dlt * dlt;
+        x[i] = Pp;
+      }
+      line_inv<MS>(x, g, act, [&](int sl) -> float2& { return X[xi<MS>(lam, sl)]; }, tws);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int c = g + G * e;
+        float2* dst = peer<CL>(Y, (G * e) / SLAB);
+        if (act) dst[yi<MS>(kr, c % SLAB)] = x[e];
+      }
+    }
+  }
+  if constexpr (MODE != kSim) {
+    window_arrive<CL>();
+    // the exit wave again, row by row, while the other blocks finish pass B;
+    // it is parked in X (free once every block of the window is past pass B)
+    float2 pv[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      const int r = r0 + RSTEP * i;
+      pv[i] = cmul(__ldg(&A.Q[r * MS + cgl]), __ldg(&zk[(size_t)r * A.n_cols + cgl]));
+    }
+    window_wait<CL>();
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) X[yi<MS>(r0 + RSTEP * i, gam)] = pv[i];
+
+    // ---- pass C: inverse column FFTs; R_k into Y
+    {
+      float2 x[E];
+#pragma unroll
+      for (int j = 0; j < E / G; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < G; ++k2) x[j * G + k2] = act ? Y[yi<MS>(g + G * j + E * k2, lam)] : f2(0.f, 0.f);
+      __syncwarp();
+      line_inv<MS>(x, g, act, [&](int sl) -> float2& { return Y[yi<MS>(sl, lam)]; }, tws);
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (act) Y[yi<MS>(g + G * e, lam)] = x[e];
+    }
+    __syncthreads();
+
+    // ---- g^0 = conj(Q)(R_k - psi) over the slab, lane = column; into Y, or
+    // straight to the increments for one level
+    float gn2 = 0.f, amax = 0.f;
+    float2* out = A.contrib + (size_t)win * M;
+    const bool direct = (MODE == kStep) && A.levels == 1;
+    {
+      float2 qv[RPT];
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) qv[i] = __ldg(&A.Q[(r0 + RSTEP * i) * MS + cgl]);
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) {
+        const int r = r0 + RSTEP * i;
+        const int o = yi<MS>(r, gam);
+        const float2 rho = csub(Y[o], X[o]);
+        const float2 gg = cmul_cj(qv[i], rho);
+        gn2 += gg.x * gg.x + gg.y * gg.y;
+        if (MODE == kStep) {
+          if (A.pnum) {
+            // the probe step's window terms (same R_k and z_k)
+            const float2 zz = __ldg(&zk[(size_t)r * A.n_cols + cgl]);
+            const float a2 = zz.x * zz.x + zz.y * zz.y;
+            A.pnum[(size_t)win * M + r * MS + cgl] = cmul_cj(zz, rho);
+            A.pa2[(size_t)win * M + r * MS + cgl] = a2;
+            amax = fmaxf(amax, a2);
+          }
+          if (direct)
+            out[r * MS + cgl] = gg;
+          else
+            Y[o] = gg;
+        }
+      }
+    }
+    if (MODE == kStep && A.pnum) {
+      const double bm = block_max((double)amax, red, tid, T);
+      if (tid == 0) A.pmax[win * CL + q] = bm;
+    }
+
+    // block partials of the window's two sums (float64); the kernel that
+    // follows combines them in block order
+    const double rs = block_sum((double)res, red, tid, T);
+    const double gs = block_sum((double)gn2, red, tid, T);
+    if (tid == 0) {
+      A.part[(size_t)(win * CL + q) * 2] = rs;
+      A.part[(size_t)(win * CL + q) * 2 + 1] = gs;
+    }
+    if (MODE != kStep || direct) return;
+
+    // ---- pass D: MAGPS V-cycle (levels >= 2) on the column slab
+    if (A.levels == 2)
+      vcycle<MS, 1>(Y, lvl, A.pyr, A.levels, q, out, tid);
+    else
+      vcycle<MS, 2>(Y, lvl, A.pyr, A.levels, q, out, tid);
+  }
+}
+

@@ -19,6 +19,7 @@ ROOT = os.path.dirname(HERE)
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libmagpie.so")
 SOURCES = [os.path.join(HERE, "csrc", "magpie.cu")]
+DEPENDS = [os.path.join(HERE, "csrc", f) for f in ("fft_lines.cuh", "window_kernel.cuh")]
 HEADER = os.path.join(ROOT, "include", "magpie.h")
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared"]
@@ -40,7 +41,7 @@ class magpie_params(ctypes.Structure):
 
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile the library for sm_103a into the package's _build/ folder."""
-    newest = max(os.path.getmtime(p) for p in SOURCES + [HEADER])
+    newest = max(os.path.getmtime(p) for p in SOURCES + DEPENDS + [HEADER])
     if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
         return LIB_PATH
     os.makedirs(BUILD_DIR, exist_ok=True)
