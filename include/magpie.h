@@ -194,6 +194,28 @@ int magpie_forward_intensities(const void* object, int32_t n_rows, int32_t n_col
                                const void* probe, int32_t m, const int32_t* positions,
                                int32_t n_pos, float* out, void* stream);
 
+/*
+ * Context groups: several independent reconstructions advanced together.
+ * magpie_group_sweep is one sweep of every member, exactly as magpie_sweep
+ * on each of them (member results are bitwise those of separate sweeps), but
+ * batched: batched step t runs step t of every member that has one, all
+ * windows of equal m in one launch and all members' object updates in one
+ * more, replayed from one CUDA graph.  Members may differ in every size.
+ *   ctxs   : n contexts created on the current device, none with
+ *            update_probe = 1, each at most once; they must outlive the group
+ *            and not be used on another stream while a group sweep runs.
+ *   stream : cudaStream_t (as void*) on which group sweeps are ordered.
+ */
+typedef struct magpie_group magpie_group;
+int magpie_group_create(magpie_group** out, magpie_ctx* const* ctxs, int32_t n, void* stream);
+
+/* orders: HOST array of n DEVICE pointers, orders[i] an int32 permutation of
+   0 .. n_pos(i)-1; copied to the members before the sweep. */
+int magpie_group_sweep(magpie_group* group, const int32_t* const* orders);
+
+/* Release the group (not its members). */
+void magpie_group_destroy(magpie_group* group);
+
 /* Static name of an error code; never NULL. */
 const char* magpie_strerror(int code);
 

@@ -43,6 +43,7 @@
 #include <cstring>
 #include <string>
 #include <utility>
+#include <algorithm>
 #include <vector>
 
 #include "magpie.h"
@@ -68,28 +69,43 @@ constexpr int kMaxCluster = 8;       // largest number of blocks per window
 // window kernel's block partials into Phi_k and ||grad Phi_k||.
 // Dynamic smem: count int2 corners + count ints.
 constexpr int kApplyTile = 16;
-__global__ void __launch_bounds__(256) apply_kernel(float2* z, int n_rows, int n_cols, const int2* corners,
-                                                    const int32_t* idx, int count, int n_pos,
-                                                    const float2* contrib, const float* w0, int MS,
-                                                    const double* part, int CL, double* phi_pos, double* gn_pos) {
+struct ApplyArgs {
+  float2* z;               // object [n_rows][n_cols]
+  int n_rows, n_cols;
+  const int2* corners;     // [count] window corners from the window kernel
+  const int32_t* idx;      // [count] window indices
+  int count, n_pos;
+  const float2* contrib;   // [count][MS][MS] increments w . Delta
+  const float* w0;         // [MS][MS] u + |Q|^2
+  int MS;
+  const double* part;      // [count][CL][2] block partials of the window kernel
+  int CL;
+  double* phi_pos;         // per-window Phi_k
+  double* gn_pos;          // per-window ||grad Phi_k||
+  int tiles_x;             // tiles per object row
+  int block0;              // batched launches: first block of this problem
+};
+
+__device__ __forceinline__ void apply_body(const ApplyArgs& P, const int tx, const int ty) {
   extern __shared__ int2 corner[];
+  const int count = P.count, MS = P.MS;
   int* list = reinterpret_cast<int*>(corner + count);
   __shared__ int warp_hits[8], n_list;
-  if (blockIdx.x == 0 && blockIdx.y == 0) {
+  if (tx == 0 && ty == 0) {
     // the window kernel's block partials -> Phi_k and ||grad Phi_k||, in block order
     for (int b = threadIdx.x; b < count; b += blockDim.x) {
-      const int k = idx[b];
-      if ((unsigned)k >= (unsigned)n_pos) continue;
+      const int k = P.idx[b];
+      if ((unsigned)k >= (unsigned)P.n_pos) continue;
       double a = 0.0, g = 0.0;
-      for (int q = 0; q < CL; ++q) {
-        a += part[(size_t)(b * CL + q) * 2];
-        g += part[(size_t)(b * CL + q) * 2 + 1];
+      for (int q = 0; q < P.CL; ++q) {
+        a += P.part[(size_t)(b * P.CL + q) * 2];
+        g += P.part[(size_t)(b * P.CL + q) * 2 + 1];
       }
-      phi_pos[k] = a / (2.0 * (double)MS * (double)MS);
-      gn_pos[k] = sqrt(g);
+      P.phi_pos[k] = a / (2.0 * (double)MS * (double)MS);
+      P.gn_pos[k] = sqrt(g);
     }
   }
-  const int R0 = blockIdx.y * kApplyTile, C0 = blockIdx.x * kApplyTile;
+  const int R0 = ty * kApplyTile, C0 = tx * kApplyTile;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   // windows meeting this tile, listed in minibatch order: every warp takes
   // 32 consecutive windows per round, ballots, and the rounds are stitched
@@ -99,7 +115,7 @@ __global__ void __launch_bounds__(256) apply_kernel(float2* z, int n_rows, int n
     const int b = b0 + threadIdx.x;
     bool hit = false;
     if (b < count) {
-      const int2 q = corners[b];
+      const int2 q = P.corners[b];
       corner[b] = q;
       hit = q.x < R0 + kApplyTile && q.x + MS > R0 && q.y < C0 + kApplyTile && q.y + MS > C0;
     }
@@ -118,7 +134,7 @@ __global__ void __launch_bounds__(256) apply_kernel(float2* z, int n_rows, int n
   __syncthreads();
   const int nl = n_list;
   const int r = R0 + (threadIdx.x >> 4), c = C0 + (threadIdx.x & 15);
-  if (r >= n_rows || c >= n_cols) return;
+  if (r >= P.n_rows || c >= P.n_cols) return;
   const size_t M = (size_t)MS * MS;
   float nx = 0.f, ny = 0.f, d = 0.f;
   for (int j0 = 0; j0 < nl; j0 += 4) {
@@ -132,8 +148,8 @@ __global__ void __launch_bounds__(256) apply_kernel(float2* z, int n_rows, int n
       const int dr = r - q.x, dc = c - q.y;
       const bool in = j < nl && (unsigned)dr < (unsigned)MS && (unsigned)dc < (unsigned)MS;
       const int o = in ? dr * MS + dc : 0;
-      v[u] = in ? contrib[(size_t)b * M + o] : make_float2(0.f, 0.f);
-      wv[u] = in ? __ldg(&w0[o]) : 0.f;
+      v[u] = in ? P.contrib[(size_t)b * M + o] : make_float2(0.f, 0.f);
+      wv[u] = in ? __ldg(&P.w0[o]) : 0.f;
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -143,12 +159,31 @@ __global__ void __launch_bounds__(256) apply_kernel(float2* z, int n_rows, int n
     }
   }
   if (d > 0.f) {
-    const size_t p = (size_t)r * n_cols + c;
-    float2 zz = z[p];
+    const size_t p = (size_t)r * P.n_cols + c;
+    float2 zz = P.z[p];
     zz.x += nx / d;
     zz.y += ny / d;
-    z[p] = zz;
+    P.z[p] = zz;
   }
+}
+
+// One problem: a 2-D grid of tiles.
+__global__ void __launch_bounds__(256) apply_kernel(ApplyArgs P) { apply_body(P, blockIdx.x, blockIdx.y); }
+
+// Several problems in one launch (1-D grid): problem i owns blocks
+// table[i].block0 .. table[i + 1].block0 - 1.
+__global__ void __launch_bounds__(256) apply_kernel_batched(const ApplyArgs* __restrict__ table, int n) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {  // last problem whose first block is <= blockIdx.x
+    const int mid = (lo + hi + 1) >> 1;
+    if (table[mid].block0 <= (int)blockIdx.x)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const ApplyArgs& P = table[lo];
+  const int t = (int)blockIdx.x - P.block0;
+  apply_body(P, t % P.tiles_x, t / P.tiles_x);
 }
 
 __global__ void sqrt_kernel(const float* d, float* a, size_t n) {
@@ -447,12 +482,38 @@ cudaError_t enqueue_pyramid(const float2* Q, int MS, int L, float alpha, unsigne
   return cudaGetLastError();
 }
 
+ApplyArgs apply_args(float2* z, int n_rows, int n_cols, const int2* corners, const int32_t* idx, int count, int n_pos,
+                     const float2* contrib, const float* w0, int MS, const double* part, double* phi_pos,
+                     double* gn_pos) {
+  ApplyArgs P{};
+  P.z = z;
+  P.n_rows = n_rows;
+  P.n_cols = n_cols;
+  P.corners = corners;
+  P.idx = idx;
+  P.count = count;
+  P.n_pos = n_pos;
+  P.contrib = contrib;
+  P.w0 = w0;
+  P.MS = MS;
+  P.part = part;
+  P.CL = cluster_of(MS);
+  P.phi_pos = phi_pos;
+  P.gn_pos = gn_pos;
+  P.tiles_x = (n_cols + kApplyTile - 1) / kApplyTile;
+  P.block0 = 0;
+  return P;
+}
+
+int apply_tiles(const ApplyArgs& P) { return P.tiles_x * ((P.n_rows + kApplyTile - 1) / kApplyTile); }
+
 cudaError_t launch_apply(float2* z, int n_rows, int n_cols, const int2* corners, const int32_t* idx, int count,
                          int n_pos, const float2* contrib, const float* w0, int MS, const double* part,
                          double* phi_pos, double* gn_pos, cudaStream_t st) {
-  const dim3 tiles((n_cols + kApplyTile - 1) / kApplyTile, (n_rows + kApplyTile - 1) / kApplyTile);
-  return launch_ex(apply_kernel, tiles, dim3(256), (sizeof(int2) + sizeof(int)) * count, st, 1, z, n_rows, n_cols,
-                   corners, idx, count, n_pos, contrib, w0, MS, part, cluster_of(MS), phi_pos, gn_pos);
+  const ApplyArgs P = apply_args(z, n_rows, n_cols, corners, idx, count, n_pos, contrib, w0, MS, part, phi_pos, gn_pos);
+  const dim3 tiles(P.tiles_x, (n_rows + kApplyTile - 1) / kApplyTile);
+  apply_kernel<<<tiles, 256, (sizeof(int2) + sizeof(int)) * count, st>>>(P);
+  return cudaGetLastError();
 }
 
 template <int MODE>
@@ -468,12 +529,34 @@ cudaError_t launch_window_m(int MS, const StepArgs& a, int blocks, cudaStream_t 
   }
 }
 
+template <int MS, int MODE>
+cudaError_t launch_window_batched(const StepArgs* table, const int2* map, int windows, cudaStream_t st) {
+  using Gm = Geo<MS>;
+  return launch_ex(window_kernel_batched<MS, MODE>, dim3((unsigned)windows * Gm::CL), dim3(Gm::T), Gm::SMEM, st,
+                   Gm::CL, table, map);
+}
+
+template <int MODE>
+cudaError_t launch_window_batched_m(int MS, const StepArgs* table, const int2* map, int windows, cudaStream_t st) {
+  switch (MS) {
+    case 8: return launch_window_batched<8, MODE>(table, map, windows, st);
+    case 16: return launch_window_batched<16, MODE>(table, map, windows, st);
+    case 32: return launch_window_batched<32, MODE>(table, map, windows, st);
+    case 64: return launch_window_batched<64, MODE>(table, map, windows, st);
+    case 128: return launch_window_batched<128, MODE>(table, map, windows, st);
+    case 256: return launch_window_batched<256, MODE>(table, map, windows, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 // Opt the window kernels of one size into their dynamic shared memory; done
 // before any launch (and so outside stream capture).
 template <int MS>
 cudaError_t prepare_size() {
   const int bytes = (int)Geo<MS>::SMEM;
   cudaError_t e = cudaFuncSetAttribute(window_kernel<MS, kStep>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(window_kernel_batched<MS, kStep>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(window_kernel<MS, kEval>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
@@ -484,6 +567,9 @@ cudaError_t prepare_size() {
 cudaError_t prepare_kernels(int MS) {
   cudaError_t e = cudaFuncSetAttribute(apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)((sizeof(int2) + sizeof(int)) * kMaxMinibatch));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(apply_kernel_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((sizeof(int2) + sizeof(int)) * kMaxMinibatch));
   if (e != cudaSuccess) return e;
   switch (MS) {
     case 8: return prepare_size<8>();
@@ -506,7 +592,32 @@ int check_positions(const int32_t* host_pos, int n_pos, int n_rows, int n_cols, 
   return MAGPIE_OK;
 }
 
+// ------------------------------------------------------------- context groups
+struct GroupWindowLaunch {
+  int ms;       // window side of this launch
+  int map_off;  // first entry of its cluster map
+  int windows;  // windows (clusters) in the launch
+};
+struct GroupApplyLaunch {
+  int tab_off;    // first entry of its problem table
+  int n;          // problems in the launch
+  int blocks;     // total tiles
+  int max_count;  // largest window count (shared memory)
+};
+
 }  // namespace
+
+struct magpie_group {
+  std::vector<magpie_ctx*> members;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  StepArgs* table = nullptr;    // one entry per (batched step, member)
+  int2* map = nullptr;          // cluster -> (table entry, window slot)
+  ApplyArgs* atable = nullptr;  // one entry per (batched step, member)
+  std::vector<std::vector<GroupWindowLaunch>> wl;  // per batched step
+  std::vector<GroupApplyLaunch> al;                // per batched step
+  cudaGraphExec_t graph = nullptr;
+};
 
 struct magpie_ctx {
   magpie_params p{};
@@ -1094,6 +1205,127 @@ int magpie_step_noalloc(void* object, int32_t n_rows, int32_t n_cols, const void
   CUDA_TRY(cudaMemcpyAsync(&h, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
   if (h) return fail(MAGPIE_EINDEX, "a window index or its position was out of range; that window was skipped");
+  return MAGPIE_OK;
+}
+
+
+void magpie_group_destroy(magpie_group* g) {
+  if (!g) return;
+  if (g->graph) cudaGraphExecDestroy(g->graph);
+  if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+  if (g->table) cudaFree(g->table);
+  if (g->map) cudaFree(g->map);
+  if (g->atable) cudaFree(g->atable);
+  delete g;
+}
+
+int magpie_group_create(magpie_group** out, magpie_ctx* const* ctxs, int32_t n, void* stream) {
+  if (!out || !ctxs || n < 1) return fail(MAGPIE_EINVAL, "need an output pointer and at least one context");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return fail(MAGPIE_EINVAL, "context " + std::to_string(i) + " is NULL");
+    if (ctxs[i]->p.update_probe) return fail(MAGPIE_EINVAL, "contexts with update_probe = 1 cannot be grouped");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return fail(MAGPIE_EINVAL, "a context appears twice in the group");
+  }
+  magpie_group* g = new magpie_group();
+  g->members.assign(ctxs, ctxs + n);
+  g->stream = (cudaStream_t)stream;
+  std::vector<StepArgs> table;
+  std::vector<int2> map;
+  std::vector<ApplyArgs> atable;
+  int steps = 0;
+  for (auto* c : g->members) steps = std::max(steps, n_steps(c));
+  for (int t = 0; t < steps; ++t) {
+    std::vector<int> entry(n, -1);
+    for (int i = 0; i < n; ++i) {
+      magpie_ctx* c = g->members[i];
+      if (t >= n_steps(c)) continue;
+      entry[i] = (int)table.size();
+      table.push_back(make_args(c, c->order + (size_t)t * c->p.minibatch));
+    }
+    std::vector<GroupWindowLaunch> wls;
+    for (int ms : {8, 16, 32, 64, 128, 256}) {
+      GroupWindowLaunch L{ms, (int)map.size(), 0};
+      for (int i = 0; i < n; ++i) {
+        magpie_ctx* c = g->members[i];
+        if (entry[i] < 0 || c->p.m != ms) continue;
+        const int cnt = std::min(c->p.minibatch, c->p.n_pos - t * c->p.minibatch);
+        for (int w = 0; w < cnt; ++w) map.push_back(make_int2(entry[i], w));
+        L.windows += cnt;
+      }
+      if (L.windows) wls.push_back(L);
+    }
+    g->wl.push_back(wls);
+    GroupApplyLaunch A{(int)atable.size(), 0, 0, 0};
+    for (int i = 0; i < n; ++i) {
+      magpie_ctx* c = g->members[i];
+      if (entry[i] < 0) continue;
+      const int cnt = std::min(c->p.minibatch, c->p.n_pos - t * c->p.minibatch);
+      ApplyArgs P = apply_args(c->z, c->p.n_rows, c->p.n_cols, c->corner, c->order + (size_t)t * c->p.minibatch, cnt,
+                               c->p.n_pos, c->contrib, c->pyr + c->M, c->p.m, c->part, c->phi_pos, c->gn_pos);
+      P.block0 = A.blocks;
+      A.blocks += apply_tiles(P);
+      A.max_count = std::max(A.max_count, cnt);
+      ++A.n;
+      atable.push_back(P);
+    }
+    g->al.push_back(A);
+  }
+  auto upload = [&](void** dst, const void* src, size_t bytes) -> int {
+    cudaError_t e = cudaMalloc(dst, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      magpie_group_destroy(g);
+      return fail(e == cudaErrorMemoryAllocation ? MAGPIE_ENOMEM : MAGPIE_ECUDA,
+                  std::string("group tables: ") + cudaGetErrorString(e));
+    }
+    return MAGPIE_OK;
+  };
+  int rc;
+  if ((rc = upload((void**)&g->table, table.data(), sizeof(StepArgs) * table.size())) ||
+      (rc = upload((void**)&g->map, map.data(), sizeof(int2) * map.size())) ||
+      (rc = upload((void**)&g->atable, atable.data(), sizeof(ApplyArgs) * atable.size())))
+    return rc;
+  cudaError_t e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    magpie_group_destroy(g);
+    return fail(MAGPIE_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+  }
+  *out = g;
+  return MAGPIE_OK;
+}
+
+int magpie_group_sweep(magpie_group* g, const int32_t* const* orders) {
+  if (!g || !orders) return fail(MAGPIE_EINVAL, "NULL argument");
+  for (size_t i = 0; i < g->members.size(); ++i)
+    if (!orders[i]) return fail(MAGPIE_EINVAL, "order " + std::to_string(i) + " is NULL");
+  if (!g->graph) {
+    cudaGraph_t gr = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (size_t t = 0; t < g->wl.size() && e == cudaSuccess; ++t) {
+      for (const auto& L : g->wl[t]) {
+        e = launch_window_batched_m<kStep>(L.ms, g->table, g->map + L.map_off, L.windows, g->cap_stream);
+        if (e != cudaSuccess) break;
+      }
+      if (e != cudaSuccess) break;
+      const GroupApplyLaunch& A = g->al[t];
+      apply_kernel_batched<<<A.blocks, 256, (sizeof(int2) + sizeof(int)) * A.max_count, g->cap_stream>>>(
+          g->atable + A.tab_off, A.n);
+      e = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &gr);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g->graph, gr, 0);
+    if (gr) cudaGraphDestroy(gr);
+    CUDA_TRY(e);
+  }
+  for (size_t i = 0; i < g->members.size(); ++i) {
+    magpie_ctx* c = g->members[i];
+    CUDA_TRY(cudaMemcpyAsync(c->order, orders[i], sizeof(int32_t) * c->p.n_pos, cudaMemcpyDeviceToDevice, g->stream));
+  }
+  CUDA_TRY(cudaGraphLaunch(g->graph, g->stream));
   return MAGPIE_OK;
 }
 

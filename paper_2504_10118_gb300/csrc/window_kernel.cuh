@@ -259,10 +259,11 @@ __device__ __forceinline__ void vcycle(const float2* Y, float2* lvl, const float
   }
 }
 
-// One cluster of Geo<MS>::CL blocks per window (grid = windows * CL), each
-// with Geo<MS>::T threads and Geo<MS>::SMEM bytes of dynamic shared memory.
+// The work of one window slot `win` of a launch: one cluster of Geo<MS>::CL
+// blocks, each with Geo<MS>::T threads and Geo<MS>::SMEM bytes of dynamic
+// shared memory.
 template <int MS, int MODE>
-__global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel(StepArgs A) {
+__device__ __forceinline__ void window_body(const StepArgs& A, const int win) {
   using Gm = Geo<MS>;
   constexpr int E = Gm::E, G = Gm::G, CL = Gm::CL, SLAB = Gm::SLAB, T = Gm::T, M = Gm::M;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -275,7 +276,6 @@ __global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel
   const int tid = threadIdx.x;
   int q = 0;
   if constexpr (CL > 1) q = (int)cg::this_cluster().block_rank();
-  const int win = blockIdx.x / CL;
   for (int i = tid; i < MS; i += T) tws[i] = A.tw[i];
   const int k = A.idx[win];
   if ((unsigned)k >= (unsigned)A.n_pos) {
@@ -473,3 +473,17 @@ __global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel
   }
 }
 
+// One problem: window slot = cluster index (grid = windows * CL).
+template <int MS, int MODE>
+__global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel(StepArgs A) {
+  window_body<MS, MODE>(A, blockIdx.x / Geo<MS>::CL);
+}
+
+// Several problems in one launch: cluster c works on window slot map[c].y of
+// the problem whose arguments are table[map[c].x].
+template <int MS, int MODE>
+__global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS)
+    window_kernel_batched(const StepArgs* __restrict__ table, const int2* __restrict__ map) {
+  const int2 e = map[blockIdx.x / Geo<MS>::CL];
+  window_body<MS, MODE>(table[e.x], e.y);
+}

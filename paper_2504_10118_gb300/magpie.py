@@ -82,6 +82,9 @@ def lib() -> ctypes.CDLL:
             "magpie_forward_intensities": (ctypes.c_int, [vp, i32, i32, vp, i32, vp, i32, vp, vp]),
             "magpie_step_noalloc": (ctypes.c_int, [vp, i32, i32, vp, i32, vp, i32, vp, vp, i32, i32,
                                                     ctypes.c_float, vp, vp, vp]),
+            "magpie_group_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(vp), i32, vp]),
+            "magpie_group_sweep": (ctypes.c_int, [vp, ctypes.POINTER(vp)]),
+            "magpie_group_destroy": (None, [vp]),
             "magpie_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             "magpie_last_error": (ctypes.c_char_p, []),
             "magpie_version": (ctypes.c_int, []),
@@ -239,6 +242,45 @@ def magpie_step_noalloc(obj, probe, positions, amplitudes, idx, levels: int, alp
                                      _dev(idx, torch.int32, idx.numel(), "idx"), idx.numel(), int(levels),
                                      float(alpha), _dev(phi, torch.float64, N, "phi"),
                                      _dev(gnorm, torch.float64, N, "gnorm"), _stream()))
+
+
+class Group:
+    """Owns a magpie_group; keeps its member contexts alive."""
+
+    def __init__(self, ctxs):
+        self.members = list(ctxs)
+        arr = (ctypes.c_void_p * len(self.members))(*[c.handle for c in self.members])
+        h = ctypes.c_void_p()
+        _check(lib().magpie_group_create(ctypes.byref(h), arr, len(self.members), _stream()))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().magpie_group_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def magpie_group_create(ctxs) -> Group:
+    return Group(ctxs)
+
+
+def magpie_group_sweep(group: Group, orders) -> None:
+    ptrs = []
+    for c, o in zip(group.members, orders):
+        ptrs.append(_dev(o, torch.int32, c.params.n_pos, "order"))
+    arr = (ctypes.c_void_p * len(ptrs))(*ptrs)
+    group._orders = list(orders)  # alive until the next call
+    _check(lib().magpie_group_sweep(group.handle, arr))
+
+
+def magpie_group_destroy(group: Group) -> None:
+    group.close()
 
 
 def magpie_strerror(code: int) -> str:

@@ -63,6 +63,27 @@ WORKLOADS = {
 }
 
 
+def make_batch(count: int = 48, seed: int = 5, levels: int = 3, minibatch: int = 64,
+               sides=(256, 384, 512, 768, 1024), probes=(64, 128, 256)) -> list:
+    """Independent problems of uneven sizes (the batched workload): object side
+    from `sides`, probe side from `probes` with m <= n/2, a g x g raster with
+    g uniform in [10, 40] (100 to 1600 windows), step s = (n - m - 2j)/(g - 1)
+    and jitter j = max(1, s/8) (integer parts), photons 10^U[5, 7]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.choice(sides))
+        m = int(rng.choice([p for p in probes if p <= n // 2]))
+        g = int(rng.integers(10, 41))
+        s = (n - m - 2) // (g - 1)
+        j = max(1, s // 8)
+        s = (n - m - 2 * j) // (g - 1)
+        photons = float(10.0 ** rng.uniform(5.0, 7.0))
+        out.append(Workload(f"batch{i}-n{n}-m{m}-N{g * g}", n, m, g, s, j, min(levels, int(math.log2(m)) + 1),
+                            min(minibatch, g * g), 0.1, photons, 1))
+    return out
+
+
 def make_object(n: int, seed: int = 1) -> np.ndarray:
     """Complex128 n x n test object."""
     rng = np.random.default_rng(seed)
@@ -121,7 +142,13 @@ def make_order(n_pos: int, sweep: int) -> np.ndarray:
 
 def make_problem(w: Workload):
     """(object z*, probe Q, positions) of a workload, complex128/int32."""
-    z_true = make_object(w.n)
+    return make_problem_seeded(w, 1)
+
+
+def make_problem_seeded(w: Workload, seed: int):
+    """make_problem with the object drawn from `seed` and the raster jitter
+    from `seed + 2` (seed 1 gives make_problem's data)."""
+    z_true = make_object(w.n, seed=seed)
     probe = make_probe(w.m)
-    pos = make_raster(w.n, w.m, w.grid, w.step, w.jitter)
+    pos = make_raster(w.n, w.m, w.grid, w.step, w.jitter, seed=seed + 2)
     return z_true, probe, pos

@@ -30,7 +30,8 @@ def declared_functions():
 def test_header_declares_the_abi():
     names = declared_functions()
     for n in ["magpie_create", "magpie_destroy", "magpie_step", "magpie_sweep", "magpie_objective",
-              "magpie_stop_metric", "magpie_set_probe", "magpie_forward_intensities", "magpie_sweep_host"]:
+              "magpie_stop_metric", "magpie_set_probe", "magpie_get_probe", "magpie_forward_intensities",
+              "magpie_sweep_host", "magpie_group_create", "magpie_group_sweep", "magpie_group_destroy"]:
         assert n in names
 
 
@@ -112,4 +113,7 @@ def test_null_arguments(L):
     assert L.magpie_stop_metric(None, ctypes.byref(v)) == magpie.EINVAL
     rc = L.magpie_create(None, None, None, None, None, None, None)
     assert rc == magpie.EINVAL
+    assert L.magpie_group_create(None, None, 0, None) == magpie.EINVAL
+    assert L.magpie_group_sweep(None, None) == magpie.EINVAL
+    L.magpie_group_destroy(None)
     L.magpie_destroy(None)

@@ -1,0 +1,108 @@
+"""Context groups (several reconstructions in batched launches) on the GPU.
+
+A group sweep must give every member exactly what a separate sweep of that
+member gives (same kernels, same order of arithmetic: bitwise), and so the
+oracle's result within the per-sweep tolerance."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import magpie_oracle as O
+from paper_2504_10118_gb300 import magpie, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    magpie.build()
+    magpie.lib()
+
+
+def f32(a):
+    return np.asarray(a).astype(np.complex64).astype(np.complex128)
+
+
+# (n, m, grid, step, jitter, levels, minibatch): different sizes, window
+# sides, counts, minibatches and level counts; two share m = 32
+SPECS = [(64, 16, 6, 8, 1, 3, 8), (128, 32, 5, 20, 2, 2, 7), (96, 32, 4, 20, 2, 4, 16),
+         (192, 64, 4, 40, 3, 1, 5), (256, 128, 3, 60, 2, 3, 4)]
+
+
+class Member:
+    def __init__(self, spec, seed):
+        n, m, g, s, j, L, B = spec
+        self.n, self.m, self.L, self.B = n, m, L, B
+        self.z_true = f32(synth.make_object(n, seed=seed))
+        self.Q = f32(synth.make_probe(m))
+        self.pos = synth.make_raster(n, m, g, s, j, seed=seed)
+        self.N = len(self.pos)
+        self.d = synth.poisson_noise(O.forward_intensities(self.z_true, self.Q, self.pos), 1e6,
+                                     seed=seed).astype(np.float32).astype(np.float64)
+        rng = np.random.default_rng(seed)
+        self.z0 = f32(self.z_true + 0.2 * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))))
+
+    def ctx(self):
+        dev = torch.device("cuda")
+        self.zt = torch.from_numpy(self.z0.astype(np.complex64)).to(dev)
+        p = magpie.magpie_params_of(self.n, self.n, self.m, self.N, self.L, self.B, 0.1)
+        return magpie.magpie_create(p, self.zt, torch.from_numpy(self.Q.astype(np.complex64)).to(dev),
+                                    torch.from_numpy(self.pos).to(dev),
+                                    torch.from_numpy(self.d.astype(np.float32)).to(dev))
+
+
+def orders(members, sweep):
+    return [torch.from_numpy(synth.make_order(mb.N, 10 * sweep + i)).cuda() for i, mb in enumerate(members)]
+
+
+def test_group_sweeps_equal_separate_sweeps_and_the_oracle():
+    members = [Member(s, 11 + i) for i, s in enumerate(SPECS)]
+    grouped = [mb.ctx() for mb in members]
+    z_grouped = [mb.zt for mb in members]
+    group = magpie.magpie_group_create(grouped)
+    separate = [mb.ctx() for mb in members]
+    z_separate = [mb.zt for mb in members]
+    for sweep in range(2):
+        ords = orders(members, sweep)
+        magpie.magpie_group_sweep(group, ords)
+        for c, o in zip(separate, ords):
+            magpie.magpie_sweep(c, o)
+    torch.cuda.synchronize()
+    for i, mb in enumerate(members):
+        assert torch.equal(z_grouped[i], z_separate[i]), i
+        a = magpie.magpie_window_values(grouped[i])
+        b = magpie.magpie_window_values(separate[i])
+        assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    # against the oracle, two sweeps from the true object plus noise
+    u = None
+    for i, mb in enumerate(members):
+        z = mb.z0
+        uu = O.rpie_regulariser(mb.Q, 0.1)
+        for sweep in range(2):
+            z = O.sweep(z, mb.Q, mb.pos, mb.d, uu, mb.L, synth.make_order(mb.N, 10 * sweep + i), mb.B)
+        got = z_grouped[i].cpu().numpy().astype(np.complex128)
+        assert np.linalg.norm(got - z) / np.linalg.norm(z) < 1e-5, i
+    group.close()
+    for c in grouped + separate:
+        c.close()
+
+
+def test_group_arguments():
+    members = [Member(SPECS[0], 3), Member(SPECS[1], 4)]
+    a, b = members[0].ctx(), members[1].ctx()
+    with pytest.raises(magpie.MagpieError) as ei:
+        magpie.magpie_group_create([a, b, a])
+    assert ei.value.code == magpie.EINVAL
+    mb = members[0]
+    dev = torch.device("cuda")
+    p = magpie.magpie_params_of(mb.n, mb.n, mb.m, mb.N, mb.L, mb.B, 0.1, 1, 0.1)
+    zp = torch.from_numpy(mb.z0.astype(np.complex64)).to(dev)
+    c = magpie.magpie_create(p, zp, torch.from_numpy(mb.Q.astype(np.complex64)).to(dev),
+                             torch.from_numpy(mb.pos).to(dev), torch.from_numpy(mb.d.astype(np.float32)).to(dev))
+    with pytest.raises(magpie.MagpieError) as ei:
+        magpie.magpie_group_create([a, c])
+    assert ei.value.code == magpie.EINVAL
+    for x in (a, b, c):
+        x.close()
