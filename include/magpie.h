@@ -216,6 +216,108 @@ int magpie_group_sweep(magpie_group* group, const int32_t* const* orders);
 /* Release the group (not its members). */
 void magpie_group_destroy(magpie_group* group);
 
+/*
+ * Learned coarse-level correction.  The paper has no network: its Algorithm
+ * MAGPS ends the recursion on the coarsest grid (side h = m / 2^(levels-1))
+ * with one proximal step e_plain = g_H / w_H, g_H = conj(Q_H)(R_H - Q_H z_H)
+ * the coarse residual gradient and w_H = u_H + |Q_H|^2.  A context with a
+ * network attached lets the network propose that correction instead:
+ *   input  x [h][h][4] = (Re z_H, Im z_H, Re e_plain / s, Im e_plain / s),
+ *          z_H = the coarse object of the restriction chain
+ *          z^{l+1} = I_h^H(W_z^l . z^l) (Eq. def_weights), s = RMS of e_plain
+ *          over the window;
+ *   output y [h][h][2]; proposal e_nn = e_plain + s (y_re + i y_im).
+ * Each window keeps the V-cycle output built on e_nn only when its quadratic
+ * surrogate 1/2 ||Q . x - R_k(z_k)||^2 (Eq. quadratic_surrogate) is no larger
+ * there than at the output built on e_plain; otherwise the plain output is
+ * used.  Everything else in the step is unchanged.
+ *
+ * The network: six 3x3 convolutions with zero padding (channels 4-32-64-128-
+ * 512-64-2; strides 1,2,2,2,1,1; nearest upsampling of the input by 1,1,1,1,
+ * 2,4; ReLU after the first five), BF16 weights and activations, FP32
+ * accumulation and biases; 980,002 parameters, stored as FP32 in layer order,
+ * each layer as weights [c_out][3][3][c_in] then biases [c_out].  All data
+ * are NHWC float32 on the DEVICE.
+ */
+typedef struct magpie_cnn magpie_cnn;
+
+/* Number of parameters (980,002). */
+int32_t magpie_cnn_param_count(void);
+
+/* A network for coarsest side h (8, 16, 32 or 64) and batches of at most
+   max_batch windows; parameters start at zero.  Calls on it are ordered on
+   `stream`. */
+int magpie_cnn_create(magpie_cnn** out, int32_t h, int32_t max_batch, void* stream);
+void magpie_cnn_destroy(magpie_cnn* cnn);
+
+/* Copy in (DEVICE float32 [param_count]) the parameters; resets the Adam
+   moments and step count.  magpie_cnn_get_params copies them out. */
+int magpie_cnn_set_params(magpie_cnn* cnn, const float* theta);
+int magpie_cnn_get_params(magpie_cnn* cnn, float* theta);
+
+/* y [batch][h][h][2] = network(x [batch][h][h][4]); keeps the activations for
+   magpie_cnn_backward. */
+int magpie_cnn_forward(magpie_cnn* cnn, const float* x, int32_t batch, float* y);
+
+/* grad [param_count] = d<dy, y>/d theta for the inputs of the last forward
+   pass (the BF16 roundings passed straight through). */
+int magpie_cnn_backward(magpie_cnn* cnn, const float* dy, float* grad);
+
+/*
+ * One training step on `batch` trajectories: forward, loss
+ * L = 1/2 mean((y - t)^2) with target t = (zh - z_H^0) / s - e_plain / s
+ * (x0 = the trajectory's first network input, zh [batch][h][h][2] = its coarse
+ * object T V-cycles later, scale [batch] = s), backward, and one Adam step
+ * (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) at learning rate lr.
+ * loss: DEVICE float64, written when the step runs (no synchronisation).
+ */
+int magpie_cnn_train_step(magpie_cnn* cnn, const float* x0, const float* zh, const float* scale, int32_t batch,
+                          float lr, double* loss);
+
+/* The network input x [count][h][h][4] and s [count] of windows idx[count]
+   (count <= minibatch) at the current object; needs levels >= 2, m <= 128 and
+   update_probe = 0.  Synchronous (index errors are reported here). */
+int magpie_coarse_state(magpie_ctx* ctx, const int32_t* idx, int32_t count, float* x, float* scale);
+
+/* patches [count][m][m] complex = the object's windows idx[count] (zeros for
+   an index out of range). */
+int magpie_gather_windows(magpie_ctx* ctx, const int32_t* idx, int32_t count, void* patches);
+
+/* Attach a network (NULL detaches): later steps and sweeps of ctx use the
+   learned coarse correction.  The network must have h = m / 2^(levels-1) and
+   max_batch >= minibatch, must outlive the attachment, and its parameters may
+   change between sweeps.  One network serves contexts on one stream. */
+int magpie_attach_cnn(magpie_ctx* ctx, magpie_cnn* cnn);
+
+/* Running totals since the first attachment: windows whose proposal was
+   evaluated, and windows that kept it.  Synchronous. */
+int magpie_learned_stats(magpie_ctx* ctx, int64_t* proposed, int64_t* accepted);
+
+/* For window slots 0..count-1 of the most recent learned step: 1 if the
+   learned output was kept, and surrogate(plain) - surrogate(learned).  HOST
+   outputs; synchronous. */
+int magpie_learned_window_values(magpie_ctx* ctx, int32_t count, int32_t* accepted, double* margin);
+
+/*
+ * Precision form: the windows' 2-D DFTs as tensor-core GEMMs.  An m-point
+ * line DFT (m = 16 Qr) is two complex matrix products, 16-point DFTs then
+ * Qr-point DFTs with FP32 twiddles between them (Cooley-Tukey); each product
+ * runs on BF16 tensor cores with hi+lo split operands (a = hi + lo, both
+ * BF16; a b taken as hi hi + hi lo + lo hi) and FP32 accumulation, so a
+ * transform carries a relative error of about 1e-5 (2^-16 per product) where
+ * the FP32 FFT path carries about 1e-6.  The projection, the V-cycle and the
+ * update are the FP32 path's; Phi_k and the gradient norms stay FP64 sums.
+ * mode 0: FP32 FFT path (default); mode 1: tensor-core DFTs (m = 64, 128 or
+ * 256, update_probe = 0).  The mode applies to later steps and sweeps.
+ */
+int magpie_set_precision(magpie_ctx* ctx, int32_t mode);
+
+/* out[c] = the 2-D DFT of in[c] (unnormalised; inverse = 1: the conjugate
+   transform, without 1/m^2) for `count` m x m complex windows (DEVICE), by
+   the precision form's tensor-core path.  in == out is allowed.  Allocates a
+   few KiB of tables per call; synchronous. */
+int magpie_dft2_tc(const void* in, void* out, int32_t m, int32_t count, int32_t inverse, void* stream);
+
 /* Static name of an error code; never NULL. */
 const char* magpie_strerror(int code);
 

@@ -58,6 +58,8 @@ constexpr int kMaxCluster = 8;       // largest number of blocks per window
 
 #include "fft_lines.cuh"
 #include "window_kernel.cuh"
+#include "learned.cuh"
+#include "precision.cuh"
 
 // z += sum_b contrib_b / sum_b w0 over the windows covering each pixel, in
 // minibatch order (bitwise reproducible).  One block of 256 threads per
@@ -570,6 +572,12 @@ cudaError_t prepare_kernels(int MS) {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(apply_kernel_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)((sizeof(int2) + sizeof(int)) * kMaxMinibatch));
+  if (e == cudaSuccess && MS <= 128)
+    e = cudaFuncSetAttribute(vcycle_up_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(2 * sizeof(float2) * (size_t)up_off(128, 8)));
+  if (e == cudaSuccess && MS >= 64)
+    e = cudaFuncSetAttribute(vcycle_up_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(float2) * (size_t)up_off(MS, ilog2(MS) + 1)));
   if (e != cudaSuccess) return e;
   switch (MS) {
     case 8: return prepare_size<8>();
@@ -619,6 +627,26 @@ struct magpie_group {
   cudaGraphExec_t graph = nullptr;
 };
 
+// The network of the learned coarse correction with its training state.
+struct magpie_cnn {
+  int h = 0, max_batch = 0, P = 0;
+  cudaStream_t stream = nullptr;
+  int off[kCnnLayers] = {};         // parameter offset of each layer (weights, then biases)
+  float* theta = nullptr;           // FP32 parameters
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  bf16* wbf = nullptr;              // BF16 copy read by the forward and backward kernels
+  float* grad = nullptr;            // [P]
+  bf16* act[kCnnLayers] = {};       // layer inputs: act[0] the BF16 network input, act[l] layer l-1's output
+  float* y = nullptr;               // [max_batch][h][h][2] output of the last forward pass
+  float* dz[2] = {};                // backward buffers
+  float* dy = nullptr;              // [max_batch][h][h][2]
+  float* part = nullptr;            // split-K and weight-gradient partial sums
+  size_t part_n = 0;
+  int last_batch = 0;               // batch of the last forward pass (backward's batch)
+  long step = 0;                    // Adam steps taken
+};
+
 struct magpie_ctx {
   magpie_params p{};
   int M = 0;
@@ -646,6 +674,18 @@ struct magpie_ctx {
   int32_t* order = nullptr;
   double* sums = nullptr;
   int* err = nullptr;
+  float* wz = nullptr;        // W_z^l tables, l = 0 .. L-2 (coarse object of the learned correction)
+  // learned coarse correction (when a network is attached)
+  magpie_cnn* cnn = nullptr;
+  float4* lx = nullptr;       // [minibatch][h][h] network input
+  float* lscale = nullptr;    // [minibatch] RMS of the plain coarse step
+  int* lacc = nullptr;        // [minibatch] 1 = learned V-cycle output kept
+  double* lmargin = nullptr;  // [minibatch] surrogate(plain) - surrogate(learned)
+  unsigned long long* lstats = nullptr;  // proposals, acceptances
+  // precision form (tensor-core DFTs)
+  int precision = 0;
+  float2* pbuf = nullptr;     // [minibatch][m][m] exit wave / spectrum / revised exit wave
+  TcTables* tabs = nullptr;
   cudaGraphExec_t graph = nullptr;
   std::vector<cudaEvent_t> events;  // 4 per minibatch step (magpie_profile_sweep)
   // host sweeps: chunked uploads of the intensities on several copy streams
@@ -680,12 +720,331 @@ StepArgs make_args(magpie_ctx* c, const int32_t* idx) {
   return a;
 }
 
+// ------------------------------------------------- learned coarse correction
+int cnn_side_in(int h, int l) {
+  int s = h;
+  for (int j = 0; j < l; ++j) s = s * kCnn[j].up / kCnn[j].stride;
+  return s;
+}
+int cnn_side_out(int h, int l) { return cnn_side_in(h, l) * kCnn[l].up / kCnn[l].stride; }
+int cnn_param_count() {
+  int P = 0;
+  for (int l = 0; l < kCnnLayers; ++l) P += kCnn[l].cout * 9 * kCnn[l].cin + kCnn[l].cout;
+  return P;
+}
+
+struct ConvPlan {
+  int gx, gy, splits, ksplit, bm, bn;
+};
+
+ConvPlan conv_plan(const ConvFwd& a) {
+  ConvPlan pl{};
+  pl.bn = a.Cout <= 8 ? 8 : (a.Cout <= 32 ? 32 : 64);
+  pl.bm = pl.bn == 64 ? 64 : 128;
+  const int Mtot = a.B * a.Ho * a.Ho;
+  pl.gx = (Mtot + pl.bm - 1) / pl.bm;
+  pl.gy = (a.Cout + pl.bn - 1) / pl.bn;
+  const int ksteps = (a.K + 31) / 32;
+  const int blocks = pl.gx * pl.gy;
+  int splits = 1;
+  if (a.Cin % 32 == 0 && blocks < 2 * 152) splits = std::max(1, std::min(ksteps / 4, (2 * 152 + blocks - 1) / blocks));
+  const int per = (ksteps + splits - 1) / splits;
+  pl.ksplit = per * 32;
+  pl.splits = (ksteps + per - 1) / per;
+  return pl;
+}
+
+// Partial-sum floats needed by any batch of 1 .. max_batch windows.
+size_t cnn_part_floats(int h, int max_batch) {
+  size_t n = 0;
+  for (int B = 1; B <= max_batch; ++B)
+  for (int l = 0; l < kCnnLayers; ++l) {
+    const int Ho = cnn_side_out(h, l);
+    ConvFwd a{};
+    a.B = B;
+    a.Ho = Ho;
+    a.Cin = kCnn[l].cin;
+    a.Cout = kCnn[l].cout;
+    a.K = 9 * a.Cin;
+    const ConvPlan pl = conv_plan(a);
+    if (pl.splits > 1) n = std::max(n, (size_t)pl.splits * B * Ho * Ho * a.Cout);
+    const int P = a.Cout * 9 * a.Cin + a.Cout, npix = B * Ho * Ho;
+    int chunks = std::max(1, std::min((262144 + P - 1) / P, std::max(1, npix / 16)));
+    const int chunk = (npix + chunks - 1) / chunks;
+    chunks = (npix + chunk - 1) / chunk;
+    n = std::max(n, (size_t)chunks * P);
+  }
+  return n;
+}
+
+cudaError_t launch_conv(const ConvFwd& a0, float* part, cudaStream_t st) {
+  ConvFwd a = a0;
+  const ConvPlan pl = conv_plan(a);
+  a.ksplit = pl.ksplit;
+  a.part = pl.splits > 1 ? part : nullptr;
+  const dim3 grid(pl.gx, pl.gy, pl.splits);
+  if (pl.bn == 8)
+    conv_fwd_kernel<128, 8><<<grid, 128, 0, st>>>(a);
+  else if (pl.bn == 32)
+    conv_fwd_kernel<128, 32><<<grid, 128, 0, st>>>(a);
+  else
+    conv_fwd_kernel<64, 64><<<grid, 128, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || pl.splits == 1) return e;
+  const size_t n = (size_t)a.B * a.Ho * a.Ho * a.Cout;
+  conv_splitk_kernel<<<(int)std::min<size_t>((n + 255) / 256, 4096), 256, 0, st>>>(a, pl.splits);
+  return cudaGetLastError();
+}
+
+// Forward pass of `batch` inputs x [batch][h][h][4] (float) into y [batch][h][h][2].
+int cnn_enqueue_forward(magpie_cnn* n, const float* x, int batch, float* y, cudaStream_t st) {
+  const int h = n->h;
+  const size_t nx = (size_t)batch * h * h * 4;
+  to_bf16_kernel<<<(int)std::min<size_t>((nx + 255) / 256, 4096), 256, 0, st>>>(x, n->act[0], nx);
+  CUDA_TRY(cudaGetLastError());
+  for (int l = 0; l < kCnnLayers; ++l) {
+    const CnnLayer& L = kCnn[l];
+    ConvFwd a{};
+    a.in = n->act[l];
+    a.w = n->wbf + n->off[l];
+    a.bias = n->theta + n->off[l] + (size_t)L.cout * 9 * L.cin;
+    a.out = l + 1 < kCnnLayers ? (void*)n->act[l + 1] : (void*)y;
+    a.B = batch;
+    a.Hin = cnn_side_in(h, l);
+    a.Cin = L.cin;
+    a.Cout = L.cout;
+    a.stride = L.stride;
+    a.up = L.up;
+    a.Ho = cnn_side_out(h, l);
+    a.relu = L.relu;
+    a.out_f32 = l + 1 == kCnnLayers;
+    a.K = 9 * L.cin;
+    CUDA_TRY(launch_conv(a, n->part, st));
+  }
+  n->last_batch = batch;
+  return MAGPIE_OK;
+}
+
+// Gradient of <dy, y> over the parameters, for the inputs of the last forward pass.
+int cnn_enqueue_backward(magpie_cnn* n, const float* dy, float* grad, cudaStream_t st) {
+  const int h = n->h, B = n->last_batch;
+  const float* dz = dy;
+  int cur = 0;
+  for (int l = kCnnLayers - 1; l >= 0; --l) {
+    const CnnLayer& L = kCnn[l];
+    const int Hin = cnn_side_in(h, l), Ho = cnn_side_out(h, l);
+    const int P = L.cout * 9 * L.cin + L.cout, npix = B * Ho * Ho;
+    int chunks = std::max(1, std::min((262144 + P - 1) / P, std::max(1, npix / 16)));
+    const int chunk = (npix + chunks - 1) / chunks;
+    chunks = (npix + chunk - 1) / chunk;
+    conv_bwd_weight_kernel<<<dim3((P + 255) / 256, chunks), 256, 0, st>>>(dz, n->act[l], n->part, B, Hin, L.cin,
+                                                                          L.cout, L.stride, L.up, Ho, chunk);
+    CUDA_TRY(cudaGetLastError());
+    chunk_sum_kernel<<<(P + 255) / 256, 256, 0, st>>>(n->part, grad + n->off[l], P, chunks);
+    CUDA_TRY(cudaGetLastError());
+    if (l > 0) {
+      const size_t nx = (size_t)B * Hin * Hin * L.cin;
+      conv_bwd_data_kernel<<<(int)std::min<size_t>((nx + 255) / 256, 8192), 256, 0, st>>>(
+          dz, n->wbf + n->off[l], n->act[l], n->dz[cur], B, Hin, L.cin, L.cout, L.stride, L.up, Ho);
+      CUDA_TRY(cudaGetLastError());
+      dz = n->dz[cur];
+      cur ^= 1;
+    }
+  }
+  return MAGPIE_OK;
+}
+
+int cnn_enqueue_params(magpie_cnn* n, cudaStream_t st) {
+  to_bf16_kernel<<<(n->P + 255) / 256, 256, 0, st>>>(n->theta, n->wbf, (size_t)n->P);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemsetAsync(n->adam_m, 0, sizeof(float) * n->P, st));
+  CUDA_TRY(cudaMemsetAsync(n->adam_v, 0, sizeof(float) * n->P, st));
+  n->step = 0;
+  return MAGPIE_OK;
+}
+
+int learned_supported(const magpie_ctx* c, const magpie_cnn* n) {
+  const int L = c->p.levels, m = c->p.m;
+  if (L < 2) return fail(MAGPIE_EINVAL, "the learned correction needs levels >= 2");
+  if (m > 128) return fail(MAGPIE_EUNSUPPORTED, "the learned correction supports m <= 128");
+  if (c->p.update_probe) return fail(MAGPIE_EINVAL, "the learned correction needs update_probe = 0");
+  if (n && n->h != (m >> (L - 1)))
+    return fail(MAGPIE_EINVAL, "network side " + std::to_string(n->h) + " != m / 2^(levels-1) = " +
+                                   std::to_string(m >> (L - 1)));
+  if (n && n->max_batch < c->p.minibatch) return fail(MAGPIE_EINVAL, "network max_batch < minibatch");
+  return MAGPIE_OK;
+}
+
+int learned_buffers(magpie_ctx* c) {
+  if (c->lx) return MAGPIE_OK;
+  const int h = c->p.m >> (c->p.levels - 1), B = c->p.minibatch;
+  cudaError_t e = cudaMalloc((void**)&c->lx, sizeof(float4) * (size_t)B * h * h);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->lscale, sizeof(float) * B);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->lacc, sizeof(int) * B);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->lmargin, sizeof(double) * B);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->lstats, sizeof(unsigned long long) * 2);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->lstats, 0, sizeof(unsigned long long) * 2, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->lacc, 0, sizeof(int) * B, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->lmargin, 0, sizeof(double) * B, c->stream);
+  if (e != cudaSuccess)
+    return fail(e == cudaErrorMemoryAllocation ? MAGPIE_ENOMEM : MAGPIE_ECUDA,
+                std::string("learned buffers: ") + cudaGetErrorString(e));
+  return MAGPIE_OK;
+}
+
+CoarseArgs coarse_args(magpie_ctx* c, const int32_t* idx, float4* x, float* scale) {
+  CoarseArgs a{};
+  a.z = c->z;
+  a.n_cols = c->p.n_cols;
+  a.pos = c->pos;
+  a.idx = idx;
+  a.n_pos = c->p.n_pos;
+  a.MS = c->p.m;
+  a.L = c->p.levels;
+  a.g0 = c->contrib;
+  a.pyr = c->pyr;
+  a.wz = c->wz;
+  a.x = x;
+  a.scale = scale;
+  return a;
+}
+
+size_t learned_up_smem(int MS, int L) { return 2 * sizeof(float2) * (size_t)up_off(MS, L); }
+
+LearnedUpArgs up_args(magpie_ctx* c, const int32_t* idx) {
+  LearnedUpArgs u{};
+  u.idx = idx;
+  u.n_pos = c->p.n_pos;
+  u.MS = c->p.m;
+  u.L = c->p.levels;
+  u.contrib = c->contrib;
+  u.pyr = c->pyr;
+  return u;
+}
+
+// From g^0 in the increments: the network's input and scale, its forward
+// pass, then the V-cycle with the kept coarse correction writes w^0 Delta
+// back to the increments.
+int enqueue_learned_tail(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st) {
+  coarse_state_kernel<<<count, 256, 0, st>>>(coarse_args(c, idx, c->lx, c->lscale));
+  CUDA_TRY(cudaGetLastError());
+  int rc = cnn_enqueue_forward(c->cnn, reinterpret_cast<const float*>(c->lx), count, c->cnn->y, st);
+  if (rc) return rc;
+  LearnedUpArgs u = up_args(c, idx);
+  u.scale = c->lscale;
+  u.y = c->cnn->y;
+  u.accepted = c->lacc;
+  u.margin = c->lmargin;
+  u.stats = c->lstats;
+  vcycle_up_kernel<true><<<count, 256, learned_up_smem(c->p.m, c->p.levels), st>>>(u);
+  CUDA_TRY(cudaGetLastError());
+  return MAGPIE_OK;
+}
+
+// ----------------------------------------------------------- precision form
+void build_tc_tables(int MS, TcTables& T) {
+  const int QR = MS / 16;
+  const double pi = 3.14159265358979323846;
+  std::memset(&T, 0, sizeof(T));
+  for (int inv = 0; inv < 2; ++inv) {
+    const double sg = inv ? 1.0 : -1.0;
+    for (int k = 0; k < 16; ++k)
+      for (int n = 0; n < 16; ++n) {
+        const double ph = 2.0 * pi * (double)((k * n) % 16) / 16.0;
+        const float fr = (float)std::cos(ph), fi = (float)(sg * std::sin(ph));
+        T.f16[inv][k * 32 + n] = fr;
+        T.f16[inv][k * 32 + 16 + n] = -fi;
+        T.f16[inv][(16 + k) * 32 + n] = fi;
+        T.f16[inv][(16 + k) * 32 + 16 + n] = fr;
+      }
+    for (int n2 = 0; n2 < QR; ++n2)
+      for (int k2 = 0; k2 < QR; ++k2) {
+        const double ph = 2.0 * pi * (double)((n2 * k2) % QR) / (double)QR;
+        const float fr = (float)std::cos(ph), fi = (float)(sg * std::sin(ph));
+        T.fq[inv][n2 * 32 + k2] = fr;
+        T.fq[inv][(QR + n2) * 32 + k2] = -fi;
+        T.fq[inv][n2 * 32 + QR + k2] = fi;
+        T.fq[inv][(QR + n2) * 32 + QR + k2] = fr;
+      }
+  }
+}
+
+template <int MS>
+cudaError_t launch_dft2_tc(float2* buf, int count, const TcTables* tabs, const float2* tw, int inv, cudaStream_t st) {
+  const dim3 grid((unsigned)count * (MS / kTcLines));
+  if (inv) {
+    dft_tc_kernel<MS, 1, 1><<<grid, 128, 0, st>>>(buf, tabs, tw, 1.f);
+    dft_tc_kernel<MS, 0, 1><<<grid, 128, 0, st>>>(buf, tabs, tw, 1.f);
+  } else {
+    dft_tc_kernel<MS, 0, 0><<<grid, 128, 0, st>>>(buf, tabs, tw, 1.f);
+    dft_tc_kernel<MS, 1, 0><<<grid, 128, 0, st>>>(buf, tabs, tw, 1.f);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dft2_tc_m(int MS, float2* buf, int count, const TcTables* tabs, const float2* tw, int inv,
+                             cudaStream_t st) {
+  switch (MS) {
+    case 64: return launch_dft2_tc<64>(buf, count, tabs, tw, inv, st);
+    case 128: return launch_dft2_tc<128>(buf, count, tabs, tw, inv, st);
+    case 256: return launch_dft2_tc<256>(buf, count, tabs, tw, inv, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Exit waves, tensor-core DFTs, projection, inverse DFTs and g^0 into the
+// increments (with the per-tile partial sums and the windows' corners).
+int enqueue_precision_g0(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st) {
+  PrecArgs a{};
+  a.z = c->z;
+  a.n_cols = c->p.n_cols;
+  a.Q = c->Q;
+  a.amp = c->amp;
+  a.pos = c->pos;
+  a.idx = idx;
+  a.n_pos = c->p.n_pos;
+  a.MS = c->p.m;
+  a.CL = cluster_of(c->p.m);
+  a.buf = c->pbuf;
+  a.contrib = c->contrib;
+  a.part = c->part;
+  a.corner = c->corner;
+  a.err = c->err;
+  const dim3 tiles((unsigned)count, (unsigned)a.CL);
+  exit_wave_kernel<<<tiles, 256, 0, st>>>(a);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(launch_dft2_tc_m(a.MS, c->pbuf, count, c->tabs, c->tw, 0, st));
+  projection_kernel<<<tiles, 256, 0, st>>>(a);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(launch_dft2_tc_m(a.MS, c->pbuf, count, c->tabs, c->tw, 1, st));
+  grad_kernel<<<tiles, 256, 0, st>>>(a);
+  CUDA_TRY(cudaGetLastError());
+  return MAGPIE_OK;
+}
+
 // ev (optional): four events recorded before/after the window kernel and
 // before/after the apply kernel.
 int enqueue_step(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st, const cudaEvent_t* ev = nullptr) {
   StepArgs a = make_args(c, idx);
   if (ev) CUDA_TRY(cudaEventRecord(ev[0], st));
-  CUDA_TRY(launch_window_m<kStep>(c->p.m, a, count, st));
+  int rc = MAGPIE_OK;
+  if (c->precision) {
+    rc = enqueue_precision_g0(c, idx, count, st);
+    if (!rc && c->cnn) {
+      rc = enqueue_learned_tail(c, idx, count, st);
+    } else if (!rc && c->p.levels >= 2) {
+      vcycle_up_kernel<false><<<count, 256, sizeof(float2) * (size_t)up_off(c->p.m, c->p.levels), st>>>(
+          up_args(c, idx));
+      CUDA_TRY(cudaGetLastError());
+    }
+  } else if (c->cnn) {
+    a.grad_only = 1;
+    CUDA_TRY(launch_window_m<kStep>(c->p.m, a, count, st));
+    rc = enqueue_learned_tail(c, idx, count, st);
+  } else {
+    CUDA_TRY(launch_window_m<kStep>(c->p.m, a, count, st));
+  }
+  if (rc) return rc;
   if (ev) CUDA_TRY(cudaEventRecord(ev[1], st));
   if (ev) CUDA_TRY(cudaEventRecord(ev[2], st));
   CUDA_TRY(launch_apply(c->z, c->p.n_rows, c->p.n_cols, c->corner, idx, count, c->p.n_pos, c->contrib,
@@ -703,6 +1062,10 @@ int enqueue_step(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st, 
 int build_pyramid(magpie_ctx* c, const void* probe) {
   CUDA_TRY(cudaMemcpyAsync(c->Q, probe, sizeof(float2) * c->M, cudaMemcpyDeviceToDevice, c->stream));
   CUDA_TRY(enqueue_pyramid(c->Q, c->p.m, c->p.levels, c->p.alpha, c->mx, c->pyr_q, c->pyr_u, c->pyr, c->stream));
+  if (c->wz) {
+    wz_kernel<<<std::max(1, c->M / 256), 256, 0, c->stream>>>(c->Q, c->p.m, c->p.levels, c->wz);
+    CUDA_TRY(cudaGetLastError());
+  }
   return MAGPIE_OK;
 }
 
@@ -895,7 +1258,8 @@ void magpie_destroy(magpie_ctx* c) {
     if (e) cudaEventDestroy(e);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   void* bufs[] = {c->Q, c->tw, c->amp, c->stage, c->pos, c->pyr, c->pyr_q, c->pyr_u, c->contrib,
-                  c->phi_pos, c->gn_pos, c->part, c->corner, c->mx, c->pnum, c->pa2, c->pmax, c->iota, c->order, c->sums, c->err};
+                  c->phi_pos, c->gn_pos, c->part, c->corner, c->mx, c->pnum, c->pa2, c->pmax, c->iota, c->order, c->sums, c->err,
+                  c->wz, c->lx, c->lscale, c->lacc, c->lmargin, c->lstats, c->pbuf, c->tabs};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete c;
@@ -944,7 +1308,8 @@ int magpie_create(magpie_ctx** out, const magpie_params* params, void* object, c
       (p.update_probe && (rc = alloc((void**)&c->pa2, sizeof(float) * M * p.minibatch))) ||
       (p.update_probe && (rc = alloc((void**)&c->pmax, sizeof(double) * kMaxCluster * p.minibatch))) ||
       (rc = alloc((void**)&c->iota, sizeof(int32_t) * N)) || (rc = alloc((void**)&c->order, sizeof(int32_t) * N)) ||
-      (rc = alloc((void**)&c->sums, sizeof(double) * 2)) || (rc = alloc((void**)&c->err, sizeof(int))))
+      (rc = alloc((void**)&c->sums, sizeof(double) * 2)) || (rc = alloc((void**)&c->err, sizeof(int))) ||
+      (p.levels >= 2 && (rc = alloc((void**)&c->wz, sizeof(float) * M * 2))))
     return rc;
 
   auto cleanup_fail = [&](int code) {
@@ -1225,6 +1590,8 @@ int magpie_group_create(magpie_group** out, magpie_ctx* const* ctxs, int32_t n, 
   for (int i = 0; i < n; ++i) {
     if (!ctxs[i]) return fail(MAGPIE_EINVAL, "context " + std::to_string(i) + " is NULL");
     if (ctxs[i]->p.update_probe) return fail(MAGPIE_EINVAL, "contexts with update_probe = 1 cannot be grouped");
+    if (ctxs[i]->cnn || ctxs[i]->precision)
+      return fail(MAGPIE_EINVAL, "contexts with a network or tensor-core DFTs cannot be grouped");
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == ctxs[i]) return fail(MAGPIE_EINVAL, "a context appears twice in the group");
   }
@@ -1326,6 +1693,245 @@ int magpie_group_sweep(magpie_group* g, const int32_t* const* orders) {
     CUDA_TRY(cudaMemcpyAsync(c->order, orders[i], sizeof(int32_t) * c->p.n_pos, cudaMemcpyDeviceToDevice, g->stream));
   }
   CUDA_TRY(cudaGraphLaunch(g->graph, g->stream));
+  return MAGPIE_OK;
+}
+
+
+// ------------------------------------------------- learned coarse correction
+
+int32_t magpie_cnn_param_count(void) { return cnn_param_count(); }
+
+void magpie_cnn_destroy(magpie_cnn* n) {
+  if (!n) return;
+  void* bufs[] = {n->theta, n->adam_m, n->adam_v, n->wbf, n->grad, n->y, n->dz[0], n->dz[1], n->dy, n->part};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  for (auto* a : n->act)
+    if (a) cudaFree(a);
+  delete n;
+}
+
+int magpie_cnn_create(magpie_cnn** out, int32_t h, int32_t max_batch, void* stream) {
+  if (!out) return fail(MAGPIE_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (h != 8 && h != 16 && h != 32 && h != 64) return fail(MAGPIE_EINVAL, "h must be 8, 16, 32 or 64");
+  if (max_batch < 1 || max_batch > kMaxMinibatch) return fail(MAGPIE_EINVAL, "max_batch must lie in [1, 4096]");
+  magpie_cnn* n = new magpie_cnn();
+  n->h = h;
+  n->max_batch = max_batch;
+  n->stream = (cudaStream_t)stream;
+  n->P = cnn_param_count();
+  int o = 0;
+  for (int l = 0; l < kCnnLayers; ++l) {
+    n->off[l] = o;
+    o += kCnn[l].cout * 9 * kCnn[l].cin + kCnn[l].cout;
+  }
+  const size_t B = max_batch, P = n->P;
+  size_t dzn = 0;
+  for (int l = 0; l < kCnnLayers; ++l) {
+    const size_t so = cnn_side_out(h, l), si = cnn_side_in(h, l);
+    dzn = std::max(dzn, B * so * so * kCnn[l].cout);
+    dzn = std::max(dzn, B * si * si * kCnn[l].cin);
+  }
+  n->part_n = cnn_part_floats(h, max_batch);
+  cudaError_t e = cudaSuccess;
+  auto al = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+  };
+  al((void**)&n->theta, sizeof(float) * P);
+  al((void**)&n->adam_m, sizeof(float) * P);
+  al((void**)&n->adam_v, sizeof(float) * P);
+  al((void**)&n->wbf, sizeof(bf16) * P);
+  al((void**)&n->grad, sizeof(float) * P);
+  for (int l = 0; l < kCnnLayers; ++l) {
+    const size_t si = cnn_side_in(h, l);
+    al((void**)&n->act[l], sizeof(bf16) * B * si * si * kCnn[l].cin);
+  }
+  al((void**)&n->y, sizeof(float) * B * h * h * 2);
+  al((void**)&n->dy, sizeof(float) * B * h * h * 2);
+  al((void**)&n->dz[0], sizeof(float) * dzn);
+  al((void**)&n->dz[1], sizeof(float) * dzn);
+  al((void**)&n->part, sizeof(float) * n->part_n);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n->theta, 0, sizeof(float) * P, n->stream);
+  if (e != cudaSuccess) {
+    magpie_cnn_destroy(n);
+    return fail(e == cudaErrorMemoryAllocation ? MAGPIE_ENOMEM : MAGPIE_ECUDA,
+                std::string("network buffers: ") + cudaGetErrorString(e));
+  }
+  const int rc = cnn_enqueue_params(n, n->stream);
+  if (rc) {
+    magpie_cnn_destroy(n);
+    return rc;
+  }
+  *out = n;
+  return MAGPIE_OK;
+}
+
+int magpie_cnn_set_params(magpie_cnn* n, const float* theta) {
+  if (!n || !theta) return fail(MAGPIE_EINVAL, "NULL argument");
+  CUDA_TRY(cudaMemcpyAsync(n->theta, theta, sizeof(float) * n->P, cudaMemcpyDeviceToDevice, n->stream));
+  return cnn_enqueue_params(n, n->stream);
+}
+
+int magpie_cnn_get_params(magpie_cnn* n, float* theta) {
+  if (!n || !theta) return fail(MAGPIE_EINVAL, "NULL argument");
+  CUDA_TRY(cudaMemcpyAsync(theta, n->theta, sizeof(float) * n->P, cudaMemcpyDeviceToDevice, n->stream));
+  return MAGPIE_OK;
+}
+
+int magpie_cnn_forward(magpie_cnn* n, const float* x, int32_t batch, float* y) {
+  if (!n || !x || !y) return fail(MAGPIE_EINVAL, "NULL argument");
+  if (batch < 1 || batch > n->max_batch) return fail(MAGPIE_EINVAL, "batch must lie in [1, max_batch]");
+  const int rc = cnn_enqueue_forward(n, x, batch, n->y, n->stream);
+  if (rc) return rc;
+  CUDA_TRY(cudaMemcpyAsync(y, n->y, sizeof(float) * (size_t)batch * n->h * n->h * 2, cudaMemcpyDeviceToDevice,
+                           n->stream));
+  return MAGPIE_OK;
+}
+
+int magpie_cnn_backward(magpie_cnn* n, const float* dy, float* grad) {
+  if (!n || !dy || !grad) return fail(MAGPIE_EINVAL, "NULL argument");
+  if (n->last_batch < 1) return fail(MAGPIE_EINVAL, "no forward pass to differentiate");
+  return cnn_enqueue_backward(n, dy, grad, n->stream);
+}
+
+int magpie_cnn_train_step(magpie_cnn* n, const float* x0, const float* zh, const float* scale, int32_t batch,
+                          float lr, double* loss) {
+  if (!n || !x0 || !zh || !scale || !loss) return fail(MAGPIE_EINVAL, "NULL argument");
+  if (batch < 1 || batch > n->max_batch) return fail(MAGPIE_EINVAL, "batch must lie in [1, max_batch]");
+  if (!(lr > 0.f) || !std::isfinite(lr)) return fail(MAGPIE_EINVAL, "lr must be finite and > 0");
+  cudaStream_t st = n->stream;
+  int rc = cnn_enqueue_forward(n, x0, batch, n->y, st);
+  if (rc) return rc;
+  cnn_loss_kernel<<<1, 1024, 0, st>>>(n->y, reinterpret_cast<const float4*>(x0), reinterpret_cast<const float2*>(zh),
+                                      scale, batch, n->h * n->h, n->dy, loss);
+  CUDA_TRY(cudaGetLastError());
+  rc = cnn_enqueue_backward(n, n->dy, n->grad, st);
+  if (rc) return rc;
+  n->step += 1;
+  const float c1 = (float)(1.0 / (1.0 - std::pow(0.9, (double)n->step)));
+  const float c2 = (float)(1.0 / (1.0 - std::pow(0.999, (double)n->step)));
+  adam_kernel<<<(n->P + 255) / 256, 256, 0, st>>>(n->theta, n->grad, n->adam_m, n->adam_v, n->wbf, n->P, lr, c1, c2);
+  CUDA_TRY(cudaGetLastError());
+  return MAGPIE_OK;
+}
+
+int magpie_coarse_state(magpie_ctx* c, const int32_t* idx, int32_t count, float* x, float* scale) {
+  if (!c || !idx || !x || !scale) return fail(MAGPIE_EINVAL, "NULL argument");
+  if (count < 1 || count > c->p.minibatch) return fail(MAGPIE_EINVAL, "count must lie in [1, minibatch]");
+  int rc = learned_supported(c, nullptr);
+  if (rc) return rc;
+  StepArgs a = make_args(c, idx);
+  a.grad_only = 1;
+  CUDA_TRY(launch_window_m<kStep>(c->p.m, a, count, c->stream));
+  coarse_state_kernel<<<count, 256, 0, c->stream>>>(coarse_args(c, idx, reinterpret_cast<float4*>(x), scale));
+  CUDA_TRY(cudaGetLastError());
+  return read_err(c);
+}
+
+int magpie_gather_windows(magpie_ctx* c, const int32_t* idx, int32_t count, void* patches) {
+  if (!c || !idx || !patches) return fail(MAGPIE_EINVAL, "NULL argument");
+  if (count < 1) return fail(MAGPIE_EINVAL, "count must be >= 1");
+  gather_windows_kernel<<<count, 256, 0, c->stream>>>(c->z, c->p.n_cols, c->pos, idx, c->p.n_pos, c->p.m,
+                                                      (float2*)patches);
+  CUDA_TRY(cudaGetLastError());
+  return MAGPIE_OK;
+}
+
+int magpie_attach_cnn(magpie_ctx* c, magpie_cnn* n) {
+  if (!c) return fail(MAGPIE_EINVAL, "NULL context");
+  if (n) {
+    int rc = learned_supported(c, n);
+    if (rc) return rc;
+    rc = learned_buffers(c);
+    if (rc) return rc;
+  }
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->cnn = n;
+  return MAGPIE_OK;
+}
+
+int magpie_learned_stats(magpie_ctx* c, int64_t* proposed, int64_t* accepted) {
+  if (!c || !proposed || !accepted) return fail(MAGPIE_EINVAL, "NULL argument");
+  unsigned long long h[2] = {0ull, 0ull};
+  if (c->lstats) {
+    CUDA_TRY(cudaMemcpyAsync(h, c->lstats, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+  }
+  *proposed = (int64_t)h[0];
+  *accepted = (int64_t)h[1];
+  return MAGPIE_OK;
+}
+
+int magpie_learned_window_values(magpie_ctx* c, int32_t count, int32_t* accepted, double* margin) {
+  if (!c || !accepted || !margin) return fail(MAGPIE_EINVAL, "NULL argument");
+  if (!c->lacc) return fail(MAGPIE_EINVAL, "no network has been attached to this context");
+  if (count < 1 || count > c->p.minibatch) return fail(MAGPIE_EINVAL, "count must lie in [1, minibatch]");
+  CUDA_TRY(cudaMemcpyAsync(accepted, c->lacc, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaMemcpyAsync(margin, c->lmargin, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return MAGPIE_OK;
+}
+
+
+// ---------------------------------------------------------- precision form
+
+int magpie_set_precision(magpie_ctx* c, int32_t mode) {
+  if (!c) return fail(MAGPIE_EINVAL, "NULL context");
+  if (mode != 0 && mode != 1) return fail(MAGPIE_EINVAL, "mode must be 0 (FP32 FFTs) or 1 (tensor-core DFTs)");
+  if (mode == 1) {
+    const int m = c->p.m;
+    if (m != 64 && m != 128 && m != 256)
+      return fail(MAGPIE_EUNSUPPORTED, "tensor-core DFTs need m = 64, 128 or 256");
+    if (c->p.update_probe) return fail(MAGPIE_EINVAL, "tensor-core DFTs need update_probe = 0");
+    if (!c->pbuf) {
+      cudaError_t e = cudaMalloc((void**)&c->pbuf, sizeof(float2) * (size_t)c->M * c->p.minibatch);
+      if (e == cudaSuccess) e = cudaMalloc((void**)&c->tabs, sizeof(TcTables));
+      if (e != cudaSuccess)
+        return fail(e == cudaErrorMemoryAllocation ? MAGPIE_ENOMEM : MAGPIE_ECUDA,
+                    std::string("precision buffers: ") + cudaGetErrorString(e));
+      TcTables h;
+      build_tc_tables(m, h);
+      CUDA_TRY(cudaMemcpy(c->tabs, &h, sizeof(TcTables), cudaMemcpyHostToDevice));
+    }
+  }
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->precision = mode;
+  return MAGPIE_OK;
+}
+
+int magpie_dft2_tc(const void* in, void* out, int32_t m, int32_t count, int32_t inverse, void* stream) {
+  if (!in || !out) return fail(MAGPIE_EINVAL, "NULL argument");
+  if (m != 64 && m != 128 && m != 256) return fail(MAGPIE_EUNSUPPORTED, "m must be 64, 128 or 256");
+  if (count < 1 || (long long)count * m * m > (1LL << 28)) return fail(MAGPIE_EINVAL, "count out of range");
+  if (inverse != 0 && inverse != 1) return fail(MAGPIE_EINVAL, "inverse must be 0 or 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  TcTables h;
+  build_tc_tables(m, h);
+  std::vector<float2> htw(m);
+  for (int t = 0; t < m; ++t) {
+    const double ang = -2.0 * 3.14159265358979323846 * (double)t / (double)m;
+    htw[t] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+  }
+  TcTables* dt = nullptr;
+  float2* dtw = nullptr;
+  cudaError_t e = cudaMalloc((void**)&dt, sizeof(TcTables));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&dtw, sizeof(float2) * m);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dt, &h, sizeof(TcTables), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dtw, htw.data(), sizeof(float2) * m, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && in != out)
+    e = cudaMemcpyAsync(out, in, sizeof(float2) * (size_t)count * m * m, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = launch_dft2_tc_m(m, (float2*)out, count, dt, dtw, inverse, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (dt) cudaFree(dt);
+  if (dtw) cudaFree(dtw);
+  if (e != cudaSuccess) return fail(MAGPIE_ECUDA, std::string("magpie_dft2_tc: ") + cudaGetErrorString(e));
   return MAGPIE_OK;
 }
 

@@ -1,0 +1,318 @@
+// precision.cuh -- the precision form of the sweep: the windows' 2-D DFTs as
+// tensor-core GEMMs with BF16 hi+lo split operands and FP32 accumulation,
+// around the same projection, V-cycle and update as the FP32 path.  Included
+// by magpie.cu inside its anonymous namespace.
+//
+// An m-point line DFT (m = 16 Qr, Qr in {4, 8, 16}) is done as two small
+// complex matrix products (Cooley-Tukey with n = Qr n1 + n2, k = k1 + 16 k2):
+//   stage 1  Y[k1][n2]  = sum_{n1} F16[k1][n1] x[Qr n1 + n2]      (16-point DFTs)
+//   twiddle  Y'[k1][n2] = Y[k1][n2] w_m^{n2 k1}                     (FP32)
+//   stage 2  X[k1 + 16 k2] = sum_{n2} Y'[k1][n2] F_Qr[n2][k2]       (Qr-point DFTs)
+// Each complex product is one real GEMM on [re; im] blocks; every operand
+// a = hi + lo with hi = bf16(a), lo = bf16(a - hi), and a b is taken as
+// hi_a hi_b + hi_a lo_b + lo_a hi_b (the lo lo term, below 2^-16 |a b|, is
+// dropped), three m16n8k16 BF16 MMAs with FP32 accumulation.
+#pragma once
+
+constexpr int kTcLines = 16;  // lines per block
+
+// Real-block DFT matrices, FP32, built on the host in float64:
+//   f16[r][c]  (32 x 32): stage 1, rows (re k1 | im k1), columns (re n1 | im n1)
+//   fq[kk][nn] (32 x 32, zero-padded): stage 2, rows (re n2 | im n2),
+//              columns (re k2 | im k2), for the Qr of the window side
+// One set for the forward (exp(-i ...)) and one for the inverse transform.
+struct TcTables {
+  float f16[2][32 * 32];
+  float fq[2][32 * 32];
+};
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// hi and lo BF16 pairs of (a, b)
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+  hi = pack_bf16(__bfloat162float(ha), __bfloat162float(hb));
+  lo = pack_bf16(a - __bfloat162float(ha), b - __bfloat162float(hb));
+}
+
+__device__ __forceinline__ void mma3(float* c, const uint32_t* ah, const uint32_t* al, const uint32_t* bh,
+                                     const uint32_t* bl) {
+  mma_bf16(c, ah, bh);
+  mma_bf16(c, ah, bl);
+  mma_bf16(c, al, bh);
+}
+
+// One block: kTcLines lines of one window, loaded to shared memory (separate
+// real and imaginary planes), transformed in two MMA stages, stored back.
+// AXIS 0: lines are columns (element stride MS); AXIS 1: rows.  `scale`
+// multiplies the output.
+template <int MS, int AXIS, int INV>
+__global__ void __launch_bounds__(128) dft_tc_kernel(float2* __restrict__ data, const TcTables* __restrict__ tabs,
+                                                     const float2* __restrict__ tw, float scale) {
+  constexpr int QR = MS / 16;
+  static_assert(QR == 4 || QR == 8 || QR == 16, "window side 64, 128 or 256");
+  constexpr int NL = kTcLines, LD = MS + 4;
+  constexpr int K2T = (2 * QR + 15) / 16;  // stage-2 k-tiles
+  constexpr int N2T = 2 * QR / 8;          // stage-2 n-tiles
+  __shared__ float Sr[NL * LD];
+  __shared__ float Si[NL * LD];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int tiles = MS / NL;
+  const int win = blockIdx.x / tiles, l0 = (blockIdx.x % tiles) * NL;
+  float2* base = data + (size_t)win * MS * MS;
+
+  // ---- load
+  if (AXIS == 1) {
+    for (int i = tid; i < NL * MS; i += 128) {
+      const int l = i / MS, p = i % MS;
+      const float2 v = base[(size_t)(l0 + l) * MS + p];
+      Sr[l * LD + p] = v.x;
+      Si[l * LD + p] = v.y;
+    }
+  } else {
+    for (int i = tid; i < NL * MS; i += 128) {
+      const int p = i / NL, l = i % NL;
+      const float2 v = base[(size_t)p * MS + l0 + l];
+      Sr[l * LD + p] = v.x;
+      Si[l * LD + p] = v.y;
+    }
+  }
+
+  // ---- stage-1 operands: the 16-point DFT matrix as A fragments (hi, lo)
+  uint32_t ah[2][2][4], al[2][2][4];
+  {
+    const float* F = tabs->f16[INV];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int kt = 0; kt < 2; ++kt) {
+        const int r = mt * 16 + g, c = kt * 16 + 2 * t;
+        split2(F[r * 32 + c], F[r * 32 + c + 1], ah[mt][kt][0], al[mt][kt][0]);
+        split2(F[(r + 8) * 32 + c], F[(r + 8) * 32 + c + 1], ah[mt][kt][1], al[mt][kt][1]);
+        split2(F[r * 32 + c + 8], F[r * 32 + c + 9], ah[mt][kt][2], al[mt][kt][2]);
+        split2(F[(r + 8) * 32 + c + 8], F[(r + 8) * 32 + c + 9], ah[mt][kt][3], al[mt][kt][3]);
+      }
+  }
+  __syncthreads();
+
+  // ---- stage 1: columns j = (line, n2), NL * QR of them, 8 per n-tile
+  constexpr int NT1 = NL * QR / 8, PER1 = NT1 / 4;
+  float acc[PER1][2][4];
+#pragma unroll
+  for (int i = 0; i < PER1; ++i)
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[i][mt][e] = 0.f;
+#pragma unroll
+  for (int i = 0; i < PER1; ++i) {
+    const int j = (warp * PER1 + i) * 8 + g;  // this thread's B column
+    const int l = j / QR, n2 = j % QR;
+    const float* xr = Sr + l * LD + n2;
+    const float* xi = Si + l * LD + n2;
+    uint32_t bh[2][2], bl[2][2];
+    // k-tile 0: real parts of n1 = 2t, 2t+1, 2t+8, 2t+9; k-tile 1: imaginary parts
+    split2(xr[QR * (2 * t)], xr[QR * (2 * t + 1)], bh[0][0], bl[0][0]);
+    split2(xr[QR * (2 * t + 8)], xr[QR * (2 * t + 9)], bh[0][1], bl[0][1]);
+    split2(xi[QR * (2 * t)], xi[QR * (2 * t + 1)], bh[1][0], bl[1][0]);
+    split2(xi[QR * (2 * t + 8)], xi[QR * (2 * t + 9)], bh[1][1], bl[1][1]);
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int kt = 0; kt < 2; ++kt) mma3(acc[i][mt], ah[mt][kt], al[mt][kt], bh[kt], bl[kt]);
+  }
+  __syncthreads();
+  // twiddle w_m^{+-n2 k1}; thread holds re/im of k1 = g, g+8 for columns 2t, 2t+1
+#pragma unroll
+  for (int i = 0; i < PER1; ++i)
+#pragma unroll
+    for (int cc = 0; cc < 2; ++cc) {
+      const int j = (warp * PER1 + i) * 8 + 2 * t + cc;
+      const int l = j / QR, n2 = j % QR;
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int k1 = g + 8 * hh;
+        const float yr = acc[i][0][2 * hh + cc], yi = acc[i][1][2 * hh + cc];
+        float2 w = tw[(n2 * k1) % MS];
+        if (INV) w.y = -w.y;
+        Sr[l * LD + k1 * QR + n2] = yr * w.x - yi * w.y;
+        Si[l * LD + k1 * QR + n2] = yr * w.y + yi * w.x;
+      }
+    }
+  __syncthreads();
+
+  // ---- stage 2: rows (line, k1), NL * 16 of them; the Qr-point DFT matrix as B fragments
+  uint32_t bh2[K2T][N2T][2], bl2[K2T][N2T][2];
+  {
+    const float* F = tabs->fq[INV];
+#pragma unroll
+    for (int kt = 0; kt < K2T; ++kt)
+#pragma unroll
+      for (int nt = 0; nt < N2T; ++nt) {
+        const int n = nt * 8 + g, k = kt * 16 + 2 * t;
+        split2(F[k * 32 + n], F[(k + 1) * 32 + n], bh2[kt][nt][0], bl2[kt][nt][0]);
+        split2(F[(k + 8) * 32 + n], F[(k + 9) * 32 + n], bh2[kt][nt][1], bl2[kt][nt][1]);
+      }
+  }
+  constexpr int MT2 = NL * 16 / 16, PER2 = MT2 / 4;  // m-tiles of 16 rows = one line each
+  float out[PER2][N2T][4];
+#pragma unroll
+  for (int i = 0; i < PER2; ++i) {
+    const int l = warp * PER2 + i;  // m-tile = line l, rows k1 = 0..15
+#pragma unroll
+    for (int nt = 0; nt < N2T; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) out[i][nt][e] = 0.f;
+#pragma unroll
+    for (int kt = 0; kt < K2T; ++kt) {
+      // A[row k1][col kk]: kk < QR real part of n2 = kk, QR <= kk < 2 QR imaginary, else 0
+      uint32_t a_h[4], a_l[4];
+      float v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int row = g + ((q >> 1) & 1) * 8;
+        const int kk = kt * 16 + 2 * t + (q & 1) + ((q >> 2) & 1) * 8;
+        float val = 0.f;
+        if (kk < QR)
+          val = Sr[l * LD + row * QR + kk];
+        else if (kk < 2 * QR)
+          val = Si[l * LD + row * QR + kk - QR];
+        v[q] = val;
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) split2(v[2 * r], v[2 * r + 1], a_h[r], a_l[r]);
+#pragma unroll
+      for (int nt = 0; nt < N2T; ++nt) mma3(out[i][nt], a_h, a_l, bh2[kt][nt], bl2[kt][nt]);
+    }
+  }
+  __syncthreads();
+  // C: rows k1 = g, g+8; columns nn = 8 nt + 2t (+1): nn < QR real part of k2 = nn, else imaginary
+#pragma unroll
+  for (int i = 0; i < PER2; ++i) {
+    const int l = warp * PER2 + i;
+#pragma unroll
+    for (int nt = 0; nt < N2T; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int k1 = g + 8 * (e >> 1);
+        const int nn = nt * 8 + 2 * t + (e & 1);
+        const float v = out[i][nt][e] * scale;
+        if (nn < QR)
+          Sr[l * LD + k1 + 16 * nn] = v;
+        else
+          Si[l * LD + k1 + 16 * (nn - QR)] = v;
+      }
+  }
+  __syncthreads();
+
+  // ---- store
+  if (AXIS == 1) {
+    for (int i = tid; i < NL * MS; i += 128) {
+      const int l = i / MS, p = i % MS;
+      base[(size_t)(l0 + l) * MS + p] = make_float2(Sr[l * LD + p], Si[l * LD + p]);
+    }
+  } else {
+    for (int i = tid; i < NL * MS; i += 128) {
+      const int p = i / NL, l = i % NL;
+      base[(size_t)p * MS + l0 + l] = make_float2(Sr[l * LD + p], Si[l * LD + p]);
+    }
+  }
+}
+
+struct PrecArgs {
+  const float2* z;     // object [n_rows][n_cols]
+  int n_cols;
+  const float2* Q;     // probe [MS][MS]
+  const float* amp;    // sqrt(d) [n_pos][MS][MS]
+  const int32_t* pos;  // [n_pos][2]
+  const int32_t* idx;  // [count]
+  int n_pos, MS, CL;   // CL: row tiles per window (partials layout of the update kernel)
+  float2* buf;         // [count][MS][MS] exit wave -> spectrum -> revised exit wave
+  float2* contrib;     // [count][MS][MS] g^0 = conj(Q)(R - Q z)
+  double* part;        // [count][CL][2] partial sums: (|Psi| - sqrt d)^2, |g^0|^2
+  int2* corner;        // [count] window corners for the update kernel
+  int* err;            // bit 0: window index out of range
+};
+
+// buf[w] = Q . z_k (row tile blockIdx.y of window blockIdx.x); records the corner.
+__global__ void __launch_bounds__(256) exit_wave_kernel(const PrecArgs A) {
+  const int w = blockIdx.x, q = blockIdx.y, MS = A.MS, rows = MS / A.CL;
+  const int k = A.idx[w];
+  const bool ok = (unsigned)k < (unsigned)A.n_pos;
+  if (threadIdx.x == 0 && q == 0) {
+    if (ok)
+      A.corner[w] = make_int2(A.pos[2 * k], A.pos[2 * k + 1]);
+    else {
+      A.corner[w] = make_int2(-(1 << 30), -(1 << 30));
+      atomicOr(A.err, 1);
+    }
+  }
+  const int pr = ok ? A.pos[2 * k] : 0, pc = ok ? A.pos[2 * k + 1] : 0;
+  float2* out = A.buf + (size_t)w * MS * MS;
+  for (int i = threadIdx.x; i < rows * MS; i += blockDim.x) {
+    const int r = q * rows + i / MS, c = i % MS;
+    float2 v = make_float2(0.f, 0.f);
+    if (ok) {
+      const float2 zz = A.z[(size_t)(pr + r) * A.n_cols + pc + c];
+      const float2 qq = __ldg(&A.Q[r * MS + c]);
+      v = make_float2(qq.x * zz.x - qq.y * zz.y, qq.x * zz.y + qq.y * zz.x);
+    }
+    out[r * MS + c] = v;
+  }
+}
+
+// Fourier modulus projection in place: Psi <- sqrt(d) Psi / |Psi| / m^2
+// (sqrt(d) / m^2 where Psi = 0), and the tile's sum of (|Psi| - sqrt d)^2.
+__global__ void __launch_bounds__(256) projection_kernel(const PrecArgs A) {
+  __shared__ double red[32];
+  const int w = blockIdx.x, q = blockIdx.y, MS = A.MS, rows = MS / A.CL;
+  const int k = A.idx[w];
+  const bool ok = (unsigned)k < (unsigned)A.n_pos;
+  float2* P = A.buf + (size_t)w * MS * MS;
+  const float* am = A.amp + (size_t)(ok ? k : 0) * MS * MS;
+  const float inv_m2 = 1.f / (float)(MS * MS);
+  float res = 0.f;
+  for (int i = threadIdx.x; i < rows * MS; i += blockDim.x) {
+    const int o = q * rows * MS + i;
+    const float2 v = P[o];
+    const float a = ok ? __ldg(&am[o]) : 0.f;
+    const float n2 = v.x * v.x + v.y * v.y;
+    const float mag = sqrtf(n2);
+    const float d = mag - a;
+    res += d * d;
+    P[o] = n2 > 0.f ? make_float2(v.x * (a / mag) * inv_m2, v.y * (a / mag) * inv_m2) : make_float2(a * inv_m2, 0.f);
+  }
+  const double s = block_sum((double)res, red, threadIdx.x, blockDim.x);
+  if (threadIdx.x == 0) A.part[((size_t)w * A.CL + q) * 2] = ok ? s : 0.0;
+}
+
+// g^0 = conj(Q)(R - Q z_k) into the increments, and the tile's sum of |g^0|^2.
+__global__ void __launch_bounds__(256) grad_kernel(const PrecArgs A) {
+  __shared__ double red[32];
+  const int w = blockIdx.x, q = blockIdx.y, MS = A.MS, rows = MS / A.CL;
+  const int k = A.idx[w];
+  const bool ok = (unsigned)k < (unsigned)A.n_pos;
+  const int pr = ok ? A.pos[2 * k] : 0, pc = ok ? A.pos[2 * k + 1] : 0;
+  const float2* R = A.buf + (size_t)w * MS * MS;
+  float2* out = A.contrib + (size_t)w * MS * MS;
+  float gn = 0.f;
+  for (int i = threadIdx.x; i < rows * MS; i += blockDim.x) {
+    const int r = q * rows + i / MS, c = i % MS, o = r * MS + c;
+    float2 g = make_float2(0.f, 0.f);
+    if (ok) {
+      const float2 zz = A.z[(size_t)(pr + r) * A.n_cols + pc + c];
+      const float2 qq = __ldg(&A.Q[o]);
+      const float2 rr = R[o];
+      const float2 d = make_float2(rr.x - (qq.x * zz.x - qq.y * zz.y), rr.y - (qq.x * zz.y + qq.y * zz.x));
+      g = make_float2(qq.x * d.x + qq.y * d.y, qq.x * d.y - qq.y * d.x);
+    }
+    gn += g.x * g.x + g.y * g.y;
+    out[o] = g;
+  }
+  const double s = block_sum((double)gn, red, threadIdx.x, blockDim.x);
+  if (threadIdx.x == 0) A.part[((size_t)w * A.CL + q) * 2 + 1] = ok ? s : 0.0;
+}

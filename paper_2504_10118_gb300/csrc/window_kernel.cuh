@@ -34,8 +34,11 @@ struct StepArgs {
   float* pa2;         // probe step only: [windows][MS][MS] |z_k|^2
   double* pmax;       // probe step only: [windows][CL] block maxima of |z_k|^2
   int* err;           // bit 0: window index out of range
+  int grad_only;      // step: write g^0 = conj(Q)(R_k - Q z_k) as the increments and skip the V-cycle
 };
 
+// Sum over the block (a fixed order: warp shuffles, then the warps in order);
+// the total is returned in thread 0 only.
 __device__ __forceinline__ double block_sum(double v, double* red, int tid, int nthreads) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -259,224 +262,11 @@ __device__ __forceinline__ void vcycle(const float2* Y, float2* lvl, const float
   }
 }
 
-// The work of one window slot `win` of a launch: one cluster of Geo<MS>::CL
-// blocks, each with Geo<MS>::T threads and Geo<MS>::SMEM bytes of dynamic
-// shared memory.
-template <int MS, int MODE>
-__device__ __forceinline__ void window_body(const StepArgs& A, const int win) {
-  using Gm = Geo<MS>;
-  constexpr int E = Gm::E, G = Gm::G, CL = Gm::CL, SLAB = Gm::SLAB, T = Gm::T, M = Gm::M;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* X = reinterpret_cast<float2*>(smem_raw);  // row slab
-  float2* Y = X + Gm::XN;                            // column slab
-  float2* tws = Y + Gm::XN;
-  float2* lvl = tws + MS;
-  double* red = reinterpret_cast<double*>(lvl + Gm::LVL);  // block_sum scratch
-
-  const int tid = threadIdx.x;
-  int q = 0;
-  if constexpr (CL > 1) q = (int)cg::this_cluster().block_rank();
-  for (int i = tid; i < MS; i += T) tws[i] = A.tw[i];
-  const int k = A.idx[win];
-  if ((unsigned)k >= (unsigned)A.n_pos) {
-    if (tid == 0 && q == 0) {
-      atomicOr(A.err, 1);
-      if (MODE == kStep) A.corner[win] = make_int2(-(1 << 30), -(1 << 30));
-    }
-    return;  // uniform across the cluster
-  }
-  const int pr = A.pos[2 * k], pc = A.pos[2 * k + 1];
-  if (MODE == kStep && tid == 0 && q == 0) A.corner[win] = make_int2(pr, pc);
-  const float2* zk = A.z + (size_t)pr * A.n_cols + pc;
-  __syncthreads();
-
-  const bool act = tid < Gm::LANES;
-  const int lam = act ? tid / G : 0, g = tid % G;
-  const int line = q * SLAB + lam;  // column (passes A, C) or row (pass B) of this lane group
-
-  // slab geometry of the row-coalesced passes: lane gam of a row of the
-  // block's column slab, rows r0, r0 + RSTEP, ...
-  constexpr int RSTEP = T / SLAB, RPT = MS / RSTEP;
-  const int gam = tid % SLAB, r0 = tid / SLAB;
-  const int cgl = q * SLAB + gam;
-
-  // ---- pass A: exit wave psi = Q z_k gathered row by row into Y, then the
-  // column FFTs; results go to the row owners' X
-  {
-    float2 pv[RPT];
-#pragma unroll
-    for (int i = 0; i < RPT; ++i) {
-      const int r = r0 + RSTEP * i;
-      pv[i] = cmul(__ldg(&A.Q[r * MS + cgl]), __ldg(&zk[(size_t)r * A.n_cols + cgl]));
-    }
-#pragma unroll
-    for (int i = 0; i < RPT; ++i) Y[yi<MS>(r0 + RSTEP * i, gam)] = pv[i];
-    __syncthreads();
-    float2 x[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) x[e] = act ? Y[yi<MS>(g + G * e, lam)] : f2(0.f, 0.f);
-    __syncwarp();
-    line_fwd<MS, false>(x, g, act, [&](int sl) -> float2& { return Y[yi<MS>(sl, lam)]; }, tws);
-#pragma unroll
-    for (int j = 0; j < E / G; ++j)
-#pragma unroll
-      for (int k2 = 0; k2 < G; ++k2) {
-        const int kr = g + G * j + E * k2;
-        float2* dst = peer<CL>(X, (E * k2) / SLAB);
-        if (act) dst[xi<MS>(kr % SLAB, line)] = x[j * G + k2];
-      }
-  }
-  window_arrive<CL>();
-  // amplitudes of this block's rows, fetched while the other blocks finish
-  float av[E];
-  if constexpr (MODE != kSim) {
-    const float* ampr = A.amp + (size_t)k * M + line * MS;
-#pragma unroll
-    for (int j = 0; j < E / G; ++j)
-#pragma unroll
-      for (int k2 = 0; k2 < G; ++k2) av[j * G + k2] = act ? __ldg(&ampr[g + G * j + E * k2]) : 0.f;
-  }
-  window_wait<CL>();
-
-  // ---- pass B: row FFTs, modulus projection, inverse row FFTs; results go
-  // to the column owners' Y
-  float res = 0.f;
-  {
-    const int kr = line;
-    float2 x[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) x[e] = act ? X[xi<MS>(lam, g + G * e)] : f2(0.f, 0.f);
-    __syncwarp();
-    line_fwd<MS, false>(x, g, act, [&](int sl) -> float2& { return X[xi<MS>(lam, sl)]; }, tws);
-    if constexpr (MODE == kSim) {
-      float* outk = A.out_int + (size_t)k * M + kr * MS;
-#pragma unroll
-      for (int j = 0; j < E / G; ++j)
-#pragma unroll
-        for (int k2 = 0; k2 < G; ++k2) {
-          const float2 P = x[j * G + k2];
-          if (act) outk[g + G * j + E * k2] = P.x * P.x + P.y * P.y;
-        }
-      return;  // no block reads another block's memory after the barrier above
-    } else {
-      constexpr float inv_m = 1.0f / float(M);
-#pragma unroll
-      for (int i = 0; i < E; ++i) {
-        const float a = av[i];
-        const float2 P = x[i];
-        const float p2 = P.x * P.x + P.y * P.y;
-        float mag;
-        float2 Pp;
-        if (p2 > 0.f) {
-          const float rs = rsqrtf(p2);
-          mag = p2 * rs;
-          const float sc = a * rs * inv_m;
-          Pp = f2(P.x * sc, P.y * sc);
-        } else {
-          mag = 0.f;
-          Pp = f2(a * inv_m, 0.f);
-        }
-        const float dlt = mag - a;
-        res += dlt * dlt;
-        x[i] = Pp;
-      }
-      line_inv<MS>(x, g, act, [&](int sl) -> float2& { return X[xi<MS>(lam, sl)]; }, tws);
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int c = g + G * e;
-        float2* dst = peer<CL>(Y, (G * e) / SLAB);
-        if (act) dst[yi<MS>(kr, c % SLAB)] = x[e];
-      }
-    }
-  }
-  if constexpr (MODE != kSim) {
-    window_arrive<CL>();
-    // the exit wave again, row by row, while the other blocks finish pass B;
-    // it is parked in X (free once every block of the window is past pass B)
-    float2 pv[RPT];
-#pragma unroll
-    for (int i = 0; i < RPT; ++i) {
-      const int r = r0 + RSTEP * i;
-      pv[i] = cmul(__ldg(&A.Q[r * MS + cgl]), __ldg(&zk[(size_t)r * A.n_cols + cgl]));
-    }
-    window_wait<CL>();
-#pragma unroll
-    for (int i = 0; i < RPT; ++i) X[yi<MS>(r0 + RSTEP * i, gam)] = pv[i];
-
-    // ---- pass C: inverse column FFTs; R_k into Y
-    {
-      float2 x[E];
-#pragma unroll
-      for (int j = 0; j < E / G; ++j)
-#pragma unroll
-        for (int k2 = 0; k2 < G; ++k2) x[j * G + k2] = act ? Y[yi<MS>(g + G * j + E * k2, lam)] : f2(0.f, 0.f);
-      __syncwarp();
-      line_inv<MS>(x, g, act, [&](int sl) -> float2& { return Y[yi<MS>(sl, lam)]; }, tws);
-#pragma unroll
-      for (int e = 0; e < E; ++e)
-        if (act) Y[yi<MS>(g + G * e, lam)] = x[e];
-    }
-    __syncthreads();
-
-    // ---- g^0 = conj(Q)(R_k - psi) over the slab, lane = column; into Y, or
-    // straight to the increments for one level
-    float gn2 = 0.f, amax = 0.f;
-    float2* out = A.contrib + (size_t)win * M;
-    const bool direct = (MODE == kStep) && A.levels == 1;
-    {
-      float2 qv[RPT];
-#pragma unroll
-      for (int i = 0; i < RPT; ++i) qv[i] = __ldg(&A.Q[(r0 + RSTEP * i) * MS + cgl]);
-#pragma unroll
-      for (int i = 0; i < RPT; ++i) {
-        const int r = r0 + RSTEP * i;
-        const int o = yi<MS>(r, gam);
-        const float2 rho = csub(Y[o], X[o]);
-        const float2 gg = cmul_cj(qv[i], rho);
-        gn2 += gg.x * gg.x + gg.y * gg.y;
-        if (MODE == kStep) {
-          if (A.pnum) {
-            // the probe step's window terms (same R_k and z_k)
-            const float2 zz = __ldg(&zk[(size_t)r * A.n_cols + cgl]);
-            const float a2 = zz.x * zz.x + zz.y * zz.y;
-            A.pnum[(size_t)win * M + r * MS + cgl] = cmul_cj(zz, rho);
-            A.pa2[(size_t)win * M + r * MS + cgl] = a2;
-            amax = fmaxf(amax, a2);
-          }
-          if (direct)
-            out[r * MS + cgl] = gg;
-          else
-            Y[o] = gg;
-        }
-      }
-    }
-    if (MODE == kStep && A.pnum) {
-      const double bm = block_max((double)amax, red, tid, T);
-      if (tid == 0) A.pmax[win * CL + q] = bm;
-    }
-
-    // block partials of the window's two sums (float64); the kernel that
-    // follows combines them in block order
-    const double rs = block_sum((double)res, red, tid, T);
-    const double gs = block_sum((double)gn2, red, tid, T);
-    if (tid == 0) {
-      A.part[(size_t)(win * CL + q) * 2] = rs;
-      A.part[(size_t)(win * CL + q) * 2 + 1] = gs;
-    }
-    if (MODE != kStep || direct) return;
-
-    // ---- pass D: MAGPS V-cycle (levels >= 2) on the column slab
-    if (A.levels == 2)
-      vcycle<MS, 1>(Y, lvl, A.pyr, A.levels, q, out, tid);
-    else
-      vcycle<MS, 2>(Y, lvl, A.pyr, A.levels, q, out, tid);
-  }
-}
-
 // One problem: window slot = cluster index (grid = windows * CL).
 template <int MS, int MODE>
 __global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel(StepArgs A) {
-  window_body<MS, MODE>(A, blockIdx.x / Geo<MS>::CL);
+  const int win = blockIdx.x / Geo<MS>::CL;
+#include "window_body.inc"
 }
 
 // Several problems in one launch: cluster c works on window slot map[c].y of
@@ -484,6 +274,11 @@ __global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel
 template <int MS, int MODE>
 __global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS)
     window_kernel_batched(const StepArgs* __restrict__ table, const int2* __restrict__ map) {
-  const int2 e = map[blockIdx.x / Geo<MS>::CL];
-  window_body<MS, MODE>(table[e.x], e.y);
+  __shared__ StepArgs args;
+  const int2 ent = map[blockIdx.x / Geo<MS>::CL];
+  if (threadIdx.x == 0) args = table[ent.x];
+  __syncthreads();
+  const StepArgs& A = args;
+  const int win = ent.y;
+#include "window_body.inc"
 }

@@ -19,7 +19,8 @@ ROOT = os.path.dirname(HERE)
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libmagpie.so")
 SOURCES = [os.path.join(HERE, "csrc", "magpie.cu")]
-DEPENDS = [os.path.join(HERE, "csrc", f) for f in ("fft_lines.cuh", "window_kernel.cuh")]
+DEPENDS = [os.path.join(HERE, "csrc", f) for f in ("fft_lines.cuh", "window_kernel.cuh", "window_body.inc",
+                                                   "learned.cuh", "precision.cuh")]
 HEADER = os.path.join(ROOT, "include", "magpie.h")
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared"]
@@ -85,6 +86,21 @@ def lib() -> ctypes.CDLL:
             "magpie_group_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(vp), i32, vp]),
             "magpie_group_sweep": (ctypes.c_int, [vp, ctypes.POINTER(vp)]),
             "magpie_group_destroy": (None, [vp]),
+            "magpie_cnn_param_count": (i32, []),
+            "magpie_cnn_create": (ctypes.c_int, [ctypes.POINTER(vp), i32, i32, vp]),
+            "magpie_cnn_destroy": (None, [vp]),
+            "magpie_cnn_set_params": (ctypes.c_int, [vp, vp]),
+            "magpie_cnn_get_params": (ctypes.c_int, [vp, vp]),
+            "magpie_cnn_forward": (ctypes.c_int, [vp, vp, i32, vp]),
+            "magpie_cnn_backward": (ctypes.c_int, [vp, vp, vp]),
+            "magpie_cnn_train_step": (ctypes.c_int, [vp, vp, vp, vp, i32, ctypes.c_float, vp]),
+            "magpie_coarse_state": (ctypes.c_int, [vp, vp, i32, vp, vp]),
+            "magpie_gather_windows": (ctypes.c_int, [vp, vp, i32, vp]),
+            "magpie_attach_cnn": (ctypes.c_int, [vp, vp]),
+            "magpie_learned_stats": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+            "magpie_learned_window_values": (ctypes.c_int, [vp, i32, vp, vp]),
+            "magpie_set_precision": (ctypes.c_int, [vp, i32]),
+            "magpie_dft2_tc": (ctypes.c_int, [vp, vp, i32, i32, i32, vp]),
             "magpie_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             "magpie_last_error": (ctypes.c_char_p, []),
             "magpie_version": (ctypes.c_int, []),
@@ -281,6 +297,117 @@ def magpie_group_sweep(group: Group, orders) -> None:
 
 def magpie_group_destroy(group: Group) -> None:
     group.close()
+
+
+# ----------------------------------------------------------- precision form
+def magpie_set_precision(ctx: Context, mode: int) -> None:
+    _check(lib().magpie_set_precision(ctx.handle, int(mode)))
+
+
+def magpie_dft2_tc(x: torch.Tensor, inverse: bool = False) -> torch.Tensor:
+    """2-D DFTs of x [count][m][m] (complex64, CUDA) by the tensor-core path."""
+    count, m, _ = x.shape
+    out = torch.empty_like(x)
+    _check(lib().magpie_dft2_tc(_dev(x, torch.complex64, count * m * m, "x"), out.data_ptr(), m, count,
+                                int(bool(inverse)), _stream()))
+    return out
+
+
+# ------------------------------------------------- learned coarse correction
+def magpie_cnn_param_count() -> int:
+    return lib().magpie_cnn_param_count()
+
+
+class Cnn:
+    """Owns a magpie_cnn (the network of the learned coarse correction)."""
+
+    def __init__(self, h: int, max_batch: int):
+        self.h, self.max_batch = h, max_batch
+        self.P = magpie_cnn_param_count()
+        hd = ctypes.c_void_p()
+        _check(lib().magpie_cnn_create(ctypes.byref(hd), h, max_batch, _stream()))
+        self.handle = hd
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().magpie_cnn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def magpie_cnn_create(h: int, max_batch: int) -> Cnn:
+    return Cnn(h, max_batch)
+
+
+def magpie_cnn_destroy(cnn: Cnn) -> None:
+    cnn.close()
+
+
+def magpie_cnn_set_params(cnn: Cnn, theta: torch.Tensor) -> None:
+    _check(lib().magpie_cnn_set_params(cnn.handle, _dev(theta, torch.float32, cnn.P, "theta")))
+
+
+def magpie_cnn_get_params(cnn: Cnn, theta: torch.Tensor) -> None:
+    _check(lib().magpie_cnn_get_params(cnn.handle, _dev(theta, torch.float32, cnn.P, "theta")))
+
+
+def magpie_cnn_forward(cnn: Cnn, x: torch.Tensor, y: torch.Tensor) -> None:
+    b = x.shape[0]
+    hh = cnn.h * cnn.h
+    _check(lib().magpie_cnn_forward(cnn.handle, _dev(x, torch.float32, b * hh * 4, "x"), b,
+                                    _dev(y, torch.float32, b * hh * 2, "y")))
+
+
+def magpie_cnn_backward(cnn: Cnn, dy: torch.Tensor, grad: torch.Tensor) -> None:
+    _check(lib().magpie_cnn_backward(cnn.handle, _dev(dy, torch.float32, dy.numel(), "dy"),
+                                     _dev(grad, torch.float32, cnn.P, "grad")))
+
+
+def magpie_cnn_train_step(cnn: Cnn, x0: torch.Tensor, zh: torch.Tensor, scale: torch.Tensor, lr: float,
+                          loss: torch.Tensor) -> None:
+    b = x0.shape[0]
+    hh = cnn.h * cnn.h
+    _check(lib().magpie_cnn_train_step(cnn.handle, _dev(x0, torch.float32, b * hh * 4, "x0"),
+                                       _dev(zh, torch.float32, b * hh * 2, "zh"),
+                                       _dev(scale, torch.float32, b, "scale"), b, float(lr),
+                                       _dev(loss, torch.float64, 1, "loss")))
+
+
+def magpie_coarse_state(ctx: Context, idx: torch.Tensor, x: torch.Tensor, scale: torch.Tensor) -> None:
+    n = idx.numel()
+    h = ctx.params.m >> (ctx.params.levels - 1)
+    _check(lib().magpie_coarse_state(ctx.handle, _dev(idx, torch.int32, n, "idx"), n,
+                                     _dev(x, torch.float32, n * h * h * 4, "x"), _dev(scale, torch.float32, n, "scale")))
+
+
+def magpie_gather_windows(ctx: Context, idx: torch.Tensor, patches: torch.Tensor) -> None:
+    n = idx.numel()
+    m = ctx.params.m
+    _check(lib().magpie_gather_windows(ctx.handle, _dev(idx, torch.int32, n, "idx"), n,
+                                       _dev(patches, torch.complex64, n * m * m, "patches")))
+
+
+def magpie_attach_cnn(ctx: Context, cnn) -> None:
+    _check(lib().magpie_attach_cnn(ctx.handle, cnn.handle if cnn is not None else None))
+    ctx._cnn = cnn  # alive while attached
+
+
+def magpie_learned_stats(ctx: Context):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().magpie_learned_stats(ctx.handle, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def magpie_learned_window_values(ctx: Context, count: int):
+    acc = (ctypes.c_int32 * count)()
+    mg = (ctypes.c_double * count)()
+    _check(lib().magpie_learned_window_values(ctx.handle, count, acc, mg))
+    return list(acc), list(mg)
 
 
 def magpie_strerror(code: int) -> str:

@@ -152,3 +152,18 @@ def make_problem_seeded(w: Workload, seed: int):
     probe = make_probe(w.m)
     pos = make_raster(w.n, w.m, w.grid, w.step, w.jitter, seed=seed + 2)
     return z_true, probe, pos
+
+
+def make_cnn_params(layers, seed: int = 7, zero_last: bool = True) -> np.ndarray:
+    """float32 initial parameters of a stack of 3x3 convolutions given as
+    (c_in, c_out) pairs: per layer, weights [c_out][3][3][c_in] drawn
+    N(0, 2 / (9 c_in)) (He initialisation) then c_out zero biases.  With
+    `zero_last` the last layer's weights are zero too."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for i, (ci, co) in enumerate(layers):
+        w = rng.normal(0.0, math.sqrt(2.0 / (9 * ci)), co * 9 * ci)
+        if zero_last and i == len(layers) - 1:
+            w[:] = 0.0
+        parts += [w, np.zeros(co)]
+    return np.concatenate(parts).astype(np.float32)

@@ -117,3 +117,28 @@ def test_null_arguments(L):
     assert L.magpie_group_sweep(None, None) == magpie.EINVAL
     L.magpie_group_destroy(None)
     L.magpie_destroy(None)
+
+
+def test_learned_and_precision_entry_points_without_a_gpu(L):
+    """Argument checks that run before any device work."""
+    assert L.magpie_cnn_param_count() == 980002
+    h = ctypes.c_void_p()
+    assert L.magpie_cnn_create(None, 16, 8, None) == magpie.EINVAL
+    assert L.magpie_cnn_create(ctypes.byref(h), 12, 8, None) == magpie.EINVAL   # h not 8/16/32/64
+    assert L.magpie_cnn_create(ctypes.byref(h), 16, 0, None) == magpie.EINVAL   # empty batch
+    assert L.magpie_cnn_set_params(None, None) == magpie.EINVAL
+    assert L.magpie_cnn_forward(None, None, 1, None) == magpie.EINVAL
+    assert L.magpie_cnn_backward(None, None, None) == magpie.EINVAL
+    assert L.magpie_cnn_train_step(None, None, None, None, 1, 1e-3, None) == magpie.EINVAL
+    assert L.magpie_coarse_state(None, None, 1, None, None) == magpie.EINVAL
+    assert L.magpie_gather_windows(None, None, 1, None) == magpie.EINVAL
+    assert L.magpie_attach_cnn(None, None) == magpie.EINVAL
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    assert L.magpie_learned_stats(None, ctypes.byref(a), ctypes.byref(b)) == magpie.EINVAL
+    assert L.magpie_learned_window_values(None, 1, None, None) == magpie.EINVAL
+    assert L.magpie_set_precision(None, 1) == magpie.EINVAL
+    assert L.magpie_dft2_tc(None, None, 64, 1, 0, None) == magpie.EINVAL
+    x = ctypes.c_void_p(16)
+    assert L.magpie_dft2_tc(x, x, 32, 1, 0, None) == magpie.EUNSUPPORTED      # m not 64/128/256
+    assert L.magpie_dft2_tc(x, x, 64, 0, 0, None) == magpie.EINVAL            # no windows
+    L.magpie_cnn_destroy(None)

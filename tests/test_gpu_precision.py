@@ -1,0 +1,148 @@
+"""GPU parity of the precision form (tensor-core BF16 hi+lo DFTs) against the
+FP64 oracle: the transforms themselves, single minibatch steps at small and
+full window size, and a run of sweeps.  Every check prints its error."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import magpie_oracle as O
+from paper_2504_10118_gb300 import magpie, synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    magpie.build()
+    magpie.lib()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+@pytest.mark.parametrize("m", [64, 128, 256])
+def test_dft2_matches_library_fft(m):
+    """Forward and conjugate 2-D DFTs of random windows against numpy's FFT in
+    float64: relative error per window within the hi+lo BF16 bound (a few
+    2^-16 per product, four products deep)."""
+    rng = np.random.default_rng(m)
+    x = (rng.normal(size=(4, m, m)) + 1j * rng.normal(size=(4, m, m))).astype(np.complex64)
+    xd = torch.from_numpy(x).to(DEV)
+    X = magpie.magpie_dft2_tc(xd).cpu().numpy()
+    Xi = magpie.magpie_dft2_tc(xd, inverse=True).cpu().numpy()
+    for c in range(4):
+        ref = O.fft2(x[c].astype(np.complex128))
+        refi = O.ifft2(x[c].astype(np.complex128)) * m * m
+        e, ei = rel(X[c], ref), rel(Xi[c], refi)
+        print(f"m={m} window {c}: forward {e:.2e} inverse {ei:.2e}")
+        assert e < 4e-5 and ei < 4e-5
+
+
+def small_problem(levels):
+    """n = 160, m = 64, 5 x 5 raster at step 20 +-1, noise-free."""
+    n, m = 160, 64
+    z_true = synth.make_object(n, seed=1)
+    Q = synth.make_probe(m)
+    pos = synth.make_raster(n, m, 5, 20, 1, seed=3)
+    d = O.forward_intensities(z_true, Q, pos)
+    rng = np.random.default_rng(8)
+    z0 = np.ones((n, n)) + 0.05 * (rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n)))
+    z0 = z0.astype(np.complex64).astype(np.complex128)
+    return n, m, Q, pos, d, z0
+
+
+def make_ctx(n, m, Q, pos, d, z0, levels, minibatch, alpha=0.1):
+    zt = torch.from_numpy(z0.astype(np.complex64)).to(DEV)
+    p = magpie.magpie_params_of(n, n, m, len(pos), levels, minibatch, alpha)
+    ctx = magpie.magpie_create(p, zt, torch.from_numpy(Q.astype(np.complex64)).to(DEV),
+                               torch.from_numpy(pos.astype(np.int32)).to(DEV),
+                               torch.from_numpy(d.astype(np.float32)).to(DEV))
+    magpie.magpie_set_precision(ctx, 1)
+    return ctx, zt
+
+
+@pytest.mark.parametrize("levels", [1, 3])
+def test_precision_step_matches_oracle(levels):
+    n, m, Q, pos, d, z0 = small_problem(levels)
+    ctx, zt = make_ctx(n, m, Q, pos, d, z0, levels, 8)
+    batch = np.array([3, 7, 11, 12, 13, 17, 21, 24], dtype=np.int32)
+    magpie.magpie_step(ctx, torch.from_numpy(batch).to(DEV))
+    u = O.rpie_regulariser(Q, 0.1)
+    zo = O.minibatch_step(z0, Q, pos, d, u, levels, list(batch))
+    zg = zt.cpu().numpy()
+    e, de = rel(zg, zo), rel(zg - z0, zo - z0)
+    print(f"levels={levels}: object {e:.2e}, increment {de:.2e}")
+    assert e < 1e-5 and de < 1e-4
+    phi, gn = magpie.magpie_window_values(ctx)
+    for k in batch:
+        zk = O.extract(z0, pos[k], m)
+        assert abs(phi[k].item() - O.objective_k(zk, Q, d[k])) < 1e-4 * O.objective_k(zk, Q, d[k])
+
+
+def fp32_ctx(n, m, Q, pos, d, z0, levels, minibatch, alpha=0.1):
+    zt = torch.from_numpy(z0.astype(np.complex64)).to(DEV)
+    p = magpie.magpie_params_of(n, n, m, len(pos), levels, minibatch, alpha)
+    ctx = magpie.magpie_create(p, zt, torch.from_numpy(Q.astype(np.complex64)).to(DEV),
+                               torch.from_numpy(pos.astype(np.int32)).to(DEV),
+                               torch.from_numpy(d.astype(np.float32)).to(DEV))
+    return ctx, zt
+
+
+# The tensor-core transforms carry a relative error of about 6e-6 (measured
+# above); FP32 radix-16 FFTs about 3e-7.  Where the projection amplifies
+# rounding (|Psi| tiny against sqrt(d), e.g. a flat start), both paths' errors
+# grow by the same conditioning factor, so the precision form is held to 20x
+# the FP32 path's error on the same step, and to the FP32 bar where that is
+# larger.
+RATIO = 20.0
+
+
+@pytest.mark.parametrize("start", ["near", "flat"])
+def test_precision_full_size_step(start):
+    """The precision workload's sizes (n = 1024, m = 256, 4 levels): one 64-window
+    minibatch step against the oracle (the context holds just those windows),
+    from a state near the object and from the flat start z = 1."""
+    w = synth.WORKLOADS["precision"]
+    z_true, Q, pos = synth.make_problem(w)
+    batch = synth.make_order(w.n_pos, 0)[:w.minibatch]
+    sub = pos[batch]
+    d = O.forward_intensities(z_true, Q, sub)
+    if start == "flat":
+        z0 = np.ones((w.n, w.n), dtype=np.complex128)
+    else:
+        rng = np.random.default_rng(9)
+        z0 = z_true * (1 + 0.02 * (rng.normal(size=z_true.shape) + 1j * rng.normal(size=z_true.shape)))
+        z0 = z0.astype(np.complex64).astype(np.complex128)
+    ctx, zt = make_ctx(w.n, w.m, Q, sub, d, z0, w.levels, w.minibatch)
+    ctx32, z32 = fp32_ctx(w.n, w.m, Q, sub, d, z0, w.levels, w.minibatch)
+    idx = torch.arange(w.minibatch, dtype=torch.int32, device=DEV)
+    magpie.magpie_step(ctx, idx)
+    magpie.magpie_step(ctx32, idx)
+    u = O.rpie_regulariser(Q, w.alpha)
+    zo = O.minibatch_step(z0, Q, sub, d, u, w.levels, list(range(w.minibatch)))
+    e_tc, e_32 = rel(zt.cpu().numpy(), zo), rel(z32.cpu().numpy(), zo)
+    print(f"n=1024 m=256 L=4 B=64, {start} start: object error tensor-core {e_tc:.2e}, FP32 FFT {e_32:.2e}")
+    assert e_tc < max(1e-5, RATIO * e_32)
+
+
+def test_precision_sweeps_track_oracle():
+    """Twenty sweeps from the same start: NRMSE between the GPU and the oracle
+    iterates, against that of the FP32 FFT path."""
+    n, m, Q, pos, d, z0 = small_problem(3)
+    ctx, zt = make_ctx(n, m, Q, pos, d, z0, 3, 8)
+    ctx32, z32 = fp32_ctx(n, m, Q, pos, d, z0, 3, 8)
+    u = O.rpie_regulariser(Q, 0.1)
+    zo = z0.copy()
+    for s in range(20):
+        order = synth.make_order(len(pos), s)
+        magpie.magpie_sweep(ctx, torch.from_numpy(order).to(DEV))
+        magpie.magpie_sweep(ctx32, torch.from_numpy(order).to(DEV))
+        zo = O.sweep(zo, Q, pos, d, u, 3, order, 8)
+    mask = O.illuminated_mask(Q, pos, zo.shape)
+    e_tc = O.nrmse(zt.cpu().numpy(), zo, mask)
+    e_32 = O.nrmse(z32.cpu().numpy(), zo, mask)
+    print(f"20 sweeps: NRMSE vs oracle tensor-core {e_tc:.2e}, FP32 FFT {e_32:.2e}")
+    assert e_tc < max(1e-4, RATIO * e_32)
