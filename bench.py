@@ -38,7 +38,7 @@ SMS = 152
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "window_kernel_m128_mid.txt")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2504_10118_gb300", "csrc", f)
-                  for f in ("fft_lines.cuh", "window_kernel.cuh")]
+                  for f in ("fft_lines.cuh", "window_kernel.cuh", "window_body.inc")]
 
 
 def flops_per_window(m: int) -> float:

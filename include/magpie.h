@@ -217,6 +217,19 @@ int magpie_group_sweep(magpie_group* group, const int32_t* const* orders);
 void magpie_group_destroy(magpie_group* group);
 
 /*
+ * The group's autotuner.  magpie_group_create times, for every window side m
+ * present in the first batched step, the batched window kernel under each of
+ * its two candidate register bounds (blocks per SM: the default and one
+ * alternative) on that step's own windows, and uses the faster in every
+ * group sweep.  magpie_group_tuning reports, for m = 8, 16, .., 256 (index
+ * i, m = 8 << i), the bound in use (minb[i]) and the measured ms per launch
+ * of the two candidates (ms[2i], ms[2i+1]; 0 where not measured; HOST
+ * arrays of 6 and 12).  magpie_group_set_minb forces a candidate.
+ */
+int magpie_group_tuning(magpie_group* group, int32_t* minb, float* ms);
+int magpie_group_set_minb(magpie_group* group, int32_t m, int32_t minb);
+
+/*
  * Learned coarse-level correction.  The paper has no network: its Algorithm
  * MAGPS ends the recursion on the coarsest grid (side h = m / 2^(levels-1))
  * with one proximal step e_plain = g_H / w_H, g_H = conj(Q_H)(R_H - Q_H z_H)
@@ -317,6 +330,23 @@ int magpie_set_precision(magpie_ctx* ctx, int32_t mode);
    the precision form's tensor-core path.  in == out is allowed.  Allocates a
    few KiB of tables per call; synchronous. */
 int magpie_dft2_tc(const void* in, void* out, int32_t m, int32_t count, int32_t inverse, void* stream);
+
+/*
+ * Variants from the paper, off by default (flags = 0), for later steps and
+ * sweeps of ctx:
+ *   bit 0  the MG/OPT correction term (Algorithm MG/OPT): every coarse
+ *          problem of the V-cycle is the paper's coarse surrogate minus
+ *          Re<v_H, z_H>, v_H = grad f_H(z_H) - I_h^H grad f_h(z_h), so the
+ *          coarse residual gradient is the plain restriction of the fine one
+ *          (needs update_probe = 0).
+ *   bit 1  the phase rule of Eq. (specification): where a window's spectrum
+ *          entry is exactly 0, the phase of that entry at the window's
+ *          previous visit is used (0 on the first visit after this call;
+ *          setting the bit again restarts the history).  Keeps one complex
+ *          value per window pixel (8 n_pos m^2 bytes).
+ * Contexts with bit 1 set cannot join a group.
+ */
+int magpie_set_variant(magpie_ctx* ctx, int32_t flags);
 
 /* Static name of an error code; never NULL. */
 const char* magpie_strerror(int code);

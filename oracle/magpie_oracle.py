@@ -29,6 +29,13 @@ notes of the repository):
     u_Q,k = beta (max |z_k|^2 - |z_k|^2), all windows of the minibatch from the
     same (z, Q).  -- parity pinned only as the exact minimiser of that
     proximal surrogate and by full-batch monotone descent
+  * Variants (off by default): the MG/OPT correction term of Algorithm
+    MG/OPT on every coarse problem (`magps_mgopt`), and the phase rule of
+    Eq. (specification) across visits of a window
+    (`minibatch_step_variant`).  -- pinned by their special cases (no
+    effect where the probe is constant on every 2x2 bin, resp. where no
+    spectrum entry is exactly 0) and by the first-order matching the
+    correction term enforces
   * Minibatch step: the paper updates one window at a time (Algorithm
     MAGPIE).  For a minibatch every window starts from the same z; the
     increments Delta_k are combined as z <- z + sum_k P_k^T (w . Delta_k) /
@@ -225,6 +232,70 @@ def magps(zk, Q, Rk, u, levels: int):
     eH = zH_hat - zH
     z_tilde = zk + prolong(eH)
     return proximal_step(z_tilde, Q, Rk, u)
+
+
+def magps_mgopt(zk, Q, Rk, u, levels: int, shift=None):
+    """Algorithm MAGPS with the MG/OPT correction term of Algorithm MG/OPT
+    (the variant the paper describes before proposing its consistent coarse
+    surrogate): every coarse problem is the paper's coarse surrogate minus
+    Re<v_H, z_H>, v_H = grad f_H(z_H) - I_h^H grad f_h(z_h), which makes the
+    coarse gradient at z_H equal to the restricted fine gradient.  `shift` is
+    the linear term this level inherited (the negative gradient of the level's
+    objective at zk is conj(Q)(R - Q zk) + shift); each proximal step moves by
+    that corrected residual gradient over u + |Q|^2."""
+    if shift is None:
+        shift = np.zeros_like(zk)
+
+    def step(z):
+        return z + safe_div(np.conj(Q) * (Rk - Q * z) + shift, u + np.abs(Q) ** 2)
+
+    if levels == 1:
+        return step(zk)
+    QH, Wz, WR, Wu = coarse_weights(Q)
+    zH = restrict(Wz * zk)
+    RH = restrict(WR * Rk)
+    uH = Wu * restrict(u)
+    g_fine = np.conj(Q) * (Rk - Q * zk) + shift
+    shift_H = restrict(g_fine) - np.conj(QH) * (RH - QH * zH)
+    zH_hat = magps_mgopt(zH, QH, RH, uH, levels - 1, shift_H)
+    return step(zk + prolong(zH_hat - zH))
+
+
+def revised_exit_wave_recycled(zk, Q, dk, prev_theta):
+    """R_k with the phase rule of Eq. (specification): where F(Q . z_k) is
+    exactly 0 the phase of the window's previous visit is reused (0 on the
+    first visit, prev_theta = None).  Returns R_k and the phases used."""
+    psi = fft2(exit_wave(zk, Q))
+    theta = np.angle(psi)
+    zero = psi == 0
+    theta[zero] = 0.0 if prev_theta is None else prev_theta[zero]
+    return ifft2(np.sqrt(dk) * np.exp(1j * theta)), theta
+
+
+def minibatch_step_variant(z, Q, positions, d, u, levels, batch, mgopt: bool = False, phases=None):
+    """minibatch_step with the paper's variants switched on: the MG/OPT
+    correction term (magps_mgopt) and/or the phase rule of Eq.
+    (specification), `phases` a dict window -> phases of its last visit,
+    updated in place (None: theta(0) = 0 at every visit)."""
+    z = np.asarray(z, dtype=np.complex128)
+    m = Q.shape[0]
+    w = u + np.abs(Q) ** 2
+    num = np.zeros(z.shape, dtype=np.complex128)
+    den = np.zeros(z.shape, dtype=np.float64)
+    for k in batch:
+        r, c = positions[k]
+        zk = z[r:r + m, c:c + m]
+        if phases is None:
+            Rk = revised_exit_wave(zk, Q, d[k])
+        else:
+            Rk, phases[k] = revised_exit_wave_recycled(zk, Q, d[k], phases.get(k))
+        zh = magps_mgopt(zk, Q, Rk, u, levels) if mgopt else magps(zk, Q, Rk, u, levels)
+        num[r:r + m, c:c + m] += w * (zh - zk)
+        den[r:r + m, c:c + m] += w
+    out = z.copy()
+    lit = den > 0
+    out[lit] += num[lit] / den[lit]
+    return out
 
 
 def rpie_update(zk, Q, dk, u):

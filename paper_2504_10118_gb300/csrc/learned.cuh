@@ -74,62 +74,87 @@ __global__ void __launch_bounds__(128) conv_fwd_kernel(const ConvFwd a) {
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
 
-  for (int k0 = kbeg; k0 < kend; k0 += BK) {
-    // ---- A: BM rows x 32 k, as 8-element chunks
-    for (int c = tid; c < BM * 4; c += 128) {
-      const int row = c >> 2, qd = c & 3;
-      const int p = bm + row;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (p < Mtot) {
-        const int b = p / HoHo, rem = p - b * HoHo;
-        const int oy = rem / a.Ho, ox = rem - oy * a.Ho;
-        if (vec) {
-          const int tap = k0 / a.Cin, ci0 = k0 - tap * a.Cin + 8 * qd;
-          const int ky = tap / 3, kx = tap - 3 * ky;
-          const int vy = oy * a.stride + ky - 1, vx = ox * a.stride + kx - 1;
-          if (vy >= 0 && vy < Hv && vx >= 0 && vx < Hv) {
-            const int iy = vy / a.up, ix = vx / a.up;
-            v = *reinterpret_cast<const uint4*>(a.in + ((size_t)(b * a.Hin + iy) * a.Hin + ix) * a.Cin + ci0);
-          }
-        } else {
-          bf16 e8[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int k = k0 + 8 * qd + j;
-            bf16 val = __float2bfloat16_rn(0.f);
-            if (k < a.K) {
-              const int tap = k / a.Cin, ci = k - tap * a.Cin;
-              const int ky = tap / 3, kx = tap - 3 * ky;
-              const int vy = oy * a.stride + ky - 1, vx = ox * a.stride + kx - 1;
-              if (vy >= 0 && vy < Hv && vx >= 0 && vx < Hv)
-                val = a.in[((size_t)(b * a.Hin + vy / a.up) * a.Hin + vx / a.up) * a.Cin + ci];
-            }
-            e8[j] = val;
-          }
-          v = *reinterpret_cast<const uint4*>(e8);
+  // global -> registers (the next stage, while the current one is multiplied)
+  constexpr int AC = (BM * 4 + 127) / 128, BC = (BN * 4 + 127) / 128;
+  uint4 ra[AC], rb[BC];
+  auto load_a = [&](int c, int k0) -> uint4 {
+    const int row = c >> 2, qd = c & 3;
+    const int p = bm + row;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (p < Mtot) {
+      const int b = p / HoHo, rem = p - b * HoHo;
+      const int oy = rem / a.Ho, ox = rem - oy * a.Ho;
+      if (vec) {
+        const int tap = k0 / a.Cin, ci0 = k0 - tap * a.Cin + 8 * qd;
+        const int ky = tap / 3, kx = tap - 3 * ky;
+        const int vy = oy * a.stride + ky - 1, vx = ox * a.stride + kx - 1;
+        if (vy >= 0 && vy < Hv && vx >= 0 && vx < Hv) {
+          const int iy = vy / a.up, ix = vx / a.up;
+          v = *reinterpret_cast<const uint4*>(a.in + ((size_t)(b * a.Hin + iy) * a.Hin + ix) * a.Cin + ci0);
         }
+      } else {
+        bf16 e8[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int k = k0 + 8 * qd + j;
+          bf16 val = __float2bfloat16_rn(0.f);
+          if (k < a.K) {
+            const int tap = k / a.Cin, ci = k - tap * a.Cin;
+            const int ky = tap / 3, kx = tap - 3 * ky;
+            const int vy = oy * a.stride + ky - 1, vx = ox * a.stride + kx - 1;
+            if (vy >= 0 && vy < Hv && vx >= 0 && vx < Hv)
+              val = a.in[((size_t)(b * a.Hin + vy / a.up) * a.Hin + vx / a.up) * a.Cin + ci];
+          }
+          e8[j] = val;
+        }
+        v = *reinterpret_cast<const uint4*>(e8);
       }
-      *reinterpret_cast<uint4*>(&As[row * LDS + 8 * qd]) = v;
     }
-    // ---- B: BN output channels x 32 k
-    for (int c = tid; c < BN * 4; c += 128) {
-      const int row = c >> 2, qd = c & 3;
-      const int co = bn + row;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (co < a.Cout) {
-        const bf16* src = a.w + (size_t)co * a.K + k0 + 8 * qd;
-        if (vec) {
-          v = *reinterpret_cast<const uint4*>(src);
-        } else {
-          bf16 e8[8];
+    return v;
+  };
+  auto load_b = [&](int c, int k0) -> uint4 {
+    const int row = c >> 2, qd = c & 3;
+    const int co = bn + row;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (co < a.Cout) {
+      const bf16* src = a.w + (size_t)co * a.K + k0 + 8 * qd;
+      if (vec) {
+        v = *reinterpret_cast<const uint4*>(src);
+      } else {
+        bf16 e8[8];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) e8[j] = (k0 + 8 * qd + j < a.K) ? src[j] : __float2bfloat16_rn(0.f);
-          v = *reinterpret_cast<const uint4*>(e8);
-        }
+        for (int j = 0; j < 8; ++j) e8[j] = (k0 + 8 * qd + j < a.K) ? src[j] : __float2bfloat16_rn(0.f);
+        v = *reinterpret_cast<const uint4*>(e8);
       }
-      *reinterpret_cast<uint4*>(&Bs[row * LDS + 8 * qd]) = v;
+    }
+    return v;
+  };
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int u = 0; u < AC; ++u) {
+      const int c = tid + 128 * u;
+      if (c < BM * 4) ra[u] = load_a(c, k0);
+    }
+#pragma unroll
+    for (int u = 0; u < BC; ++u) {
+      const int c = tid + 128 * u;
+      if (c < BN * 4) rb[u] = load_b(c, k0);
+    }
+  };
+  if (kbeg < kend) fetch(kbeg);
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+#pragma unroll
+    for (int u = 0; u < AC; ++u) {
+      const int c = tid + 128 * u;
+      if (c < BM * 4) *reinterpret_cast<uint4*>(&As[(c >> 2) * LDS + 8 * (c & 3)]) = ra[u];
+    }
+#pragma unroll
+    for (int u = 0; u < BC; ++u) {
+      const int c = tid + 128 * u;
+      if (c < BN * 4) *reinterpret_cast<uint4*>(&Bs[(c >> 2) * LDS + 8 * (c & 3)]) = rb[u];
     }
     __syncthreads();
+    if (k0 + BK < kend) fetch(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; kk += 16) {
       uint32_t af[2][4], bfr[WN][2];
@@ -237,36 +262,72 @@ __global__ void __launch_bounds__(256) conv_bwd_data_kernel(const float* __restr
   }
 }
 
-// Partial weight and bias gradients of one layer over a chunk of output
-// pixels: part[chunk][p], p < Cout 9 Cin the weights, then the biases.
-__global__ void __launch_bounds__(256) conv_bwd_weight_kernel(const float* __restrict__ dz,
-                                                              const bf16* __restrict__ a_in, float* __restrict__ part,
-                                                              int B, int Hin, int Cin, int Cout, int stride, int up,
-                                                              int Ho, int chunk) {
-  const int Wn = Cout * 9 * Cin, P = Wn + Cout;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P) return;
+// Weight and bias gradients of one layer as an FP32 GEMM over the output
+// pixels p: dW[co][k] = sum_p dz[p][co] A[p][k], where A is the forward
+// pass's gather (k < K = 9 Cin) and A[p][K] = 1 (the bias column).  Block:
+// 64 channels x 64 k, 256 threads with 4 x 4 results each, 16 pixels per
+// shared-memory stage; the pixel range is split over gridDim.z (chunks of
+// `chunk` pixels) into partial sums part[z][param] (weights, then biases).
+__global__ void __launch_bounds__(256) conv_wgrad_kernel(const float* __restrict__ dz, const bf16* __restrict__ a_in,
+                                                         float* __restrict__ part, int B, int Hin, int Cin, int Cout,
+                                                         int stride, int up, int Ho, int chunk) {
+  __shared__ float Ds[16][64];
+  __shared__ float As[16][64];
+  const int K = 9 * Cin, Kb = K + 1, P = Cout * K + Cout;
+  const int co0 = blockIdx.y * 64, k0 = blockIdx.x * 64;
   const int npix = B * Ho * Ho;
-  const int o0 = blockIdx.y * chunk, o1 = min(npix, o0 + chunk);
+  const int p0 = blockIdx.z * chunk, p1 = min(npix, p0 + chunk);
   const int Hv = Hin * up;
-  float acc = 0.f;
-  if (p < Wn) {
-    const int co = p / (9 * Cin), rem = p - co * 9 * Cin;
-    const int tap = rem / Cin, ci = rem - tap * Cin;
-    const int ky = tap / 3, kx = tap - 3 * ky;
-    for (int o = o0; o < o1; ++o) {
-      const int b = o / (Ho * Ho), r2 = o - b * Ho * Ho;
-      const int oy = r2 / Ho, ox = r2 - oy * Ho;
-      const int vy = oy * stride + ky - 1, vx = ox * stride + kx - 1;
-      if (vy < 0 || vy >= Hv || vx < 0 || vx >= Hv) continue;
-      const float av = __bfloat162float(a_in[((size_t)(b * Hin + vy / up) * Hin + vx / up) * Cin + ci]);
-      acc += dz[(size_t)o * Cout + co] * av;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int pb = p0; pb < p1; pb += 16) {
+    for (int i = threadIdx.x; i < 16 * 64; i += 256) {
+      const int pp = i / 64, c = i % 64;
+      const int p = pb + pp, co = co0 + c, k = k0 + c;
+      Ds[pp][c] = (p < p1 && co < Cout) ? dz[(size_t)p * Cout + co] : 0.f;
+      float av = 0.f;
+      if (p < p1 && k < Kb) {
+        if (k == K) {
+          av = 1.f;
+        } else {
+          const int tap = k / Cin, ci = k - tap * Cin;
+          const int ky = tap / 3, kx = tap - 3 * ky;
+          const int b = p / (Ho * Ho), r2 = p - b * Ho * Ho;
+          const int oy = r2 / Ho, ox = r2 - oy * Ho;
+          const int vy = oy * stride + ky - 1, vx = ox * stride + kx - 1;
+          if (vy >= 0 && vy < Hv && vx >= 0 && vx < Hv)
+            av = __bfloat162float(a_in[((size_t)(b * Hin + vy / up) * Hin + vx / up) * Cin + ci]);
+        }
+      }
+      As[pp][c] = av;
     }
-  } else {
-    const int co = p - Wn;
-    for (int o = o0; o < o1; ++o) acc += dz[(size_t)o * Cout + co];
+    __syncthreads();
+#pragma unroll
+    for (int pp = 0; pp < 16; ++pp) {
+      float d[4], a[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        d[j] = Ds[pp][ty * 4 + j];
+        a[j] = As[pp][tx * 4 + j];
+      }
+#pragma unroll
+      for (int i2 = 0; i2 < 4; ++i2)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i2][j] += d[i2] * a[j];
+    }
+    __syncthreads();
   }
-  part[(size_t)blockIdx.y * P + p] = acc;
+#pragma unroll
+  for (int i2 = 0; i2 < 4; ++i2)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int co = co0 + ty * 4 + i2, k = k0 + tx * 4 + j;
+      if (co < Cout && k < Kb) part[(size_t)blockIdx.z * P + (k < K ? co * K + k : Cout * K + co)] = acc[i2][j];
+    }
 }
 
 // grad[p] = sum over chunks of part[chunk][p], in chunk order.
@@ -375,7 +436,7 @@ struct CoarseArgs {
 
 // One block per window: z_H and g_H on the coarsest grid as weighted sums over
 // each coarse pixel's fine block, e_plain = g_H / w_H, s = RMS(e_plain).
-__global__ void __launch_bounds__(256) coarse_state_kernel(const CoarseArgs A) {
+__global__ void __launch_bounds__(1024) coarse_state_kernel(const CoarseArgs A) {
   __shared__ double red[32];
   const int w = blockIdx.x, tid = threadIdx.x;
   const int MS = A.MS, L = A.L, F = 1 << (L - 1), h = MS >> (L - 1);
@@ -456,7 +517,7 @@ __host__ __device__ __forceinline__ int up_off(int MS, int l) {
 // and the kept one written back as w^0 Delta; otherwise one pyramid (the plain
 // MAGPS V-cycle, as the window kernel's pass D computes it).
 template <bool LEARN>
-__global__ void __launch_bounds__(256) vcycle_up_kernel(const LearnedUpArgs A) {
+__global__ void __launch_bounds__(1024) vcycle_up_kernel(const LearnedUpArgs A) {
   extern __shared__ __align__(16) unsigned char lsm[];
   __shared__ double red[32];
   __shared__ int keep;

@@ -248,7 +248,7 @@ __device__ __forceinline__ void coarsen(const double2* q4, const double* u4, dou
 // also written in float64 to qtop/utop when coarser levels remain.
 __global__ void __launch_bounds__(256) pyramid_tile_kernel(const float2* Q, int MS, int L, float alpha,
                                                             const unsigned long long* mx_bits, double2* qtop,
-                                                            double* utop, float* pyr) {
+                                                            double* utop, float* pyr, int unit_wu) {
   __shared__ double2 qsh[2][256];
   __shared__ double ush[2][256];
   const int TS = MS < 16 ? MS : 16;
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(256) pyramid_tile_kernel(const float2* Q, int 
       const int s = MS >> l;
       const int o = ((R0 >> l) + r) * s + (C0 >> l) + c;
       float* base = pyr + lvl_off(MS, l);
-      base[o] = wu;
+      base[o] = unit_wu ? 1.f : wu;
       base[s * s + o] = iw;
       base[2 * s * s + o] = rr;
       qsh[dst][r * ts + c] = qm;
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(256) pyramid_tile_kernel(const float2* Q, int 
 
 // Levels coarser than a tile, from the level-`lt` float64 arrays (one block).
 __global__ void __launch_bounds__(256) pyramid_top_kernel(int MS, int L, int lt, double2* qtop, double* utop,
-                                                           float* pyr) {
+                                                           float* pyr, int unit_wu) {
   int off = 0;  // level l's arrays at qtop + off (level lt at 0)
   for (int l = lt + 1; l < L; ++l) {
     const int sf = MS >> (l - 1), s = MS >> l;
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(256) pyramid_top_kernel(int MS, int L, int lt,
       float wu, iw, rr;
       coarsen(q4, u4, qm, uh, wu, iw, rr);
       float* base = pyr + lvl_off(MS, l);
-      base[i] = wu;
+      base[i] = unit_wu ? 1.f : wu;
       base[s * s + i] = iw;
       base[2 * s * s + i] = rr;
       qtop[noff + i] = qm;
@@ -469,18 +469,21 @@ int cluster_of(int m) { return m >= 256 ? 8 : m == 128 ? 4 : m == 64 ? 2 : 1; }
 
 // The per-level probe factors of probe Q (float64 arithmetic) into pyr.
 // mx: one 8-byte scratch word; qtop/utop: float64 scratch of 2 MS^2 entries.
+// unit_wu: store W_u^l = 1 (the MG/OPT correction term: the coarse residual
+// gradient becomes the plain restriction of the fine one; u^l and w^l keep the
+// paper's weights).
 cudaError_t enqueue_pyramid(const float2* Q, int MS, int L, float alpha, unsigned long long* mx, double2* qtop,
-                            double* utop, float* pyr, cudaStream_t st) {
+                            double* utop, float* pyr, cudaStream_t st, int unit_wu = 0) {
   const int M = MS * MS;
   cudaError_t e = cudaMemsetAsync(mx, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   const int mb = (M + 255) / 256 < 64 ? (M + 255) / 256 : 64;
   probe_max_kernel<<<mb, 256, 0, st>>>(Q, M, mx);
   const int TS = MS < 16 ? MS : 16;
-  pyramid_tile_kernel<<<dim3(MS / TS, MS / TS), TS * TS, 0, st>>>(Q, MS, L, alpha, mx, qtop, utop, pyr);
+  pyramid_tile_kernel<<<dim3(MS / TS, MS / TS), TS * TS, 0, st>>>(Q, MS, L, alpha, mx, qtop, utop, pyr, unit_wu);
   int lt = 0;
   while ((TS >> (lt + 1)) >= 1 && lt + 1 <= L - 1) ++lt;
-  if (lt < L - 1) pyramid_top_kernel<<<1, 256, 0, st>>>(MS, L, lt, qtop, utop, pyr);
+  if (lt < L - 1) pyramid_top_kernel<<<1, 256, 0, st>>>(MS, L, lt, qtop, utop, pyr, unit_wu);
   return cudaGetLastError();
 }
 
@@ -531,34 +534,64 @@ cudaError_t launch_window_m(int MS, const StepArgs& a, int blocks, cudaStream_t 
   }
 }
 
+// Candidate register bounds of the batched window kernel: blocks per SM.
+template <int MS>
+constexpr int alt_minb() {
+  return Geo<MS>::T >= 512 ? 1 : (Geo<MS>::MIN_BLOCKS == 1 ? 2 : 1);
+}
+
 template <int MS, int MODE>
-cudaError_t launch_window_batched(const StepArgs* table, const int2* map, int windows, cudaStream_t st) {
+cudaError_t launch_window_batched(const StepArgs* table, const int2* map, int windows, cudaStream_t st, int minb) {
   using Gm = Geo<MS>;
-  return launch_ex(window_kernel_batched<MS, MODE>, dim3((unsigned)windows * Gm::CL), dim3(Gm::T), Gm::SMEM, st,
-                   Gm::CL, table, map);
+  const dim3 grid((unsigned)windows * Gm::CL);
+  if (minb == alt_minb<MS>() && minb != Gm::MIN_BLOCKS)
+    return launch_ex(window_kernel_batched<MS, MODE, alt_minb<MS>()>, grid, dim3(Gm::T), Gm::SMEM, st, Gm::CL, table,
+                     map);
+  return launch_ex(window_kernel_batched<MS, MODE, Gm::MIN_BLOCKS>, grid, dim3(Gm::T), Gm::SMEM, st, Gm::CL, table,
+                   map);
 }
 
 template <int MODE>
-cudaError_t launch_window_batched_m(int MS, const StepArgs* table, const int2* map, int windows, cudaStream_t st) {
+cudaError_t launch_window_batched_m(int MS, const StepArgs* table, const int2* map, int windows, cudaStream_t st,
+                                    int minb) {
   switch (MS) {
-    case 8: return launch_window_batched<8, MODE>(table, map, windows, st);
-    case 16: return launch_window_batched<16, MODE>(table, map, windows, st);
-    case 32: return launch_window_batched<32, MODE>(table, map, windows, st);
-    case 64: return launch_window_batched<64, MODE>(table, map, windows, st);
-    case 128: return launch_window_batched<128, MODE>(table, map, windows, st);
-    case 256: return launch_window_batched<256, MODE>(table, map, windows, st);
+    case 8: return launch_window_batched<8, MODE>(table, map, windows, st, minb);
+    case 16: return launch_window_batched<16, MODE>(table, map, windows, st, minb);
+    case 32: return launch_window_batched<32, MODE>(table, map, windows, st, minb);
+    case 64: return launch_window_batched<64, MODE>(table, map, windows, st, minb);
+    case 128: return launch_window_batched<128, MODE>(table, map, windows, st, minb);
+    case 256: return launch_window_batched<256, MODE>(table, map, windows, st, minb);
     default: return cudaErrorInvalidValue;
   }
 }
 
-// Opt the window kernels of one size into their dynamic shared memory; done
-// before any launch (and so outside stream capture).
+// The two register bounds the autotuner tries for window side MS (equal when
+// there is only one).
+void minb_candidates(int MS, int* c) {
+  switch (MS) {
+#define MAGPIE_MINB(S)              \
+  case S:                            \
+    c[0] = Geo<S>::MIN_BLOCKS;       \
+    c[1] = alt_minb<S>();            \
+    return;
+    MAGPIE_MINB(8) MAGPIE_MINB(16) MAGPIE_MINB(32) MAGPIE_MINB(64) MAGPIE_MINB(128) MAGPIE_MINB(256)
+#undef MAGPIE_MINB
+    default: c[0] = c[1] = 1;
+  }
+}
+
 template <int MS>
 cudaError_t prepare_size() {
   const int bytes = (int)Geo<MS>::SMEM;
   cudaError_t e = cudaFuncSetAttribute(window_kernel<MS, kStep>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(window_kernel_batched<MS, kStep>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    e = cudaFuncSetAttribute(window_kernel_batched<MS, kStep, Geo<MS>::MIN_BLOCKS>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(window_kernel_batched<MS, kStep, alt_minb<MS>()>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(window_kernel<MS, kStepRecycle>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(window_kernel<MS, kEval>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
@@ -625,6 +658,11 @@ struct magpie_group {
   std::vector<std::vector<GroupWindowLaunch>> wl;  // per batched step
   std::vector<GroupApplyLaunch> al;                // per batched step
   cudaGraphExec_t graph = nullptr;
+  // autotuner: register bound (blocks per SM) of the batched window kernel
+  // per window side m = 8 << i, and the measured ms per launch of batched
+  // step 0 for the two candidates (0 where not measured)
+  int minb[6] = {0, 0, 0, 0, 0, 0};
+  float tune_ms[6][2] = {};
 };
 
 // The network of the learned coarse correction with its training state.
@@ -682,6 +720,9 @@ struct magpie_ctx {
   int* lacc = nullptr;        // [minibatch] 1 = learned V-cycle output kept
   double* lmargin = nullptr;  // [minibatch] surrogate(plain) - surrogate(learned)
   unsigned long long* lstats = nullptr;  // proposals, acceptances
+  // paper variants: bit 0 the MG/OPT correction term, bit 1 the phase rule of Eq. (specification)
+  int variant = 0;
+  float2* phase = nullptr;    // [n_pos][m][m] unit phases of the last visit (phase rule)
   // precision form (tensor-core DFTs)
   int precision = 0;
   float2* pbuf = nullptr;     // [minibatch][m][m] exit wave / spectrum / revised exit wave
@@ -717,6 +758,7 @@ StepArgs make_args(magpie_ctx* c, const int32_t* idx) {
   a.pa2 = c->pa2;
   a.pmax = c->pmax;
   a.err = c->err;
+  a.phase = (c->variant & 2) ? c->phase : nullptr;
   return a;
 }
 
@@ -754,6 +796,24 @@ ConvPlan conv_plan(const ConvFwd& a) {
   return pl;
 }
 
+// Pixel chunks of the weight-gradient GEMM of layer l (enough blocks to
+// fill the GPU, at least 64 pixels per chunk).
+struct WgradPlan {
+  int gx, gy, chunks, chunk;
+};
+WgradPlan wgrad_plan(int h, int l, int B) {
+  const CnnLayer& L = kCnn[l];
+  const int Ho = cnn_side_out(h, l), npix = B * Ho * Ho;
+  WgradPlan w{};
+  w.gx = (9 * L.cin + 1 + 63) / 64;
+  w.gy = (L.cout + 63) / 64;
+  const int want = std::max(1, (2 * 152 + w.gx * w.gy - 1) / (w.gx * w.gy));
+  w.chunks = std::max(1, std::min(want, npix / 64));
+  w.chunk = (npix + w.chunks - 1) / w.chunks;
+  w.chunks = (npix + w.chunk - 1) / w.chunk;
+  return w;
+}
+
 // Partial-sum floats needed by any batch of 1 .. max_batch windows.
 size_t cnn_part_floats(int h, int max_batch) {
   size_t n = 0;
@@ -768,11 +828,8 @@ size_t cnn_part_floats(int h, int max_batch) {
     a.K = 9 * a.Cin;
     const ConvPlan pl = conv_plan(a);
     if (pl.splits > 1) n = std::max(n, (size_t)pl.splits * B * Ho * Ho * a.Cout);
-    const int P = a.Cout * 9 * a.Cin + a.Cout, npix = B * Ho * Ho;
-    int chunks = std::max(1, std::min((262144 + P - 1) / P, std::max(1, npix / 16)));
-    const int chunk = (npix + chunks - 1) / chunks;
-    chunks = (npix + chunk - 1) / chunk;
-    n = std::max(n, (size_t)chunks * P);
+    const int P = a.Cout * 9 * a.Cin + a.Cout;
+    n = std::max(n, (size_t)wgrad_plan(h, l, B).chunks * P);
   }
   return n;
 }
@@ -833,14 +890,12 @@ int cnn_enqueue_backward(magpie_cnn* n, const float* dy, float* grad, cudaStream
   for (int l = kCnnLayers - 1; l >= 0; --l) {
     const CnnLayer& L = kCnn[l];
     const int Hin = cnn_side_in(h, l), Ho = cnn_side_out(h, l);
-    const int P = L.cout * 9 * L.cin + L.cout, npix = B * Ho * Ho;
-    int chunks = std::max(1, std::min((262144 + P - 1) / P, std::max(1, npix / 16)));
-    const int chunk = (npix + chunks - 1) / chunks;
-    chunks = (npix + chunk - 1) / chunk;
-    conv_bwd_weight_kernel<<<dim3((P + 255) / 256, chunks), 256, 0, st>>>(dz, n->act[l], n->part, B, Hin, L.cin,
-                                                                          L.cout, L.stride, L.up, Ho, chunk);
+    const int P = L.cout * 9 * L.cin + L.cout;
+    const WgradPlan wp = wgrad_plan(h, l, B);
+    conv_wgrad_kernel<<<dim3(wp.gx, wp.gy, wp.chunks), 256, 0, st>>>(dz, n->act[l], n->part, B, Hin, L.cin, L.cout,
+                                                                      L.stride, L.up, Ho, wp.chunk);
     CUDA_TRY(cudaGetLastError());
-    chunk_sum_kernel<<<(P + 255) / 256, 256, 0, st>>>(n->part, grad + n->off[l], P, chunks);
+    chunk_sum_kernel<<<(P + 255) / 256, 256, 0, st>>>(n->part, grad + n->off[l], P, wp.chunks);
     CUDA_TRY(cudaGetLastError());
     if (l > 0) {
       const size_t nx = (size_t)B * Hin * Hin * L.cin;
@@ -926,7 +981,7 @@ LearnedUpArgs up_args(magpie_ctx* c, const int32_t* idx) {
 // pass, then the V-cycle with the kept coarse correction writes w^0 Delta
 // back to the increments.
 int enqueue_learned_tail(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st) {
-  coarse_state_kernel<<<count, 256, 0, st>>>(coarse_args(c, idx, c->lx, c->lscale));
+  coarse_state_kernel<<<count, 1024, 0, st>>>(coarse_args(c, idx, c->lx, c->lscale));
   CUDA_TRY(cudaGetLastError());
   int rc = cnn_enqueue_forward(c->cnn, reinterpret_cast<const float*>(c->lx), count, c->cnn->y, st);
   if (rc) return rc;
@@ -936,7 +991,7 @@ int enqueue_learned_tail(magpie_ctx* c, const int32_t* idx, int count, cudaStrea
   u.accepted = c->lacc;
   u.margin = c->lmargin;
   u.stats = c->lstats;
-  vcycle_up_kernel<true><<<count, 256, learned_up_smem(c->p.m, c->p.levels), st>>>(u);
+  vcycle_up_kernel<true><<<count, 1024, learned_up_smem(c->p.m, c->p.levels), st>>>(u);
   CUDA_TRY(cudaGetLastError());
   return MAGPIE_OK;
 }
@@ -1010,6 +1065,7 @@ int enqueue_precision_g0(magpie_ctx* c, const int32_t* idx, int count, cudaStrea
   a.part = c->part;
   a.corner = c->corner;
   a.err = c->err;
+  a.phase = (c->variant & 2) ? c->phase : nullptr;
   const dim3 tiles((unsigned)count, (unsigned)a.CL);
   exit_wave_kernel<<<tiles, 256, 0, st>>>(a);
   CUDA_TRY(cudaGetLastError());
@@ -1033,16 +1089,17 @@ int enqueue_step(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st, 
     if (!rc && c->cnn) {
       rc = enqueue_learned_tail(c, idx, count, st);
     } else if (!rc && c->p.levels >= 2) {
-      vcycle_up_kernel<false><<<count, 256, sizeof(float2) * (size_t)up_off(c->p.m, c->p.levels), st>>>(
+      vcycle_up_kernel<false><<<count, 1024, sizeof(float2) * (size_t)up_off(c->p.m, c->p.levels), st>>>(
           up_args(c, idx));
       CUDA_TRY(cudaGetLastError());
     }
-  } else if (c->cnn) {
-    a.grad_only = 1;
-    CUDA_TRY(launch_window_m<kStep>(c->p.m, a, count, st));
-    rc = enqueue_learned_tail(c, idx, count, st);
   } else {
-    CUDA_TRY(launch_window_m<kStep>(c->p.m, a, count, st));
+    a.grad_only = c->cnn ? 1 : 0;
+    if (a.phase)
+      CUDA_TRY(launch_window_m<kStepRecycle>(c->p.m, a, count, st));
+    else
+      CUDA_TRY(launch_window_m<kStep>(c->p.m, a, count, st));
+    if (c->cnn) rc = enqueue_learned_tail(c, idx, count, st);
   }
   if (rc) return rc;
   if (ev) CUDA_TRY(cudaEventRecord(ev[1], st));
@@ -1053,7 +1110,8 @@ int enqueue_step(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st, 
     probe_apply_kernel<<<(c->M + 255) / 256, 256, 0, st>>>(c->Q, c->M, idx, count, c->p.n_pos, c->pnum, c->pa2,
                                                            c->pmax, cluster_of(c->p.m), c->p.beta);
     CUDA_TRY(cudaGetLastError());
-    CUDA_TRY(enqueue_pyramid(c->Q, c->p.m, c->p.levels, c->p.alpha, c->mx, c->pyr_q, c->pyr_u, c->pyr, st));
+    CUDA_TRY(enqueue_pyramid(c->Q, c->p.m, c->p.levels, c->p.alpha, c->mx, c->pyr_q, c->pyr_u, c->pyr, st,
+                             c->variant & 1));
   }
   if (ev) CUDA_TRY(cudaEventRecord(ev[3], st));
   return MAGPIE_OK;
@@ -1061,7 +1119,8 @@ int enqueue_step(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st, 
 
 int build_pyramid(magpie_ctx* c, const void* probe) {
   CUDA_TRY(cudaMemcpyAsync(c->Q, probe, sizeof(float2) * c->M, cudaMemcpyDeviceToDevice, c->stream));
-  CUDA_TRY(enqueue_pyramid(c->Q, c->p.m, c->p.levels, c->p.alpha, c->mx, c->pyr_q, c->pyr_u, c->pyr, c->stream));
+  CUDA_TRY(enqueue_pyramid(c->Q, c->p.m, c->p.levels, c->p.alpha, c->mx, c->pyr_q, c->pyr_u, c->pyr, c->stream,
+                           c->variant & 1));
   if (c->wz) {
     wz_kernel<<<std::max(1, c->M / 256), 256, 0, c->stream>>>(c->Q, c->p.m, c->p.levels, c->wz);
     CUDA_TRY(cudaGetLastError());
@@ -1228,6 +1287,55 @@ int noalloc_scratch(NoAllocScratch* out) {
 
 }  // namespace
 
+
+// Autotuner of a group: for every window side of batched step 0, launch the
+// batched window kernel with each candidate register bound (one warm-up, then
+// three timed launches on the group's stream) and keep the faster.  The
+// launches only write the members' per-window scratch (increments, partial
+// sums, corners), never an object; the members' permutations are set to the
+// identity first so that every index is valid.
+int group_autotune(magpie_group* g) {
+  cudaStream_t st = g->stream;
+  for (auto* c : g->members)
+    CUDA_TRY(cudaMemcpyAsync(c->order, c->iota, sizeof(int32_t) * c->p.n_pos, cudaMemcpyDeviceToDevice, st));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaEventCreate(&e0));
+  cudaError_t e = cudaEventCreate(&e1);
+  for (int i = 0; i < 6 && e == cudaSuccess; ++i) {
+    int cand[2];
+    minb_candidates(8 << i, cand);
+    g->minb[i] = cand[0];
+  }
+  if (!g->wl.empty())
+    for (const auto& L : g->wl[0]) {
+      if (e != cudaSuccess) break;
+      const int i = ilog2(L.ms) - 3;
+      int cand[2];
+      minb_candidates(L.ms, cand);
+      if (cand[0] == cand[1]) continue;
+      float best = 0.f;
+      for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+        e = launch_window_batched_m<kStep>(L.ms, g->table, g->map + L.map_off, L.windows, st, cand[v]);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+          e = launch_window_batched_m<kStep>(L.ms, g->table, g->map + L.map_off, L.windows, st, cand[v]);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        g->tune_ms[i][v] = ms / 3.f;
+        if (v == 0 || ms / 3.f < best) {
+          best = ms / 3.f;
+          g->minb[i] = cand[v];
+        }
+      }
+    }
+  cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return fail(MAGPIE_ECUDA, std::string("group autotuner: ") + cudaGetErrorString(e));
+  return MAGPIE_OK;
+}
+
 extern "C" {
 
 int magpie_version(void) { return kVersion; }
@@ -1259,7 +1367,7 @@ void magpie_destroy(magpie_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   void* bufs[] = {c->Q, c->tw, c->amp, c->stage, c->pos, c->pyr, c->pyr_q, c->pyr_u, c->contrib,
                   c->phi_pos, c->gn_pos, c->part, c->corner, c->mx, c->pnum, c->pa2, c->pmax, c->iota, c->order, c->sums, c->err,
-                  c->wz, c->lx, c->lscale, c->lacc, c->lmargin, c->lstats, c->pbuf, c->tabs};
+                  c->wz, c->lx, c->lscale, c->lacc, c->lmargin, c->lstats, c->pbuf, c->tabs, c->phase};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete c;
@@ -1590,8 +1698,8 @@ int magpie_group_create(magpie_group** out, magpie_ctx* const* ctxs, int32_t n, 
   for (int i = 0; i < n; ++i) {
     if (!ctxs[i]) return fail(MAGPIE_EINVAL, "context " + std::to_string(i) + " is NULL");
     if (ctxs[i]->p.update_probe) return fail(MAGPIE_EINVAL, "contexts with update_probe = 1 cannot be grouped");
-    if (ctxs[i]->cnn || ctxs[i]->precision)
-      return fail(MAGPIE_EINVAL, "contexts with a network or tensor-core DFTs cannot be grouped");
+    if (ctxs[i]->cnn || ctxs[i]->precision || (ctxs[i]->variant & 2))
+      return fail(MAGPIE_EINVAL, "contexts with a network, tensor-core DFTs or the phase rule cannot be grouped");
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == ctxs[i]) return fail(MAGPIE_EINVAL, "a context appears twice in the group");
   }
@@ -1659,6 +1767,11 @@ int magpie_group_create(magpie_group** out, magpie_ctx* const* ctxs, int32_t n, 
     magpie_group_destroy(g);
     return fail(MAGPIE_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
   }
+  rc = group_autotune(g);
+  if (rc) {
+    magpie_group_destroy(g);
+    return rc;
+  }
   *out = g;
   return MAGPIE_OK;
 }
@@ -1673,7 +1786,8 @@ int magpie_group_sweep(magpie_group* g, const int32_t* const* orders) {
     cudaError_t e = cudaSuccess;
     for (size_t t = 0; t < g->wl.size() && e == cudaSuccess; ++t) {
       for (const auto& L : g->wl[t]) {
-        e = launch_window_batched_m<kStep>(L.ms, g->table, g->map + L.map_off, L.windows, g->cap_stream);
+        e = launch_window_batched_m<kStep>(L.ms, g->table, g->map + L.map_off, L.windows, g->cap_stream,
+                                           g->minb[ilog2(L.ms) - 3]);
         if (e != cudaSuccess) break;
       }
       if (e != cudaSuccess) break;
@@ -1824,7 +1938,7 @@ int magpie_coarse_state(magpie_ctx* c, const int32_t* idx, int32_t count, float*
   StepArgs a = make_args(c, idx);
   a.grad_only = 1;
   CUDA_TRY(launch_window_m<kStep>(c->p.m, a, count, c->stream));
-  coarse_state_kernel<<<count, 256, 0, c->stream>>>(coarse_args(c, idx, reinterpret_cast<float4*>(x), scale));
+  coarse_state_kernel<<<count, 1024, 0, c->stream>>>(coarse_args(c, idx, reinterpret_cast<float4*>(x), scale));
   CUDA_TRY(cudaGetLastError());
   return read_err(c);
 }
@@ -1932,6 +2046,66 @@ int magpie_dft2_tc(const void* in, void* out, int32_t m, int32_t count, int32_t 
   if (dt) cudaFree(dt);
   if (dtw) cudaFree(dtw);
   if (e != cudaSuccess) return fail(MAGPIE_ECUDA, std::string("magpie_dft2_tc: ") + cudaGetErrorString(e));
+  return MAGPIE_OK;
+}
+
+
+// ---------------------------------------------------------- paper variants
+
+__global__ void fill_unit_kernel(float2* p, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    p[i] = make_float2(1.f, 0.f);
+}
+
+int magpie_set_variant(magpie_ctx* c, int32_t flags) {
+  if (!c) return fail(MAGPIE_EINVAL, "NULL context");
+  if (flags & ~3) return fail(MAGPIE_EINVAL, "flags: bit 0 MG/OPT correction, bit 1 phase rule");
+  if ((flags & 1) && c->p.update_probe) return fail(MAGPIE_EINVAL, "the MG/OPT variant needs update_probe = 0");
+  if (flags & 2) {
+    const size_t n = (size_t)c->M * c->p.n_pos;
+    if (!c->phase) {
+      cudaError_t e = cudaMalloc((void**)&c->phase, sizeof(float2) * n);
+      if (e != cudaSuccess)
+        return fail(e == cudaErrorMemoryAllocation ? MAGPIE_ENOMEM : MAGPIE_ECUDA,
+                    std::string("phase buffer: ") + cudaGetErrorString(e));
+    }
+    fill_unit_kernel<<<1024, 256, 0, c->stream>>>(c->phase, n);
+    CUDA_TRY(cudaGetLastError());
+  }
+  const int old = c->variant;
+  c->variant = flags;
+  if ((old ^ flags) & 1)
+    CUDA_TRY(enqueue_pyramid(c->Q, c->p.m, c->p.levels, c->p.alpha, c->mx, c->pyr_q, c->pyr_u, c->pyr, c->stream,
+                             flags & 1));
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return MAGPIE_OK;
+}
+
+
+int magpie_group_tuning(magpie_group* g, int32_t* minb, float* ms) {
+  if (!g || !minb || !ms) return fail(MAGPIE_EINVAL, "NULL argument");
+  for (int i = 0; i < 6; ++i) {
+    minb[i] = g->minb[i];
+    ms[2 * i] = g->tune_ms[i][0];
+    ms[2 * i + 1] = g->tune_ms[i][1];
+  }
+  return MAGPIE_OK;
+}
+
+int magpie_group_set_minb(magpie_group* g, int32_t m, int32_t minb) {
+  if (!g) return fail(MAGPIE_EINVAL, "NULL group");
+  if (m < 8 || m > 256 || (m & (m - 1))) return fail(MAGPIE_EINVAL, "m must be a power of two in [8, 256]");
+  int cand[2];
+  minb_candidates(m, cand);
+  if (minb != cand[0] && minb != cand[1]) return fail(MAGPIE_EINVAL, "not a candidate register bound for this m");
+  g->minb[ilog2(m) - 3] = minb;
+  if (g->graph) {
+    cudaGraphExecDestroy(g->graph);
+    g->graph = nullptr;
+  }
   return MAGPIE_OK;
 }
 

@@ -236,6 +236,7 @@ struct PrecArgs {
   double* part;        // [count][CL][2] partial sums: (|Psi| - sqrt d)^2, |g^0|^2
   int2* corner;        // [count] window corners for the update kernel
   int* err;            // bit 0: window index out of range
+  float2* phase;       // phase rule: [n_pos][MS][MS] unit phases of the last visit, else null
 };
 
 // buf[w] = Q . z_k (row tile blockIdx.y of window blockIdx.x); records the corner.
@@ -284,7 +285,14 @@ __global__ void __launch_bounds__(256) projection_kernel(const PrecArgs A) {
     const float mag = sqrtf(n2);
     const float d = mag - a;
     res += d * d;
-    P[o] = n2 > 0.f ? make_float2(v.x * (a / mag) * inv_m2, v.y * (a / mag) * inv_m2) : make_float2(a * inv_m2, 0.f);
+    float2 u = make_float2(1.f, 0.f);  // theta(0) = 0
+    if (n2 > 0.f) {
+      u = make_float2(v.x / mag, v.y / mag);
+      if (A.phase && ok) A.phase[(size_t)k * MS * MS + o] = u;
+    } else if (A.phase && ok) {
+      u = A.phase[(size_t)k * MS * MS + o];  // Eq. (specification): the previous visit's phase
+    }
+    P[o] = make_float2(a * inv_m2 * u.x, a * inv_m2 * u.y);
   }
   const double s = block_sum((double)res, red, threadIdx.x, blockDim.x);
   if (threadIdx.x == 0) A.part[((size_t)w * A.CL + q) * 2] = ok ? s : 0.0;

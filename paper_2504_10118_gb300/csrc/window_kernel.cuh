@@ -13,7 +13,10 @@ __host__ __device__ __forceinline__ int lvl_off(int MS, int l) {
 }
 __host__ __device__ __forceinline__ int pyr_size(int MS, int L) { return lvl_off(MS, L); }
 
-enum Mode { kStep = 0, kEval = 1, kSim = 2 };
+// kStep: a minibatch step; kStepRecycle: the same with the phase rule of
+// Eq. (specification) across visits (phases kept per window); kEval: the
+// objective only; kSim: forward intensities.
+enum Mode { kStep = 0, kEval = 1, kSim = 2, kStepRecycle = 3 };
 
 struct StepArgs {
   const float2* z;    // object [n_rows][n_cols]
@@ -35,6 +38,7 @@ struct StepArgs {
   double* pmax;       // probe step only: [windows][CL] block maxima of |z_k|^2
   int* err;           // bit 0: window index out of range
   int grad_only;      // step: write g^0 = conj(Q)(R_k - Q z_k) as the increments and skip the V-cycle
+  float2* phase;      // kStepRecycle: [n_pos][MS][MS] unit phase of each spectrum entry at the last visit
 };
 
 // Sum over the block (a fixed order: warp shuffles, then the warps in order);
@@ -271,8 +275,10 @@ __global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel
 
 // Several problems in one launch: cluster c works on window slot map[c].y of
 // the problem whose arguments are table[map[c].x].
-template <int MS, int MODE>
-__global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS)
+// MINB: blocks per SM the register allocation is bounded for (the group's
+// autotuner picks it per window side by timing).
+template <int MS, int MODE, int MINB>
+__global__ void __launch_bounds__(Geo<MS>::T, MINB)
     window_kernel_batched(const StepArgs* __restrict__ table, const int2* __restrict__ map) {
   __shared__ StepArgs args;
   const int2 ent = map[blockIdx.x / Geo<MS>::CL];

@@ -2,12 +2,15 @@
 solver, through the library's C ABI (every arithmetic step runs in its CUDA
 kernels; this module only schedules the calls and moves tensors).
 
-A trajectory is one scan window followed for T V-cycles on its own: windows of
-the current object are tiled without overlap into a tall object, and a
-context over that object with all of them in one minibatch advances each
-exactly as the plain method advances a single window (Algorithm MAGPS with its
-revised exit wave refreshed every cycle).  The network input at the start and
-the coarse object after T cycles give one training pair.
+The plain solver runs from z = 1 on seeded problems; the network input of a
+window at an intermediate sweep and the window's coarse object in the
+solver's final state give one training pair (the network learns where the
+method's own iteration takes a window's coarse state).  The alternative
+"local" target follows one window for T V-cycles on its own: windows of the
+current object are tiled without overlap into a tall object, and a context
+over that object with all of them in one minibatch advances each exactly as
+the plain method advances a single window (Algorithm MAGPS with its revised
+exit wave refreshed every cycle).
 """
 from __future__ import annotations
 
@@ -79,28 +82,54 @@ def window_trajectories(ctx: magpie.Context, Q: torch.Tensor, d: torch.Tensor, i
     return Trajectories(x0, xT[..., 0:2].contiguous(), s0)
 
 
-def generate(w: synth.Workload, seeds, stages, per_stage: int, T: int, dev: torch.device,
-             rng_seed: int = 11) -> Trajectories:
-    """Trajectories from problems drawn with `seeds`: the plain solver runs
-    from z = 1, and after each number of sweeps in `stages` `per_stage`
-    random windows start a T-cycle trajectory."""
+def generate(w: synth.Workload, seeds, stages, per_stage: int, dev: torch.device, final_sweeps: int = 60,
+             target: str = "final", T: int = 4, rng_seed: int = 11) -> Trajectories:
+    """Training pairs from problems drawn with `seeds`.  The plain solver runs
+    from z = 1 for `final_sweeps` sweeps; after each number of sweeps in
+    `stages`, `per_stage` random windows give a network input.  Their target
+    is the coarse object of the same windows in the solver's final state
+    (target "final"), or after T further cycles of each window on its own
+    (target "local", `window_trajectories`)."""
     rng = np.random.default_rng(rng_seed)
-    parts = []
+    h = coarse_side(w.m, w.levels)
+    X, Z, S = [], [], []
     for seed in seeds:
         _, Q, pos, d = problem(w, seed, dev)
         z = torch.ones((w.n, w.n), dtype=torch.complex64, device=dev)
         p = magpie.magpie_params_of(w.n, w.n, w.m, w.n_pos, w.levels, w.minibatch, w.alpha)
         ctx = magpie.magpie_create(p, z, Q, pos, d)
-        done = 0
+        saved = {}
+        last = final_sweeps if target == "final" else max(stages)
+        for s in range(last + 1):
+            if s in stages:
+                saved[s] = z.clone()
+            if s < last:
+                magpie.magpie_sweep(ctx, torch.from_numpy(synth.make_order(w.n_pos, s)).to(dev))
+        z_final = z.clone()
         for s in sorted(stages):
-            while done < s:
-                magpie.magpie_sweep(ctx, torch.from_numpy(synth.make_order(w.n_pos, done)).to(dev))
-                done += 1
             idx = torch.from_numpy(rng.choice(w.n_pos, per_stage, replace=False).astype(np.int32)).to(dev)
-            parts.append(window_trajectories(ctx, Q, d, idx, T))
+            z.copy_(saved[s])
+            if target == "local":
+                t = window_trajectories(ctx, Q, d, idx, T)
+                X.append(t.x0)
+                Z.append(t.zh)
+                S.append(t.scale)
+                continue
+            for i0 in range(0, per_stage, w.minibatch):
+                sel = idx[i0:i0 + w.minibatch]
+                x0 = torch.empty((sel.numel(), h, h, 4), dtype=torch.float32, device=dev)
+                s0 = torch.empty(sel.numel(), dtype=torch.float32, device=dev)
+                xf = torch.empty_like(x0)
+                sf = torch.empty_like(s0)
+                z.copy_(saved[s])
+                magpie.magpie_coarse_state(ctx, sel, x0, s0)
+                z.copy_(z_final)
+                magpie.magpie_coarse_state(ctx, sel, xf, sf)
+                X.append(x0)
+                Z.append(xf[..., 0:2].contiguous())
+                S.append(s0)
         magpie.magpie_destroy(ctx)
-    return Trajectories(torch.cat([t.x0 for t in parts]), torch.cat([t.zh for t in parts]),
-                        torch.cat([t.scale for t in parts]))
+    return Trajectories(torch.cat(X), torch.cat(Z), torch.cat(S))
 
 
 def train(net: magpie.Cnn, data: Trajectories, epochs: int, batch: int = 64, lr: float = 3e-4,

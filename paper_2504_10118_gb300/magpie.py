@@ -86,6 +86,8 @@ def lib() -> ctypes.CDLL:
             "magpie_group_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(vp), i32, vp]),
             "magpie_group_sweep": (ctypes.c_int, [vp, ctypes.POINTER(vp)]),
             "magpie_group_destroy": (None, [vp]),
+            "magpie_group_tuning": (ctypes.c_int, [vp, vp, vp]),
+            "magpie_group_set_minb": (ctypes.c_int, [vp, i32, i32]),
             "magpie_cnn_param_count": (i32, []),
             "magpie_cnn_create": (ctypes.c_int, [ctypes.POINTER(vp), i32, i32, vp]),
             "magpie_cnn_destroy": (None, [vp]),
@@ -100,6 +102,7 @@ def lib() -> ctypes.CDLL:
             "magpie_learned_stats": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
             "magpie_learned_window_values": (ctypes.c_int, [vp, i32, vp, vp]),
             "magpie_set_precision": (ctypes.c_int, [vp, i32]),
+            "magpie_set_variant": (ctypes.c_int, [vp, i32]),
             "magpie_dft2_tc": (ctypes.c_int, [vp, vp, i32, i32, i32, vp]),
             "magpie_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             "magpie_last_error": (ctypes.c_char_p, []),
@@ -297,6 +300,27 @@ def magpie_group_sweep(group: Group, orders) -> None:
 
 def magpie_group_destroy(group: Group) -> None:
     group.close()
+
+
+def magpie_group_tuning(group: Group):
+    """{m: (register bound in use, ms per launch of the two candidates)} for
+    the window sides the autotuner measured."""
+    minb = (ctypes.c_int32 * 6)()
+    ms = (ctypes.c_float * 12)()
+    _check(lib().magpie_group_tuning(group.handle, minb, ms))
+    return {8 << i: (minb[i], (ms[2 * i], ms[2 * i + 1])) for i in range(6) if ms[2 * i] > 0}
+
+
+def magpie_group_set_minb(group: Group, m: int, minb: int) -> None:
+    _check(lib().magpie_group_set_minb(group.handle, int(m), int(minb)))
+
+
+# ----------------------------------------------------------- paper variants
+MGOPT, PHASE_RULE = 1, 2
+
+
+def magpie_set_variant(ctx: Context, flags: int) -> None:
+    _check(lib().magpie_set_variant(ctx.handle, int(flags)))
 
 
 # ----------------------------------------------------------- precision form

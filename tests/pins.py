@@ -459,6 +459,78 @@ def check_probe_step(O):
         prev = cur
 
 
+def check_mgopt_variant(O):
+    """The MG/OPT correction term (Algorithm MG/OPT): (a) it vanishes where
+    the probe is constant on every bin of every level (W_u = 1, the coarse
+    surrogate is then first-order consistent by itself); (b) for two levels
+    the result is the minimiser of the coarse surrogate minus Re<v_H, z_H>,
+    v_H = grad f_H(z_H) - I_h^H grad f_h(z), followed by the fine proximal
+    step, both solved here from their stationarity conditions with the
+    gradients grad f(x) = conj(Q)(Q x - R) of Eq. (misfit_derivative);
+    (c) the residual form with the plain restriction g^{l+1} = I_h^H g^l (the
+    weights W_u replaced by 1, u^l and w^l unchanged) gives the same step."""
+    rng = np.random.default_rng(31)
+    m = 16
+    q4 = _crand(rng, m // 4, m // 4)
+    Qc = O.prolong(O.prolong(q4))  # constant on 4 x 4 blocks
+    zk, Rk = _crand(rng, m, m), _crand(rng, m, m)
+    u = O.rpie_regulariser(Qc, 0.1)
+    for L in (2, 3):
+        assert _rel(O.magps_mgopt(zk, Qc, Rk, u, L), O.magps(zk, Qc, Rk, u, L)) < 1e-12
+    Q = _crand(rng, m, m)
+    u = O.rpie_regulariser(Q, 0.1)
+    QH, Wz, WR, Wu = O.coarse_weights(Q)
+    zH, RH, uH = O.restrict(Wz * zk), O.restrict(WR * Rk), Wu * O.restrict(u)
+    grad_h = np.conj(Q) * (Q * zk - Rk)
+    grad_H = np.conj(QH) * (QH * zH - RH)
+    vH = grad_H - O.restrict(grad_h)
+    # stationarity of 1/2|QH y - RH|^2 - Re<vH, y> + 1/2 uH |y - zH|^2
+    yH = (np.conj(QH) * RH + vH + uH * zH) / (np.abs(QH) ** 2 + uH)
+    zt = zk + O.prolong(yH - zH)
+    # stationarity of 1/2|Q x - R|^2 + 1/2 u |x - zt|^2
+    x = (np.conj(Q) * Rk + u * zt) / (np.abs(Q) ** 2 + u)
+    assert _rel(O.magps_mgopt(zk, Q, Rk, u, 2), x) < 1e-12
+    assert _rel(O.magps_mgopt(zk, Q, Rk, u, 2), O.magps(zk, Q, Rk, u, 2)) > 1e-6
+    for L in (2, 3, 4):
+        gs, us, ws = [np.conj(Q) * (Rk - Q * zk)], [u], [u + np.abs(Q) ** 2]
+        Ql = Q
+        for lvl in range(L - 1):
+            _, _, _, Wl = O.coarse_weights(Ql)
+            gs.append(O.restrict(gs[-1]))
+            us.append(Wl * O.restrict(us[-1]))
+            ws.append(Wl * O.restrict(ws[-1]))
+            Ql = O.restrict(Ql)
+        e = gs[-1] / ws[-1]
+        for lvl in range(L - 2, -1, -1):
+            e = (gs[lvl] + us[lvl] * O.prolong(e)) / ws[lvl]
+        assert _rel(O.magps_mgopt(zk, Q, Rk, u, L) - zk, e) < 1e-11
+
+
+def check_phase_rule_variant(O):
+    """Eq. (specification) across visits: with no exact zero in the spectrum
+    the rule changes nothing; a window whose object patch is exactly zero has
+    a zero spectrum, so its first visit uses theta = 0 and every later visit
+    the phases of the visit before (here: of a visit with a nonzero patch)."""
+    z_true, Q, pos, d = _small_problem(O, seed=32)
+    u = O.rpie_regulariser(Q, 0.1)
+    rng = np.random.default_rng(32)
+    z = z_true + 0.2 * _crand(rng, *z_true.shape)
+    batch = list(range(len(pos)))
+    ph = {}
+    a = O.minibatch_step_variant(z, Q, pos, d, u, 2, batch, phases=ph)
+    assert _rel(a, O.minibatch_step(z, Q, pos, d, u, 2, batch)) < 1e-14
+    m = Q.shape[0]
+    k = 3
+    zk = O.extract(z, pos[k], m)
+    R1, th1 = O.revised_exit_wave_recycled(zk, Q, d[k], None)
+    zero = np.zeros_like(zk)
+    R2, th2 = O.revised_exit_wave_recycled(zero, Q, d[k], th1)
+    assert np.array_equal(th2, th1)
+    assert _rel(R2, O.ifft2(np.sqrt(d[k]) * np.exp(1j * np.angle(O.fft2(Q * zk))))) < 1e-12
+    R0, th0 = O.revised_exit_wave_recycled(zero, Q, d[k], None)
+    assert np.all(th0 == 0) and _rel(R0, O.ifft2(np.sqrt(d[k]))) < 1e-14
+
+
 ALL_CHECKS = [
     check_dft_defining_sum, check_dft_parseval_inverse, check_dft_closed_forms,
     check_scan_adjoint, check_transfer_operators, check_objective_forms,
@@ -467,5 +539,5 @@ ALL_CHECKS = [
     check_weight_properties, check_coarse_step_closed_form,
     check_coarse_prox_is_argmin, check_auto_regularisation,
     check_consistency_bounds, check_residual_form, check_special_cases,
-    check_probe_step, check_recovery,
+    check_probe_step, check_recovery, check_mgopt_variant, check_phase_rule_variant,
 ]

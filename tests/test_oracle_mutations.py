@@ -124,10 +124,44 @@ def m_objective_no_half(O):
     O.objective_k = lambda zk, Q, dk: 2.0 * orig(zk, Q, dk)
 
 
+def m_mgopt_shift_sign(O):
+    orig = O.magps_mgopt
+
+    def mg(zk, Q, Rk, u, levels, shift=None):
+        return orig(zk, Q, Rk, u, levels, None if shift is None else -shift)
+    O.magps_mgopt = mg
+
+
+def m_mgopt_weighted_restriction(O):
+    def mg(zk, Q, Rk, u, levels, shift=None):
+        if shift is None:
+            shift = np.zeros_like(zk)
+
+        def step(z):
+            return z + O.safe_div(np.conj(Q) * (Rk - Q * z) + shift, u + np.abs(Q) ** 2)
+        if levels == 1:
+            return step(zk)
+        QH, Wz, WR, Wu = O.coarse_weights(Q)
+        zH, RH, uH = O.restrict(Wz * zk), O.restrict(WR * Rk), Wu * O.restrict(u)
+        g = np.conj(Q) * (Rk - Q * zk) + shift
+        sH = Wu * O.restrict(g) - np.conj(QH) * (RH - QH * zH)
+        return step(zk + O.prolong(mg(zH, QH, RH, uH, levels - 1, sH) - zH))
+    O.magps_mgopt = mg
+
+
+def m_phase_rule_forgets(O):
+    def rec(zk, Q, dk, prev_theta):
+        psi = O.fft2(O.exit_wave(zk, Q))
+        theta = np.angle(psi)
+        return O.ifft2(np.sqrt(dk) * np.exp(1j * theta)), theta
+    O.revised_exit_wave_recycled = rec
+
+
 MUTATIONS = [m_restrict_sum, m_prolong_scaled, m_fft_sign, m_fft_unnormalised_inverse,
              m_no_sqrt, m_gradient_no_conj, m_wr_no_conj, m_wz_unnormalised,
              m_uh_unweighted, m_post_smooth_from_z, m_minibatch_count_average,
-             m_regulariser_amplitude, m_extract_transposed, m_objective_no_half]
+             m_regulariser_amplitude, m_extract_transposed, m_objective_no_half,
+             m_mgopt_shift_sign, m_mgopt_weighted_restriction, m_phase_rule_forgets]
 
 FAST_CHECKS = [c for c in pins.ALL_CHECKS if c is not pins.check_recovery]
 
