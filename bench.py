@@ -48,6 +48,24 @@ def flops_per_window(m: int) -> float:
     return 10.0 * M * math.log2(M) + 43.0 * M
 
 
+def tc_flops_per_window(m: int) -> float:
+    """Tensor-core flops of one window in the precision form: a forward and an
+    inverse 2-D DFT, each 2 m lines x 2 stages of real block GEMMs
+    (stage 1: 32 x 32 by 32 x m/16; stage 2: m rows x K x 2 m/16 with K the
+    stage's padded depth), three BF16 products each for the hi+lo split."""
+    qr = m // 16
+    k2 = 16 * ((2 * qr + 15) // 16)
+    per_line = 2 * 32 * 32 * qr + 2 * 16 * k2 * 2 * qr
+    return 2 * 2 * m * per_line * 3.0
+
+
+def cnn_flops_per_window(h: int) -> float:
+    """Tensor-core flops of the learned correction's network on one window
+    (side h on the coarsest grid): 2 x weights x output pixels per layer."""
+    layers = ((4, 32, h), (32, 64, h // 2), (64, 128, h // 4), (128, 512, h // 8), (512, 64, h // 4), (64, 2, h))
+    return float(sum(2 * 9 * ci * co * s * s for ci, co, s in layers))
+
+
 def hbm_bytes_per_window(m: int) -> float:
     """Compulsory HBM bytes of one window: its float32 amplitudes."""
     return 4.0 * m * m
@@ -336,6 +354,48 @@ def config_of(w):
             "parallelism": "replicas", "l2": "flushed (256 MiB write) before every timed sweep"}
 
 
+def nrmse_lit(z, z_true, q2, pos, rel: float = 1e-3) -> float:
+    """Reconstruction error modulo a global phase, min_phi ||e^{i phi} z - z*|| / ||z*||,
+    over the pixels whose summed illumination sum_k P_k^T |Q|^2 reaches
+    `rel` of its maximum (unlit pixels carry no data)."""
+    m = q2.shape[0]
+    cov = np.zeros(z_true.shape)
+    for r, c in pos:
+        cov[r:r + m, c:c + m] += q2
+    lit = cov >= rel * cov.max()
+    a, b = np.asarray(z, dtype=np.complex128)[lit], np.asarray(z_true, dtype=np.complex128)[lit]
+    ip = np.vdot(a, b)
+    ph = ip / abs(ip) if abs(ip) > 0 else 1.0
+    return float(np.linalg.norm(ph * a - b) / np.linalg.norm(b))
+
+
+def launches_per_step(args, w) -> int:
+    """Kernel launches of one minibatch step of the configured form."""
+    if args.learned:
+        return 1 + 1 + 1 + 6 + 4 + 1 + 1  # window, coarse state, cast, 6 convolutions, split-K sums, V-cycle, update
+    if args.dft == "tc":
+        return 1 + 4 + 1 + 1 + (1 if w.levels >= 2 else 0) + 1
+    return 2
+
+
+def tensor_roofline(args, w, windows, wk_ms, ap_ms, prof_sweeps, launches, pk, src):
+    """Roofline of the tensor-core work of the precision or learned form over
+    its window phase (every kernel between the window's exit wave and the
+    update kernel), against the measured BF16 dense peak."""
+    if args.learned:
+        fl = cnn_flops_per_window(w.m >> (w.levels - 1))
+        what = "learned form: window phase (window kernel, coarse state, 6 BF16 convolutions, V-cycle)"
+    else:
+        fl = tc_flops_per_window(w.m)
+        what = "precision form: window phase (exit wave, 4 tensor-core DFT launches, projection, g0, V-cycle)"
+    ach = windows * fl / (wk_ms * 1e-3) / 1e12
+    peak = pk.get("bf16_tflops", 1900.0)
+    return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": None, "kernel": what, "avg_launch_ms": wk_ms / max(launches, 1),
+            "peak_source": f"bf16 dense, {src}", "tensor_flops_per_window": fl,
+            "apply_kernel_ms_per_sweep": ap_ms / prof_sweeps, "window_phase_ms_per_sweep": wk_ms / prof_sweeps}
+
+
 def run_ours(args, w):
     import torch
     from paper_2504_10118_gb300 import magpie
@@ -358,6 +418,23 @@ def run_ours(args, w):
     z = torch.ones((w.n, w.n), dtype=torch.complex64, device=dev)
     ctx = magpie.magpie_create(magpie.magpie_params_of(w.n, w.n, w.m, w.n_pos, w.levels, w.minibatch, w.alpha),
                                z, Qt, post, dt)
+    if args.dft == "tc":
+        magpie.magpie_set_precision(ctx, 1)
+    net = None
+    train_info = None
+    if args.learned:
+        from paper_2504_10118_gb300 import learned
+        t0 = time.perf_counter()
+        data = learned.generate(w, seeds=[11, 12, 13], stages=[0, 1, 2, 3, 4, 6, 8, 12, 16, 24], per_stage=100,
+                                dev=dev, final_sweeps=60)
+        net = magpie.magpie_cnn_create(learned.coarse_side(w.m, w.levels), w.minibatch)
+        magpie.magpie_cnn_set_params(net, learned.initial_params(dev=dev))
+        losses = learned.train(net, data, epochs=40, batch=64, lr=3e-4)
+        torch.cuda.synchronize()
+        train_info = {"trajectories": len(data), "epochs": 40, "loss_first_epoch": float(losses[0]),
+                      "loss_last_epoch": float(losses[-1]), "seconds": time.perf_counter() - t0,
+                      "untimed": "generation and training run before the timed region"}
+        magpie.magpie_attach_cnn(ctx, net)
     orders = torch.from_numpy(np.stack([synth.make_order(w.n_pos, s)
                                         for s in range(args.warmup + args.steps)])).to(dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
@@ -384,6 +461,14 @@ def run_ours(args, w):
     clk = clocks.stop()
     total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)), pg, dev)
 
+    # reconstruction quality after warm-up + timed sweeps (host arithmetic on
+    # the downloaded object, outside every timed region)
+    quality = {"sweeps": args.warmup + args.steps,
+               "nrmse_vs_truth": nrmse_lit(z.cpu().numpy(), z_true, np.abs(Qt.cpu().numpy()) ** 2, post.cpu().numpy()),
+               "objective": magpie.magpie_objective(ctx)}
+    if args.learned:
+        quality["proposals_kept"], quality["proposals"] = magpie.magpie_learned_stats(ctx)[::-1]
+
     # dominant kernel: the per-window kernel, timed with events captured in
     # the sweep graph over the same kind of sweeps
     prof_sweeps = min(args.steps, 20)
@@ -400,7 +485,7 @@ def run_ours(args, w):
     alu_peak = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
     achieved_tf = windows * flops_per_window(w.m) / (wk_ms * 1e-3) / 1e12
     achieved_gbs = windows * hbm_bytes_per_window(w.m) / (wk_ms * 1e-3) / 1e9
-    traffic = measured_traffic()
+    traffic = measured_traffic() if args.dft == "fft" and not args.learned else None
 
     # end to end through the host-buffer call: order + intensities in, object out
     order_h = [torch.from_numpy(synth.make_order(w.n_pos, 1000 + s)).pin_memory() for s in range(args.steps)]
@@ -424,10 +509,14 @@ def run_ours(args, w):
         line = {
             "metric": "patterns/s per sweep", "value": value, "unit": "patterns/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x3 (hi+lo) DFTs, f32" if args.dft == "tc" else ("f32 + bf16 network" if args.learned else "f32"),
             "data": "synthetic (seeded object, probe, raster and Poisson noise)",
-            "config": config_of(w),
-            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
+            "config": dict(config_of(w), workload=("learned correction on " + w.name) if args.learned else w.name,
+                           dft="tensor-core BF16 hi+lo" if args.dft == "tc" else "FP32 FFT"),
+            "quality": quality,
+            "training": train_info,
+            "roofline": ({"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": achieved_tf / alu_peak, "traffic": traffic,
                          "kernel": f"window_kernel<{w.m}, step>",
                          "avg_launch_ms": wk_ms / max(launches, 1),
@@ -436,13 +525,15 @@ def run_ours(args, w):
                          "hbm_view": {"achieved": achieved_gbs, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
                                       "frac": achieved_gbs / pk.get("hbm_gbs", 6800.0)},
                          "apply_kernel_ms_per_sweep": ap_ms / prof_sweeps,
-                         "window_kernel_ms_per_sweep": wk_ms / prof_sweeps},
+                         "window_kernel_ms_per_sweep": wk_ms / prof_sweeps}
+                         if args.dft == "fft" and not args.learned else
+                         tensor_roofline(args, w, windows, wk_ms, ap_ms, prof_sweeps, launches, pk, src)),
             "cpu_baseline": cpu,
             "e2e": {"value": whole_job_value(world, args.steps, w.n_pos, 1e3 * e2e_s), "unit": "patterns/s",
                     "h2d_bytes_per_step": 4 * w.n_pos + 4 * w.n_pos * w.m * w.m,
                     "d2h_bytes_per_step": 8 * w.n * w.n,
                     "call": "magpie_sweep_host (order and intensities in, object out, pinned buffers)"},
-            "gpu_launches": 2 * math.ceil(w.n_pos / w.minibatch) * args.steps,
+            "gpu_launches": launches_per_step(args, w) * math.ceil(w.n_pos / w.minibatch) * args.steps,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
@@ -458,7 +549,9 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(synth.WORKLOADS) + ["batched"], default="mid")
+    ap.add_argument("--workload", choices=sorted(synth.WORKLOADS) + ["batched", "learned"], default="mid")
+    ap.add_argument("--dft", choices=["fft", "tc"], default=None,
+                    help="fft: FP32 FFT path; tc: tensor-core BF16 hi+lo DFTs (default for the precision workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -468,7 +561,10 @@ def main():
             print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no CPU reference arm"}))
             return 0
         return run_batched(args)
-    w = synth.WORKLOADS[args.workload]
+    if args.dft is None:
+        args.dft = "tc" if args.workload == "precision" else "fft"
+    args.learned = args.workload == "learned"
+    w = synth.WORKLOADS["mid" if args.learned else args.workload]
     if args.impl == "reference":
         return run_reference(args, w)
     return run_ours(args, w)

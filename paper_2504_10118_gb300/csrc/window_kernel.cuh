@@ -55,6 +55,31 @@ __device__ __forceinline__ double block_sum(double v, double* red, int tid, int 
   return r;
 }
 
+// Two sums over the block at once: each warp adds its lanes' FP32 partials
+// with a fixed shuffle tree, thread 0 adds the warps' results in FP64 in warp
+// order (totals valid in thread 0 only).  `red` holds 2 nthreads/32 doubles
+// and is not reused before the block's next barrier.
+__device__ __forceinline__ void block_sum2(float a, float b, double* red, int tid, int nthreads, double& sa,
+                                           double& sb) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  if ((tid & 31) == 0) {
+    red[2 * (tid >> 5)] = a;
+    red[2 * (tid >> 5) + 1] = b;
+  }
+  __syncthreads();
+  sa = 0.0;
+  sb = 0.0;
+  if (tid == 0)
+    for (int i = 0; i < nthreads / 32; ++i) {
+      sa += red[2 * i];
+      sb += red[2 * i + 1];
+    }
+}
+
 __device__ __forceinline__ double block_max(double v, double* red, int tid, int nthreads) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
