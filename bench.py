@@ -325,6 +325,12 @@ def run_batched(args):
     total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)), pg, dev)
     steps_max = max(math.ceil(w.n_pos / w.minibatch) for w in ws)
     launches = sum(len({w.m for w in ws if math.ceil(w.n_pos / w.minibatch) > t}) + 1 for t in range(steps_max))
+    tuning = magpie.magpie_group_tuning(group)
+    pk, src = peaks()
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    alu_peak = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    flops = sum(w.n_pos * flops_per_window(w.m) for w in ws) * args.steps
+    achieved = flops / (total_ms * 1e-3) / 1e12
     group.close()
     for c in ctxs:
         c.close()
@@ -340,6 +346,11 @@ def run_batched(args):
                        "levels": 3, "minibatch": 64, "parallelism": "replicas",
                        "l2": "flushed (256 MiB write) before every timed sweep"},
             "gpu_launches": launches * args.steps, "clocks": clk,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                         "frac": achieved / alu_peak, "traffic": None,
+                         "kernel": "whole group sweep (batched window and update launches)",
+                         "peak_source": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz ({src})"},
+            "autotuner": {str(m): {"minb": v[0], "ms_per_launch": list(v[1])} for m, v in tuning.items()},
         }
         print(json.dumps(line), flush=True)
     if pg:

@@ -55,7 +55,7 @@ namespace cg = cooperative_groups;
 constexpr int kVersion = 10100;  // 1.1.0
 constexpr int kMaxMinibatch = 4096;  // the update kernel keeps the minibatch's corners in smem (48 KiB)
 constexpr int kMaxCluster = 8;       // largest number of blocks per window
-constexpr int kApplyUnroll = 8;      // increments in flight per thread in the update kernel
+constexpr int kApplyUnroll = 4;      // increments in flight per thread in the update kernel
 
 #include "fft_lines.cuh"
 #include "window_kernel.cuh"
@@ -67,7 +67,7 @@ constexpr int kApplyUnroll = 8;      // increments in flight per thread in the u
 // 16 x 16 object tile, one pixel per thread: the block first lists, in
 // minibatch order, the windows that overlap its tile (corners as recorded by
 // the window kernel; a ballot compaction over all warps); each thread then
-// walks that short list eight entries at a time with predicated loads, so
+// walks that short list four entries at a time with predicated loads, so
 // several increments are in flight per thread.  Block (0, 0) also turns the
 // window kernel's block partials into Phi_k and ||grad Phi_k||.
 // Dynamic smem: count int2 corners + count ints.
@@ -139,8 +139,6 @@ __device__ __forceinline__ void apply_body(const ApplyArgs& P, const int tx, con
   const int r = R0 + (threadIdx.x >> 4), c = C0 + (threadIdx.x & 15);
   if (r >= P.n_rows || c >= P.n_cols) return;
   const size_t M = (size_t)MS * MS;
-  const size_t p = (size_t)r * P.n_cols + c;
-  float2 zz = P.z[p];  // in flight with the increments below
   float nx = 0.f, ny = 0.f, d = 0.f;
   for (int j0 = 0; j0 < nl; j0 += kApplyUnroll) {
     float2 v[kApplyUnroll];
@@ -164,6 +162,8 @@ __device__ __forceinline__ void apply_body(const ApplyArgs& P, const int tx, con
     }
   }
   if (d > 0.f) {
+    const size_t p = (size_t)r * P.n_cols + c;
+    float2 zz = P.z[p];
     zz.x += nx / d;
     zz.y += ny / d;
     P.z[p] = zz;
