@@ -502,10 +502,14 @@ def run_ours(args, w):
     order_h = [torch.from_numpy(synth.make_order(w.n_pos, 1000 + s)).pin_memory() for s in range(args.steps)]
     d_pin = torch.from_numpy(d_host).pin_memory()
     z_out = torch.empty((w.n, w.n), dtype=torch.complex64).pin_memory()
+    for s in range(2):  # both data buffers allocated and their sweep graphs captured, untimed
+        magpie.magpie_sweep_host_async(ctx, order_h[s], d_pin, z_out)
+    magpie.magpie_sync(ctx)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for s in range(args.steps):
-        magpie.magpie_sweep_host(ctx, order_h[s], d_pin, z_out)
+        magpie.magpie_sweep_host_async(ctx, order_h[s], d_pin, z_out)
+    magpie.magpie_sync(ctx)
     e2e_s = max_over_ranks(time.perf_counter() - t0, pg, dev)
 
     cpu = None
@@ -543,7 +547,9 @@ def run_ours(args, w):
             "e2e": {"value": whole_job_value(world, args.steps, w.n_pos, 1e3 * e2e_s), "unit": "patterns/s",
                     "h2d_bytes_per_step": 4 * w.n_pos + 4 * w.n_pos * w.m * w.m,
                     "d2h_bytes_per_step": 8 * w.n * w.n,
-                    "call": "magpie_sweep_host (order and intensities in, object out, pinned buffers)"},
+                    "call": "magpie_sweep_host_async x steps, then magpie_sync: every sweep copies its order "
+                            "and the whole intensity set in (pinned host buffers, on a copy stream while the "
+                            "previous sweep computes) and the object out"},
             "gpu_launches": launches_per_step(args, w) * math.ceil(w.n_pos / w.minibatch) * args.steps,
             "clocks": clk,
         }

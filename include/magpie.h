@@ -184,6 +184,23 @@ int magpie_sweep_host(magpie_ctx* ctx, const int32_t* order, const float* intens
                       void* object_out);
 
 /*
+ * Pipelined end-to-end sweep from host memory: enqueues, without waiting,
+ * the copy of `intensities` (HOST float32 [n_pos][m][m], page-locked for
+ * asynchronous copies) and of `order` (HOST int32 [n_pos]) to the device, one
+ * sweep on them, and the copy of the object to `object_out` (HOST complex
+ * [n_rows][n_cols], may be NULL).  Consecutive calls alternate between two
+ * device buffers for the data, and the data copy of a call runs on a copy
+ * stream while the previous call's sweep computes, so a sequence of sweeps
+ * runs at close to the device rate with every sweep's data brought in anew.
+ * Results are those of magpie_sweep_host; the context's own data set (used by
+ * magpie_sweep / magpie_step) is left unchanged.  Host buffers must stay valid
+ * and unmodified until magpie_sync returns; magpie_sync waits for all enqueued
+ * work and reports errors.
+ */
+int magpie_sweep_host_async(magpie_ctx* ctx, const int32_t* order, const float* intensities, void* object_out);
+int magpie_sync(magpie_ctx* ctx);
+
+/*
  * Forward model of Section 2.1 without noise, d_k = |F(Q . P_k z)|^2 for
  * k = 0..n_pos-1, no context needed.  DEVICE pointers: object complex
  * [n_rows][n_cols], probe complex [m][m], positions int32 [n_pos][2],

@@ -729,6 +729,16 @@ struct magpie_ctx {
   float2* pbuf = nullptr;     // [minibatch][m][m] exit wave / spectrum / revised exit wave
   TcTables* tabs = nullptr;
   cudaGraphExec_t graph = nullptr;
+  // pipelined host sweeps (magpie_sweep_host_async): two amplitude buffers,
+  // their raw-intensity staging, a sweep graph per buffer, and per buffer the
+  // events "data landed" and "sweep done with it"
+  float* amp2[2] = {nullptr, nullptr};
+  float* stage2[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph2[2] = {nullptr, nullptr};
+  cudaEvent_t landed[2][4] = {};
+  cudaEvent_t used[2] = {nullptr, nullptr};
+  cudaStream_t copy2[4] = {};  // four chunks in flight (several copy engines)
+  int next_buf = 0;
   std::vector<cudaEvent_t> events;  // 4 per minibatch step (magpie_profile_sweep)
   // host sweeps: chunked uploads of the intensities on several copy streams
   cudaStream_t copy_streams[4] = {};
@@ -1157,25 +1167,42 @@ int evaluate(magpie_ctx* c, double* phi, double* stop) {
 
 int n_steps(const magpie_ctx* c) { return (c->p.n_pos + c->p.minibatch - 1) / c->p.minibatch; }
 
+// Drops the captured sweep graphs (their launches bake in the context's mode).
+void invalidate_graphs(magpie_ctx* c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+  for (int b = 0; b < 2; ++b) {
+    if (c->graph2[b]) cudaGraphExecDestroy(c->graph2[b]);
+    c->graph2[b] = nullptr;
+  }
+}
+
+// Captures the graph of one sweep over the permutation in c->order.
+int capture_sweep(magpie_ctx* c, cudaGraphExec_t* out) {
+  const int N = c->p.n_pos, B = c->p.minibatch;
+  cudaGraph_t g = nullptr;
+  CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = MAGPIE_OK;
+  for (int s = 0; s < N && rc == MAGPIE_OK; s += B)
+    rc = enqueue_step(c, c->order + s, N - s < B ? N - s : B, c->cap_stream);
+  cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  CUDA_TRY(e);
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  CUDA_TRY(e);
+  return MAGPIE_OK;
+}
+
 // Replays (capturing it on first use) the graph of one sweep over the
 // permutation already in c->order.
 int launch_sweep(magpie_ctx* c) {
-  const int N = c->p.n_pos, B = c->p.minibatch;
   if (!c->graph) {
-    cudaGraph_t g = nullptr;
-    CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-    int rc = MAGPIE_OK;
-    for (int s = 0; s < N && rc == MAGPIE_OK; s += B)
-      rc = enqueue_step(c, c->order + s, N - s < B ? N - s : B, c->cap_stream);
-    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
-    if (rc) {
-      if (g) cudaGraphDestroy(g);
-      return rc;
-    }
-    CUDA_TRY(e);
-    e = cudaGraphInstantiate(&c->graph, g, 0);
-    cudaGraphDestroy(g);
-    CUDA_TRY(e);
+    const int rc = capture_sweep(c, &c->graph);
+    if (rc) return rc;
   }
   CUDA_TRY(cudaGraphLaunch(c->graph, c->stream));
   return MAGPIE_OK;
@@ -1358,6 +1385,16 @@ const char* magpie_last_error(void) { return g_last_error.c_str(); }
 void magpie_destroy(magpie_ctx* c) {
   if (!c) return;
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (int b = 0; b < 2; ++b) {
+    if (c->graph2[b]) cudaGraphExecDestroy(c->graph2[b]);
+    for (auto e : c->landed[b])
+      if (e) cudaEventDestroy(e);
+    if (c->used[b]) cudaEventDestroy(c->used[b]);
+    if (c->amp2[b]) cudaFree(c->amp2[b]);
+    if (c->stage2[b]) cudaFree(c->stage2[b]);
+  }
+  for (auto cs : c->copy2)
+    if (cs) cudaStreamDestroy(cs);
   for (int i = 0; i < 4; ++i) {
     if (c->copy_streams[i]) cudaStreamDestroy(c->copy_streams[i]);
     if (c->copy_done[i]) cudaEventDestroy(c->copy_done[i]);
@@ -1961,10 +1998,7 @@ int magpie_attach_cnn(magpie_ctx* c, magpie_cnn* n) {
     rc = learned_buffers(c);
     if (rc) return rc;
   }
-  if (c->graph) {
-    cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
-  }
+  invalidate_graphs(c);
   c->cnn = n;
   return MAGPIE_OK;
 }
@@ -2013,10 +2047,7 @@ int magpie_set_precision(magpie_ctx* c, int32_t mode) {
       CUDA_TRY(cudaMemcpy(c->tabs, &h, sizeof(TcTables), cudaMemcpyHostToDevice));
     }
   }
-  if (c->graph) {
-    cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
-  }
+  invalidate_graphs(c);
   c->precision = mode;
   return MAGPIE_OK;
 }
@@ -2078,10 +2109,7 @@ int magpie_set_variant(magpie_ctx* c, int32_t flags) {
   if ((old ^ flags) & 1)
     CUDA_TRY(enqueue_pyramid(c->Q, c->p.m, c->p.levels, c->p.alpha, c->mx, c->pyr_q, c->pyr_u, c->pyr, c->stream,
                              flags & 1));
-  if (c->graph) {
-    cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
-  }
+  invalidate_graphs(c);
   return MAGPIE_OK;
 }
 
@@ -2108,6 +2136,62 @@ int magpie_group_set_minb(magpie_group* g, int32_t m, int32_t minb) {
     g->graph = nullptr;
   }
   return MAGPIE_OK;
+}
+
+
+
+
+int magpie_sweep_host_async(magpie_ctx* c, const int32_t* order, const float* intensities, void* object_out) {
+  if (!c || !order || !intensities) return fail(MAGPIE_EINVAL, "NULL argument");
+  const size_t N = c->p.n_pos, M = c->M;
+  const int b = c->next_buf;
+  constexpr int kChunks = 4;
+  if (!c->amp2[b]) {
+    CUDA_TRY(cudaMalloc((void**)&c->amp2[b], sizeof(float) * N * M));
+    CUDA_TRY(cudaMalloc((void**)&c->stage2[b], sizeof(float) * N * M));
+    for (int i = 0; i < kChunks; ++i) CUDA_TRY(cudaEventCreateWithFlags(&c->landed[b][i], cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&c->used[b], cudaEventDisableTiming));
+    CUDA_TRY(cudaEventRecord(c->used[b], c->stream));
+    for (int i = 0; i < kChunks; ++i)
+      if (!c->copy2[i]) CUDA_TRY(cudaStreamCreateWithFlags(&c->copy2[i], cudaStreamNonBlocking));
+  }
+  if (!c->graph2[b]) {
+    float* own = c->amp;
+    c->amp = c->amp2[b];
+    const int rc = capture_sweep(c, &c->graph2[b]);
+    c->amp = own;
+    if (rc) return rc;
+  }
+  // copy streams: once the sweep before last is done with buffer b, bring in
+  // this sweep's intensities in four chunks and take their square roots
+  const size_t total = N * M, per = (total + kChunks - 1) / kChunks;
+  for (int i = 0; i < kChunks; ++i) {
+    const size_t b0 = i * per, n = b0 >= total ? 0 : std::min(per, total - b0);
+    cudaStream_t cs = c->copy2[i];
+    CUDA_TRY(cudaStreamWaitEvent(cs, c->used[b], 0));
+    if (n) {
+      CUDA_TRY(cudaMemcpyAsync(c->stage2[b] + b0, intensities + b0, sizeof(float) * n, cudaMemcpyHostToDevice, cs));
+      sqrt_kernel<<<256, 256, 0, cs>>>(c->stage2[b] + b0, c->amp2[b] + b0, n);
+      CUDA_TRY(cudaGetLastError());
+    }
+    CUDA_TRY(cudaEventRecord(c->landed[b][i], cs));
+  }
+  // main stream: the permutation, the sweep on buffer b, the object out
+  CUDA_TRY(cudaMemcpyAsync(c->order, order, sizeof(int32_t) * N, cudaMemcpyHostToDevice, c->stream));
+  for (int i = 0; i < kChunks; ++i) CUDA_TRY(cudaStreamWaitEvent(c->stream, c->landed[b][i], 0));
+  CUDA_TRY(cudaGraphLaunch(c->graph2[b], c->stream));
+  CUDA_TRY(cudaEventRecord(c->used[b], c->stream));
+  if (object_out)
+    CUDA_TRY(cudaMemcpyAsync(object_out, c->z, sizeof(float2) * (size_t)c->p.n_rows * c->p.n_cols,
+                             cudaMemcpyDeviceToHost, c->stream));
+  c->next_buf = b ^ 1;
+  return MAGPIE_OK;
+}
+
+int magpie_sync(magpie_ctx* c) {
+  if (!c) return fail(MAGPIE_EINVAL, "NULL context");
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return read_err(c);
 }
 
 }  // extern "C"

@@ -80,6 +80,8 @@ def lib() -> ctypes.CDLL:
             "magpie_get_probe": (ctypes.c_int, [vp, vp]),
             "magpie_window_values": (ctypes.c_int, [vp, vp, vp]),
             "magpie_sweep_host": (ctypes.c_int, [vp, vp, vp, vp]),
+            "magpie_sweep_host_async": (ctypes.c_int, [vp, vp, vp, vp]),
+            "magpie_sync": (ctypes.c_int, [vp]),
             "magpie_forward_intensities": (ctypes.c_int, [vp, i32, i32, vp, i32, vp, i32, vp, vp]),
             "magpie_step_noalloc": (ctypes.c_int, [vp, i32, i32, vp, i32, vp, i32, vp, vp, i32, i32,
                                                     ctypes.c_float, vp, vp, vp]),
@@ -236,6 +238,22 @@ def magpie_sweep_host(ctx: Context, order: torch.Tensor, intensities=None, objec
     d = None if intensities is None else _host(intensities, torch.float32, p.n_pos * p.m * p.m, "intensities")
     z = None if object_out is None else _host(object_out, torch.complex64, p.n_rows * p.n_cols, "object_out")
     _check(lib().magpie_sweep_host(ctx.handle, o, d, z))
+
+
+def magpie_sweep_host_async(ctx: Context, order: torch.Tensor, intensities: torch.Tensor, object_out=None) -> None:
+    """Enqueue one pipelined host sweep (see the C header); the tensors are
+    kept alive until magpie_sync."""
+    p = ctx.params
+    o = _host(order, torch.int32, p.n_pos, "order")
+    d = _host(intensities, torch.float32, p.n_pos * p.m * p.m, "intensities")
+    z = None if object_out is None else _host(object_out, torch.complex64, p.n_rows * p.n_cols, "object_out")
+    ctx._pending = getattr(ctx, "_pending", []) + [(order, intensities, object_out)]
+    _check(lib().magpie_sweep_host_async(ctx.handle, o, d, z))
+
+
+def magpie_sync(ctx: Context) -> None:
+    _check(lib().magpie_sync(ctx.handle))
+    ctx._pending = []
 
 
 def magpie_forward_intensities(obj, probe, positions, m: int) -> torch.Tensor:

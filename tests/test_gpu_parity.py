@@ -353,6 +353,34 @@ def test_sweep_from_host_buffers():
     ctx.close()
 
 
+def test_pipelined_host_sweeps():
+    """Three pipelined host sweeps (two data buffers in turn, the data of a
+    sweep copied while the previous one computes) give exactly the results of
+    three magpie_sweep_host calls; the context's own data is untouched."""
+    P, w = tiny_problem()
+    orders = [torch.from_numpy(synth.make_order(P.N, s)).pin_memory() for s in range(3)]
+    d = torch.from_numpy(P.d.astype(np.float32)).pin_memory()
+    d2 = (d * 1.25).pin_memory()  # a second data set for the middle sweep
+    outs = [torch.empty((w.n, w.n), dtype=torch.complex64).pin_memory() for _ in range(3)]
+    ctx = P.ctx()
+    for s, dd in enumerate((d, d2, d)):
+        magpie.magpie_sweep_host_async(ctx, orders[s], dd, outs[s])
+    magpie.magpie_sync(ctx)
+    ref_out = torch.empty((w.n, w.n), dtype=torch.complex64).pin_memory()
+    ctx2 = P.ctx()
+    for s, dd in enumerate((d, d2, d)):
+        magpie.magpie_sweep_host(ctx2, orders[s], dd, ref_out)
+        assert np.array_equal(outs[s].numpy(), ref_out.numpy())
+    ref = O.sweep(P.z0, P.Q, P.pos, P.d, P.u, w.levels, orders[0].numpy(), w.minibatch)
+    ctx3 = P.ctx()
+    magpie.magpie_sweep_host_async(ctx3, orders[0], d, outs[0])
+    magpie.magpie_sync(ctx3)
+    assert rel(outs[0].numpy().astype(np.complex128), ref) < STEP_TOL
+    ctx.close()
+    ctx2.close()
+    ctx3.close()
+
+
 def test_bad_positions_rejected():
     P, w = tiny_problem()
     P.pos = P.pos.copy()
