@@ -192,10 +192,14 @@ int magpie_sweep_host(magpie_ctx* ctx, const int32_t* order, const float* intens
  * device buffers for the data, and the data copy of a call runs on a copy
  * stream while the previous call's sweep computes, so a sequence of sweeps
  * runs at close to the device rate with every sweep's data brought in anew.
- * Results are those of magpie_sweep_host; the context's own data set (used by
- * magpie_sweep / magpie_step) is left unchanged.  Host buffers must stay valid
- * and unmodified until magpie_sync returns; magpie_sync waits for all enqueued
- * work and reports errors.
+ * The permutation and the data travel on the copy streams; for the FP32 FFT
+ * path the window kernels read the raw intensities and take their square
+ * roots themselves; an object_out in pinned (mapped) memory is written by a
+ * kernel over the host link, other memory by a copy.  Results are those of
+ * magpie_sweep_host; the context's own data set and permutation (used by
+ * magpie_sweep / magpie_step) are left unchanged.  Host buffers must stay
+ * valid and unmodified until magpie_sync returns; magpie_sync waits for all
+ * enqueued work and reports errors.
  */
 int magpie_sweep_host_async(magpie_ctx* ctx, const int32_t* order, const float* intensities, void* object_out);
 int magpie_sync(magpie_ctx* ctx);

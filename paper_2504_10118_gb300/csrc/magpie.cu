@@ -189,6 +189,13 @@ __global__ void __launch_bounds__(256) apply_kernel_batched(const ApplyArgs* __r
   apply_body(P, t % P.tiles_x, t / P.tiles_x);
 }
 
+// dst[i] = src[i] with dst in mapped host memory (the object of a pipelined
+// host sweep, written over the host link without the copy engines).
+__global__ void store_host_kernel(const float2* __restrict__ src, float2* __restrict__ dst, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
 __global__ void sqrt_kernel(const float* d, float* a, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     a[i] = sqrtf(fmaxf(d[i], 0.f));
@@ -734,6 +741,8 @@ struct magpie_ctx {
   // events "data landed" and "sweep done with it"
   float* amp2[2] = {nullptr, nullptr};
   float* stage2[2] = {nullptr, nullptr};
+  int32_t* order2[2] = {nullptr, nullptr};  // the permutation of each buffer's sweep
+  int amp_raw = 0;                          // set while a sweep reading raw intensities is captured
   cudaGraphExec_t graph2[2] = {nullptr, nullptr};
   cudaEvent_t landed[2][4] = {};
   cudaEvent_t used[2] = {nullptr, nullptr};
@@ -756,6 +765,7 @@ StepArgs make_args(magpie_ctx* c, const int32_t* idx) {
   a.Q = c->Q;
   a.tw = c->tw;
   a.amp = c->amp;
+  a.amp_raw = c->amp_raw;
   a.out_int = nullptr;
   a.pos = c->pos;
   a.idx = idx;
@@ -1392,6 +1402,7 @@ void magpie_destroy(magpie_ctx* c) {
     if (c->used[b]) cudaEventDestroy(c->used[b]);
     if (c->amp2[b]) cudaFree(c->amp2[b]);
     if (c->stage2[b]) cudaFree(c->stage2[b]);
+    if (c->order2[b]) cudaFree(c->order2[b]);
   }
   for (auto cs : c->copy2)
     if (cs) cudaStreamDestroy(cs);
@@ -2149,41 +2160,69 @@ int magpie_sweep_host_async(magpie_ctx* c, const int32_t* order, const float* in
   if (!c->amp2[b]) {
     CUDA_TRY(cudaMalloc((void**)&c->amp2[b], sizeof(float) * N * M));
     CUDA_TRY(cudaMalloc((void**)&c->stage2[b], sizeof(float) * N * M));
+    CUDA_TRY(cudaMalloc((void**)&c->order2[b], sizeof(int32_t) * N));
     for (int i = 0; i < kChunks; ++i) CUDA_TRY(cudaEventCreateWithFlags(&c->landed[b][i], cudaEventDisableTiming));
     CUDA_TRY(cudaEventCreateWithFlags(&c->used[b], cudaEventDisableTiming));
     CUDA_TRY(cudaEventRecord(c->used[b], c->stream));
     for (int i = 0; i < kChunks; ++i)
       if (!c->copy2[i]) CUDA_TRY(cudaStreamCreateWithFlags(&c->copy2[i], cudaStreamNonBlocking));
   }
+  // the FP32 path reads the raw intensities and takes square roots in the
+  // window kernel (no separate pass); the other paths read square roots
+  const bool raw = !c->precision && !c->cnn && !c->p.update_probe;
   if (!c->graph2[b]) {
     float* own = c->amp;
-    c->amp = c->amp2[b];
+    int32_t* own_order = c->order;
+    c->amp = raw ? c->stage2[b] : c->amp2[b];
+    c->order = c->order2[b];
+    c->amp_raw = raw ? 1 : 0;
     const int rc = capture_sweep(c, &c->graph2[b]);
     c->amp = own;
+    c->order = own_order;
+    c->amp_raw = 0;
     if (rc) return rc;
   }
   // copy streams: once the sweep before last is done with buffer b, bring in
-  // this sweep's intensities in four chunks and take their square roots
+  // this sweep's permutation and intensities in four chunks and take the
+  // square roots; the main stream carries no copy engine work, so nothing of
+  // the next sweep's input queues behind this sweep's result
   const size_t total = N * M, per = (total + kChunks - 1) / kChunks;
   for (int i = 0; i < kChunks; ++i) {
     const size_t b0 = i * per, n = b0 >= total ? 0 : std::min(per, total - b0);
     cudaStream_t cs = c->copy2[i];
     CUDA_TRY(cudaStreamWaitEvent(cs, c->used[b], 0));
+    if (i == 0)
+      CUDA_TRY(cudaMemcpyAsync(c->order2[b], order, sizeof(int32_t) * N, cudaMemcpyHostToDevice, cs));
     if (n) {
       CUDA_TRY(cudaMemcpyAsync(c->stage2[b] + b0, intensities + b0, sizeof(float) * n, cudaMemcpyHostToDevice, cs));
-      sqrt_kernel<<<256, 256, 0, cs>>>(c->stage2[b] + b0, c->amp2[b] + b0, n);
-      CUDA_TRY(cudaGetLastError());
+      if (!raw) {
+        sqrt_kernel<<<256, 256, 0, cs>>>(c->stage2[b] + b0, c->amp2[b] + b0, n);
+        CUDA_TRY(cudaGetLastError());
+      }
     }
     CUDA_TRY(cudaEventRecord(c->landed[b][i], cs));
   }
-  // main stream: the permutation, the sweep on buffer b, the object out
-  CUDA_TRY(cudaMemcpyAsync(c->order, order, sizeof(int32_t) * N, cudaMemcpyHostToDevice, c->stream));
+  // main stream: the sweep on buffer b, then the object out -- written by a
+  // kernel straight into mapped host memory when object_out is mapped
+  // (pinned), else by a copy
   for (int i = 0; i < kChunks; ++i) CUDA_TRY(cudaStreamWaitEvent(c->stream, c->landed[b][i], 0));
   CUDA_TRY(cudaGraphLaunch(c->graph2[b], c->stream));
   CUDA_TRY(cudaEventRecord(c->used[b], c->stream));
-  if (object_out)
-    CUDA_TRY(cudaMemcpyAsync(object_out, c->z, sizeof(float2) * (size_t)c->p.n_rows * c->p.n_cols,
-                             cudaMemcpyDeviceToHost, c->stream));
+  if (object_out) {
+    const size_t nz = (size_t)c->p.n_rows * c->p.n_cols;
+    cudaPointerAttributes at{};
+    const bool mapped = cudaPointerGetAttributes(&at, object_out) == cudaSuccess &&
+                        at.type == cudaMemoryTypeHost && at.devicePointer &&
+                        ((uintptr_t)at.devicePointer % 16) == 0;
+    cudaGetLastError();
+    if (mapped) {
+      store_host_kernel<<<(int)std::min<size_t>((nz + 255) / 256, 1024), 256, 0, c->stream>>>(
+          c->z, (float2*)at.devicePointer, nz);
+      CUDA_TRY(cudaGetLastError());
+    } else {
+      CUDA_TRY(cudaMemcpyAsync(object_out, c->z, sizeof(float2) * nz, cudaMemcpyDeviceToHost, c->stream));
+    }
+  }
   c->next_buf = b ^ 1;
   return MAGPIE_OK;
 }

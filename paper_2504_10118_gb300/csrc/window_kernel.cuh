@@ -39,6 +39,7 @@ struct StepArgs {
   int* err;           // bit 0: window index out of range
   int grad_only;      // step: write g^0 = conj(Q)(R_k - Q z_k) as the increments and skip the V-cycle
   float2* phase;      // kStepRecycle: [n_pos][MS][MS] unit phase of each spectrum entry at the last visit
+  int amp_raw;        // amp holds the intensities d themselves: the kernel uses sqrt(max(d, 0))
 };
 
 // Sum over the block (a fixed order: warp shuffles, then the warps in order);
