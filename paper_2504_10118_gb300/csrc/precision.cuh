@@ -65,20 +65,21 @@ __global__ void __launch_bounds__(128) dft_tc_kernel(float2* __restrict__ data, 
   const int win = blockIdx.x / tiles, l0 = (blockIdx.x % tiles) * NL;
   float2* base = data + (size_t)win * MS * MS;
 
-  // ---- load
-  if (AXIS == 1) {
-    for (int i = tid; i < NL * MS; i += 128) {
-      const int l = i / MS, p = i % MS;
-      const float2 v = base[(size_t)(l0 + l) * MS + p];
-      Sr[l * LD + p] = v.x;
-      Si[l * LD + p] = v.y;
+  // ---- load, eight loads in flight per thread
+  static_assert((NL * MS) % (128 * 8) == 0, "load batches");
+  for (int i0 = tid; i0 < NL * MS; i0 += 128 * 8) {
+    float2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = i0 + 128 * u;
+      v[u] = AXIS == 1 ? base[(size_t)(l0 + i / MS) * MS + i % MS] : base[(size_t)(i / NL) * MS + l0 + i % NL];
     }
-  } else {
-    for (int i = tid; i < NL * MS; i += 128) {
-      const int p = i / NL, l = i % NL;
-      const float2 v = base[(size_t)p * MS + l0 + l];
-      Sr[l * LD + p] = v.x;
-      Si[l * LD + p] = v.y;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = i0 + 128 * u;
+      const int l = AXIS == 1 ? i / MS : i % NL, p = AXIS == 1 ? i % MS : i / NL;
+      Sr[l * LD + p] = v[u].x;
+      Si[l * LD + p] = v[u].y;
     }
   }
 
