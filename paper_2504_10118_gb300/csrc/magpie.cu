@@ -734,6 +734,7 @@ struct magpie_ctx {
   // precision form (tensor-core DFTs)
   int precision = 0;
   float2* pbuf = nullptr;     // [minibatch][m][m] exit wave / spectrum / revised exit wave
+  float2* g1buf = nullptr;    // [minibatch][m/2][m/2] level-1 residual gradient, then increment
   TcTables* tabs = nullptr;
   cudaGraphExec_t graph = nullptr;
   // pipelined host sweeps (magpie_sweep_host_async): two amplitude buffers,
@@ -1070,7 +1071,7 @@ cudaError_t launch_dft2_tc_m(int MS, float2* buf, int count, const TcTables* tab
 
 // Exit waves, tensor-core DFTs, projection, inverse DFTs and g^0 into the
 // increments (with the per-tile partial sums and the windows' corners).
-int enqueue_precision_g0(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st) {
+PrecArgs precision_args(magpie_ctx* c, const int32_t* idx) {
   PrecArgs a{};
   a.z = c->z;
   a.n_cols = c->p.n_cols;
@@ -1087,6 +1088,14 @@ int enqueue_precision_g0(magpie_ctx* c, const int32_t* idx, int count, cudaStrea
   a.corner = c->corner;
   a.err = c->err;
   a.phase = (c->variant & 2) ? c->phase : nullptr;
+  a.g1 = (c->p.levels >= 2 && !c->cnn) ? c->g1buf : nullptr;
+  a.pyr = c->pyr;
+  a.L = c->p.levels;
+  return a;
+}
+
+int enqueue_precision_g0(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st) {
+  const PrecArgs a = precision_args(c, idx);
   const dim3 tiles((unsigned)count, (unsigned)a.CL);
   exit_wave_kernel<<<tiles, 256, 0, st>>>(a);
   CUDA_TRY(cudaGetLastError());
@@ -1110,8 +1119,17 @@ int enqueue_step(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st, 
     if (!rc && c->cnn) {
       rc = enqueue_learned_tail(c, idx, count, st);
     } else if (!rc && c->p.levels >= 2) {
-      vcycle_up_kernel<false><<<count, 1024, sizeof(float2) * (size_t)up_off(c->p.m, c->p.levels), st>>>(
-          up_args(c, idx));
+      // the V-cycle above g^0 (g^1 already restricted by the gradient
+      // kernel): levels 2 .. L-1 one block per window, the finest level
+      // over row tiles
+      const PrecArgs v = precision_args(c, idx);
+      if (c->p.levels >= 3) {
+        int o = 0;
+        for (int j = 2; j < c->p.levels; ++j) o += (c->p.m >> j) * (c->p.m >> j);
+        coarse_cycle_kernel<<<count, 1024, sizeof(float2) * (size_t)o, st>>>(v);
+        CUDA_TRY(cudaGetLastError());
+      }
+      fine_cycle_kernel<<<dim3((unsigned)count, (unsigned)v.CL), 256, 0, st>>>(v);
       CUDA_TRY(cudaGetLastError());
     }
   } else {
@@ -1416,7 +1434,7 @@ void magpie_destroy(magpie_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   void* bufs[] = {c->Q, c->tw, c->amp, c->stage, c->pos, c->pyr, c->pyr_q, c->pyr_u, c->contrib,
                   c->phi_pos, c->gn_pos, c->part, c->corner, c->mx, c->pnum, c->pa2, c->pmax, c->iota, c->order, c->sums, c->err,
-                  c->wz, c->lx, c->lscale, c->lacc, c->lmargin, c->lstats, c->pbuf, c->tabs, c->phase};
+                  c->wz, c->lx, c->lscale, c->lacc, c->lmargin, c->lstats, c->pbuf, c->tabs, c->phase, c->g1buf};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete c;
@@ -2049,6 +2067,7 @@ int magpie_set_precision(magpie_ctx* c, int32_t mode) {
     if (c->p.update_probe) return fail(MAGPIE_EINVAL, "tensor-core DFTs need update_probe = 0");
     if (!c->pbuf) {
       cudaError_t e = cudaMalloc((void**)&c->pbuf, sizeof(float2) * (size_t)c->M * c->p.minibatch);
+      if (e == cudaSuccess) e = cudaMalloc((void**)&c->g1buf, sizeof(float2) * (size_t)(c->M / 4) * c->p.minibatch);
       if (e == cudaSuccess) e = cudaMalloc((void**)&c->tabs, sizeof(TcTables));
       if (e != cudaSuccess)
         return fail(e == cudaErrorMemoryAllocation ? MAGPIE_ENOMEM : MAGPIE_ECUDA,

@@ -238,6 +238,9 @@ struct PrecArgs {
   int2* corner;        // [count] window corners for the update kernel
   int* err;            // bit 0: window index out of range
   float2* phase;       // phase rule: [n_pos][MS][MS] unit phases of the last visit, else null
+  float2* g1;          // levels >= 2: [count][MS/2][MS/2] g^1 = W_u^0 . I(g^0) (then e^1), else null
+  const float* pyr;    // level factors (window-kernel layout)
+  int L;               // levels
 };
 
 // buf[w] = Q . z_k (row tile blockIdx.y of window blockIdx.x); records the corner.
@@ -302,26 +305,119 @@ __global__ void __launch_bounds__(256) projection_kernel(const PrecArgs A) {
 // g^0 = conj(Q)(R - Q z_k) into the increments, and the tile's sum of |g^0|^2.
 __global__ void __launch_bounds__(256) grad_kernel(const PrecArgs A) {
   __shared__ double red[32];
-  const int w = blockIdx.x, q = blockIdx.y, MS = A.MS, rows = MS / A.CL;
+  const int w = blockIdx.x, q = blockIdx.y, MS = A.MS, rows = MS / A.CL, h = MS / 2;
   const int k = A.idx[w];
   const bool ok = (unsigned)k < (unsigned)A.n_pos;
   const int pr = ok ? A.pos[2 * k] : 0, pc = ok ? A.pos[2 * k + 1] : 0;
   const float2* R = A.buf + (size_t)w * MS * MS;
   float2* out = A.contrib + (size_t)w * MS * MS;
+  const float* wu0 = A.pyr + lvl_off(MS, 1);
   float gn = 0.f;
-  for (int i = threadIdx.x; i < rows * MS; i += blockDim.x) {
-    const int r = q * rows + i / MS, c = i % MS, o = r * MS + c;
-    float2 g = make_float2(0.f, 0.f);
-    if (ok) {
-      const float2 zz = A.z[(size_t)(pr + r) * A.n_cols + pc + c];
-      const float2 qq = __ldg(&A.Q[o]);
-      const float2 rr = R[o];
-      const float2 d = make_float2(rr.x - (qq.x * zz.x - qq.y * zz.y), rr.y - (qq.x * zz.y + qq.y * zz.x));
-      g = make_float2(qq.x * d.x + qq.y * d.y, qq.x * d.y - qq.y * d.x);
+  // one 2 x 2 bin per iteration: its four g^0 and, for two levels or more,
+  // g^1 = W_u^0 . (mean of the four)
+  for (int i = threadIdx.x; i < (rows / 2) * h; i += blockDim.x) {
+    const int br = q * (rows / 2) + i / h, bc = i % h;
+    float2 sum = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const int r = 2 * br + a, c = 2 * bc + b, o = r * MS + c;
+        float2 g = make_float2(0.f, 0.f);
+        if (ok) {
+          const float2 zz = A.z[(size_t)(pr + r) * A.n_cols + pc + c];
+          const float2 qq = __ldg(&A.Q[o]);
+          const float2 rr = R[o];
+          const float2 d = make_float2(rr.x - (qq.x * zz.x - qq.y * zz.y), rr.y - (qq.x * zz.y + qq.y * zz.x));
+          g = make_float2(qq.x * d.x + qq.y * d.y, qq.x * d.y - qq.y * d.x);
+        }
+        gn += g.x * g.x + g.y * g.y;
+        out[o] = g;
+        sum.x += g.x;
+        sum.y += g.y;
+      }
+    if (A.g1) {
+      const float f = 0.25f * __ldg(&wu0[br * h + bc]);
+      A.g1[(size_t)w * h * h + br * h + bc] = make_float2(f * sum.x, f * sum.y);
     }
-    gn += g.x * g.x + g.y * g.y;
-    out[o] = g;
   }
   const double s = block_sum((double)gn, red, threadIdx.x, blockDim.x);
   if (threadIdx.x == 0) A.part[((size_t)w * A.CL + q) * 2 + 1] = ok ? s : 0.0;
+}
+
+// Levels 2 .. L-1 of the V-cycle of one window (levels >= 3), one block per
+// window: restrictions from g^1 (global) into shared memory, the coarsest
+// step, the way up, and e^1 = g^1 / w^1 + (u^1 / w^1) I_H^h e^2 written over
+// g^1.  Dynamic shared memory: levels 2 .. L-1 as float2.
+__global__ void __launch_bounds__(1024) coarse_cycle_kernel(const PrecArgs A) {
+  extern __shared__ __align__(16) unsigned char csm[];
+  float2* E = reinterpret_cast<float2*>(csm);
+  const int w = blockIdx.x, tid = threadIdx.x, nt = blockDim.x, MS = A.MS, L = A.L;
+  if ((unsigned)A.idx[w] >= (unsigned)A.n_pos) return;
+  auto off = [&](int l) {  // level l >= 2
+    int o = 0;
+    for (int j = 2; j < l; ++j) o += (MS >> j) * (MS >> j);
+    return o;
+  };
+  float2* g1 = A.g1 + (size_t)w * (MS / 2) * (MS / 2);
+  for (int l = 2; l < L; ++l) {
+    const int s = MS >> l, sf = MS >> (l - 1);
+    const float2* src = l == 2 ? g1 : E + off(l - 1);
+    const float* wu = A.pyr + lvl_off(MS, l);
+    for (int i = tid; i < s * s; i += nt) {
+      const int r = i / s, c = i - r * s;
+      const float2 a = src[(2 * r) * sf + 2 * c], b = src[(2 * r) * sf + 2 * c + 1];
+      const float2 cc = src[(2 * r + 1) * sf + 2 * c], d = src[(2 * r + 1) * sf + 2 * c + 1];
+      const float f = 0.25f * __ldg(&wu[i]);
+      E[off(l) + i] = make_float2(f * (a.x + b.x + cc.x + d.x), f * (a.y + b.y + cc.y + d.y));
+    }
+    __syncthreads();
+  }
+  {
+    const int s = MS >> (L - 1);
+    const float* iw = A.pyr + lvl_off(MS, L - 1) + s * s;
+    for (int i = tid; i < s * s; i += nt) {
+      const float2 g = E[off(L - 1) + i];
+      const float f = __ldg(&iw[i]);
+      E[off(L - 1) + i] = make_float2(g.x * f, g.y * f);
+    }
+    __syncthreads();
+  }
+  for (int l = L - 2; l >= 1; --l) {
+    const int s = MS >> l, sc = MS >> (l + 1);
+    const float* iw = A.pyr + lvl_off(MS, l) + s * s;
+    const float* rr = iw + s * s;
+    float2* a = l == 1 ? g1 : E + off(l);
+    const float2* pe = E + off(l + 1);
+    for (int i = tid; i < s * s; i += nt) {
+      const int r = i / s, c = i - r * s;
+      const float2 p = pe[(r >> 1) * sc + (c >> 1)];
+      const float2 g = a[i];
+      const float f = __ldg(&iw[i]), q = __ldg(&rr[i]);
+      a[i] = make_float2(g.x * f + q * p.x, g.y * f + q * p.y);
+    }
+    __syncthreads();
+  }
+}
+
+// w^0 Delta = g^0 + u^0 I_H^h e^1 over a row tile of each window; with two
+// levels e^1 = g^1 / w^1 (the coarsest step) is formed here.
+__global__ void __launch_bounds__(256) fine_cycle_kernel(const PrecArgs A) {
+  const int w = blockIdx.x, q = blockIdx.y, MS = A.MS, rows = MS / A.CL, h = MS / 2;
+  if ((unsigned)A.idx[w] >= (unsigned)A.n_pos) return;
+  const float* u0 = A.pyr;
+  const float* iw1 = A.pyr + lvl_off(MS, 1) + h * h;
+  const float2* e1 = A.g1 + (size_t)w * h * h;
+  float2* out = A.contrib + (size_t)w * MS * MS;
+  for (int i = threadIdx.x; i < rows * MS; i += blockDim.x) {
+    const int r = q * rows + i / MS, c = i % MS, o = r * MS + c, pi = (r >> 1) * h + (c >> 1);
+    float2 e = e1[pi];
+    if (A.L == 2) {
+      const float f = __ldg(&iw1[pi]);
+      e = make_float2(e.x * f, e.y * f);
+    }
+    const float u = __ldg(&u0[o]);
+    const float2 g = out[o];
+    out[o] = make_float2(g.x + u * e.x, g.y + u * e.y);
+  }
 }
