@@ -48,13 +48,18 @@ __device__ __forceinline__ void mma3(float* c, const uint32_t* ah, const uint32_
 // One block: kTcLines lines of one window, loaded to shared memory (separate
 // real and imaginary planes), transformed in two MMA stages, stored back.
 // AXIS 0: lines are columns (element stride MS); AXIS 1: rows.  `scale`
-// multiplies the output.
+// multiplies the output.  Within a line, element i sits at sx(i) = i +
+// 4 (i / QR): every run of QR elements is followed by four pad words, so the
+// fragment loads and stores that stride by QR (stage-1 B columns, the twiddle
+// scatter, stage-2 A rows) hit distinct banks or at most two threads per bank.
+// The line pitch LD = MS + 68 keeps lines four banks apart.
 template <int MS, int AXIS, int INV>
 __global__ void __launch_bounds__(128) dft_tc_kernel(float2* __restrict__ data, const TcTables* __restrict__ tabs,
                                                      const float2* __restrict__ tw, float scale) {
   constexpr int QR = MS / 16;
   static_assert(QR == 4 || QR == 8 || QR == 16, "window side 64, 128 or 256");
-  constexpr int NL = kTcLines, LD = MS + 4;
+  constexpr int NL = kTcLines, LD = MS + 68;
+  auto sx = [](int i) { return i + 4 * (i / QR); };
   constexpr int K2T = (2 * QR + 15) / 16;  // stage-2 k-tiles
   constexpr int N2T = 2 * QR / 8;          // stage-2 n-tiles
   __shared__ float Sr[NL * LD];
@@ -78,8 +83,8 @@ __global__ void __launch_bounds__(128) dft_tc_kernel(float2* __restrict__ data, 
     for (int u = 0; u < 8; ++u) {
       const int i = i0 + 128 * u;
       const int l = AXIS == 1 ? i / MS : i % NL, p = AXIS == 1 ? i % MS : i / NL;
-      Sr[l * LD + p] = v[u].x;
-      Si[l * LD + p] = v[u].y;
+      Sr[l * LD + sx(p)] = v[u].x;
+      Si[l * LD + sx(p)] = v[u].y;
     }
   }
 
@@ -117,10 +122,11 @@ __global__ void __launch_bounds__(128) dft_tc_kernel(float2* __restrict__ data, 
     const float* xi = Si + l * LD + n2;
     uint32_t bh[2][2], bl[2][2];
     // k-tile 0: real parts of n1 = 2t, 2t+1, 2t+8, 2t+9; k-tile 1: imaginary parts
-    split2(xr[QR * (2 * t)], xr[QR * (2 * t + 1)], bh[0][0], bl[0][0]);
-    split2(xr[QR * (2 * t + 8)], xr[QR * (2 * t + 9)], bh[0][1], bl[0][1]);
-    split2(xi[QR * (2 * t)], xi[QR * (2 * t + 1)], bh[1][0], bl[1][0]);
-    split2(xi[QR * (2 * t + 8)], xi[QR * (2 * t + 9)], bh[1][1], bl[1][1]);
+    constexpr int RS = QR + 4;
+    split2(xr[RS * (2 * t)], xr[RS * (2 * t + 1)], bh[0][0], bl[0][0]);
+    split2(xr[RS * (2 * t + 8)], xr[RS * (2 * t + 9)], bh[0][1], bl[0][1]);
+    split2(xi[RS * (2 * t)], xi[RS * (2 * t + 1)], bh[1][0], bl[1][0]);
+    split2(xi[RS * (2 * t + 8)], xi[RS * (2 * t + 9)], bh[1][1], bl[1][1]);
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
@@ -140,8 +146,8 @@ __global__ void __launch_bounds__(128) dft_tc_kernel(float2* __restrict__ data, 
         const float yr = acc[i][0][2 * hh + cc], yi = acc[i][1][2 * hh + cc];
         float2 w = tw[(n2 * k1) % MS];
         if (INV) w.y = -w.y;
-        Sr[l * LD + k1 * QR + n2] = yr * w.x - yi * w.y;
-        Si[l * LD + k1 * QR + n2] = yr * w.y + yi * w.x;
+        Sr[l * LD + sx(k1 * QR + n2)] = yr * w.x - yi * w.y;
+        Si[l * LD + sx(k1 * QR + n2)] = yr * w.y + yi * w.x;
       }
     }
   __syncthreads();
@@ -179,9 +185,9 @@ __global__ void __launch_bounds__(128) dft_tc_kernel(float2* __restrict__ data, 
         const int kk = kt * 16 + 2 * t + (q & 1) + ((q >> 2) & 1) * 8;
         float val = 0.f;
         if (kk < QR)
-          val = Sr[l * LD + row * QR + kk];
+          val = Sr[l * LD + sx(row * QR + kk)];
         else if (kk < 2 * QR)
-          val = Si[l * LD + row * QR + kk - QR];
+          val = Si[l * LD + sx(row * QR + kk - QR)];
         v[q] = val;
       }
 #pragma unroll
@@ -203,9 +209,9 @@ __global__ void __launch_bounds__(128) dft_tc_kernel(float2* __restrict__ data, 
         const int nn = nt * 8 + 2 * t + (e & 1);
         const float v = out[i][nt][e] * scale;
         if (nn < QR)
-          Sr[l * LD + k1 + 16 * nn] = v;
+          Sr[l * LD + sx(k1 + 16 * nn)] = v;
         else
-          Si[l * LD + k1 + 16 * (nn - QR)] = v;
+          Si[l * LD + sx(k1 + 16 * (nn - QR))] = v;
       }
   }
   __syncthreads();
@@ -214,12 +220,12 @@ __global__ void __launch_bounds__(128) dft_tc_kernel(float2* __restrict__ data, 
   if (AXIS == 1) {
     for (int i = tid; i < NL * MS; i += 128) {
       const int l = i / MS, p = i % MS;
-      base[(size_t)(l0 + l) * MS + p] = make_float2(Sr[l * LD + p], Si[l * LD + p]);
+      base[(size_t)(l0 + l) * MS + p] = make_float2(Sr[l * LD + sx(p)], Si[l * LD + sx(p)]);
     }
   } else {
     for (int i = tid; i < NL * MS; i += 128) {
       const int p = i / NL, l = i % NL;
-      base[(size_t)p * MS + l0 + l] = make_float2(Sr[l * LD + p], Si[l * LD + p]);
+      base[(size_t)p * MS + l0 + l] = make_float2(Sr[l * LD + sx(p)], Si[l * LD + sx(p)]);
     }
   }
 }
