@@ -1,4 +1,5 @@
 """Host logic of the benchmark's multi-rank (replica) mode, on CPU with gloo."""
+import json
 import os
 import socket
 import subprocess
@@ -52,3 +53,17 @@ def test_reference_arm_runs_on_rank_0_only():
                         "--steps", "3", "--warmup", "3"], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_reference_arm_times_the_oracle_on_every_core():
+    """Rank 0 of the reference arm prints one line: the FP64 oracle run by one
+    process per host core, its value the line's cpu_baseline and e2e."""
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1", LOCAL_RANK="0")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "tiny",
+                        "--steps", "2", "--warmup", "3"], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["cores"] == bench.host_cores()
+    assert line["cpu_baseline"]["value"] == line["value"] == line["e2e"]["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
