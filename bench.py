@@ -434,6 +434,58 @@ def nrmse_lit(z, z_true, q2, pos, rel: float = 1e-3) -> float:
     return float(np.linalg.norm(ph * a - b) / np.linalg.norm(b))
 
 
+def sweeps_to_nrmse(w, dev, magpie, target: float, max_sweeps: int, every: int = 10) -> dict:
+    """Sweeps of workload w from z = 1 until the object's NRMSE against the
+    truth (global phase removed, lit pixels, as nrmse_lit) is at most
+    `target`, checked every `every` sweeps, or `max_sweeps` have run.  Only the
+    sweeps are timed (CUDA events around each chunk); the checks are not."""
+    import torch
+    z_true, Qt, post, dt, _ = make_data(w, dev, magpie)
+    q2 = np.abs(Qt.cpu().numpy().astype(np.complex128)) ** 2
+    pos = post.cpu().numpy()
+    cov = np.zeros(z_true.shape)
+    for r, c in pos:
+        cov[r:r + w.m, c:c + w.m] += q2
+    lit = torch.from_numpy(cov >= 1e-3 * cov.max()).to(dev)
+    zt = torch.from_numpy(z_true.astype(np.complex64)).to(dev)[lit].to(torch.complex128)
+    z = torch.ones((w.n, w.n), dtype=torch.complex64, device=dev)
+    ctx = magpie.magpie_create(magpie.magpie_params_of(w.n, w.n, w.m, w.n_pos, w.levels, w.minibatch, w.alpha),
+                               z, Qt, post, dt)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sweeps, ms, err, best = 0, 0.0, 1.0, 1.0
+    while sweeps < max_sweeps and err > target:
+        orders = [torch.from_numpy(synth.make_order(w.n_pos, sweeps + i)).to(dev) for i in range(every)]
+        torch.cuda.synchronize()
+        ev0.record()
+        for o in orders:
+            magpie.magpie_sweep(ctx, o)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms += ev0.elapsed_time(ev1)
+        sweeps += every
+        a = z[lit].to(torch.complex128)
+        ip = torch.vdot(a, zt)
+        ph = ip / ip.abs() if ip.abs() > 0 else 1.0
+        err = float(torch.linalg.vector_norm(ph * a - zt) / torch.linalg.vector_norm(zt))
+        best = min(best, err)
+    ctx.close()
+    return {"levels": w.levels, "minibatch": w.minibatch, "reached": err <= target, "sweeps": sweeps,
+            "seconds": ms * 1e-3, "nrmse": err, "best_nrmse": best}
+
+
+def time_to_nrmse(w, dev, magpie) -> dict:
+    """Wall time (device, sweeps only) to NRMSE <= 1e-3 on the noise-free
+    version of workload w, for the default form (w's levels and minibatch)
+    and for the fastest setting measured to reach it (one level, minibatch
+    16).  With 1e6 photons per pattern the NRMSE of every form levels off
+    near 0.09, so the target is only reachable on noise-free data."""
+    import dataclasses
+    clean = dataclasses.replace(w, photons=None)
+    chosen = sweeps_to_nrmse(dataclasses.replace(clean, levels=1, minibatch=16), dev, magpie, 1e-3, 3000)
+    plain = sweeps_to_nrmse(clean, dev, magpie, 1e-3, 3000)
+    return {"target": 1e-3, "data": f"noise-free intensities of {w.name}", "chosen": chosen, "plain": plain}
+
+
 def launches_per_step(args, w) -> int:
     """Kernel launches of one minibatch step of the configured form."""
     if args.learned:
@@ -566,6 +618,9 @@ def run_ours(args, w):
     magpie.magpie_sync(ctx)
     e2e_s = max_over_ranks(time.perf_counter() - t0, pg, dev)
 
+    ttn = time_to_nrmse(w, dev, magpie) if (w.name == synth.WORKLOADS["mid"].name and args.dft == "fft"
+                                            and not args.learned and rank == 0 and world == 1) else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v1, nwin1, el1 = oracle_windows_per_second(w, budget_s=30.0)
@@ -588,6 +643,7 @@ def run_ours(args, w):
             "config": dict(config_of(w), workload=("learned correction on " + w.name) if args.learned else w.name,
                            dft="tensor-core BF16 hi+lo" if args.dft == "tc" else "FP32 FFT"),
             "quality": quality,
+            "time_to_nrmse": ttn,
             "training": train_info,
             "roofline": ({"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": achieved_tf / alu_peak, "traffic": traffic,
