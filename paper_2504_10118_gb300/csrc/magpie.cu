@@ -55,6 +55,8 @@ namespace cg = cooperative_groups;
 constexpr int kVersion = 10100;  // 1.1.0
 constexpr int kMaxMinibatch = 4096;  // the update kernel keeps the minibatch's corners in smem (48 KiB)
 constexpr int kMaxCluster = 8;       // largest number of blocks per window
+constexpr int kMaxSlots = 16;        // partial-sum slots per window: the window kernel's blocks, or m / 16
+                                     // blocks of the precision form (m <= 256)
 constexpr int kApplyUnroll = 4;      // increments in flight per thread in the update kernel
 
 #include "fft_lines.cuh"
@@ -81,8 +83,8 @@ struct ApplyArgs {
   const float2* contrib;   // [count][MS][MS] increments w . Delta
   const float* w0;         // [MS][MS] u + |Q|^2
   int MS;
-  const double* part;      // [count][CL][2] block partials of the window kernel
-  int CL;
+  const double* part;      // [count][slots][2] partial sums of the window phase
+  int slots;               // partial-sum slots per window
   double* phi_pos;         // per-window Phi_k
   double* gn_pos;          // per-window ||grad Phi_k||
   int tiles_x;             // tiles per object row
@@ -100,9 +102,9 @@ __device__ __forceinline__ void apply_body(const ApplyArgs& P, const int tx, con
       const int k = P.idx[b];
       if ((unsigned)k >= (unsigned)P.n_pos) continue;
       double a = 0.0, g = 0.0;
-      for (int q = 0; q < P.CL; ++q) {
-        a += P.part[(size_t)(b * P.CL + q) * 2];
-        g += P.part[(size_t)(b * P.CL + q) * 2 + 1];
+      for (int q = 0; q < P.slots; ++q) {
+        a += P.part[(size_t)(b * P.slots + q) * 2];
+        g += P.part[(size_t)(b * P.slots + q) * 2 + 1];
       }
       P.phi_pos[k] = a / (2.0 * (double)MS * (double)MS);
       P.gn_pos[k] = sqrt(g);
@@ -497,7 +499,7 @@ cudaError_t enqueue_pyramid(const float2* Q, int MS, int L, float alpha, unsigne
 
 ApplyArgs apply_args(float2* z, int n_rows, int n_cols, const int2* corners, const int32_t* idx, int count, int n_pos,
                      const float2* contrib, const float* w0, int MS, const double* part, double* phi_pos,
-                     double* gn_pos) {
+                     double* gn_pos, int slots = 0) {
   ApplyArgs P{};
   P.z = z;
   P.n_rows = n_rows;
@@ -510,7 +512,7 @@ ApplyArgs apply_args(float2* z, int n_rows, int n_cols, const int2* corners, con
   P.w0 = w0;
   P.MS = MS;
   P.part = part;
-  P.CL = cluster_of(MS);
+  P.slots = slots ? slots : cluster_of(MS);  // default: one per block of the window kernel
   P.phi_pos = phi_pos;
   P.gn_pos = gn_pos;
   P.tiles_x = (n_cols + kApplyTile - 1) / kApplyTile;
@@ -522,8 +524,9 @@ int apply_tiles(const ApplyArgs& P) { return P.tiles_x * ((P.n_rows + kApplyTile
 
 cudaError_t launch_apply(float2* z, int n_rows, int n_cols, const int2* corners, const int32_t* idx, int count,
                          int n_pos, const float2* contrib, const float* w0, int MS, const double* part,
-                         double* phi_pos, double* gn_pos, cudaStream_t st) {
-  const ApplyArgs P = apply_args(z, n_rows, n_cols, corners, idx, count, n_pos, contrib, w0, MS, part, phi_pos, gn_pos);
+                         double* phi_pos, double* gn_pos, cudaStream_t st, int slots = 0) {
+  const ApplyArgs P =
+      apply_args(z, n_rows, n_cols, corners, idx, count, n_pos, contrib, w0, MS, part, phi_pos, gn_pos, slots);
   const dim3 tiles(P.tiles_x, (n_rows + kApplyTile - 1) / kApplyTile);
   apply_kernel<<<tiles, 256, (sizeof(int2) + sizeof(int)) * count, st>>>(P);
   return cudaGetLastError();
@@ -710,7 +713,7 @@ struct magpie_ctx {
   float2* contrib = nullptr;
   double* phi_pos = nullptr;
   double* gn_pos = nullptr;
-  double* part = nullptr;     // [n_pos][kMaxCluster][2] per-block partial sums
+  double* part = nullptr;     // [n_pos][kMaxSlots][2] per-block partial sums
   int2* corner = nullptr;     // [minibatch] corners of a step's windows
   unsigned long long* mx = nullptr;  // max |Q|^2 (bits of a double)
   float2* pnum = nullptr;     // probe step: [minibatch][m][m]
@@ -1082,6 +1085,7 @@ PrecArgs precision_args(magpie_ctx* c, const int32_t* idx) {
   a.n_pos = c->p.n_pos;
   a.MS = c->p.m;
   a.CL = cluster_of(c->p.m);
+  a.T = c->p.m / kTcLines;
   a.buf = c->pbuf;
   a.contrib = c->contrib;
   a.part = c->part;
@@ -1094,17 +1098,24 @@ PrecArgs precision_args(magpie_ctx* c, const int32_t* idx) {
   return a;
 }
 
+template <int MS>
+cudaError_t launch_precision_g0(const PrecArgs& a, int count, const TcTables* tabs, const float2* tw,
+                                cudaStream_t st) {
+  const dim3 grid((unsigned)count * (MS / kTcLines));
+  exit_dft_kernel<MS><<<grid, 128, 0, st>>>(a, tabs, tw);
+  project_dft_kernel<MS><<<grid, 128, 0, st>>>(a, tabs, tw);
+  grad_dft_kernel<MS><<<grid, 128, 0, st>>>(a, tabs, tw);
+  return cudaGetLastError();
+}
+
 int enqueue_precision_g0(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st) {
   const PrecArgs a = precision_args(c, idx);
-  const dim3 tiles((unsigned)count, (unsigned)a.CL);
-  exit_wave_kernel<<<tiles, 256, 0, st>>>(a);
-  CUDA_TRY(cudaGetLastError());
-  CUDA_TRY(launch_dft2_tc_m(a.MS, c->pbuf, count, c->tabs, c->tw, 0, st));
-  projection_kernel<<<tiles, 256, 0, st>>>(a);
-  CUDA_TRY(cudaGetLastError());
-  CUDA_TRY(launch_dft2_tc_m(a.MS, c->pbuf, count, c->tabs, c->tw, 1, st));
-  grad_kernel<<<tiles, 256, 0, st>>>(a);
-  CUDA_TRY(cudaGetLastError());
+  switch (a.MS) {
+    case 64: CUDA_TRY(launch_precision_g0<64>(a, count, c->tabs, c->tw, st)); break;
+    case 128: CUDA_TRY(launch_precision_g0<128>(a, count, c->tabs, c->tw, st)); break;
+    case 256: CUDA_TRY(launch_precision_g0<256>(a, count, c->tabs, c->tw, st)); break;
+    default: return fail(MAGPIE_EUNSUPPORTED, "the precision form needs m = 64, 128 or 256");
+  }
   return MAGPIE_OK;
 }
 
@@ -1144,7 +1155,8 @@ int enqueue_step(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st, 
   if (ev) CUDA_TRY(cudaEventRecord(ev[1], st));
   if (ev) CUDA_TRY(cudaEventRecord(ev[2], st));
   CUDA_TRY(launch_apply(c->z, c->p.n_rows, c->p.n_cols, c->corner, idx, count, c->p.n_pos, c->contrib,
-                        c->pyr + c->M, c->p.m, c->part, c->phi_pos, c->gn_pos, st));
+                        c->pyr + c->M, c->p.m, c->part, c->phi_pos, c->gn_pos, st,
+                        c->precision ? c->p.m / kTcLines : 0));
   if (c->p.update_probe) {
     probe_apply_kernel<<<(c->M + 255) / 256, 256, 0, st>>>(c->Q, c->M, idx, count, c->p.n_pos, c->pnum, c->pa2,
                                                            c->pmax, cluster_of(c->p.m), c->p.beta);
@@ -1476,7 +1488,7 @@ int magpie_create(magpie_ctx** out, const magpie_params* params, void* object, c
       (rc = alloc((void**)&c->pyr_q, sizeof(double2) * 2 * M)) || (rc = alloc((void**)&c->pyr_u, sizeof(double) * 2 * M)) ||
       (rc = alloc((void**)&c->contrib, sizeof(float2) * M * p.minibatch)) ||
       (rc = alloc((void**)&c->phi_pos, sizeof(double) * N)) || (rc = alloc((void**)&c->gn_pos, sizeof(double) * N)) ||
-      (rc = alloc((void**)&c->part, sizeof(double) * 2 * kMaxCluster * N)) ||
+      (rc = alloc((void**)&c->part, sizeof(double) * 2 * kMaxSlots * N)) ||
       (rc = alloc((void**)&c->mx, sizeof(unsigned long long))) ||
       (rc = alloc((void**)&c->corner, sizeof(int2) * p.minibatch)) ||
       (p.update_probe && (rc = alloc((void**)&c->pnum, sizeof(float2) * M * p.minibatch))) ||

@@ -45,48 +45,69 @@ __device__ __forceinline__ void mma3(float* c, const uint32_t* ah, const uint32_
   mma_bf16(c, al, bh);
 }
 
-// One block: kTcLines lines of one window, loaded to shared memory (separate
-// real and imaginary planes), transformed in two MMA stages, stored back.
-// AXIS 0: lines are columns (element stride MS); AXIS 1: rows.  `scale`
-// multiplies the output.  Within a line, element i sits at sx(i) = i +
-// 4 (i / QR): every run of QR elements is followed by four pad words, so the
-// fragment loads and stores that stride by QR (stage-1 B columns, the twiddle
-// scatter, stage-2 A rows) hit distinct banks or at most two threads per bank.
-// The line pitch LD = MS + 68 keeps lines four banks apart.
-template <int MS, int AXIS, int INV>
-__global__ void __launch_bounds__(128) dft_tc_kernel(float2* __restrict__ data, const TcTables* __restrict__ tabs,
-                                                     const float2* __restrict__ tw, float scale) {
-  constexpr int QR = MS / 16;
+// Shared-memory layout of a block's kTcLines lines: separate real and
+// imaginary planes.  Within a line, element i sits at i + 4 (i / Qr): every
+// run of Qr elements is followed by four pad words, so the fragment loads
+// and stores that stride by Qr (stage-1 B columns, the twiddle scatter,
+// stage-2 A rows) hit distinct banks or at most two threads per bank.  The
+// line pitch LD = MS + 68 keeps lines four banks apart.
+template <int MS>
+struct TcSm {
+  static constexpr int QR = MS / 16, NL = kTcLines, LD = MS + 68;
   static_assert(QR == 4 || QR == 8 || QR == 16, "window side 64, 128 or 256");
-  constexpr int NL = kTcLines, LD = MS + 68;
-  auto sx = [](int i) { return i + 4 * (i / QR); };
-  constexpr int K2T = (2 * QR + 15) / 16;  // stage-2 k-tiles
-  constexpr int N2T = 2 * QR / 8;          // stage-2 n-tiles
-  __shared__ float Sr[NL * LD];
-  __shared__ float Si[NL * LD];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int g = lane >> 2, t = lane & 3;
-  const int tiles = MS / NL;
-  const int win = blockIdx.x / tiles, l0 = (blockIdx.x % tiles) * NL;
-  float2* base = data + (size_t)win * MS * MS;
+  __device__ static __forceinline__ int at(int l, int i) { return l * LD + i + 4 * (i / QR); }
+};
 
-  // ---- load, eight loads in flight per thread
+// Fills the NL lines from src(l, p) (line l, position p along the line),
+// eight loads in flight per thread.  AXIS 1: consecutive threads take
+// consecutive positions of a line (rows of a window); AXIS 0: consecutive
+// lines at one position (columns).
+template <int MS, int AXIS, typename Src>
+__device__ __forceinline__ void tc_load(float* Sr, float* Si, Src src) {
+  using S = TcSm<MS>;
+  constexpr int NL = S::NL;
   static_assert((NL * MS) % (128 * 8) == 0, "load batches");
-  for (int i0 = tid; i0 < NL * MS; i0 += 128 * 8) {
+  for (int i0 = threadIdx.x; i0 < NL * MS; i0 += 128 * 8) {
     float2 v[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int i = i0 + 128 * u;
-      v[u] = AXIS == 1 ? base[(size_t)(l0 + i / MS) * MS + i % MS] : base[(size_t)(i / NL) * MS + l0 + i % NL];
+      v[u] = AXIS == 1 ? src(i / MS, i % MS) : src(i % NL, i / NL);
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int i = i0 + 128 * u;
       const int l = AXIS == 1 ? i / MS : i % NL, p = AXIS == 1 ? i % MS : i / NL;
-      Sr[l * LD + sx(p)] = v[u].x;
-      Si[l * LD + sx(p)] = v[u].y;
+      Sr[S::at(l, p)] = v[u].x;
+      Si[S::at(l, p)] = v[u].y;
     }
   }
+}
+
+// dst(l, p, value) for every element of the NL lines, in the thread order of
+// tc_load.
+template <int MS, int AXIS, typename Dst>
+__device__ __forceinline__ void tc_store(const float* Sr, const float* Si, Dst dst) {
+  using S = TcSm<MS>;
+  constexpr int NL = S::NL;
+  for (int i = threadIdx.x; i < NL * MS; i += 128) {
+    const int l = AXIS == 1 ? i / MS : i % NL, p = AXIS == 1 ? i % MS : i / NL;
+    dst(l, p, make_float2(Sr[S::at(l, p)], Si[S::at(l, p)]));
+  }
+}
+
+// The forward (INV = 0) or conjugate (INV = 1) DFT of the block's NL lines,
+// in place in shared memory, the output multiplied by `scale`.  128 threads;
+// begins with a barrier (the lines must be in place) and ends with one.
+template <int MS, int INV>
+__device__ __forceinline__ void tc_lines(float* Sr, float* Si, const TcTables* __restrict__ tabs,
+                                         const float2* __restrict__ tw, float scale) {
+  using S = TcSm<MS>;
+  constexpr int QR = S::QR, NL = S::NL;
+  constexpr int K2T = (2 * QR + 15) / 16;  // stage-2 k-tiles
+  constexpr int N2T = 2 * QR / 8;          // stage-2 n-tiles
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
 
   // ---- stage-1 operands: the 16-point DFT matrix as A fragments (hi, lo)
   uint32_t ah[2][2][4], al[2][2][4];
@@ -118,8 +139,8 @@ __global__ void __launch_bounds__(128) dft_tc_kernel(float2* __restrict__ data, 
   for (int i = 0; i < PER1; ++i) {
     const int j = (warp * PER1 + i) * 8 + g;  // this thread's B column
     const int l = j / QR, n2 = j % QR;
-    const float* xr = Sr + l * LD + n2;
-    const float* xi = Si + l * LD + n2;
+    const float* xr = Sr + S::at(l, n2);
+    const float* xi = Si + S::at(l, n2);
     uint32_t bh[2][2], bl[2][2];
     // k-tile 0: real parts of n1 = 2t, 2t+1, 2t+8, 2t+9; k-tile 1: imaginary parts
     constexpr int RS = QR + 4;
@@ -146,8 +167,8 @@ __global__ void __launch_bounds__(128) dft_tc_kernel(float2* __restrict__ data, 
         const float yr = acc[i][0][2 * hh + cc], yi = acc[i][1][2 * hh + cc];
         float2 w = tw[(n2 * k1) % MS];
         if (INV) w.y = -w.y;
-        Sr[l * LD + sx(k1 * QR + n2)] = yr * w.x - yi * w.y;
-        Si[l * LD + sx(k1 * QR + n2)] = yr * w.y + yi * w.x;
+        Sr[S::at(l, k1 * QR + n2)] = yr * w.x - yi * w.y;
+        Si[S::at(l, k1 * QR + n2)] = yr * w.y + yi * w.x;
       }
     }
   __syncthreads();
@@ -185,9 +206,9 @@ __global__ void __launch_bounds__(128) dft_tc_kernel(float2* __restrict__ data, 
         const int kk = kt * 16 + 2 * t + (q & 1) + ((q >> 2) & 1) * 8;
         float val = 0.f;
         if (kk < QR)
-          val = Sr[l * LD + sx(row * QR + kk)];
+          val = Sr[S::at(l, row * QR + kk)];
         else if (kk < 2 * QR)
-          val = Si[l * LD + sx(row * QR + kk - QR)];
+          val = Si[S::at(l, row * QR + kk - QR)];
         v[q] = val;
       }
 #pragma unroll
@@ -209,25 +230,37 @@ __global__ void __launch_bounds__(128) dft_tc_kernel(float2* __restrict__ data, 
         const int nn = nt * 8 + 2 * t + (e & 1);
         const float v = out[i][nt][e] * scale;
         if (nn < QR)
-          Sr[l * LD + sx(k1 + 16 * nn)] = v;
+          Sr[S::at(l, k1 + 16 * nn)] = v;
         else
-          Si[l * LD + sx(k1 + 16 * (nn - QR))] = v;
+          Si[S::at(l, k1 + 16 * (nn - QR))] = v;
       }
   }
   __syncthreads();
 
-  // ---- store
-  if (AXIS == 1) {
-    for (int i = tid; i < NL * MS; i += 128) {
-      const int l = i / MS, p = i % MS;
-      base[(size_t)(l0 + l) * MS + p] = make_float2(Sr[l * LD + sx(p)], Si[l * LD + sx(p)]);
-    }
-  } else {
-    for (int i = tid; i < NL * MS; i += 128) {
-      const int p = i / NL, l = i % NL;
-      base[(size_t)p * MS + l0 + l] = make_float2(Sr[l * LD + sx(p)], Si[l * LD + sx(p)]);
-    }
-  }
+}
+
+// One block: kTcLines lines of one window through the transform, in place in
+// `data` ([windows][MS][MS]).  AXIS 0: lines are columns (element stride
+// MS); AXIS 1: rows.  `scale` multiplies the output.
+template <int MS, int AXIS, int INV>
+__global__ void __launch_bounds__(128) dft_tc_kernel(float2* __restrict__ data, const TcTables* __restrict__ tabs,
+                                                     const float2* __restrict__ tw, float scale) {
+  using S = TcSm<MS>;
+  __shared__ float Sr[S::NL * S::LD];
+  __shared__ float Si[S::NL * S::LD];
+  const int tiles = MS / S::NL;
+  const int win = blockIdx.x / tiles, l0 = (blockIdx.x % tiles) * S::NL;
+  float2* base = data + (size_t)win * MS * MS;
+  tc_load<MS, AXIS>(Sr, Si, [&](int l, int p) {
+    return AXIS == 1 ? base[(size_t)(l0 + l) * MS + p] : base[(size_t)p * MS + l0 + l];
+  });
+  tc_lines<MS, INV>(Sr, Si, tabs, tw, scale);
+  tc_store<MS, AXIS>(Sr, Si, [&](int l, int p, float2 v) {
+    if (AXIS == 1)
+      base[(size_t)(l0 + l) * MS + p] = v;
+    else
+      base[(size_t)p * MS + l0 + l] = v;
+  });
 }
 
 struct PrecArgs {
@@ -237,10 +270,11 @@ struct PrecArgs {
   const float* amp;    // sqrt(d) [n_pos][MS][MS]
   const int32_t* pos;  // [n_pos][2]
   const int32_t* idx;  // [count]
-  int n_pos, MS, CL;   // CL: row tiles per window (partials layout of the update kernel)
+  int n_pos, MS, CL;   // CL: row tiles per window of the finest V-cycle level
+  int T;               // partial-sum slots per window: one per block of kTcLines lines
   float2* buf;         // [count][MS][MS] exit wave -> spectrum -> revised exit wave
   float2* contrib;     // [count][MS][MS] g^0 = conj(Q)(R - Q z)
-  double* part;        // [count][CL][2] partial sums: (|Psi| - sqrt d)^2, |g^0|^2
+  double* part;        // [count][T][2] partial sums: (|Psi| - sqrt d)^2, |g^0|^2
   int2* corner;        // [count] window corners for the update kernel
   int* err;            // bit 0: window index out of range
   float2* phase;       // phase rule: [n_pos][MS][MS] unit phases of the last visit, else null
@@ -249,106 +283,171 @@ struct PrecArgs {
   int L;               // levels
 };
 
-// buf[w] = Q . z_k (row tile blockIdx.y of window blockIdx.x); records the corner.
-__global__ void __launch_bounds__(256) exit_wave_kernel(const PrecArgs A) {
-  const int w = blockIdx.x, q = blockIdx.y, MS = A.MS, rows = MS / A.CL;
-  const int k = A.idx[w];
-  const bool ok = (unsigned)k < (unsigned)A.n_pos;
-  if (threadIdx.x == 0 && q == 0) {
-    if (ok)
-      A.corner[w] = make_int2(A.pos[2 * k], A.pos[2 * k + 1]);
+// The three window-phase kernels of a minibatch step.  Each block takes
+// kTcLines lines of one window (grid: windows x MS / kTcLines) through one
+// or two tensor-core transforms, with the element-wise steps around them
+// fused into its loads and stores:
+//   exit_dft_kernel    columns: psi = Q . z_k loaded from the object, forward DFT
+//   project_dft_kernel rows:    forward DFT, modulus projection (+ the tile's
+//                               sum of (|Psi| - sqrt d)^2), inverse DFT
+//   grad_dft_kernel    columns: inverse DFT, g^0 = conj(Q)(R - Q z_k) into the
+//                               increments (+ the tile's sum of |g^0|^2), and
+//                               for two levels or more g^1 = W_u^0 . I(g^0)
+// The window buffer holds psi's column transforms, then R's row transforms.
+
+// Window index of block b, its first line, and whether the index is valid.
+struct TcBlock {
+  int w, tile, l0, k;
+  bool ok;
+};
+template <int MS>
+__device__ __forceinline__ TcBlock tc_block(const PrecArgs& A) {
+  constexpr int tiles = MS / kTcLines;
+  TcBlock b;
+  b.w = blockIdx.x / tiles;
+  b.tile = blockIdx.x % tiles;
+  b.l0 = b.tile * kTcLines;
+  b.k = A.idx[b.w];
+  b.ok = (unsigned)b.k < (unsigned)A.n_pos;
+  return b;
+}
+
+template <int MS>
+__global__ void __launch_bounds__(128) exit_dft_kernel(const PrecArgs A, const TcTables* __restrict__ tabs,
+                                                       const float2* __restrict__ tw) {
+  using S = TcSm<MS>;
+  __shared__ float Sr[S::NL * S::LD];
+  __shared__ float Si[S::NL * S::LD];
+  const TcBlock B = tc_block<MS>(A);
+  if (threadIdx.x == 0 && B.tile == 0) {
+    if (B.ok)
+      A.corner[B.w] = make_int2(A.pos[2 * B.k], A.pos[2 * B.k + 1]);
     else {
-      A.corner[w] = make_int2(-(1 << 30), -(1 << 30));
+      A.corner[B.w] = make_int2(-(1 << 30), -(1 << 30));
       atomicOr(A.err, 1);
     }
   }
-  const int pr = ok ? A.pos[2 * k] : 0, pc = ok ? A.pos[2 * k + 1] : 0;
-  float2* out = A.buf + (size_t)w * MS * MS;
-  for (int i = threadIdx.x; i < rows * MS; i += blockDim.x) {
-    const int r = q * rows + i / MS, c = i % MS;
-    float2 v = make_float2(0.f, 0.f);
-    if (ok) {
-      const float2 zz = A.z[(size_t)(pr + r) * A.n_cols + pc + c];
-      const float2 qq = __ldg(&A.Q[r * MS + c]);
-      v = make_float2(qq.x * zz.x - qq.y * zz.y, qq.x * zz.y + qq.y * zz.x);
-    }
-    out[r * MS + c] = v;
-  }
+  const float2* zk = A.z + (B.ok ? (size_t)A.pos[2 * B.k] * A.n_cols + A.pos[2 * B.k + 1] : 0);
+  tc_load<MS, 0>(Sr, Si, [&](int l, int p) {
+    if (!B.ok) return make_float2(0.f, 0.f);
+    const float2 zz = zk[(size_t)p * A.n_cols + B.l0 + l];
+    const float2 qq = __ldg(&A.Q[p * MS + B.l0 + l]);
+    return make_float2(qq.x * zz.x - qq.y * zz.y, qq.x * zz.y + qq.y * zz.x);
+  });
+  tc_lines<MS, 0>(Sr, Si, tabs, tw, 1.f);
+  float2* base = A.buf + (size_t)B.w * MS * MS;
+  tc_store<MS, 0>(Sr, Si, [&](int l, int p, float2 v) { base[(size_t)p * MS + B.l0 + l] = v; });
 }
 
-// Fourier modulus projection in place: Psi <- sqrt(d) Psi / |Psi| / m^2
-// (sqrt(d) / m^2 where Psi = 0), and the tile's sum of (|Psi| - sqrt d)^2.
-__global__ void __launch_bounds__(256) projection_kernel(const PrecArgs A) {
-  __shared__ double red[32];
-  const int w = blockIdx.x, q = blockIdx.y, MS = A.MS, rows = MS / A.CL;
-  const int k = A.idx[w];
-  const bool ok = (unsigned)k < (unsigned)A.n_pos;
-  float2* P = A.buf + (size_t)w * MS * MS;
-  const float* am = A.amp + (size_t)(ok ? k : 0) * MS * MS;
+template <int MS>
+__global__ void __launch_bounds__(128) project_dft_kernel(const PrecArgs A, const TcTables* __restrict__ tabs,
+                                                          const float2* __restrict__ tw) {
+  using S = TcSm<MS>;
+  __shared__ float Sr[S::NL * S::LD];
+  __shared__ float Si[S::NL * S::LD];
+  __shared__ double red[4];
+  const TcBlock B = tc_block<MS>(A);
+  float2* base = A.buf + (size_t)B.w * MS * MS;
+  tc_load<MS, 1>(Sr, Si, [&](int l, int p) { return base[(size_t)(B.l0 + l) * MS + p]; });
+  tc_lines<MS, 0>(Sr, Si, tabs, tw, 1.f);
+  // Psi <- sqrt(d) Psi / |Psi| / m^2 (sqrt(d) / m^2 where Psi = 0, or the
+  // previous visit's phase under the phase rule)
+  const float* am = A.amp + (size_t)(B.ok ? B.k : 0) * MS * MS;
   const float inv_m2 = 1.f / (float)(MS * MS);
   float res = 0.f;
-  for (int i = threadIdx.x; i < rows * MS; i += blockDim.x) {
-    const int o = q * rows * MS + i;
-    const float2 v = P[o];
-    const float a = ok ? __ldg(&am[o]) : 0.f;
-    const float n2 = v.x * v.x + v.y * v.y;
-    const float mag = sqrtf(n2);
-    const float d = mag - a;
-    res += d * d;
-    float2 u = make_float2(1.f, 0.f);  // theta(0) = 0
-    if (n2 > 0.f) {
-      u = make_float2(v.x / mag, v.y / mag);
-      if (A.phase && ok) A.phase[(size_t)k * MS * MS + o] = u;
-    } else if (A.phase && ok) {
-      u = A.phase[(size_t)k * MS * MS + o];  // Eq. (specification): the previous visit's phase
+  for (int i0 = threadIdx.x; i0 < S::NL * MS; i0 += 128 * 8) {
+    float av[8];  // eight amplitude loads in flight per thread
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = i0 + 128 * u;
+      av[u] = B.ok ? __ldg(&am[(B.l0 + i / MS) * MS + i % MS]) : 0.f;
     }
-    P[o] = make_float2(a * inv_m2 * u.x, a * inv_m2 * u.y);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = i0 + 128 * u;
+      const int l = i / MS, p = i % MS, o = (B.l0 + l) * MS + p;
+      const float vx = Sr[S::at(l, p)], vy = Si[S::at(l, p)];
+      const float a = av[u];
+      const float n2 = vx * vx + vy * vy;
+      const float mag = sqrtf(n2);
+      const float d = mag - a;
+      res += d * d;
+      float2 ph = make_float2(1.f, 0.f);  // theta(0) = 0
+      if (n2 > 0.f) {
+        ph = make_float2(vx / mag, vy / mag);
+        if (A.phase && B.ok) A.phase[(size_t)B.k * MS * MS + o] = ph;
+      } else if (A.phase && B.ok) {
+        ph = A.phase[(size_t)B.k * MS * MS + o];  // Eq. (specification): the previous visit's phase
+      }
+      Sr[S::at(l, p)] = a * inv_m2 * ph.x;
+      Si[S::at(l, p)] = a * inv_m2 * ph.y;
+    }
   }
-  const double s = block_sum((double)res, red, threadIdx.x, blockDim.x);
-  if (threadIdx.x == 0) A.part[((size_t)w * A.CL + q) * 2] = ok ? s : 0.0;
+  const double s = block_sum((double)res, red, threadIdx.x, 128);
+  if (threadIdx.x == 0) A.part[((size_t)B.w * A.T + B.tile) * 2] = B.ok ? s : 0.0;
+  tc_lines<MS, 1>(Sr, Si, tabs, tw, 1.f);
+  tc_store<MS, 1>(Sr, Si, [&](int l, int p, float2 v) { base[(size_t)(B.l0 + l) * MS + p] = v; });
 }
 
-// g^0 = conj(Q)(R - Q z_k) into the increments, and the tile's sum of |g^0|^2.
-__global__ void __launch_bounds__(256) grad_kernel(const PrecArgs A) {
-  __shared__ double red[32];
-  const int w = blockIdx.x, q = blockIdx.y, MS = A.MS, rows = MS / A.CL, h = MS / 2;
-  const int k = A.idx[w];
-  const bool ok = (unsigned)k < (unsigned)A.n_pos;
-  const int pr = ok ? A.pos[2 * k] : 0, pc = ok ? A.pos[2 * k + 1] : 0;
-  const float2* R = A.buf + (size_t)w * MS * MS;
-  float2* out = A.contrib + (size_t)w * MS * MS;
-  const float* wu0 = A.pyr + lvl_off(MS, 1);
+template <int MS>
+__global__ void __launch_bounds__(128) grad_dft_kernel(const PrecArgs A, const TcTables* __restrict__ tabs,
+                                                       const float2* __restrict__ tw) {
+  using S = TcSm<MS>;
+  constexpr int NL = S::NL, h = MS / 2;
+  __shared__ float Sr[NL * S::LD];
+  __shared__ float Si[NL * S::LD];
+  __shared__ double red[4];
+  const TcBlock B = tc_block<MS>(A);
+  const float2* base = A.buf + (size_t)B.w * MS * MS;
+  tc_load<MS, 0>(Sr, Si, [&](int l, int p) { return base[(size_t)p * MS + B.l0 + l]; });
+  tc_lines<MS, 1>(Sr, Si, tabs, tw, 1.f);
+  const float2* zk = A.z + (B.ok ? (size_t)A.pos[2 * B.k] * A.n_cols + A.pos[2 * B.k + 1] : 0);
+  float2* out = A.contrib + (size_t)B.w * MS * MS;
   float gn = 0.f;
-  // one 2 x 2 bin per iteration: its four g^0 and, for two levels or more,
-  // g^1 = W_u^0 . (mean of the four)
-  for (int i = threadIdx.x; i < (rows / 2) * h; i += blockDim.x) {
-    const int br = q * (rows / 2) + i / h, bc = i % h;
-    float2 sum = make_float2(0.f, 0.f);
+  for (int i0 = threadIdx.x; i0 < NL * MS; i0 += 128 * 8) {
+    float2 zv[8], qv[8];  // eight object and probe loads in flight per thread
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+    for (int u = 0; u < 8; ++u) {
+      const int i = i0 + 128 * u, c = B.l0 + i % NL, p = i / NL;
+      zv[u] = B.ok ? zk[(size_t)p * A.n_cols + c] : make_float2(0.f, 0.f);
+      qv[u] = __ldg(&A.Q[p * MS + c]);
+    }
 #pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        const int r = 2 * br + a, c = 2 * bc + b, o = r * MS + c;
-        float2 g = make_float2(0.f, 0.f);
-        if (ok) {
-          const float2 zz = A.z[(size_t)(pr + r) * A.n_cols + pc + c];
-          const float2 qq = __ldg(&A.Q[o]);
-          const float2 rr = R[o];
-          const float2 d = make_float2(rr.x - (qq.x * zz.x - qq.y * zz.y), rr.y - (qq.x * zz.y + qq.y * zz.x));
-          g = make_float2(qq.x * d.x + qq.y * d.y, qq.x * d.y - qq.y * d.x);
-        }
-        gn += g.x * g.x + g.y * g.y;
-        out[o] = g;
-        sum.x += g.x;
-        sum.y += g.y;
+    for (int u = 0; u < 8; ++u) {
+      const int i = i0 + 128 * u, l = i % NL, p = i / NL, c = B.l0 + l;
+      const float2 zz = zv[u], qq = qv[u];
+      float2 g = make_float2(0.f, 0.f);
+      if (B.ok) {
+        const float dx = Sr[S::at(l, p)] - (qq.x * zz.x - qq.y * zz.y);
+        const float dy = Si[S::at(l, p)] - (qq.x * zz.y + qq.y * zz.x);
+        g = make_float2(qq.x * dx + qq.y * dy, qq.x * dy - qq.y * dx);
       }
-    if (A.g1) {
-      const float f = 0.25f * __ldg(&wu0[br * h + bc]);
-      A.g1[(size_t)w * h * h + br * h + bc] = make_float2(f * sum.x, f * sum.y);
+      gn += g.x * g.x + g.y * g.y;
+      out[(size_t)p * MS + c] = g;
+      Sr[S::at(l, p)] = g.x;
+      Si[S::at(l, p)] = g.y;
     }
   }
-  const double s = block_sum((double)gn, red, threadIdx.x, blockDim.x);
-  if (threadIdx.x == 0) A.part[((size_t)w * A.CL + q) * 2 + 1] = ok ? s : 0.0;
+  const double s = block_sum((double)gn, red, threadIdx.x, 128);  // also the barrier before g^1
+  if (threadIdx.x == 0) A.part[((size_t)B.w * A.T + B.tile) * 2 + 1] = B.ok ? s : 0.0;
+  if (A.g1) {
+    // the block's NL / 2 bin columns, every bin row; the four g^0 of a bin
+    // summed row by row
+    const float* wu0 = A.pyr + lvl_off(MS, 1);
+    for (int i = threadIdx.x; i < (NL / 2) * h; i += 128) {
+      const int j = i % (NL / 2), br = i / (NL / 2), bc = B.l0 / 2 + j;
+      float sx = 0.f, sy = 0.f;
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          sx += Sr[S::at(2 * j + b, 2 * br + a)];
+          sy += Si[S::at(2 * j + b, 2 * br + a)];
+        }
+      const float f = 0.25f * __ldg(&wu0[br * h + bc]);
+      A.g1[(size_t)B.w * h * h + br * h + bc] = make_float2(f * sx, f * sy);
+    }
+  }
 }
 
 // Levels 2 .. L-1 of the V-cycle of one window (levels >= 3), one block per
