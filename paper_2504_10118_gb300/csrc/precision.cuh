@@ -54,6 +54,9 @@ __device__ __forceinline__ void mma3(float* c, const uint32_t* ah, const uint32_
 template <int MS>
 struct TcSm {
   static constexpr int QR = MS / 16, NL = kTcLines, LD = MS + 68;
+  // resident blocks per SM the fused kernels' registers are bounded for
+  // (m = 256: three 128-thread blocks, which measured faster than two)
+  static constexpr int MIN_BLOCKS = MS == 256 ? 3 : 1;
   static_assert(QR == 4 || QR == 8 || QR == 16, "window side 64, 128 or 256");
   __device__ static __forceinline__ int at(int l, int i) { return l * LD + i + 4 * (i / QR); }
 };
@@ -313,7 +316,7 @@ __device__ __forceinline__ TcBlock tc_block(const PrecArgs& A) {
 }
 
 template <int MS>
-__global__ void __launch_bounds__(128) exit_dft_kernel(const PrecArgs A, const TcTables* __restrict__ tabs,
+__global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) exit_dft_kernel(const PrecArgs A, const TcTables* __restrict__ tabs,
                                                        const float2* __restrict__ tw) {
   using S = TcSm<MS>;
   __shared__ float Sr[S::NL * S::LD];
@@ -340,7 +343,7 @@ __global__ void __launch_bounds__(128) exit_dft_kernel(const PrecArgs A, const T
 }
 
 template <int MS>
-__global__ void __launch_bounds__(128) project_dft_kernel(const PrecArgs A, const TcTables* __restrict__ tabs,
+__global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) project_dft_kernel(const PrecArgs A, const TcTables* __restrict__ tabs,
                                                           const float2* __restrict__ tw) {
   using S = TcSm<MS>;
   __shared__ float Sr[S::NL * S::LD];
@@ -390,7 +393,7 @@ __global__ void __launch_bounds__(128) project_dft_kernel(const PrecArgs A, cons
 }
 
 template <int MS>
-__global__ void __launch_bounds__(128) grad_dft_kernel(const PrecArgs A, const TcTables* __restrict__ tabs,
+__global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) grad_dft_kernel(const PrecArgs A, const TcTables* __restrict__ tabs,
                                                        const float2* __restrict__ tw) {
   using S = TcSm<MS>;
   constexpr int NL = S::NL, h = MS / 2;
@@ -433,8 +436,18 @@ __global__ void __launch_bounds__(128) grad_dft_kernel(const PrecArgs A, const T
   if (A.g1) {
     // the block's NL / 2 bin columns, every bin row; the four g^0 of a bin
     // summed row by row
+    constexpr int NB = (NL / 2) * h / 128;  // bins per thread
+    static_assert(NB >= 1 && (NL / 2) * h % 128 == 0, "bins per thread");
     const float* wu0 = A.pyr + lvl_off(MS, 1);
-    for (int i = threadIdx.x; i < (NL / 2) * h; i += 128) {
+    float wv[NB];  // the bins' W_u^0, loaded together
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      const int i = threadIdx.x + 128 * u;
+      wv[u] = __ldg(&wu0[(i / (NL / 2)) * h + B.l0 / 2 + i % (NL / 2)]);
+    }
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      const int i = threadIdx.x + 128 * u;
       const int j = i % (NL / 2), br = i / (NL / 2), bc = B.l0 / 2 + j;
       float sx = 0.f, sy = 0.f;
 #pragma unroll
@@ -444,7 +457,7 @@ __global__ void __launch_bounds__(128) grad_dft_kernel(const PrecArgs A, const T
           sx += Sr[S::at(2 * j + b, 2 * br + a)];
           sy += Si[S::at(2 * j + b, 2 * br + a)];
         }
-      const float f = 0.25f * __ldg(&wu0[br * h + bc]);
+      const float f = 0.25f * wv[u];
       A.g1[(size_t)B.w * h * h + br * h + bc] = make_float2(f * sx, f * sy);
     }
   }
