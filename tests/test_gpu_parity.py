@@ -210,6 +210,32 @@ def test_sweeps_are_bitwise_reproducible():
     assert np.array_equal(outs[0], outs[1])
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_checkpoint_and_resume_is_bitwise(precision):
+    """Checkpoint/resume: the reconstruction state is the caller's object
+    (the probe is fixed), so six sweeps, a host copy of the object, a fresh
+    context built from that copy and six more sweeps give bit for bit the
+    object of twelve uninterrupted sweeps, for the FP32 and the precision
+    form alike."""
+    P = Problem(160, 64, 5, 20, 1, 3, 8)
+    orders = [dev_i32(synth.make_order(P.N, it)) for it in range(12)]
+
+    def run(z, sweeps):
+        ctx = P.ctx(z=z)
+        if precision:
+            magpie.magpie_set_precision(ctx, 1)
+        for o in sweeps:
+            magpie.magpie_sweep(ctx, o)
+        out = P.z_gpu()
+        ctx.close()
+        return out
+
+    straight = run(None, orders)
+    saved = run(None, orders[:6]).astype(np.complex64)  # the checkpoint: a host copy of the object
+    resumed = run(saved.astype(np.complex128), orders[6:])
+    assert np.array_equal(straight, resumed)
+
+
 def oracle_with_float32_ffts():
     """A private copy of the oracle whose 2-D DFTs run in float32 (SciPy),
     used only to measure how much float32 rounding alone moves a result."""
