@@ -351,6 +351,12 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) project_dft_kernel(
   __shared__ double red[4];
   const TcBlock B = tc_block<MS>(A);
   float2* base = A.buf + (size_t)B.w * MS * MS;
+  if (B.ok) {
+    // the block's amplitude rows on their way into L2 while the forward transform runs
+    const char* ab = reinterpret_cast<const char*>(A.amp + (size_t)B.k * MS * MS + (size_t)B.l0 * MS);
+    for (int i = threadIdx.x; i < S::NL * MS * 4 / 128; i += 128)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(ab + 128 * i)));
+  }
   tc_load<MS, 1>(Sr, Si, [&](int l, int p) { return base[(size_t)(B.l0 + l) * MS + p]; });
   tc_lines<MS, 0>(Sr, Si, tabs, tw, 1.f);
   // Psi <- sqrt(d) Psi / |Psi| / m^2 (sqrt(d) / m^2 where Psi = 0, or the
