@@ -176,6 +176,38 @@ def test_learned_step_matches_oracle(levels, seed, scale):
     assert prop == len(batch) and kept == int(np.sum(acc))
 
 
+@pytest.mark.parametrize("levels", [2, 3])
+def test_learned_step_on_precision_form_matches_oracle(levels):
+    """The learned correction on top of the precision form (tensor-core
+    DFTs, m = 64): one 8-window step against the FP64 oracle's learned step;
+    the keep/reject decisions of the clearly decided windows, the margins and
+    the object, within the transforms' own error."""
+    import dataclasses
+    w = dataclasses.replace(synth.WORKLOADS["tiny"], name="n160-m64", n=160, m=64, grid=5, step=20, jitter=1)
+    z_true, Q, pos = synth.make_problem(w)
+    d = O.forward_intensities(z_true, Q, pos)
+    rng = np.random.default_rng(35)
+    z0 = (np.ones((w.n, w.n)) + 0.1 * rng.normal(size=(w.n, w.n)) * np.exp(1j * rng.normal(size=(w.n, w.n))))
+    z0 = z0.astype(np.complex64).astype(np.complex128)
+    h = w.m >> (levels - 1)
+    theta = random_theta(L, 36 + levels, scale=0.3).astype(np.float32).astype(np.float64)
+    ctx, zt = make_ctx(w, z0, Q, pos, d, levels, 8)
+    magpie.magpie_set_precision(ctx, 1)
+    magpie.magpie_attach_cnn(ctx, net_with(theta, h, 8))
+    batch = np.array([0, 3, 6, 9, 12, 16, 20, 24], dtype=np.int32)
+    magpie.magpie_step(ctx, torch.from_numpy(batch).to(DEV))
+    acc, margin = magpie.magpie_learned_window_values(ctx, len(batch))
+    u = O.rpie_regulariser(Q, w.alpha)
+    zo, acc_o, marg_o = L.learned_minibatch_step(z0, Q, pos, d, u, levels, list(batch), theta)
+    clear = np.abs(marg_o) > 1e-3 * np.abs(marg_o).max()
+    e = rel(zt.cpu().numpy(), zo)
+    print(f"levels={levels}: object {e:.2e}, kept {int(np.sum(acc))} of {len(batch)}, "
+          f"margins {rel(np.array(margin)[clear], marg_o[clear]):.2e}")
+    assert np.array_equal(np.array(acc)[clear], acc_o[clear])
+    assert rel(np.array(margin)[clear], marg_o[clear]) < 2e-2
+    assert e < 1e-4
+
+
 def test_zero_last_layer_is_plain_step():
     """A network whose last layer is zero proposes the plain coarse step: every
     window keeps it and the step equals the plain step."""
