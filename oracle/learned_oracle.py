@@ -22,9 +22,10 @@ its reasons in the design notes of the repository:
     the learned output is kept only when its value is not larger, otherwise
     the plain V-cycle output is used (the plain coarse solve is both the
     fallback and the judge).
-  * Training target: the change of z_H over T further V-cycles of the same
-    window with refreshed R (a window-local trajectory of the plain solver),
-    in the network's scaled units: t = (z_H^(T) - z_H^(0)) / s - e_plain / s.
+  * Training target: the change of the window's coarse object z_H between
+    the input state and a later state of the plain solver (its final state,
+    or T further V-cycles of that window alone with refreshed R), in the
+    network's scaled units: t = (z_H^(T) - z_H^(0)) / s - e_plain / s.
   * Arithmetic of the network as the CUDA path does it: BF16 weights and
     BF16 activations between layers, products accumulated in FP32 (here
     FP64), FP32 biases.  `bf16` rounds to nearest even.
