@@ -116,6 +116,22 @@ def test_minibatch_step(n, m, grid, step, jit, L, B, cnt):
     ctx.close()
 
 
+def test_largest_minibatch():
+    """The largest minibatch the library takes (4096 windows, the update
+    kernel's corner list filling 48 KiB of shared memory): one step of
+    4096 windows of 8 x 8 on a 64 x 64 raster against the oracle."""
+    P = Problem(136, 8, 64, 2, 0, 2, 4096, seed=41)
+    assert P.N == 4096
+    ctx = P.ctx()
+    batch = synth.make_order(P.N, 3)
+    magpie.magpie_step(ctx, dev_i32(batch))
+    got = P.z_gpu()
+    ref = O.minibatch_step(P.z0, P.Q, P.pos, P.d, P.u, 2, batch)
+    assert rel(got, ref) < STEP_TOL
+    assert rel(got - P.z0, ref - P.z0) < 2e-4
+    ctx.close()
+
+
 def test_duplicate_and_border_windows():
     n, m = 64, 16
     P = Problem(n, m, 4, 12, 0, 3, 6)
