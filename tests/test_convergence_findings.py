@@ -1,0 +1,41 @@
+"""What the FP64 oracle shows about convergence on the workloads' probe
+recipe (sequential steps, noise-free data, n = 64, m = 16, a 12 x 12 raster
+at step 4): with the disk's quadratic phase two levels drift away from the
+truth while one level (rPIE) converges; with the same disk and no phase, two
+levels converge faster than one, the behaviour the paper reports for its
+probe.  Guards the reading of the measured stall of the multilevel forms."""
+import numpy as np
+import pytest
+
+from oracle import magpie_oracle as O
+from paper_2504_10118_gb300 import synth
+
+N, M, GRID, STEP, SWEEPS = 64, 16, 12, 4, 60
+
+
+def _run(Q, levels):
+    z_true = synth.make_object(N, seed=1)
+    pos = synth.make_raster(N, M, GRID, STEP, 1, seed=3)
+    d = O.forward_intensities(z_true, Q, pos)
+    u = O.rpie_regulariser(Q, 0.1)
+    mask = O.illuminated_mask(Q, pos, z_true.shape)
+    z = np.ones((N, N), complex)
+    for s in range(SWEEPS):
+        z = O.sweep(z, Q, pos, d, u, levels, synth.make_order(len(pos), s), 1)
+    return O.nrmse(z, z_true, mask)
+
+
+@pytest.fixture(scope="module")
+def errors():
+    Q = synth.make_probe(M)
+    flat = np.abs(Q).astype(complex)
+    return {(ph, L): _run(Q if ph else flat, L) for ph in (True, False) for L in (1, 2)}
+
+
+def test_defocused_probe_two_levels_drift(errors):
+    assert errors[(True, 1)] < 0.35          # one level converging (0.31 after 60 sweeps)
+    assert errors[(True, 2)] > 1.0           # two levels far from the truth (1.38)
+
+
+def test_flat_probe_two_levels_beat_one(errors):
+    assert errors[(False, 2)] < errors[(False, 1)] < 0.01
