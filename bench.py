@@ -469,21 +469,25 @@ def sweeps_to_nrmse(w, dev, magpie, target: float, max_sweeps: int, every: int =
         err = float(torch.linalg.vector_norm(ph * a - zt) / torch.linalg.vector_norm(zt))
         best = min(best, err)
     ctx.close()
-    return {"levels": w.levels, "minibatch": w.minibatch, "reached": err <= target, "sweeps": sweeps,
-            "seconds": ms * 1e-3, "nrmse": err, "best_nrmse": best}
+    return {"levels": w.levels, "minibatch": w.minibatch, "alpha": w.alpha, "reached": err <= target,
+            "sweeps": sweeps, "seconds": ms * 1e-3, "nrmse": err, "best_nrmse": best}
 
 
 def time_to_nrmse(w, dev, magpie) -> dict:
     """Wall time (device, sweeps only) to NRMSE <= 1e-3 on the noise-free
-    version of workload w, for the default form (w's levels and minibatch)
-    and for the fastest setting measured to reach it (one level, minibatch
-    16).  With 1e6 photons per pattern the NRMSE of every form levels off
-    near 0.09, so the target is only reachable on noise-free data."""
+    version of workload w: the chosen setting (three levels, minibatch 16,
+    alpha 0.3, the fastest measured), the fastest one-level (rPIE) setting
+    measured (minibatch 16 at the workload's alpha), and the default form
+    (w's levels, minibatch and alpha).  With 1e6 photons per pattern the
+    NRMSE of every form levels off near 0.09, so the target is only
+    reachable on noise-free data."""
     import dataclasses
     clean = dataclasses.replace(w, photons=None)
-    chosen = sweeps_to_nrmse(dataclasses.replace(clean, levels=1, minibatch=16), dev, magpie, 1e-3, 3000)
+    chosen = sweeps_to_nrmse(dataclasses.replace(clean, levels=3, minibatch=16, alpha=0.3), dev, magpie, 1e-3, 3000)
+    rpie = sweeps_to_nrmse(dataclasses.replace(clean, levels=1, minibatch=16), dev, magpie, 1e-3, 3000)
     plain = sweeps_to_nrmse(clean, dev, magpie, 1e-3, 3000)
-    return {"target": 1e-3, "data": f"noise-free intensities of {w.name}", "chosen": chosen, "plain": plain}
+    return {"target": 1e-3, "data": f"noise-free intensities of {w.name}", "chosen": chosen, "rpie": rpie,
+            "plain": plain}
 
 
 def launches_per_step(args, w) -> int:
