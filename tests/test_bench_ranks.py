@@ -67,3 +67,22 @@ def test_reference_arm_times_the_oracle_on_every_core():
     assert line["cpu_baseline"]["cores"] == bench.host_cores()
     assert line["cpu_baseline"]["value"] == line["value"] == line["e2e"]["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_bench_nrmse_is_the_oracle_definition():
+    """The bench's quality figure (its own code: the bench runs no oracle on
+    the GPU side) equals the oracle's NRMSE over the illuminated mask, and is
+    blind to a global phase."""
+    import numpy as np
+
+    from oracle import magpie_oracle as O
+    from paper_2504_10118_gb300 import synth
+
+    w = synth.WORKLOADS["tiny"]
+    z_true, Q, pos = synth.make_problem(w)
+    rng = np.random.default_rng(5)
+    z = z_true + 0.05 * (rng.normal(size=z_true.shape) + 1j * rng.normal(size=z_true.shape))
+    q2 = np.abs(Q) ** 2
+    ref = O.nrmse(z, z_true, O.illuminated_mask(Q, pos, z_true.shape))
+    assert bench.nrmse_lit(z, z_true, q2, pos) == pytest.approx(ref, rel=1e-12)
+    assert bench.nrmse_lit(np.exp(0.7j) * z, z_true, q2, pos) == pytest.approx(ref, rel=1e-9)
