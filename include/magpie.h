@@ -282,6 +282,8 @@ int32_t magpie_cnn_param_count(void);
    max_batch windows; parameters start at zero.  Calls on it are ordered on
    `stream`. */
 int magpie_cnn_create(magpie_cnn** out, int32_t h, int32_t max_batch, void* stream);
+/* Frees the network and its buffers (after its stream work); it must not be
+   attached to a context that still sweeps. */
 void magpie_cnn_destroy(magpie_cnn* cnn);
 
 /* Copy in (DEVICE float32 [param_count]) the parameters; resets the Adam
