@@ -386,8 +386,8 @@ const char* magpie_strerror(int code);
  * this library holds until the process exits.  This entry point is an
  * addition of this library; the paper has no counterpart.
  *   object      : DEVICE complex [n_rows][n_cols], updated in place
- *   probe       : DEVICE complex [m][m]; its per-level factors (Eq.
- *                 def_weights) are recomputed on every call
+ *   probe       : DEVICE complex [m][m]; its per-level factors are
+ *                 recomputed on every call
  *   positions   : DEVICE int32 [n_pos][2]
  *   amplitudes  : DEVICE float32 [n_pos][m][m], the square roots sqrt(d_k)
  *                 of the measured intensities (DFT order)
@@ -395,8 +395,9 @@ const char* magpie_strerror(int code);
  *   phi, gnorm  : DEVICE float64 [n_pos] outputs, Phi_k and ||grad Phi_k||
  *                 of the windows of this minibatch (other entries untouched)
  *   stream      : cudaStream_t as void*
- * Limits: m <= 128 (MAGPIE_EUNSUPPORTED otherwise), count * m^2 <= 2^20
- * (e.g. 64 windows of 128 x 128), otherwise MAGPIE_EINVAL.  Windows whose index or position is
+ * Limits: m <= 128 (MAGPIE_EUNSUPPORTED otherwise); 1 <= count <=
+ * min(n_pos, 4096) and count * m^2 <= 2^20 (e.g. 64 windows of 128 x 128),
+ * otherwise MAGPIE_EINVAL.  Windows whose index or position is
  * out of range are skipped and reported as MAGPIE_EINDEX.  Synchronous: it
  * waits for the step to finish before returning.  The first call on each
  * device looks up the workspace's device address (cudaGetSymbolAddress) with

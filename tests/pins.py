@@ -531,6 +531,65 @@ def check_phase_rule_variant(O):
     assert np.all(th0 == 0) and _rel(R0, O.ifft2(np.sqrt(d[k]))) < 1e-14
 
 
+# ----------------------------------------------------------- metrics
+def check_stop_metric_closed_form(O):
+    """Stopping criterion of Section 5, (1/(N m)) sum_k ||grad Phi_k(z_k)||_2,
+    on data whose revised exit wave is known in closed form: with
+    d_k = s_k^2 |F(Q . z_k)|^2 (s_k > 0) the projection keeps every phase and
+    scales every modulus by s_k, so R_k = s_k Q . z_k and
+    grad Phi_k = (1 - s_k) |Q|^2 . z_k; no transform is needed to state the
+    expected value.  (a) One window, constant probe c and constant patch a:
+    the metric is |1 - s| |c|^2 |a| (the m of the norm cancels the 1/m);
+    (b) three windows with different s_k fix the 1/N average."""
+    m = 8
+    c, a, s = 0.6 - 0.3j, 1.3 + 0.4j, 1.75
+    Q = np.full((m, m), c)
+    z = np.full((m, m), a)
+    d = (s * np.abs(O.fft2(Q * z))) ** 2
+    pos = np.array([(0, 0)])
+    val = O.stop_metric(z, Q, pos, d[None])
+    assert abs(val - abs(1 - s) * abs(c) ** 2 * abs(a)) < 1e-12 * abs(c) ** 2 * abs(a), val
+    rng = np.random.default_rng(33)
+    n = 20
+    z = _crand(rng, n, n)
+    yy, xx = np.meshgrid(np.arange(m) - 3.5, np.arange(m) - 3.5, indexing="ij")
+    Q = np.exp(-(xx ** 2 + yy ** 2) / 18.0) * np.exp(0.2j * xx)
+    pos = np.array([(0, 0), (5, 9), (12, 3)])
+    sk = np.array([0.5, 1.25, 3.0])
+    d = np.stack([(sk[i] * np.abs(O.fft2(Q * O.extract(z, p, m)))) ** 2 for i, p in enumerate(pos)])
+    expect = sum(abs(1 - sk[i]) * np.linalg.norm(np.abs(Q) ** 2 * z[r:r + m, cc:cc + m])
+                 for i, (r, cc) in enumerate(pos)) / (len(pos) * m)
+    val = O.stop_metric(z, Q, pos, d)
+    assert abs(val - expect) < 1e-10 * expect, (val, expect)
+
+
+def check_nrmse_definition(O):
+    """NRMSE(a, b) = min_phi ||e^{i phi} a - b||_M / ||b||_M with b the
+    reference: a = 2b gives 1 and b against 2b gives 1/2 (the reference's
+    norm divides); a global phase alone gives 0; a real perturbation delta of
+    a positive real b on the mask gives ||delta||_M / ||b||_M whatever lies
+    off the mask; and the closed-form phase matches a brute-force search."""
+    rng = np.random.default_rng(34)
+    b = _crand(rng, 6, 7)
+    assert abs(O.nrmse(2 * b, b) - 1.0) < 1e-14
+    assert abs(O.nrmse(b, 2 * b) - 0.5) < 1e-14
+    assert O.nrmse(np.exp(0.7j) * b, b) < 1e-14
+    br = 0.5 + rng.random((10, 10))
+    mask = rng.random((10, 10)) < 0.5
+    delta = 0.01 * rng.standard_normal((10, 10)) * mask
+    a = np.exp(-1.1j) * (br + delta)
+    a[~mask] = 1e3 * _crand(rng, int((~mask).sum()))
+    expect = np.linalg.norm(delta[mask]) / np.linalg.norm(br[mask])
+    assert abs(O.nrmse(a, br, mask) - expect) < 1e-12 * expect
+    a, b = _crand(rng, 5, 5), _crand(rng, 5, 5)
+    phis = np.linspace(0.0, 2 * np.pi, 200001)
+    brute = min(np.linalg.norm(np.exp(1j * p) * a - b) for p in phis[::100])
+    p0 = phis[::100][int(np.argmin([np.linalg.norm(np.exp(1j * p) * a - b) for p in phis[::100]]))]
+    fine = np.linspace(p0 - 0.01, p0 + 0.01, 20001)
+    brute = min(brute, min(np.linalg.norm(np.exp(1j * p) * a - b) for p in fine)) / np.linalg.norm(b)
+    assert abs(O.nrmse(a, b) - brute) < 1e-9, (O.nrmse(a, b), brute)
+
+
 ALL_CHECKS = [
     check_dft_defining_sum, check_dft_parseval_inverse, check_dft_closed_forms,
     check_scan_adjoint, check_transfer_operators, check_objective_forms,
@@ -540,4 +599,5 @@ ALL_CHECKS = [
     check_coarse_prox_is_argmin, check_auto_regularisation,
     check_consistency_bounds, check_residual_form, check_special_cases,
     check_probe_step, check_recovery, check_mgopt_variant, check_phase_rule_variant,
+    check_stop_metric_closed_form, check_nrmse_definition,
 ]

@@ -157,11 +157,58 @@ def m_phase_rule_forgets(O):
     O.revised_exit_wave_recycled = rec
 
 
+def m_stop_metric_extra_inv_m(O):
+    orig = O.stop_metric
+    O.stop_metric = lambda z, Q, positions, d: orig(z, Q, positions, d) / Q.shape[0]
+
+
+def m_stop_metric_squared_norms(O):
+    def stop(z, Q, positions, d):
+        m = Q.shape[0]
+        tot = sum(np.linalg.norm(O.gradient_k(O.extract(z, p, m), Q, dk)) ** 2 for p, dk in zip(positions, d))
+        return float(tot) / (len(positions) * m)
+    O.stop_metric = stop
+
+
+def m_stop_metric_sum_not_mean(O):
+    orig = O.stop_metric
+    O.stop_metric = lambda z, Q, positions, d: orig(z, Q, positions, d) * len(positions)
+
+
+def m_nrmse_swapped(O):
+    orig = O.nrmse
+    O.nrmse = lambda a, b, mask=None: orig(b, a, mask)
+
+
+def m_nrmse_no_phase(O):
+    def nr(a, b, mask=None):
+        a = np.asarray(a, dtype=np.complex128)
+        b = np.asarray(b, dtype=np.complex128)
+        if mask is not None:
+            a, b = a[mask], b[mask]
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    O.nrmse = nr
+
+
+def m_nrmse_conjugate_phase(O):
+    def nr(a, b, mask=None):
+        a = np.asarray(a, dtype=np.complex128)
+        b = np.asarray(b, dtype=np.complex128)
+        if mask is not None:
+            a, b = a[mask], b[mask]
+        ip = np.vdot(a, b)
+        ph = np.conj(ip) / abs(ip) if abs(ip) > 0 else 1.0
+        return float(np.linalg.norm(ph * a - b) / np.linalg.norm(b))
+    O.nrmse = nr
+
+
 MUTATIONS = [m_restrict_sum, m_prolong_scaled, m_fft_sign, m_fft_unnormalised_inverse,
              m_no_sqrt, m_gradient_no_conj, m_wr_no_conj, m_wz_unnormalised,
              m_uh_unweighted, m_post_smooth_from_z, m_minibatch_count_average,
              m_regulariser_amplitude, m_extract_transposed, m_objective_no_half,
-             m_mgopt_shift_sign, m_mgopt_weighted_restriction, m_phase_rule_forgets]
+             m_mgopt_shift_sign, m_mgopt_weighted_restriction, m_phase_rule_forgets,
+             m_stop_metric_extra_inv_m, m_stop_metric_squared_norms, m_stop_metric_sum_not_mean,
+             m_nrmse_swapped, m_nrmse_no_phase, m_nrmse_conjugate_phase]
 
 FAST_CHECKS = [c for c in pins.ALL_CHECKS if c is not pins.check_recovery]
 
