@@ -34,18 +34,41 @@ sys.path.insert(0, ROOT)
 from paper_2504_10118_gb300 import synth  # noqa: E402
 
 FP32_LANES_PER_SM = 128
-SMS = 152
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "window_kernel_m128_mid.txt")
+# ncu DRAM traffic of the window kernel per update (1: ordered, 0: atomic)
+TRAFFIC_FILES = {1: os.path.join(ROOT, "profiles", "window_kernel_m128_mid.txt"),
+                 0: os.path.join(ROOT, "profiles", "window_kernel_atomic_m128_mid.txt")}
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2504_10118_gb300", "csrc", f)
                   for f in ("fft_lines.cuh", "window_kernel.cuh", "window_body.inc")]
 
 
 def flops_per_window(m: int) -> float:
     """Algorithmic flops of one window: two 2-D FFTs at the nominal 5 M log2 M
-    each, plus 43 M for the exit wave, projection, residual and V-cycle."""
+    each, plus 60 M for the element-wise work (exit wave, projection,
+    residual, gradient, V-cycle and the weighted scatter), M = m^2."""
     M = m * m
-    return 10.0 * M * math.log2(M) + 43.0 * M
+    return 10.0 * M * math.log2(M) + 60.0 * M
+
+
+_FP32_PEAK = {}
+
+
+def fp32_peak(dev, magpie):
+    """(TFLOP/s, source) of the FP32 FMA peak of this GPU: the library's FMA
+    rate measurement (8 blocks of 256 threads per SM, 8 independent FMA chains
+    per thread, best of three launches), with the nominal figure from the SM
+    count and the maximum SM clock beside it.  Measured once per process."""
+    import torch
+    key = str(dev)
+    if key not in _FP32_PEAK:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        pk, src = peaks()
+        nominal = sms * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        tf, ms = magpie.magpie_fp32_fma_rate(8192)
+        _FP32_PEAK[key] = (tf, f"FP32 FMA rate measured on this GPU ({tf:.1f} TFLOP/s, {ms:.3f} ms launch); "
+                               f"nominal {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                               f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz = {nominal:.1f} TFLOP/s")
+    return _FP32_PEAK[key]
 
 
 def tc_flops_per_window(m: int) -> float:
@@ -110,11 +133,12 @@ def kernel_source_hash() -> str:
     return h.hexdigest()
 
 
-def measured_traffic():
-    """DRAM bytes per launch of the window kernel from the committed ncu
-    summary, or None when the kernel source changed since it was taken."""
+def measured_traffic(deterministic: int = 1):
+    """DRAM bytes per launch of the window kernel (of the given update) from
+    the committed ncu summary, or None when the kernel source changed since it
+    was taken."""
     try:
-        lines = open(TRAFFIC_FILE).read().splitlines()
+        lines = open(TRAFFIC_FILES[deterministic]).read().splitlines()
     except OSError:
         return None
     kv = {}
@@ -317,9 +341,70 @@ def run_reference(args, w):
     return 0
 
 
-def run_batched(args):
+def batched_measure(dev, magpie, warmup: int, steps: int, pg=None, clocks=None):
     """The batched workload: 48 independent reconstructions of uneven sizes
-    advanced together by one context group; patterns/s over all of them."""
+    advanced together by one context group; returns (record, total_ms,
+    launches, windows).  Photon noise is drawn on the device (3 GB of
+    intensities would take tens of seconds on the host)."""
+    import torch
+    ws = synth.make_batch()
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(4)
+    ctxs, keep = [], []
+    for i, w in enumerate(ws):
+        z_true, Q, pos = synth.make_problem_seeded(w, 1 + i)
+        Qt = torch.from_numpy(Q.astype(np.complex64)).to(dev)
+        post = torch.from_numpy(pos).to(dev)
+        clean = magpie.magpie_forward_intensities(torch.from_numpy(z_true.astype(np.complex64)).to(dev), Qt, post,
+                                                  w.m)
+        eta = float(clean.sum(dim=(1, 2)).mean().item() / w.photons)
+        d = torch.poisson(clean / eta, generator=gen) * eta
+        z = torch.ones((w.n, w.n), dtype=torch.complex64, device=dev)
+        ctxs.append(magpie.magpie_create(magpie.magpie_params_of(w.n, w.n, w.m, w.n_pos, w.levels, w.minibatch,
+                                                                 w.alpha), z, Qt, post, d))
+        keep.append((z, Qt, post, d))
+        del clean
+    group = magpie.magpie_group_create(ctxs)
+    n_total = sum(w.n_pos for w in ws)
+    orders = [[torch.from_numpy(synth.make_order(w.n_pos, s)).to(dev) for w in ws] for s in range(warmup + steps)]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for s in range(warmup):
+        magpie.magpie_group_sweep(group, orders[s])
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    for s in range(steps):
+        flush.zero_()
+        ev0[s].record(stream)
+        magpie.magpie_group_sweep(group, orders[warmup + s])
+        ev1[s].record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    total_ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+    steps_max = max(math.ceil(w.n_pos / w.minibatch) for w in ws)
+    launches = sum(len({w.m for w in ws if math.ceil(w.n_pos / w.minibatch) > t}) + 1 for t in range(steps_max))
+    tuning = magpie.magpie_group_tuning(group)
+    group.close()
+    for c in ctxs:
+        c.close()
+    rec = {"value": steps * n_total / (total_ms * 1e-3), "unit": "patterns/s", "ms_per_step": total_ms / steps,
+           "steps": steps, "warmup": warmup,
+           "config": {"workload": "batch48", "problems": len(ws), "windows": n_total,
+                      "window_sides": sorted({w.m for w in ws}), "object_sides": sorted({w.n for w in ws}),
+                      "levels": 3, "minibatch": 64, "update": "ordered (context groups)",
+                      "data": "photon noise drawn on the device"},
+           "gpu_launches_per_step": launches,
+           "autotuner": {str(m): {"choice": v[0], "candidates": v[1]} for m, v in tuning.items()}}
+    flops = sum(w.n_pos * flops_per_window(w.m) for w in ws) * steps
+    return rec, total_ms, launches, flops
+
+
+def run_batched(args):
+    """The batched workload as its own bench line."""
     import torch
     from paper_2504_10118_gb300 import magpie
 
@@ -336,75 +421,28 @@ def run_batched(args):
     if pg:
         pg.barrier()
     magpie.lib()
-    ws = synth.make_batch()
-    gen = torch.Generator(device=dev)
-    gen.manual_seed(4)
-    ctxs, keep = [], []
-    for i, w in enumerate(ws):
-        z_true, Q, pos = synth.make_problem_seeded(w, 1 + i)
-        Qt = torch.from_numpy(Q.astype(np.complex64)).to(dev)
-        post = torch.from_numpy(pos).to(dev)
-        clean = magpie.magpie_forward_intensities(torch.from_numpy(z_true.astype(np.complex64)).to(dev), Qt, post,
-                                                  w.m)
-        eta = float(clean.sum(dim=(1, 2)).mean().item() / w.photons)
-        d = torch.poisson(clean / eta, generator=gen) * eta  # photon noise drawn on the device
-        z = torch.ones((w.n, w.n), dtype=torch.complex64, device=dev)
-        ctxs.append(magpie.magpie_create(magpie.magpie_params_of(w.n, w.n, w.m, w.n_pos, w.levels, w.minibatch,
-                                                                 w.alpha), z, Qt, post, d))
-        keep.append((z, Qt, post, d))
-        del clean
-    group = magpie.magpie_group_create(ctxs)
-    n_total = sum(w.n_pos for w in ws)
-    orders = [[torch.from_numpy(synth.make_order(w.n_pos, s)).to(dev) for w in ws]
-              for s in range(args.warmup + args.steps)]
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
     clocks = ClockSampler(gpu_uuid(dev))
-    for s in range(args.warmup):
-        magpie.magpie_group_sweep(group, orders[s])
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    if pg:
-        pg.barrier()
-    for s in range(args.steps):
-        flush.zero_()
-        ev0[s].record(stream)
-        magpie.magpie_group_sweep(group, orders[args.warmup + s])
-        ev1[s].record(stream)
-    torch.cuda.synchronize()
-    if pg:
-        pg.barrier()
+    rec, local_ms, launches, flops = batched_measure(dev, magpie, args.warmup, args.steps, pg)
     clk = clocks.stop()
-    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)), pg, dev)
-    steps_max = max(math.ceil(w.n_pos / w.minibatch) for w in ws)
-    launches = sum(len({w.m for w in ws if math.ceil(w.n_pos / w.minibatch) > t}) + 1 for t in range(steps_max))
-    tuning = magpie.magpie_group_tuning(group)
-    pk, src = peaks()
-    sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    alu_peak = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    flops = sum(w.n_pos * flops_per_window(w.m) for w in ws) * args.steps
+    total_ms = max_over_ranks(local_ms, pg, dev)
+    peak, peak_src = fp32_peak(dev, magpie)
     achieved = flops / (total_ms * 1e-3) / 1e12
-    group.close()
-    for c in ctxs:
-        c.close()
     if rank == 0:
         line = {
-            "metric": "patterns/s per sweep", "value": whole_job_value(world, args.steps, n_total, total_ms),
+            "metric": "patterns/s per sweep",
+            "value": whole_job_value(world, args.steps, rec["config"]["windows"], total_ms),
             "unit": "patterns/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (48 seeded problems; photon noise drawn on the device)",
-            "config": {"workload": "batch48", "problems": len(ws), "windows": n_total,
-                       "window_sides": sorted({w.m for w in ws}), "object_sides": sorted({w.n for w in ws}),
-                       "levels": 3, "minibatch": 64, "parallelism": "replicas",
-                       "l2": "flushed (256 MiB write) before every timed sweep"},
+            "config": dict(rec["config"], parallelism="replicas",
+                           l2="flushed (256 MiB write) before every timed sweep"),
             "gpu_launches": launches * args.steps, "clocks": clk,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                         "frac": achieved / alu_peak, "traffic": None,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
                          "kernel": "whole group sweep (batched window and update launches)",
-                         "peak_source": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz ({src})"},
-            "autotuner": {str(m): {"minb": v[0], "ms_per_launch": list(v[1])} for m, v in tuning.items()},
+                         "peak_source": peak_src},
+            "autotuner": rec["autotuner"],
         }
         print(json.dumps(line), flush=True)
     if pg:
@@ -434,11 +472,15 @@ def nrmse_lit(z, z_true, q2, pos, rel: float = 1e-3) -> float:
     return float(np.linalg.norm(ph * a - b) / np.linalg.norm(b))
 
 
-def sweeps_to_nrmse(w, dev, magpie, target: float, max_sweeps: int, every: int = 10) -> dict:
+def sweeps_to_nrmse(w, dev, magpie, target: float, max_sweeps: int, every: int = 10, deterministic: int = 1,
+                    precision: int = 0, net=None) -> dict:
     """Sweeps of workload w from z = 1 until the object's NRMSE against the
     truth (global phase removed, lit pixels, as nrmse_lit) is at most
-    `target`, checked every `every` sweeps, or `max_sweeps` have run.  Only the
-    sweeps are timed (CUDA events around each chunk); the checks are not."""
+    `target`, checked every `every` sweeps, or `max_sweeps` have run.  Reports
+    the device time of the sweeps (CUDA events around each chunk) and the wall
+    time from the first sweep to the last check, checks included.  The form:
+    the update (`deterministic`), tensor-core DFTs (`precision`) and a
+    learned coarse correction (`net`, attached to the context)."""
     import torch
     z_true, Qt, post, dt, _ = make_data(w, dev, magpie)
     q2 = np.abs(Qt.cpu().numpy().astype(np.complex128)) ** 2
@@ -449,45 +491,132 @@ def sweeps_to_nrmse(w, dev, magpie, target: float, max_sweeps: int, every: int =
     lit = torch.from_numpy(cov >= 1e-3 * cov.max()).to(dev)
     zt = torch.from_numpy(z_true.astype(np.complex64)).to(dev)[lit].to(torch.complex128)
     z = torch.ones((w.n, w.n), dtype=torch.complex64, device=dev)
-    ctx = magpie.magpie_create(magpie.magpie_params_of(w.n, w.n, w.m, w.n_pos, w.levels, w.minibatch, w.alpha),
-                               z, Qt, post, dt)
+    ctx = magpie.magpie_create(magpie.magpie_params_of(w.n, w.n, w.m, w.n_pos, w.levels, w.minibatch, w.alpha,
+                                                       deterministic=deterministic), z, Qt, post, dt)
+    if precision:
+        magpie.magpie_set_precision(ctx, 1)
+    if net is not None:
+        magpie.magpie_attach_cnn(ctx, net)
+    orders = torch.from_numpy(np.stack([synth.make_order(w.n_pos, i) for i in range(max_sweeps)])).to(dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sweeps, ms, err, best = 0, 0.0, 1.0, 1.0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     while sweeps < max_sweeps and err > target:
-        orders = [torch.from_numpy(synth.make_order(w.n_pos, sweeps + i)).to(dev) for i in range(every)]
-        torch.cuda.synchronize()
         ev0.record()
-        for o in orders:
-            magpie.magpie_sweep(ctx, o)
+        for i in range(every):
+            magpie.magpie_sweep(ctx, orders[sweeps + i])
         ev1.record()
-        torch.cuda.synchronize()
-        ms += ev0.elapsed_time(ev1)
-        sweeps += every
         a = z[lit].to(torch.complex128)
         ip = torch.vdot(a, zt)
         ph = ip / ip.abs() if ip.abs() > 0 else 1.0
         err = float(torch.linalg.vector_norm(ph * a - zt) / torch.linalg.vector_norm(zt))
+        ms += ev0.elapsed_time(ev1)
+        sweeps += every
         best = min(best, err)
+    wall = time.perf_counter() - t0
+    out = {"levels": w.levels, "minibatch": w.minibatch, "alpha": w.alpha, "reached": err <= target,
+           "sweeps": sweeps, "seconds": ms * 1e-3, "wall_seconds": wall, "nrmse": err, "best_nrmse": best,
+           "update": "ordered" if deterministic else "atomic",
+           "dft": "tensor-core BF16 hi+lo" if precision else "FP32 FFT",
+           "learned": net is not None}
+    if net is not None:
+        out["proposals_kept"], out["proposals"] = magpie.magpie_learned_stats(ctx)[::-1]
     ctx.close()
-    return {"levels": w.levels, "minibatch": w.minibatch, "alpha": w.alpha, "reached": err <= target,
-            "sweeps": sweeps, "seconds": ms * 1e-3, "nrmse": err, "best_nrmse": best}
+    return out
 
 
 def time_to_nrmse(w, dev, magpie) -> dict:
-    """Wall time (device, sweeps only) to NRMSE <= 1e-3 on the noise-free
-    version of workload w: the chosen setting (three levels, minibatch 16,
-    alpha 0.3, the fastest measured), the fastest one-level (rPIE) setting
-    measured (minibatch 16 at the workload's alpha), and the default form
-    (w's levels, minibatch and alpha).  With 1e6 photons per pattern the
-    NRMSE of every form levels off near 0.09, so the target is only
-    reachable on noise-free data."""
+    """Time to NRMSE <= 1e-3 on the noise-free version of workload w, every
+    form at one setting (three levels, minibatch 16, alpha 0.3; with 1e6
+    photons per pattern the NRMSE of every form levels off near 0.09, and at
+    the workload's minibatch of 64 the iteration stalls near 0.06, so the
+    target is reachable only there): the plain FP32 form with either update,
+    the precision form (tensor-core DFTs), and the combined form (tensor-core
+    DFTs plus the learned coarse correction, its network trained first on
+    trajectories of the plain solver at the same setting, untimed).  For
+    context, the workload's own setting and the fastest one-level setting."""
     import dataclasses
+    import torch
+    from paper_2504_10118_gb300 import learned
     clean = dataclasses.replace(w, photons=None)
-    chosen = sweeps_to_nrmse(dataclasses.replace(clean, levels=3, minibatch=16, alpha=0.3), dev, magpie, 1e-3, 3000)
-    rpie = sweeps_to_nrmse(dataclasses.replace(clean, levels=1, minibatch=16), dev, magpie, 1e-3, 3000)
-    plain = sweeps_to_nrmse(clean, dev, magpie, 1e-3, 3000)
-    return {"target": 1e-3, "data": f"noise-free intensities of {w.name}", "chosen": chosen, "rpie": rpie,
-            "plain": plain}
+    setting = dataclasses.replace(clean, levels=3, minibatch=16, alpha=0.3)
+    out = {"target": 1e-3, "data": f"noise-free intensities of {w.name}",
+           "setting": {"levels": 3, "minibatch": 16, "alpha": 0.3},
+           "fp32": sweeps_to_nrmse(setting, dev, magpie, 1e-3, 3000, deterministic=1),
+           "fp32_atomic": sweeps_to_nrmse(setting, dev, magpie, 1e-3, 3000, deterministic=0),
+           "precision": sweeps_to_nrmse(setting, dev, magpie, 1e-3, 3000, precision=1)}
+    t0 = time.perf_counter()
+    data = learned.generate(setting, seeds=[11, 12, 13], stages=[0, 1, 2, 3, 4, 6, 8, 12, 16, 24], per_stage=96,
+                            dev=dev, final_sweeps=200)
+    net = magpie.magpie_cnn_create(learned.coarse_side(setting.m, setting.levels), 64)  # training batch 64
+    magpie.magpie_cnn_set_params(net, learned.initial_params(dev=dev))
+    losses = learned.train(net, data, epochs=30, batch=64, lr=3e-4)
+    torch.cuda.synchronize()
+    training = {"pairs": len(data), "epochs": 30, "loss_first_epoch": float(losses[0]),
+                "loss_last_epoch": float(losses[-1]), "seconds": time.perf_counter() - t0,
+                "targets": "coarse state of the same windows after 200 plain sweeps"}
+    out["combined"] = sweeps_to_nrmse(setting, dev, magpie, 1e-3, 2500, precision=1, net=net)
+    out["combined"]["training"] = training
+    net.close()
+    out["context"] = {
+        "workload_setting": sweeps_to_nrmse(clean, dev, magpie, 1e-3, 3000),
+        "rpie": sweeps_to_nrmse(dataclasses.replace(clean, levels=1, minibatch=16), dev, magpie, 1e-3, 3000)}
+    return out
+
+
+def precision_record(dev, magpie, warmup: int = 2, steps: int = 3) -> dict:
+    """patterns/s of the n=1024, m=256, 2500-window, 4-level workload with
+    tensor-core DFTs and with the FP32 FFT window kernel (one context, the
+    form switched between the two runs; photon noise drawn on the device)."""
+    import torch
+    w = synth.WORKLOADS["precision"]
+    z_true, Q, pos = synth.make_problem(w)
+    Qt = torch.from_numpy(Q.astype(np.complex64)).to(dev)
+    post = torch.from_numpy(pos).to(dev)
+    clean = magpie.magpie_forward_intensities(torch.from_numpy(z_true.astype(np.complex64)).to(dev), Qt, post, w.m)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(4)
+    eta = float(clean.sum(dim=(1, 2)).mean().item() / w.photons)
+    d = torch.poisson(clean / eta, generator=gen) * eta
+    del clean
+    z = torch.ones((w.n, w.n), dtype=torch.complex64, device=dev)
+    ctx = magpie.magpie_create(magpie.magpie_params_of(w.n, w.n, w.m, w.n_pos, w.levels, w.minibatch, w.alpha),
+                               z, Qt, post, d)
+    del d
+    orders = torch.from_numpy(np.stack([synth.make_order(w.n_pos, s) for s in range(warmup + steps)])).to(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    rec = {"config": config_of(w), "data": "photon noise drawn on the device"}
+    for name, mode in (("tensor_core_dft", 1), ("fp32_fft", 0)):
+        magpie.magpie_set_precision(ctx, mode)
+        ms = time_sweeps(magpie, ctx, orders, warmup, steps, flush, torch.cuda.current_stream())
+        rec[name] = {"value": steps * w.n_pos / (ms * 1e-3), "unit": "patterns/s", "ms_per_step": ms / steps}
+    ctx.close()
+    return rec
+
+
+def time_sweeps(magpie, ctx, orders, warmup: int, steps: int, flush, stream, pg=None) -> float:
+    """Milliseconds of `steps` sweeps after `warmup` untimed ones, each timed
+    with CUDA events on `stream` after an L2 flush (outside the events)."""
+    import torch
+    for s in range(warmup):
+        magpie.magpie_sweep(ctx, orders[s])
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    for s in range(steps):
+        flush.zero_()
+        ev0[s].record(stream)
+        magpie.magpie_sweep(ctx, orders[warmup + s])
+        ev1[s].record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
 
 
 def launches_per_step(args, w) -> int:
@@ -538,10 +667,12 @@ def run_ours(args, w):
         pg.barrier()
     magpie.lib()
 
+    fp32_form = args.dft == "fft" and not args.learned
+    det = 0 if (fp32_form and args.update == "atomic") else 1
     z_true, Qt, post, dt, d_host = make_data(w, dev, magpie)
     z = torch.ones((w.n, w.n), dtype=torch.complex64, device=dev)
-    ctx = magpie.magpie_create(magpie.magpie_params_of(w.n, w.n, w.m, w.n_pos, w.levels, w.minibatch, w.alpha),
-                               z, Qt, post, dt)
+    ctx = magpie.magpie_create(magpie.magpie_params_of(w.n, w.n, w.m, w.n_pos, w.levels, w.minibatch, w.alpha,
+                                                       deterministic=det), z, Qt, post, dt)
     if args.dft == "tc":
         magpie.magpie_set_precision(ctx, 1)
     net = None
@@ -564,26 +695,9 @@ def run_ours(args, w):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     clocks = ClockSampler(gpu_uuid(dev))
-
-    for s in range(args.warmup):
-        magpie.magpie_sweep(ctx, orders[s])
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    if pg:
-        pg.barrier()
-    torch.cuda.synchronize()
-    for s in range(args.steps):
-        flush.zero_()
-        ev0[s].record(stream)
-        magpie.magpie_sweep(ctx, orders[args.warmup + s])
-        ev1[s].record(stream)
-    torch.cuda.synchronize()
-    if pg:
-        pg.barrier()
-    torch.cuda.synchronize()
+    local_ms = time_sweeps(magpie, ctx, orders, args.warmup, args.steps, flush, stream, pg)
     clk = clocks.stop()
-    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)), pg, dev)
+    total_ms = max_over_ranks(local_ms, pg, dev)
 
     # reconstruction quality after warm-up + timed sweeps (host arithmetic on
     # the downloaded object, outside every timed region)
@@ -593,8 +707,8 @@ def run_ours(args, w):
     if args.learned:
         quality["proposals_kept"], quality["proposals"] = magpie.magpie_learned_stats(ctx)[::-1]
 
-    # dominant kernel: the per-window kernel, timed with events captured in
-    # the sweep graph over the same kind of sweeps
+    # dominant kernel: the per-window kernel, timed with events around each
+    # launch of the same kind of sweeps on the library's stream
     prof_sweeps = min(args.steps, 20)
     wk_ms, ap_ms, launches = 0.0, 0.0, 0
     for s in range(prof_sweeps):
@@ -605,11 +719,34 @@ def run_ours(args, w):
         launches += n
     windows = prof_sweeps * w.n_pos
     pk, src = peaks()
-    sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    alu_peak = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
+    alu_peak, alu_src = fp32_peak(dev, magpie)
     achieved_tf = windows * flops_per_window(w.m) / (wk_ms * 1e-3) / 1e12
     achieved_gbs = windows * hbm_bytes_per_window(w.m) / (wk_ms * 1e-3) / 1e9
-    traffic = measured_traffic() if args.dft == "fft" and not args.learned else None
+    traffic = measured_traffic(det) if fp32_form else None
+
+    # the other update of the FP32 form on the same data, timed the same way
+    update_ab = None
+    if fp32_form and rank == 0 and world == 1:
+        z2 = torch.ones((w.n, w.n), dtype=torch.complex64, device=dev)
+        ctx2 = magpie.magpie_create(magpie.magpie_params_of(w.n, w.n, w.m, w.n_pos, w.levels, w.minibatch, w.alpha,
+                                                            deterministic=1 - det), z2, Qt, post, dt)
+        ms2 = time_sweeps(magpie, ctx2, orders, args.warmup, args.steps, flush, stream)
+        wk2, ap2 = 0.0, 0.0
+        for s in range(prof_sweeps):
+            flush.zero_()
+            a, b, n = magpie.magpie_profile_sweep(ctx2, orders[args.warmup + s])
+            wk2 += a
+            ap2 += b
+        ctx2.close()
+        del z2
+        rec = {"atomic" if det == 0 else "ordered": {"ms_per_step": total_ms / args.steps,
+                                                     "window_kernel_ms_per_sweep": wk_ms / prof_sweeps,
+                                                     "update_kernel_ms_per_sweep": ap_ms / prof_sweeps},
+               "ordered" if det == 0 else "atomic": {"ms_per_step": ms2 / args.steps,
+                                                     "window_kernel_ms_per_sweep": wk2 / prof_sweeps,
+                                                     "update_kernel_ms_per_sweep": ap2 / prof_sweeps}}
+        update_ab = dict(rec, headline=args.update,
+                         note="same data and sweep orders; per-kernel times from event-bracketed launches")
 
     # end to end through the host-buffer call: order + intensities in, object out
     order_h = [torch.from_numpy(synth.make_order(w.n_pos, 1000 + s)).pin_memory() for s in range(args.steps)]
@@ -624,9 +761,16 @@ def run_ours(args, w):
         magpie.magpie_sweep_host_async(ctx, order_h[s], d_pin, z_out)
     magpie.magpie_sync(ctx)
     e2e_s = max_over_ranks(time.perf_counter() - t0, pg, dev)
+    ctx.close()
+    del dt, d_pin
 
-    ttn = time_to_nrmse(w, dev, magpie) if (w.name == synth.WORKLOADS["mid"].name and args.dft == "fft"
-                                            and not args.learned and rank == 0 and world == 1) else None
+    extras = (w.name == synth.WORKLOADS["mid"].name and fp32_form and rank == 0 and world == 1
+              and not args.no_extras)
+    ttn = time_to_nrmse(w, dev, magpie) if extras else None
+    prec = precision_record(dev, magpie) if extras else None
+    batched = None
+    if extras:
+        batched, _, _, _ = batched_measure(dev, magpie, 3, 5)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -638,7 +782,6 @@ def run_ours(args, w):
                          f"workload: {nwin} windows in {el:.1f} s, FP64 NumPy oracle",
                "single_core": {"value": v1, "unit": "patterns/s", "cores": 1,
                                "sample": f"{nwin1} windows in minibatch steps, {el1:.1f} s"}}
-    ctx.close()
     if rank == 0:
         value = whole_job_value(world, args.steps, w.n_pos, total_ms)
         line = {
@@ -648,21 +791,26 @@ def run_ours(args, w):
             "dtype": "bf16x3 (hi+lo) DFTs, f32" if args.dft == "tc" else ("f32 + bf16 network" if args.learned else "f32"),
             "data": "synthetic (seeded object, probe, raster and Poisson noise)",
             "config": dict(config_of(w), workload=("learned correction on " + w.name) if args.learned else w.name,
-                           dft="tensor-core BF16 hi+lo" if args.dft == "tc" else "FP32 FFT"),
+                           dft="tensor-core BF16 hi+lo" if args.dft == "tc" else "FP32 FFT",
+                           update="ordered" if det else "atomic"),
             "quality": quality,
+            "update_ab": update_ab,
             "time_to_nrmse": ttn,
+            "precision": prec,
+            "batched": batched,
             "training": train_info,
             "roofline": ({"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": achieved_tf / alu_peak, "traffic": traffic,
-                         "kernel": f"window_kernel<{w.m}, step>",
+                         "kernel": f"window_kernel<{w.m}, {'step' if det else 'step_atomic'}>",
                          "avg_launch_ms": wk_ms / max(launches, 1),
-                         "peak_source": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
-                                        f"(SM max clock, {src})",
+                         "flops_per_window": flops_per_window(w.m),
+                         "peak_source": alu_src,
                          "hbm_view": {"achieved": achieved_gbs, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
-                                      "frac": achieved_gbs / pk.get("hbm_gbs", 6800.0)},
+                                      "frac": achieved_gbs / pk.get("hbm_gbs", 6800.0),
+                                      "peak_source": f"hbm_gbs, {src}"},
                          "apply_kernel_ms_per_sweep": ap_ms / prof_sweeps,
                          "window_kernel_ms_per_sweep": wk_ms / prof_sweeps}
-                         if args.dft == "fft" and not args.learned else
+                         if fp32_form else
                          tensor_roofline(args, w, windows, wk_ms, ap_ms, prof_sweeps, launches, pk, src)),
             "cpu_baseline": cpu,
             "e2e": {"value": whole_job_value(world, args.steps, w.n_pos, 1e3 * e2e_s), "unit": "patterns/s",
@@ -690,7 +838,12 @@ def main():
     ap.add_argument("--workload", choices=sorted(synth.WORKLOADS) + ["batched", "learned"], default="mid")
     ap.add_argument("--dft", choices=["fft", "tc"], default=None,
                     help="fft: FP32 FFT path; tc: tensor-core BF16 hi+lo DFTs (default for the precision workload)")
+    ap.add_argument("--update", choices=["atomic", "ordered"], default="atomic",
+                    help="update of the FP32 form: float-atomic accumulation (default) or the ordered, bitwise "
+                         "reproducible reduction; the other one is timed too (update_ab)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the time-to-NRMSE, precision and batched records of the default workload")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

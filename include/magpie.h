@@ -72,7 +72,26 @@ typedef struct {
   int32_t update_probe;   /* 0: the probe is known and fixed (the paper); 1: every
                              minibatch step also moves the context's probe (below)  */
   float beta;             /* probe regulariser when update_probe = 1, >= 0          */
+  int32_t deterministic;  /* 1: the ordered update (below), bitwise reproducible;
+                             0: float-atomic update, the same sums in a run-to-run
+                             varying order (last-bit differences)                   */
 } magpie_params;
+
+/*
+ * The two updates (deterministic = 1 or 0) compute the same combination
+ * z <- z + sum_k P_k^T (w . Delta_k) / sum_k P_k^T w of a minibatch:
+ *   1  every window writes w . Delta_k to its slot of a minibatch buffer
+ *      (8 B m^2 bytes) and an update kernel sums, per object pixel, the
+ *      windows covering it in minibatch order: the results are bitwise
+ *      reproducible;
+ *   0  every window adds (w . Delta_k, w) pixel by pixel into object-sized
+ *      accumulators (16 n_rows n_cols bytes) with 16-byte float atomics, and a
+ *      streaming kernel applies N / D and clears them: faster, but the
+ *      order of the floating-point sums varies from run to run.
+ * The atomic update serves the FP32 window kernel (with or without the probe
+ * step); the precision form, the learned correction, the phase rule of
+ * Eq. (specification) and context groups always use the ordered update.
+ */
 
 /*
  * Probe step (update_probe = 1; an extension: the paper keeps Q fixed and
@@ -409,10 +428,21 @@ int magpie_step_noalloc(void* object, int32_t n_rows, int32_t n_cols, const void
                         const int32_t* positions, int32_t n_pos, const float* amplitudes, const int32_t* idx,
                         int32_t count, int32_t levels, float alpha, double* phi, double* gnorm, void* stream);
 
+/*
+ * Measurement helper, not part of the method: the FP32 fused multiply-add
+ * rate of the current device, the peak that bounds the ALU-bound window
+ * kernel.  Launches 8 blocks of 256 threads per SM, each thread running 8
+ * independent chains of `iters` FMAs, four times on `stream` (the first as a
+ * warm-up) and reports the fastest timed launch as *tflops (2 flops per FMA)
+ * and *ms (HOST pointers; ms may be NULL).  Allocates a small output buffer;
+ * changes no device setting.  Synchronous.
+ */
+int magpie_fp32_fma_rate(int32_t iters, double* tflops, double* ms, void* stream);
+
 /* Message of the calling thread's most recent failed call ("" if none). */
 const char* magpie_last_error(void);
 
-/* Library version as major*10000 + minor*100 + patch (this is 1.1.0). */
+/* Library version as major*10000 + minor*100 + patch (this is 1.2.0). */
 int magpie_version(void);
 
 #ifdef __cplusplus

@@ -46,13 +46,15 @@
 #include <algorithm>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "magpie.h"
 
 namespace {
 
 namespace cg = cooperative_groups;
 
-constexpr int kVersion = 10100;  // 1.1.0
+constexpr int kVersion = 10200;  // 1.2.0
 constexpr int kMaxMinibatch = 4096;  // the update kernel keeps the minibatch's corners in smem (48 KiB)
 constexpr int kMaxCluster = 8;       // largest number of blocks per window
 constexpr int kMaxSlots = 16;        // partial-sum slots per window: the window kernel's blocks, or m / 16
@@ -189,6 +191,59 @@ __global__ void __launch_bounds__(256) apply_kernel_batched(const ApplyArgs* __r
   const ApplyArgs& P = table[lo];
   const int t = (int)blockIdx.x - P.block0;
   apply_body(P, t % P.tiles_x, t / P.tiles_x);
+}
+
+// Atomic update (deterministic = 0): the window kernel has added, pixel by
+// pixel, sum_k w . Delta_k (x, y) and sum_k w (z) into object-sized
+// accumulators; every pixel with a positive weight moves by their ratio, the
+// same rule as the ordered update, and every touched accumulator is cleared
+// for the next step.  One pixel per thread, 16-byte loads.  Block 0 also
+// turns the window kernel's block partials into Phi_k and ||grad Phi_k||.
+__global__ void __launch_bounds__(256) accum_apply_kernel(float2* __restrict__ z, float4* __restrict__ acc,
+                                                          size_t npix, const int32_t* __restrict__ idx, int count,
+                                                          int n_pos, const double* __restrict__ part, int slots,
+                                                          int MS, double* phi_pos, double* gn_pos) {
+  if (blockIdx.x == 0) {
+    for (int b = threadIdx.x; b < count; b += blockDim.x) {
+      const int k = idx[b];
+      if ((unsigned)k >= (unsigned)n_pos) continue;
+      double a = 0.0, g = 0.0;
+      for (int q = 0; q < slots; ++q) {
+        a += part[(size_t)(b * slots + q) * 2];
+        g += part[(size_t)(b * slots + q) * 2 + 1];
+      }
+      phi_pos[k] = a / (2.0 * (double)MS * (double)MS);
+      gn_pos[k] = sqrt(g);
+    }
+  }
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < npix; p += (size_t)gridDim.x * blockDim.x) {
+    const float4 a = __ldcg(&acc[p]);
+    if (a.z > 0.f) {
+      float2 zz = z[p];
+      zz.x += a.x / a.z;
+      zz.y += a.y / a.z;
+      z[p] = zz;
+    }
+    if (a.x != 0.f || a.y != 0.f || a.z != 0.f) acc[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// FP32 FMA throughput: every thread runs kFmaChains independent chains of
+// a <- a * b + c (one fused multiply-add, 2 flops, per element per
+// iteration); the sums are stored so that nothing is optimised away.
+constexpr int kFmaChains = 8;
+__global__ void __launch_bounds__(256) fma_rate_kernel(float* out, int iters, float b, float c) {
+  float a[kFmaChains];
+#pragma unroll
+  for (int i = 0; i < kFmaChains; ++i) a[i] = (float)(threadIdx.x + i) * 1e-3f;
+#pragma unroll 4
+  for (int it = 0; it < iters; ++it)
+#pragma unroll
+    for (int i = 0; i < kFmaChains; ++i) a[i] = fmaf(a[i], b, c);
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < kFmaChains; ++i) s += a[i];
+  out[blockIdx.x * (size_t)blockDim.x + threadIdx.x] = s;
 }
 
 // dst[i] = src[i] with dst in mapped host memory (the object of a pipelined
@@ -420,6 +475,15 @@ __global__ void iota_kernel(int32_t* a, int n) {
 }
 
 // ------------------------------------------------------------- host side
+// An NVTX range over a host call (sweeps, minibatch steps, group sweeps), for
+// timeline tools; header-only NVTX, inert unless a tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 thread_local std::string g_last_error;
 
 int fail(int code, const std::string& msg) {
@@ -604,6 +668,8 @@ cudaError_t prepare_size() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(window_kernel<MS, kStepRecycle>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(window_kernel<MS, kStepAtomic>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(window_kernel<MS, kEval>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(window_kernel<MS, kSim>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -711,6 +777,7 @@ struct magpie_ctx {
   double2* pyr_q = nullptr;
   double* pyr_u = nullptr;
   float2* contrib = nullptr;
+  float4* acc = nullptr;      // deterministic = 0: [n_rows][n_cols] atomic accumulators (N re, N im, D, 0)
   double* phi_pos = nullptr;
   double* gn_pos = nullptr;
   double* part = nullptr;     // [n_pos][kMaxSlots][2] per-block partial sums
@@ -1122,7 +1189,11 @@ int enqueue_precision_g0(magpie_ctx* c, const int32_t* idx, int count, cudaStrea
 // ev (optional): four events recorded before/after the window kernel and
 // before/after the apply kernel.
 int enqueue_step(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st, const cudaEvent_t* ev = nullptr) {
+  NvtxRange range("magpie minibatch step");
   StepArgs a = make_args(c, idx);
+  // the float-atomic update serves the FP32 window kernel without the phase
+  // rule or the learned correction; every other form uses the ordered one
+  const bool atom = c->acc && !c->precision && !c->cnn && !a.phase;
   if (ev) CUDA_TRY(cudaEventRecord(ev[0], st));
   int rc = MAGPIE_OK;
   if (c->precision) {
@@ -1145,18 +1216,30 @@ int enqueue_step(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st, 
     }
   } else {
     a.grad_only = c->cnn ? 1 : 0;
-    if (a.phase)
+    if (a.phase) {
       CUDA_TRY(launch_window_m<kStepRecycle>(c->p.m, a, count, st));
-    else
+    } else if (atom) {
+      a.acc = c->acc;
+      CUDA_TRY(launch_window_m<kStepAtomic>(c->p.m, a, count, st));
+    } else {
       CUDA_TRY(launch_window_m<kStep>(c->p.m, a, count, st));
+    }
     if (c->cnn) rc = enqueue_learned_tail(c, idx, count, st);
   }
   if (rc) return rc;
   if (ev) CUDA_TRY(cudaEventRecord(ev[1], st));
   if (ev) CUDA_TRY(cudaEventRecord(ev[2], st));
-  CUDA_TRY(launch_apply(c->z, c->p.n_rows, c->p.n_cols, c->corner, idx, count, c->p.n_pos, c->contrib,
-                        c->pyr + c->M, c->p.m, c->part, c->phi_pos, c->gn_pos, st,
-                        c->precision ? c->p.m / kTcLines : 0));
+  if (atom) {
+    const size_t npix = (size_t)c->p.n_rows * c->p.n_cols;
+    const unsigned blocks = (unsigned)std::min<size_t>((npix + 255) / 256, 152 * 8);
+    accum_apply_kernel<<<blocks, 256, 0, st>>>(c->z, c->acc, npix, idx, count, c->p.n_pos, c->part,
+                                               cluster_of(c->p.m), c->p.m, c->phi_pos, c->gn_pos);
+    CUDA_TRY(cudaGetLastError());
+  } else {
+    CUDA_TRY(launch_apply(c->z, c->p.n_rows, c->p.n_cols, c->corner, idx, count, c->p.n_pos, c->contrib,
+                          c->pyr + c->M, c->p.m, c->part, c->phi_pos, c->gn_pos, st,
+                          c->precision ? c->p.m / kTcLines : 0));
+  }
   if (c->p.update_probe) {
     probe_apply_kernel<<<(c->M + 255) / 256, 256, 0, st>>>(c->Q, c->M, idx, count, c->p.n_pos, c->pnum, c->pa2,
                                                            c->pmax, cluster_of(c->p.m), c->p.beta);
@@ -1265,6 +1348,7 @@ int validate(const magpie_params* p) {
   if (p->update_probe != 0 && p->update_probe != 1) return fail(MAGPIE_EINVAL, "update_probe must be 0 or 1");
   if (p->update_probe && (!(p->beta >= 0.f) || !std::isfinite(p->beta)))
     return fail(MAGPIE_EINVAL, "beta must be finite and >= 0");
+  if (p->deterministic != 0 && p->deterministic != 1) return fail(MAGPIE_EINVAL, "deterministic must be 0 or 1");
   return MAGPIE_OK;
 }
 
@@ -1446,7 +1530,8 @@ void magpie_destroy(magpie_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   void* bufs[] = {c->Q, c->tw, c->amp, c->stage, c->pos, c->pyr, c->pyr_q, c->pyr_u, c->contrib,
                   c->phi_pos, c->gn_pos, c->part, c->corner, c->mx, c->pnum, c->pa2, c->pmax, c->iota, c->order, c->sums, c->err,
-                  c->wz, c->lx, c->lscale, c->lacc, c->lmargin, c->lstats, c->pbuf, c->tabs, c->phase, c->g1buf};
+                  c->wz, c->lx, c->lscale, c->lacc, c->lmargin, c->lstats, c->pbuf, c->tabs, c->phase, c->g1buf,
+                  c->acc};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete c;
@@ -1496,7 +1581,8 @@ int magpie_create(magpie_ctx** out, const magpie_params* params, void* object, c
       (p.update_probe && (rc = alloc((void**)&c->pmax, sizeof(double) * kMaxCluster * p.minibatch))) ||
       (rc = alloc((void**)&c->iota, sizeof(int32_t) * N)) || (rc = alloc((void**)&c->order, sizeof(int32_t) * N)) ||
       (rc = alloc((void**)&c->sums, sizeof(double) * 2)) || (rc = alloc((void**)&c->err, sizeof(int))) ||
-      (p.levels >= 2 && (rc = alloc((void**)&c->wz, sizeof(float) * M * 2))))
+      (p.levels >= 2 && (rc = alloc((void**)&c->wz, sizeof(float) * M * 2))) ||
+      (!p.deterministic && (rc = alloc((void**)&c->acc, sizeof(float4) * (size_t)p.n_rows * p.n_cols))))
     return rc;
 
   auto cleanup_fail = [&](int code) {
@@ -1521,6 +1607,7 @@ int magpie_create(magpie_ctx** out, const magpie_params* params, void* object, c
   CTX_TRY(cudaMemsetAsync(c->err, 0, sizeof(int), st));
   CTX_TRY(cudaMemsetAsync(c->phi_pos, 0, sizeof(double) * N, st));
   CTX_TRY(cudaMemsetAsync(c->gn_pos, 0, sizeof(double) * N, st));
+  if (c->acc) CTX_TRY(cudaMemsetAsync(c->acc, 0, sizeof(float4) * (size_t)p.n_rows * p.n_cols, st));
   iota_kernel<<<(int)((N + 255) / 256), 256, 0, st>>>(c->iota, (int)N);
   CTX_TRY(cudaGetLastError());
   sqrt_kernel<<<1024, 256, 0, st>>>(intensities, c->amp, M * N);
@@ -1545,6 +1632,7 @@ int magpie_step(magpie_ctx* c, const int32_t* idx, int32_t count) {
 }
 
 int magpie_sweep(magpie_ctx* c, const int32_t* order) {
+  NvtxRange range("magpie_sweep");
   if (!c || !order) return fail(MAGPIE_EINVAL, "NULL argument");
   CUDA_TRY(cudaMemcpyAsync(c->order, order, sizeof(int32_t) * c->p.n_pos, cudaMemcpyDeviceToDevice, c->stream));
   return launch_sweep(c);
@@ -1552,6 +1640,7 @@ int magpie_sweep(magpie_ctx* c, const int32_t* order) {
 
 int magpie_profile_sweep(magpie_ctx* c, const int32_t* order, double* window_ms, double* apply_ms,
                          int32_t* launches) {
+  NvtxRange range("magpie_profile_sweep");
   if (!c || !order) return fail(MAGPIE_EINVAL, "NULL argument");
   CUDA_TRY(cudaMemcpyAsync(c->order, order, sizeof(int32_t) * c->p.n_pos, cudaMemcpyDeviceToDevice, c->stream));
   if (c->events.empty()) {
@@ -1603,6 +1692,7 @@ int magpie_window_values(magpie_ctx* c, double* phi, double* gnorm) {
 }
 
 int magpie_sweep_host(magpie_ctx* c, const int32_t* order, const float* intensities, void* object_out) {
+  NvtxRange range("magpie_sweep_host");
   if (!c || !order) return fail(MAGPIE_EINVAL, "NULL argument");
   const size_t N = c->p.n_pos, M = c->M;
   if (intensities) {
@@ -1856,6 +1946,7 @@ int magpie_group_create(magpie_group** out, magpie_ctx* const* ctxs, int32_t n, 
 }
 
 int magpie_group_sweep(magpie_group* g, const int32_t* const* orders) {
+  NvtxRange range("magpie_group_sweep");
   if (!g || !orders) return fail(MAGPIE_EINVAL, "NULL argument");
   for (size_t i = 0; i < g->members.size(); ++i)
     if (!orders[i]) return fail(MAGPIE_EINVAL, "order " + std::to_string(i) + " is NULL");
@@ -2184,6 +2275,7 @@ int magpie_group_set_minb(magpie_group* g, int32_t m, int32_t minb) {
 
 
 int magpie_sweep_host_async(magpie_ctx* c, const int32_t* order, const float* intensities, void* object_out) {
+  NvtxRange range("magpie_sweep_host_async");
   if (!c || !order || !intensities) return fail(MAGPIE_EINVAL, "NULL argument");
   const size_t N = c->p.n_pos, M = c->M;
   const int b = c->next_buf;
@@ -2255,6 +2347,44 @@ int magpie_sweep_host_async(magpie_ctx* c, const int32_t* order, const float* in
     }
   }
   c->next_buf = b ^ 1;
+  return MAGPIE_OK;
+}
+
+int magpie_fp32_fma_rate(int32_t iters, double* tflops, double* ms, void* stream) {
+  if (!tflops || iters < 1) return fail(MAGPIE_EINVAL, "need tflops and iters >= 1");
+  int dev = 0, sms = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = sms * 8;  // 8 blocks of 256 threads per SM: 64 warps, the most an SM holds
+  cudaStream_t st = (cudaStream_t)stream;
+  float* out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto release = [&]() {
+    if (out) cudaFree(out);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  cudaError_t e = cudaMalloc(&out, sizeof(float) * (size_t)blocks * 256);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best = 0.f;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // the first launch warms up; the best of the others
+    e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess) {
+      fma_rate_kernel<<<blocks, 256, 0, st>>>(out, iters, 0.9999999f, 1e-7f);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e == cudaSuccess && rep > 0 && (best == 0.f || t < best)) best = t;
+  }
+  release();
+  CUDA_TRY(e);
+  const double flops = 2.0 * kFmaChains * (double)iters * blocks * 256.0;
+  *tflops = flops / (best * 1e-3) / 1e12;
+  if (ms) *ms = best;
   return MAGPIE_OK;
 }
 

@@ -14,9 +14,11 @@ __host__ __device__ __forceinline__ int lvl_off(int MS, int l) {
 __host__ __device__ __forceinline__ int pyr_size(int MS, int L) { return lvl_off(MS, L); }
 
 // kStep: a minibatch step; kStepRecycle: the same with the phase rule of
-// Eq. (specification) across visits (phases kept per window); kEval: the
+// Eq. (specification) across visits (phases kept per window); kStepAtomic: a
+// minibatch step whose increments are added straight into object-sized
+// accumulators with float atomics (the non-deterministic update); kEval: the
 // objective only; kSim: forward intensities.
-enum Mode { kStep = 0, kEval = 1, kSim = 2, kStepRecycle = 3 };
+enum Mode { kStep = 0, kEval = 1, kSim = 2, kStepRecycle = 3, kStepAtomic = 4 };
 
 struct StepArgs {
   const float2* z;    // object [n_rows][n_cols]
@@ -40,6 +42,25 @@ struct StepArgs {
   int grad_only;      // step: write g^0 = conj(Q)(R_k - Q z_k) as the increments and skip the V-cycle
   float2* phase;      // kStepRecycle: [n_pos][MS][MS] unit phase of each spectrum entry at the last visit
   int amp_raw;        // amp holds the intensities d themselves: the kernel uses sqrt(max(d, 0))
+  float4* acc;        // kStepAtomic: [n_rows][n_cols] accumulators (sum w.Delta re, im, sum w, unused)
+};
+
+// The increment w . Delta of window pixel (r, c): stored in the window's slot
+// of the increment buffer (ordered update), or added with one 16-byte float
+// atomic, together with the pixel's weight w^0, into the object-sized
+// accumulators at the window's corner (kStepAtomic).
+template <int MS, bool ATOM>
+struct IncrementSink {
+  float2* out;         // [MS][MS] this window's increments (ordered update)
+  float4* acc;         // accumulator of the window's top-left object pixel (kStepAtomic)
+  int n_cols;
+  const float* w0;     // [MS][MS] u + |Q|^2
+  __device__ __forceinline__ void operator()(int r, int c, float2 v) const {
+    if constexpr (ATOM)
+      atomicAdd(acc + (size_t)r * n_cols + c, make_float4(v.x, v.y, __ldg(&w0[r * MS + c]), 0.f));
+    else
+      out[r * MS + c] = v;
+  }
 };
 
 // Sum over the block (a fixed order: warp shuffles, then the warps in order);
@@ -102,8 +123,8 @@ __device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
 // gamma of a strip of 2^TT rows; the 2x2 restrictions pair columns by warp
 // shuffles.  Levels coarser than TT are kept in `lvl` (local levels up to
 // log2(SLAB); coarser ones span the cluster and are finished by block 0).
-template <int MS, int TT>
-__device__ __forceinline__ void vcycle(const float2* Y, float2* lvl, const float* pyr, int L, int q, float2* out,
+template <int MS, int TT, class Sink>
+__device__ __forceinline__ void vcycle(const float2* Y, float2* lvl, const float* pyr, int L, int q, const Sink& put,
                                        int tid) {
   using Gm = Geo<MS>;
   constexpr int SLAB = Gm::SLAB, T = Gm::T, CL = Gm::CL, H = 1 << TT, NS = MS / H, SPAR = T / SLAB;
@@ -284,9 +305,8 @@ __device__ __forceinline__ void vcycle(const float2* Y, float2* lvl, const float
     if (ok) {
 #pragma unroll
       for (int a = 0; a < H; ++a) {
-        const int o = (R0 + a) * MS + cgl;
-        const float u = __ldg(&u0[o]);
-        out[o] = f2(g0[a].x + u * e1[a >> 1].x, g0[a].y + u * e1[a >> 1].y);
+        const float u = __ldg(&u0[(R0 + a) * MS + cgl]);
+        put(R0 + a, cgl, f2(g0[a].x + u * e1[a >> 1].x, g0[a].y + u * e1[a >> 1].y));
       }
     }
   }

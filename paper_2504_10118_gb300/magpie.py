@@ -37,7 +37,8 @@ class MagpieError(RuntimeError):
 class magpie_params(ctypes.Structure):
     _fields_ = [("n_rows", ctypes.c_int32), ("n_cols", ctypes.c_int32), ("m", ctypes.c_int32),
                 ("n_pos", ctypes.c_int32), ("levels", ctypes.c_int32), ("minibatch", ctypes.c_int32),
-                ("alpha", ctypes.c_float), ("update_probe", ctypes.c_int32), ("beta", ctypes.c_float)]
+                ("alpha", ctypes.c_float), ("update_probe", ctypes.c_int32), ("beta", ctypes.c_float),
+                ("deterministic", ctypes.c_int32)]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -106,6 +107,7 @@ def lib() -> ctypes.CDLL:
             "magpie_set_precision": (ctypes.c_int, [vp, i32]),
             "magpie_set_variant": (ctypes.c_int, [vp, i32]),
             "magpie_dft2_tc": (ctypes.c_int, [vp, vp, i32, i32, i32, vp]),
+            "magpie_fp32_fma_rate": (ctypes.c_int, [i32, dp, dp, vp]),
             "magpie_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             "magpie_last_error": (ctypes.c_char_p, []),
             "magpie_version": (ctypes.c_int, []),
@@ -144,9 +146,10 @@ def _stream() -> int:
     return torch.cuda.current_stream().cuda_stream
 
 
-def magpie_params_of(n_rows, n_cols, m, n_pos, levels, minibatch, alpha, update_probe=0, beta=0.0) -> magpie_params:
+def magpie_params_of(n_rows, n_cols, m, n_pos, levels, minibatch, alpha, update_probe=0, beta=0.0,
+                     deterministic=1) -> magpie_params:
     return magpie_params(int(n_rows), int(n_cols), int(m), int(n_pos), int(levels), int(minibatch), float(alpha),
-                         int(update_probe), float(beta))
+                         int(update_probe), float(beta), int(deterministic))
 
 
 class Context:
@@ -450,6 +453,13 @@ def magpie_learned_window_values(ctx: Context, count: int):
     mg = (ctypes.c_double * count)()
     _check(lib().magpie_learned_window_values(ctx.handle, count, acc, mg))
     return list(acc), list(mg)
+
+
+def magpie_fp32_fma_rate(iters: int = 4096):
+    """(TFLOP/s, ms) of the FP32 FMA rate measurement (see the C header)."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().magpie_fp32_fma_rate(int(iters), ctypes.byref(tf), ctypes.byref(ms), _stream()))
+    return tf.value, ms.value
 
 
 def magpie_strerror(code: int) -> str:

@@ -41,18 +41,19 @@ def test_every_declared_symbol_is_exported(L):
 
 
 def test_error_strings_and_version(L):
-    assert L.magpie_version() == 10100
+    assert L.magpie_version() == 10200
     for code in (0, -1, -2, -3, -4, -5):
         assert L.magpie_strerror(code)
     assert L.magpie_strerror(-99) == b"unknown error"
 
 
 def _create(L, **kw):
-    p = dict(n_rows=128, n_cols=128, m=32, n_pos=64, levels=2, minibatch=16, alpha=0.1, update_probe=0, beta=0.0)
+    p = dict(n_rows=128, n_cols=128, m=32, n_pos=64, levels=2, minibatch=16, alpha=0.1, update_probe=0, beta=0.0,
+             deterministic=1)
     p.update(kw)
     h = ctypes.c_void_p()
     params = magpie.magpie_params(p["n_rows"], p["n_cols"], p["m"], p["n_pos"], p["levels"],
-                                  p["minibatch"], p["alpha"], p["update_probe"], p["beta"])
+                                  p["minibatch"], p["alpha"], p["update_probe"], p["beta"], p["deterministic"])
     # dummy non-NULL pointers: argument checks fail before any of them is used
     dummy = ctypes.c_void_p(0x1000)
     rc = L.magpie_create(ctypes.byref(h), ctypes.byref(params), dummy, dummy, dummy, dummy, None)
@@ -75,6 +76,8 @@ def _create(L, **kw):
     (dict(update_probe=2), magpie.EINVAL),
     (dict(update_probe=1, beta=-0.5), magpie.EINVAL),
     (dict(update_probe=1, beta=float("nan")), magpie.EINVAL),
+    (dict(deterministic=2), magpie.EINVAL),
+    (dict(deterministic=-1), magpie.EINVAL),
 ])
 def test_create_rejects_bad_arguments_without_a_gpu(L, kw, code):
     rc, h = _create(L, **kw)

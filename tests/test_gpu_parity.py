@@ -1,10 +1,12 @@
 """CUDA path (FP32) against the FP64 oracle, through the C ABI (GPU).
 
 Both sides start from the same FP32-representable inputs.  Tolerances: a
-minibatch step, a sweep and the objective/stopping values must agree with the
-oracle to 1e-5 relative (norm-wise over the object, or on the scalar); the
-forward intensities to 1e-5 norm-wise; after the 50-sweep run of the small
-workload the two objects must agree to NRMSE 1e-4 (global phase removed).
+minibatch step must agree with the oracle to 1e-5 relative, both over the
+whole object and over the step's increment z_after - z_before; the
+objective/stopping values to 1e-5 relative; the forward intensities to 1e-5
+norm-wise; after the 50-sweep run of the small workload the two objects must
+agree to NRMSE 1e-4 (global phase removed).  At full size every step's
+increment is also compared pixel by pixel (bars derived in the test).
 """
 import numpy as np
 import pytest
@@ -16,6 +18,7 @@ from paper_2504_10118_gb300 import magpie, synth
 pytestmark = pytest.mark.gpu
 
 STEP_TOL = 1e-5
+INC_TOL = 1e-5  # the same bar on the increment of a step, ||dz_gpu - dz_orc|| / ||dz_orc||
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -50,11 +53,11 @@ class Problem:
         self.z0 = f32(z0)
         self.u = O.rpie_regulariser(self.Q, alpha)
 
-    def ctx(self, z=None, update_probe=0, beta=0.0, probe=None):
+    def ctx(self, z=None, update_probe=0, beta=0.0, probe=None, deterministic=1):
         dev = torch.device("cuda")
         self.zt = torch.from_numpy((self.z0 if z is None else z).astype(np.complex64)).to(dev)
         p = magpie.magpie_params_of(self.n, self.n, self.m, self.N, self.levels, self.B, self.alpha,
-                                    update_probe, beta)
+                                    update_probe, beta, deterministic)
         Q = self.Q if probe is None else probe
         return magpie.magpie_create(p, self.zt, torch.from_numpy(Q.astype(np.complex64)).to(dev),
                                     torch.from_numpy(self.pos).to(dev),
@@ -110,9 +113,9 @@ def test_minibatch_step(n, m, grid, step, jit, L, B, cnt):
     got = P.z_gpu()
     ref = O.minibatch_step(P.z0, P.Q, P.pos, P.d, P.u, L, batch)
     assert rel(got, ref) < STEP_TOL
-    # the increments themselves, where they are not negligible
+    # the increments themselves
     inc_rel = rel(got - P.z0, ref - P.z0)
-    assert inc_rel < 2e-4, inc_rel
+    assert inc_rel < INC_TOL, inc_rel
     ctx.close()
 
 
@@ -128,7 +131,7 @@ def test_largest_minibatch():
     got = P.z_gpu()
     ref = O.minibatch_step(P.z0, P.Q, P.pos, P.d, P.u, 2, batch)
     assert rel(got, ref) < STEP_TOL
-    assert rel(got - P.z0, ref - P.z0) < 2e-4
+    assert rel(got - P.z0, ref - P.z0) < INC_TOL
     ctx.close()
 
 
@@ -268,34 +271,72 @@ def oracle_with_float32_ffts():
     return mod
 
 
-def test_mid_workload_full_size():
-    """The n=512, m=128, 900-window, 3-level, B=64 Poisson workload at full
-    size, in the launch configuration the benchmark times.
+def increment_errors(before, got, ref):
+    """Errors of one step's increment dz = z_after - z_before against the
+    oracle's: norm-wise relative, and the largest element-wise relative error
+    on the pixels whose oracle increment exceeds 1e-3 and 1e-2 of its
+    largest modulus."""
+    dg, do = got - before, ref - before
+    a = np.abs(do)
+    out = [rel(dg, do)]
+    for t in (1e-3, 1e-2):
+        big = a > t * a.max()
+        out.append(float(np.max(np.abs(dg[big] - do[big]) / a[big])))
+    return out
 
-    Every one of the 15 minibatch steps of a sweep meets the 1e-5 bar when the
-    oracle starts from the state the GPU reached before that step.  Whole
-    sweeps are compared with a bar set by the conditioning of the iteration:
-    rounding-level differences grow about 1.7x per step here, so the oracle's
-    own arithmetic with float32 FFTs ends a sweep ~2.4e-5 from its FP64 result
-    (from the true object plus noise) or ~2.5e-3 (from the flat start z = 1,
-    whose window spectra are F(Q) itself, with exact zeros where the phase is
-    decided by rounding: theta(0) = 0 in FP64, a rounding-noise phase in
-    FP32).  The CUDA path must stay within twice the distance measured that
-    way."""
+
+# Element-wise bars on a step's increment at full size.  Every pixel's
+# increment carries an absolute float32 error of a few 1e-6 of the largest
+# increment (the transforms' and the V-cycle's rounding, relative to the
+# spectrum and the object, not to the pixel's own increment), so the relative
+# error of a pixel grows as its increment shrinks: measured at most 1.8e-3
+# where |dz| > 1e-3 max|dz| and 5.4e-4 where |dz| > 1e-2 max|dz| over the 15
+# steps of a sweep; the bars leave a factor of about 3.
+EW_TOL = {1e-3: 5e-3, 1e-2: 2e-3}
+
+
+def check_mid_steps(deterministic):
+    """Every step of one sweep of the mid workload from the GPU's own state
+    before the step: object and increment to 1e-5, increment element-wise."""
     w = synth.WORKLOADS["mid"]
     P = Problem(w.n, w.m, w.grid, w.step, w.jitter, w.levels, w.minibatch, alpha=w.alpha,
                 photons=w.photons, perturb=0.2)
     order = synth.make_order(P.N, 0)
-    ctx = P.ctx()
-    worst = 0.0
+    ctx = P.ctx(deterministic=deterministic)
+    worst = np.zeros(4)
     for s in range(0, P.N, w.minibatch):
         before = P.z_gpu()
         batch = order[s:s + w.minibatch]
         magpie.magpie_step(ctx, dev_i32(batch))
+        got = P.z_gpu()
         ref = O.minibatch_step(before, P.Q, P.pos, P.d, P.u, w.levels, batch)
-        worst = max(worst, rel(P.z_gpu(), ref))
-    assert worst < STEP_TOL, worst
+        worst = np.maximum(worst, [rel(got, ref)] + increment_errors(before, got, ref))
     ctx.close()
+    assert worst[0] < STEP_TOL, worst
+    assert worst[1] < INC_TOL, worst
+    assert worst[2] < EW_TOL[1e-3], worst
+    assert worst[3] < EW_TOL[1e-2], worst
+    return P, order
+
+
+def test_mid_workload_full_size():
+    """The n=512, m=128, 900-window, 3-level, B=64 Poisson workload at full
+    size, in the launch configuration the benchmark times.
+
+    Every one of the 15 minibatch steps of a sweep meets the 1e-5 bar, on the
+    object and on the step's increment, when the oracle starts from the state
+    the GPU reached before that step, and its increment matches pixel by
+    pixel (EW_TOL).  Whole sweeps are compared with a bar set by the
+    conditioning of the iteration (a reading recorded in the design notes):
+    a step's rounding-level differences are carried into every later window
+    that overlaps it, so the oracle's own arithmetic with float32 FFTs ends a
+    sweep 4.3e-5 from its FP64 result from the true object plus noise, and
+    2.5e-3 from the flat start z = 1, whose window spectra are F(Q) itself,
+    with exact zeros where the phase is decided by rounding (theta(0) = 0 in
+    FP64, a rounding-noise phase in FP32).  The CUDA path (2.4e-5 and 2.6e-3
+    measured) must stay within twice the distance measured that way."""
+    w = synth.WORKLOADS["mid"]
+    P, order = check_mid_steps(1)
 
     f32_oracle = oracle_with_float32_ffts()
     for start in (P.z0, np.ones((w.n, w.n), dtype=np.complex128)):
