@@ -58,6 +58,8 @@ extern "C" {
 #define MAGPIE_ENOMEM (-3)      /* device memory allocation failed              */
 #define MAGPIE_EUNSUPPORTED (-4)/* a valid size this build has no kernel for    */
 #define MAGPIE_EINDEX (-5)      /* a device-side window index was out of range  */
+#define MAGPIE_ETIMEOUT (-6)    /* a bounded device wait ran out (a tensor-core
+                                   convolution stopped waiting for its MMAs)     */
 
 typedef struct magpie_ctx magpie_ctx;
 
@@ -305,6 +307,24 @@ int magpie_cnn_create(magpie_cnn** out, int32_t h, int32_t max_batch, void* stre
    attached to a context that still sweeps. */
 void magpie_cnn_destroy(magpie_cnn* cnn);
 
+/*
+ * Which tensor-core instructions the network's forward convolutions use:
+ * 1 (the default) the 5th-generation tensor cores (tcgen05.mma, operands in
+ * shared memory in the 128-byte-swizzled K-major layout, FP32 accumulators
+ * in tensor memory) for every layer whose input channels and output channels
+ * are multiples of 64, the register-fragment mma.sync kernel for the others;
+ * 0 mma.sync for every layer.  Both accumulate the same BF16 products in
+ * FP32 (summation order differs).  MAGPIE_EINVAL for another value.
+ */
+int magpie_cnn_set_tensor_path(magpie_cnn* net, int32_t path);
+
+/*
+ * Synchronous status of the network's stream: MAGPIE_ETIMEOUT (and the flag
+ * cleared) when a tensor-core convolution's bounded wait for its MMAs ran out
+ * since the last call (that block skipped its output), else MAGPIE_OK.
+ */
+int magpie_cnn_status(magpie_cnn* net);
+
 /* Copy in (DEVICE float32 [param_count]) the parameters; resets the Adam
    moments and step count.  magpie_cnn_get_params copies them out. */
 int magpie_cnn_set_params(magpie_cnn* cnn, const float* theta);
@@ -438,6 +458,19 @@ int magpie_step_noalloc(void* object, int32_t n_rows, int32_t n_cols, const void
  * changes no device setting.  Synchronous.
  */
 int magpie_fp32_fma_rate(int32_t iters, double* tflops, double* ms, void* stream);
+
+/*
+ * Measurement helper, not part of the method: one minibatch step of the FP32
+ * form (as magpie_step, object updated) with thread 0 of every block of the
+ * window kernel recording %globaltimer (ns) at ten points: start, exit wave
+ * gathered, column FFTs sent, row data received, row pass sent, column data
+ * received, inverse column FFTs done, g^0 done, block sums done, V-cycle
+ * done (0 where a point is not reached).  stamps: HOST uint64
+ * [count][blocks per window][10], capacity its length.  Synchronous.
+ * Returns MAGPIE_EUNSUPPORTED unless the library was built with
+ * MAGPIE_STAGE_TIMES defined (the stamps are compiled out otherwise).
+ */
+int magpie_stage_times(magpie_ctx* ctx, const int32_t* idx, int32_t count, uint64_t* stamps, int64_t capacity);
 
 /* Message of the calling thread's most recent failed call ("" if none). */
 const char* magpie_last_error(void);

@@ -147,6 +147,14 @@ __device__ __forceinline__ void window_wait() {
     __syncthreads();
 }
 
+// ---- mbarriers (the tensor-core kernels' stage barriers)
+constexpr int kMaxWaitTries = 1 << 20;  // bound of every mbarrier wait (a try returns within about a microsecond)
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
 // Barrier over the window's blocks; with CL = 1 an ordinary block barrier.
 template <int CL>
 __device__ __forceinline__ void window_sync() {

@@ -65,6 +65,7 @@ constexpr int kApplyUnroll = 4;      // increments in flight per thread in the u
 #include "window_kernel.cuh"
 #include "learned.cuh"
 #include "precision.cuh"
+#include "umma.cuh"
 
 // z += sum_b contrib_b / sum_b w0 over the windows covering each pixel, in
 // minibatch order (bitwise reproducible).  One block of 256 threads per
@@ -760,6 +761,8 @@ struct magpie_cnn {
   size_t part_n = 0;
   int last_batch = 0;               // batch of the last forward pass (backward's batch)
   long step = 0;                    // Adam steps taken
+  int tensor_path = 1;              // convolutions: 1 tcgen05 (where the layer fits it), 0 mma.sync
+  int* err = nullptr;               // bit 2: a bounded wait of a tcgen05 convolution ran out
 };
 
 struct magpie_ctx {
@@ -778,6 +781,7 @@ struct magpie_ctx {
   double* pyr_u = nullptr;
   float2* contrib = nullptr;
   float4* acc = nullptr;      // deterministic = 0: [n_rows][n_cols] atomic accumulators (N re, N im, D, 0)
+  unsigned long long* stamps = nullptr;  // magpie_stage_times: per-stage timestamps of the window kernel
   double* phi_pos = nullptr;
   double* gn_pos = nullptr;
   double* part = nullptr;     // [n_pos][kMaxSlots][2] per-block partial sums
@@ -851,6 +855,7 @@ StepArgs make_args(magpie_ctx* c, const int32_t* idx) {
   a.pmax = c->pmax;
   a.err = c->err;
   a.phase = (c->variant & 2) ? c->phase : nullptr;
+  a.stamps = c->stamps;
   return a;
 }
 
@@ -888,6 +893,29 @@ ConvPlan conv_plan(const ConvFwd& a) {
   return pl;
 }
 
+// Layers the tcgen05 convolution serves: whole 64-element K steps inside one
+// tap (Cin a multiple of 64) and whole 64-wide N tiles.
+bool conv_tc_fits(const ConvFwd& a) { return a.Cin % 64 == 0 && a.Cout % 64 == 0; }
+
+// Tiles of the tcgen05 convolution: 128 output pixels x 128 (or 64) output
+// channels, K split so that about two blocks per SM run (at least two K steps
+// of 64 per split).
+ConvPlan conv_plan_tc(const ConvFwd& a) {
+  ConvPlan pl{};
+  pl.bn = a.Cout % 128 == 0 ? 128 : 64;
+  pl.bm = kTcBM;
+  const int Mtot = a.B * a.Ho * a.Ho;
+  pl.gx = (Mtot + kTcBM - 1) / kTcBM;
+  pl.gy = a.Cout / pl.bn;
+  const int ksteps = a.K / kTcBK;
+  const int blocks = pl.gx * pl.gy;
+  const int splits = std::max(1, std::min(ksteps / 2, (2 * 152 + blocks - 1) / blocks));
+  const int per = (ksteps + splits - 1) / splits;
+  pl.ksplit = per * kTcBK;
+  pl.splits = (ksteps + per - 1) / per;
+  return pl;
+}
+
 // Pixel chunks of the weight-gradient GEMM of layer l (enough blocks to
 // fill the GPU, at least 64 pixels per chunk).
 struct WgradPlan {
@@ -920,19 +948,28 @@ size_t cnn_part_floats(int h, int max_batch) {
     a.K = 9 * a.Cin;
     const ConvPlan pl = conv_plan(a);
     if (pl.splits > 1) n = std::max(n, (size_t)pl.splits * B * Ho * Ho * a.Cout);
+    if (conv_tc_fits(a)) {
+      const ConvPlan pt = conv_plan_tc(a);
+      if (pt.splits > 1) n = std::max(n, (size_t)pt.splits * B * Ho * Ho * a.Cout);
+    }
     const int P = a.Cout * 9 * a.Cin + a.Cout;
     n = std::max(n, (size_t)wgrad_plan(h, l, B).chunks * P);
   }
   return n;
 }
 
-cudaError_t launch_conv(const ConvFwd& a0, float* part, cudaStream_t st) {
+cudaError_t launch_conv(const ConvFwd& a0, float* part, cudaStream_t st, int tensor_path = 0, int* err = nullptr) {
   ConvFwd a = a0;
-  const ConvPlan pl = conv_plan(a);
+  const bool tc = tensor_path == 1 && conv_tc_fits(a) && err;
+  const ConvPlan pl = tc ? conv_plan_tc(a) : conv_plan(a);
   a.ksplit = pl.ksplit;
   a.part = pl.splits > 1 ? part : nullptr;
   const dim3 grid(pl.gx, pl.gy, pl.splits);
-  if (pl.bn == 8)
+  if (tc && pl.bn == 128)
+    conv_fwd_tc_kernel<128><<<grid, 128, TcConv<128>::SMEM, st>>>(a, err);
+  else if (tc)
+    conv_fwd_tc_kernel<64><<<grid, 128, TcConv<64>::SMEM, st>>>(a, err);
+  else if (pl.bn == 8)
     conv_fwd_kernel<128, 8><<<grid, 128, 0, st>>>(a);
   else if (pl.bn == 32)
     conv_fwd_kernel<128, 32><<<grid, 128, 0, st>>>(a);
@@ -968,7 +1005,7 @@ int cnn_enqueue_forward(magpie_cnn* n, const float* x, int batch, float* y, cuda
     a.relu = L.relu;
     a.out_f32 = l + 1 == kCnnLayers;
     a.K = 9 * L.cin;
-    CUDA_TRY(launch_conv(a, n->part, st));
+    CUDA_TRY(launch_conv(a, n->part, st, n->tensor_path, n->err));
   }
   n->last_batch = batch;
   return MAGPIE_OK;
@@ -1500,6 +1537,7 @@ const char* magpie_strerror(int code) {
     case MAGPIE_ENOMEM: return "out of device memory";
     case MAGPIE_EUNSUPPORTED: return "unsupported size";
     case MAGPIE_EINDEX: return "window index out of range";
+    case MAGPIE_ETIMEOUT: return "bounded device wait ran out";
     default: return "unknown error";
   }
 }
@@ -1987,7 +2025,7 @@ int32_t magpie_cnn_param_count(void) { return cnn_param_count(); }
 
 void magpie_cnn_destroy(magpie_cnn* n) {
   if (!n) return;
-  void* bufs[] = {n->theta, n->adam_m, n->adam_v, n->wbf, n->grad, n->y, n->dz[0], n->dz[1], n->dy, n->part};
+  void* bufs[] = {n->theta, n->adam_m, n->adam_v, n->wbf, n->grad, n->y, n->dz[0], n->dz[1], n->dy, n->part, n->err};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (auto* a : n->act)
@@ -2036,6 +2074,16 @@ int magpie_cnn_create(magpie_cnn** out, int32_t h, int32_t max_batch, void* stre
   al((void**)&n->dz[0], sizeof(float) * dzn);
   al((void**)&n->dz[1], sizeof(float) * dzn);
   al((void**)&n->part, sizeof(float) * n->part_n);
+  al((void**)&n->err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(n->err, 0, sizeof(int), n->stream);
+  for (int l = 0; l < kCnnLayers && e == cudaSuccess; ++l)
+    if (n->off[l] % 8) e = cudaErrorMisalignedAddress;  // 16-byte rows of every layer's BF16 weights
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(conv_fwd_tc_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TcConv<128>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(conv_fwd_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TcConv<64>::SMEM);
   if (e == cudaSuccess) e = cudaMemsetAsync(n->theta, 0, sizeof(float) * P, n->stream);
   if (e != cudaSuccess) {
     magpie_cnn_destroy(n);
@@ -2132,6 +2180,24 @@ int magpie_attach_cnn(magpie_ctx* c, magpie_cnn* n) {
   }
   invalidate_graphs(c);
   c->cnn = n;
+  return MAGPIE_OK;
+}
+
+int magpie_cnn_set_tensor_path(magpie_cnn* n, int32_t path) {
+  if (!n || (path != 0 && path != 1)) return fail(MAGPIE_EINVAL, "need a network and path 0 or 1");
+  n->tensor_path = path;
+  return MAGPIE_OK;
+}
+
+int magpie_cnn_status(magpie_cnn* n) {
+  if (!n) return fail(MAGPIE_EINVAL, "NULL argument");
+  int h = 0;
+  CUDA_TRY(cudaMemcpyAsync(&h, n->err, sizeof(int), cudaMemcpyDeviceToHost, n->stream));
+  CUDA_TRY(cudaStreamSynchronize(n->stream));
+  if (h) {
+    CUDA_TRY(cudaMemsetAsync(n->err, 0, sizeof(int), n->stream));
+    return fail(MAGPIE_ETIMEOUT, "a tensor-core convolution stopped waiting for its MMAs (bounded wait ran out)");
+  }
   return MAGPIE_OK;
 }
 
@@ -2386,6 +2452,34 @@ int magpie_fp32_fma_rate(int32_t iters, double* tflops, double* ms, void* stream
   *tflops = flops / (best * 1e-3) / 1e12;
   if (ms) *ms = best;
   return MAGPIE_OK;
+}
+
+int magpie_stage_times(magpie_ctx* c, const int32_t* idx, int32_t count, uint64_t* stamps, int64_t capacity) {
+#ifndef MAGPIE_STAGE_TIMES
+  (void)c;
+  (void)idx;
+  (void)count;
+  (void)stamps;
+  (void)capacity;
+  return fail(MAGPIE_EUNSUPPORTED, "this build has no per-stage timestamps (build with MAGPIE_STAGE_TIMES)");
+#else
+  if (!c || !idx || !stamps) return fail(MAGPIE_EINVAL, "NULL argument");
+  if (count < 1 || count > c->p.minibatch) return fail(MAGPIE_EINVAL, "count must lie in [1, minibatch]");
+  if (c->precision || c->cnn) return fail(MAGPIE_EINVAL, "per-stage timestamps time the FP32 window kernel");
+  const size_t n = (size_t)count * cluster_of(c->p.m) * kStages;
+  if (capacity < (int64_t)n) return fail(MAGPIE_EINVAL, "capacity below count * blocks per window * stages");
+  CUDA_TRY(cudaMalloc(&c->stamps, sizeof(unsigned long long) * n));
+  cudaError_t e = cudaMemsetAsync(c->stamps, 0, sizeof(unsigned long long) * n, c->stream);
+  int rc = e == cudaSuccess ? enqueue_step(c, idx, count, c->stream) : MAGPIE_OK;
+  if (e == cudaSuccess && rc == MAGPIE_OK)
+    e = cudaMemcpyAsync(stamps, c->stamps, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(c->stamps);
+  c->stamps = nullptr;
+  CUDA_TRY(e);
+  if (rc) return rc;
+  return read_err(c);
+#endif
 }
 
 int magpie_sync(magpie_ctx* c) {

@@ -43,7 +43,24 @@ struct StepArgs {
   float2* phase;      // kStepRecycle: [n_pos][MS][MS] unit phase of each spectrum entry at the last visit
   int amp_raw;        // amp holds the intensities d themselves: the kernel uses sqrt(max(d, 0))
   float4* acc;        // kStepAtomic: [n_rows][n_cols] accumulators (sum w.Delta re, im, sum w, unused)
+  unsigned long long* stamps;  // builds with MAGPIE_STAGE_TIMES: [windows][CL][kStages] %globaltimer stamps
 };
+
+// Per-stage timestamps of the window kernel (thread 0 of every block), for
+// builds with MAGPIE_STAGE_TIMES defined; compiled out otherwise.
+constexpr int kStages = 10;
+#ifdef MAGPIE_STAGE_TIMES
+#define MAGPIE_STAMP(stage)                                                          \
+  do {                                                                               \
+    if (tid == 0 && A.stamps) {                                                      \
+      unsigned long long t_;                                                         \
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_));                         \
+      A.stamps[((size_t)win * Geo<MS>::CL + q) * kStages + (stage)] = t_;            \
+    }                                                                                \
+  } while (0)
+#else
+#define MAGPIE_STAMP(stage) ((void)0)
+#endif
 
 // The increment w . Delta of window pixel (r, c): stored in the window's slot
 // of the increment buffer (ordered update), or added with one 16-byte float

@@ -18,6 +18,14 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libmagpie.so")
+# the same library with the window kernel's per-stage timestamps compiled in
+# (MAGPIE_STAGE_TIMES); build() and lib() use it when the environment variable
+# MAGPIE_STAGE_TIMES is 1
+STAGES_LIB_PATH = os.path.join(BUILD_DIR, "libmagpie_stages.so")
+
+
+def _stages() -> bool:
+    return os.environ.get("MAGPIE_STAGE_TIMES") == "1"
 SOURCES = [os.path.join(HERE, "csrc", "magpie.cu")]
 DEPENDS = [os.path.join(HERE, "csrc", f) for f in ("fft_lines.cuh", "window_kernel.cuh", "window_body.inc",
                                                    "learned.cuh", "precision.cuh")]
@@ -25,7 +33,7 @@ HEADER = os.path.join(ROOT, "include", "magpie.h")
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared"]
 
-OK, EINVAL, ECUDA, ENOMEM, EUNSUPPORTED, EINDEX = 0, -1, -2, -3, -4, -5
+OK, EINVAL, ECUDA, ENOMEM, EUNSUPPORTED, EINDEX, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 
 
 class MagpieError(RuntimeError):
@@ -42,18 +50,21 @@ class magpie_params(ctypes.Structure):
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile the library for sm_103a into the package's _build/ folder."""
+    """Compile the library for sm_103a into the package's _build/ folder
+    (the per-stage timestamp variant when MAGPIE_STAGE_TIMES=1)."""
+    path = STAGES_LIB_PATH if _stages() else LIB_PATH
     newest = max(os.path.getmtime(p) for p in SOURCES + DEPENDS + [HEADER])
-    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
-        return LIB_PATH
+    if not force and os.path.exists(path) and os.path.getmtime(path) >= newest:
+        return path
     os.makedirs(BUILD_DIR, exist_ok=True)
-    tmp = LIB_PATH + ".tmp"
-    cmd = ["nvcc", *NVCC_FLAGS, "-I", os.path.join(ROOT, "include"), "-o", tmp, *SOURCES]
+    tmp = path + ".tmp"
+    cmd = ["nvcc", *NVCC_FLAGS, *(["-DMAGPIE_STAGE_TIMES"] if _stages() else []), "-I",
+           os.path.join(ROOT, "include"), "-o", tmp, *SOURCES]
     if verbose:
         print(" ".join(cmd))
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, path)
+    return path
 
 
 _lib = None
@@ -63,10 +74,11 @@ def lib() -> ctypes.CDLL:
     """The loaded library; raises if it has not been built."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"MAGPIE CUDA library not built ({LIB_PATH} missing); "
+        path = STAGES_LIB_PATH if _stages() else LIB_PATH
+        if not os.path.exists(path):
+            raise RuntimeError(f"MAGPIE CUDA library not built ({path} missing); "
                                "run paper_2504_10118_gb300.magpie.build()")
-        L = ctypes.CDLL(LIB_PATH)
+        L = ctypes.CDLL(path)
         vp, i32, f32p = ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)
         dp = ctypes.POINTER(ctypes.c_double)
         sig = {
@@ -94,6 +106,8 @@ def lib() -> ctypes.CDLL:
             "magpie_cnn_param_count": (i32, []),
             "magpie_cnn_create": (ctypes.c_int, [ctypes.POINTER(vp), i32, i32, vp]),
             "magpie_cnn_destroy": (None, [vp]),
+            "magpie_cnn_set_tensor_path": (ctypes.c_int, [vp, i32]),
+            "magpie_cnn_status": (ctypes.c_int, [vp]),
             "magpie_cnn_set_params": (ctypes.c_int, [vp, vp]),
             "magpie_cnn_get_params": (ctypes.c_int, [vp, vp]),
             "magpie_cnn_forward": (ctypes.c_int, [vp, vp, i32, vp]),
@@ -108,6 +122,7 @@ def lib() -> ctypes.CDLL:
             "magpie_set_variant": (ctypes.c_int, [vp, i32]),
             "magpie_dft2_tc": (ctypes.c_int, [vp, vp, i32, i32, i32, vp]),
             "magpie_fp32_fma_rate": (ctypes.c_int, [i32, dp, dp, vp]),
+            "magpie_stage_times": (ctypes.c_int, [vp, vp, i32, vp, ctypes.c_int64]),
             "magpie_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             "magpie_last_error": (ctypes.c_char_p, []),
             "magpie_version": (ctypes.c_int, []),
@@ -393,6 +408,16 @@ def magpie_cnn_destroy(cnn: Cnn) -> None:
     cnn.close()
 
 
+def magpie_cnn_set_tensor_path(cnn: Cnn, path: int) -> None:
+    """1: tcgen05 convolutions where the layer fits, 0: mma.sync everywhere."""
+    _check(lib().magpie_cnn_set_tensor_path(cnn.handle, int(path)))
+
+
+def magpie_cnn_status(cnn: Cnn) -> None:
+    """Raises MagpieError(ETIMEOUT) if a convolution's bounded wait ran out."""
+    _check(lib().magpie_cnn_status(cnn.handle))
+
+
 def magpie_cnn_set_params(cnn: Cnn, theta: torch.Tensor) -> None:
     _check(lib().magpie_cnn_set_params(cnn.handle, _dev(theta, torch.float32, cnn.P, "theta")))
 
@@ -460,6 +485,16 @@ def magpie_fp32_fma_rate(iters: int = 4096):
     tf, ms = ctypes.c_double(), ctypes.c_double()
     _check(lib().magpie_fp32_fma_rate(int(iters), ctypes.byref(tf), ctypes.byref(ms), _stream()))
     return tf.value, ms.value
+
+
+def magpie_stage_times(ctx: Context, idx: torch.Tensor, blocks_per_window: int) -> torch.Tensor:
+    """Per-stage %globaltimer stamps of one step (see the C header): uint64
+    [count][blocks_per_window][10] on the host."""
+    count = idx.numel()
+    out = torch.zeros((count, blocks_per_window, 10), dtype=torch.int64)
+    _check(lib().magpie_stage_times(ctx.handle, _dev(idx, torch.int32, count, "idx"), count, out.data_ptr(),
+                                    out.numel()))
+    return out
 
 
 def magpie_strerror(code: int) -> str:

@@ -42,7 +42,7 @@ def test_every_declared_symbol_is_exported(L):
 
 def test_error_strings_and_version(L):
     assert L.magpie_version() == 10200
-    for code in (0, -1, -2, -3, -4, -5):
+    for code in (0, -1, -2, -3, -4, -5, -6):
         assert L.magpie_strerror(code)
     assert L.magpie_strerror(-99) == b"unknown error"
 

@@ -35,15 +35,21 @@ def test_param_count():
     assert magpie.magpie_cnn_param_count() == L.param_count() == 980002
 
 
+@pytest.mark.parametrize("path", [1, 0], ids=["tcgen05", "mma_sync"])
 @pytest.mark.parametrize("h,B,check", [(8, 3, 3), (16, 5, 5), (32, 64, 4)])
-def test_forward_matches_oracle(h, B, check):
-    """BF16 tensor-core forward vs the oracle's BF16-rounded FP64 forward; at
-    h = 32 a full 64-window batch runs and four windows are checked."""
+def test_forward_matches_oracle(h, B, check, path):
+    """BF16 tensor-core forward vs the oracle's BF16-rounded FP64 forward,
+    with the 5th-generation tensor cores (tcgen05, TMEM accumulators) for the
+    layers with 64-multiple channel counts and with register-fragment mma.sync
+    everywhere; at h = 32 a full 64-window batch runs and four windows are
+    checked."""
     theta = random_theta(L, 21).astype(np.float32).astype(np.float64)
     x = np.random.default_rng(22).normal(size=(B, h, h, 4)).astype(np.float32)
     net = net_with(theta, h, B)
+    magpie.magpie_cnn_set_tensor_path(net, path)
     y = torch.empty((B, h, h, 2), dtype=torch.float32, device=DEV)
     magpie.magpie_cnn_forward(net, torch.from_numpy(x).to(DEV), y)
+    magpie.magpie_cnn_status(net)
     yg = y.cpu().numpy().astype(np.float64)
     sel = np.linspace(0, B - 1, check).astype(int)
     yo, _ = L.forward(theta, x[sel].astype(np.float64))
@@ -64,6 +70,10 @@ def test_backward_matches_oracle(h, B, seed, scale, tol):
     x = rng.normal(size=(B, h, h, 4)).astype(np.float32)
     dy = rng.normal(size=(B, h, h, 2)).astype(np.float32)
     net = net_with(theta, h, B)
+    # the cases were chosen where the register-fragment forward takes every
+    # BF16 rounding decision as the oracle does; this test is about the FP32
+    # backward pass, so it keeps that forward
+    magpie.magpie_cnn_set_tensor_path(net, 0)
     y = torch.empty((B, h, h, 2), dtype=torch.float32, device=DEV)
     magpie.magpie_cnn_forward(net, torch.from_numpy(x).to(DEV), y)
     g = torch.empty(L.param_count(), dtype=torch.float32, device=DEV)
@@ -79,6 +89,26 @@ def test_backward_matches_oracle(h, B, seed, scale, tol):
         assert rel(gg[o:o + n], go[o:o + n]) < tol, ("weights", ci, co)
         assert rel(gg[o + n:o + n + co], go[o + n:o + n + co]) < tol, ("biases", ci, co)
         o += n + co
+
+
+@pytest.mark.parametrize("h,B", [(32, 64), (32, 16), (16, 7), (64, 4)])
+def test_tensor_paths_agree(h, B):
+    """The tcgen05 convolutions (TMEM accumulators, split-K over 64-element
+    steps) and the mma.sync ones compute the same BF16 products with FP32
+    accumulation in another order: outputs agree to the BF16 rounding of the
+    activations, and no bounded wait ran out."""
+    theta = random_theta(L, 31).astype(np.float32)
+    x = torch.from_numpy(np.random.default_rng(32).normal(size=(B, h, h, 4)).astype(np.float32)).to(DEV)
+    out = []
+    for path in (1, 0):
+        net = net_with(theta, h, B)
+        magpie.magpie_cnn_set_tensor_path(net, path)
+        y = torch.empty((B, h, h, 2), dtype=torch.float32, device=DEV)
+        magpie.magpie_cnn_forward(net, x, y)
+        magpie.magpie_cnn_status(net)
+        out.append(y.cpu().numpy().astype(np.float64))
+        net.close()
+    assert rel(out[0], out[1]) < 2e-3, rel(out[0], out[1])
 
 
 def test_train_step_matches_oracle():
