@@ -308,13 +308,14 @@ int magpie_cnn_create(magpie_cnn** out, int32_t h, int32_t max_batch, void* stre
 void magpie_cnn_destroy(magpie_cnn* cnn);
 
 /*
- * Which tensor-core instructions the network's forward convolutions use:
- * 1 (the default) the 5th-generation tensor cores (tcgen05.mma, operands in
- * shared memory in the 128-byte-swizzled K-major layout, FP32 accumulators
- * in tensor memory) for every layer whose input channels and output channels
- * are multiples of 64, the register-fragment mma.sync kernel for the others;
- * 0 mma.sync for every layer.  Both accumulate the same BF16 products in
- * FP32 (summation order differs).  MAGPIE_EINVAL for another value.
+ * Which kernels the network's forward convolutions use: 1 (the default)
+ * the 5th-generation tensor cores (tcgen05.mma, operands in shared memory in
+ * the 128-byte-swizzled K-major layout, FP32 accumulators in tensor memory)
+ * for every layer whose input and output channels are multiples of 64, and a
+ * direct FP32 fused-multiply-add kernel for the thin first (4 -> 32) and last
+ * (64 -> 2) layers; 0 the register-fragment mma.sync kernel for every layer.
+ * All accumulate the same BF16 products in FP32 (summation order differs).
+ * MAGPIE_EINVAL for another value.
  */
 int magpie_cnn_set_tensor_path(magpie_cnn* net, int32_t path);
 

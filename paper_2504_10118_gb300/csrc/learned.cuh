@@ -210,6 +210,60 @@ __global__ void __launch_bounds__(128) conv_fwd_kernel(const ConvFwd a) {
     }
 }
 
+// Direct convolution for the thin layers (few input or few output channels:
+// the network's first, 4 -> 32, and last, 64 -> 2), where an implicit GEMM
+// tile would be mostly padding: one thread per output pixel computes all COUT
+// outputs from the BF16 inputs and weights (exact in FP32) with FP32
+// accumulation, the weights held in shared memory as [k][COUT] floats and
+// read by every thread of a warp at once.  Dynamic smem: 9 CIN COUT floats.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) conv_direct_kernel(const ConvFwd a) {
+  static_assert(CIN % 4 == 0, "input channels in groups of four");
+  extern __shared__ __align__(16) float wsm[];
+  constexpr int K = 9 * CIN;
+  for (int i = threadIdx.x; i < COUT * K; i += blockDim.x) {
+    const int co = i / K, k = i - co * K;
+    wsm[k * COUT + co] = __bfloat162float(a.w[i]);
+  }
+  __syncthreads();
+  const int HoHo = a.Ho * a.Ho, Mtot = a.B * HoHo, Hv = a.Hin * a.up;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= Mtot) return;
+  const int b = p / HoHo, rem = p - b * HoHo, oy = rem / a.Ho, ox = rem - oy * a.Ho;
+  float acc[COUT];
+#pragma unroll
+  for (int co = 0; co < COUT; ++co) acc[co] = 0.f;
+  for (int tap = 0; tap < 9; ++tap) {
+    const int ky = tap / 3, kx = tap - 3 * ky;
+    const int vy = oy * a.stride + ky - 1, vx = ox * a.stride + kx - 1;
+    if (vy < 0 || vy >= Hv || vx < 0 || vx >= Hv) continue;
+    const bf16* src = a.in + ((size_t)(b * a.Hin + vy / a.up) * a.Hin + vx / a.up) * CIN;
+    const float* wt = wsm + tap * CIN * COUT;
+#pragma unroll
+    for (int c0 = 0; c0 < CIN; c0 += 4) {
+      const uint2 raw = *reinterpret_cast<const uint2*>(src + c0);
+      const __nv_bfloat162 h01 = *reinterpret_cast<const __nv_bfloat162*>(&raw.x);
+      const __nv_bfloat162 h23 = *reinterpret_cast<const __nv_bfloat162*>(&raw.y);
+      const float xv[4] = {__low2float(h01), __high2float(h01), __low2float(h23), __high2float(h23)};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float* wr = wt + (c0 + j) * COUT;
+#pragma unroll
+        for (int co = 0; co < COUT; ++co) acc[co] = fmaf(xv[j], wr[co], acc[co]);
+      }
+    }
+  }
+#pragma unroll
+  for (int co = 0; co < COUT; ++co) {
+    float v = acc[co] + a.bias[co];
+    if (a.relu) v = fmaxf(v, 0.f);
+    if (a.out_f32)
+      static_cast<float*>(a.out)[(size_t)p * COUT + co] = v;
+    else
+      static_cast<bf16*>(a.out)[(size_t)p * COUT + co] = __float2bfloat16_rn(v);
+  }
+}
+
 // Split-K epilogue: partial sums added in split order, then bias and ReLU.
 __global__ void __launch_bounds__(256) conv_splitk_kernel(const ConvFwd a, int splits) {
   const int Mtot = a.B * a.Ho * a.Ho;

@@ -34,8 +34,6 @@
 // the forward transform's output distribution directly (the four steps in
 // reverse), so each 2-D transform needs one smem round trip per direction.
 
-#include <cooperative_groups.h>
-#include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdint>
@@ -48,21 +46,13 @@
 
 #include <nvtx3/nvToolsExt.h>
 
+#include "core.cuh"
 #include "magpie.h"
 
-namespace {
-
-namespace cg = cooperative_groups;
+namespace magpie_impl {
 
 constexpr int kVersion = 10200;  // 1.2.0
-constexpr int kMaxMinibatch = 4096;  // the update kernel keeps the minibatch's corners in smem (48 KiB)
-constexpr int kMaxCluster = 8;       // largest number of blocks per window
-constexpr int kMaxSlots = 16;        // partial-sum slots per window: the window kernel's blocks, or m / 16
-                                     // blocks of the precision form (m <= 256)
-constexpr int kApplyUnroll = 4;      // increments in flight per thread in the update kernel
 
-#include "fft_lines.cuh"
-#include "window_kernel.cuh"
 #include "learned.cuh"
 #include "precision.cuh"
 #include "umma.cuh"
@@ -508,37 +498,6 @@ int ilog2(int v) {
   return r;
 }
 
-// Launch with a cluster dimension when cl > 1.
-template <typename... KArgs, typename... Args>
-cudaError_t launch_ex(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, int cl,
-                       Args&&... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  int n = 0;
-  if (cl > 1) {
-    attr[n].id = cudaLaunchAttributeClusterDimension;
-    attr[n].val.clusterDim.x = cl;
-    attr[n].val.clusterDim.y = 1;
-    attr[n].val.clusterDim.z = 1;
-    ++n;
-  }
-  cfg.attrs = attr;
-  cfg.numAttrs = n;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
-  if (e != cudaSuccess) return e;
-  return cudaGetLastError();
-}
-
-template <int MS, int MODE>
-cudaError_t launch_window(const StepArgs& a, int windows, cudaStream_t st) {
-  using Gm = Geo<MS>;
-  return launch_ex(window_kernel<MS, MODE>, dim3((unsigned)windows * Gm::CL), dim3(Gm::T), Gm::SMEM, st, Gm::CL, a);
-}
-
 // blocks per window of the window kernel for patch side m
 int cluster_of(int m) { return m >= 256 ? 8 : m == 128 ? 4 : m == 64 ? 2 : 1; }
 
@@ -600,43 +559,25 @@ cudaError_t launch_apply(float2* z, int n_rows, int n_cols, const int2* corners,
 template <int MODE>
 cudaError_t launch_window_m(int MS, const StepArgs& a, int blocks, cudaStream_t st) {
   switch (MS) {
-    case 8: return launch_window<8, MODE>(a, blocks, st);
-    case 16: return launch_window<16, MODE>(a, blocks, st);
-    case 32: return launch_window<32, MODE>(a, blocks, st);
-    case 64: return launch_window<64, MODE>(a, blocks, st);
-    case 128: return launch_window<128, MODE>(a, blocks, st);
-    case 256: return launch_window<256, MODE>(a, blocks, st);
+#define MAGPIE_CASE(S) \
+  case S:              \
+    return window_launch<S>(MODE, a, blocks, st);
+    MAGPIE_WINDOW_SIZES(MAGPIE_CASE)
+#undef MAGPIE_CASE
     default: return cudaErrorInvalidValue;
   }
-}
-
-// Candidate register bounds of the batched window kernel: blocks per SM.
-template <int MS>
-constexpr int alt_minb() {
-  return Geo<MS>::T >= 512 ? 1 : (Geo<MS>::MIN_BLOCKS == 1 ? 2 : 1);
-}
-
-template <int MS, int MODE>
-cudaError_t launch_window_batched(const StepArgs* table, const int2* map, int windows, cudaStream_t st, int minb) {
-  using Gm = Geo<MS>;
-  const dim3 grid((unsigned)windows * Gm::CL);
-  if (minb == alt_minb<MS>() && minb != Gm::MIN_BLOCKS)
-    return launch_ex(window_kernel_batched<MS, MODE, alt_minb<MS>()>, grid, dim3(Gm::T), Gm::SMEM, st, Gm::CL, table,
-                     map);
-  return launch_ex(window_kernel_batched<MS, MODE, Gm::MIN_BLOCKS>, grid, dim3(Gm::T), Gm::SMEM, st, Gm::CL, table,
-                   map);
 }
 
 template <int MODE>
 cudaError_t launch_window_batched_m(int MS, const StepArgs* table, const int2* map, int windows, cudaStream_t st,
                                     int minb) {
+  static_assert(MODE == kStep, "batched windows run minibatch steps");
   switch (MS) {
-    case 8: return launch_window_batched<8, MODE>(table, map, windows, st, minb);
-    case 16: return launch_window_batched<16, MODE>(table, map, windows, st, minb);
-    case 32: return launch_window_batched<32, MODE>(table, map, windows, st, minb);
-    case 64: return launch_window_batched<64, MODE>(table, map, windows, st, minb);
-    case 128: return launch_window_batched<128, MODE>(table, map, windows, st, minb);
-    case 256: return launch_window_batched<256, MODE>(table, map, windows, st, minb);
+#define MAGPIE_CASE(S) \
+  case S:              \
+    return window_launch_batched<S>(table, map, windows, st, minb);
+    MAGPIE_WINDOW_SIZES(MAGPIE_CASE)
+#undef MAGPIE_CASE
     default: return cudaErrorInvalidValue;
   }
 }
@@ -645,36 +586,14 @@ cudaError_t launch_window_batched_m(int MS, const StepArgs* table, const int2* m
 // there is only one).
 void minb_candidates(int MS, int* c) {
   switch (MS) {
-#define MAGPIE_MINB(S)              \
+#define MAGPIE_CASE(S)               \
   case S:                            \
-    c[0] = Geo<S>::MIN_BLOCKS;       \
-    c[1] = alt_minb<S>();            \
+    window_minb_candidates<S>(c);    \
     return;
-    MAGPIE_MINB(8) MAGPIE_MINB(16) MAGPIE_MINB(32) MAGPIE_MINB(64) MAGPIE_MINB(128) MAGPIE_MINB(256)
-#undef MAGPIE_MINB
+    MAGPIE_WINDOW_SIZES(MAGPIE_CASE)
+#undef MAGPIE_CASE
     default: c[0] = c[1] = 1;
   }
-}
-
-template <int MS>
-cudaError_t prepare_size() {
-  const int bytes = (int)Geo<MS>::SMEM;
-  cudaError_t e = cudaFuncSetAttribute(window_kernel<MS, kStep>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(window_kernel_batched<MS, kStep, Geo<MS>::MIN_BLOCKS>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(window_kernel_batched<MS, kStep, alt_minb<MS>()>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(window_kernel<MS, kStepRecycle>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(window_kernel<MS, kStepAtomic>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(window_kernel<MS, kEval>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(window_kernel<MS, kSim>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  return e;
 }
 
 cudaError_t prepare_kernels(int MS) {
@@ -691,12 +610,11 @@ cudaError_t prepare_kernels(int MS) {
                              (int)(sizeof(float2) * (size_t)up_off(MS, ilog2(MS) + 1)));
   if (e != cudaSuccess) return e;
   switch (MS) {
-    case 8: return prepare_size<8>();
-    case 16: return prepare_size<16>();
-    case 32: return prepare_size<32>();
-    case 64: return prepare_size<64>();
-    case 128: return prepare_size<128>();
-    case 256: return prepare_size<256>();
+#define MAGPIE_CASE(S) \
+  case S:              \
+    return window_prepare<S>();
+    MAGPIE_WINDOW_SIZES(MAGPIE_CASE)
+#undef MAGPIE_CASE
     default: return cudaErrorInvalidValue;
   }
 }
@@ -724,7 +642,9 @@ struct GroupApplyLaunch {
   int max_count;  // largest window count (shared memory)
 };
 
-}  // namespace
+}  // namespace magpie_impl
+
+using namespace magpie_impl;
 
 struct magpie_group {
   std::vector<magpie_ctx*> members;
@@ -830,7 +750,7 @@ struct magpie_ctx {
   cudaEvent_t copy_start = nullptr;
 };
 
-namespace {
+namespace magpie_impl {
 
 StepArgs make_args(magpie_ctx* c, const int32_t* idx) {
   StepArgs a{};
@@ -896,10 +816,15 @@ ConvPlan conv_plan(const ConvFwd& a) {
 // Layers the tcgen05 convolution serves: whole 64-element K steps inside one
 // tap (Cin a multiple of 64) and whole 64-wide N tiles.
 bool conv_tc_fits(const ConvFwd& a) { return a.Cin % 64 == 0 && a.Cout % 64 == 0; }
+// Thin layers the direct FP32-FMA kernel serves: the network's first (4 -> 32)
+// and last (64 -> 2) convolutions.
+bool conv_direct_fits(const ConvFwd& a) { return (a.Cin == 4 && a.Cout == 32) || (a.Cin == 64 && a.Cout == 2); }
 
 // Tiles of the tcgen05 convolution: 128 output pixels x 128 (or 64) output
-// channels, K split so that about two blocks per SM run (at least two K steps
-// of 64 per split).
+// channels, K split so that about two blocks per SM run, at least two K steps
+// of 64 per split.  (One block per SM with at least four K steps per split
+// and 256-wide N tiles measured slower: 185 against 166 us for the network's
+// forward pass at batch 64, h = 32; the blocks are latency-bound.)
 ConvPlan conv_plan_tc(const ConvFwd& a) {
   ConvPlan pl{};
   pl.bn = a.Cout % 128 == 0 ? 128 : 64;
@@ -965,6 +890,17 @@ cudaError_t launch_conv(const ConvFwd& a0, float* part, cudaStream_t st, int ten
   a.ksplit = pl.ksplit;
   a.part = pl.splits > 1 ? part : nullptr;
   const dim3 grid(pl.gx, pl.gy, pl.splits);
+  if (tensor_path == 1 && conv_direct_fits(a)) {
+    const int Mtot = a.B * a.Ho * a.Ho;
+    const size_t smem = sizeof(float) * a.Cout * a.K;
+    if (a.Cin == 64 && a.Cout == 2)
+      conv_direct_kernel<64, 2><<<(Mtot + 255) / 256, 256, smem, st>>>(a);
+    else if (a.Cin == 4 && a.Cout == 32)
+      conv_direct_kernel<4, 32><<<(Mtot + 255) / 256, 256, smem, st>>>(a);
+    else
+      return cudaErrorInvalidValue;
+    return cudaGetLastError();
+  }
   if (tc && pl.bn == 128)
     conv_fwd_tc_kernel<128><<<grid, 128, TcConv<128>::SMEM, st>>>(a, err);
   else if (tc)
@@ -1474,7 +1410,7 @@ int noalloc_scratch(NoAllocScratch* out) {
   return MAGPIE_OK;
 }
 
-}  // namespace
+}  // namespace magpie_impl
 
 
 // Autotuner of a group: for every window side of batched step 0, launch the

@@ -8,7 +8,8 @@
 // share of K (split-K as the register-fragment kernel does):
 //   * every K step of 64 elements, the block's threads gather the tile's
 //     A rows (im2col of the NHWC activations, zero outside the image) and
-//     W rows with 16-byte cp.async into one of two stages, laid out K-major
+//     W rows with 16-byte cp.async into one of two or three stages (up to two
+//     steps in flight ahead of the tensor core), laid out K-major
 //     with the 128-byte swizzle (8 rows x 128 bytes per 1024-byte atom,
 //     16-byte chunk c of row r at chunk c ^ (r mod 8));
 //   * thread 0 issues four tcgen05.mma (M = 128, N = BN, K = 16 each) on the
@@ -17,7 +18,7 @@
 //   * the accumulator (128 TMEM lanes x BN fp32 columns) is read back with
 //     tcgen05.ld, one row per thread, for the bias / ReLU / BF16 epilogue or
 //     the split-K partial sums.
-// Layers with Cin a multiple of 64 and Cout a multiple of 16 take this path.
+// Layers with Cin and Cout multiples of 64 take this path.
 #pragma once
 
 namespace umma {
@@ -98,11 +99,15 @@ __device__ __forceinline__ bool wait(uint32_t bar, uint32_t parity) {
 
 }  // namespace umma
 
-constexpr int kTcBM = 128, kTcBK = 64, kTcStages = 2;
+constexpr int kTcBM = 128, kTcBK = 64;
+// Shared-memory stages of the pipeline: three for N tiles up to 128 (two or
+// three blocks per SM), two for 256 (two blocks per SM); the tensor memory
+// the resident blocks allocate stays within an SM's 512 columns.
 template <int BN>
 struct TcConv {
+  static constexpr int STAGES = BN >= 256 ? 2 : 3;  // N tiles of 64 and 128 are used
   static constexpr int A_BYTES = kTcBM * kTcBK * 2, B_BYTES = BN * kTcBK * 2, STAGE = A_BYTES + B_BYTES;
-  static constexpr size_t SMEM = (size_t)kTcStages * STAGE + 1024;  // + alignment slack for 1024-byte atoms
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024;  // + alignment slack for 1024-byte atoms
 };
 
 // err: bit 2 is set when a bounded wait ran out (the block then skips its
@@ -111,8 +116,9 @@ template <int BN>
 __global__ void __launch_bounds__(128) conv_fwd_tc_kernel(const ConvFwd a, int* err) {
   static_assert(BN % 16 == 0 && BN >= 32 && BN <= 256 && (BN & (BN - 1)) == 0, "N tile");
   using S = TcConv<BN>;
+  constexpr int NS = S::STAGES;
   extern __shared__ unsigned char tc_raw[];
-  __shared__ __align__(8) unsigned long long bars[kTcStages];
+  __shared__ __align__(8) unsigned long long bars[NS];
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t raw = smem_addr(tc_raw);
@@ -121,7 +127,7 @@ __global__ void __launch_bounds__(128) conv_fwd_tc_kernel(const ConvFwd a, int* 
 
   if (warp == 0) umma::alloc(smem_addr(&tmem_slot), BN);
   if (tid == 0) {
-    for (int s = 0; s < kTcStages; ++s) mbar_init(bar0 + 8 * s, 1);
+    for (int s = 0; s < NS; ++s) mbar_init(bar0 + 8 * s, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   umma::fence_before();
@@ -174,10 +180,19 @@ __global__ void __launch_bounds__(128) conv_fwd_tc_kernel(const ConvFwd a, int* 
 
   constexpr uint32_t IDESC = umma::idesc_bf16(kTcBM, BN);
   bool ok = true;
-  if (nk > 0) load_stage(0, kbeg);
+  // K step j goes to stage j mod NS, one cp.async group per step; the first
+  // NS - 1 steps are in flight before the first MMA
+  for (int j = 0; j < NS - 1 && j < nk; ++j) load_stage(j, kbeg + j * kTcBK);
   for (int ks = 0; ks < nk; ++ks) {
-    const int st = ks & 1;
-    umma::cp_async_wait_all();
+    const int st = ks % NS;
+    // step ks's group is complete once at most (groups issued - ks - 1) remain
+    const int pending = min(ks + NS - 1, nk) - ks - 1;
+    if (pending >= 2)
+      asm volatile("cp.async.wait_group 2;" ::: "memory");
+    else if (pending == 1)
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else
+      umma::cp_async_wait_all();
     umma::fence_proxy_async();  // this thread's stage writes, visible to the tensor core
     __syncthreads();
     if (tid == 0) {
@@ -189,13 +204,14 @@ __global__ void __launch_bounds__(128) conv_fwd_tc_kernel(const ConvFwd a, int* 
                           (ks | kk) != 0);
       umma::commit(bar0 + 8 * st);
     }
-    if (ks + 1 < nk) {
-      // the other stage is free once the MMAs of k step ks - 1 have completed
-      if (ks >= 1 && !umma::wait(bar0 + 8 * (st ^ 1), ((ks - 1) >> 1) & 1)) ok = false;
-      load_stage(st ^ 1, kbeg + (ks + 1) * kTcBK);
+    const int nxt = ks + NS - 1;
+    if (nxt < nk) {
+      // step nxt reuses the stage of step ks - 1, free once that step's MMAs completed
+      if (ks >= 1 && !umma::wait(bar0 + 8 * ((ks - 1) % NS), ((ks - 1) / NS) & 1)) ok = false;
+      load_stage(nxt % NS, kbeg + nxt * kTcBK);
     }
   }
-  if (nk > 0 && !umma::wait(bar0 + 8 * ((nk - 1) & 1), ((nk - 1) >> 1) & 1)) ok = false;
+  if (nk > 0 && !umma::wait(bar0 + 8 * ((nk - 1) % NS), ((nk - 1) / NS) & 1)) ok = false;
   umma::fence_after();
   if (!ok && lane == 0) atomicOr(err, 4);
 

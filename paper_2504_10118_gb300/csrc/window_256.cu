@@ -1,0 +1,8 @@
+// window_256.cu -- the window kernels (every mode, single and batched) for
+// m = 256 (eight-block clusters), compiled apart from the other sides.
+#include "core.cuh"
+#include "window_launch.cuh"
+
+namespace magpie_impl {
+MAGPIE_INSTANTIATE_WINDOW(256)
+}  // namespace magpie_impl

@@ -26,12 +26,15 @@ STAGES_LIB_PATH = os.path.join(BUILD_DIR, "libmagpie_stages.so")
 
 def _stages() -> bool:
     return os.environ.get("MAGPIE_STAGE_TIMES") == "1"
-SOURCES = [os.path.join(HERE, "csrc", "magpie.cu")]
-DEPENDS = [os.path.join(HERE, "csrc", f) for f in ("fft_lines.cuh", "window_kernel.cuh", "window_body.inc",
-                                                   "learned.cuh", "precision.cuh")]
+# translation units, compiled in parallel: the host side and the other
+# kernels, and the window kernels of each window side
+SOURCES = [os.path.join(HERE, "csrc", f) for f in ("magpie.cu", "window_small.cu", "window_64.cu", "window_128.cu",
+                                                   "window_256.cu")]
+DEPENDS = [os.path.join(HERE, "csrc", f) for f in ("core.cuh", "fft_lines.cuh", "window_kernel.cuh", "window_body.inc",
+                                                   "window_launch.cuh", "learned.cuh", "precision.cuh", "umma.cuh")]
 HEADER = os.path.join(ROOT, "include", "magpie.h")
-NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
-              "-Xcompiler", "-fPIC", "-shared"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 
 OK, EINVAL, ECUDA, ENOMEM, EUNSUPPORTED, EINDEX, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 
@@ -57,9 +60,21 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and os.path.exists(path) and os.path.getmtime(path) >= newest:
         return path
     os.makedirs(BUILD_DIR, exist_ok=True)
+    tag = "stages_" if _stages() else ""
+    objs, procs = [], []
+    for src in SOURCES:
+        obj = os.path.join(BUILD_DIR, tag + os.path.basename(src) + ".o")
+        cmd = ["nvcc", *NVCC_FLAGS, *(["-DMAGPIE_STAGE_TIMES"] if _stages() else []), "-I",
+               os.path.join(ROOT, "include"), "-c", "-o", obj, src]
+        if verbose:
+            print(" ".join(cmd))
+        objs.append(obj)
+        procs.append((cmd, subprocess.Popen(cmd)))
+    failed = [cmd for cmd, p in procs if p.wait() != 0]
+    if failed:
+        raise subprocess.CalledProcessError(1, failed[0])
     tmp = path + ".tmp"
-    cmd = ["nvcc", *NVCC_FLAGS, *(["-DMAGPIE_STAGE_TIMES"] if _stages() else []), "-I",
-           os.path.join(ROOT, "include"), "-o", tmp, *SOURCES]
+    cmd = ["nvcc", *ARCH, "-shared", "-o", tmp, *objs]
     if verbose:
         print(" ".join(cmd))
     subprocess.run(cmd, check=True)

@@ -298,15 +298,18 @@ def test_training_lowers_the_loss():
     assert losses[-1] < 0.7 * losses[0]
 
 
-def test_trained_network_gain():
-    """What the trained network gains over the method without it, on the mid
-    workload's sizes (n = 512, m = 128, 900 windows, 3 levels, 10^6 photons):
-    trained on the plain solver's trajectories of three other seeded objects,
-    then 40 sweeps of the held-out problem with and without it from z = 1.
-    Reported: proposals kept, objective and NRMSE against the ground truth.
-    Required: some proposals pass the surrogate test, and the learned run ends
-    within 5% of the plain one (the test keeps a proposal only where the
-    window's surrogate is no worse than the plain V-cycle's)."""
+def test_trained_network_effect():
+    """What the trained network changes against the method without it, on the
+    mid workload's sizes (n = 512, m = 128, 900 windows, 3 levels, 10^6
+    photons): trained on the plain solver's trajectories of three other seeded
+    objects, then 40 sweeps of the held-out problem with and without it from
+    z = 1.  Reported: proposals kept, objective and NRMSE against the ground
+    truth.  No gain has been measured: about 2% of the proposals pass the
+    surrogate test and the two runs end within a few percent of each other
+    (the design notes record the runs).  Checked: the acceptance mechanics
+    (every window proposes, some proposals are kept) and that the learned run,
+    which keeps a proposal only where the window's surrogate is no worse than
+    the plain V-cycle's, ends within 5% of the plain one."""
     w = synth.WORKLOADS["mid"]
     h = learned.coarse_side(w.m, w.levels)
     data = learned.generate(w, seeds=[11, 12, 13], stages=[0, 1, 2, 3, 4, 6, 8, 12, 16, 24], per_stage=100,
