@@ -450,6 +450,13 @@ int magpie_step_noalloc(void* object, int32_t n_rows, int32_t n_cols, const void
                         int32_t count, int32_t levels, float alpha, double* phi, double* gnorm, void* stream);
 
 /*
+ * Thread blocks (one thread-block cluster) per window of the window kernel
+ * for window side m, the second dimension of magpie_stage_times' output;
+ * 0 for an m without a kernel.
+ */
+int32_t magpie_window_blocks(int32_t m);
+
+/*
  * Measurement helper, not part of the method: the FP32 fused multiply-add
  * rate of the current device, the peak that bounds the ALU-bound window
  * kernel.  Launches 8 blocks of 256 threads per SM, each thread running 8

@@ -499,7 +499,16 @@ int ilog2(int v) {
 }
 
 // blocks per window of the window kernel for patch side m
-int cluster_of(int m) { return m >= 256 ? 8 : m == 128 ? 4 : m == 64 ? 2 : 1; }
+int cluster_of(int m) {
+  switch (m) {
+#define MAGPIE_CASE(S) \
+  case S:              \
+    return Geo<S>::CL;
+    MAGPIE_WINDOW_SIZES(MAGPIE_CASE)
+#undef MAGPIE_CASE
+    default: return 1;
+  }
+}
 
 // The per-level probe factors of probe Q (float64 arithmetic) into pyr.
 // mx: one 8-byte scratch word; qtop/utop: float64 scratch of 2 MS^2 entries.
@@ -2351,6 +2360,8 @@ int magpie_sweep_host_async(magpie_ctx* c, const int32_t* order, const float* in
   c->next_buf = b ^ 1;
   return MAGPIE_OK;
 }
+
+int32_t magpie_window_blocks(int32_t m) { return supported_m(m) ? cluster_of(m) : 0; }
 
 int magpie_fp32_fma_rate(int32_t iters, double* tflops, double* ms, void* stream) {
   if (!tflops || iters < 1) return fail(MAGPIE_EINVAL, "need tflops and iters >= 1");

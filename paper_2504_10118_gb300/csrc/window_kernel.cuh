@@ -145,7 +145,7 @@ __device__ __forceinline__ void vcycle(const float2* Y, float2* lvl, const float
                                        int tid) {
   using Gm = Geo<MS>;
   constexpr int SLAB = Gm::SLAB, T = Gm::T, CL = Gm::CL, H = 1 << TT, NS = MS / H, SPAR = T / SLAB;
-  constexpr int LLOC = (SLAB >= 32) ? 5 : (SLAB == 16 ? 4 : 3);  // log2(SLAB)
+  constexpr int LLOC = SLAB >= 64 ? 6 : SLAB == 32 ? 5 : (SLAB == 16 ? 4 : 3);  // log2(SLAB)
   static_assert((1 << LLOC) == SLAB, "slab levels");
   const int gam = tid % SLAB, s0 = tid / SLAB;
   const int cgl = q * SLAB + gam;  // column in the window

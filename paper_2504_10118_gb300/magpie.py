@@ -138,6 +138,7 @@ def lib() -> ctypes.CDLL:
             "magpie_dft2_tc": (ctypes.c_int, [vp, vp, i32, i32, i32, vp]),
             "magpie_fp32_fma_rate": (ctypes.c_int, [i32, dp, dp, vp]),
             "magpie_stage_times": (ctypes.c_int, [vp, vp, i32, vp, ctypes.c_int64]),
+            "magpie_window_blocks": (i32, [i32]),
             "magpie_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             "magpie_last_error": (ctypes.c_char_p, []),
             "magpie_version": (ctypes.c_int, []),
@@ -500,6 +501,11 @@ def magpie_fp32_fma_rate(iters: int = 4096):
     tf, ms = ctypes.c_double(), ctypes.c_double()
     _check(lib().magpie_fp32_fma_rate(int(iters), ctypes.byref(tf), ctypes.byref(ms), _stream()))
     return tf.value, ms.value
+
+
+def blocks_per_window(m: int) -> int:
+    """Thread blocks per window of the window kernel for window side m."""
+    return int(lib().magpie_window_blocks(int(m)))
 
 
 def magpie_stage_times(ctx: Context, idx: torch.Tensor, blocks_per_window: int) -> torch.Tensor:

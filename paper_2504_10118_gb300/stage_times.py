@@ -45,7 +45,7 @@ def main(argv=None) -> int:
     det = 1 if args.update == "ordered" else 0
     ctx = magpie.magpie_create(magpie.magpie_params_of(w.n, w.n, w.m, w.n_pos, w.levels, w.minibatch, w.alpha,
                                                        deterministic=det), z, Qt, post, d)
-    cl = {64: 2, 128: 4, 256: 8}.get(w.m, 1)
+    cl = magpie.blocks_per_window(w.m)
     order = synth.make_order(w.n_pos, 0)
     rows = []
     for s in range(3 + args.steps):
