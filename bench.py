@@ -388,6 +388,7 @@ def batched_measure(dev, magpie, warmup: int, steps: int, pg=None, clocks=None):
     steps_max = max(math.ceil(w.n_pos / w.minibatch) for w in ws)
     launches = sum(len({w.m for w in ws if math.ceil(w.n_pos / w.minibatch) > t}) + 1 for t in range(steps_max))
     tuning = magpie.magpie_group_tuning(group)
+    shape, shapes = magpie.magpie_group_apply_tuning(group)
     group.close()
     for c in ctxs:
         c.close()
@@ -398,7 +399,10 @@ def batched_measure(dev, magpie, warmup: int, steps: int, pg=None, clocks=None):
                       "levels": 3, "minibatch": 64, "update": "ordered (context groups)",
                       "data": "photon noise drawn on the device"},
            "gpu_launches_per_step": launches,
-           "autotuner": {str(m): {"choice": v[0], "candidates": v[1]} for m, v in tuning.items()}}
+           "autotuner": {"window_register_bound": {str(m): {"blocks_per_sm": v[0], "ms_per_launch": list(v[1])}
+                                                   for m, v in tuning.items()},
+                         "update_tile": {"choice": f"{shapes[shape][0]}x{shapes[shape][1]}",
+                                         "ms_per_launch": {f"{w}x{h}": ms for w, h, ms in shapes}}}}
     flops = sum(w.n_pos * flops_per_window(w.m) for w in ws) * steps
     return rec, total_ms, launches, flops
 

@@ -120,9 +120,11 @@ typedef struct {
  *                 context stores the amplitudes sqrt(d_k) in its own buffer.
  *   stream      : cudaStream_t (as void*) on which every call is ordered.
  * The context owns its workspaces: amplitudes (4 N m^2 bytes), the per-level
- * probe factors, the minibatch increment buffer (8 B m^2 bytes) and small
- * per-window arrays.  Returns MAGPIE_EINVAL for bad sizes, NULL pointers or
- * out-of-range positions, MAGPIE_EUNSUPPORTED for an m without a kernel.
+ * probe factors, the minibatch increment buffer (8 B m^2 bytes), with
+ * deterministic = 0 the object-sized accumulators (16 n_rows n_cols bytes),
+ * and small per-window arrays.  Returns MAGPIE_EINVAL for bad sizes, NULL
+ * pointers, out-of-range positions or a deterministic value other than 0 or
+ * 1, MAGPIE_EUNSUPPORTED for an m without a kernel.
  */
 int magpie_create(magpie_ctx** out, const magpie_params* params, void* object,
                   const void* probe, const int32_t* positions,
@@ -270,6 +272,21 @@ void magpie_group_destroy(magpie_group* group);
  */
 int magpie_group_tuning(magpie_group* group, int32_t* minb, float* ms);
 int magpie_group_set_minb(magpie_group* group, int32_t m, int32_t minb);
+
+/*
+ * The autotuner's second dimension: the tile shape of the group's update
+ * kernel, one of 16 x 16, 32 x 8 and 32 x 32 pixels per 256-thread block (one,
+ * one and four pixels per thread).  magpie_group_create times each on the
+ * first batched step with the members' objects replaced by scratch copies
+ * (the members' objects are not touched) and uses the fastest.  Every shape
+ * sums each pixel's windows in minibatch order, so the results are bitwise
+ * identical.  magpie_group_apply_tuning reports the shape in use (*shape, an
+ * index 0..2), the three shapes (tile_w[3], tile_h[3]) and their measured ms
+ * per launch (ms[3]); HOST pointers.  magpie_group_set_apply_shape forces
+ * one (MAGPIE_EINVAL outside 0..2).
+ */
+int magpie_group_apply_tuning(magpie_group* group, int32_t* shape, int32_t* tile_w, int32_t* tile_h, float* ms);
+int magpie_group_set_apply_shape(magpie_group* group, int32_t shape);
 
 /*
  * Learned coarse-level correction.  The paper has no network: its Algorithm

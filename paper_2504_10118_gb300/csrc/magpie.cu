@@ -65,8 +65,15 @@ constexpr int kVersion = 10200;  // 1.2.0
 // walks that short list four entries at a time with predicated loads, so
 // several increments are in flight per thread.  Block (0, 0) also turns the
 // window kernel's block partials into Phi_k and ||grad Phi_k||.
-// Dynamic smem: count int2 corners + count ints.
+// Dynamic smem: count int2 corners + count ints.  The tile is TW x TH pixels
+// (16 x 16 for single problems; the group autotuner also tries 32 x 8 and
+// 32 x 32, four pixels per thread); every shape sums each pixel's windows in
+// minibatch order, so all give bitwise equal objects.
 constexpr int kApplyTile = 16;
+struct ApplyShape {
+  int tw, th;
+};
+constexpr ApplyShape kApplyShapes[3] = {{16, 16}, {32, 8}, {32, 32}};
 struct ApplyArgs {
   float2* z;               // object [n_rows][n_cols]
   int n_rows, n_cols;
@@ -80,11 +87,14 @@ struct ApplyArgs {
   int slots;               // partial-sum slots per window
   double* phi_pos;         // per-window Phi_k
   double* gn_pos;          // per-window ||grad Phi_k||
-  int tiles_x;             // tiles per object row
+  int tiles_x, tiles_y;    // tiles per object row and column
   int block0;              // batched launches: first block of this problem
 };
 
+template <int TW, int TH>
 __device__ __forceinline__ void apply_body(const ApplyArgs& P, const int tx, const int ty) {
+  static_assert((TW * TH) % 256 == 0 && 256 % TW == 0, "256 threads cover the tile in whole rows");
+  constexpr int PPT = TW * TH / 256, RS = 256 / TW;  // pixels per thread, rows per pass
   extern __shared__ int2 corner[];
   const int count = P.count, MS = P.MS;
   int* list = reinterpret_cast<int*>(corner + count);
@@ -103,7 +113,7 @@ __device__ __forceinline__ void apply_body(const ApplyArgs& P, const int tx, con
       P.gn_pos[k] = sqrt(g);
     }
   }
-  const int R0 = ty * kApplyTile, C0 = tx * kApplyTile;
+  const int R0 = ty * TH, C0 = tx * TW;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   // windows meeting this tile, listed in minibatch order: every warp takes
   // 32 consecutive windows per round, ballots, and the rounds are stitched
@@ -115,7 +125,7 @@ __device__ __forceinline__ void apply_body(const ApplyArgs& P, const int tx, con
     if (b < count) {
       const int2 q = P.corners[b];
       corner[b] = q;
-      hit = q.x < R0 + kApplyTile && q.x + MS > R0 && q.y < C0 + kApplyTile && q.y + MS > C0;
+      hit = q.x < R0 + TH && q.x + MS > R0 && q.y < C0 + TW && q.y + MS > C0;
     }
     const unsigned mask = __ballot_sync(0xffffffffu, hit);
     if (lane == 0) warp_hits[wid] = __popc(mask);
@@ -131,45 +141,51 @@ __device__ __forceinline__ void apply_body(const ApplyArgs& P, const int tx, con
   if (threadIdx.x == 0) n_list = base;
   __syncthreads();
   const int nl = n_list;
-  const int r = R0 + (threadIdx.x >> 4), c = C0 + (threadIdx.x & 15);
-  if (r >= P.n_rows || c >= P.n_cols) return;
   const size_t M = (size_t)MS * MS;
-  float nx = 0.f, ny = 0.f, d = 0.f;
-  for (int j0 = 0; j0 < nl; j0 += kApplyUnroll) {
-    float2 v[kApplyUnroll];
-    float wv[kApplyUnroll];
+#pragma unroll 1
+  for (int pp = 0; pp < PPT; ++pp) {
+    const int r = R0 + (int)(threadIdx.x / TW) + pp * RS, c = C0 + (int)(threadIdx.x % TW);
+    if (r >= P.n_rows || c >= P.n_cols) continue;
+    float nx = 0.f, ny = 0.f, d = 0.f;
+    for (int j0 = 0; j0 < nl; j0 += kApplyUnroll) {
+      float2 v[kApplyUnroll];
+      float wv[kApplyUnroll];
 #pragma unroll
-    for (int u = 0; u < kApplyUnroll; ++u) {
-      const int j = j0 + u;
-      const int b = j < nl ? list[j] : 0;
-      const int2 q = corner[b];
-      const int dr = r - q.x, dc = c - q.y;
-      const bool in = j < nl && (unsigned)dr < (unsigned)MS && (unsigned)dc < (unsigned)MS;
-      const int o = in ? dr * MS + dc : 0;
-      v[u] = in ? P.contrib[(size_t)b * M + o] : make_float2(0.f, 0.f);
-      wv[u] = in ? __ldg(&P.w0[o]) : 0.f;
-    }
+      for (int u = 0; u < kApplyUnroll; ++u) {
+        const int j = j0 + u;
+        const int b = j < nl ? list[j] : 0;
+        const int2 q = corner[b];
+        const int dr = r - q.x, dc = c - q.y;
+        const bool in = j < nl && (unsigned)dr < (unsigned)MS && (unsigned)dc < (unsigned)MS;
+        const int o = in ? dr * MS + dc : 0;
+        v[u] = in ? P.contrib[(size_t)b * M + o] : make_float2(0.f, 0.f);
+        wv[u] = in ? __ldg(&P.w0[o]) : 0.f;
+      }
 #pragma unroll
-    for (int u = 0; u < kApplyUnroll; ++u) {
-      nx += v[u].x;
-      ny += v[u].y;
-      d += wv[u];
+      for (int u = 0; u < kApplyUnroll; ++u) {
+        nx += v[u].x;
+        ny += v[u].y;
+        d += wv[u];
+      }
     }
-  }
-  if (d > 0.f) {
-    const size_t p = (size_t)r * P.n_cols + c;
-    float2 zz = P.z[p];
-    zz.x += nx / d;
-    zz.y += ny / d;
-    P.z[p] = zz;
+    if (d > 0.f) {
+      const size_t p = (size_t)r * P.n_cols + c;
+      float2 zz = P.z[p];
+      zz.x += nx / d;
+      zz.y += ny / d;
+      P.z[p] = zz;
+    }
   }
 }
 
 // One problem: a 2-D grid of tiles.
-__global__ void __launch_bounds__(256) apply_kernel(ApplyArgs P) { apply_body(P, blockIdx.x, blockIdx.y); }
+__global__ void __launch_bounds__(256) apply_kernel(ApplyArgs P) {
+  apply_body<kApplyTile, kApplyTile>(P, blockIdx.x, blockIdx.y);
+}
 
 // Several problems in one launch (1-D grid): problem i owns blocks
 // table[i].block0 .. table[i + 1].block0 - 1.
+template <int TW, int TH>
 __global__ void __launch_bounds__(256) apply_kernel_batched(const ApplyArgs* __restrict__ table, int n) {
   int lo = 0, hi = n - 1;
   while (lo < hi) {  // last problem whose first block is <= blockIdx.x
@@ -181,15 +197,18 @@ __global__ void __launch_bounds__(256) apply_kernel_batched(const ApplyArgs* __r
   }
   const ApplyArgs& P = table[lo];
   const int t = (int)blockIdx.x - P.block0;
-  apply_body(P, t % P.tiles_x, t / P.tiles_x);
+  apply_body<TW, TH>(P, t % P.tiles_x, t / P.tiles_x);
 }
+
+constexpr int kAccumPix = 4;  // pixels per thread of the atomic update kernel
 
 // Atomic update (deterministic = 0): the window kernel has added, pixel by
 // pixel, sum_k w . Delta_k (x, y) and sum_k w (z) into object-sized
 // accumulators; every pixel with a positive weight moves by their ratio, the
 // same rule as the ordered update, and every touched accumulator is cleared
-// for the next step.  One pixel per thread, 16-byte loads.  Block 0 also
-// turns the window kernel's block partials into Phi_k and ||grad Phi_k||.
+// for the next step.  Four pixels per thread, all their loads in flight at
+// once.  Block 0 also turns the window kernel's block partials into Phi_k
+// and ||grad Phi_k||.
 __global__ void __launch_bounds__(256) accum_apply_kernel(float2* __restrict__ z, float4* __restrict__ acc,
                                                           size_t npix, const int32_t* __restrict__ idx, int count,
                                                           int n_pos, const double* __restrict__ part, int slots,
@@ -207,15 +226,25 @@ __global__ void __launch_bounds__(256) accum_apply_kernel(float2* __restrict__ z
       gn_pos[k] = sqrt(g);
     }
   }
-  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < npix; p += (size_t)gridDim.x * blockDim.x) {
-    const float4 a = __ldcg(&acc[p]);
-    if (a.z > 0.f) {
-      float2 zz = z[p];
-      zz.x += a.x / a.z;
-      zz.y += a.y / a.z;
-      z[p] = zz;
+  // kAccumPix pixels per thread, strided by the grid so that each warp's
+  // loads stay coalesced, all loads issued before any is used
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t p0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p0 < npix; p0 += kAccumPix * stride) {
+    float4 a[kAccumPix];
+    float2 zz[kAccumPix];
+#pragma unroll
+    for (int u = 0; u < kAccumPix; ++u) {
+      const size_t p = p0 + u * stride;
+      a[u] = p < npix ? __ldcg(&acc[p]) : make_float4(0.f, 0.f, 0.f, 0.f);
+      zz[u] = p < npix ? z[p] : make_float2(0.f, 0.f);  // unconditional: no second round trip
     }
-    if (a.x != 0.f || a.y != 0.f || a.z != 0.f) acc[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < kAccumPix; ++u) {
+      const size_t p = p0 + u * stride;
+      if (p >= npix) continue;
+      if (a[u].z > 0.f) z[p] = make_float2(zz[u].x + a[u].x / a[u].z, zz[u].y + a[u].y / a[u].z);
+      if (a[u].x != 0.f || a[u].y != 0.f || a[u].z != 0.f) acc[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
   }
 }
 
@@ -532,7 +561,7 @@ cudaError_t enqueue_pyramid(const float2* Q, int MS, int L, float alpha, unsigne
 
 ApplyArgs apply_args(float2* z, int n_rows, int n_cols, const int2* corners, const int32_t* idx, int count, int n_pos,
                      const float2* contrib, const float* w0, int MS, const double* part, double* phi_pos,
-                     double* gn_pos, int slots = 0) {
+                     double* gn_pos, int slots = 0, ApplyShape shape = kApplyShapes[0]) {
   ApplyArgs P{};
   P.z = z;
   P.n_rows = n_rows;
@@ -548,12 +577,13 @@ ApplyArgs apply_args(float2* z, int n_rows, int n_cols, const int2* corners, con
   P.slots = slots ? slots : cluster_of(MS);  // default: one per block of the window kernel
   P.phi_pos = phi_pos;
   P.gn_pos = gn_pos;
-  P.tiles_x = (n_cols + kApplyTile - 1) / kApplyTile;
+  P.tiles_x = (n_cols + shape.tw - 1) / shape.tw;
+  P.tiles_y = (n_rows + shape.th - 1) / shape.th;
   P.block0 = 0;
   return P;
 }
 
-int apply_tiles(const ApplyArgs& P) { return P.tiles_x * ((P.n_rows + kApplyTile - 1) / kApplyTile); }
+int apply_tiles(const ApplyArgs& P) { return P.tiles_x * P.tiles_y; }
 
 cudaError_t launch_apply(float2* z, int n_rows, int n_cols, const int2* corners, const int32_t* idx, int count,
                          int n_pos, const float2* contrib, const float* w0, int MS, const double* part,
@@ -609,7 +639,13 @@ cudaError_t prepare_kernels(int MS) {
   cudaError_t e = cudaFuncSetAttribute(apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)((sizeof(int2) + sizeof(int)) * kMaxMinibatch));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(apply_kernel_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(apply_kernel_batched<16, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((sizeof(int2) + sizeof(int)) * kMaxMinibatch));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(apply_kernel_batched<32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((sizeof(int2) + sizeof(int)) * kMaxMinibatch));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(apply_kernel_batched<32, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)((sizeof(int2) + sizeof(int)) * kMaxMinibatch));
   if (e == cudaSuccess && MS <= 128)
     e = cudaFuncSetAttribute(vcycle_up_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -661,15 +697,20 @@ struct magpie_group {
   cudaStream_t cap_stream = nullptr;
   StepArgs* table = nullptr;    // one entry per (batched step, member)
   int2* map = nullptr;          // cluster -> (table entry, window slot)
-  ApplyArgs* atable = nullptr;  // one entry per (batched step, member)
+  ApplyArgs* atable[3] = {};    // per apply tile shape: one entry per (batched step, member)
   std::vector<std::vector<GroupWindowLaunch>> wl;  // per batched step
-  std::vector<GroupApplyLaunch> al;                // per batched step
+  std::vector<GroupApplyLaunch> al[3];             // per apply tile shape, per batched step
+  std::vector<ApplyArgs> atable_host[3];           // host copies (the autotuner's scratch tables)
   cudaGraphExec_t graph = nullptr;
   // autotuner: register bound (blocks per SM) of the batched window kernel
   // per window side m = 8 << i, and the measured ms per launch of batched
   // step 0 for the two candidates (0 where not measured)
   int minb[6] = {0, 0, 0, 0, 0, 0};
   float tune_ms[6][2] = {};
+  // autotuner: tile shape of the update kernel (index into kApplyShapes) and
+  // the measured ms per launch of batched step 0 for each shape
+  int apply_shape = 0;
+  float apply_ms[3] = {};
 };
 
 // The network of the learned coarse correction with its training state.
@@ -1213,7 +1254,7 @@ int enqueue_step(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st, 
   if (ev) CUDA_TRY(cudaEventRecord(ev[2], st));
   if (atom) {
     const size_t npix = (size_t)c->p.n_rows * c->p.n_cols;
-    const unsigned blocks = (unsigned)std::min<size_t>((npix + 255) / 256, 152 * 8);
+    const unsigned blocks = (unsigned)std::min<size_t>((npix + 256 * kAccumPix - 1) / (256 * kAccumPix), 152 * 8);
     accum_apply_kernel<<<blocks, 256, 0, st>>>(c->z, c->acc, npix, idx, count, c->p.n_pos, c->part,
                                                cluster_of(c->p.m), c->p.m, c->phi_pos, c->gn_pos);
     CUDA_TRY(cudaGetLastError());
@@ -1428,6 +1469,63 @@ int noalloc_scratch(NoAllocScratch* out) {
 // launches only write the members' per-window scratch (increments, partial
 // sums, corners), never an object; the members' permutations are set to the
 // identity first so that every index is valid.
+// The update of batched step t with apply tile shape v, from the device table
+// `table` (default: the group's own table of that shape).
+cudaError_t launch_apply_batched(magpie_group* g, int v, int t, cudaStream_t st, const ApplyArgs* table = nullptr) {
+  const GroupApplyLaunch& A = g->al[v][t];
+  const ApplyArgs* tab = table ? table : g->atable[v] + A.tab_off;
+  const size_t smem = (sizeof(int2) + sizeof(int)) * A.max_count;
+  switch (v) {
+    case 0: apply_kernel_batched<16, 16><<<A.blocks, 256, smem, st>>>(tab, A.n); break;
+    case 1: apply_kernel_batched<32, 8><<<A.blocks, 256, smem, st>>>(tab, A.n); break;
+    case 2: apply_kernel_batched<32, 32><<<A.blocks, 256, smem, st>>>(tab, A.n); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// Times every apply tile shape on batched step 0 (one warm-up, then three
+// launches each), with every member's object replaced by a scratch copy so
+// that the members' objects are not touched, and keeps the fastest.
+int group_tune_apply(magpie_group* g, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+  if (g->al[0].empty()) return MAGPIE_OK;
+  size_t total = 0;
+  for (auto* c : g->members) total += (size_t)c->p.n_rows * c->p.n_cols;
+  float2* scratch = nullptr;
+  ApplyArgs* tab = nullptr;
+  cudaError_t e = cudaMalloc(&scratch, sizeof(float2) * total);
+  if (e == cudaSuccess) e = cudaMalloc(&tab, sizeof(ApplyArgs) * g->members.size());
+  if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, sizeof(float2) * total, st);
+  float best = 0.f;
+  for (int v = 0; v < 3 && e == cudaSuccess; ++v) {
+    const GroupApplyLaunch& A = g->al[v][0];
+    std::vector<ApplyArgs> at(g->atable_host[v].begin() + A.tab_off, g->atable_host[v].begin() + A.tab_off + A.n);
+    size_t off = 0;
+    for (auto& P : at) {
+      P.z = scratch + off;
+      off += (size_t)P.n_rows * P.n_cols;
+    }
+    e = cudaMemcpyAsync(tab, at.data(), sizeof(ApplyArgs) * at.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_apply_batched(g, v, 0, st, tab);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_apply_batched(g, v, 0, st, tab);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    g->apply_ms[v] = ms / 3.f;
+    if (e == cudaSuccess && (v == 0 || ms / 3.f < best)) {
+      best = ms / 3.f;
+      g->apply_shape = v;
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (scratch) cudaFree(scratch);
+  if (tab) cudaFree(tab);
+  if (e != cudaSuccess) return fail(MAGPIE_ECUDA, std::string("group autotuner (update): ") + cudaGetErrorString(e));
+  return MAGPIE_OK;
+}
+
 int group_autotune(magpie_group* g) {
   cudaStream_t st = g->stream;
   for (auto* c : g->members)
@@ -1464,10 +1562,12 @@ int group_autotune(magpie_group* g) {
         }
       }
     }
+  int rc = MAGPIE_OK;
+  if (e == cudaSuccess) rc = group_tune_apply(g, st, e0, e1);
   cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (e != cudaSuccess) return fail(MAGPIE_ECUDA, std::string("group autotuner: ") + cudaGetErrorString(e));
-  return MAGPIE_OK;
+  return rc;
 }
 
 extern "C" {
@@ -1840,7 +1940,8 @@ void magpie_group_destroy(magpie_group* g) {
   if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
   if (g->table) cudaFree(g->table);
   if (g->map) cudaFree(g->map);
-  if (g->atable) cudaFree(g->atable);
+  for (auto* a : g->atable)
+    if (a) cudaFree(a);
   delete g;
 }
 
@@ -1860,7 +1961,6 @@ int magpie_group_create(magpie_group** out, magpie_ctx* const* ctxs, int32_t n, 
   g->stream = (cudaStream_t)stream;
   std::vector<StepArgs> table;
   std::vector<int2> map;
-  std::vector<ApplyArgs> atable;
   int steps = 0;
   for (auto* c : g->members) steps = std::max(steps, n_steps(c));
   for (int t = 0; t < steps; ++t) {
@@ -1884,20 +1984,24 @@ int magpie_group_create(magpie_group** out, magpie_ctx* const* ctxs, int32_t n, 
       if (L.windows) wls.push_back(L);
     }
     g->wl.push_back(wls);
-    GroupApplyLaunch A{(int)atable.size(), 0, 0, 0};
-    for (int i = 0; i < n; ++i) {
-      magpie_ctx* c = g->members[i];
-      if (entry[i] < 0) continue;
-      const int cnt = std::min(c->p.minibatch, c->p.n_pos - t * c->p.minibatch);
-      ApplyArgs P = apply_args(c->z, c->p.n_rows, c->p.n_cols, c->corner, c->order + (size_t)t * c->p.minibatch, cnt,
-                               c->p.n_pos, c->contrib, c->pyr + c->M, c->p.m, c->part, c->phi_pos, c->gn_pos);
-      P.block0 = A.blocks;
-      A.blocks += apply_tiles(P);
-      A.max_count = std::max(A.max_count, cnt);
-      ++A.n;
-      atable.push_back(P);
+    for (int v = 0; v < 3; ++v) {
+      std::vector<ApplyArgs>& at = g->atable_host[v];
+      GroupApplyLaunch A{(int)at.size(), 0, 0, 0};
+      for (int i = 0; i < n; ++i) {
+        magpie_ctx* c = g->members[i];
+        if (entry[i] < 0) continue;
+        const int cnt = std::min(c->p.minibatch, c->p.n_pos - t * c->p.minibatch);
+        ApplyArgs P = apply_args(c->z, c->p.n_rows, c->p.n_cols, c->corner, c->order + (size_t)t * c->p.minibatch,
+                                 cnt, c->p.n_pos, c->contrib, c->pyr + c->M, c->p.m, c->part, c->phi_pos,
+                                 c->gn_pos, 0, kApplyShapes[v]);
+        P.block0 = A.blocks;
+        A.blocks += apply_tiles(P);
+        A.max_count = std::max(A.max_count, cnt);
+        ++A.n;
+        at.push_back(P);
+      }
+      g->al[v].push_back(A);
     }
-    g->al.push_back(A);
   }
   auto upload = [&](void** dst, const void* src, size_t bytes) -> int {
     cudaError_t e = cudaMalloc(dst, bytes);
@@ -1911,9 +2015,11 @@ int magpie_group_create(magpie_group** out, magpie_ctx* const* ctxs, int32_t n, 
   };
   int rc;
   if ((rc = upload((void**)&g->table, table.data(), sizeof(StepArgs) * table.size())) ||
-      (rc = upload((void**)&g->map, map.data(), sizeof(int2) * map.size())) ||
-      (rc = upload((void**)&g->atable, atable.data(), sizeof(ApplyArgs) * atable.size())))
+      (rc = upload((void**)&g->map, map.data(), sizeof(int2) * map.size())))
     return rc;
+  for (int v = 0; v < 3; ++v)
+    if ((rc = upload((void**)&g->atable[v], g->atable_host[v].data(), sizeof(ApplyArgs) * g->atable_host[v].size())))
+      return rc;
   cudaError_t e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     magpie_group_destroy(g);
@@ -1944,10 +2050,7 @@ int magpie_group_sweep(magpie_group* g, const int32_t* const* orders) {
         if (e != cudaSuccess) break;
       }
       if (e != cudaSuccess) break;
-      const GroupApplyLaunch& A = g->al[t];
-      apply_kernel_batched<<<A.blocks, 256, (sizeof(int2) + sizeof(int)) * A.max_count, g->cap_stream>>>(
-          g->atable + A.tab_off, A.n);
-      e = cudaGetLastError();
+      e = launch_apply_batched(g, g->apply_shape, t, g->cap_stream);
     }
     cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &gr);
     if (e == cudaSuccess) e = e2;
@@ -2264,6 +2367,27 @@ int magpie_group_tuning(magpie_group* g, int32_t* minb, float* ms) {
     minb[i] = g->minb[i];
     ms[2 * i] = g->tune_ms[i][0];
     ms[2 * i + 1] = g->tune_ms[i][1];
+  }
+  return MAGPIE_OK;
+}
+
+int magpie_group_apply_tuning(magpie_group* g, int32_t* shape, int32_t* tile_w, int32_t* tile_h, float* ms) {
+  if (!g || !shape || !tile_w || !tile_h || !ms) return fail(MAGPIE_EINVAL, "NULL argument");
+  *shape = g->apply_shape;
+  for (int v = 0; v < 3; ++v) {
+    tile_w[v] = kApplyShapes[v].tw;
+    tile_h[v] = kApplyShapes[v].th;
+    ms[v] = g->apply_ms[v];
+  }
+  return MAGPIE_OK;
+}
+
+int magpie_group_set_apply_shape(magpie_group* g, int32_t shape) {
+  if (!g || shape < 0 || shape > 2) return fail(MAGPIE_EINVAL, "need a group and a shape index in [0, 2]");
+  g->apply_shape = shape;
+  if (g->graph) {
+    cudaGraphExecDestroy(g->graph);
+    g->graph = nullptr;
   }
   return MAGPIE_OK;
 }

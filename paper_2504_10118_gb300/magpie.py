@@ -118,6 +118,8 @@ def lib() -> ctypes.CDLL:
             "magpie_group_destroy": (None, [vp]),
             "magpie_group_tuning": (ctypes.c_int, [vp, vp, vp]),
             "magpie_group_set_minb": (ctypes.c_int, [vp, i32, i32]),
+            "magpie_group_apply_tuning": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+            "magpie_group_set_apply_shape": (ctypes.c_int, [vp, i32]),
             "magpie_cnn_param_count": (i32, []),
             "magpie_cnn_create": (ctypes.c_int, [ctypes.POINTER(vp), i32, i32, vp]),
             "magpie_cnn_destroy": (None, [vp]),
@@ -361,6 +363,19 @@ def magpie_group_tuning(group: Group):
     ms = (ctypes.c_float * 12)()
     _check(lib().magpie_group_tuning(group.handle, minb, ms))
     return {8 << i: (minb[i], (ms[2 * i], ms[2 * i + 1])) for i in range(6) if ms[2 * i] > 0}
+
+
+def magpie_group_apply_tuning(group: Group):
+    """(shape in use, [(tile_w, tile_h, ms per launch)] for the three update tile shapes)."""
+    shape = ctypes.c_int32()
+    tw, th = (ctypes.c_int32 * 3)(), (ctypes.c_int32 * 3)()
+    ms = (ctypes.c_float * 3)()
+    _check(lib().magpie_group_apply_tuning(group.handle, ctypes.byref(shape), tw, th, ms))
+    return shape.value, [(tw[i], th[i], ms[i]) for i in range(3)]
+
+
+def magpie_group_set_apply_shape(group: Group, shape: int) -> None:
+    _check(lib().magpie_group_set_apply_shape(group.handle, int(shape)))
 
 
 def magpie_group_set_minb(group: Group, m: int, minb: int) -> None:

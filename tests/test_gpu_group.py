@@ -133,3 +133,32 @@ def test_autotuner_choices_give_identical_results():
         assert np.array_equal(a, b)
     with pytest.raises(magpie.MagpieError):
         magpie.magpie_group_set_minb(magpie.magpie_group_create([members[0].ctx()]), 128, 3)
+
+
+def test_update_tile_shapes_give_identical_results():
+    """The autotuner timed the update kernel's three tile shapes (16 x 16,
+    32 x 8, 32 x 32) without touching the members' objects, and every shape
+    sums each pixel's windows in minibatch order: groups forced to each shape
+    give bitwise equal objects."""
+    members = [Member(spec, seed=60 + i) for i, spec in enumerate(SPECS)]
+    outs = []
+    for shape in (0, 1, 2):
+        ctxs = [mb.ctx() for mb in members]
+        before = [mb.zt.clone() for mb in members]
+        g = magpie.magpie_group_create(ctxs)
+        torch.cuda.synchronize()
+        assert all(torch.equal(a, mb.zt) for a, mb in zip(before, members))
+        chosen, shapes = magpie.magpie_group_apply_tuning(g)
+        print("update tile shapes:", chosen, shapes)
+        assert chosen in (0, 1, 2) and [s[:2] for s in shapes] == [(16, 16), (32, 8), (32, 32)]
+        assert all(ms > 0 for _, _, ms in shapes)
+        magpie.magpie_group_set_apply_shape(g, shape)
+        for s in range(2):
+            magpie.magpie_group_sweep(g, orders(members, s))
+        outs.append([mb.zt.cpu().numpy() for mb in members])
+        g.close()
+        for c in ctxs:
+            c.close()
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            assert np.array_equal(a, b)
