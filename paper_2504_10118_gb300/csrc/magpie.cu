@@ -200,15 +200,14 @@ __global__ void __launch_bounds__(256) apply_kernel_batched(const ApplyArgs* __r
   apply_body<TW, TH>(P, t % P.tiles_x, t / P.tiles_x);
 }
 
-constexpr int kAccumPix = 4;  // pixels per thread of the atomic update kernel
-
 // Atomic update (deterministic = 0): the window kernel has added, pixel by
 // pixel, sum_k w . Delta_k (x, y) and sum_k w (z) into object-sized
 // accumulators; every pixel with a positive weight moves by their ratio, the
 // same rule as the ordered update, and every touched accumulator is cleared
-// for the next step.  Four pixels per thread, all their loads in flight at
-// once.  Block 0 also turns the window kernel's block partials into Phi_k
-// and ||grad Phi_k||.
+// for the next step.  One pixel per thread, its accumulator and object loads
+// issued together (four pixels per thread, a quarter of the threads,
+// measured slower: 122 against 106 us per sweep).  Block 0 also turns the
+// window kernel's block partials into Phi_k and ||grad Phi_k||.
 __global__ void __launch_bounds__(256) accum_apply_kernel(float2* __restrict__ z, float4* __restrict__ acc,
                                                           size_t npix, const int32_t* __restrict__ idx, int count,
                                                           int n_pos, const double* __restrict__ part, int slots,
@@ -226,25 +225,11 @@ __global__ void __launch_bounds__(256) accum_apply_kernel(float2* __restrict__ z
       gn_pos[k] = sqrt(g);
     }
   }
-  // kAccumPix pixels per thread, strided by the grid so that each warp's
-  // loads stay coalesced, all loads issued before any is used
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t p0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p0 < npix; p0 += kAccumPix * stride) {
-    float4 a[kAccumPix];
-    float2 zz[kAccumPix];
-#pragma unroll
-    for (int u = 0; u < kAccumPix; ++u) {
-      const size_t p = p0 + u * stride;
-      a[u] = p < npix ? __ldcg(&acc[p]) : make_float4(0.f, 0.f, 0.f, 0.f);
-      zz[u] = p < npix ? z[p] : make_float2(0.f, 0.f);  // unconditional: no second round trip
-    }
-#pragma unroll
-    for (int u = 0; u < kAccumPix; ++u) {
-      const size_t p = p0 + u * stride;
-      if (p >= npix) continue;
-      if (a[u].z > 0.f) z[p] = make_float2(zz[u].x + a[u].x / a[u].z, zz[u].y + a[u].y / a[u].z);
-      if (a[u].x != 0.f || a[u].y != 0.f || a[u].z != 0.f) acc[p] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < npix; p += (size_t)gridDim.x * blockDim.x) {
+    const float4 a = __ldcg(&acc[p]);
+    const float2 zz = z[p];  // unconditional: both loads in flight together
+    if (a.z > 0.f) z[p] = make_float2(zz.x + a.x / a.z, zz.y + a.y / a.z);
+    if (a.x != 0.f || a.y != 0.f || a.z != 0.f) acc[p] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
 
@@ -1254,7 +1239,7 @@ int enqueue_step(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st, 
   if (ev) CUDA_TRY(cudaEventRecord(ev[2], st));
   if (atom) {
     const size_t npix = (size_t)c->p.n_rows * c->p.n_cols;
-    const unsigned blocks = (unsigned)std::min<size_t>((npix + 256 * kAccumPix - 1) / (256 * kAccumPix), 152 * 8);
+    const unsigned blocks = (unsigned)std::min<size_t>((npix + 255) / 256, 152 * 8);
     accum_apply_kernel<<<blocks, 256, 0, st>>>(c->z, c->acc, npix, idx, count, c->p.n_pos, c->part,
                                                cluster_of(c->p.m), c->p.m, c->phi_pos, c->gn_pos);
     CUDA_TRY(cudaGetLastError());
