@@ -479,3 +479,38 @@ def test_bad_positions_rejected():
     with pytest.raises(magpie.MagpieError) as ei:
         P.ctx()
     assert ei.value.code == magpie.EINVAL
+
+
+@pytest.mark.parametrize("deterministic", [1, 0])
+@pytest.mark.parametrize("levels,alpha", [(1, 0.1), (3, 0.1), (3, 0.0), (1, 0.0)])
+def test_hard_edged_probe(levels, alpha, deterministic):
+    """A probe that is exactly zero outside its disk and on a 4 x 4 block
+    inside it: the division rule (a quotient with a zero denominator is 0)
+    acts on dead 2 x 2 bins at every level, and with alpha = 0 (u = 0) the
+    weight w = |Q|^2 vanishes there, so pixels that only zero parts of the
+    probe reach keep their value (the update's positive-denominator rule)."""
+    n, m, grid, step = 96, 32, 5, 14
+    P = Problem(n, m, grid, step, 1, levels, 8, alpha=alpha, seed=5)
+    c = (m - 1) / 2.0
+    yy, xx = np.meshgrid(np.arange(m) - c, np.arange(m) - c, indexing="ij")
+    Q = P.Q * (np.sqrt(xx ** 2 + yy ** 2) <= 10.0 * m / 32.0)
+    Q[12:16, 12:16] = 0.0
+    P.Q = f32(Q)
+    P.d = O.forward_intensities(P.z_true, P.Q, P.pos).astype(np.float32).astype(np.float64)
+    P.u = O.rpie_regulariser(P.Q, alpha)
+    assert np.sum(np.abs(P.Q) == 0) > 100
+    ctx = P.ctx(deterministic=deterministic)
+    batch = synth.make_order(P.N, 2)[:8]
+    magpie.magpie_step(ctx, dev_i32(batch))
+    got = P.z_gpu()
+    ref = O.minibatch_step(P.z0, P.Q, P.pos, P.d, P.u, levels, batch)
+    assert rel(got, ref) < STEP_TOL
+    assert rel(got - P.z0, ref - P.z0) < INC_TOL
+    # pixels no window of the batch reaches with a nonzero weight are unchanged, bit for bit
+    w = P.u + np.abs(P.Q) ** 2
+    den = np.zeros((n, n))
+    for k in batch:
+        r, cc = P.pos[k]
+        den[r:r + m, cc:cc + m] += w
+    assert np.array_equal(got[den == 0], P.z0[den == 0])
+    ctx.close()
