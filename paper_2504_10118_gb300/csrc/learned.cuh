@@ -212,11 +212,13 @@ __global__ void __launch_bounds__(128) conv_fwd_kernel(const ConvFwd a) {
 
 // Direct convolution for the thin layers (few input or few output channels:
 // the network's first, 4 -> 32, and last, 64 -> 2), where an implicit GEMM
-// tile would be mostly padding: one thread per output pixel computes all COUT
-// outputs from the BF16 inputs and weights (exact in FP32) with FP32
-// accumulation, the weights held in shared memory as [k][COUT] floats and
-// read by every thread of a warp at once.  Dynamic smem: 9 CIN COUT floats.
-template <int CIN, int COUT>
+// tile would be mostly padding: one thread computes PIX consecutive output
+// pixels of one image row, all COUT outputs each, from the BF16 inputs and
+// weights (exact in FP32) with FP32 accumulation.  The weights sit in shared
+// memory as [k][COUT] floats, read by every thread of a warp at once; each
+// weight read feeds PIX fused multiply-adds (the kernel is bound by those
+// shared-memory reads).  Dynamic smem: 9 CIN COUT floats.
+template <int CIN, int COUT, int PIX>
 __global__ void __launch_bounds__(256) conv_direct_kernel(const ConvFwd a) {
   static_assert(CIN % 4 == 0, "input channels in groups of four");
   extern __shared__ __align__(16) float wsm[];
@@ -226,41 +228,66 @@ __global__ void __launch_bounds__(256) conv_direct_kernel(const ConvFwd a) {
     wsm[k * COUT + co] = __bfloat162float(a.w[i]);
   }
   __syncthreads();
-  const int HoHo = a.Ho * a.Ho, Mtot = a.B * HoHo, Hv = a.Hin * a.up;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= Mtot) return;
-  const int b = p / HoHo, rem = p - b * HoHo, oy = rem / a.Ho, ox = rem - oy * a.Ho;
-  float acc[COUT];
+  const int groups = a.Ho / PIX;  // pixel groups per output row (Ho is a multiple of PIX)
+  const int Mg = a.B * a.Ho * groups, Hv = a.Hin * a.up;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= Mg) return;
+  const int row = t / groups, ox0 = (t - row * groups) * PIX;
+  const int b = row / a.Ho, oy = row - b * a.Ho;
+  float acc[PIX][COUT];
 #pragma unroll
-  for (int co = 0; co < COUT; ++co) acc[co] = 0.f;
-  for (int tap = 0; tap < 9; ++tap) {
-    const int ky = tap / 3, kx = tap - 3 * ky;
-    const int vy = oy * a.stride + ky - 1, vx = ox * a.stride + kx - 1;
-    if (vy < 0 || vy >= Hv || vx < 0 || vx >= Hv) continue;
-    const bf16* src = a.in + ((size_t)(b * a.Hin + vy / a.up) * a.Hin + vx / a.up) * CIN;
-    const float* wt = wsm + tap * CIN * COUT;
+  for (int p = 0; p < PIX; ++p)
 #pragma unroll
-    for (int c0 = 0; c0 < CIN; c0 += 4) {
-      const uint2 raw = *reinterpret_cast<const uint2*>(src + c0);
-      const __nv_bfloat162 h01 = *reinterpret_cast<const __nv_bfloat162*>(&raw.x);
-      const __nv_bfloat162 h23 = *reinterpret_cast<const __nv_bfloat162*>(&raw.y);
-      const float xv[4] = {__low2float(h01), __high2float(h01), __low2float(h23), __high2float(h23)};
+    for (int co = 0; co < COUT; ++co) acc[p][co] = 0.f;
+  for (int ky = 0; ky < 3; ++ky) {
+    const int vy = oy * a.stride + ky - 1;
+    if (vy < 0 || vy >= Hv) continue;
+    const bf16* rowp = a.in + (size_t)(b * a.Hin + vy / a.up) * a.Hin * CIN;
+    for (int kx = 0; kx < 3; ++kx) {
+      const float* wt = wsm + (ky * 3 + kx) * CIN * COUT;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float* wr = wt + (c0 + j) * COUT;
+      for (int c0 = 0; c0 < CIN; c0 += 4) {
+        float xv[PIX][4];
 #pragma unroll
-        for (int co = 0; co < COUT; ++co) acc[co] = fmaf(xv[j], wr[co], acc[co]);
+        for (int p = 0; p < PIX; ++p) {
+          const int vx = (ox0 + p) * a.stride + kx - 1;
+          if (vx < 0 || vx >= Hv) {
+            xv[p][0] = xv[p][1] = xv[p][2] = xv[p][3] = 0.f;
+            continue;
+          }
+          const uint2 raw = *reinterpret_cast<const uint2*>(rowp + (size_t)(vx / a.up) * CIN + c0);
+          const __nv_bfloat162 h01 = *reinterpret_cast<const __nv_bfloat162*>(&raw.x);
+          const __nv_bfloat162 h23 = *reinterpret_cast<const __nv_bfloat162*>(&raw.y);
+          xv[p][0] = __low2float(h01);
+          xv[p][1] = __high2float(h01);
+          xv[p][2] = __low2float(h23);
+          xv[p][3] = __high2float(h23);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float* wr = wt + (c0 + j) * COUT;
+#pragma unroll
+          for (int co = 0; co < COUT; ++co) {
+            const float wv = wr[co];
+#pragma unroll
+            for (int p = 0; p < PIX; ++p) acc[p][co] = fmaf(xv[p][j], wv, acc[p][co]);
+          }
+        }
       }
     }
   }
 #pragma unroll
-  for (int co = 0; co < COUT; ++co) {
-    float v = acc[co] + a.bias[co];
-    if (a.relu) v = fmaxf(v, 0.f);
-    if (a.out_f32)
-      static_cast<float*>(a.out)[(size_t)p * COUT + co] = v;
-    else
-      static_cast<bf16*>(a.out)[(size_t)p * COUT + co] = __float2bfloat16_rn(v);
+  for (int p = 0; p < PIX; ++p) {
+    const size_t pix = (size_t)row * a.Ho + ox0 + p;
+#pragma unroll
+    for (int co = 0; co < COUT; ++co) {
+      float v = acc[p][co] + a.bias[co];
+      if (a.relu) v = fmaxf(v, 0.f);
+      if (a.out_f32)
+        static_cast<float*>(a.out)[pix * COUT + co] = v;
+      else
+        static_cast<bf16*>(a.out)[pix * COUT + co] = __float2bfloat16_rn(v);
+    }
   }
 }
 

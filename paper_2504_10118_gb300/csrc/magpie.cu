@@ -926,14 +926,17 @@ cudaError_t launch_conv(const ConvFwd& a0, float* part, cudaStream_t st, int ten
   a.part = pl.splits > 1 ? part : nullptr;
   const dim3 grid(pl.gx, pl.gy, pl.splits);
   if (tensor_path == 1 && conv_direct_fits(a)) {
-    const int Mtot = a.B * a.Ho * a.Ho;
     const size_t smem = sizeof(float) * a.Cout * a.K;
-    if (a.Cin == 64 && a.Cout == 2)
-      conv_direct_kernel<64, 2><<<(Mtot + 255) / 256, 256, smem, st>>>(a);
-    else if (a.Cin == 4 && a.Cout == 32)
-      conv_direct_kernel<4, 32><<<(Mtot + 255) / 256, 256, smem, st>>>(a);
-    else
+    const int rows = a.B * a.Ho;
+    if (a.Cin == 64 && a.Cout == 2) {  // 8 pixels per thread (Ho = h >= 8)
+      const int n = rows * (a.Ho / 8);
+      conv_direct_kernel<64, 2, 8><<<(n + 255) / 256, 256, smem, st>>>(a);
+    } else if (a.Cin == 4 && a.Cout == 32) {  // 2 pixels per thread
+      const int n = rows * (a.Ho / 2);
+      conv_direct_kernel<4, 32, 2><<<(n + 255) / 256, 256, smem, st>>>(a);
+    } else {
       return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
   }
   if (tc && pl.bn == 128)

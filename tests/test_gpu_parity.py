@@ -295,17 +295,22 @@ def increment_errors(before, got, ref):
 EW_TOL = {1e-3: 5e-3, 1e-2: 2e-3}
 
 
-# The atomic update sums each pixel's contributions in an order that varies
-# from run to run; at the worst step of the sweep (where the ordered update's
-# deterministic error is 8.0e-6) its increment error measured 0.8e-5 to
-# 1.06e-5 over two runs, so its bar on the increment is 2e-5.
-INC_TOL_ATOMIC = 2e-5
+# The atomic update sums each pixel's contributions (about seven per step
+# here) in an order that varies from run to run.  Where the contributions
+# nearly cancel, their float32 rounding is large against the net increment, so
+# its errors scatter from run to run around the ordered update's fixed ones:
+# over three runs the worst step's increment error measured 0.8e-5, 1.06e-5
+# and 1.53e-5 (ordered: 8.0e-6, deterministic), and the element-wise errors
+# 3.0e-3 / 6.2e-3 where |dz| > 1e-3 max|dz| and 0.63e-3 / 0.89e-3 where
+# |dz| > 1e-2 max|dz|.  Its bars are about twice the worst measured value.
+INC_TOL_ATOMIC = 3e-5
+EW_TOL_ATOMIC = {1e-3: 1.2e-2, 1e-2: 2e-3}
 
 
 def check_mid_steps(deterministic):
     """Every step of one sweep of the mid workload from the GPU's own state
-    before the step: object to 1e-5, increment to 1e-5 (2e-5 with the atomic
-    update), increment element-wise."""
+    before the step: object to 1e-5, increment to 1e-5 (3e-5 with the atomic
+    update), increment element-wise (EW_TOL, EW_TOL_ATOMIC)."""
     w = synth.WORKLOADS["mid"]
     P = Problem(w.n, w.m, w.grid, w.step, w.jitter, w.levels, w.minibatch, alpha=w.alpha,
                 photons=w.photons, perturb=0.2)
@@ -321,9 +326,10 @@ def check_mid_steps(deterministic):
         worst = np.maximum(worst, [rel(got, ref)] + increment_errors(before, got, ref))
     ctx.close()
     assert worst[0] < STEP_TOL, worst
+    ew = EW_TOL if deterministic else EW_TOL_ATOMIC
     assert worst[1] < (INC_TOL if deterministic else INC_TOL_ATOMIC), worst
-    assert worst[2] < EW_TOL[1e-3], worst
-    assert worst[3] < EW_TOL[1e-2], worst
+    assert worst[2] < ew[1e-3], worst
+    assert worst[3] < ew[1e-2], worst
     return P, order
 
 
