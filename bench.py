@@ -369,24 +369,37 @@ def batched_measure(dev, magpie, warmup: int, steps: int, pg=None, clocks=None):
     orders = [[torch.from_numpy(synth.make_order(w.n_pos, s)).to(dev) for w in ws] for s in range(warmup + steps)]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    for s in range(warmup):
-        magpie.magpie_group_sweep(group, orders[s])
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    torch.cuda.synchronize()
-    if pg:
-        pg.barrier()
-    for s in range(steps):
-        flush.zero_()
-        ev0[s].record(stream)
-        magpie.magpie_group_sweep(group, orders[warmup + s])
-        ev1[s].record(stream)
-    torch.cuda.synchronize()
-    if pg:
-        pg.barrier()
-    total_ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+
+    def timed():
+        for s in range(warmup):
+            magpie.magpie_group_sweep(group, orders[s])
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        for s in range(steps):
+            flush.zero_()
+            ev0[s].record(stream)
+            magpie.magpie_group_sweep(group, orders[warmup + s])
+            ev1[s].record(stream)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        return sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+
+    persistent, form_ms = magpie.magpie_group_form_tuning(group)
+    total_ms = timed()
+    status = magpie.magpie_group_status(group)
+    # the other form of a batched step, timed the same way (members' objects
+    # continue from where the timed sweeps left them)
+    magpie.magpie_group_set_persistent(group, 1 - persistent)
+    other_ms = timed()
+    status = status or magpie.magpie_group_status(group)
+    magpie.magpie_group_set_persistent(group, persistent)
     steps_max = max(math.ceil(w.n_pos / w.minibatch) for w in ws)
-    launches = sum(len({w.m for w in ws if math.ceil(w.n_pos / w.minibatch) > t}) + 1 for t in range(steps_max))
+    sides = [len({w.m for w in ws if math.ceil(w.n_pos / w.minibatch) > t}) for t in range(steps_max)]
+    launches = sum(sides) if persistent else sum(n + 1 for n in sides)
     tuning = magpie.magpie_group_tuning(group)
     shape, shapes = magpie.magpie_group_apply_tuning(group)
     group.close()
@@ -399,10 +412,17 @@ def batched_measure(dev, magpie, warmup: int, steps: int, pg=None, clocks=None):
                       "levels": 3, "minibatch": 64, "update": "ordered (context groups)",
                       "data": "photon noise drawn on the device"},
            "gpu_launches_per_step": launches,
+           "form": {"used": "persistent" if persistent else "separate launches",
+                    "ms_per_sweep": {"persistent" if persistent else "separate launches": total_ms / steps,
+                                     "separate launches" if persistent else "persistent": other_ms / steps},
+                    "bounded_waits": "none ran out" if status == magpie.OK else "a wait ran out"},
            "autotuner": {"window_register_bound": {str(m): {"blocks_per_sm": v[0], "ms_per_launch": list(v[1])}
                                                    for m, v in tuning.items()},
                          "update_tile": {"choice": f"{shapes[shape][0]}x{shapes[shape][1]}",
-                                         "ms_per_launch": {f"{w}x{h}": ms for w, h, ms in shapes}}}}
+                                         "ms_per_launch": {f"{w}x{h}": ms for w, h, ms in shapes}},
+                         "step_form": {"choice": "persistent" if persistent else "separate launches",
+                                       "ms_batched_step0": {"separate launches": form_ms[0],
+                                                            "persistent": form_ms[1]}}}}
     flops = sum(w.n_pos * flops_per_window(w.m) for w in ws) * steps
     return rec, total_ms, launches, flops
 
@@ -444,9 +464,10 @@ def run_batched(args):
             "gpu_launches": launches * args.steps, "clocks": clk,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "whole group sweep (batched window and update launches)",
+                         "kernel": "whole group sweep (window and update work of every member)",
                          "peak_source": peak_src},
             "autotuner": rec["autotuner"],
+            "form": rec["form"],
         }
         print(json.dumps(line), flush=True)
     if pg:

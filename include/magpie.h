@@ -244,7 +244,9 @@ int magpie_forward_intensities(const void* object, int32_t n_rows, int32_t n_col
  * on each of them (member results are bitwise those of separate sweeps), but
  * batched: batched step t runs step t of every member that has one, all
  * windows of equal m in one launch and all members' object updates in one
- * more, replayed from one CUDA graph.  Members may differ in every size.
+ * more (or, in the persistent form below, one launch per m for windows and
+ * updates together), replayed from one CUDA graph.  Members may differ in
+ * every size.
  *   ctxs   : n contexts created on the current device, none with
  *            update_probe = 1, each at most once; they must outlive the group
  *            and not be used on another stream while a group sweep runs.
@@ -287,6 +289,46 @@ int magpie_group_set_minb(magpie_group* group, int32_t m, int32_t minb);
  */
 int magpie_group_apply_tuning(magpie_group* group, int32_t* shape, int32_t* tile_w, int32_t* tile_h, float* ms);
 int magpie_group_set_apply_shape(magpie_group* group, int32_t shape);
+
+/*
+ * The autotuner's third dimension: the form of a batched step.
+ *   0: separate launches, as above (the batched window kernel per window
+ *      side, then one update kernel for all members);
+ *   1: persistent, one launch per window side whose clusters (as many as fit
+ *      on the GPU at once) take work items from a device queue: first every
+ *      window of the side's members, then the members' update tiles (32 x 32
+ *      pixels; 16 x 16 for sides below 64).  An update tile waits until every
+ *      block of its member's windows has counted itself done, so one member's
+ *      update overlaps the other members' windows; the launches of different
+ *      sides run concurrently (forked streams in the sweep's graph).  Each wait
+ *      is bounded (1 s of GPU time by default): a wait that runs out sets an
+ *      error flag and skips its tile, the launch still ends, and
+ *      magpie_group_status reports MAGPIE_ETIMEOUT.
+ * Both forms sum each pixel's windows in minibatch order and give bitwise
+ * identical objects.  magpie_group_create times batched step 0 in both forms
+ * (updates writing scratch copies of the objects) and uses the faster.
+ * magpie_group_form_tuning reports the form in use (*persistent) and the two
+ * measured ms per batched step 0 (ms[2], HOST); magpie_group_set_persistent
+ * forces one (MAGPIE_EINVAL unless 0 or 1).  magpie_group_set_wait_limit sets
+ * the bound of each wait (seconds in [1e-6, 60]).
+ */
+int magpie_group_form_tuning(magpie_group* group, int32_t* persistent, float* ms);
+int magpie_group_set_persistent(magpie_group* group, int32_t persistent);
+int magpie_group_set_wait_limit(magpie_group* group, double seconds);
+
+/* Waits for the group's stream, then reads and clears the error flag of the
+   persistent form: MAGPIE_ETIMEOUT if a dependency wait ran out since the
+   last call (that update tile was skipped), else MAGPIE_OK. */
+int magpie_group_status(magpie_group* group);
+
+/* Self-test of the bounded waits (no counterpart in the paper): runs batched
+   step 0 in the persistent form with every update tile waiting for one block
+   more than its member's windows have, which never arrives, under a limit of
+   `seconds` (in [1e-6, 10]).  Every wait runs out, every update tile is
+   skipped (the members' objects are unchanged; their per-window scratch is
+   overwritten), the launch ends, and the call returns MAGPIE_ETIMEOUT; the
+   group stays usable. */
+int magpie_group_check_waits(magpie_group* group, double seconds);
 
 /*
  * Learned coarse-level correction.  The paper has no network: its Algorithm
@@ -500,7 +542,7 @@ int magpie_stage_times(magpie_ctx* ctx, const int32_t* idx, int32_t count, uint6
 /* Message of the calling thread's most recent failed call ("" if none). */
 const char* magpie_last_error(void);
 
-/* Library version as major*10000 + minor*100 + patch (this is 1.2.0). */
+/* Library version as major*10000 + minor*100 + patch (this is 1.3.0). */
 int magpie_version(void);
 
 #ifdef __cplusplus

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <algorithm>
 #include <utility>
 
 namespace magpie_impl {
@@ -22,27 +23,35 @@ constexpr int kMaxSlots = 16;        // partial-sum slots per window: the window
 constexpr int kApplyUnroll = 4;      // increments in flight per thread in the update kernel
 
 #include "fft_lines.cuh"
+#include "update.cuh"
 #include "window_kernel.cuh"
 
 // the window sides with a window kernel
 #define MAGPIE_WINDOW_SIZES(X) X(8) X(16) X(32) X(64) X(128) X(256)
 
-// Launch with a cluster dimension when cl > 1.
+// Launch with a cluster dimension when cl > 1, and as a programmatic dependent
+// launch when pdl is set (the kernel must then call grid_dep_wait before it
+// touches memory that the stream's previous kernel reads or writes).
 template <typename... KArgs, typename... Args>
 cudaError_t launch_ex(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, int cl,
-                       Args&&... args) {
+                       bool pdl, Args&&... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   int n = 0;
   if (cl > 1) {
     attr[n].id = cudaLaunchAttributeClusterDimension;
     attr[n].val.clusterDim.x = cl;
     attr[n].val.clusterDim.y = 1;
     attr[n].val.clusterDim.z = 1;
+    ++n;
+  }
+  if (pdl) {  // see grid_dep_wait
+    attr[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[n].val.programmaticStreamSerializationAllowed = 1;
     ++n;
   }
   cfg.attrs = attr;
@@ -62,8 +71,15 @@ cudaError_t window_launch_batched(const StepArgs* table, const int2* map, int wi
 // the shared-memory attribute of every window kernel of this side;
 template <int MS>
 cudaError_t window_prepare();
-// the register bounds the group autotuner tries (c[0] the default).
+// the register bounds the group autotuner tries (c[0] the default);
 template <int MS>
 void window_minb_candidates(int* c);
+// the persistent step kernel on `clusters` clusters, with shared memory for
+// update lists of up to max_count windows;
+template <int MS>
+cudaError_t window_launch_persistent(const PersistArgs& P, int clusters, int max_count, cudaStream_t st, int minb);
+// the clusters of the persistent step kernel that fit on the GPU at once.
+template <int MS>
+int window_persistent_capacity(int max_count, int minb);
 
 }  // namespace magpie_impl

@@ -1,6 +1,6 @@
 // fft_lines.cuh -- complex helpers, in-register DFTs, the per-size split of
 // a window over a cluster, the slab layouts and the line FFTs of the MAGPIE
-// window kernel.  Included by magpie.cu inside its anonymous namespace.
+// window kernel.  Included by core.cuh inside namespace magpie_impl.
 #pragma once
 
 // ------------------------------------------------------------------ helpers
@@ -146,6 +146,15 @@ __device__ __forceinline__ void window_wait() {
   else
     __syncthreads();
 }
+
+// ---- programmatic dependent launch.  A kernel launched with the
+// programmatic-serialization attribute may begin while the previous kernel in
+// its stream is still running.  grid_dep_wait returns once that kernel has
+// finished and its memory operations are visible (at once when the launch
+// had no such attribute); grid_dep_launch lets the next such kernel begin
+// launching its blocks once every block of this grid has called it or exited.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // ---- mbarriers (the tensor-core kernels' stage barriers)
 constexpr int kMaxWaitTries = 1 << 20;  // bound of every mbarrier wait (a try returns within about a microsecond)

@@ -210,85 +210,140 @@ __global__ void __launch_bounds__(128) conv_fwd_kernel(const ConvFwd a) {
     }
 }
 
-// Direct convolution for the thin layers (few input or few output channels:
-// the network's first, 4 -> 32, and last, 64 -> 2), where an implicit GEMM
-// tile would be mostly padding: one thread computes PIX consecutive output
-// pixels of one image row, all COUT outputs each, from the BF16 inputs and
-// weights (exact in FP32) with FP32 accumulation.  The weights sit in shared
-// memory as [k][COUT] floats, read by every thread of a warp at once; each
-// weight read feeds PIX fused multiply-adds (the kernel is bound by those
-// shared-memory reads).  Dynamic smem: 9 CIN COUT floats.
-template <int CIN, int COUT, int PIX>
-__global__ void __launch_bounds__(256) conv_direct_kernel(const ConvFwd a) {
-  static_assert(CIN % 4 == 0, "input channels in groups of four");
-  extern __shared__ __align__(16) float wsm[];
-  constexpr int K = 9 * CIN;
-  for (int i = threadIdx.x; i < COUT * K; i += blockDim.x) {
-    const int co = i / K, k = i - co * K;
-    wsm[k * COUT + co] = __bfloat162float(a.w[i]);
+// Direct convolutions for the thin layers, where an implicit-GEMM tile would
+// be mostly padding.  Both read the BF16 inputs and weights (exact in FP32)
+// and accumulate in FP32; consecutive lanes take consecutive 16-byte pieces of
+// one pixel's channels, so a warp's loads and stores are contiguous.
+//
+// Few outputs (the last layer, 64 -> 2): S = CIN / 8 lanes per output pixel,
+// lane `part` holding input channels 8 part .. 8 part + 7 of every tap; the S
+// partial sums of each output are added with butterfly shuffles.  Weights sit
+// in shared memory as BF16 [tap][co][ci], so the S lanes of a pixel read one
+// contiguous 16 S-byte row per (tap, co).  Needs `in` 16-byte aligned.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) conv_thin_out_kernel(const ConvFwd a) {
+  constexpr int S = CIN / 8;
+  static_assert(CIN % 8 == 0 && (S & (S - 1)) == 0 && S <= 32, "channel split");
+  __shared__ __align__(16) bf16 wsm[9 * COUT * CIN];
+  for (int i = threadIdx.x; i < 9 * COUT * CIN; i += blockDim.x) {
+    const int co = i / (9 * CIN), r = i - co * 9 * CIN, tap = r / CIN, ci = r - tap * CIN;
+    wsm[(tap * COUT + co) * CIN + ci] = a.w[i];
   }
   __syncthreads();
-  const int groups = a.Ho / PIX;  // pixel groups per output row (Ho is a multiple of PIX)
-  const int Mg = a.B * a.Ho * groups, Hv = a.Hin * a.up;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= Mg) return;
-  const int row = t / groups, ox0 = (t - row * groups) * PIX;
-  const int b = row / a.Ho, oy = row - b * a.Ho;
-  float acc[PIX][COUT];
+  const int HH = a.Ho * a.Ho, Mtot = a.B * HH, Hv = a.Hin * a.up;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = t < (long long)Mtot * S;  // whole pixel groups: S divides 32
+  const int pix = live ? (int)(t / S) : 0, part = (int)(t % S);
+  const int b = pix / HH, rem = pix - b * HH, oy = rem / a.Ho, ox = rem - oy * a.Ho;
+  float acc[COUT];
 #pragma unroll
-  for (int p = 0; p < PIX; ++p)
-#pragma unroll
-    for (int co = 0; co < COUT; ++co) acc[p][co] = 0.f;
+  for (int co = 0; co < COUT; ++co) acc[co] = 0.f;
   for (int ky = 0; ky < 3; ++ky) {
     const int vy = oy * a.stride + ky - 1;
-    if (vy < 0 || vy >= Hv) continue;
-    const bf16* rowp = a.in + (size_t)(b * a.Hin + vy / a.up) * a.Hin * CIN;
+    if (!live || vy < 0 || vy >= Hv) continue;
+    const bf16* rowp = a.in + (size_t)(b * a.Hin + vy / a.up) * a.Hin * CIN + part * 8;
+#pragma unroll
     for (int kx = 0; kx < 3; ++kx) {
-      const float* wt = wsm + (ky * 3 + kx) * CIN * COUT;
+      const int vx = ox * a.stride + kx - 1;
+      if (vx < 0 || vx >= Hv) continue;
+      const uint4 raw = __ldg(reinterpret_cast<const uint4*>(rowp + (size_t)(vx / a.up) * CIN));
+      const __nv_bfloat162* xh = reinterpret_cast<const __nv_bfloat162*>(&raw);
+      float x[8];
 #pragma unroll
-      for (int c0 = 0; c0 < CIN; c0 += 4) {
-        float xv[PIX][4];
+      for (int j = 0; j < 4; ++j) {
+        x[2 * j] = __low2float(xh[j]);
+        x[2 * j + 1] = __high2float(xh[j]);
+      }
 #pragma unroll
-        for (int p = 0; p < PIX; ++p) {
-          const int vx = (ox0 + p) * a.stride + kx - 1;
-          if (vx < 0 || vx >= Hv) {
-            xv[p][0] = xv[p][1] = xv[p][2] = xv[p][3] = 0.f;
-            continue;
-          }
-          const uint2 raw = *reinterpret_cast<const uint2*>(rowp + (size_t)(vx / a.up) * CIN + c0);
-          const __nv_bfloat162 h01 = *reinterpret_cast<const __nv_bfloat162*>(&raw.x);
-          const __nv_bfloat162 h23 = *reinterpret_cast<const __nv_bfloat162*>(&raw.y);
-          xv[p][0] = __low2float(h01);
-          xv[p][1] = __high2float(h01);
-          xv[p][2] = __low2float(h23);
-          xv[p][3] = __high2float(h23);
-        }
+      for (int co = 0; co < COUT; ++co) {
+        const uint4 wr = *reinterpret_cast<const uint4*>(&wsm[((ky * 3 + kx) * COUT + co) * CIN + part * 8]);
+        const __nv_bfloat162* wh = reinterpret_cast<const __nv_bfloat162*>(&wr);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const float* wr = wt + (c0 + j) * COUT;
-#pragma unroll
-          for (int co = 0; co < COUT; ++co) {
-            const float wv = wr[co];
-#pragma unroll
-            for (int p = 0; p < PIX; ++p) acc[p][co] = fmaf(xv[p][j], wv, acc[p][co]);
-          }
+          acc[co] = fmaf(x[2 * j], __low2float(wh[j]), acc[co]);
+          acc[co] = fmaf(x[2 * j + 1], __high2float(wh[j]), acc[co]);
         }
       }
     }
   }
 #pragma unroll
-  for (int p = 0; p < PIX; ++p) {
-    const size_t pix = (size_t)row * a.Ho + ox0 + p;
+  for (int co = 0; co < COUT; ++co)
 #pragma unroll
-    for (int co = 0; co < COUT; ++co) {
-      float v = acc[p][co] + a.bias[co];
-      if (a.relu) v = fmaxf(v, 0.f);
-      if (a.out_f32)
-        static_cast<float*>(a.out)[pix * COUT + co] = v;
-      else
-        static_cast<bf16*>(a.out)[pix * COUT + co] = __float2bfloat16_rn(v);
+    for (int off = S / 2; off > 0; off >>= 1) acc[co] += __shfl_xor_sync(0xffffffffu, acc[co], off);
+  if (!live || part != 0) return;
+#pragma unroll
+  for (int co = 0; co < COUT; ++co) {
+    float v = acc[co] + a.bias[co];
+    if (a.relu) v = fmaxf(v, 0.f);
+    if (a.out_f32)
+      static_cast<float*>(a.out)[(size_t)pix * COUT + co] = v;
+    else
+      static_cast<bf16*>(a.out)[(size_t)pix * COUT + co] = __float2bfloat16_rn(v);
+  }
+}
+
+// Few inputs (the first layer, 4 -> 32): OS = COUT / 8 lanes per output pixel,
+// lane `part` computing outputs 8 part .. 8 part + 7 from the pixel's 9 x 4
+// inputs (one 8-byte load per tap, shared by the OS lanes).  Weights sit in
+// shared memory as FP32 [tap][ci][co]; the OS lanes of a pixel read
+// consecutive 32-byte pieces of one row.  BF16 output only, stored as one
+// 16-byte piece per lane; needs `in` 8-byte and `out` 16-byte aligned.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) conv_thin_in_kernel(const ConvFwd a) {
+  constexpr int OS = COUT / 8;
+  static_assert(CIN == 4 && COUT % 8 == 0 && (OS & (OS - 1)) == 0 && OS <= 32, "output split");
+  __shared__ __align__(16) float wsm[9 * CIN * COUT];
+  for (int i = threadIdx.x; i < 9 * COUT * CIN; i += blockDim.x) {
+    const int co = i / (9 * CIN), r = i - co * 9 * CIN;
+    wsm[r * COUT + co] = __bfloat162float(a.w[i]);
+  }
+  __syncthreads();
+  const int HH = a.Ho * a.Ho, Mtot = a.B * HH, Hv = a.Hin * a.up;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)Mtot * OS) return;
+  const int pix = (int)(t / OS), part = (int)(t % OS);
+  const int b = pix / HH, rem = pix - b * HH, oy = rem / a.Ho, ox = rem - oy * a.Ho;
+  float acc[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+  for (int ky = 0; ky < 3; ++ky) {
+    const int vy = oy * a.stride + ky - 1;
+    if (vy < 0 || vy >= Hv) continue;
+    const bf16* rowp = a.in + (size_t)(b * a.Hin + vy / a.up) * a.Hin * CIN;
+#pragma unroll
+    for (int kx = 0; kx < 3; ++kx) {
+      const int vx = ox * a.stride + kx - 1;
+      if (vx < 0 || vx >= Hv) continue;
+      const uint2 raw = __ldg(reinterpret_cast<const uint2*>(rowp + (size_t)(vx / a.up) * CIN));
+      const __nv_bfloat162* xh = reinterpret_cast<const __nv_bfloat162*>(&raw);
+      const float x[4] = {__low2float(xh[0]), __high2float(xh[0]), __low2float(xh[1]), __high2float(xh[1])};
+#pragma unroll
+      for (int ci = 0; ci < CIN; ++ci) {
+        const float4* wr = reinterpret_cast<const float4*>(&wsm[((ky * 3 + kx) * CIN + ci) * COUT + part * 8]);
+        const float4 w0 = wr[0], w1 = wr[1];
+        acc[0] = fmaf(x[ci], w0.x, acc[0]);
+        acc[1] = fmaf(x[ci], w0.y, acc[1]);
+        acc[2] = fmaf(x[ci], w0.z, acc[2]);
+        acc[3] = fmaf(x[ci], w0.w, acc[3]);
+        acc[4] = fmaf(x[ci], w1.x, acc[4]);
+        acc[5] = fmaf(x[ci], w1.y, acc[5]);
+        acc[6] = fmaf(x[ci], w1.z, acc[6]);
+        acc[7] = fmaf(x[ci], w1.w, acc[7]);
+      }
     }
   }
+  uint4 o;
+  __nv_bfloat162* oh = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float v0 = acc[2 * j] + a.bias[part * 8 + 2 * j], v1 = acc[2 * j + 1] + a.bias[part * 8 + 2 * j + 1];
+    if (a.relu) {
+      v0 = fmaxf(v0, 0.f);
+      v1 = fmaxf(v1, 0.f);
+    }
+    oh[j] = __floats2bfloat162_rn(v0, v1);
+  }
+  *reinterpret_cast<uint4*>(static_cast<bf16*>(a.out) + (size_t)pix * COUT + part * 8) = o;
 }
 
 // Split-K epilogue: partial sums added in split order, then bias and ReLU.

@@ -51,135 +51,18 @@
 
 namespace magpie_impl {
 
-constexpr int kVersion = 10200;  // 1.2.0
+constexpr int kVersion = 10300;  // 1.3.0
 
 #include "learned.cuh"
 #include "precision.cuh"
 #include "umma.cuh"
 
-// z += sum_b contrib_b / sum_b w0 over the windows covering each pixel, in
-// minibatch order (bitwise reproducible).  One block of 256 threads per
-// 16 x 16 object tile, one pixel per thread: the block first lists, in
-// minibatch order, the windows that overlap its tile (corners as recorded by
-// the window kernel; a ballot compaction over all warps); each thread then
-// walks that short list four entries at a time with predicated loads, so
-// several increments are in flight per thread.  Block (0, 0) also turns the
-// window kernel's block partials into Phi_k and ||grad Phi_k||.
-// Dynamic smem: count int2 corners + count ints.  The tile is TW x TH pixels
-// (16 x 16 for single problems; the group autotuner also tries 32 x 8 and
-// 32 x 32, four pixels per thread); every shape sums each pixel's windows in
-// minibatch order, so all give bitwise equal objects.
-constexpr int kApplyTile = 16;
-struct ApplyShape {
-  int tw, th;
-};
-constexpr ApplyShape kApplyShapes[3] = {{16, 16}, {32, 8}, {32, 32}};
-struct ApplyArgs {
-  float2* z;               // object [n_rows][n_cols]
-  int n_rows, n_cols;
-  const int2* corners;     // [count] window corners from the window kernel
-  const int32_t* idx;      // [count] window indices
-  int count, n_pos;
-  const float2* contrib;   // [count][MS][MS] increments w . Delta
-  const float* w0;         // [MS][MS] u + |Q|^2
-  int MS;
-  const double* part;      // [count][slots][2] partial sums of the window phase
-  int slots;               // partial-sum slots per window
-  double* phi_pos;         // per-window Phi_k
-  double* gn_pos;          // per-window ||grad Phi_k||
-  int tiles_x, tiles_y;    // tiles per object row and column
-  int block0;              // batched launches: first block of this problem
-};
-
-template <int TW, int TH>
-__device__ __forceinline__ void apply_body(const ApplyArgs& P, const int tx, const int ty) {
-  static_assert((TW * TH) % 256 == 0 && 256 % TW == 0, "256 threads cover the tile in whole rows");
-  constexpr int PPT = TW * TH / 256, RS = 256 / TW;  // pixels per thread, rows per pass
-  extern __shared__ int2 corner[];
-  const int count = P.count, MS = P.MS;
-  int* list = reinterpret_cast<int*>(corner + count);
-  __shared__ int warp_hits[8], n_list;
-  if (tx == 0 && ty == 0) {
-    // the window kernel's block partials -> Phi_k and ||grad Phi_k||, in block order
-    for (int b = threadIdx.x; b < count; b += blockDim.x) {
-      const int k = P.idx[b];
-      if ((unsigned)k >= (unsigned)P.n_pos) continue;
-      double a = 0.0, g = 0.0;
-      for (int q = 0; q < P.slots; ++q) {
-        a += P.part[(size_t)(b * P.slots + q) * 2];
-        g += P.part[(size_t)(b * P.slots + q) * 2 + 1];
-      }
-      P.phi_pos[k] = a / (2.0 * (double)MS * (double)MS);
-      P.gn_pos[k] = sqrt(g);
-    }
-  }
-  const int R0 = ty * TH, C0 = tx * TW;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  // windows meeting this tile, listed in minibatch order: every warp takes
-  // 32 consecutive windows per round, ballots, and the rounds are stitched
-  // together by per-warp counts
-  int base = 0;
-  for (int b0 = 0; b0 < count; b0 += 256) {
-    const int b = b0 + threadIdx.x;
-    bool hit = false;
-    if (b < count) {
-      const int2 q = P.corners[b];
-      corner[b] = q;
-      hit = q.x < R0 + TH && q.x + MS > R0 && q.y < C0 + TW && q.y + MS > C0;
-    }
-    const unsigned mask = __ballot_sync(0xffffffffu, hit);
-    if (lane == 0) warp_hits[wid] = __popc(mask);
-    __syncthreads();
-    int off = base;
-    for (int i = 0; i < wid; ++i) off += warp_hits[i];
-    if (hit) list[off + __popc(mask & ((1u << lane) - 1u))] = b;
-    int tot = 0;
-    for (int i = 0; i < 8; ++i) tot += warp_hits[i];
-    base += tot;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) n_list = base;
-  __syncthreads();
-  const int nl = n_list;
-  const size_t M = (size_t)MS * MS;
-#pragma unroll 1
-  for (int pp = 0; pp < PPT; ++pp) {
-    const int r = R0 + (int)(threadIdx.x / TW) + pp * RS, c = C0 + (int)(threadIdx.x % TW);
-    if (r >= P.n_rows || c >= P.n_cols) continue;
-    float nx = 0.f, ny = 0.f, d = 0.f;
-    for (int j0 = 0; j0 < nl; j0 += kApplyUnroll) {
-      float2 v[kApplyUnroll];
-      float wv[kApplyUnroll];
-#pragma unroll
-      for (int u = 0; u < kApplyUnroll; ++u) {
-        const int j = j0 + u;
-        const int b = j < nl ? list[j] : 0;
-        const int2 q = corner[b];
-        const int dr = r - q.x, dc = c - q.y;
-        const bool in = j < nl && (unsigned)dr < (unsigned)MS && (unsigned)dc < (unsigned)MS;
-        const int o = in ? dr * MS + dc : 0;
-        v[u] = in ? P.contrib[(size_t)b * M + o] : make_float2(0.f, 0.f);
-        wv[u] = in ? __ldg(&P.w0[o]) : 0.f;
-      }
-#pragma unroll
-      for (int u = 0; u < kApplyUnroll; ++u) {
-        nx += v[u].x;
-        ny += v[u].y;
-        d += wv[u];
-      }
-    }
-    if (d > 0.f) {
-      const size_t p = (size_t)r * P.n_cols + c;
-      float2 zz = P.z[p];
-      zz.x += nx / d;
-      zz.y += ny / d;
-      P.z[p] = zz;
-    }
-  }
-}
-
 // One problem: a 2-D grid of tiles.
+// Launched as a programmatic dependent of the window kernel (its blocks, let
+// in early, would slow the next window kernel: 0.328 against 0.319 ms per
+// sweep, so it does not trigger its dependents).
 __global__ void __launch_bounds__(256) apply_kernel(ApplyArgs P) {
+  grid_dep_wait();
   apply_body<kApplyTile, kApplyTile>(P, blockIdx.x, blockIdx.y);
 }
 
@@ -212,6 +95,7 @@ __global__ void __launch_bounds__(256) accum_apply_kernel(float2* __restrict__ z
                                                           size_t npix, const int32_t* __restrict__ idx, int count,
                                                           int n_pos, const double* __restrict__ part, int slots,
                                                           int MS, double* phi_pos, double* gn_pos) {
+  grid_dep_wait();  // launched as a programmatic dependent of the window kernel
   if (blockIdx.x == 0) {
     for (int b = threadIdx.x; b < count; b += blockDim.x) {
       const int k = idx[b];
@@ -576,8 +460,7 @@ cudaError_t launch_apply(float2* z, int n_rows, int n_cols, const int2* corners,
   const ApplyArgs P =
       apply_args(z, n_rows, n_cols, corners, idx, count, n_pos, contrib, w0, MS, part, phi_pos, gn_pos, slots);
   const dim3 tiles(P.tiles_x, (n_rows + kApplyTile - 1) / kApplyTile);
-  apply_kernel<<<tiles, 256, (sizeof(int2) + sizeof(int)) * count, st>>>(P);
-  return cudaGetLastError();
+  return launch_ex(apply_kernel, tiles, dim3(256), (sizeof(int2) + sizeof(int)) * count, st, 1, true, P);
 }
 
 template <int MODE>
@@ -671,6 +554,53 @@ struct GroupApplyLaunch {
   int blocks;     // total tiles
   int max_count;  // largest window count (shared memory)
 };
+// One launch of the persistent form: the members of one window side at one
+// batched step, their windows and then their update tiles.
+struct GroupPersistLaunch {
+  int ms;         // window side
+  int map_off;    // first window item (entries of the group's map and wmember)
+  int nw;         // window items
+  int tab_off;    // first entry of its update table
+  int na;         // members
+  int ntiles;     // update tiles
+  int q_off;      // its queue counter in the counter buffer, followed by na done counters
+  int max_count;  // largest window count of its members
+  int clusters;   // its grid (set by plan_persistent)
+};
+
+// threads per block of the window kernels of side m
+int window_threads(int m) {
+  switch (m) {
+#define MAGPIE_CASE(S) \
+  case S:              \
+    return Geo<S>::T;
+    MAGPIE_WINDOW_SIZES(MAGPIE_CASE)
+#undef MAGPIE_CASE
+    default: return 0;
+  }
+}
+
+cudaError_t launch_persistent_m(int MS, const PersistArgs& P, int clusters, int max_count, cudaStream_t st, int minb) {
+  switch (MS) {
+#define MAGPIE_CASE(S) \
+  case S:              \
+    return window_launch_persistent<S>(P, clusters, max_count, st, minb);
+    MAGPIE_WINDOW_SIZES(MAGPIE_CASE)
+#undef MAGPIE_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int persistent_capacity_m(int MS, int max_count, int minb) {
+  switch (MS) {
+#define MAGPIE_CASE(S) \
+  case S:              \
+    return window_persistent_capacity<S>(max_count, minb);
+    MAGPIE_WINDOW_SIZES(MAGPIE_CASE)
+#undef MAGPIE_CASE
+    default: return 0;
+  }
+}
 
 }  // namespace magpie_impl
 
@@ -696,6 +626,20 @@ struct magpie_group {
   // the measured ms per launch of batched step 0 for each shape
   int apply_shape = 0;
   float apply_ms[3] = {};
+  // persistent form: per batched step, one launch per window side (the
+  // sides' launches run concurrently), windows and updates from a work queue
+  std::vector<std::vector<GroupPersistLaunch>> pl;  // per batched step
+  std::vector<ApplyArgs> ptable_host;                // update tables of the persistent launches
+  ApplyArgs* ptable = nullptr;
+  int* wmember = nullptr;     // member (within its launch) of every window item, aligned with map
+  int* qbuf = nullptr;        // queue and done counters of every launch, zeroed at the start of a sweep
+  size_t qbuf_n = 0;
+  int* err = nullptr;         // bit 3: a dependency wait of the persistent form ran out
+  cudaStream_t side[6] = {};  // streams of the concurrent per-side launches (side[0] unused)
+  cudaEvent_t fork = nullptr, join[6] = {};
+  int persistent = 0;         // 1: sweeps use the persistent form (chosen by the autotuner)
+  float form_ms[2] = {};      // autotuner: batched step 0 as separate launches (0) and persistent (1)
+  unsigned long long limit_ns = 1000000000ull;  // bound of each dependency wait
 };
 
 // The network of the learned coarse correction with its training state.
@@ -851,9 +795,15 @@ ConvPlan conv_plan(const ConvFwd& a) {
 // Layers the tcgen05 convolution serves: whole 64-element K steps inside one
 // tap (Cin a multiple of 64) and whole 64-wide N tiles.
 bool conv_tc_fits(const ConvFwd& a) { return a.Cin % 64 == 0 && a.Cout % 64 == 0; }
-// Thin layers the direct FP32-FMA kernel serves: the network's first (4 -> 32)
-// and last (64 -> 2) convolutions.
-bool conv_direct_fits(const ConvFwd& a) { return (a.Cin == 4 && a.Cout == 32) || (a.Cin == 64 && a.Cout == 2); }
+// Thin layers the direct FP32-FMA kernels serve: the network's first (4 -> 32,
+// BF16 output) and last (64 -> 2) convolutions, with the alignment their
+// 16-byte (8-byte) loads and stores need.
+bool conv_direct_fits(const ConvFwd& a) {
+  const auto al = [](const void* p, uintptr_t n) { return ((uintptr_t)p & (n - 1)) == 0; };
+  if (a.Cin == 64 && a.Cout == 2) return al(a.in, 16);
+  if (a.Cin == 4 && a.Cout == 32) return !a.out_f32 && al(a.in, 8) && al(a.out, 16);
+  return false;
+}
 
 // Tiles of the tcgen05 convolution: 128 output pixels x 128 (or 64) output
 // channels, K split so that about two blocks per SM run, at least two K steps
@@ -926,16 +876,11 @@ cudaError_t launch_conv(const ConvFwd& a0, float* part, cudaStream_t st, int ten
   a.part = pl.splits > 1 ? part : nullptr;
   const dim3 grid(pl.gx, pl.gy, pl.splits);
   if (tensor_path == 1 && conv_direct_fits(a)) {
-    const size_t smem = sizeof(float) * a.Cout * a.K;
-    const int rows = a.B * a.Ho;
-    if (a.Cin == 64 && a.Cout == 2) {  // 8 pixels per thread (Ho = h >= 8)
-      const int n = rows * (a.Ho / 8);
-      conv_direct_kernel<64, 2, 8><<<(n + 255) / 256, 256, smem, st>>>(a);
-    } else if (a.Cin == 4 && a.Cout == 32) {  // 2 pixels per thread
-      const int n = rows * (a.Ho / 2);
-      conv_direct_kernel<4, 32, 2><<<(n + 255) / 256, 256, smem, st>>>(a);
-    } else {
-      return cudaErrorInvalidValue;
+    const long long pixels = (long long)a.B * a.Ho * a.Ho;
+    if (a.Cin == 64) {  // 8 lanes per pixel
+      conv_thin_out_kernel<64, 2><<<(int)((pixels * 8 + 255) / 256), 256, 0, st>>>(a);
+    } else {  // 4 lanes per pixel
+      conv_thin_in_kernel<4, 32><<<(int)((pixels * 4 + 255) / 256), 256, 0, st>>>(a);
     }
     return cudaGetLastError();
   }
@@ -1243,9 +1188,8 @@ int enqueue_step(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st, 
   if (atom) {
     const size_t npix = (size_t)c->p.n_rows * c->p.n_cols;
     const unsigned blocks = (unsigned)std::min<size_t>((npix + 255) / 256, 152 * 8);
-    accum_apply_kernel<<<blocks, 256, 0, st>>>(c->z, c->acc, npix, idx, count, c->p.n_pos, c->part,
-                                               cluster_of(c->p.m), c->p.m, c->phi_pos, c->gn_pos);
-    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(launch_ex(accum_apply_kernel, dim3(blocks), dim3(256), 0, st, 1, true, c->z, c->acc, npix, idx, count,
+                       c->p.n_pos, (const double*)c->part, cluster_of(c->p.m), c->p.m, c->phi_pos, c->gn_pos));
   } else {
     CUDA_TRY(launch_apply(c->z, c->p.n_rows, c->p.n_cols, c->corner, idx, count, c->p.n_pos, c->contrib,
                           c->pyr + c->M, c->p.m, c->part, c->phi_pos, c->gn_pos, st,
@@ -1514,6 +1458,122 @@ int group_tune_apply(magpie_group* g, cudaStream_t st, cudaEvent_t e0, cudaEvent
   return MAGPIE_OK;
 }
 
+// Grid of every launch of the persistent form: as many clusters as fit on
+// the GPU at once with the side's register bound, at most one per item.
+// Called outside stream capture (the occupancy queries).
+int plan_persistent(magpie_group* g) {
+  for (auto& Ls : g->pl)
+    for (auto& L : Ls) {
+      const int CL = cluster_of(L.ms);
+      const int items = L.nw + (L.ntiles + CL - 1) / CL;
+      const int cap = persistent_capacity_m(L.ms, L.max_count, g->minb[ilog2(L.ms) - 3]);
+      if (cap < 1) return fail(MAGPIE_ECUDA, "persistent step kernel: no cluster of it fits on the GPU");
+      L.clusters = std::min(cap, items);
+    }
+  return MAGPIE_OK;
+}
+
+// Batched step t of the persistent form on stream st: one launch per window
+// side, forked onto the group's side streams and joined back so that the
+// sides run concurrently.  ptab: the update table (the group's own, or the
+// autotuner's scratch copy); bias: added to every dependency-wait target.
+// The step's counters in qbuf must be zero.
+int enqueue_persistent_step(magpie_group* g, size_t t, cudaStream_t st, const ApplyArgs* ptab, int bias) {
+  const auto& Ls = g->pl[t];
+  if (Ls.size() > 1) CUDA_TRY(cudaEventRecord(g->fork, st));
+  for (size_t j = 0; j < Ls.size(); ++j) {
+    const GroupPersistLaunch& L = Ls[j];
+    cudaStream_t s = j == 0 ? st : g->side[j];
+    if (j > 0) CUDA_TRY(cudaStreamWaitEvent(s, g->fork, 0));
+    PersistArgs P{};
+    P.table = g->table;
+    P.map = g->map + L.map_off;
+    P.wmember = g->wmember + L.map_off;
+    P.atab = ptab + L.tab_off;
+    P.nw = L.nw;
+    P.na = L.na;
+    P.ntiles = L.ntiles;
+    P.head = g->qbuf + L.q_off;
+    P.done = P.head + 1;
+    P.err = g->err;
+    P.limit_ns = g->limit_ns;
+    P.bias = bias;
+    CUDA_TRY(launch_persistent_m(L.ms, P, L.clusters, L.max_count, s, g->minb[ilog2(L.ms) - 3]));
+    if (j > 0) {
+      CUDA_TRY(cudaEventRecord(g->join[j], s));
+      CUDA_TRY(cudaStreamWaitEvent(st, g->join[j], 0));
+    }
+  }
+  return MAGPIE_OK;
+}
+
+// Times batched step 0 as separate launches (the batched window kernels and
+// the update kernel with the tuned tile shape) and in the persistent form,
+// one warm-up and three timed runs each, with the updates writing scratch
+// copies of the members' objects, and keeps the faster form for the sweeps.
+int group_tune_form(magpie_group* g, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+  if (g->pl.empty() || g->al[0].empty() || g->wl.empty()) return MAGPIE_OK;
+  int rc = plan_persistent(g);
+  if (rc) return rc;
+  size_t total = 0;
+  for (auto* c : g->members) total += (size_t)c->p.n_rows * c->p.n_cols;
+  const GroupApplyLaunch& A = g->al[g->apply_shape][0];
+  int np = 0;
+  for (const auto& L : g->pl[0]) np = std::max(np, L.tab_off + L.na);
+  float2* scratch = nullptr;
+  ApplyArgs *atab = nullptr, *ptab = nullptr;
+  cudaError_t e = cudaMalloc(&scratch, sizeof(float2) * total);
+  if (e == cudaSuccess) e = cudaMalloc(&atab, sizeof(ApplyArgs) * A.n);
+  if (e == cudaSuccess) e = cudaMalloc(&ptab, sizeof(ApplyArgs) * np);
+  if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, sizeof(float2) * total, st);
+  std::vector<ApplyArgs> at(g->atable_host[g->apply_shape].begin() + A.tab_off,
+                            g->atable_host[g->apply_shape].begin() + A.tab_off + A.n);
+  std::vector<ApplyArgs> pt(g->ptable_host.begin(), g->ptable_host.begin() + np);
+  for (auto* v : {&at, &pt}) {
+    size_t off = 0;
+    for (auto& P : *v) {
+      P.z = scratch + off;
+      off += (size_t)P.n_rows * P.n_cols;
+    }
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(atab, at.data(), sizeof(ApplyArgs) * at.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ptab, pt.data(), sizeof(ApplyArgs) * pt.size(), cudaMemcpyHostToDevice, st);
+  auto run = [&](int form) -> int {
+    if (form == 0) {
+      for (const auto& L : g->wl[0]) {
+        cudaError_t le = launch_window_batched_m<kStep>(L.ms, g->table, g->map + L.map_off, L.windows, st,
+                                                        g->minb[ilog2(L.ms) - 3]);
+        if (le != cudaSuccess) return fail(MAGPIE_ECUDA, std::string("group autotuner: ") + cudaGetErrorString(le));
+      }
+      CUDA_TRY(launch_apply_batched(g, g->apply_shape, 0, st, atab));
+      return MAGPIE_OK;
+    }
+    CUDA_TRY(cudaMemsetAsync(g->qbuf, 0, sizeof(int) * g->qbuf_n, st));
+    return enqueue_persistent_step(g, 0, st, ptab, 0);
+  };
+  for (int form = 0; form < 2 && e == cudaSuccess && !rc; ++form) {
+    rc = run(form);
+    if (!rc) e = cudaEventRecord(e0, st);
+    for (int r = 0; r < 3 && e == cudaSuccess && !rc; ++r) rc = run(form);
+    if (!rc && e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (!rc && e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (!rc && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    g->form_ms[form] = ms / 3.f;
+  }
+  if (!rc && e == cudaSuccess) e = cudaStreamSynchronize(st);
+  int h = 0;
+  if (!rc && e == cudaSuccess) e = cudaMemcpy(&h, g->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (scratch) cudaFree(scratch);
+  if (atab) cudaFree(atab);
+  if (ptab) cudaFree(ptab);
+  if (rc) return rc;
+  if (e != cudaSuccess) return fail(MAGPIE_ECUDA, std::string("group autotuner (form): ") + cudaGetErrorString(e));
+  if (h) return fail(MAGPIE_ETIMEOUT, "group autotuner: a dependency wait of the persistent form ran out");
+  g->persistent = g->form_ms[1] < g->form_ms[0] ? 1 : 0;
+  return MAGPIE_OK;
+}
+
 int group_autotune(magpie_group* g) {
   cudaStream_t st = g->stream;
   for (auto* c : g->members)
@@ -1552,6 +1612,7 @@ int group_autotune(magpie_group* g) {
     }
   int rc = MAGPIE_OK;
   if (e == cudaSuccess) rc = group_tune_apply(g, st, e0, e1);
+  if (e == cudaSuccess && !rc) rc = group_tune_form(g, st, e0, e1);
   cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (e != cudaSuccess) return fail(MAGPIE_ECUDA, std::string("group autotuner: ") + cudaGetErrorString(e));
@@ -1930,6 +1991,14 @@ void magpie_group_destroy(magpie_group* g) {
   if (g->map) cudaFree(g->map);
   for (auto* a : g->atable)
     if (a) cudaFree(a);
+  void* bufs[] = {g->ptable, g->wmember, g->qbuf, g->err};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  for (int j = 0; j < 6; ++j) {
+    if (g->side[j]) cudaStreamDestroy(g->side[j]);
+    if (g->join[j]) cudaEventDestroy(g->join[j]);
+  }
+  if (g->fork) cudaEventDestroy(g->fork);
   delete g;
 }
 
@@ -1949,6 +2018,8 @@ int magpie_group_create(magpie_group** out, magpie_ctx* const* ctxs, int32_t n, 
   g->stream = (cudaStream_t)stream;
   std::vector<StepArgs> table;
   std::vector<int2> map;
+  std::vector<int> wmem;
+  int q_total = 0, max_sides = 0;
   int steps = 0;
   for (auto* c : g->members) steps = std::max(steps, n_steps(c));
   for (int t = 0; t < steps; ++t) {
@@ -1960,18 +2031,39 @@ int magpie_group_create(magpie_group** out, magpie_ctx* const* ctxs, int32_t n, 
       table.push_back(make_args(c, c->order + (size_t)t * c->p.minibatch));
     }
     std::vector<GroupWindowLaunch> wls;
+    std::vector<GroupPersistLaunch> pls;
     for (int ms : {8, 16, 32, 64, 128, 256}) {
       GroupWindowLaunch L{ms, (int)map.size(), 0};
+      GroupPersistLaunch PL{ms, (int)map.size(), 0, (int)g->ptable_host.size(), 0, 0, q_total, 0, 0};
+      const int pt = window_threads(ms) >= 256 ? 32 : 16;  // the persistent kernel's update tile
       for (int i = 0; i < n; ++i) {
         magpie_ctx* c = g->members[i];
         if (entry[i] < 0 || c->p.m != ms) continue;
         const int cnt = std::min(c->p.minibatch, c->p.n_pos - t * c->p.minibatch);
-        for (int w = 0; w < cnt; ++w) map.push_back(make_int2(entry[i], w));
+        for (int w = 0; w < cnt; ++w) {
+          map.push_back(make_int2(entry[i], w));
+          wmem.push_back(PL.na);
+        }
         L.windows += cnt;
+        ApplyArgs P = apply_args(c->z, c->p.n_rows, c->p.n_cols, c->corner, c->order + (size_t)t * c->p.minibatch,
+                                 cnt, c->p.n_pos, c->contrib, c->pyr + c->M, c->p.m, c->part, c->phi_pos,
+                                 c->gn_pos, 0, ApplyShape{pt, pt});
+        P.block0 = PL.ntiles;
+        PL.ntiles += apply_tiles(P);
+        PL.max_count = std::max(PL.max_count, cnt);
+        ++PL.na;
+        g->ptable_host.push_back(P);
       }
-      if (L.windows) wls.push_back(L);
+      if (L.windows) {
+        wls.push_back(L);
+        PL.nw = L.windows;
+        q_total += 1 + PL.na;
+        pls.push_back(PL);
+      }
     }
     g->wl.push_back(wls);
+    max_sides = std::max(max_sides, (int)pls.size());
+    g->pl.push_back(pls);
     for (int v = 0; v < 3; ++v) {
       std::vector<ApplyArgs>& at = g->atable_host[v];
       GroupApplyLaunch A{(int)at.size(), 0, 0, 0};
@@ -2008,10 +2100,23 @@ int magpie_group_create(magpie_group** out, magpie_ctx* const* ctxs, int32_t n, 
   for (int v = 0; v < 3; ++v)
     if ((rc = upload((void**)&g->atable[v], g->atable_host[v].data(), sizeof(ApplyArgs) * g->atable_host[v].size())))
       return rc;
-  cudaError_t e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
+  if ((rc = upload((void**)&g->ptable, g->ptable_host.data(), sizeof(ApplyArgs) * g->ptable_host.size())) ||
+      (rc = upload((void**)&g->wmember, wmem.data(), sizeof(int) * wmem.size())))
+    return rc;
+  g->qbuf_n = (size_t)q_total;
+  cudaError_t e = cudaMalloc(&g->qbuf, sizeof(int) * g->qbuf_n);
+  if (e == cudaSuccess) e = cudaMalloc(&g->err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(g->err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess && max_sides > 1) e = cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming);
+  for (int j = 1; j < max_sides && e == cudaSuccess; ++j) {
+    e = cudaStreamCreateWithFlags(&g->side[j], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->join[j], cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
     magpie_group_destroy(g);
-    return fail(MAGPIE_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+    return fail(e == cudaErrorMemoryAllocation ? MAGPIE_ENOMEM : MAGPIE_ECUDA,
+                std::string("group setup: ") + cudaGetErrorString(e));
   }
   rc = group_autotune(g);
   if (rc) {
@@ -2028,19 +2133,36 @@ int magpie_group_sweep(magpie_group* g, const int32_t* const* orders) {
   for (size_t i = 0; i < g->members.size(); ++i)
     if (!orders[i]) return fail(MAGPIE_EINVAL, "order " + std::to_string(i) + " is NULL");
   if (!g->graph) {
+    if (g->persistent) {
+      const int rc = plan_persistent(g);
+      if (rc) return rc;
+    }
     cudaGraph_t gr = nullptr;
     CUDA_TRY(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    for (size_t t = 0; t < g->wl.size() && e == cudaSuccess; ++t) {
-      for (const auto& L : g->wl[t]) {
-        e = launch_window_batched_m<kStep>(L.ms, g->table, g->map + L.map_off, L.windows, g->cap_stream,
-                                           g->minb[ilog2(L.ms) - 3]);
+    int rc = MAGPIE_OK;
+    if (g->persistent) {
+      // the counters of every step's launches start at zero; one step after
+      // another, its sides' launches concurrent
+      e = cudaMemsetAsync(g->qbuf, 0, sizeof(int) * g->qbuf_n, g->cap_stream);
+      for (size_t t = 0; t < g->pl.size() && e == cudaSuccess && !rc; ++t)
+        rc = enqueue_persistent_step(g, t, g->cap_stream, g->ptable, 0);
+    } else {
+      for (size_t t = 0; t < g->wl.size() && e == cudaSuccess; ++t) {
+        for (const auto& L : g->wl[t]) {
+          e = launch_window_batched_m<kStep>(L.ms, g->table, g->map + L.map_off, L.windows, g->cap_stream,
+                                             g->minb[ilog2(L.ms) - 3]);
+          if (e != cudaSuccess) break;
+        }
         if (e != cudaSuccess) break;
+        e = launch_apply_batched(g, g->apply_shape, t, g->cap_stream);
       }
-      if (e != cudaSuccess) break;
-      e = launch_apply_batched(g, g->apply_shape, t, g->cap_stream);
     }
     cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &gr);
+    if (rc) {
+      if (gr) cudaGraphDestroy(gr);
+      return rc;
+    }
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&g->graph, gr, 0);
     if (gr) cudaGraphDestroy(gr);
@@ -2378,6 +2500,61 @@ int magpie_group_set_apply_shape(magpie_group* g, int32_t shape) {
     g->graph = nullptr;
   }
   return MAGPIE_OK;
+}
+
+int magpie_group_form_tuning(magpie_group* g, int32_t* persistent, float* ms) {
+  if (!g || !persistent || !ms) return fail(MAGPIE_EINVAL, "NULL argument");
+  *persistent = g->persistent;
+  ms[0] = g->form_ms[0];
+  ms[1] = g->form_ms[1];
+  return MAGPIE_OK;
+}
+
+int magpie_group_set_persistent(magpie_group* g, int32_t persistent) {
+  if (!g || (persistent != 0 && persistent != 1)) return fail(MAGPIE_EINVAL, "need a group and 0 or 1");
+  g->persistent = persistent;
+  if (g->graph) {
+    cudaGraphExecDestroy(g->graph);
+    g->graph = nullptr;
+  }
+  return MAGPIE_OK;
+}
+
+int magpie_group_set_wait_limit(magpie_group* g, double seconds) {
+  if (!g || !(seconds >= 1e-6 && seconds <= 60.0)) return fail(MAGPIE_EINVAL, "need a group and a limit in [1e-6, 60] s");
+  g->limit_ns = (unsigned long long)(seconds * 1e9);
+  if (g->graph) {
+    cudaGraphExecDestroy(g->graph);
+    g->graph = nullptr;
+  }
+  return MAGPIE_OK;
+}
+
+int magpie_group_status(magpie_group* g) {
+  if (!g) return fail(MAGPIE_EINVAL, "NULL group");
+  int h = 0;
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  CUDA_TRY(cudaMemcpy(&h, g->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    CUDA_TRY(cudaMemset(g->err, 0, sizeof(int)));
+    return fail(MAGPIE_ETIMEOUT, "a dependency wait of the persistent step kernel ran out; its update tile was skipped");
+  }
+  return MAGPIE_OK;
+}
+
+int magpie_group_check_waits(magpie_group* g, double seconds) {
+  if (!g || !(seconds >= 1e-6 && seconds <= 10.0)) return fail(MAGPIE_EINVAL, "need a group and a limit in [1e-6, 10] s");
+  int rc = plan_persistent(g);
+  if (rc) return rc;
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  const unsigned long long keep = g->limit_ns;
+  g->limit_ns = (unsigned long long)(seconds * 1e9);
+  cudaError_t e = cudaMemsetAsync(g->qbuf, 0, sizeof(int) * g->qbuf_n, g->stream);
+  if (e == cudaSuccess) rc = enqueue_persistent_step(g, 0, g->stream, g->ptable, 1);
+  g->limit_ns = keep;
+  CUDA_TRY(e);
+  if (rc) return rc;
+  return magpie_group_status(g);
 }
 
 int magpie_group_set_minb(magpie_group* g, int32_t m, int32_t minb) {

@@ -1,7 +1,7 @@
 // precision.cuh -- the precision form of the sweep: the windows' 2-D DFTs as
 // tensor-core GEMMs with BF16 hi+lo split operands and FP32 accumulation,
 // around the same projection, V-cycle and update as the FP32 path.  Included
-// by magpie.cu inside its anonymous namespace.
+// by magpie.cu inside namespace magpie_impl.
 //
 // An m-point line DFT (m = 16 Qr, Qr in {4, 8, 16}) is done as two small
 // complex matrix products (Cooley-Tukey with n = Qr n1 + n2, k = k1 + 16 k2):

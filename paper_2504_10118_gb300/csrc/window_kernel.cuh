@@ -1,6 +1,7 @@
 // window_kernel.cuh -- the per-window kernel of the MAGPIE sweep (gather,
-// 2-D FFT, modulus projection, inverse FFT, MAGPS V-cycle) and its level
-// factor layout.  Included by magpie.cu inside its anonymous namespace.
+// 2-D FFT, modulus projection, inverse FFT, MAGPS V-cycle), its level factor
+// layout, and the persistent step kernel of context groups.  Included by
+// core.cuh inside namespace magpie_impl.
 #pragma once
 
 // Offset of level-l (l >= 1) factor arrays in the float pyramid buffer:
@@ -135,6 +136,17 @@ __device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
   return f2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
 }
 
+// One up-pass entry: e = g / w + (u / w) P(e_coarse), i.e. g * iw + rr * p,
+// with the rounding spelled out (the product g * iw rounded, the other fused
+// into the add), so that every kernel the V-cycle is compiled into gives
+// the same bits (left to the compiler, either product could be the fused
+// one, and the choice followed the surrounding kernel).
+__device__ __forceinline__ float2 prolong(float2 g, float iw, float rr, float2 p) {
+  return f2(__fmaf_rn(rr, p.x, __fmul_rn(g.x, iw)), __fmaf_rn(rr, p.y, __fmul_rn(g.y, iw)));
+}
+// a * s with each product rounded (never fused into a later add)
+__device__ __forceinline__ float2 cscale_rn(float2 a, float s) { return f2(__fmul_rn(a.x, s), __fmul_rn(a.y, s)); }
+
 // MAGPS V-cycle of one window in residual form, on this block's column slab
 // Y (g^0 for MS rows x SLAB columns).  Lane gamma of a warp owns column
 // gamma of a strip of 2^TT rows; the 2x2 restrictions pair columns by warp
@@ -172,7 +184,7 @@ __device__ __forceinline__ void vcycle(const float2* Y, float2* lvl, const float
       float2 v = cadd(g0[2 * a], g0[2 * a + 1]);
       v = cadd(v, shfl_xor2(v, 1));
       const float w = ok ? __ldg(&wu1[(R0 / 2 + a) * (MS / 2) + (cgl >> 1)]) : 0.f;
-      g1[a] = cscale(v, 0.25f * w);
+      g1[a] = cscale_rn(v, 0.25f * w);  // rounded products: their sum below is never fused
     }
     if constexpr (TT == 1) {
       return g1[0];
@@ -262,9 +274,7 @@ __device__ __forceinline__ void vcycle(const float2* Y, float2* lvl, const float
             const float* rr = iw + n * n;
             for (int i = 0; i < n * n; ++i) {
               const int r = i / n, c = i % n;
-              const float2 p = pe[(r >> 1) * nc + (c >> 1)];
-              const float2 v = cscale(a[i], iw[i]);
-              a[i] = f2(v.x + rr[i] * p.x, v.y + rr[i] * p.y);
+              a[i] = prolong(a[i], iw[i], rr[i], pe[(r >> 1) * nc + (c >> 1)]);
             }
           }
           for (int qq = 0; qq < CL; ++qq) {
@@ -286,10 +296,7 @@ __device__ __forceinline__ void vcycle(const float2* Y, float2* lvl, const float
       for (int i = tid; i < rows * cols; i += T) {
         const int r = i / cols, c = i - (i / cols) * cols;
         const int o = r * (MS >> l) + q * cols + c;
-        const float2 p = pe[(r >> 1) * cc + (c >> 1)];
-        const float2 v = cscale(a[i], __ldg(&iw[o]));
-        const float w = __ldg(&rr[o]);
-        a[i] = f2(v.x + w * p.x, v.y + w * p.y);
+        a[i] = prolong(a[i], __ldg(&iw[o]), __ldg(&rr[o]), pe[(r >> 1) * cc + (c >> 1)]);
       }
       __syncthreads();
     }
@@ -314,9 +321,7 @@ __device__ __forceinline__ void vcycle(const float2* Y, float2* lvl, const float
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
         const int o = (R0 / 2 + a) * (MS / 2) + (cgl >> 1);
-        const float2 v = cscale(g1[a], ok ? __ldg(&iw1[o]) : 0.f);
-        const float w = ok ? __ldg(&rr1[o]) : 0.f;
-        e1[a] = f2(v.x + w * eT.x, v.y + w * eT.y);
+        e1[a] = prolong(g1[a], ok ? __ldg(&iw1[o]) : 0.f, ok ? __ldg(&rr1[o]) : 0.f, eT);
       }
     }
     if (ok) {
@@ -350,4 +355,120 @@ __global__ void __launch_bounds__(Geo<MS>::T, MINB)
   const StepArgs& A = args;
   const int win = ent.y;
 #include "window_body.inc"
+}
+
+// ---- persistent minibatch step of a context group (the members of one
+// window side): one launch takes the step's windows and then the members'
+// update tiles from a device work queue.  Items are handed out in index order,
+// windows first; a cluster fetches its next item while it works on the
+// current one.  An update tile waits (bounded) until every block of its
+// member's windows has counted itself done, so a member's update overlaps
+// the other members' windows.  Every window item has been handed out to a
+// running cluster, and one that holds a window never waits, before any
+// cluster takes an update item: the waits always end unless the launch is
+// broken, and then they run out.
+struct PersistArgs {
+  const StepArgs* table;         // per (batched step, member) entries
+  const int2* map;               // [nw] window items: (table entry, window slot)
+  const int* wmember;            // [nw] the item's member, 0 .. na - 1
+  const ApplyArgs* atab;         // [na] the members' updates; block0 = first tile of each
+  int nw, na, ntiles;            // window items, members, update tiles
+  int* head;                     // work-queue counter, zero before the launch
+  int* done;                     // [na] blocks finished on each member's windows, zero before the launch
+  int* err;                      // bit 3: a dependency wait ran out (its tile is skipped)
+  unsigned long long limit_ns;   // bound of each dependency wait
+  int bias;                      // added to every wait target: 1 makes every wait run out (a self-test)
+};
+
+constexpr int kMaxSpins = 1 << 26;  // backstop of the time bound of a dependency wait
+
+// Thread 0's wait until *ctr >= target (acquire), for at most limit_ns of
+// %globaltimer time or kMaxSpins polls; returns 0 and sets err bit 3 when
+// it runs out.
+__device__ __forceinline__ int wait_count(const int* ctr, int target, unsigned long long limit_ns, int* err) {
+  unsigned long long t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (int i = 0; i < kMaxSpins; ++i) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+    if (v >= target) return 1;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > limit_ns) break;
+    __nanosleep(256);
+  }
+  atomicOr(err, 8);
+  return 0;
+}
+
+// Update tile of the persistent step: 32 x 32 pixels for blocks of 256 or
+// more threads, 16 x 16 below.
+template <int NT>
+struct PersistTile {
+  static constexpr int TW = NT >= 256 ? 32 : 16, TH = TW;
+};
+
+// Update tile t of the persistent step, after its member's windows (a
+// separate function, so that its registers do not add to the window path's).
+template <int MS>
+__device__ __noinline__ void persistent_update(const PersistArgs& P, int t) {
+  constexpr int CL = Geo<MS>::CL, NT = Geo<MS>::T;
+  __shared__ int ready;
+  int lo = 0, hi = P.na - 1;
+  while (lo < hi) {  // last member whose first tile is <= t
+    const int mid = (lo + hi + 1) >> 1;
+    if (P.atab[mid].block0 <= t)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const ApplyArgs& U = P.atab[lo];
+  if (threadIdx.x == 0) ready = wait_count(&P.done[lo], U.count * CL + P.bias, P.limit_ns, P.err);
+  __syncthreads();
+  if (ready) {
+    const int lt = t - U.block0;
+    apply_body<PersistTile<NT>::TW, PersistTile<NT>::TH, NT>(U, lt % U.tiles_x, lt / U.tiles_x);
+  }
+}
+
+// Window item of the persistent step (a separate function: the window
+// path keeps the register allocation it has in the other window kernels).
+template <int MS>
+__device__ __noinline__ void persistent_window(const StepArgs& A, const int win) {
+  constexpr int MODE = kStep;
+#include "window_body.inc"
+}
+
+template <int MS, int MINB>
+__global__ void __launch_bounds__(Geo<MS>::T, MINB) window_kernel_persistent(const PersistArgs P) {
+  constexpr int CL = Geo<MS>::CL;
+  __shared__ StepArgs args;
+  __shared__ int next[2];
+  int rank = 0;
+  if constexpr (CL > 1) rank = (int)cg::this_cluster().block_rank();
+  const bool leader = rank == 0 && threadIdx.x == 0;
+  const int items = P.nw + (P.ntiles + CL - 1) / CL;
+  if (leader) next[0] = atomicAdd(P.head, 1);
+  window_sync<CL>();
+  int item = *peer<CL>(&next[0], 0);
+  for (int it = 0; item < items; ++it) {
+    if (leader) next[(it + 1) & 1] = atomicAdd(P.head, 1);
+    if (item < P.nw) {
+      const int2 ent = P.map[item];
+      if (threadIdx.x == 0) args = P.table[ent.x];
+      __syncthreads();
+      persistent_window<MS>(args, ent.y);
+      // this block's increments, corner and partials, then its count
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(&P.done[P.wmember[item]], 1);
+      }
+    } else {
+      const int t = (item - P.nw) * CL + rank;
+      if (t < P.ntiles) persistent_update<MS>(P, t);
+    }
+    window_sync<CL>();  // the cluster is done with this item; next[] holds the following one
+    item = *peer<CL>(&next[(it + 1) & 1], 0);
+  }
+  window_sync<CL>();  // no block leaves while another may still read its next[]
 }

@@ -8,7 +8,10 @@ namespace magpie_impl {
 template <int MS, int MODE>
 cudaError_t launch_window(const StepArgs& a, int windows, cudaStream_t st) {
   using Gm = Geo<MS>;
-  return launch_ex(window_kernel<MS, MODE>, dim3((unsigned)windows * Gm::CL), dim3(Gm::T), Gm::SMEM, st, Gm::CL, a);
+  // minibatch steps overlap their launch with the previous kernel's tail
+  constexpr bool pdl = MODE == kStep || MODE == kStepAtomic || MODE == kStepRecycle;
+  return launch_ex(window_kernel<MS, MODE>, dim3((unsigned)windows * Gm::CL), dim3(Gm::T), Gm::SMEM, st, Gm::CL, pdl,
+                   a);
 }
 
 template <int MS>
@@ -35,15 +38,61 @@ cudaError_t window_launch_batched(const StepArgs* table, const int2* map, int wi
   const dim3 grid((unsigned)windows * Gm::CL);
   if (minb == alt_minb<MS>() && minb != Gm::MIN_BLOCKS)
     return launch_ex(window_kernel_batched<MS, kStep, alt_minb<MS>()>, grid, dim3(Gm::T), Gm::SMEM, st, Gm::CL,
-                     table, map);
-  return launch_ex(window_kernel_batched<MS, kStep, Gm::MIN_BLOCKS>, grid, dim3(Gm::T), Gm::SMEM, st, Gm::CL, table,
-                   map);
+                     false, table, map);
+  return launch_ex(window_kernel_batched<MS, kStep, Gm::MIN_BLOCKS>, grid, dim3(Gm::T), Gm::SMEM, st, Gm::CL, false,
+                   table, map);
 }
 
 template <int MS>
 void window_minb_candidates(int* c) {
   c[0] = Geo<MS>::MIN_BLOCKS;
   c[1] = alt_minb<MS>();
+}
+
+template <int MS>
+size_t persistent_smem(int max_count) {
+  return std::max(Geo<MS>::SMEM, (sizeof(int2) + sizeof(int)) * (size_t)max_count);
+}
+
+template <int MS>
+cudaError_t window_launch_persistent(const PersistArgs& P, int clusters, int max_count, cudaStream_t st, int minb) {
+  using Gm = Geo<MS>;
+  const dim3 grid((unsigned)clusters * Gm::CL);
+  const size_t smem = persistent_smem<MS>(max_count);
+  if (minb == alt_minb<MS>() && minb != Gm::MIN_BLOCKS)
+    return launch_ex(window_kernel_persistent<MS, alt_minb<MS>()>, grid, dim3(Gm::T), smem, st, Gm::CL, false, P);
+  return launch_ex(window_kernel_persistent<MS, Gm::MIN_BLOCKS>, grid, dim3(Gm::T), smem, st, Gm::CL, false, P);
+}
+
+template <int MS>
+int window_persistent_capacity(int max_count, int minb) {
+  using Gm = Geo<MS>;
+  void (*k)(PersistArgs) = (minb == alt_minb<MS>() && minb != Gm::MIN_BLOCKS)
+                               ? window_kernel_persistent<MS, alt_minb<MS>()>
+                               : window_kernel_persistent<MS, Gm::MIN_BLOCKS>;
+  const size_t smem = persistent_smem<MS>(max_count);
+  int dev = 0, sms = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  if constexpr (Gm::CL == 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, Gm::T, smem) != cudaSuccess) return 0;
+    return n * sms;
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(Gm::CL * sms));
+    cfg.blockDim = dim3(Gm::T);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = Gm::CL;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    if (cudaOccupancyMaxActiveClusters(&n, (void*)k, &cfg) != cudaSuccess) return 0;
+    return n;
+  }
 }
 
 template <int MS>
@@ -64,6 +113,13 @@ cudaError_t window_prepare() {
     e = cudaFuncSetAttribute(window_kernel<MS, kEval>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(window_kernel<MS, kSim>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  const int pbytes = (int)persistent_smem<MS>(kMaxMinibatch);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(window_kernel_persistent<MS, Geo<MS>::MIN_BLOCKS>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, pbytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(window_kernel_persistent<MS, alt_minb<MS>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             pbytes);
   return e;
 }
 
@@ -71,6 +127,8 @@ cudaError_t window_prepare() {
   template cudaError_t window_launch<S>(int, const StepArgs&, int, cudaStream_t);                          \
   template cudaError_t window_launch_batched<S>(const StepArgs*, const int2*, int, cudaStream_t, int);     \
   template cudaError_t window_prepare<S>();                                                                \
-  template void window_minb_candidates<S>(int*);
+  template void window_minb_candidates<S>(int*);                                                            \
+  template cudaError_t window_launch_persistent<S>(const PersistArgs&, int, int, cudaStream_t, int);      \
+  template int window_persistent_capacity<S>(int, int);
 
 }  // namespace magpie_impl

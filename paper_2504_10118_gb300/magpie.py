@@ -31,7 +31,8 @@ def _stages() -> bool:
 SOURCES = [os.path.join(HERE, "csrc", f) for f in ("magpie.cu", "window_small.cu", "window_64.cu", "window_128.cu",
                                                    "window_256.cu")]
 DEPENDS = [os.path.join(HERE, "csrc", f) for f in ("core.cuh", "fft_lines.cuh", "window_kernel.cuh", "window_body.inc",
-                                                   "window_launch.cuh", "learned.cuh", "precision.cuh", "umma.cuh")]
+                                                   "window_launch.cuh", "learned.cuh", "precision.cuh", "umma.cuh",
+                                                   "update.cuh")]
 HEADER = os.path.join(ROOT, "include", "magpie.h")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
@@ -120,6 +121,11 @@ def lib() -> ctypes.CDLL:
             "magpie_group_set_minb": (ctypes.c_int, [vp, i32, i32]),
             "magpie_group_apply_tuning": (ctypes.c_int, [vp, vp, vp, vp, vp]),
             "magpie_group_set_apply_shape": (ctypes.c_int, [vp, i32]),
+            "magpie_group_form_tuning": (ctypes.c_int, [vp, vp, vp]),
+            "magpie_group_set_persistent": (ctypes.c_int, [vp, i32]),
+            "magpie_group_set_wait_limit": (ctypes.c_int, [vp, ctypes.c_double]),
+            "magpie_group_status": (ctypes.c_int, [vp]),
+            "magpie_group_check_waits": (ctypes.c_int, [vp, ctypes.c_double]),
             "magpie_cnn_param_count": (i32, []),
             "magpie_cnn_create": (ctypes.c_int, [ctypes.POINTER(vp), i32, i32, vp]),
             "magpie_cnn_destroy": (None, [vp]),
@@ -380,6 +386,35 @@ def magpie_group_set_apply_shape(group: Group, shape: int) -> None:
 
 def magpie_group_set_minb(group: Group, m: int, minb: int) -> None:
     _check(lib().magpie_group_set_minb(group.handle, int(m), int(minb)))
+
+
+def magpie_group_form_tuning(group: Group):
+    """(1 if sweeps use the persistent form else 0, (ms per batched step 0 as
+    separate launches, ms in the persistent form))."""
+    on = ctypes.c_int32()
+    ms = (ctypes.c_float * 2)()
+    _check(lib().magpie_group_form_tuning(group.handle, ctypes.byref(on), ms))
+    return on.value, (ms[0], ms[1])
+
+
+def magpie_group_set_persistent(group: Group, persistent: int) -> None:
+    _check(lib().magpie_group_set_persistent(group.handle, int(persistent)))
+
+
+def magpie_group_set_wait_limit(group: Group, seconds: float) -> None:
+    _check(lib().magpie_group_set_wait_limit(group.handle, float(seconds)))
+
+
+def magpie_group_status(group: Group) -> int:
+    """OK, or ETIMEOUT if a dependency wait of the persistent form ran out
+    since the last call (returned, not raised)."""
+    return lib().magpie_group_status(group.handle)
+
+
+def magpie_group_check_waits(group: Group, seconds: float) -> int:
+    """Self-test of the persistent form's bounded waits: ETIMEOUT expected
+    (returned, not raised)."""
+    return lib().magpie_group_check_waits(group.handle, float(seconds))
 
 
 # ----------------------------------------------------------- paper variants

@@ -41,7 +41,7 @@ def test_every_declared_symbol_is_exported(L):
 
 
 def test_error_strings_and_version(L):
-    assert L.magpie_version() == 10200
+    assert L.magpie_version() == 10300
     for code in (0, -1, -2, -3, -4, -5, -6):
         assert L.magpie_strerror(code)
     assert L.magpie_strerror(-99) == b"unknown error"
@@ -118,6 +118,12 @@ def test_null_arguments(L):
     assert rc == magpie.EINVAL
     assert L.magpie_group_create(None, None, 0, None) == magpie.EINVAL
     assert L.magpie_group_sweep(None, None) == magpie.EINVAL
+    on, ms = ctypes.c_int32(), (ctypes.c_float * 2)()
+    assert L.magpie_group_form_tuning(None, ctypes.byref(on), ms) == magpie.EINVAL
+    assert L.magpie_group_set_persistent(None, 1) == magpie.EINVAL
+    assert L.magpie_group_set_wait_limit(None, ctypes.c_double(1.0)) == magpie.EINVAL
+    assert L.magpie_group_status(None) == magpie.EINVAL
+    assert L.magpie_group_check_waits(None, ctypes.c_double(1e-3)) == magpie.EINVAL
     L.magpie_group_destroy(None)
     L.magpie_destroy(None)
 

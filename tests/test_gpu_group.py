@@ -162,3 +162,87 @@ def test_update_tile_shapes_give_identical_results():
     for other in outs[1:]:
         for a, b in zip(outs[0], other):
             assert np.array_equal(a, b)
+
+
+# the group specs plus window sides 8 (32-thread blocks) and 256 (512-thread
+# blocks in clusters of 8), so that every update tile of the persistent form
+# (16 x 16 and 32 x 32 over 32 .. 512 threads) runs
+FORM_SPECS = SPECS + [(48, 8, 5, 8, 1, 2, 6), (320, 256, 2, 48, 2, 3, 3)]
+
+
+def _group_run(members, persistent, sweeps=2):
+    ctxs = [mb.ctx() for mb in members]
+    before = [mb.zt.clone() for mb in members]
+    g = magpie.magpie_group_create(ctxs)
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, mb.zt) for a, mb in zip(before, members))  # the autotuner wrote scratch only
+    chosen, ms = magpie.magpie_group_form_tuning(g)
+    print("step form:", chosen, ms)
+    assert chosen in (0, 1) and ms[0] > 0 and ms[1] > 0
+    magpie.magpie_group_set_persistent(g, persistent)
+    for s in range(sweeps):
+        magpie.magpie_group_sweep(g, orders(members, s))
+    assert magpie.magpie_group_status(g) == magpie.OK
+    out = [mb.zt.cpu().numpy() for mb in members]
+    g.close()
+    for c in ctxs:
+        c.close()
+    return out
+
+
+def test_persistent_form_equals_separate_launches_and_sweeps():
+    """The persistent form (windows and update tiles of each window side from
+    one launch's work queue, sides concurrent) gives bitwise the objects of
+    the separate-launch form and of each member swept alone."""
+    members = [Member(spec, seed=80 + i) for i, spec in enumerate(FORM_SPECS)]
+    pers = _group_run(members, 1)
+    sep = _group_run(members, 0)
+    alone = []
+    for i, mb in enumerate(members):
+        c = mb.ctx()
+        for s in range(2):
+            magpie.magpie_sweep(c, orders(members, s)[i])
+        alone.append(mb.zt.cpu().numpy())
+        c.close()
+    for i, (a, b, c) in enumerate(zip(pers, sep, alone)):
+        assert np.array_equal(a, b), i
+        assert np.array_equal(a, c), i
+
+
+def test_bounded_waits_run_out_and_the_group_stays_usable():
+    """Every dependency wait of a persistent step whose targets nothing meets
+    runs out after its limit: the call returns MAGPIE_ETIMEOUT, skips every
+    update (the objects are unchanged), ends promptly, and the next sweeps
+    still give the objects of members swept alone."""
+    import time
+    members = [Member(spec, seed=90 + i) for i, spec in enumerate(SPECS)]
+    ctxs = [mb.ctx() for mb in members]
+    g = magpie.magpie_group_create(ctxs)
+    magpie.magpie_group_set_persistent(g, 1)
+    torch.cuda.synchronize()
+    before = [mb.zt.clone() for mb in members]
+    t0 = time.perf_counter()
+    rc = magpie.magpie_group_check_waits(g, 2e-3)
+    took = time.perf_counter() - t0
+    assert rc == magpie.ETIMEOUT
+    assert took < 5.0
+    assert all(torch.equal(a, mb.zt) for a, mb in zip(before, members))
+    assert magpie.magpie_group_status(g) == magpie.OK  # the flag was cleared
+    with pytest.raises(magpie.MagpieError) as ei:
+        magpie.magpie_group_set_wait_limit(g, 0.0)
+    assert ei.value.code == magpie.EINVAL
+    magpie.magpie_group_set_wait_limit(g, 0.5)
+    for s in range(2):
+        magpie.magpie_group_sweep(g, orders(members, s))
+    assert magpie.magpie_group_status(g) == magpie.OK
+    got = [mb.zt.cpu().numpy() for mb in members]
+    g.close()
+    for c in ctxs:
+        c.close()
+    for i, mb in enumerate(members):
+        mb.z0 = before[i].cpu().numpy().astype(np.complex128)
+        c = mb.ctx()
+        for s in range(2):
+            magpie.magpie_sweep(c, orders(members, s)[i])
+        assert np.array_equal(mb.zt.cpu().numpy(), got[i]), i
+        c.close()
