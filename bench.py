@@ -553,10 +553,11 @@ def sweeps_to_nrmse(w, dev, magpie, target: float, max_sweeps: int, every: int =
 
 def time_to_nrmse(w, dev, magpie) -> dict:
     """Time to NRMSE <= 1e-3 on the noise-free version of workload w, every
-    form at one setting (three levels, minibatch 16, alpha 0.3; with 1e6
+    form at one setting (three levels, minibatch 16, alpha 0.5; with 1e6
     photons per pattern the NRMSE of every form levels off near 0.09, and at
-    the workload's minibatch of 64 the iteration stalls near 0.06, so the
-    target is reachable only there): the plain FP32 form with either update,
+    the workload's minibatch of 64 the iteration stalls near 0.06; at alpha
+    0.3 whether a run leaves a plateau at 0.052 turns on rounding, while at
+    0.5 every run tried reached the target): the plain FP32 form with either update,
     the precision form (tensor-core DFTs), and the combined form (tensor-core
     DFTs plus the learned coarse correction, its network trained first on
     trajectories of the plain solver at the same setting, untimed).  For
@@ -565,14 +566,14 @@ def time_to_nrmse(w, dev, magpie) -> dict:
     import torch
     from paper_2504_10118_gb300 import learned
     clean = dataclasses.replace(w, photons=None)
-    setting = dataclasses.replace(clean, levels=3, minibatch=16, alpha=0.3)
+    setting = dataclasses.replace(clean, levels=3, minibatch=16, alpha=0.5)
     # every form first runs ten untimed sweeps on a context of its own, so
     # that no timed arm pays the process's one-time loading of its kernels
     # (each timed arm still captures its own sweep graph)
     for det, prec in ((1, 0), (0, 0), (1, 1)):
         sweeps_to_nrmse(setting, dev, magpie, 0.0, 10, deterministic=det, precision=prec)
     out = {"target": 1e-3, "data": f"noise-free intensities of {w.name}",
-           "setting": {"levels": 3, "minibatch": 16, "alpha": 0.3},
+           "setting": {"levels": 3, "minibatch": 16, "alpha": 0.5},
            "warm_up": "10 untimed sweeps of every form on a context of its own first",
            "fp32": sweeps_to_nrmse(setting, dev, magpie, 1e-3, 3000, deterministic=1),
            "fp32_atomic": sweeps_to_nrmse(setting, dev, magpie, 1e-3, 3000, deterministic=0),

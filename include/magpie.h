@@ -265,12 +265,14 @@ void magpie_group_destroy(magpie_group* group);
 /*
  * The group's autotuner.  magpie_group_create times, for every window side m
  * present in the first batched step, the batched window kernel under each of
- * its two candidate register bounds (blocks per SM: the default and one
- * alternative) on that step's own windows, and uses the faster in every
- * group sweep.  magpie_group_tuning reports, for m = 8, 16, .., 256 (index
- * i, m = 8 << i), the bound in use (minb[i]) and the measured ms per launch
- * of the two candidates (ms[2i], ms[2i+1]; 0 where not measured; HOST
- * arrays of 6 and 12).  magpie_group_set_minb forces a candidate.
+ * its candidate register bounds (blocks per SM: the default, an alternative
+ * and a denser third: 2 / 1 / 3 for 256-thread blocks, 1 / 2 / 4 for smaller
+ * ones, 1 only for m = 256) on that step's own windows, and uses the fastest
+ * in every group sweep.  magpie_group_tuning reports, for m = 8, 16, .., 256
+ * (index i, m = 8 << i), the bound in use (minb[i]) and the measured ms per
+ * launch of the three candidates (ms[3i], ms[3i+1], ms[3i+2]; 0 where not
+ * measured or equal to an earlier candidate; HOST arrays of 6 and 18).
+ * magpie_group_set_minb forces a candidate.
  */
 int magpie_group_tuning(magpie_group* group, int32_t* minb, float* ms);
 int magpie_group_set_minb(magpie_group* group, int32_t m, int32_t minb);

@@ -71,7 +71,8 @@ cudaError_t window_launch_batched(const StepArgs* table, const int2* map, int wi
 // the shared-memory attribute of every window kernel of this side;
 template <int MS>
 cudaError_t window_prepare();
-// the register bounds the group autotuner tries (c[0] the default);
+// the three register bounds the group autotuner tries (c[0] the default;
+// equal entries are one candidate);
 template <int MS>
 void window_minb_candidates(int* c);
 // the persistent step kernel on `clusters` clusters, with shared memory for

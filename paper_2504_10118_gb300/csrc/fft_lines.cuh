@@ -8,17 +8,26 @@ __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return f2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return f2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return f2(a.x * s, a.y * s); }
+// The products below spell out their rounding (the second product rounded,
+// the first fused into the add): left to the compiler, either product of a
+// sum of two could be the fused one, and the choice followed the kernel the
+// code was compiled into (its register bound, inlining), so that window
+// kernels of different register bounds gave different bits.
+__device__ __forceinline__ float dot2(float a, float b, float c, float d) {  // a b + c d
+  return __fmaf_rn(a, b, __fmul_rn(c, d));
+}
+__device__ __forceinline__ float cabs2(float2 a) { return dot2(a.x, a.x, a.y, a.y); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return f2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  return f2(dot2(a.x, b.x, -a.y, b.y), dot2(a.x, b.y, a.y, b.x));
 }
 // conj(a) * b
 __device__ __forceinline__ float2 cmul_cj(float2 a, float2 b) {
-  return f2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+  return f2(dot2(a.x, b.x, a.y, b.y), dot2(a.x, b.y, -a.y, b.x));
 }
 // a * w (forward) or a * conj(w) (inverse)
 template <bool INV>
 __device__ __forceinline__ float2 twmul(float2 a, float2 w) {
-  return INV ? f2(a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y) : cmul(a, w);
+  return INV ? f2(dot2(a.x, w.x, a.y, w.y), dot2(a.y, w.x, -a.x, w.y)) : cmul(a, w);
 }
 
 // cos and sin of 2 pi r / 16 (exact decimal expansions of cos(pi/8),
@@ -43,7 +52,7 @@ __device__ __forceinline__ float2 rot16(float2 a, int r) {
   if (r == 12) return INV ? f2(a.y, -a.x) : f2(-a.y, a.x);
   const float c = cos16(r);
   const float s = INV ? sin16(r) : -sin16(r);
-  return f2(a.x * c - a.y * s, a.x * s + a.y * c);
+  return f2(dot2(a.x, c, -a.y, s), dot2(a.x, s, a.y, c));
 }
 
 template <int N>

@@ -489,8 +489,8 @@ cudaError_t launch_window_batched_m(int MS, const StepArgs* table, const int2* m
   }
 }
 
-// The two register bounds the autotuner tries for window side MS (equal when
-// there is only one).
+// The three register bounds the autotuner tries for window side MS (c[3];
+// equal entries are one candidate).
 void minb_candidates(int MS, int* c) {
   switch (MS) {
 #define MAGPIE_CASE(S)               \
@@ -499,7 +499,7 @@ void minb_candidates(int MS, int* c) {
     return;
     MAGPIE_WINDOW_SIZES(MAGPIE_CASE)
 #undef MAGPIE_CASE
-    default: c[0] = c[1] = 1;
+    default: c[0] = c[1] = c[2] = 1;
   }
 }
 
@@ -621,7 +621,7 @@ struct magpie_group {
   // per window side m = 8 << i, and the measured ms per launch of batched
   // step 0 for the two candidates (0 where not measured)
   int minb[6] = {0, 0, 0, 0, 0, 0};
-  float tune_ms[6][2] = {};
+  float tune_ms[6][3] = {};
   // autotuner: tile shape of the update kernel (index into kApplyShapes) and
   // the measured ms per launch of batched step 0 for each shape
   int apply_shape = 0;
@@ -1395,12 +1395,6 @@ int noalloc_scratch(NoAllocScratch* out) {
 }  // namespace magpie_impl
 
 
-// Autotuner of a group: for every window side of batched step 0, launch the
-// batched window kernel with each candidate register bound (one warm-up, then
-// three timed launches on the group's stream) and keep the faster.  The
-// launches only write the members' per-window scratch (increments, partial
-// sums, corners), never an object; the members' permutations are set to the
-// identity first so that every index is valid.
 // The update of batched step t with apply tile shape v, from the device table
 // `table` (default: the group's own table of that shape).
 cudaError_t launch_apply_batched(magpie_group* g, int v, int t, cudaStream_t st, const ApplyArgs* table = nullptr) {
@@ -1574,6 +1568,13 @@ int group_tune_form(magpie_group* g, cudaStream_t st, cudaEvent_t e0, cudaEvent_
   return MAGPIE_OK;
 }
 
+// Autotuner of a group: for every window side of batched step 0, launch the
+// batched window kernel with each candidate register bound (one warm-up, then
+// three timed launches on the group's stream) and keep the fastest; then the
+// update's tile shape and the step's form.  The window launches only write
+// the members' per-window scratch (increments, partial sums, corners), never
+// an object; the members' permutations are set to the identity first so that
+// every index is valid.
 int group_autotune(magpie_group* g) {
   cudaStream_t st = g->stream;
   for (auto* c : g->members)
@@ -1582,7 +1583,7 @@ int group_autotune(magpie_group* g) {
   CUDA_TRY(cudaEventCreate(&e0));
   cudaError_t e = cudaEventCreate(&e1);
   for (int i = 0; i < 6 && e == cudaSuccess; ++i) {
-    int cand[2];
+    int cand[3];
     minb_candidates(8 << i, cand);
     g->minb[i] = cand[0];
   }
@@ -1590,11 +1591,12 @@ int group_autotune(magpie_group* g) {
     for (const auto& L : g->wl[0]) {
       if (e != cudaSuccess) break;
       const int i = ilog2(L.ms) - 3;
-      int cand[2];
+      int cand[3];
       minb_candidates(L.ms, cand);
-      if (cand[0] == cand[1]) continue;
+      if (cand[0] == cand[1] && cand[0] == cand[2]) continue;
       float best = 0.f;
-      for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+      for (int v = 0; v < 3 && e == cudaSuccess; ++v) {
+        if ((v == 1 && cand[1] == cand[0]) || (v == 2 && (cand[2] == cand[0] || cand[2] == cand[1]))) continue;
         e = launch_window_batched_m<kStep>(L.ms, g->table, g->map + L.map_off, L.windows, st, cand[v]);
         if (e == cudaSuccess) e = cudaEventRecord(e0, st);
         for (int r = 0; r < 3 && e == cudaSuccess; ++r)
@@ -2475,8 +2477,7 @@ int magpie_group_tuning(magpie_group* g, int32_t* minb, float* ms) {
   if (!g || !minb || !ms) return fail(MAGPIE_EINVAL, "NULL argument");
   for (int i = 0; i < 6; ++i) {
     minb[i] = g->minb[i];
-    ms[2 * i] = g->tune_ms[i][0];
-    ms[2 * i + 1] = g->tune_ms[i][1];
+    for (int v = 0; v < 3; ++v) ms[3 * i + v] = g->tune_ms[i][v];
   }
   return MAGPIE_OK;
 }
@@ -2560,9 +2561,10 @@ int magpie_group_check_waits(magpie_group* g, double seconds) {
 int magpie_group_set_minb(magpie_group* g, int32_t m, int32_t minb) {
   if (!g) return fail(MAGPIE_EINVAL, "NULL group");
   if (m < 8 || m > 256 || (m & (m - 1))) return fail(MAGPIE_EINVAL, "m must be a power of two in [8, 256]");
-  int cand[2];
+  int cand[3];
   minb_candidates(m, cand);
-  if (minb != cand[0] && minb != cand[1]) return fail(MAGPIE_EINVAL, "not a candidate register bound for this m");
+  if (minb != cand[0] && minb != cand[1] && minb != cand[2])
+    return fail(MAGPIE_EINVAL, "not a candidate register bound for this m");
   g->minb[ilog2(m) - 3] = minb;
   if (g->graph) {
     cudaGraphExecDestroy(g->graph);

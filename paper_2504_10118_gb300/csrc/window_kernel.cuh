@@ -66,16 +66,19 @@ constexpr int kStages = 10;
 // The increment w . Delta of window pixel (r, c): stored in the window's slot
 // of the increment buffer (ordered update), or added with one 16-byte float
 // atomic, together with the pixel's weight w^0, into the object-sized
-// accumulators at the window's corner (kStepAtomic).
+// accumulators at the window's corner (kStepAtomic).  It reads the step's
+// arguments in place (parameter space in the single-problem kernel) rather
+// than caching pointers in registers: cached, they spilled 56 bytes per
+// thread of the float-atomic kernel.
 template <int MS, bool ATOM>
 struct IncrementSink {
+  const StepArgs* a;   // the step's arguments (the accumulators and the weights w^0 = u + |Q|^2)
   float2* out;         // [MS][MS] this window's increments (ordered update)
-  float4* acc;         // accumulator of the window's top-left object pixel (kStepAtomic)
-  int n_cols;
-  const float* w0;     // [MS][MS] u + |Q|^2
+  int pr, pc;          // the window's corner (kStepAtomic)
   __device__ __forceinline__ void operator()(int r, int c, float2 v) const {
     if constexpr (ATOM)
-      atomicAdd(acc + (size_t)r * n_cols + c, make_float4(v.x, v.y, __ldg(&w0[r * MS + c]), 0.f));
+      atomicAdd(a->acc + (size_t)(pr + r) * a->n_cols + (pc + c),
+                make_float4(v.x, v.y, __ldg(&a->pyr[MS * MS + r * MS + c]), 0.f));
     else
       out[r * MS + c] = v;
   }
@@ -137,12 +140,14 @@ __device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
 }
 
 // One up-pass entry: e = g / w + (u / w) P(e_coarse), i.e. g * iw + rr * p,
-// with the rounding spelled out (the product g * iw rounded, the other fused
-// into the add), so that every kernel the V-cycle is compiled into gives
-// the same bits (left to the compiler, either product could be the fused
-// one, and the choice followed the surrounding kernel).
+// with the rounding spelled out so that every kernel the V-cycle is compiled
+// into gives the same bits (left to the compiler, either product could be
+// the one fused into the add, and the choice followed the surrounding
+// kernel).  The product g * iw is the fused one: against the oracle, one
+// step's increment on the full-size workload measured 7.5e-6 relative this
+// way and 1.16e-5 with rr * p fused.
 __device__ __forceinline__ float2 prolong(float2 g, float iw, float rr, float2 p) {
-  return f2(__fmaf_rn(rr, p.x, __fmul_rn(g.x, iw)), __fmaf_rn(rr, p.y, __fmul_rn(g.y, iw)));
+  return f2(__fmaf_rn(g.x, iw, __fmul_rn(rr, p.x)), __fmaf_rn(g.y, iw, __fmul_rn(rr, p.y)));
 }
 // a * s with each product rounded (never fused into a later add)
 __device__ __forceinline__ float2 cscale_rn(float2 a, float s) { return f2(__fmul_rn(a.x, s), __fmul_rn(a.y, s)); }
@@ -328,7 +333,7 @@ __device__ __forceinline__ void vcycle(const float2* Y, float2* lvl, const float
 #pragma unroll
       for (int a = 0; a < H; ++a) {
         const float u = __ldg(&u0[(R0 + a) * MS + cgl]);
-        put(R0 + a, cgl, f2(g0[a].x + u * e1[a >> 1].x, g0[a].y + u * e1[a >> 1].y));
+        put(R0 + a, cgl, f2(__fmaf_rn(u, e1[a >> 1].x, g0[a].x), __fmaf_rn(u, e1[a >> 1].y, g0[a].y)));
       }
     }
   }
@@ -336,7 +341,7 @@ __device__ __forceinline__ void vcycle(const float2* Y, float2* lvl, const float
 
 // One problem: window slot = cluster index (grid = windows * CL).
 template <int MS, int MODE>
-__global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel(StepArgs A) {
+__global__ void __launch_bounds__(Geo<MS>::T, Geo<MS>::MIN_BLOCKS) window_kernel(const __grid_constant__ StepArgs A) {
   const int win = blockIdx.x / Geo<MS>::CL;
 #include "window_body.inc"
 }

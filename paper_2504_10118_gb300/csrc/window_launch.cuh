@@ -27,15 +27,25 @@ cudaError_t window_launch(int mode, const StepArgs& a, int windows, cudaStream_t
 }
 
 // Candidate register bounds of the batched window kernel: blocks per SM.
+// The default (Geo::MIN_BLOCKS), an alternative, and a third, denser one:
+// three 256-thread blocks (80 registers; three of the m = 128 kernel's
+// 72 KB of shared memory fit an SM), or four of 128 threads or fewer.
 template <int MS>
 constexpr int alt_minb() {
   return Geo<MS>::T >= 512 ? 1 : (Geo<MS>::MIN_BLOCKS == 1 ? 2 : 1);
+}
+template <int MS>
+constexpr int third_minb() {
+  return Geo<MS>::T >= 512 ? 1 : (Geo<MS>::T == 256 ? 3 : 4);
 }
 
 template <int MS>
 cudaError_t window_launch_batched(const StepArgs* table, const int2* map, int windows, cudaStream_t st, int minb) {
   using Gm = Geo<MS>;
   const dim3 grid((unsigned)windows * Gm::CL);
+  if (minb == third_minb<MS>() && minb != Gm::MIN_BLOCKS && minb != alt_minb<MS>())
+    return launch_ex(window_kernel_batched<MS, kStep, third_minb<MS>()>, grid, dim3(Gm::T), Gm::SMEM, st, Gm::CL,
+                     false, table, map);
   if (minb == alt_minb<MS>() && minb != Gm::MIN_BLOCKS)
     return launch_ex(window_kernel_batched<MS, kStep, alt_minb<MS>()>, grid, dim3(Gm::T), Gm::SMEM, st, Gm::CL,
                      false, table, map);
@@ -47,6 +57,7 @@ template <int MS>
 void window_minb_candidates(int* c) {
   c[0] = Geo<MS>::MIN_BLOCKS;
   c[1] = alt_minb<MS>();
+  c[2] = third_minb<MS>();
 }
 
 template <int MS>
@@ -105,6 +116,12 @@ cudaError_t window_prepare() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(window_kernel_batched<MS, kStep, alt_minb<MS>()>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(window_kernel_batched<MS, kStep, third_minb<MS>()>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)  // the densest bound needs the whole shared-memory carve-out
+    e = cudaFuncSetAttribute(window_kernel_batched<MS, kStep, third_minb<MS>()>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(window_kernel<MS, kStepRecycle>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)

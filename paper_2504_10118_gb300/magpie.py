@@ -363,12 +363,13 @@ def magpie_group_destroy(group: Group) -> None:
 
 
 def magpie_group_tuning(group: Group):
-    """{m: (register bound in use, ms per launch of the two candidates)} for
-    the window sides the autotuner measured."""
+    """{m: (register bound in use, ms per launch of the three candidates, 0
+    for one equal to an earlier candidate)} for the window sides the
+    autotuner measured."""
     minb = (ctypes.c_int32 * 6)()
-    ms = (ctypes.c_float * 12)()
+    ms = (ctypes.c_float * 18)()
     _check(lib().magpie_group_tuning(group.handle, minb, ms))
-    return {8 << i: (minb[i], (ms[2 * i], ms[2 * i + 1])) for i in range(6) if ms[2 * i] > 0}
+    return {8 << i: (minb[i], tuple(ms[3 * i + v] for v in range(3))) for i in range(6) if ms[3 * i] > 0}
 
 
 def magpie_group_apply_tuning(group: Group):

@@ -109,19 +109,20 @@ def test_group_arguments():
 
 
 def test_autotuner_choices_give_identical_results():
-    """The autotuner measured both register bounds for the window sides whose
-    two candidates differ, and its choice does not change results: groups
-    forced to either candidate give bitwise equal objects."""
+    """The autotuner measured the three register bounds for every window side
+    whose candidates differ, and its choice does not change results: groups
+    forced to each candidate give bitwise equal objects."""
     members = [Member(spec, seed=40 + i) for i, spec in enumerate(SPECS)]
     outs = []
-    for force in (0, 1):
+    for force in (0, 1, 2):
         ctxs = [mb.ctx() for mb in members]
         g = magpie.magpie_group_create(ctxs)
         tuning = magpie.magpie_group_tuning(g)
         print("autotuner:", tuning)
-        assert 128 in tuning and all(ms[0] > 0 and ms[1] > 0 for _, ms in tuning.values())
+        assert 128 in tuning and all(all(x > 0 for x in ms) for _, ms in tuning.values())
         for m in (8, 16, 32, 64, 128, 256):
-            minb = {8: (1, 2), 16: (1, 2), 32: (1, 2), 64: (2, 1), 128: (2, 1), 256: (1, 1)}[m][force]
+            minb = {8: (1, 2, 4), 16: (1, 2, 4), 32: (1, 2, 4), 64: (2, 1, 3), 128: (2, 1, 3),
+                    256: (1, 1, 1)}[m][force]
             magpie.magpie_group_set_minb(g, m, minb)
         for s in range(2):
             magpie.magpie_group_sweep(g, orders(members, s))
@@ -129,10 +130,11 @@ def test_autotuner_choices_give_identical_results():
         g.close()
         for c in ctxs:
             c.close()
-    for a, b in zip(*outs):
-        assert np.array_equal(a, b)
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            assert np.array_equal(a, b)
     with pytest.raises(magpie.MagpieError):
-        magpie.magpie_group_set_minb(magpie.magpie_group_create([members[0].ctx()]), 128, 3)
+        magpie.magpie_group_set_minb(magpie.magpie_group_create([members[0].ctx()]), 128, 4)
 
 
 def test_update_tile_shapes_give_identical_results():

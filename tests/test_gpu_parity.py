@@ -289,9 +289,10 @@ def increment_errors(before, got, ref):
 # increment carries an absolute float32 error of a few 1e-6 of the largest
 # increment (the transforms' and the V-cycle's rounding, relative to the
 # spectrum and the object, not to the pixel's own increment), so the relative
-# error of a pixel grows as its increment shrinks: measured at most 1.8e-3
-# where |dz| > 1e-3 max|dz| and 5.4e-4 where |dz| > 1e-2 max|dz| over the 15
-# steps of a sweep; the bars leave a factor of about 3.
+# error of a pixel grows as its increment shrinks: measured at most 1.8e-3 to
+# 3.2e-3 where |dz| > 1e-3 max|dz| (depending on how the kernels' sums of two
+# products are rounded) and 4.5e-4 to 6.7e-4 where |dz| > 1e-2 max|dz| over
+# the 15 steps of a sweep; the bars leave a factor of 1.5 to 4.
 EW_TOL = {1e-3: 5e-3, 1e-2: 2e-3}
 
 
@@ -300,7 +301,7 @@ EW_TOL = {1e-3: 5e-3, 1e-2: 2e-3}
 # nearly cancel, their float32 rounding is large against the net increment, so
 # its errors scatter from run to run around the ordered update's fixed ones:
 # over three runs the worst step's increment error measured 0.8e-5, 1.06e-5
-# and 1.53e-5 (ordered: 8.0e-6, deterministic), and the element-wise errors
+# and 1.53e-5 (ordered: 7.5e-6, deterministic), and the element-wise errors
 # 3.0e-3 / 6.2e-3 where |dz| > 1e-3 max|dz| and 0.63e-3 / 0.89e-3 where
 # |dz| > 1e-2 max|dz|.  Its bars are about twice the worst measured value.
 INC_TOL_ATOMIC = 3e-5
