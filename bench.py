@@ -621,10 +621,13 @@ def precision_record(dev, magpie, warmup: int = 2, steps: int = 3) -> dict:
     orders = torch.from_numpy(np.stack([synth.make_order(w.n_pos, s) for s in range(warmup + steps)])).to(dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     rec = {"config": config_of(w), "data": "photon noise drawn on the device"}
-    for name, mode in (("tensor_core_dft", 1), ("fp32_fft", 0)):
+    for name, mode in (("tensor_core_dft", 1), ("tensor_core_dft_tcgen05", 2), ("fp32_fft", 0)):
         magpie.magpie_set_precision(ctx, mode)
         ms = time_sweeps(magpie, ctx, orders, warmup, steps, flush, torch.cuda.current_stream())
         rec[name] = {"value": steps * w.n_pos / (ms * 1e-3), "unit": "patterns/s", "ms_per_step": ms / steps}
+    rec["tensor_core_dft"]["mma"] = "mma.sync m16n8k16 (register fragments)"
+    rec["tensor_core_dft_tcgen05"]["mma"] = "tcgen05.mma M = 128 (operands in shared memory, accumulators in TMEM)"
+    magpie.magpie_stop_metric(ctx)  # reads the context's error flags (a bounded wait that ran out raises)
     ctx.close()
     return rec
 

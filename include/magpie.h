@@ -58,8 +58,10 @@ extern "C" {
 #define MAGPIE_ENOMEM (-3)      /* device memory allocation failed              */
 #define MAGPIE_EUNSUPPORTED (-4)/* a valid size this build has no kernel for    */
 #define MAGPIE_EINDEX (-5)      /* a device-side window index was out of range  */
-#define MAGPIE_ETIMEOUT (-6)    /* a bounded device wait ran out (a tensor-core
-                                   convolution stopped waiting for its MMAs)     */
+#define MAGPIE_ETIMEOUT (-6)    /* a bounded device wait ran out (a tcgen05
+                                   convolution or transform stopped waiting for
+                                   its MMAs, or a persistent group step for its
+                                   windows)                                      */
 
 typedef struct magpie_ctx magpie_ctx;
 
@@ -444,16 +446,24 @@ int magpie_learned_window_values(magpie_ctx* ctx, int32_t count, int32_t* accept
  * transform carries a relative error of about 1e-5 (2^-16 per product) where
  * the FP32 FFT path carries about 1e-6.  The projection, the V-cycle and the
  * update are the FP32 path's; Phi_k and the gradient norms stay FP64 sums.
- * mode 0: FP32 FFT path (default); mode 1: tensor-core DFTs (m = 64, 128 or
- * 256, update_probe = 0).  The mode applies to later steps and sweeps.
+ * mode 0: FP32 FFT path (default); mode 1: tensor-core DFTs with
+ * register-fragment MMAs (mma.sync m16n8k16); mode 2: the same DFTs on the
+ * 5th-generation tensor cores (tcgen05.mma, operands in shared memory,
+ * accumulators in tensor memory; each block's waits on its MMAs are
+ * bounded, and one that runs out makes the next objective, stop metric or
+ * window-value call return MAGPIE_ETIMEOUT).  Modes 1 and 2 need m = 64, 128
+ * or 256 and update_probe = 0.  The mode applies to later steps and sweeps.
  */
 int magpie_set_precision(magpie_ctx* ctx, int32_t mode);
 
 /* out[c] = the 2-D DFT of in[c] (unnormalised; inverse = 1: the conjugate
    transform, without 1/m^2) for `count` m x m complex windows (DEVICE), by
-   the precision form's tensor-core path.  in == out is allowed.  Allocates a
-   few KiB of tables per call; synchronous. */
+   the precision form's tensor-core path: magpie_dft2_tc with mma.sync,
+   magpie_dft2_tcgen05 with tcgen05 (MAGPIE_ETIMEOUT if a bounded wait ran
+   out).  in == out is allowed.  Allocates a few KiB of tables per call;
+   synchronous. */
 int magpie_dft2_tc(const void* in, void* out, int32_t m, int32_t count, int32_t inverse, void* stream);
+int magpie_dft2_tcgen05(const void* in, void* out, int32_t m, int32_t count, int32_t inverse, void* stream);
 
 /*
  * Variants from the paper, off by default (flags = 0), for later steps and

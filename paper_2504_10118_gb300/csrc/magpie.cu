@@ -54,8 +54,8 @@ namespace magpie_impl {
 constexpr int kVersion = 10300;  // 1.3.0
 
 #include "learned.cuh"
-#include "precision.cuh"
 #include "umma.cuh"
+#include "precision.cuh"
 
 // One problem: a 2-D grid of tiles.
 // Launched as a programmatic dependent of the window kernel (its blocks, let
@@ -1072,25 +1072,64 @@ void build_tc_tables(int MS, TcTables& T) {
   }
 }
 
+// Dynamic shared memory of the tcgen05 transform kernels (their operand
+// buffers, on top of the lines' static 15-42 KB), set once per process.
 template <int MS>
-cudaError_t launch_dft2_tc(float2* buf, int count, const TcTables* tabs, const float2* tw, int inv, cudaStream_t st) {
+cudaError_t prepare_dft_umma() {
+  static cudaError_t done = [] {
+    const int b = kUmmaDftSmem;
+    cudaError_t e = cudaFuncSetAttribute(dft_tc_kernel<MS, 0, 0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(dft_tc_kernel<MS, 1, 0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(dft_tc_kernel<MS, 0, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(dft_tc_kernel<MS, 1, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(exit_dft_kernel<MS, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(project_dft_kernel<MS, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(grad_dft_kernel<MS, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    return e;
+  }();
+  return done;
+}
+
+// path 0: register-fragment (mma.sync) transforms; 1: tcgen05 transforms
+// (err: bit 4 set when one of their bounded waits ran out).
+template <int MS, int PATH>
+cudaError_t launch_dft2_tc_p(float2* buf, int count, const TcTables* tabs, const float2* tw, int inv, cudaStream_t st,
+                             int* err) {
   const dim3 grid((unsigned)count * (MS / kTcLines));
+  const size_t smem = PATH ? kUmmaDftSmem : 0;
   if (inv) {
-    dft_tc_kernel<MS, 1, 1><<<grid, 128, 0, st>>>(buf, tabs, tw, 1.f);
-    dft_tc_kernel<MS, 0, 1><<<grid, 128, 0, st>>>(buf, tabs, tw, 1.f);
+    dft_tc_kernel<MS, 1, 1, PATH><<<grid, 128, smem, st>>>(buf, tabs, tw, 1.f, err);
+    dft_tc_kernel<MS, 0, 1, PATH><<<grid, 128, smem, st>>>(buf, tabs, tw, 1.f, err);
   } else {
-    dft_tc_kernel<MS, 0, 0><<<grid, 128, 0, st>>>(buf, tabs, tw, 1.f);
-    dft_tc_kernel<MS, 1, 0><<<grid, 128, 0, st>>>(buf, tabs, tw, 1.f);
+    dft_tc_kernel<MS, 0, 0, PATH><<<grid, 128, smem, st>>>(buf, tabs, tw, 1.f, err);
+    dft_tc_kernel<MS, 1, 0, PATH><<<grid, 128, smem, st>>>(buf, tabs, tw, 1.f, err);
   }
   return cudaGetLastError();
 }
 
+template <int MS>
+cudaError_t launch_dft2_tc(float2* buf, int count, const TcTables* tabs, const float2* tw, int inv, cudaStream_t st,
+                           int path, int* err) {
+  if (path) {
+    const cudaError_t e = prepare_dft_umma<MS>();
+    if (e != cudaSuccess) return e;
+    return launch_dft2_tc_p<MS, 1>(buf, count, tabs, tw, inv, st, err);
+  }
+  return launch_dft2_tc_p<MS, 0>(buf, count, tabs, tw, inv, st, err);
+}
+
 cudaError_t launch_dft2_tc_m(int MS, float2* buf, int count, const TcTables* tabs, const float2* tw, int inv,
-                             cudaStream_t st) {
+                             cudaStream_t st, int path = 0, int* err = nullptr) {
   switch (MS) {
-    case 64: return launch_dft2_tc<64>(buf, count, tabs, tw, inv, st);
-    case 128: return launch_dft2_tc<128>(buf, count, tabs, tw, inv, st);
-    case 256: return launch_dft2_tc<256>(buf, count, tabs, tw, inv, st);
+    case 64: return launch_dft2_tc<64>(buf, count, tabs, tw, inv, st, path, err);
+    case 128: return launch_dft2_tc<128>(buf, count, tabs, tw, inv, st, path, err);
+    case 256: return launch_dft2_tc<256>(buf, count, tabs, tw, inv, st, path, err);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1123,20 +1162,28 @@ PrecArgs precision_args(magpie_ctx* c, const int32_t* idx) {
 
 template <int MS>
 cudaError_t launch_precision_g0(const PrecArgs& a, int count, const TcTables* tabs, const float2* tw,
-                                cudaStream_t st) {
+                                cudaStream_t st, int path) {
   const dim3 grid((unsigned)count * (MS / kTcLines));
-  exit_dft_kernel<MS><<<grid, 128, 0, st>>>(a, tabs, tw);
-  project_dft_kernel<MS><<<grid, 128, 0, st>>>(a, tabs, tw);
-  grad_dft_kernel<MS><<<grid, 128, 0, st>>>(a, tabs, tw);
+  if (path) {
+    const cudaError_t e = prepare_dft_umma<MS>();
+    if (e != cudaSuccess) return e;
+    exit_dft_kernel<MS, 1><<<grid, 128, kUmmaDftSmem, st>>>(a, tabs, tw);
+    project_dft_kernel<MS, 1><<<grid, 128, kUmmaDftSmem, st>>>(a, tabs, tw);
+    grad_dft_kernel<MS, 1><<<grid, 128, kUmmaDftSmem, st>>>(a, tabs, tw);
+  } else {
+    exit_dft_kernel<MS, 0><<<grid, 128, 0, st>>>(a, tabs, tw);
+    project_dft_kernel<MS, 0><<<grid, 128, 0, st>>>(a, tabs, tw);
+    grad_dft_kernel<MS, 0><<<grid, 128, 0, st>>>(a, tabs, tw);
+  }
   return cudaGetLastError();
 }
 
 int enqueue_precision_g0(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st) {
   const PrecArgs a = precision_args(c, idx);
   switch (a.MS) {
-    case 64: CUDA_TRY(launch_precision_g0<64>(a, count, c->tabs, c->tw, st)); break;
-    case 128: CUDA_TRY(launch_precision_g0<128>(a, count, c->tabs, c->tw, st)); break;
-    case 256: CUDA_TRY(launch_precision_g0<256>(a, count, c->tabs, c->tw, st)); break;
+    case 64: CUDA_TRY(launch_precision_g0<64>(a, count, c->tabs, c->tw, st, c->precision == 2)); break;
+    case 128: CUDA_TRY(launch_precision_g0<128>(a, count, c->tabs, c->tw, st, c->precision == 2)); break;
+    case 256: CUDA_TRY(launch_precision_g0<256>(a, count, c->tabs, c->tw, st, c->precision == 2)); break;
     default: return fail(MAGPIE_EUNSUPPORTED, "the precision form needs m = 64, 128 or 256");
   }
   return MAGPIE_OK;
@@ -1223,6 +1270,7 @@ int read_err(magpie_ctx* c) {
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   if (h) {
     CUDA_TRY(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+    if (h & 16) return fail(MAGPIE_ETIMEOUT, "a bounded wait of a tcgen05 transform ran out");
     return fail(MAGPIE_EINDEX, "a window index passed to a step or sweep was outside [0, n_pos)");
   }
   return MAGPIE_OK;
@@ -2388,8 +2436,9 @@ int magpie_learned_window_values(magpie_ctx* c, int32_t count, int32_t* accepted
 
 int magpie_set_precision(magpie_ctx* c, int32_t mode) {
   if (!c) return fail(MAGPIE_EINVAL, "NULL context");
-  if (mode != 0 && mode != 1) return fail(MAGPIE_EINVAL, "mode must be 0 (FP32 FFTs) or 1 (tensor-core DFTs)");
-  if (mode == 1) {
+  if (mode < 0 || mode > 2)
+    return fail(MAGPIE_EINVAL, "mode must be 0 (FP32 FFTs), 1 (mma.sync DFTs) or 2 (tcgen05 DFTs)");
+  if (mode >= 1) {
     const int m = c->p.m;
     if (m != 64 && m != 128 && m != 256)
       return fail(MAGPIE_EUNSUPPORTED, "tensor-core DFTs need m = 64, 128 or 256");
@@ -2411,7 +2460,17 @@ int magpie_set_precision(magpie_ctx* c, int32_t mode) {
   return MAGPIE_OK;
 }
 
+static int dft2_tc(const void* in, void* out, int32_t m, int32_t count, int32_t inverse, void* stream, int path);
+
 int magpie_dft2_tc(const void* in, void* out, int32_t m, int32_t count, int32_t inverse, void* stream) {
+  return dft2_tc(in, out, m, count, inverse, stream, 0);
+}
+
+int magpie_dft2_tcgen05(const void* in, void* out, int32_t m, int32_t count, int32_t inverse, void* stream) {
+  return dft2_tc(in, out, m, count, inverse, stream, 1);
+}
+
+static int dft2_tc(const void* in, void* out, int32_t m, int32_t count, int32_t inverse, void* stream, int path) {
   if (!in || !out) return fail(MAGPIE_EINVAL, "NULL argument");
   if (m != 64 && m != 128 && m != 256) return fail(MAGPIE_EUNSUPPORTED, "m must be 64, 128 or 256");
   if (count < 1 || (long long)count * m * m > (1LL << 28)) return fail(MAGPIE_EINVAL, "count out of range");
@@ -2426,17 +2485,24 @@ int magpie_dft2_tc(const void* in, void* out, int32_t m, int32_t count, int32_t 
   }
   TcTables* dt = nullptr;
   float2* dtw = nullptr;
+  int* derr = nullptr;
+  int herr = 0;
   cudaError_t e = cudaMalloc((void**)&dt, sizeof(TcTables));
   if (e == cudaSuccess) e = cudaMalloc((void**)&dtw, sizeof(float2) * m);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&derr, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(int), st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dt, &h, sizeof(TcTables), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dtw, htw.data(), sizeof(float2) * m, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && in != out)
     e = cudaMemcpyAsync(out, in, sizeof(float2) * (size_t)count * m * m, cudaMemcpyDeviceToDevice, st);
-  if (e == cudaSuccess) e = launch_dft2_tc_m(m, (float2*)out, count, dt, dtw, inverse, st);
+  if (e == cudaSuccess) e = launch_dft2_tc_m(m, (float2*)out, count, dt, dtw, inverse, st, path, derr);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (dt) cudaFree(dt);
   if (dtw) cudaFree(dtw);
+  if (derr) cudaFree(derr);
   if (e != cudaSuccess) return fail(MAGPIE_ECUDA, std::string("magpie_dft2_tc: ") + cudaGetErrorString(e));
+  if (herr & 16) return fail(MAGPIE_ETIMEOUT, "a bounded wait of a tcgen05 transform ran out");
   return MAGPIE_OK;
 }
 

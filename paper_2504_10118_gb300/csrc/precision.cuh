@@ -242,28 +242,244 @@ __device__ __forceinline__ void tc_lines(float* Sr, float* Si, const TcTables* _
 
 }
 
+// ---- the same transform on the 5th-generation tensor cores (tcgen05).
+// Both stages become M = 128 matrix products with the block's rows as M:
+//   stage 1: D[j][r] = sum_c X[j][c] f16[r][c], j = (line, n2) (NL QR rows,
+//            128 per tile), r = (re k1 | im k1), c = (re n1 | im n1), K = 32;
+//   stage 2: D[(line, k1)][nn] = sum_kk Y'[(line, k1)][kk] fq[kk][nn], 256
+//            rows in two tiles, K = N = 2 QR (both padded to 16 for m = 64).
+// For each tile the threads write the A rows, one per thread, as hi and lo
+// BF16 into a 64-byte-swizzled K-major buffer; thread 0 issues the
+// tcgen05.mma (hi hi + hi lo + lo hi per 16-deep K step) into 32 TMEM
+// columns and commits them to an mbarrier; every thread waits (bounded),
+// reads its row of the accumulator with tcgen05.ld, and does the twiddle
+// (stage 1) or the scaled store (stage 2) in FP32 from registers.  The B
+// operands (the DFT matrices) are written the same way at the start.
+struct TcUmma {
+  uint32_t a_hi, a_lo;    // A tile: 128 rows x 64 bytes each
+  uint32_t b1_hi, b1_lo;  // stage-1 DFT matrix: 32 rows x 64 bytes
+  uint32_t b2_hi, b2_lo;  // stage-2 DFT matrix: up to 32 rows x 64 bytes
+  uint32_t bar, tmem, phase;
+  int ok;                 // 0 once a bounded wait ran out
+};
+constexpr int kUmmaDftSmem = 2 * 8192 + 4 * 2048 + 1024;  // operand buffers + 1024-byte alignment slack
+
+// hi and lo BF16 of 8 consecutive K elements (one 16-byte chunk), chunk c of
+// row r of the two 64-byte-swizzled buffers
+__device__ __forceinline__ void put_chunk(uint32_t hi_base, uint32_t lo_base, int r, int c, const float (&v)[8]) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) split2(v[2 * i], v[2 * i + 1], h[i], l[i]);
+  const uint32_t o = umma::sw64_off(r, c);
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(hi_base + o), "r"(h[0]), "r"(h[1]), "r"(h[2]),
+               "r"(h[3])
+               : "memory");
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(lo_base + o), "r"(l[0]), "r"(l[1]), "r"(l[2]),
+               "r"(l[3])
+               : "memory");
+}
+
+// One tile's products: the A rows written, KS K steps of 16 against B
+// (N rows), accumulator in U.tmem; returns once the products are complete
+// (or the bounded wait ran out: U.ok = 0).
+template <int N>
+__device__ __forceinline__ void umma_tile(TcUmma& U, uint32_t b_hi, uint32_t b_lo, int KS) {
+  umma::fence_proxy_async();  // this thread's operand writes, visible to the tensor core
+  umma::fence_before();       // and its earlier tcgen05.ld ordered before the barrier
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    umma::fence_after();
+    constexpr uint32_t ID = umma::idesc_bf16(128, N);
+    for (int k = 0; k < KS; ++k) {
+      const uint32_t o = 32u * (uint32_t)k;
+      const uint64_t ah = umma::desc_sw64(U.a_hi + o), al = umma::desc_sw64(U.a_lo + o);
+      const uint64_t bh = umma::desc_sw64(b_hi + o), bl = umma::desc_sw64(b_lo + o);
+      umma::mma_bf16_ss(U.tmem, ah, bh, ID, k != 0);
+      umma::mma_bf16_ss(U.tmem, ah, bl, ID, 1);
+      umma::mma_bf16_ss(U.tmem, al, bh, ID, 1);
+    }
+    umma::commit(U.bar);
+  }
+  if (!umma::wait(U.bar, U.phase)) U.ok = 0;
+  U.phase ^= 1u;
+  umma::fence_after();
+}
+
+template <int MS, int INV>
+__device__ __forceinline__ void tc_lines_umma(float* Sr, float* Si, const TcTables* __restrict__ tabs,
+                                              const float2* __restrict__ tw, float scale, TcUmma& U) {
+  using S = TcSm<MS>;
+  constexpr int QR = S::QR, NL = S::NL;
+  constexpr int Q2 = 2 * QR < 16 ? 16 : 2 * QR;  // stage-2 K and N, padded to 16
+  const int tid = threadIdx.x;
+  const uint32_t trow = U.tmem + ((uint32_t)(tid & ~31) << 16);  // this warp's TMEM lanes
+  // B operands: stage 1 rows r, K c: f16[r][c]; stage 2 rows nn, K kk: fq[kk][nn] (0 in the padding)
+  {
+    const float* F1 = tabs->f16[INV];
+    const int r = tid >> 2, c = tid & 3;
+    float v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = F1[r * 32 + 8 * c + k];
+    put_chunk(U.b1_hi, U.b1_lo, r, c, v);
+    const float* F2 = tabs->fq[INV];
+    if (tid < Q2 * (Q2 / 8)) {
+      const int r2 = tid / (Q2 / 8), c2 = tid % (Q2 / 8);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int kk = 8 * c2 + k;
+        v[k] = kk < 2 * QR && r2 < 2 * QR ? F2[kk * 32 + r2] : 0.f;
+      }
+      put_chunk(U.b2_hi, U.b2_lo, r2, c2, v);
+    }
+  }
+  __syncthreads();  // the lines in place
+
+  // ---- stage 1: rows j = (line, n2)
+  constexpr int J = NL * QR, T1 = (J + 127) / 128;
+#pragma unroll 1
+  for (int mt = 0; mt < T1; ++mt) {
+    const int j = mt * 128 + tid;
+    const bool live = j < J;
+    const int l = live ? j / QR : 0, n2 = live ? j % QR : 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int kk = 8 * c + k, n1 = kk & 15;
+        v[k] = live ? (kk < 16 ? Sr : Si)[S::at(l, QR * n1 + n2)] : 0.f;
+      }
+      put_chunk(U.a_hi, U.a_lo, tid, c, v);
+    }
+    umma_tile<32>(U, U.b1_hi, U.b1_lo, 2);
+    float y[32];
+    umma::ld16(trow, *reinterpret_cast<float(*)[16]>(&y[0]));
+    umma::ld16(trow + 16u, *reinterpret_cast<float(*)[16]>(&y[16]));
+    if (live) {
+#pragma unroll
+      for (int k1 = 0; k1 < 16; ++k1) {
+        float2 w = tw[(n2 * k1) % MS];
+        if (INV) w.y = -w.y;
+        const float yr = y[k1], yi = y[16 + k1];
+        Sr[S::at(l, k1 * QR + n2)] = yr * w.x - yi * w.y;
+        Si[S::at(l, k1 * QR + n2)] = yr * w.y + yi * w.x;
+      }
+    }
+  }
+  __syncthreads();  // stage 1's rows in place before stage 2 reads them
+
+  // ---- stage 2: rows (line, k1), two tiles of 128
+#pragma unroll 1
+  for (int mt = 0; mt < NL * 16 / 128; ++mt) {
+    const int row = mt * 128 + tid, l = row >> 4, k1 = row & 15;
+#pragma unroll
+    for (int c = 0; c < Q2 / 8; ++c) {
+      float v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int kk = 8 * c + k;
+        v[k] = kk < QR ? Sr[S::at(l, k1 * QR + kk)] : kk < 2 * QR ? Si[S::at(l, k1 * QR + kk - QR)] : 0.f;
+      }
+      put_chunk(U.a_hi, U.a_lo, tid, c, v);
+    }
+    umma_tile<Q2>(U, U.b2_hi, U.b2_lo, Q2 / 16);
+    float o[32];
+    umma::ld16(trow, *reinterpret_cast<float(*)[16]>(&o[0]));
+    if constexpr (Q2 > 16) umma::ld16(trow + 16u, *reinterpret_cast<float(*)[16]>(&o[16]));
+#pragma unroll
+    for (int nn = 0; nn < 2 * QR; ++nn) {
+      const float v = o[nn] * scale;
+      if (nn < QR)
+        Sr[S::at(l, k1 + 16 * nn)] = v;
+      else
+        Si[S::at(l, k1 + 16 * (nn - QR))] = v;
+    }
+  }
+  __syncthreads();
+}
+
+// Per-block state of a transform path: PATH 0 the register-fragment
+// (mma.sync) transforms, nothing to set up; PATH 1 the tcgen05 transforms,
+// with 32 tensor-memory columns, one mbarrier and kUmmaDftSmem bytes of
+// dynamic shared memory for the operands.  end() frees the tensor memory and
+// sets bit 4 of `err` if a bounded wait ran out.  Every thread of the block
+// calls begin() and end().
+template <int PATH>
+struct TcPath {
+  __device__ __forceinline__ void begin() {}
+  __device__ __forceinline__ void end(int*) {}
+  template <int MS, int INV>
+  __device__ __forceinline__ void lines(float* Sr, float* Si, const TcTables* tabs, const float2* tw, float sc) {
+    tc_lines<MS, INV>(Sr, Si, tabs, tw, sc);
+  }
+};
+template <>
+struct TcPath<1> {
+  TcUmma U;
+  __device__ __forceinline__ void begin() {
+    extern __shared__ __align__(16) unsigned char tc_dyn[];
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ uint32_t slot;
+    const uint32_t base = (smem_addr(tc_dyn) + 1023u) & ~1023u;
+    U.a_hi = base;
+    U.a_lo = base + 8192;
+    U.b1_hi = base + 16384;
+    U.b1_lo = base + 18432;
+    U.b2_hi = base + 20480;
+    U.b2_lo = base + 22528;
+    if (threadIdx.x < 32) umma::alloc(smem_addr(&slot), 32);
+    if (threadIdx.x == 0) {
+      mbar_init(smem_addr(&bar), 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    umma::fence_before();
+    __syncthreads();
+    umma::fence_after();
+    U.tmem = slot;
+    U.bar = smem_addr(&bar);
+    U.phase = 0;
+    U.ok = 1;
+  }
+  __device__ __forceinline__ void end(int* err) {
+    umma::fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      umma::fence_after();
+      umma::dealloc(U.tmem, 32);
+    }
+    if (!U.ok && err) atomicOr(err, 16);
+  }
+  template <int MS, int INV>
+  __device__ __forceinline__ void lines(float* Sr, float* Si, const TcTables* tabs, const float2* tw, float sc) {
+    tc_lines_umma<MS, INV>(Sr, Si, tabs, tw, sc, U);
+  }
+};
+
 // One block: kTcLines lines of one window through the transform, in place in
 // `data` ([windows][MS][MS]).  AXIS 0: lines are columns (element stride
 // MS); AXIS 1: rows.  `scale` multiplies the output.
-template <int MS, int AXIS, int INV>
+template <int MS, int AXIS, int INV, int PATH>
 __global__ void __launch_bounds__(128) dft_tc_kernel(float2* __restrict__ data, const TcTables* __restrict__ tabs,
-                                                     const float2* __restrict__ tw, float scale) {
+                                                     const float2* __restrict__ tw, float scale, int* err) {
   using S = TcSm<MS>;
   __shared__ float Sr[S::NL * S::LD];
   __shared__ float Si[S::NL * S::LD];
+  TcPath<PATH> T;
+  T.begin();
   const int tiles = MS / S::NL;
   const int win = blockIdx.x / tiles, l0 = (blockIdx.x % tiles) * S::NL;
   float2* base = data + (size_t)win * MS * MS;
   tc_load<MS, AXIS>(Sr, Si, [&](int l, int p) {
     return AXIS == 1 ? base[(size_t)(l0 + l) * MS + p] : base[(size_t)p * MS + l0 + l];
   });
-  tc_lines<MS, INV>(Sr, Si, tabs, tw, scale);
+  T.template lines<MS, INV>(Sr, Si, tabs, tw, scale);
   tc_store<MS, AXIS>(Sr, Si, [&](int l, int p, float2 v) {
     if (AXIS == 1)
       base[(size_t)(l0 + l) * MS + p] = v;
     else
       base[(size_t)p * MS + l0 + l] = v;
   });
+  T.end(err);
 }
 
 struct PrecArgs {
@@ -315,12 +531,14 @@ __device__ __forceinline__ TcBlock tc_block(const PrecArgs& A) {
   return b;
 }
 
-template <int MS>
+template <int MS, int PATH>
 __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) exit_dft_kernel(const PrecArgs A, const TcTables* __restrict__ tabs,
                                                        const float2* __restrict__ tw) {
   using S = TcSm<MS>;
   __shared__ float Sr[S::NL * S::LD];
   __shared__ float Si[S::NL * S::LD];
+  TcPath<PATH> T;
+  T.begin();
   const TcBlock B = tc_block<MS>(A);
   if (threadIdx.x == 0 && B.tile == 0) {
     if (B.ok)
@@ -337,18 +555,21 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) exit_dft_kernel(con
     const float2 qq = __ldg(&A.Q[p * MS + B.l0 + l]);
     return make_float2(qq.x * zz.x - qq.y * zz.y, qq.x * zz.y + qq.y * zz.x);
   });
-  tc_lines<MS, 0>(Sr, Si, tabs, tw, 1.f);
+  T.template lines<MS, 0>(Sr, Si, tabs, tw, 1.f);
   float2* base = A.buf + (size_t)B.w * MS * MS;
   tc_store<MS, 0>(Sr, Si, [&](int l, int p, float2 v) { base[(size_t)p * MS + B.l0 + l] = v; });
+  T.end(A.err);
 }
 
-template <int MS>
+template <int MS, int PATH>
 __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) project_dft_kernel(const PrecArgs A, const TcTables* __restrict__ tabs,
                                                           const float2* __restrict__ tw) {
   using S = TcSm<MS>;
   __shared__ float Sr[S::NL * S::LD];
   __shared__ float Si[S::NL * S::LD];
   __shared__ double red[4];
+  TcPath<PATH> T;
+  T.begin();
   const TcBlock B = tc_block<MS>(A);
   float2* base = A.buf + (size_t)B.w * MS * MS;
   if (B.ok) {
@@ -358,7 +579,7 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) project_dft_kernel(
       asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(ab + 128 * i)));
   }
   tc_load<MS, 1>(Sr, Si, [&](int l, int p) { return base[(size_t)(B.l0 + l) * MS + p]; });
-  tc_lines<MS, 0>(Sr, Si, tabs, tw, 1.f);
+  T.template lines<MS, 0>(Sr, Si, tabs, tw, 1.f);
   // Psi <- sqrt(d) Psi / |Psi| / m^2 (sqrt(d) / m^2 where Psi = 0, or the
   // previous visit's phase under the phase rule)
   const float* am = A.amp + (size_t)(B.ok ? B.k : 0) * MS * MS;
@@ -394,11 +615,12 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) project_dft_kernel(
   }
   const double s = block_sum((double)res, red, threadIdx.x, 128);
   if (threadIdx.x == 0) A.part[((size_t)B.w * A.T + B.tile) * 2] = B.ok ? s : 0.0;
-  tc_lines<MS, 1>(Sr, Si, tabs, tw, 1.f);
+  T.template lines<MS, 1>(Sr, Si, tabs, tw, 1.f);
   tc_store<MS, 1>(Sr, Si, [&](int l, int p, float2 v) { base[(size_t)(B.l0 + l) * MS + p] = v; });
+  T.end(A.err);
 }
 
-template <int MS>
+template <int MS, int PATH>
 __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) grad_dft_kernel(const PrecArgs A, const TcTables* __restrict__ tabs,
                                                        const float2* __restrict__ tw) {
   using S = TcSm<MS>;
@@ -406,10 +628,12 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) grad_dft_kernel(con
   __shared__ float Sr[NL * S::LD];
   __shared__ float Si[NL * S::LD];
   __shared__ double red[4];
+  TcPath<PATH> T;
+  T.begin();
   const TcBlock B = tc_block<MS>(A);
   const float2* base = A.buf + (size_t)B.w * MS * MS;
   tc_load<MS, 0>(Sr, Si, [&](int l, int p) { return base[(size_t)p * MS + B.l0 + l]; });
-  tc_lines<MS, 1>(Sr, Si, tabs, tw, 1.f);
+  T.template lines<MS, 1>(Sr, Si, tabs, tw, 1.f);
   const float2* zk = A.z + (B.ok ? (size_t)A.pos[2 * B.k] * A.n_cols + A.pos[2 * B.k + 1] : 0);
   float2* out = A.contrib + (size_t)B.w * MS * MS;
   float gn = 0.f;
@@ -467,6 +691,7 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) grad_dft_kernel(con
       A.g1[(size_t)B.w * h * h + br * h + bc] = make_float2(f * sx, f * sy);
     }
   }
+  T.end(A.err);
 }
 
 // Levels 2 .. L-1 of the V-cycle of one window (levels >= 3), one block per

@@ -1,7 +1,8 @@
-// umma.cuh -- the learned correction's convolutions on the 5th-generation
-// tensor cores (tcgen05): BF16 operands staged in shared memory, FP32
-// accumulators in tensor memory.  Included by magpie.cu inside its anonymous
-// namespace, after learned.cuh (ConvFwd, bf16).
+// umma.cuh -- the 5th-generation tensor-core (tcgen05) helpers, and the
+// learned correction's convolutions on them: BF16 operands staged in shared
+// memory, FP32 accumulators in tensor memory.  Included by magpie.cu inside
+// namespace magpie_impl, after learned.cuh (ConvFwd, bf16) and before
+// precision.cuh (whose transforms also run on them).
 //
 // One 128-thread block computes a 128 x BN tile of the implicit GEMM
 // D[pixel][cout] = sum_k A[pixel][k] W[cout][k], k = (ky, kx, ci), over its
@@ -34,6 +35,22 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   d |= (uint64_t)1 << 46;
   d |= (uint64_t)2 << 61;
   return d;
+}
+
+// The same for the 64-byte swizzle (rows of 64 bytes, 8-row atoms of 512
+// bytes, 16-byte chunk c of row r at chunk c ^ ((r >> 1) mod 4)): swizzle
+// mode 4, stride between 8-row groups 512 bytes.
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+// byte offset of 16-byte chunk c of row r in a 64-byte-swizzled operand
+__host__ __device__ constexpr uint32_t sw64_off(int r, int c) {
+  return (uint32_t)((r >> 3) * 512 + (r & 7) * 64 + ((c ^ ((r >> 1) & 3)) << 4));
 }
 
 // Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16

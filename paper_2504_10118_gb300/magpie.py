@@ -144,6 +144,7 @@ def lib() -> ctypes.CDLL:
             "magpie_set_precision": (ctypes.c_int, [vp, i32]),
             "magpie_set_variant": (ctypes.c_int, [vp, i32]),
             "magpie_dft2_tc": (ctypes.c_int, [vp, vp, i32, i32, i32, vp]),
+            "magpie_dft2_tcgen05": (ctypes.c_int, [vp, vp, i32, i32, i32, vp]),
             "magpie_fp32_fma_rate": (ctypes.c_int, [i32, dp, dp, vp]),
             "magpie_stage_times": (ctypes.c_int, [vp, vp, i32, vp, ctypes.c_int64]),
             "magpie_window_blocks": (i32, [i32]),
@@ -428,15 +429,17 @@ def magpie_set_variant(ctx: Context, flags: int) -> None:
 
 # ----------------------------------------------------------- precision form
 def magpie_set_precision(ctx: Context, mode: int) -> None:
+    """0: FP32 FFTs; 1: tensor-core DFTs with mma.sync; 2: with tcgen05."""
     _check(lib().magpie_set_precision(ctx.handle, int(mode)))
 
 
-def magpie_dft2_tc(x: torch.Tensor, inverse: bool = False) -> torch.Tensor:
-    """2-D DFTs of x [count][m][m] (complex64, CUDA) by the tensor-core path."""
+def magpie_dft2_tc(x: torch.Tensor, inverse: bool = False, path: int = 1) -> torch.Tensor:
+    """2-D DFTs of x [count][m][m] (complex64, CUDA) by the tensor-core path
+    (path 1: mma.sync, 2: tcgen05; the numbering of magpie_set_precision)."""
     count, m, _ = x.shape
     out = torch.empty_like(x)
-    _check(lib().magpie_dft2_tc(_dev(x, torch.complex64, count * m * m, "x"), out.data_ptr(), m, count,
-                                int(bool(inverse)), _stream()))
+    fn = lib().magpie_dft2_tcgen05 if path == 2 else lib().magpie_dft2_tc
+    _check(fn(_dev(x, torch.complex64, count * m * m, "x"), out.data_ptr(), m, count, int(bool(inverse)), _stream()))
     return out
 
 

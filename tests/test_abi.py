@@ -150,4 +150,8 @@ def test_learned_and_precision_entry_points_without_a_gpu(L):
     x = ctypes.c_void_p(16)
     assert L.magpie_dft2_tc(x, x, 32, 1, 0, None) == magpie.EUNSUPPORTED      # m not 64/128/256
     assert L.magpie_dft2_tc(x, x, 64, 0, 0, None) == magpie.EINVAL            # no windows
+    assert L.magpie_dft2_tcgen05(None, None, 64, 1, 0, None) == magpie.EINVAL
+    assert L.magpie_dft2_tcgen05(x, x, 32, 1, 0, None) == magpie.EUNSUPPORTED
+    assert L.magpie_dft2_tcgen05(x, x, 64, 1, 2, None) == magpie.EINVAL        # inverse not 0/1
+    assert L.magpie_set_precision(None, 2) == magpie.EINVAL
     L.magpie_cnn_destroy(None)

@@ -1,6 +1,8 @@
 """GPU parity of the precision form (tensor-core BF16 hi+lo DFTs) against the
 FP64 oracle: the transforms themselves, single minibatch steps at small and
-full window size, and a run of sweeps.  Every check prints its error."""
+full window size, and a run of sweeps, each on both tensor-core paths
+(path 1: register-fragment mma.sync; path 2: tcgen05 with TMEM
+accumulators).  Every check prints its error."""
 import numpy as np
 import pytest
 import torch
@@ -11,6 +13,7 @@ from paper_2504_10118_gb300 import magpie, synth
 pytestmark = pytest.mark.gpu
 
 DEV = torch.device("cuda")
+PATHS = [1, 2]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -23,21 +26,22 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("m", [64, 128, 256])
-def test_dft2_matches_library_fft(m):
+def test_dft2_matches_library_fft(m, path):
     """Forward and conjugate 2-D DFTs of random windows against numpy's FFT in
     float64: relative error per window within the hi+lo BF16 bound (a few
     2^-16 per product, four products deep)."""
     rng = np.random.default_rng(m)
     x = (rng.normal(size=(4, m, m)) + 1j * rng.normal(size=(4, m, m))).astype(np.complex64)
     xd = torch.from_numpy(x).to(DEV)
-    X = magpie.magpie_dft2_tc(xd).cpu().numpy()
-    Xi = magpie.magpie_dft2_tc(xd, inverse=True).cpu().numpy()
+    X = magpie.magpie_dft2_tc(xd, path=path).cpu().numpy()
+    Xi = magpie.magpie_dft2_tc(xd, inverse=True, path=path).cpu().numpy()
     for c in range(4):
         ref = O.fft2(x[c].astype(np.complex128))
         refi = O.ifft2(x[c].astype(np.complex128)) * m * m
         e, ei = rel(X[c], ref), rel(Xi[c], refi)
-        print(f"m={m} window {c}: forward {e:.2e} inverse {ei:.2e}")
+        print(f"path {path} m={m} window {c}: forward {e:.2e} inverse {ei:.2e}")
         assert e < 4e-5 and ei < 4e-5
 
 
@@ -54,27 +58,28 @@ def small_problem(levels):
     return n, m, Q, pos, d, z0
 
 
-def make_ctx(n, m, Q, pos, d, z0, levels, minibatch, alpha=0.1):
+def make_ctx(n, m, Q, pos, d, z0, levels, minibatch, alpha=0.1, path=1):
     zt = torch.from_numpy(z0.astype(np.complex64)).to(DEV)
     p = magpie.magpie_params_of(n, n, m, len(pos), levels, minibatch, alpha)
     ctx = magpie.magpie_create(p, zt, torch.from_numpy(Q.astype(np.complex64)).to(DEV),
                                torch.from_numpy(pos.astype(np.int32)).to(DEV),
                                torch.from_numpy(d.astype(np.float32)).to(DEV))
-    magpie.magpie_set_precision(ctx, 1)
+    magpie.magpie_set_precision(ctx, path)
     return ctx, zt
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("levels", [1, 3])
-def test_precision_step_matches_oracle(levels):
+def test_precision_step_matches_oracle(levels, path):
     n, m, Q, pos, d, z0 = small_problem(levels)
-    ctx, zt = make_ctx(n, m, Q, pos, d, z0, levels, 8)
+    ctx, zt = make_ctx(n, m, Q, pos, d, z0, levels, 8, path=path)
     batch = np.array([3, 7, 11, 12, 13, 17, 21, 24], dtype=np.int32)
     magpie.magpie_step(ctx, torch.from_numpy(batch).to(DEV))
     u = O.rpie_regulariser(Q, 0.1)
     zo = O.minibatch_step(z0, Q, pos, d, u, levels, list(batch))
     zg = zt.cpu().numpy()
     e, de = rel(zg, zo), rel(zg - z0, zo - z0)
-    print(f"levels={levels}: object {e:.2e}, increment {de:.2e}")
+    print(f"path {path} levels={levels}: object {e:.2e}, increment {de:.2e}")
     assert e < 1e-5 and de < 1e-4
     phi, gn = magpie.magpie_window_values(ctx)
     for k in batch:
@@ -82,7 +87,8 @@ def test_precision_step_matches_oracle(levels):
         assert abs(phi[k].item() - O.objective_k(zk, Q, d[k])) < 1e-4 * O.objective_k(zk, Q, d[k])
 
 
-def test_precision_step_m128_matches_oracle():
+@pytest.mark.parametrize("path", PATHS)
+def test_precision_step_m128_matches_oracle(path):
     """The fused transform kernels at m = 128 (eight 16-line blocks per
     window): one 8-window step with three levels, noise-free, from a state
     near the object, against the oracle; and each window's Phi_k."""
@@ -94,13 +100,13 @@ def test_precision_step_m128_matches_oracle():
     rng = np.random.default_rng(10)
     z0 = z_true * (1 + 0.05 * (rng.normal(size=z_true.shape) + 1j * rng.normal(size=z_true.shape)))
     z0 = z0.astype(np.complex64).astype(np.complex128)
-    ctx, zt = make_ctx(n, m, Q, pos, d, z0, 3, 8)
+    ctx, zt = make_ctx(n, m, Q, pos, d, z0, 3, 8, path=path)
     batch = np.array([0, 2, 5, 7, 8, 11, 13, 15], dtype=np.int32)
     magpie.magpie_step(ctx, torch.from_numpy(batch).to(DEV))
     zo = O.minibatch_step(z0, Q, pos, d, O.rpie_regulariser(Q, 0.1), 3, list(batch))
     zg = zt.cpu().numpy()
     e, de = rel(zg, zo), rel(zg - z0, zo - z0)
-    print(f"m=128 L=3 B=8: object {e:.2e}, increment {de:.2e}")
+    print(f"path {path} m=128 L=3 B=8: object {e:.2e}, increment {de:.2e}")
     assert e < 1e-5 and de < 1e-3
     phi, _ = magpie.magpie_window_values(ctx)
     for k in batch:
@@ -117,7 +123,7 @@ def fp32_ctx(n, m, Q, pos, d, z0, levels, minibatch, alpha=0.1):
     return ctx, zt
 
 
-def transform_error_ratio(z_true, Q, pos):
+def transform_error_ratio(z_true, Q, pos, path=1):
     """Relative error of the windows' intensities |F(Q z_k)|^2 by the
     tensor-core transform over that of the FP32 FFT path (the library's
     forward model), both against the oracle, on the same windows."""
@@ -127,13 +133,14 @@ def transform_error_ratio(z_true, Q, pos):
     pt = torch.from_numpy(pos.astype(np.int32)).to(DEV)
     i32 = magpie.magpie_forward_intensities(zt, Qt, pt, m).cpu().numpy()
     psi = np.stack([Q * O.extract(z_true, p, m) for p in pos]).astype(np.complex64)
-    itc = np.abs(magpie.magpie_dft2_tc(torch.from_numpy(psi).to(DEV)).cpu().numpy()) ** 2
+    itc = np.abs(magpie.magpie_dft2_tc(torch.from_numpy(psi).to(DEV), path=path).cpu().numpy()) ** 2
     ref = O.forward_intensities(z_true, Q, pos)
     return rel(itc, ref) / rel(i32, ref)
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("start", ["near", "flat"])
-def test_precision_full_size_step(start):
+def test_precision_full_size_step(start, path):
     """The precision workload's sizes (n = 1024, m = 256, 4 levels): one 64-window
     minibatch step against the oracle (the context holds just those windows),
     from a state near the object and from the flat start z = 1."""
@@ -148,7 +155,7 @@ def test_precision_full_size_step(start):
         rng = np.random.default_rng(9)
         z0 = z_true * (1 + 0.02 * (rng.normal(size=z_true.shape) + 1j * rng.normal(size=z_true.shape)))
         z0 = z0.astype(np.complex64).astype(np.complex128)
-    ctx, zt = make_ctx(w.n, w.m, Q, sub, d, z0, w.levels, w.minibatch)
+    ctx, zt = make_ctx(w.n, w.m, Q, sub, d, z0, w.levels, w.minibatch, path=path)
     ctx32, z32 = fp32_ctx(w.n, w.m, Q, sub, d, z0, w.levels, w.minibatch)
     idx = torch.arange(w.minibatch, dtype=torch.int32, device=DEV)
     magpie.magpie_step(ctx, idx)
@@ -156,8 +163,8 @@ def test_precision_full_size_step(start):
     u = O.rpie_regulariser(Q, w.alpha)
     zo = O.minibatch_step(z0, Q, sub, d, u, w.levels, list(range(w.minibatch)))
     e_tc, e_32 = rel(zt.cpu().numpy(), zo), rel(z32.cpu().numpy(), zo)
-    ratio = transform_error_ratio(z_true, Q, sub[:8])
-    print(f"n=1024 m=256 L=4 B=64, {start} start: object error tensor-core {e_tc:.2e}, FP32 FFT {e_32:.2e}; "
+    ratio = transform_error_ratio(z_true, Q, sub[:8], path)
+    print(f"path {path} n=1024 m=256 L=4 B=64, {start} start: object error tensor-core {e_tc:.2e}, FP32 FFT {e_32:.2e}; "
           f"transform error ratio {ratio:.1f}")
     # Where the projection amplifies rounding (|Psi| tiny against sqrt(d), as
     # at a flat start) both paths' errors grow by the same conditioning
@@ -166,11 +173,12 @@ def test_precision_full_size_step(start):
     assert e_tc < max(1e-5, 2 * ratio * e_32)
 
 
-def test_precision_sweeps_track_oracle():
+@pytest.mark.parametrize("path", PATHS)
+def test_precision_sweeps_track_oracle(path):
     """Twenty sweeps from the same start: NRMSE between the GPU and the oracle
     iterates, against that of the FP32 FFT path."""
     n, m, Q, pos, d, z0 = small_problem(3)
-    ctx, zt = make_ctx(n, m, Q, pos, d, z0, 3, 8)
+    ctx, zt = make_ctx(n, m, Q, pos, d, z0, 3, 8, path=path)
     ctx32, z32 = fp32_ctx(n, m, Q, pos, d, z0, 3, 8)
     u = O.rpie_regulariser(Q, 0.1)
     zo = z0.copy()
@@ -182,6 +190,6 @@ def test_precision_sweeps_track_oracle():
     mask = O.illuminated_mask(Q, pos, zo.shape)
     e_tc = O.nrmse(zt.cpu().numpy(), zo, mask)
     e_32 = O.nrmse(z32.cpu().numpy(), zo, mask)
-    ratio = transform_error_ratio(O.extract(zo, (0, 0), n), Q, pos[:8])
-    print(f"20 sweeps: NRMSE vs oracle tensor-core {e_tc:.2e}, FP32 FFT {e_32:.2e}; transform error ratio {ratio:.1f}")
+    ratio = transform_error_ratio(O.extract(zo, (0, 0), n), Q, pos[:8], path)
+    print(f"path {path} 20 sweeps: NRMSE vs oracle tensor-core {e_tc:.2e}, FP32 FFT {e_32:.2e}; transform error ratio {ratio:.1f}")
     assert e_tc < max(1e-4, 2 * ratio * e_32)
