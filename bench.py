@@ -660,7 +660,7 @@ def launches_per_step(args, w) -> int:
     """Kernel launches of one minibatch step of the configured form."""
     if args.learned:
         return 1 + 1 + 1 + 6 + 4 + 1 + 1  # window, coarse state, cast, 6 convolutions, split-K sums, V-cycle, update
-    if args.dft == "tc":
+    if args.dft in ("tc", "tcgen05"):
         # exit wave + column DFTs, row DFTs + projection, inverse column DFTs + g^0,
         # coarse levels, finest level, update
         return 3 + (1 if w.levels >= 3 else 0) + (1 if w.levels >= 2 else 0) + 1
@@ -710,8 +710,8 @@ def run_ours(args, w):
     z = torch.ones((w.n, w.n), dtype=torch.complex64, device=dev)
     ctx = magpie.magpie_create(magpie.magpie_params_of(w.n, w.n, w.m, w.n_pos, w.levels, w.minibatch, w.alpha,
                                                        deterministic=det), z, Qt, post, dt)
-    if args.dft == "tc":
-        magpie.magpie_set_precision(ctx, 1)
+    if args.dft in ("tc", "tcgen05"):
+        magpie.magpie_set_precision(ctx, 2 if args.dft == "tcgen05" else 1)
     net = None
     train_info = None
     if args.learned:
@@ -825,10 +825,13 @@ def run_ours(args, w):
             "metric": "patterns/s per sweep", "value": value, "unit": "patterns/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16x3 (hi+lo) DFTs, f32" if args.dft == "tc" else ("f32 + bf16 network" if args.learned else "f32"),
+            "dtype": "bf16x3 (hi+lo) DFTs, f32" if args.dft in ("tc", "tcgen05")
+                     else ("f32 + bf16 network" if args.learned else "f32"),
             "data": "synthetic (seeded object, probe, raster and Poisson noise)",
             "config": dict(config_of(w), workload=("learned correction on " + w.name) if args.learned else w.name,
-                           dft="tensor-core BF16 hi+lo" if args.dft == "tc" else "FP32 FFT",
+                           dft={"tc": "tensor-core BF16 hi+lo (mma.sync)",
+                                "tcgen05": "tensor-core BF16 hi+lo (tcgen05, TMEM accumulators)"}.get(args.dft,
+                                                                                                  "FP32 FFT"),
                            update="ordered" if det else "atomic"),
             "quality": quality,
             "update_ab": update_ab,
@@ -873,8 +876,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(synth.WORKLOADS) + ["batched", "learned"], default="mid")
-    ap.add_argument("--dft", choices=["fft", "tc"], default=None,
-                    help="fft: FP32 FFT path; tc: tensor-core BF16 hi+lo DFTs (default for the precision workload)")
+    ap.add_argument("--dft", choices=["fft", "tc", "tcgen05"], default=None,
+                    help="fft: FP32 FFT path; tc: tensor-core BF16 hi+lo DFTs on mma.sync (default for the "
+                         "precision workload); tcgen05: the same DFTs on tcgen05 with TMEM accumulators")
     ap.add_argument("--update", choices=["atomic", "ordered"], default="atomic",
                     help="update of the FP32 form: float-atomic accumulation (default) or the ordered, bitwise "
                          "reproducible reduction; the other one is timed too (update_ab)")
