@@ -786,7 +786,7 @@ def run_ours(args, w):
                          note="same data and sweep orders; per-kernel times from event-bracketed launches")
 
     # end to end through the host-buffer call: order + intensities in, object out
-    order_h = [torch.from_numpy(synth.make_order(w.n_pos, 1000 + s)).pin_memory() for s in range(args.steps)]
+    order_h = [torch.from_numpy(synth.make_order(w.n_pos, 1000 + s)).pin_memory() for s in range(max(2, args.steps))]
     d_pin = torch.from_numpy(d_host).pin_memory()
     z_out = torch.empty((w.n, w.n), dtype=torch.complex64).pin_memory()
     for s in range(2):  # both data buffers allocated and their sweep graphs captured, untimed
