@@ -378,6 +378,7 @@ def batched_measure(dev, magpie, warmup: int, steps: int, pg=None, clocks=None):
         torch.cuda.synchronize()
         if pg:
             pg.barrier()
+        hold_gpu(min(100.0, 5.0 + 0.25 * steps))
         for s in range(steps):
             flush.zero_()
             ev0[s].record(stream)
@@ -632,9 +633,58 @@ def precision_record(dev, magpie, warmup: int = 2, steps: int = 3) -> dict:
     return rec
 
 
+def learned_record(dev, magpie, warmup: int = 3, steps: int = 5) -> dict:
+    """patterns/s of the learned form on the mid workload (its network
+    generated and trained first, untimed, as `--workload learned` does),
+    beside the plain FP32 form with the ordered update on the same data."""
+    import torch
+    from paper_2504_10118_gb300 import learned
+    w = synth.WORKLOADS["mid"]
+    z_true, Qt, post, dt, _ = make_data(w, dev, magpie)
+    t0 = time.perf_counter()
+    data = learned.generate(w, seeds=[11, 12, 13], stages=[0, 1, 2, 3, 4, 6, 8, 12, 16, 24], per_stage=100,
+                            dev=dev, final_sweeps=60)
+    net = magpie.magpie_cnn_create(learned.coarse_side(w.m, w.levels), w.minibatch)
+    magpie.magpie_cnn_set_params(net, learned.initial_params(dev=dev))
+    losses = learned.train(net, data, epochs=40, batch=64, lr=3e-4)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    orders = torch.from_numpy(np.stack([synth.make_order(w.n_pos, s) for s in range(warmup + steps)])).to(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    rec = {"config": dict(config_of(w), workload="learned correction on " + w.name),
+           "training": {"pairs": len(data), "epochs": 40, "loss_first_epoch": float(losses[0]),
+                        "loss_last_epoch": float(losses[-1]), "seconds": train_s,
+                        "untimed": "generation and training run before the timed sweeps"}}
+    for name, attach in (("learned", True), ("plain_ordered", False)):
+        z = torch.ones((w.n, w.n), dtype=torch.complex64, device=dev)
+        ctx = magpie.magpie_create(magpie.magpie_params_of(w.n, w.n, w.m, w.n_pos, w.levels, w.minibatch, w.alpha),
+                                   z, Qt, post, dt)
+        if attach:
+            magpie.magpie_attach_cnn(ctx, net)
+        ms = time_sweeps(magpie, ctx, orders, warmup, steps, flush, torch.cuda.current_stream())
+        rec[name] = {"value": steps * w.n_pos / (ms * 1e-3), "unit": "patterns/s", "ms_per_step": ms / steps}
+        if attach:
+            kept, total = magpie.magpie_learned_stats(ctx)[::-1]
+            rec[name]["proposals_kept"], rec[name]["proposals"] = kept, total
+        ctx.close()
+    net.close()
+    return rec
+
+
+def hold_gpu(ms: float = 20.0) -> None:
+    """A bounded spin kernel (about `ms` of GPU time) on the current stream,
+    so that the host queues the timed work behind it instead of racing the
+    GPU: a timed interval then never includes the GPU waiting for the host's
+    next submission (host jitter on a shared machine once inflated a sweep's
+    event-timed interval by a third)."""
+    import torch
+    torch.cuda._sleep(int(ms * 1e-3 * 2.07e9))
+
+
 def time_sweeps(magpie, ctx, orders, warmup: int, steps: int, flush, stream, pg=None) -> float:
     """Milliseconds of `steps` sweeps after `warmup` untimed ones, each timed
-    with CUDA events on `stream` after an L2 flush (outside the events)."""
+    with CUDA events on `stream` after an L2 flush (outside the events), the
+    timed sweeps queued behind a short GPU hold (hold_gpu)."""
     import torch
     for s in range(warmup):
         magpie.magpie_sweep(ctx, orders[s])
@@ -644,6 +694,7 @@ def time_sweeps(magpie, ctx, orders, warmup: int, steps: int, flush, stream, pg=
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
+    hold_gpu(min(100.0, 5.0 + 0.25 * steps))
     for s in range(steps):
         flush.zero_()
         ev0[s].record(stream)
@@ -808,6 +859,7 @@ def run_ours(args, w):
     batched = None
     if extras:
         batched, _, _, _ = batched_measure(dev, magpie, 3, 5)
+    learned_rec = learned_record(dev, magpie) if extras else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -839,6 +891,7 @@ def run_ours(args, w):
             "precision": prec,
             "batched": batched,
             "training": train_info,
+            "learned": learned_rec,
             "roofline": ({"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": achieved_tf / alu_peak, "traffic": traffic,
                          "kernel": f"window_kernel<{w.m}, {'step' if det else 'step_atomic'}>",
