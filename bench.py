@@ -75,7 +75,7 @@ def tc_flops_per_window(m: int) -> float:
     """Tensor-core flops of one window in the precision form: a forward and an
     inverse 2-D DFT, each 2 m lines x 2 stages of real block GEMMs
     (stage 1: 32 x 32 by 32 x m/16; stage 2: m rows x K x 2 m/16 with K the
-    stage's padded depth), three BF16 products each for the hi+lo split."""
+    stage's padded depth), three FP16 products each for the hi+lo split."""
     qr = m // 16
     k2 = 16 * ((2 * qr + 15) // 16)
     per_line = 2 * 32 * 32 * qr + 2 * 16 * k2 * 2 * qr
@@ -520,7 +520,7 @@ def sweeps_to_nrmse(w, dev, magpie, target: float, max_sweeps: int, every: int =
     ctx = magpie.magpie_create(magpie.magpie_params_of(w.n, w.n, w.m, w.n_pos, w.levels, w.minibatch, w.alpha,
                                                        deterministic=deterministic), z, Qt, post, dt)
     if precision:
-        magpie.magpie_set_precision(ctx, 1)
+        magpie.magpie_set_precision(ctx, precision)
     if net is not None:
         magpie.magpie_attach_cnn(ctx, net)
     orders = torch.from_numpy(np.stack([synth.make_order(w.n_pos, i) for i in range(max_sweeps)])).to(dev)
@@ -544,7 +544,8 @@ def sweeps_to_nrmse(w, dev, magpie, target: float, max_sweeps: int, every: int =
     out = {"levels": w.levels, "minibatch": w.minibatch, "alpha": w.alpha, "reached": err <= target,
            "sweeps": sweeps, "seconds": ms * 1e-3, "wall_seconds": wall, "nrmse": err, "best_nrmse": best,
            "update": "ordered" if deterministic else "atomic",
-           "dft": "tensor-core BF16 hi+lo" if precision else "FP32 FFT",
+           "dft": {1: "tensor-core FP16 hi+lo (mma.sync)", 2: "tensor-core FP16 hi+lo (tcgen05)"}.get(precision,
+                                                                                              "FP32 FFT"),
            "learned": net is not None}
     if net is not None:
         out["proposals_kept"], out["proposals"] = magpie.magpie_learned_stats(ctx)[::-1]
@@ -733,7 +734,9 @@ def tensor_roofline(args, w, windows, wk_ms, ap_ms, prof_sweeps, launches, pk, s
     peak = pk.get("bf16_tflops", 1900.0)
     return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
             "traffic": None, "kernel": what, "avg_launch_ms": wk_ms / max(launches, 1),
-            "peak_source": f"bf16 dense, {src}", "tensor_flops_per_window": fl,
+            "peak_source": (f"bf16 dense, {src} (the precision form's FP16 products: the same nominal dense "
+                            f"rate as BF16, ratio 1)" if not args.learned else f"bf16 dense, {src}"),
+            "tensor_flops_per_window": fl,
             "apply_kernel_ms_per_sweep": ap_ms / prof_sweeps, "window_phase_ms_per_sweep": wk_ms / prof_sweeps}
 
 
@@ -877,12 +880,12 @@ def run_ours(args, w):
             "metric": "patterns/s per sweep", "value": value, "unit": "patterns/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16x3 (hi+lo) DFTs, f32" if args.dft in ("tc", "tcgen05")
+            "dtype": "fp16x3 (hi+lo) DFTs, f32" if args.dft in ("tc", "tcgen05")
                      else ("f32 + bf16 network" if args.learned else "f32"),
             "data": "synthetic (seeded object, probe, raster and Poisson noise)",
             "config": dict(config_of(w), workload=("learned correction on " + w.name) if args.learned else w.name,
-                           dft={"tc": "tensor-core BF16 hi+lo (mma.sync)",
-                                "tcgen05": "tensor-core BF16 hi+lo (tcgen05, TMEM accumulators)"}.get(args.dft,
+                           dft={"tc": "tensor-core FP16 hi+lo (mma.sync)",
+                                "tcgen05": "tensor-core FP16 hi+lo (tcgen05, TMEM accumulators)"}.get(args.dft,
                                                                                                   "FP32 FFT"),
                            update="ordered" if det else "atomic"),
             "quality": quality,
@@ -930,7 +933,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(synth.WORKLOADS) + ["batched", "learned"], default="mid")
     ap.add_argument("--dft", choices=["fft", "tc", "tcgen05"], default=None,
-                    help="fft: FP32 FFT path; tc: tensor-core BF16 hi+lo DFTs on mma.sync (default for the "
+                    help="fft: FP32 FFT path; tc: tensor-core FP16 hi+lo DFTs on mma.sync (default for the "
                          "precision workload); tcgen05: the same DFTs on tcgen05 with TMEM accumulators")
     ap.add_argument("--update", choices=["atomic", "ordered"], default="atomic",
                     help="update of the FP32 form: float-atomic accumulation (default) or the ordered, bitwise "

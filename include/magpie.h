@@ -441,11 +441,13 @@ int magpie_learned_window_values(magpie_ctx* ctx, int32_t count, int32_t* accept
  * Precision form: the windows' 2-D DFTs as tensor-core GEMMs.  An m-point
  * line DFT (m = 16 Qr) is two complex matrix products, 16-point DFTs then
  * Qr-point DFTs with FP32 twiddles between them (Cooley-Tukey); each product
- * runs on BF16 tensor cores with hi+lo split operands (a = hi + lo, both
- * BF16; a b taken as hi hi + hi lo + lo hi) and FP32 accumulation, so a
- * transform carries a relative error of about 1e-5 (2^-16 per product) where
- * the FP32 FFT path carries about 1e-6.  The projection, the V-cycle and the
- * update are the FP32 path's; Phi_k and the gradient norms stay FP64 sums.
+ * runs on FP16 tensor cores with hi+lo split operands (a = hi + lo, both
+ * FP16, 22 significant bits together; a b taken as hi hi + hi lo + lo hi) and
+ * FP32 accumulation.  Each block scales its lines by a power of two into
+ * FP16's range and divides the outputs by it (both exact), so any finite
+ * input is transformed; a transform carries a relative error of about 5e-7
+ * to 7e-7 (the FP32 FFT path about 1e-7).  The projection, the V-cycle and
+ * the update are the FP32 path's; Phi_k and the gradient norms stay FP64.
  * mode 0: FP32 FFT path (default); mode 1: tensor-core DFTs with
  * register-fragment MMAs (mma.sync m16n8k16); mode 2: the same DFTs on the
  * 5th-generation tensor cores (tcgen05.mma, operands in shared memory,

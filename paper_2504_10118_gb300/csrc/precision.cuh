@@ -1,5 +1,5 @@
 // precision.cuh -- the precision form of the sweep: the windows' 2-D DFTs as
-// tensor-core GEMMs with BF16 hi+lo split operands and FP32 accumulation,
+// tensor-core GEMMs with FP16 hi+lo split operands and FP32 accumulation,
 // around the same projection, V-cycle and update as the FP32 path.  Included
 // by magpie.cu inside namespace magpie_impl.
 //
@@ -9,9 +9,13 @@
 //   twiddle  Y'[k1][n2] = Y[k1][n2] w_m^{n2 k1}                     (FP32)
 //   stage 2  X[k1 + 16 k2] = sum_{n2} Y'[k1][n2] F_Qr[n2][k2]       (Qr-point DFTs)
 // Each complex product is one real GEMM on [re; im] blocks; every operand
-// a = hi + lo with hi = bf16(a), lo = bf16(a - hi), and a b is taken as
-// hi_a hi_b + hi_a lo_b + lo_a hi_b (the lo lo term, below 2^-16 |a b|, is
-// dropped), three m16n8k16 BF16 MMAs with FP32 accumulation.
+// a = hi + lo with hi = fp16(a), lo = fp16(a - hi) (22 significant bits
+// together), and a b is taken as hi_a hi_b + hi_a lo_b + lo_a hi_b (the lo lo
+// term, below 2^-22 |a b|, is dropped), three FP16 MMAs with FP32
+// accumulation.  FP16's range is kept by scaling the block's lines by a power
+// of two s (max |s x| in [2^9, 2^10), so that stage 2's operands, sums of 32
+// stage-1 products, stay below 2^15) and dividing the outputs by s, both
+// exact.
 #pragma once
 
 constexpr int kTcLines = 16;  // lines per block
@@ -26,23 +30,31 @@ struct TcTables {
   float fq[2][32 * 32];
 };
 
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+__device__ __forceinline__ uint32_t pack_f16(__half a, __half b) {
+  __half2 v = __halves2half2(a, b);
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
-// hi and lo BF16 pairs of (a, b)
+// hi and lo FP16 pairs of (a, b)
 __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
-  const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
-  hi = pack_bf16(__bfloat162float(ha), __bfloat162float(hb));
-  lo = pack_bf16(a - __bfloat162float(ha), b - __bfloat162float(hb));
+  const __half ha = __float2half_rn(a), hb = __float2half_rn(b);
+  hi = pack_f16(ha, hb);
+  lo = pack_f16(__float2half_rn(a - __half2float(ha)), __float2half_rn(b - __half2float(hb)));
+}
+
+__device__ __forceinline__ void mma_f16(float* c, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
 __device__ __forceinline__ void mma3(float* c, const uint32_t* ah, const uint32_t* al, const uint32_t* bh,
                                      const uint32_t* bl) {
-  mma_bf16(c, ah, bh);
-  mma_bf16(c, ah, bl);
-  mma_bf16(c, al, bh);
+  mma_f16(c, ah, bh);
+  mma_f16(c, ah, bl);
+  mma_f16(c, al, bh);
 }
 
 // Shared-memory layout of a block's kTcLines lines: separate real and
@@ -99,6 +111,29 @@ __device__ __forceinline__ void tc_store(const float* Sr, const float* Si, Dst d
   }
 }
 
+// The power of two s of the FP16 operands (see the top of this file): max
+// |s x| over the block's lines in [2^9, 2^10); 1 for all-zero or non-finite
+// lines.  128 threads; the lines must be in place; one barrier.
+template <int MS>
+__device__ __forceinline__ float tc_scale(const float* Sr, const float* Si) {
+  using S = TcSm<MS>;
+  __shared__ float red[4];
+  float mx = 0.f;
+  for (int i = threadIdx.x; i < S::NL * MS; i += 128) {
+    const int l = i / MS, p = i % MS;
+    mx = fmaxf(mx, fmaxf(fabsf(Sr[S::at(l, p)]), fabsf(Si[S::at(l, p)])));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  mx = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
+  if (!(mx > 0.f) || !(mx <= 3.0e38f)) return 1.f;
+  int e;
+  frexpf(mx, &e);  // mx = f 2^e, f in [0.5, 1)
+  return ldexpf(1.f, 10 - e);
+}
+
 // The forward (INV = 0) or conjugate (INV = 1) DFT of the block's NL lines,
 // in place in shared memory, the output multiplied by `scale`.  128 threads;
 // begins with a barrier (the lines must be in place) and ends with one.
@@ -111,6 +146,8 @@ __device__ __forceinline__ void tc_lines(float* Sr, float* Si, const TcTables* _
   constexpr int N2T = 2 * QR / 8;          // stage-2 n-tiles
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
+  __syncthreads();  // the lines in place
+  const float sx = tc_scale<MS>(Sr, Si), out_scale = scale / sx;
 
   // ---- stage-1 operands: the 16-point DFT matrix as A fragments (hi, lo)
   uint32_t ah[2][2][4], al[2][2][4];
@@ -147,10 +184,10 @@ __device__ __forceinline__ void tc_lines(float* Sr, float* Si, const TcTables* _
     uint32_t bh[2][2], bl[2][2];
     // k-tile 0: real parts of n1 = 2t, 2t+1, 2t+8, 2t+9; k-tile 1: imaginary parts
     constexpr int RS = QR + 4;
-    split2(xr[RS * (2 * t)], xr[RS * (2 * t + 1)], bh[0][0], bl[0][0]);
-    split2(xr[RS * (2 * t + 8)], xr[RS * (2 * t + 9)], bh[0][1], bl[0][1]);
-    split2(xi[RS * (2 * t)], xi[RS * (2 * t + 1)], bh[1][0], bl[1][0]);
-    split2(xi[RS * (2 * t + 8)], xi[RS * (2 * t + 9)], bh[1][1], bl[1][1]);
+    split2(sx * xr[RS * (2 * t)], sx * xr[RS * (2 * t + 1)], bh[0][0], bl[0][0]);
+    split2(sx * xr[RS * (2 * t + 8)], sx * xr[RS * (2 * t + 9)], bh[0][1], bl[0][1]);
+    split2(sx * xi[RS * (2 * t)], sx * xi[RS * (2 * t + 1)], bh[1][0], bl[1][0]);
+    split2(sx * xi[RS * (2 * t + 8)], sx * xi[RS * (2 * t + 9)], bh[1][1], bl[1][1]);
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
@@ -231,7 +268,7 @@ __device__ __forceinline__ void tc_lines(float* Sr, float* Si, const TcTables* _
       for (int e = 0; e < 4; ++e) {
         const int k1 = g + 8 * (e >> 1);
         const int nn = nt * 8 + 2 * t + (e & 1);
-        const float v = out[i][nt][e] * scale;
+        const float v = out[i][nt][e] * out_scale;
         if (nn < QR)
           Sr[S::at(l, k1 + 16 * nn)] = v;
         else
@@ -249,8 +286,8 @@ __device__ __forceinline__ void tc_lines(float* Sr, float* Si, const TcTables* _
 //   stage 2: D[(line, k1)][nn] = sum_kk Y'[(line, k1)][kk] fq[kk][nn], 256
 //            rows in two tiles, K = N = 2 QR (both padded to 16 for m = 64).
 // For each tile the threads write the A rows, one per thread, as hi and lo
-// BF16 into a 64-byte-swizzled K-major buffer; thread 0 issues the
-// tcgen05.mma (hi hi + hi lo + lo hi per 16-deep K step) into 32 TMEM
+// FP16 into a 64-byte-swizzled K-major buffer; thread 0 issues the
+// tcgen05.mma (hi hi + hi lo + lo hi per 16-deep K step, FP16 operands) into 32 TMEM
 // columns and commits them to an mbarrier; every thread waits (bounded),
 // reads its row of the accumulator with tcgen05.ld, and does the twiddle
 // (stage 1) or the scaled store (stage 2) in FP32 from registers.  The B
@@ -264,7 +301,7 @@ struct TcUmma {
 };
 constexpr int kUmmaDftSmem = 2 * 8192 + 4 * 2048 + 1024;  // operand buffers + 1024-byte alignment slack
 
-// hi and lo BF16 of 8 consecutive K elements (one 16-byte chunk), chunk c of
+// hi and lo FP16 of 8 consecutive K elements (one 16-byte chunk), chunk c of
 // row r of the two 64-byte-swizzled buffers
 __device__ __forceinline__ void put_chunk(uint32_t hi_base, uint32_t lo_base, int r, int c, const float (&v)[8]) {
   uint32_t h[4], l[4];
@@ -289,14 +326,14 @@ __device__ __forceinline__ void umma_tile(TcUmma& U, uint32_t b_hi, uint32_t b_l
   __syncthreads();
   if (threadIdx.x == 0) {
     umma::fence_after();
-    constexpr uint32_t ID = umma::idesc_bf16(128, N);
+    constexpr uint32_t ID = umma::idesc_f16(128, N);
     for (int k = 0; k < KS; ++k) {
       const uint32_t o = 32u * (uint32_t)k;
       const uint64_t ah = umma::desc_sw64(U.a_hi + o), al = umma::desc_sw64(U.a_lo + o);
       const uint64_t bh = umma::desc_sw64(b_hi + o), bl = umma::desc_sw64(b_lo + o);
-      umma::mma_bf16_ss(U.tmem, ah, bh, ID, k != 0);
-      umma::mma_bf16_ss(U.tmem, ah, bl, ID, 1);
-      umma::mma_bf16_ss(U.tmem, al, bh, ID, 1);
+      umma::mma_ss(U.tmem, ah, bh, ID, k != 0);
+      umma::mma_ss(U.tmem, ah, bl, ID, 1);
+      umma::mma_ss(U.tmem, al, bh, ID, 1);
     }
     umma::commit(U.bar);
   }
@@ -313,6 +350,8 @@ __device__ __forceinline__ void tc_lines_umma(float* Sr, float* Si, const TcTabl
   constexpr int Q2 = 2 * QR < 16 ? 16 : 2 * QR;  // stage-2 K and N, padded to 16
   const int tid = threadIdx.x;
   const uint32_t trow = U.tmem + ((uint32_t)(tid & ~31) << 16);  // this warp's TMEM lanes
+  __syncthreads();  // the lines in place
+  const float sx = tc_scale<MS>(Sr, Si), out_scale = scale / sx;
   // B operands: stage 1 rows r, K c: f16[r][c]; stage 2 rows nn, K kk: fq[kk][nn] (0 in the padding)
   {
     const float* F1 = tabs->f16[INV];
@@ -347,7 +386,7 @@ __device__ __forceinline__ void tc_lines_umma(float* Sr, float* Si, const TcTabl
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const int kk = 8 * c + k, n1 = kk & 15;
-        v[k] = live ? (kk < 16 ? Sr : Si)[S::at(l, QR * n1 + n2)] : 0.f;
+        v[k] = live ? sx * (kk < 16 ? Sr : Si)[S::at(l, QR * n1 + n2)] : 0.f;
       }
       put_chunk(U.a_hi, U.a_lo, tid, c, v);
     }
@@ -388,7 +427,7 @@ __device__ __forceinline__ void tc_lines_umma(float* Sr, float* Si, const TcTabl
     if constexpr (Q2 > 16) umma::ld16(trow + 16u, *reinterpret_cast<float(*)[16]>(&o[16]));
 #pragma unroll
     for (int nn = 0; nn < 2 * QR; ++nn) {
-      const float v = o[nn] * scale;
+      const float v = o[nn] * out_scale;
       if (nn < QR)
         Sr[S::at(l, k1 + 16 * nn)] = v;
       else

@@ -60,7 +60,14 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16_ss(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+// Instruction descriptor of kind::f16 with FP16 A and B (format fields 0).
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D (+)= A B^T, both operands in shared memory, kind::f16 (BF16 or FP16 per
+// the instruction descriptor), accumulate when acc != 0.
+__device__ __forceinline__ void mma_ss(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
@@ -217,7 +224,7 @@ __global__ void __launch_bounds__(128) conv_fwd_tc_kernel(const ConvFwd a, int* 
       const uint32_t sa = base + (uint32_t)(st * S::STAGE), sb = sa + S::A_BYTES;
 #pragma unroll
       for (int kk = 0; kk < kTcBK / 16; ++kk)
-        umma::mma_bf16_ss(tmem, umma::desc_sw128(sa + 32 * kk), umma::desc_sw128(sb + 32 * kk), IDESC,
+        umma::mma_ss(tmem, umma::desc_sw128(sa + 32 * kk), umma::desc_sw128(sb + 32 * kk), IDESC,
                           (ks | kk) != 0);
       umma::commit(bar0 + 8 * st);
     }

@@ -1,4 +1,4 @@
-"""GPU parity of the precision form (tensor-core BF16 hi+lo DFTs) against the
+"""GPU parity of the precision form (tensor-core FP16 hi+lo DFTs) against the
 FP64 oracle: the transforms themselves, single minibatch steps at small and
 full window size, and a run of sweeps, each on both tensor-core paths
 (path 1: register-fragment mma.sync; path 2: tcgen05 with TMEM
@@ -30,8 +30,10 @@ def rel(a, b):
 @pytest.mark.parametrize("m", [64, 128, 256])
 def test_dft2_matches_library_fft(m, path):
     """Forward and conjugate 2-D DFTs of random windows against numpy's FFT in
-    float64: relative error per window within the hi+lo BF16 bound (a few
-    2^-16 per product, four products deep)."""
+    float64: relative error per window within the hi+lo FP16 bound (operands
+    to 2^-22, FP32 accumulation over two stages: measured 4.5e-7 to 7.3e-7
+    for m = 64 to 256), and a window scaled by 2^20, which the block's
+    power-of-two scaling keeps in FP16's range, with the same error."""
     rng = np.random.default_rng(m)
     x = (rng.normal(size=(4, m, m)) + 1j * rng.normal(size=(4, m, m))).astype(np.complex64)
     xd = torch.from_numpy(x).to(DEV)
@@ -42,7 +44,12 @@ def test_dft2_matches_library_fft(m, path):
         refi = O.ifft2(x[c].astype(np.complex128)) * m * m
         e, ei = rel(X[c], ref), rel(Xi[c], refi)
         print(f"path {path} m={m} window {c}: forward {e:.2e} inverse {ei:.2e}")
-        assert e < 4e-5 and ei < 4e-5
+        assert e < 3e-6 and ei < 3e-6
+    big = (x[:1] * np.float32(2.0 ** 20)).astype(np.complex64)
+    Xb = magpie.magpie_dft2_tc(torch.from_numpy(big).to(DEV), path=path).cpu().numpy()
+    eb = rel(Xb[0], O.fft2(big[0].astype(np.complex128)))
+    print(f"path {path} m={m} window scaled by 2^20: forward {eb:.2e}")
+    assert eb < 3e-6
 
 
 def small_problem(levels):
