@@ -21,7 +21,7 @@ its reasons in the design notes of the repository:
     at z_k), is evaluated at the V-cycle's output with e_nn and with e_plain;
     the learned output is kept only when its value is not larger, otherwise
     the plain V-cycle output is used (the plain coarse solve is both the
-    fallback and the judge).
+    fallback and the yardstick the proposal is measured against).
   * Training target: the change of the window's coarse object z_H between
     the input state and a later state of the plain solver (its final state,
     or T further V-cycles of that window alone with refreshed R), in the

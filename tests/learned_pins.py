@@ -211,7 +211,7 @@ def plain_coarse_step_is_magps(L):
 
 def acceptance_rule(L):
     """A wild proposal raises the window surrogate and is rejected (the output
-    is the plain V-cycle); the plain coarse step scaled slightly is judged by
+    is the plain V-cycle); the plain coarse step scaled slightly is assessed by
     the surrogate values written out."""
     zk, Q, Rk, u, _, levels = _window()
     theta = random_theta(L, 14, scale=30.0)
