@@ -32,8 +32,9 @@ def test_dft2_matches_library_fft(m, path):
     """Forward and conjugate 2-D DFTs of random windows against numpy's FFT in
     float64: relative error per window within the hi+lo FP16 bound (operands
     to 2^-22, FP32 accumulation over two stages: measured 4.5e-7 to 7.3e-7
-    for m = 64 to 256), and a window scaled by 2^20, which the block's
-    power-of-two scaling keeps in FP16's range, with the same error."""
+    for m = 64 to 256); windows scaled by 2^20 and 2^-30, which the block's
+    power-of-two scaling brings into FP16's range, with the same error; and
+    an all-zero window, transformed to zeros."""
     rng = np.random.default_rng(m)
     x = (rng.normal(size=(4, m, m)) + 1j * rng.normal(size=(4, m, m))).astype(np.complex64)
     xd = torch.from_numpy(x).to(DEV)
@@ -45,11 +46,14 @@ def test_dft2_matches_library_fft(m, path):
         e, ei = rel(X[c], ref), rel(Xi[c], refi)
         print(f"path {path} m={m} window {c}: forward {e:.2e} inverse {ei:.2e}")
         assert e < 3e-6 and ei < 3e-6
-    big = (x[:1] * np.float32(2.0 ** 20)).astype(np.complex64)
-    Xb = magpie.magpie_dft2_tc(torch.from_numpy(big).to(DEV), path=path).cpu().numpy()
-    eb = rel(Xb[0], O.fft2(big[0].astype(np.complex128)))
-    print(f"path {path} m={m} window scaled by 2^20: forward {eb:.2e}")
-    assert eb < 3e-6
+    for k in (20, -30):  # far above FP16's range, and far below its normal range
+        sc = (x[:1] * np.float32(2.0 ** k)).astype(np.complex64)
+        Xs = magpie.magpie_dft2_tc(torch.from_numpy(sc).to(DEV), path=path).cpu().numpy()
+        es = rel(Xs[0], O.fft2(sc[0].astype(np.complex128)))
+        print(f"path {path} m={m} window scaled by 2^{k}: forward {es:.2e}")
+        assert es < 3e-6
+    zero = torch.zeros((1, m, m), dtype=torch.complex64, device=DEV)
+    assert torch.count_nonzero(magpie.magpie_dft2_tc(zero, path=path)) == 0
 
 
 def small_problem(levels):
