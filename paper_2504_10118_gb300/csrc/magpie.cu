@@ -66,6 +66,13 @@ __global__ void __launch_bounds__(256) apply_kernel(ApplyArgs P) {
   apply_body<kApplyTile, kApplyTile>(P, blockIdx.x, blockIdx.y);
 }
 
+// The precision form's update: the same ordered sum, each window's
+// increment formed from g^0 and its coarse corrections as it is read.
+__global__ void __launch_bounds__(256) apply_tail_kernel(ApplyArgs P) {
+  grid_dep_wait();
+  apply_body<kApplyTile, kApplyTile, 256, true>(P, blockIdx.x, blockIdx.y);
+}
+
 // Several problems in one launch (1-D grid): problem i owns blocks
 // table[i].block0 .. table[i + 1].block0 - 1.
 template <int TW, int TH>
@@ -507,6 +514,9 @@ cudaError_t prepare_kernels(int MS) {
   cudaError_t e = cudaFuncSetAttribute(apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)((sizeof(int2) + sizeof(int)) * kMaxMinibatch));
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(apply_tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((sizeof(int2) + sizeof(int)) * kMaxMinibatch));
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(apply_kernel_batched<16, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)((sizeof(int2) + sizeof(int)) * kMaxMinibatch));
   if (e == cudaSuccess)
@@ -707,7 +717,8 @@ struct magpie_ctx {
   // precision form (tensor-core DFTs)
   int precision = 0;
   float2* pbuf = nullptr;     // [minibatch][m][m] exit wave / spectrum / revised exit wave
-  float2* g1buf = nullptr;    // [minibatch][m/2][m/2] level-1 residual gradient, then increment
+  float2* g1buf = nullptr;    // [minibatch][m/2][m/2] level-1 residual gradient
+  float2* e2buf = nullptr;    // [minibatch][m/4][m/4] level-2 increment (three levels or more)
   TcTables* tabs = nullptr;
   cudaGraphExec_t graph = nullptr;
   // pipelined host sweeps (magpie_sweep_host_async): two amplitude buffers,
@@ -1146,7 +1157,6 @@ PrecArgs precision_args(magpie_ctx* c, const int32_t* idx) {
   a.idx = idx;
   a.n_pos = c->p.n_pos;
   a.MS = c->p.m;
-  a.CL = cluster_of(c->p.m);
   a.T = c->p.m / kTcLines;
   a.buf = c->pbuf;
   a.contrib = c->contrib;
@@ -1155,6 +1165,7 @@ PrecArgs precision_args(magpie_ctx* c, const int32_t* idx) {
   a.err = c->err;
   a.phase = (c->variant & 2) ? c->phase : nullptr;
   a.g1 = (c->p.levels >= 2 && !c->cnn) ? c->g1buf : nullptr;
+  a.e2 = (c->p.levels >= 3 && !c->cnn) ? c->e2buf : nullptr;
   a.pyr = c->pyr;
   a.L = c->p.levels;
   return a;
@@ -1167,15 +1178,19 @@ cudaError_t launch_precision_g0(const PrecArgs& a, int count, const TcTables* ta
   if (path) {
     const cudaError_t e = prepare_dft_umma<MS>();
     if (e != cudaSuccess) return e;
-    exit_dft_kernel<MS, 1><<<grid, 128, kUmmaDftSmem, st>>>(a, tabs, tw);
-    project_dft_kernel<MS, 1><<<grid, 128, kUmmaDftSmem, st>>>(a, tabs, tw);
-    grad_dft_kernel<MS, 1><<<grid, 128, kUmmaDftSmem, st>>>(a, tabs, tw);
-  } else {
-    exit_dft_kernel<MS, 0><<<grid, 128, 0, st>>>(a, tabs, tw);
-    project_dft_kernel<MS, 0><<<grid, 128, 0, st>>>(a, tabs, tw);
-    grad_dft_kernel<MS, 0><<<grid, 128, 0, st>>>(a, tabs, tw);
+    cudaError_t e2 = launch_ex(exit_dft_kernel<MS, 1>, grid, dim3(128), kUmmaDftSmem, st, 1, true, a, tabs, tw);
+    if (e2 == cudaSuccess)
+      e2 = launch_ex(project_dft_kernel<MS, 1>, grid, dim3(128), kUmmaDftSmem, st, 1, true, a, tabs, tw);
+    if (e2 == cudaSuccess)
+      e2 = launch_ex(grad_dft_kernel<MS, 1>, grid, dim3(128), kUmmaDftSmem, st, 1, true, a, tabs, tw);
+    return e2;
   }
-  return cudaGetLastError();
+  // each a programmatic dependent of the kernel before it (its blocks are
+  // set up while that kernel drains)
+  cudaError_t e = launch_ex(exit_dft_kernel<MS, 0>, grid, dim3(128), 0, st, 1, true, a, tabs, tw);
+  if (e == cudaSuccess) e = launch_ex(project_dft_kernel<MS, 0>, grid, dim3(128), 0, st, 1, true, a, tabs, tw);
+  if (e == cudaSuccess) e = launch_ex(grad_dft_kernel<MS, 0>, grid, dim3(128), 0, st, 1, true, a, tabs, tw);
+  return e;
 }
 
 int enqueue_precision_g0(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st) {
@@ -1205,17 +1220,15 @@ int enqueue_step(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st, 
       rc = enqueue_learned_tail(c, idx, count, st);
     } else if (!rc && c->p.levels >= 2) {
       // the V-cycle above g^0 (g^1 already restricted by the gradient
-      // kernel): levels 2 .. L-1 one block per window, the finest level
-      // over row tiles
+      // kernel): levels 2 .. L-1 one block per window; the finest two
+      // levels are formed by the update kernel as it sums the windows
       const PrecArgs v = precision_args(c, idx);
       if (c->p.levels >= 3) {
         int o = 0;
         for (int j = 2; j < c->p.levels; ++j) o += (c->p.m >> j) * (c->p.m >> j);
-        coarse_cycle_kernel<<<count, 1024, sizeof(float2) * (size_t)o, st>>>(v);
-        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(launch_ex(coarse_cycle_kernel, dim3((unsigned)count), dim3(1024), sizeof(float2) * (size_t)o, st, 1,
+                           true, v));
       }
-      fine_cycle_kernel<<<dim3((unsigned)count, (unsigned)v.CL), 256, 0, st>>>(v);
-      CUDA_TRY(cudaGetLastError());
     }
   } else {
     a.grad_only = c->cnn ? 1 : 0;
@@ -1237,6 +1250,16 @@ int enqueue_step(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st, 
     const unsigned blocks = (unsigned)std::min<size_t>((npix + 255) / 256, 152 * 8);
     CUDA_TRY(launch_ex(accum_apply_kernel, dim3(blocks), dim3(256), 0, st, 1, true, c->z, c->acc, npix, idx, count,
                        c->p.n_pos, (const double*)c->part, cluster_of(c->p.m), c->p.m, c->phi_pos, c->gn_pos));
+  } else if (c->precision && !c->cnn && c->p.levels >= 2) {
+    // contrib holds g^0: the update forms w . Delta from g^0, g^1 and e^2
+    ApplyArgs P = apply_args(c->z, c->p.n_rows, c->p.n_cols, c->corner, idx, count, c->p.n_pos, c->contrib,
+                             c->pyr + c->M, c->p.m, c->part, c->phi_pos, c->gn_pos, c->p.m / kTcLines);
+    P.g1 = c->g1buf;
+    P.e2 = c->p.levels >= 3 ? c->e2buf : nullptr;
+    P.iw1 = c->pyr + lvl_off(c->p.m, 1) + c->M / 4;
+    P.u0 = c->pyr;
+    const dim3 tiles(P.tiles_x, (c->p.n_rows + kApplyTile - 1) / kApplyTile);
+    CUDA_TRY(launch_ex(apply_tail_kernel, tiles, dim3(256), (sizeof(int2) + sizeof(int)) * count, st, 1, true, P));
   } else {
     CUDA_TRY(launch_apply(c->z, c->p.n_rows, c->p.n_cols, c->corner, idx, count, c->p.n_pos, c->contrib,
                           c->pyr + c->M, c->p.m, c->part, c->phi_pos, c->gn_pos, st,
@@ -1713,7 +1736,7 @@ void magpie_destroy(magpie_ctx* c) {
   void* bufs[] = {c->Q, c->tw, c->amp, c->stage, c->pos, c->pyr, c->pyr_q, c->pyr_u, c->contrib,
                   c->phi_pos, c->gn_pos, c->part, c->corner, c->mx, c->pnum, c->pa2, c->pmax, c->iota, c->order, c->sums, c->err,
                   c->wz, c->lx, c->lscale, c->lacc, c->lmargin, c->lstats, c->pbuf, c->tabs, c->phase, c->g1buf,
-                  c->acc};
+                  c->e2buf, c->acc};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete c;
@@ -2446,6 +2469,7 @@ int magpie_set_precision(magpie_ctx* c, int32_t mode) {
     if (!c->pbuf) {
       cudaError_t e = cudaMalloc((void**)&c->pbuf, sizeof(float2) * (size_t)c->M * c->p.minibatch);
       if (e == cudaSuccess) e = cudaMalloc((void**)&c->g1buf, sizeof(float2) * (size_t)(c->M / 4) * c->p.minibatch);
+      if (e == cudaSuccess) e = cudaMalloc((void**)&c->e2buf, sizeof(float2) * (size_t)(c->M / 16) * c->p.minibatch);
       if (e == cudaSuccess) e = cudaMalloc((void**)&c->tabs, sizeof(TcTables));
       if (e != cudaSuccess)
         return fail(e == cudaErrorMemoryAllocation ? MAGPIE_ENOMEM : MAGPIE_ECUDA,

@@ -528,7 +528,7 @@ struct PrecArgs {
   const float* amp;    // sqrt(d) [n_pos][MS][MS]
   const int32_t* pos;  // [n_pos][2]
   const int32_t* idx;  // [count]
-  int n_pos, MS, CL;   // CL: row tiles per window of the finest V-cycle level
+  int n_pos, MS;
   int T;               // partial-sum slots per window: one per block of kTcLines lines
   float2* buf;         // [count][MS][MS] exit wave -> spectrum -> revised exit wave
   float2* contrib;     // [count][MS][MS] g^0 = conj(Q)(R - Q z)
@@ -536,7 +536,8 @@ struct PrecArgs {
   int2* corner;        // [count] window corners for the update kernel
   int* err;            // bit 0: window index out of range
   float2* phase;       // phase rule: [n_pos][MS][MS] unit phases of the last visit, else null
-  float2* g1;          // levels >= 2: [count][MS/2][MS/2] g^1 = W_u^0 . I(g^0) (then e^1), else null
+  float2* g1;          // levels >= 2: [count][MS/2][MS/2] g^1 = W_u^0 . I(g^0), else null
+  float2* e2;          // levels >= 3: [count][MS/4][MS/4] e^2 from the coarse levels
   const float* pyr;    // level factors (window-kernel layout)
   int L;               // levels
 };
@@ -576,6 +577,7 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) exit_dft_kernel(con
   using S = TcSm<MS>;
   __shared__ float Sr[S::NL * S::LD];
   __shared__ float Si[S::NL * S::LD];
+  grid_dep_wait();  // launched as a programmatic dependent of the kernel before
   TcPath<PATH> T;
   T.begin();
   const TcBlock B = tc_block<MS>(A);
@@ -607,6 +609,7 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) project_dft_kernel(
   __shared__ float Sr[S::NL * S::LD];
   __shared__ float Si[S::NL * S::LD];
   __shared__ double red[4];
+  grid_dep_wait();  // launched as a programmatic dependent of the kernel before
   TcPath<PATH> T;
   T.begin();
   const TcBlock B = tc_block<MS>(A);
@@ -667,6 +670,7 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) grad_dft_kernel(con
   __shared__ float Sr[NL * S::LD];
   __shared__ float Si[NL * S::LD];
   __shared__ double red[4];
+  grid_dep_wait();  // launched as a programmatic dependent of the kernel before
   TcPath<PATH> T;
   T.begin();
   const TcBlock B = tc_block<MS>(A);
@@ -735,12 +739,16 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) grad_dft_kernel(con
 
 // Levels 2 .. L-1 of the V-cycle of one window (levels >= 3), one block per
 // window: restrictions from g^1 (global) into shared memory, the coarsest
-// step, the way up, and e^1 = g^1 / w^1 + (u^1 / w^1) I_H^h e^2 written over
-// g^1.  Dynamic shared memory: levels 2 .. L-1 as float2.
+// step, the way up to level 2, and e^2 written to global memory.  The finest
+// two levels (e^1 = g^1 / w^1 + (u^1 / w^1) I_H^h e^2, then w . Delta =
+// g^0 + u^0 I_H^h e^1) are formed pixel by pixel by the update kernel.
+// Dynamic shared memory: levels 2 .. L-1 as float2.  Launched as a
+// programmatic dependent of the gradient kernel.
 __global__ void __launch_bounds__(1024) coarse_cycle_kernel(const PrecArgs A) {
   extern __shared__ __align__(16) unsigned char csm[];
   float2* E = reinterpret_cast<float2*>(csm);
   const int w = blockIdx.x, tid = threadIdx.x, nt = blockDim.x, MS = A.MS, L = A.L;
+  grid_dep_wait();
   if ((unsigned)A.idx[w] >= (unsigned)A.n_pos) return;
   auto off = [&](int l) {  // level l >= 2
     int o = 0;
@@ -771,11 +779,11 @@ __global__ void __launch_bounds__(1024) coarse_cycle_kernel(const PrecArgs A) {
     }
     __syncthreads();
   }
-  for (int l = L - 2; l >= 1; --l) {
+  for (int l = L - 2; l >= 2; --l) {
     const int s = MS >> l, sc = MS >> (l + 1);
     const float* iw = A.pyr + lvl_off(MS, l) + s * s;
     const float* rr = iw + s * s;
-    float2* a = l == 1 ? g1 : E + off(l);
+    float2* a = E + off(l);
     const float2* pe = E + off(l + 1);
     for (int i = tid; i < s * s; i += nt) {
       const int r = i / s, c = i - r * s;
@@ -786,26 +794,10 @@ __global__ void __launch_bounds__(1024) coarse_cycle_kernel(const PrecArgs A) {
     }
     __syncthreads();
   }
-}
-
-// w^0 Delta = g^0 + u^0 I_H^h e^1 over a row tile of each window; with two
-// levels e^1 = g^1 / w^1 (the coarsest step) is formed here.
-__global__ void __launch_bounds__(256) fine_cycle_kernel(const PrecArgs A) {
-  const int w = blockIdx.x, q = blockIdx.y, MS = A.MS, rows = MS / A.CL, h = MS / 2;
-  if ((unsigned)A.idx[w] >= (unsigned)A.n_pos) return;
-  const float* u0 = A.pyr;
-  const float* iw1 = A.pyr + lvl_off(MS, 1) + h * h;
-  const float2* e1 = A.g1 + (size_t)w * h * h;
-  float2* out = A.contrib + (size_t)w * MS * MS;
-  for (int i = threadIdx.x; i < rows * MS; i += blockDim.x) {
-    const int r = q * rows + i / MS, c = i % MS, o = r * MS + c, pi = (r >> 1) * h + (c >> 1);
-    float2 e = e1[pi];
-    if (A.L == 2) {
-      const float f = __ldg(&iw1[pi]);
-      e = make_float2(e.x * f, e.y * f);
-    }
-    const float u = __ldg(&u0[o]);
-    const float2 g = out[o];
-    out[o] = make_float2(g.x + u * e.x, g.y + u * e.y);
+  {
+    const int s = MS >> 2;
+    float2* e2 = A.e2 + (size_t)w * s * s;
+    for (int i = tid; i < s * s; i += nt) e2[i] = E[off(2) + i];
   }
 }
+

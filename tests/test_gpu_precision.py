@@ -80,7 +80,7 @@ def make_ctx(n, m, Q, pos, d, z0, levels, minibatch, alpha=0.1, path=1):
 
 
 @pytest.mark.parametrize("path", PATHS)
-@pytest.mark.parametrize("levels", [1, 3])
+@pytest.mark.parametrize("levels", [1, 2, 3, 4])
 def test_precision_step_matches_oracle(levels, path):
     n, m, Q, pos, d, z0 = small_problem(levels)
     ctx, zt = make_ctx(n, m, Q, pos, d, z0, levels, 8, path=path)
