@@ -458,6 +458,26 @@ int magpie_learned_window_values(magpie_ctx* ctx, int32_t count, int32_t* accept
  */
 int magpie_set_precision(magpie_ctx* ctx, int32_t mode);
 
+/*
+ * The transform kernels of a precision-form step hand windows to one another
+ * one by one: each kernel lets the next one launch once all of its own
+ * blocks run, and a block of the next kernel waits only for the tiles of its
+ * own window (a count per window, released by the producer and polled with
+ * acquire loads), so that the last wave of one kernel overlaps the first
+ * windows of the next.  Every such wait is bounded (0.2 s); one that runs out
+ * skips its tile and makes the next objective, stop metric or window-value
+ * call return MAGPIE_ETIMEOUT.
+ * Self-test of those bounds (no counterpart in the paper): runs the
+ * transform and coarse kernels of one step over windows 0 .. min(minibatch,
+ * n_pos) - 1 with every wait asking for one tile more than its window has,
+ * under a limit of `seconds` (in [1e-6, 10]), and no update.  Every wait
+ * runs out, the kernels end, and the call returns MAGPIE_ETIMEOUT; the
+ * object is unchanged (the per-window scratch is overwritten) and the
+ * context stays usable.  MAGPIE_EINVAL when the context is not in the
+ * precision form (mode 1 or 2).  Synchronous.
+ */
+int magpie_precision_check_waits(magpie_ctx* ctx, double seconds);
+
 /* out[c] = the 2-D DFT of in[c] (unnormalised; inverse = 1: the conjugate
    transform, without 1/m^2) for `count` m x m complex windows (DEVICE), by
    the precision form's tensor-core path: magpie_dft2_tc with mma.sync,

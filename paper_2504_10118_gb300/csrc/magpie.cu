@@ -57,12 +57,21 @@ constexpr int kVersion = 10300;  // 1.3.0
 #include "umma.cuh"
 #include "precision.cuh"
 
+// The precision form's window hand-off counts are final once the update
+// kernel that ends the step may run: block (0, 0) zeroes them for the next
+// step (whose exit kernel waits for this grid to complete).
+__device__ __forceinline__ void clear_handoff(const ApplyArgs& P) {
+  if (P.hand && blockIdx.x == 0 && blockIdx.y == 0)
+    for (int i = threadIdx.x; i < P.nhand; i += blockDim.x) P.hand[i] = 0;
+}
+
 // One problem: a 2-D grid of tiles.
 // Launched as a programmatic dependent of the window kernel (its blocks, let
 // in early, would slow the next window kernel: 0.328 against 0.319 ms per
 // sweep, so it does not trigger its dependents).
 __global__ void __launch_bounds__(256) apply_kernel(ApplyArgs P) {
   grid_dep_wait();
+  clear_handoff(P);
   apply_body<kApplyTile, kApplyTile>(P, blockIdx.x, blockIdx.y);
 }
 
@@ -70,6 +79,7 @@ __global__ void __launch_bounds__(256) apply_kernel(ApplyArgs P) {
 // increment formed from g^0 and its coarse corrections as it is read.
 __global__ void __launch_bounds__(256) apply_tail_kernel(ApplyArgs P) {
   grid_dep_wait();
+  clear_handoff(P);
   apply_body<kApplyTile, kApplyTile, 256, true>(P, blockIdx.x, blockIdx.y);
 }
 
@@ -719,6 +729,7 @@ struct magpie_ctx {
   float2* pbuf = nullptr;     // [minibatch][m][m] exit wave / spectrum / revised exit wave
   float2* g1buf = nullptr;    // [minibatch][m/2][m/2] level-1 residual gradient
   float2* e2buf = nullptr;    // [minibatch][m/4][m/4] level-2 increment (three levels or more)
+  int* hand = nullptr;        // [3][minibatch] window hand-off counts of the transform kernels
   TcTables* tabs = nullptr;
   cudaGraphExec_t graph = nullptr;
   // pipelined host sweeps (magpie_sweep_host_async): two amplitude buffers,
@@ -1147,7 +1158,7 @@ cudaError_t launch_dft2_tc_m(int MS, float2* buf, int count, const TcTables* tab
 
 // Exit waves, tensor-core DFTs, projection, inverse DFTs and g^0 into the
 // increments (with the per-tile partial sums and the windows' corners).
-PrecArgs precision_args(magpie_ctx* c, const int32_t* idx) {
+PrecArgs precision_args(magpie_ctx* c, const int32_t* idx, int count) {
   PrecArgs a{};
   a.z = c->z;
   a.n_cols = c->p.n_cols;
@@ -1166,6 +1177,10 @@ PrecArgs precision_args(magpie_ctx* c, const int32_t* idx) {
   a.phase = (c->variant & 2) ? c->phase : nullptr;
   a.g1 = (c->p.levels >= 2 && !c->cnn) ? c->g1buf : nullptr;
   a.e2 = (c->p.levels >= 3 && !c->cnn) ? c->e2buf : nullptr;
+  a.count = count;
+  a.hand = c->hand;
+  a.wait_bias = 0;
+  a.wait_ns = kHandoffNs;
   a.pyr = c->pyr;
   a.L = c->p.levels;
   return a;
@@ -1193,8 +1208,7 @@ cudaError_t launch_precision_g0(const PrecArgs& a, int count, const TcTables* ta
   return e;
 }
 
-int enqueue_precision_g0(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st) {
-  const PrecArgs a = precision_args(c, idx);
+int enqueue_precision_g0(magpie_ctx* c, const PrecArgs& a, int count, cudaStream_t st) {
   switch (a.MS) {
     case 64: CUDA_TRY(launch_precision_g0<64>(a, count, c->tabs, c->tw, st, c->precision == 2)); break;
     case 128: CUDA_TRY(launch_precision_g0<128>(a, count, c->tabs, c->tw, st, c->precision == 2)); break;
@@ -1202,6 +1216,9 @@ int enqueue_precision_g0(magpie_ctx* c, const int32_t* idx, int count, cudaStrea
     default: return fail(MAGPIE_EUNSUPPORTED, "the precision form needs m = 64, 128 or 256");
   }
   return MAGPIE_OK;
+}
+int enqueue_precision_g0(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st) {
+  return enqueue_precision_g0(c, precision_args(c, idx, count), count, st);
 }
 
 // ev (optional): four events recorded before/after the window kernel and
@@ -1222,7 +1239,7 @@ int enqueue_step(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st, 
       // the V-cycle above g^0 (g^1 already restricted by the gradient
       // kernel): levels 2 .. L-1 one block per window; the finest two
       // levels are formed by the update kernel as it sums the windows
-      const PrecArgs v = precision_args(c, idx);
+      const PrecArgs v = precision_args(c, idx, count);
       if (c->p.levels >= 3) {
         int o = 0;
         for (int j = 2; j < c->p.levels; ++j) o += (c->p.m >> j) * (c->p.m >> j);
@@ -1258,12 +1275,20 @@ int enqueue_step(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st, 
     P.e2 = c->p.levels >= 3 ? c->e2buf : nullptr;
     P.iw1 = c->pyr + lvl_off(c->p.m, 1) + c->M / 4;
     P.u0 = c->pyr;
+    P.hand = c->hand;
+    P.nhand = 3 * count;
     const dim3 tiles(P.tiles_x, (c->p.n_rows + kApplyTile - 1) / kApplyTile);
     CUDA_TRY(launch_ex(apply_tail_kernel, tiles, dim3(256), (sizeof(int2) + sizeof(int)) * count, st, 1, true, P));
   } else {
-    CUDA_TRY(launch_apply(c->z, c->p.n_rows, c->p.n_cols, c->corner, idx, count, c->p.n_pos, c->contrib,
-                          c->pyr + c->M, c->p.m, c->part, c->phi_pos, c->gn_pos, st,
-                          c->precision ? c->p.m / kTcLines : 0));
+    ApplyArgs P = apply_args(c->z, c->p.n_rows, c->p.n_cols, c->corner, idx, count, c->p.n_pos, c->contrib,
+                             c->pyr + c->M, c->p.m, c->part, c->phi_pos, c->gn_pos,
+                             c->precision ? c->p.m / kTcLines : 0);
+    if (c->precision) {  // the transform kernels' hand-off counts
+      P.hand = c->hand;
+      P.nhand = 3 * count;
+    }
+    const dim3 tiles(P.tiles_x, (c->p.n_rows + kApplyTile - 1) / kApplyTile);
+    CUDA_TRY(launch_ex(apply_kernel, tiles, dim3(256), (sizeof(int2) + sizeof(int)) * count, st, 1, true, P));
   }
   if (c->p.update_probe) {
     probe_apply_kernel<<<(c->M + 255) / 256, 256, 0, st>>>(c->Q, c->M, idx, count, c->p.n_pos, c->pnum, c->pa2,
@@ -1736,7 +1761,7 @@ void magpie_destroy(magpie_ctx* c) {
   void* bufs[] = {c->Q, c->tw, c->amp, c->stage, c->pos, c->pyr, c->pyr_q, c->pyr_u, c->contrib,
                   c->phi_pos, c->gn_pos, c->part, c->corner, c->mx, c->pnum, c->pa2, c->pmax, c->iota, c->order, c->sums, c->err,
                   c->wz, c->lx, c->lscale, c->lacc, c->lmargin, c->lstats, c->pbuf, c->tabs, c->phase, c->g1buf,
-                  c->e2buf, c->acc};
+                  c->e2buf, c->hand, c->acc};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete c;
@@ -2470,6 +2495,8 @@ int magpie_set_precision(magpie_ctx* c, int32_t mode) {
       cudaError_t e = cudaMalloc((void**)&c->pbuf, sizeof(float2) * (size_t)c->M * c->p.minibatch);
       if (e == cudaSuccess) e = cudaMalloc((void**)&c->g1buf, sizeof(float2) * (size_t)(c->M / 4) * c->p.minibatch);
       if (e == cudaSuccess) e = cudaMalloc((void**)&c->e2buf, sizeof(float2) * (size_t)(c->M / 16) * c->p.minibatch);
+      if (e == cudaSuccess) e = cudaMalloc((void**)&c->hand, sizeof(int) * 3 * (size_t)c->p.minibatch);
+      if (e == cudaSuccess) e = cudaMemset(c->hand, 0, sizeof(int) * 3 * (size_t)c->p.minibatch);
       if (e == cudaSuccess) e = cudaMalloc((void**)&c->tabs, sizeof(TcTables));
       if (e != cudaSuccess)
         return fail(e == cudaErrorMemoryAllocation ? MAGPIE_ENOMEM : MAGPIE_ECUDA,
@@ -2482,6 +2509,27 @@ int magpie_set_precision(magpie_ctx* c, int32_t mode) {
   invalidate_graphs(c);
   c->precision = mode;
   return MAGPIE_OK;
+}
+
+int magpie_precision_check_waits(magpie_ctx* c, double seconds) {
+  if (!c) return fail(MAGPIE_EINVAL, "NULL context");
+  if (!c->precision) return fail(MAGPIE_EINVAL, "the context is not in the precision form");
+  if (!(seconds >= 1e-6 && seconds <= 10.0)) return fail(MAGPIE_EINVAL, "seconds must lie in [1e-6, 10]");
+  const int count = std::min(c->p.minibatch, c->p.n_pos);
+  PrecArgs a = precision_args(c, c->iota, count);
+  a.wait_bias = 1;  // one tile more than any window has: every hand-off wait runs out
+  a.wait_ns = (unsigned long long)(seconds * 1e9);
+  const int rc = enqueue_precision_g0(c, a, count, c->stream);
+  if (rc) return rc;
+  if (c->p.levels >= 3 && !c->cnn) {
+    int o = 0;
+    for (int j = 2; j < c->p.levels; ++j) o += (c->p.m >> j) * (c->p.m >> j);
+    CUDA_TRY(launch_ex(coarse_cycle_kernel, dim3((unsigned)count), dim3(1024), sizeof(float2) * (size_t)o, c->stream,
+                       1, true, a));
+  }
+  // no update kernel runs: clear the counts here
+  CUDA_TRY(cudaMemsetAsync(c->hand, 0, sizeof(int) * 3 * (size_t)count, c->stream));
+  return read_err(c);
 }
 
 static int dft2_tc(const void* in, void* out, int32_t m, int32_t count, int32_t inverse, void* stream, int path);

@@ -529,6 +529,7 @@ struct PrecArgs {
   const int32_t* pos;  // [n_pos][2]
   const int32_t* idx;  // [count]
   int n_pos, MS;
+  int count;           // windows of the step
   int T;               // partial-sum slots per window: one per block of kTcLines lines
   float2* buf;         // [count][MS][MS] exit wave -> spectrum -> revised exit wave
   float2* contrib;     // [count][MS][MS] g^0 = conj(Q)(R - Q z)
@@ -538,6 +539,10 @@ struct PrecArgs {
   float2* phase;       // phase rule: [n_pos][MS][MS] unit phases of the last visit, else null
   float2* g1;          // levels >= 2: [count][MS/2][MS/2] g^1 = W_u^0 . I(g^0), else null
   float2* e2;          // levels >= 3: [count][MS/4][MS/4] e^2 from the coarse levels
+  int* hand;           // [3][count] tiles of each window finished by the exit, project and gradient
+                       // kernels (zeroed by the update kernel that ends the step)
+  int wait_bias;       // added to every hand-off target: 1 makes every wait run out (a self-test)
+  unsigned long long wait_ns;  // bound of each hand-off wait
   const float* pyr;    // level factors (window-kernel layout)
   int L;               // levels
 };
@@ -553,6 +558,53 @@ struct PrecArgs {
 //                               increments (+ the tile's sum of |g^0|^2), and
 //                               for two levels or more g^1 = W_u^0 . I(g^0)
 // The window buffer holds psi's column transforms, then R's row transforms.
+
+// Window hand-off between the step's kernels.  Each transform kernel lets
+// the next one launch as soon as all of its own blocks are running
+// (griddepcontrol.launch_dependents at block start), and the next kernel's
+// blocks wait, window by window, for the count of that window's finished
+// tiles instead of for the whole previous grid: the last partial wave of
+// one kernel then overlaps the first windows of the next.  The producer
+// block counts its tile after its last global store (block barrier, fence,
+// atomic add: a release at GPU scope); the consumer's thread 0 polls with
+// acquire loads, bounded by kHandoffNs of %globaltimer time (on expiry it
+// sets bit 4 of the error word, MAGPIE_ETIMEOUT, and the block skips its
+// tile but still counts it).  Consumers read the handed-off buffers through
+// L2 (ld.global.cg).
+constexpr unsigned long long kHandoffNs = 200000000ull;  // 0.2 s, the default bound
+__device__ __forceinline__ void handoff_signal(int* cnt) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(cnt, 1);
+  }
+}
+// Returns false (in every thread of the block) when the wait ran out.
+__device__ __forceinline__ bool handoff_wait(const PrecArgs& A, const int* cnt, int tiles) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    const int target = tiles + A.wait_bias;
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    int good = 1;
+    for (int i = 0;; ++i) {
+      int v;
+      asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(cnt) : "memory");
+      if (v >= target) break;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (t - t0 > A.wait_ns || i >= (1 << 26)) {
+        atomicOr(A.err, 16);
+        good = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
 
 // Window index of block b, its first line, and whether the index is valid.
 struct TcBlock {
@@ -577,7 +629,8 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) exit_dft_kernel(con
   using S = TcSm<MS>;
   __shared__ float Sr[S::NL * S::LD];
   __shared__ float Si[S::NL * S::LD];
-  grid_dep_wait();  // launched as a programmatic dependent of the kernel before
+  grid_dep_wait();  // launched as a programmatic dependent of the step's last kernel before
+  grid_dep_launch();
   TcPath<PATH> T;
   T.begin();
   const TcBlock B = tc_block<MS>(A);
@@ -599,6 +652,7 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) exit_dft_kernel(con
   T.template lines<MS, 0>(Sr, Si, tabs, tw, 1.f);
   float2* base = A.buf + (size_t)B.w * MS * MS;
   tc_store<MS, 0>(Sr, Si, [&](int l, int p, float2 v) { base[(size_t)p * MS + B.l0 + l] = v; });
+  handoff_signal(&A.hand[B.w]);
   T.end(A.err);
 }
 
@@ -609,7 +663,7 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) project_dft_kernel(
   __shared__ float Sr[S::NL * S::LD];
   __shared__ float Si[S::NL * S::LD];
   __shared__ double red[4];
-  grid_dep_wait();  // launched as a programmatic dependent of the kernel before
+  grid_dep_launch();  // the exit kernel's windows are handed off one by one
   TcPath<PATH> T;
   T.begin();
   const TcBlock B = tc_block<MS>(A);
@@ -620,7 +674,12 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) project_dft_kernel(
     for (int i = threadIdx.x; i < S::NL * MS * 4 / 128; i += 128)
       asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(ab + 128 * i)));
   }
-  tc_load<MS, 1>(Sr, Si, [&](int l, int p) { return base[(size_t)(B.l0 + l) * MS + p]; });
+  if (!handoff_wait(A, &A.hand[B.w], MS / kTcLines)) {  // ran out: skip the tile
+    handoff_signal(&A.hand[A.count + B.w]);
+    T.end(A.err);
+    return;
+  }
+  tc_load<MS, 1>(Sr, Si, [&](int l, int p) { return __ldcg(&base[(size_t)(B.l0 + l) * MS + p]); });
   T.template lines<MS, 0>(Sr, Si, tabs, tw, 1.f);
   // Psi <- sqrt(d) Psi / |Psi| / m^2 (sqrt(d) / m^2 where Psi = 0, or the
   // previous visit's phase under the phase rule)
@@ -659,6 +718,7 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) project_dft_kernel(
   if (threadIdx.x == 0) A.part[((size_t)B.w * A.T + B.tile) * 2] = B.ok ? s : 0.0;
   T.template lines<MS, 1>(Sr, Si, tabs, tw, 1.f);
   tc_store<MS, 1>(Sr, Si, [&](int l, int p, float2 v) { base[(size_t)(B.l0 + l) * MS + p] = v; });
+  handoff_signal(&A.hand[A.count + B.w]);
   T.end(A.err);
 }
 
@@ -670,12 +730,17 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) grad_dft_kernel(con
   __shared__ float Sr[NL * S::LD];
   __shared__ float Si[NL * S::LD];
   __shared__ double red[4];
-  grid_dep_wait();  // launched as a programmatic dependent of the kernel before
+  grid_dep_launch();  // the project kernel's windows are handed off one by one
   TcPath<PATH> T;
   T.begin();
   const TcBlock B = tc_block<MS>(A);
   const float2* base = A.buf + (size_t)B.w * MS * MS;
-  tc_load<MS, 0>(Sr, Si, [&](int l, int p) { return base[(size_t)p * MS + B.l0 + l]; });
+  if (!handoff_wait(A, &A.hand[A.count + B.w], MS / kTcLines)) {  // ran out: skip the tile
+    handoff_signal(&A.hand[2 * A.count + B.w]);
+    T.end(A.err);
+    return;
+  }
+  tc_load<MS, 0>(Sr, Si, [&](int l, int p) { return __ldcg(&base[(size_t)p * MS + B.l0 + l]); });
   T.template lines<MS, 1>(Sr, Si, tabs, tw, 1.f);
   const float2* zk = A.z + (B.ok ? (size_t)A.pos[2 * B.k] * A.n_cols + A.pos[2 * B.k + 1] : 0);
   float2* out = A.contrib + (size_t)B.w * MS * MS;
@@ -734,6 +799,7 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) grad_dft_kernel(con
       A.g1[(size_t)B.w * h * h + br * h + bc] = make_float2(f * sx, f * sy);
     }
   }
+  handoff_signal(&A.hand[2 * A.count + B.w]);
   T.end(A.err);
 }
 
@@ -748,8 +814,9 @@ __global__ void __launch_bounds__(1024) coarse_cycle_kernel(const PrecArgs A) {
   extern __shared__ __align__(16) unsigned char csm[];
   float2* E = reinterpret_cast<float2*>(csm);
   const int w = blockIdx.x, tid = threadIdx.x, nt = blockDim.x, MS = A.MS, L = A.L;
-  grid_dep_wait();
+  grid_dep_launch();  // the update kernel after it waits for the whole grid
   if ((unsigned)A.idx[w] >= (unsigned)A.n_pos) return;
+  if (!handoff_wait(A, &A.hand[2 * A.count + w], MS / kTcLines)) return;  // ran out: skip the window
   auto off = [&](int l) {  // level l >= 2
     int o = 0;
     for (int j = 2; j < l; ++j) o += (MS >> j) * (MS >> j);
@@ -762,8 +829,18 @@ __global__ void __launch_bounds__(1024) coarse_cycle_kernel(const PrecArgs A) {
     const float* wu = A.pyr + lvl_off(MS, l);
     for (int i = tid; i < s * s; i += nt) {
       const int r = i / s, c = i - r * s;
-      const float2 a = src[(2 * r) * sf + 2 * c], b = src[(2 * r) * sf + 2 * c + 1];
-      const float2 cc = src[(2 * r + 1) * sf + 2 * c], d = src[(2 * r + 1) * sf + 2 * c + 1];
+      float2 a, b, cc, d;
+      if (l == 2) {  // handed off by the gradient kernel: read through L2
+        a = __ldcg(&src[(2 * r) * sf + 2 * c]);
+        b = __ldcg(&src[(2 * r) * sf + 2 * c + 1]);
+        cc = __ldcg(&src[(2 * r + 1) * sf + 2 * c]);
+        d = __ldcg(&src[(2 * r + 1) * sf + 2 * c + 1]);
+      } else {
+        a = src[(2 * r) * sf + 2 * c];
+        b = src[(2 * r) * sf + 2 * c + 1];
+        cc = src[(2 * r + 1) * sf + 2 * c];
+        d = src[(2 * r + 1) * sf + 2 * c + 1];
+      }
       const float f = 0.25f * __ldg(&wu[i]);
       E[off(l) + i] = make_float2(f * (a.x + b.x + cc.x + d.x), f * (a.y + b.y + cc.y + d.y));
     }

@@ -43,6 +43,8 @@ struct ApplyArgs {
   const float2* e2;        // [count][MS/4][MS/4] e^2, or null for two levels
   const float* iw1;        // [MS/2][MS/2] 1 / w^1, followed by u^1 / w^1
   const float* u0;         // [MS][MS] u^0
+  int* hand;               // precision form: the step's window hand-off counts, zeroed by
+  int nhand;               // block (0, 0) once the grid may run (null otherwise)
 };
 
 template <int TW, int TH, int NT = 256, bool TAIL = false>

@@ -105,6 +105,7 @@ def lib() -> ctypes.CDLL:
             "magpie_objective": (ctypes.c_int, [vp, dp]),
             "magpie_profile_sweep": (ctypes.c_int, [vp, vp, dp, dp, ctypes.POINTER(i32)]),
             "magpie_stop_metric": (ctypes.c_int, [vp, dp]),
+            "magpie_precision_check_waits": (ctypes.c_int, [vp, ctypes.c_double]),
             "magpie_set_probe": (ctypes.c_int, [vp, vp]),
             "magpie_get_probe": (ctypes.c_int, [vp, vp]),
             "magpie_window_values": (ctypes.c_int, [vp, vp, vp]),
@@ -431,6 +432,12 @@ def magpie_set_variant(ctx: Context, flags: int) -> None:
 def magpie_set_precision(ctx: Context, mode: int) -> None:
     """0: FP32 FFTs; 1: tensor-core DFTs with mma.sync; 2: with tcgen05."""
     _check(lib().magpie_set_precision(ctx.handle, int(mode)))
+
+
+def magpie_precision_check_waits(ctx: Context, seconds: float) -> int:
+    """Return code of the hand-off wait self-test (MAGPIE_ETIMEOUT when every
+    bounded wait ran out, as it should)."""
+    return int(lib().magpie_precision_check_waits(ctx.handle, float(seconds)))
 
 
 def magpie_dft2_tc(x: torch.Tensor, inverse: bool = False, path: int = 1) -> torch.Tensor:

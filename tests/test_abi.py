@@ -154,4 +154,5 @@ def test_learned_and_precision_entry_points_without_a_gpu(L):
     assert L.magpie_dft2_tcgen05(x, x, 32, 1, 0, None) == magpie.EUNSUPPORTED
     assert L.magpie_dft2_tcgen05(x, x, 64, 1, 2, None) == magpie.EINVAL        # inverse not 0/1
     assert L.magpie_set_precision(None, 2) == magpie.EINVAL
+    assert L.magpie_precision_check_waits(None, ctypes.c_double(1e-3)) == magpie.EINVAL
     L.magpie_cnn_destroy(None)

@@ -204,3 +204,56 @@ def test_precision_sweeps_track_oracle(path):
     ratio = transform_error_ratio(O.extract(zo, (0, 0), n), Q, pos[:8], path)
     print(f"path {path} 20 sweeps: NRMSE vs oracle tensor-core {e_tc:.2e}, FP32 FFT {e_32:.2e}; transform error ratio {ratio:.1f}")
     assert e_tc < max(1e-4, 2 * ratio * e_32)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_precision_sweeps_bitwise_reproducible(path):
+    """Each transform kernel of a step hands its windows to the next one
+    window by window (counted tiles, bounded waits) so that their waves
+    overlap; the arithmetic does not depend on that timing.  Two contexts
+    on the precision workload's sizes (n = 1024, m = 256, 4 levels, five
+    64-window minibatches, 1024 blocks per transform launch) end two sweeps
+    bit for bit equal, and no wait runs out."""
+    w = synth.WORKLOADS["precision"]
+    z_true, Q, pos = synth.make_problem(w)
+    pos = np.ascontiguousarray(pos[:5 * w.minibatch])
+    Qt = torch.from_numpy(Q.astype(np.complex64)).to(DEV)
+    pt = torch.from_numpy(pos.astype(np.int32)).to(DEV)
+    d = magpie.magpie_forward_intensities(torch.from_numpy(z_true.astype(np.complex64)).to(DEV), Qt, pt, w.m)
+    outs = []
+    for _ in range(2):
+        zt = torch.ones((w.n, w.n), dtype=torch.complex64, device=DEV)
+        p = magpie.magpie_params_of(w.n, w.n, w.m, len(pos), w.levels, w.minibatch, w.alpha)
+        ctx = magpie.magpie_create(p, zt, Qt, pt, d)
+        magpie.magpie_set_precision(ctx, path)
+        for s in range(2):
+            magpie.magpie_sweep(ctx, torch.from_numpy(synth.make_order(len(pos), s)).to(DEV))
+        magpie.magpie_stop_metric(ctx)  # raises on a wait that ran out
+        torch.cuda.synchronize()
+        outs.append(zt.clone())
+        ctx.close()
+    assert torch.equal(outs[0], outs[1])
+    assert float((outs[0] - 1).abs().max()) > 0  # the sweeps moved the object
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_handoff_waits_run_out_and_report(path):
+    """The self-test of the hand-off waits: every wait asks for one tile more
+    than its window has, runs out under a 1 ms limit and skips its tile; the
+    call returns MAGPIE_ETIMEOUT, the object is untouched, and the context's
+    next step still matches the oracle (the counts were cleared)."""
+    n, m, Q, pos, d, z0 = small_problem(3)
+    ctx, zt = make_ctx(n, m, Q, pos, d, z0, 3, 8, path=path)
+    before = zt.clone()
+    assert magpie.magpie_precision_check_waits(ctx, 1e-3) == magpie.ETIMEOUT
+    torch.cuda.synchronize()
+    assert torch.equal(zt, before)
+    batch = np.array([3, 7, 11, 12, 13, 17, 21, 24], dtype=np.int32)
+    magpie.magpie_step(ctx, torch.from_numpy(batch).to(DEV))
+    zo = O.minibatch_step(z0, Q, pos, d, O.rpie_regulariser(Q, 0.1), 3, list(batch))
+    assert rel(zt.cpu().numpy(), zo) < 1e-5
+    magpie.magpie_stop_metric(ctx)  # no wait ran out in the real step
+    ctx.close()
+    ctx32, _ = fp32_ctx(n, m, Q, pos, d, z0, 3, 8)
+    assert magpie.magpie_precision_check_waits(ctx32, 1e-3) == magpie.EINVAL
+    ctx32.close()
