@@ -727,8 +727,7 @@ struct magpie_ctx {
   // precision form (tensor-core DFTs)
   int precision = 0;
   float2* pbuf = nullptr;     // [minibatch][m][m] exit wave / spectrum / revised exit wave
-  float2* g1buf = nullptr;    // [minibatch][m/2][m/2] level-1 residual gradient
-  float2* e2buf = nullptr;    // [minibatch][m/4][m/4] level-2 increment (three levels or more)
+  float2* g1buf = nullptr;    // [minibatch][m/2][m/2] level-1 residual gradient, then increment
   int* hand = nullptr;        // [3][minibatch] window hand-off counts of the transform kernels
   TcTables* tabs = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -1176,7 +1175,6 @@ PrecArgs precision_args(magpie_ctx* c, const int32_t* idx, int count) {
   a.err = c->err;
   a.phase = (c->variant & 2) ? c->phase : nullptr;
   a.g1 = (c->p.levels >= 2 && !c->cnn) ? c->g1buf : nullptr;
-  a.e2 = (c->p.levels >= 3 && !c->cnn) ? c->e2buf : nullptr;
   a.count = count;
   a.hand = c->hand;
   a.wait_bias = 0;
@@ -1268,12 +1266,10 @@ int enqueue_step(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st, 
     CUDA_TRY(launch_ex(accum_apply_kernel, dim3(blocks), dim3(256), 0, st, 1, true, c->z, c->acc, npix, idx, count,
                        c->p.n_pos, (const double*)c->part, cluster_of(c->p.m), c->p.m, c->phi_pos, c->gn_pos));
   } else if (c->precision && !c->cnn && c->p.levels >= 2) {
-    // contrib holds g^0: the update forms w . Delta from g^0, g^1 and e^2
+    // contrib holds g^0 and g1buf e^1: the update forms w . Delta from them
     ApplyArgs P = apply_args(c->z, c->p.n_rows, c->p.n_cols, c->corner, idx, count, c->p.n_pos, c->contrib,
                              c->pyr + c->M, c->p.m, c->part, c->phi_pos, c->gn_pos, c->p.m / kTcLines);
-    P.g1 = c->g1buf;
-    P.e2 = c->p.levels >= 3 ? c->e2buf : nullptr;
-    P.iw1 = c->pyr + lvl_off(c->p.m, 1) + c->M / 4;
+    P.e1 = c->g1buf;
     P.u0 = c->pyr;
     P.hand = c->hand;
     P.nhand = 3 * count;
@@ -1761,7 +1757,7 @@ void magpie_destroy(magpie_ctx* c) {
   void* bufs[] = {c->Q, c->tw, c->amp, c->stage, c->pos, c->pyr, c->pyr_q, c->pyr_u, c->contrib,
                   c->phi_pos, c->gn_pos, c->part, c->corner, c->mx, c->pnum, c->pa2, c->pmax, c->iota, c->order, c->sums, c->err,
                   c->wz, c->lx, c->lscale, c->lacc, c->lmargin, c->lstats, c->pbuf, c->tabs, c->phase, c->g1buf,
-                  c->e2buf, c->hand, c->acc};
+                  c->hand, c->acc};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete c;
@@ -2494,7 +2490,6 @@ int magpie_set_precision(magpie_ctx* c, int32_t mode) {
     if (!c->pbuf) {
       cudaError_t e = cudaMalloc((void**)&c->pbuf, sizeof(float2) * (size_t)c->M * c->p.minibatch);
       if (e == cudaSuccess) e = cudaMalloc((void**)&c->g1buf, sizeof(float2) * (size_t)(c->M / 4) * c->p.minibatch);
-      if (e == cudaSuccess) e = cudaMalloc((void**)&c->e2buf, sizeof(float2) * (size_t)(c->M / 16) * c->p.minibatch);
       if (e == cudaSuccess) e = cudaMalloc((void**)&c->hand, sizeof(int) * 3 * (size_t)c->p.minibatch);
       if (e == cudaSuccess) e = cudaMemset(c->hand, 0, sizeof(int) * 3 * (size_t)c->p.minibatch);
       if (e == cudaSuccess) e = cudaMalloc((void**)&c->tabs, sizeof(TcTables));

@@ -537,8 +537,7 @@ struct PrecArgs {
   int2* corner;        // [count] window corners for the update kernel
   int* err;            // bit 0: window index out of range
   float2* phase;       // phase rule: [n_pos][MS][MS] unit phases of the last visit, else null
-  float2* g1;          // levels >= 2: [count][MS/2][MS/2] g^1 = W_u^0 . I(g^0), else null
-  float2* e2;          // levels >= 3: [count][MS/4][MS/4] e^2 from the coarse levels
+  float2* g1;          // levels >= 2: [count][MS/2][MS/2] g^1 = W_u^0 . I(g^0), then e^1; else null
   int* hand;           // [3][count] tiles of each window finished by the exit, project and gradient
                        // kernels (zeroed by the update kernel that ends the step)
   int wait_bias;       // added to every hand-off target: 1 makes every wait run out (a self-test)
@@ -796,20 +795,25 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) grad_dft_kernel(con
           sy += Si[S::at(2 * j + b, 2 * br + a)];
         }
       const float f = 0.25f * wv[u];
-      A.g1[(size_t)B.w * h * h + br * h + bc] = make_float2(f * sx, f * sy);
+      float2 g1 = make_float2(f * sx, f * sy);
+      if (A.L == 2) {  // the coarsest step e^1 = g^1 / w^1, rounded after g^1
+        const float iw = __ldg(&A.pyr[lvl_off(MS, 1) + h * h + br * h + bc]);
+        g1 = make_float2(__fmul_rn(g1.x, iw), __fmul_rn(g1.y, iw));
+      }
+      A.g1[(size_t)B.w * h * h + br * h + bc] = g1;
     }
   }
   handoff_signal(&A.hand[2 * A.count + B.w]);
   T.end(A.err);
 }
 
-// Levels 2 .. L-1 of the V-cycle of one window (levels >= 3), one block per
+// Levels 1 .. L-1 of the V-cycle of one window (levels >= 3), one block per
 // window: restrictions from g^1 (global) into shared memory, the coarsest
-// step, the way up to level 2, and e^2 written to global memory.  The finest
-// two levels (e^1 = g^1 / w^1 + (u^1 / w^1) I_H^h e^2, then w . Delta =
-// g^0 + u^0 I_H^h e^1) are formed pixel by pixel by the update kernel.
-// Dynamic shared memory: levels 2 .. L-1 as float2.  Launched as a
-// programmatic dependent of the gradient kernel.
+// step, the way up, and e^1 = g^1 / w^1 + (u^1 / w^1) I_H^h e^2 written over
+// g^1.  The finest level (w . Delta = g^0 + u^0 I_H^h e^1) is formed pixel by
+// pixel by the update kernel.  Dynamic shared memory: levels 2 .. L-1 as
+// float2.  Launched as a programmatic dependent of the gradient kernel; each
+// block starts on its window once the gradient kernel has handed it over.
 __global__ void __launch_bounds__(1024) coarse_cycle_kernel(const PrecArgs A) {
   extern __shared__ __align__(16) unsigned char csm[];
   float2* E = reinterpret_cast<float2*>(csm);
@@ -872,9 +876,19 @@ __global__ void __launch_bounds__(1024) coarse_cycle_kernel(const PrecArgs A) {
     __syncthreads();
   }
   {
-    const int s = MS >> 2;
-    float2* e2 = A.e2 + (size_t)w * s * s;
-    for (int i = tid; i < s * s; i += nt) e2[i] = E[off(2) + i];
+    // level 1: e^1 = g^1 / w^1 + (u^1 / w^1) I_H^h e^2 over g^1 (in place),
+    // every product rounded as written
+    const int s = MS >> 1, sc = MS >> 2;
+    const float* iw = A.pyr + lvl_off(MS, 1) + s * s;
+    const float* rr = iw + s * s;
+    const float2* pe = E + off(2);
+    for (int i = tid; i < s * s; i += nt) {
+      const int r = i / s, c = i - r * s;
+      const float2 p = pe[(r >> 1) * sc + (c >> 1)];
+      const float2 g = __ldcg(&g1[i]);
+      const float f = __ldg(&iw[i]), q = __ldg(&rr[i]);
+      g1[i] = make_float2(__fmaf_rn(q, p.x, __fmul_rn(g.x, f)), __fmaf_rn(q, p.y, __fmul_rn(g.y, f)));
+    }
   }
 }
 

@@ -37,11 +37,8 @@ struct ApplyArgs {
   int block0;              // batched launches: first block of this problem
   // The precision form's V-cycle tail (apply_body<..., true>): contrib holds
   // g^0, and each window's w . Delta = g^0 + u^0 I_H^h e^1 is formed here as
-  // it is summed, with e^1 = g^1 / w^1, plus (u^1 / w^1) I_H^h e^2 from three
-  // levels on (the finest prolongation of Algorithm MAGPS, residual form).
-  const float2* g1;        // [count][MS/2][MS/2] g^1 = W_u^0 . I(g^0)
-  const float2* e2;        // [count][MS/4][MS/4] e^2, or null for two levels
-  const float* iw1;        // [MS/2][MS/2] 1 / w^1, followed by u^1 / w^1
+  // it is summed (the finest prolongation of Algorithm MAGPS, residual form).
+  const float2* e1;        // [count][MS/2][MS/2] e^1
   const float* u0;         // [MS][MS] u^0
   int* hand;               // precision form: the step's window hand-off counts, zeroed by
   int nhand;               // block (0, 0) once the grid may run (null otherwise)
@@ -117,21 +114,11 @@ __device__ __forceinline__ void apply_body(const ApplyArgs& P, const int tx, con
         v[u] = in ? P.contrib[(size_t)b * M + o] : make_float2(0.f, 0.f);
         wv[u] = in ? __ldg(&P.w0[o]) : 0.f;
         if constexpr (TAIL) {
-          // w . Delta = g^0 + u^0 e^1 at this window pixel; e^1 of its 2 x 2
-          // bin, e^2 of its 4 x 4 bin (every product rounded as written)
-          const int h = MS >> 1, hq = MS >> 2;
-          const int pi = in ? (dr >> 1) * h + (dc >> 1) : 0;
-          const float2 g1 = in ? P.g1[(size_t)b * h * h + pi] : make_float2(0.f, 0.f);
-          const float f = __ldg(&P.iw1[pi]);
-          float ex = __fmul_rn(g1.x, f), ey = __fmul_rn(g1.y, f);
-          if (P.e2) {
-            const float2 p = in ? P.e2[(size_t)b * hq * hq + (dr >> 2) * hq + (dc >> 2)] : make_float2(0.f, 0.f);
-            const float r1 = __ldg(&P.iw1[h * h + pi]);
-            ex = __fmaf_rn(r1, p.x, ex);
-            ey = __fmaf_rn(r1, p.y, ey);
-          }
+          // w . Delta = g^0 + u^0 e^1 at this window pixel, e^1 of its 2 x 2 bin
+          const int h = MS >> 1;
+          const float2 e = in ? P.e1[(size_t)b * h * h + (dr >> 1) * h + (dc >> 1)] : make_float2(0.f, 0.f);
           const float uo = in ? __ldg(&P.u0[o]) : 0.f;
-          v[u] = make_float2(__fmaf_rn(uo, ex, v[u].x), __fmaf_rn(uo, ey, v[u].y));
+          v[u] = make_float2(__fmaf_rn(uo, e.x, v[u].x), __fmaf_rn(uo, e.y, v[u].y));
         }
       }
 #pragma unroll
