@@ -728,6 +728,7 @@ struct magpie_ctx {
   int precision = 0;
   float2* pbuf = nullptr;     // [minibatch][m][m] exit wave / spectrum / revised exit wave
   float2* g1buf = nullptr;    // [minibatch][m/2][m/2] level-1 residual gradient, then increment
+  float2* g2buf = nullptr;    // [minibatch][m/4][m/4] level-2 residual gradient (three levels or more)
   int* hand = nullptr;        // [3][minibatch] window hand-off counts of the transform kernels
   TcTables* tabs = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -1175,6 +1176,7 @@ PrecArgs precision_args(magpie_ctx* c, const int32_t* idx, int count) {
   a.err = c->err;
   a.phase = (c->variant & 2) ? c->phase : nullptr;
   a.g1 = (c->p.levels >= 2 && !c->cnn) ? c->g1buf : nullptr;
+  a.g2 = (c->p.levels >= 3 && !c->cnn) ? c->g2buf : nullptr;
   a.count = count;
   a.hand = c->hand;
   a.wait_bias = 0;
@@ -1234,14 +1236,15 @@ int enqueue_step(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st, 
     if (!rc && c->cnn) {
       rc = enqueue_learned_tail(c, idx, count, st);
     } else if (!rc && c->p.levels >= 2) {
-      // the V-cycle above g^0 (g^1 already restricted by the gradient
-      // kernel): levels 2 .. L-1 one block per window; the finest two
-      // levels are formed by the update kernel as it sums the windows
+      // the V-cycle above g^0 (g^1 and g^2 already restricted by the
+      // gradient kernel): levels 1 .. L-1 on four blocks per window; the
+      // finest level is formed by the update kernel as it sums the windows
       const PrecArgs v = precision_args(c, idx, count);
       if (c->p.levels >= 3) {
         int o = 0;
         for (int j = 2; j < c->p.levels; ++j) o += (c->p.m >> j) * (c->p.m >> j);
-        CUDA_TRY(launch_ex(coarse_cycle_kernel, dim3((unsigned)count), dim3(1024), sizeof(float2) * (size_t)o, st, 1,
+        CUDA_TRY(launch_ex(coarse_cycle_kernel, dim3((unsigned)count, kCoarseSplit), dim3(1024),
+                           sizeof(float2) * (size_t)o, st, 1,
                            true, v));
       }
     }
@@ -1757,7 +1760,7 @@ void magpie_destroy(magpie_ctx* c) {
   void* bufs[] = {c->Q, c->tw, c->amp, c->stage, c->pos, c->pyr, c->pyr_q, c->pyr_u, c->contrib,
                   c->phi_pos, c->gn_pos, c->part, c->corner, c->mx, c->pnum, c->pa2, c->pmax, c->iota, c->order, c->sums, c->err,
                   c->wz, c->lx, c->lscale, c->lacc, c->lmargin, c->lstats, c->pbuf, c->tabs, c->phase, c->g1buf,
-                  c->hand, c->acc};
+                  c->g2buf, c->hand, c->acc};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete c;
@@ -2490,6 +2493,7 @@ int magpie_set_precision(magpie_ctx* c, int32_t mode) {
     if (!c->pbuf) {
       cudaError_t e = cudaMalloc((void**)&c->pbuf, sizeof(float2) * (size_t)c->M * c->p.minibatch);
       if (e == cudaSuccess) e = cudaMalloc((void**)&c->g1buf, sizeof(float2) * (size_t)(c->M / 4) * c->p.minibatch);
+      if (e == cudaSuccess) e = cudaMalloc((void**)&c->g2buf, sizeof(float2) * (size_t)(c->M / 16) * c->p.minibatch);
       if (e == cudaSuccess) e = cudaMalloc((void**)&c->hand, sizeof(int) * 3 * (size_t)c->p.minibatch);
       if (e == cudaSuccess) e = cudaMemset(c->hand, 0, sizeof(int) * 3 * (size_t)c->p.minibatch);
       if (e == cudaSuccess) e = cudaMalloc((void**)&c->tabs, sizeof(TcTables));
@@ -2519,7 +2523,8 @@ int magpie_precision_check_waits(magpie_ctx* c, double seconds) {
   if (c->p.levels >= 3 && !c->cnn) {
     int o = 0;
     for (int j = 2; j < c->p.levels; ++j) o += (c->p.m >> j) * (c->p.m >> j);
-    CUDA_TRY(launch_ex(coarse_cycle_kernel, dim3((unsigned)count), dim3(1024), sizeof(float2) * (size_t)o, c->stream,
+    CUDA_TRY(launch_ex(coarse_cycle_kernel, dim3((unsigned)count, kCoarseSplit), dim3(1024),
+                       sizeof(float2) * (size_t)o, c->stream,
                        1, true, a));
   }
   // no update kernel runs: clear the counts here

@@ -538,6 +538,7 @@ struct PrecArgs {
   int* err;            // bit 0: window index out of range
   float2* phase;       // phase rule: [n_pos][MS][MS] unit phases of the last visit, else null
   float2* g1;          // levels >= 2: [count][MS/2][MS/2] g^1 = W_u^0 . I(g^0), then e^1; else null
+  float2* g2;          // levels >= 3: [count][MS/4][MS/4] g^2 = W_u^1 . I(g^1)
   int* hand;           // [3][count] tiles of each window finished by the exit, project and gradient
                        // kernels (zeroed by the update kernel that ends the step)
   int wait_bias;       // added to every hand-off target: 1 makes every wait run out (a self-test)
@@ -777,6 +778,7 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) grad_dft_kernel(con
     static_assert(NB >= 1 && (NL / 2) * h % 128 == 0, "bins per thread");
     const float* wu0 = A.pyr + lvl_off(MS, 1);
     float wv[NB];  // the bins' W_u^0, loaded together
+    float2 gv[NB];
 #pragma unroll
     for (int u = 0; u < NB; ++u) {
       const int i = threadIdx.x + 128 * u;
@@ -796,28 +798,55 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) grad_dft_kernel(con
         }
       const float f = 0.25f * wv[u];
       float2 g1 = make_float2(f * sx, f * sy);
+      gv[u] = g1;
       if (A.L == 2) {  // the coarsest step e^1 = g^1 / w^1, rounded after g^1
         const float iw = __ldg(&A.pyr[lvl_off(MS, 1) + h * h + br * h + bc]);
         g1 = make_float2(__fmul_rn(g1.x, iw), __fmul_rn(g1.y, iw));
       }
       A.g1[(size_t)B.w * h * h + br * h + bc] = g1;
     }
+    if (A.L >= 3) {
+      // g^2 = W_u^1 . I(g^1) of the block's NL / 4 level-2 columns (the four
+      // g^1 of a bin summed row by row, as the coarse kernel's restrictions),
+      // through shared memory: g^1 as [bin row][NL / 2]
+      __syncthreads();  // every thread is done reading g^0
+#pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        const int i = threadIdx.x + 128 * u;
+        Sr[i] = gv[u].x;
+        Si[i] = gv[u].y;
+      }
+      __syncthreads();
+      constexpr int h2 = h / 2, C2 = NL / 4;
+      const float* wu1 = A.pyr + lvl_off(MS, 2);
+      for (int i = threadIdx.x; i < C2 * h2; i += 128) {
+        const int c2 = i % C2, r2 = i / C2, o = r2 * (MS / 4) + B.l0 / 4 + c2;
+        const int a0 = (2 * r2) * (NL / 2) + 2 * c2, a1 = a0 + NL / 2;
+        const float f = 0.25f * __ldg(&wu1[o]);
+        A.g2[(size_t)B.w * h2 * h2 + o] = make_float2(f * (Sr[a0] + Sr[a0 + 1] + Sr[a1] + Sr[a1 + 1]),
+                                                      f * (Si[a0] + Si[a0 + 1] + Si[a1] + Si[a1 + 1]));
+      }
+    }
   }
   handoff_signal(&A.hand[2 * A.count + B.w]);
   T.end(A.err);
 }
 
-// Levels 1 .. L-1 of the V-cycle of one window (levels >= 3), one block per
-// window: restrictions from g^1 (global) into shared memory, the coarsest
-// step, the way up, and e^1 = g^1 / w^1 + (u^1 / w^1) I_H^h e^2 written over
-// g^1.  The finest level (w . Delta = g^0 + u^0 I_H^h e^1) is formed pixel by
-// pixel by the update kernel.  Dynamic shared memory: levels 2 .. L-1 as
-// float2.  Launched as a programmatic dependent of the gradient kernel; each
-// block starts on its window once the gradient kernel has handed it over.
+// Levels 1 .. L-1 of the V-cycle of one window (levels >= 3), four blocks
+// per window (blockIdx.y = q): each takes g^2 from the gradient kernel into
+// shared memory, restricts it to the coarser levels, takes the coarsest step
+// and the way up to level 2 (the same work in all four blocks), then writes
+// e^1 = g^1 / w^1 + (u^1 / w^1) I_H^h e^2 over its quarter of the rows of
+// g^1, every product rounded as written.  The finest level (w . Delta =
+// g^0 + u^0 I_H^h e^1) is formed pixel by pixel by the update kernel.
+// Dynamic shared memory: levels 2 .. L-1 as float2.  Launched as a
+// programmatic dependent of the gradient kernel; each block starts on its
+// window once the gradient kernel has handed it over.
+constexpr int kCoarseSplit = 4;
 __global__ void __launch_bounds__(1024) coarse_cycle_kernel(const PrecArgs A) {
   extern __shared__ __align__(16) unsigned char csm[];
   float2* E = reinterpret_cast<float2*>(csm);
-  const int w = blockIdx.x, tid = threadIdx.x, nt = blockDim.x, MS = A.MS, L = A.L;
+  const int w = blockIdx.x, q = blockIdx.y, tid = threadIdx.x, nt = blockDim.x, MS = A.MS, L = A.L;
   grid_dep_launch();  // the update kernel after it waits for the whole grid
   if ((unsigned)A.idx[w] >= (unsigned)A.n_pos) return;
   if (!handoff_wait(A, &A.hand[2 * A.count + w], MS / kTcLines)) return;  // ran out: skip the window
@@ -826,25 +855,20 @@ __global__ void __launch_bounds__(1024) coarse_cycle_kernel(const PrecArgs A) {
     for (int j = 2; j < l; ++j) o += (MS >> j) * (MS >> j);
     return o;
   };
-  float2* g1 = A.g1 + (size_t)w * (MS / 2) * (MS / 2);
-  for (int l = 2; l < L; ++l) {
+  {
+    const int s2 = MS >> 2;
+    const float2* g2 = A.g2 + (size_t)w * s2 * s2;
+    for (int i = tid; i < s2 * s2; i += nt) E[i] = __ldcg(&g2[i]);  // off(2) = 0
+    __syncthreads();
+  }
+  for (int l = 3; l < L; ++l) {
     const int s = MS >> l, sf = MS >> (l - 1);
-    const float2* src = l == 2 ? g1 : E + off(l - 1);
+    const float2* src = E + off(l - 1);
     const float* wu = A.pyr + lvl_off(MS, l);
     for (int i = tid; i < s * s; i += nt) {
       const int r = i / s, c = i - r * s;
-      float2 a, b, cc, d;
-      if (l == 2) {  // handed off by the gradient kernel: read through L2
-        a = __ldcg(&src[(2 * r) * sf + 2 * c]);
-        b = __ldcg(&src[(2 * r) * sf + 2 * c + 1]);
-        cc = __ldcg(&src[(2 * r + 1) * sf + 2 * c]);
-        d = __ldcg(&src[(2 * r + 1) * sf + 2 * c + 1]);
-      } else {
-        a = src[(2 * r) * sf + 2 * c];
-        b = src[(2 * r) * sf + 2 * c + 1];
-        cc = src[(2 * r + 1) * sf + 2 * c];
-        d = src[(2 * r + 1) * sf + 2 * c + 1];
-      }
+      const float2 a = src[(2 * r) * sf + 2 * c], b = src[(2 * r) * sf + 2 * c + 1];
+      const float2 cc = src[(2 * r + 1) * sf + 2 * c], d = src[(2 * r + 1) * sf + 2 * c + 1];
       const float f = 0.25f * __ldg(&wu[i]);
       E[off(l) + i] = make_float2(f * (a.x + b.x + cc.x + d.x), f * (a.y + b.y + cc.y + d.y));
     }
@@ -870,24 +894,24 @@ __global__ void __launch_bounds__(1024) coarse_cycle_kernel(const PrecArgs A) {
       const int r = i / s, c = i - r * s;
       const float2 p = pe[(r >> 1) * sc + (c >> 1)];
       const float2 g = a[i];
-      const float f = __ldg(&iw[i]), q = __ldg(&rr[i]);
-      a[i] = make_float2(g.x * f + q * p.x, g.y * f + q * p.y);
+      const float f = __ldg(&iw[i]), q2 = __ldg(&rr[i]);
+      a[i] = make_float2(__fmaf_rn(q2, p.x, __fmul_rn(g.x, f)), __fmaf_rn(q2, p.y, __fmul_rn(g.y, f)));
     }
     __syncthreads();
   }
   {
-    // level 1: e^1 = g^1 / w^1 + (u^1 / w^1) I_H^h e^2 over g^1 (in place),
-    // every product rounded as written
-    const int s = MS >> 1, sc = MS >> 2;
+    // level 1 over this block's quarter of the rows of g^1 (in place)
+    const int s = MS >> 1, sc = MS >> 2, rows = s / kCoarseSplit;
+    float2* g1 = A.g1 + (size_t)w * s * s;
     const float* iw = A.pyr + lvl_off(MS, 1) + s * s;
     const float* rr = iw + s * s;
-    const float2* pe = E + off(2);
-    for (int i = tid; i < s * s; i += nt) {
+    const float2* pe = E;  // level 2
+    for (int i = q * rows * s + tid; i < (q + 1) * rows * s; i += nt) {
       const int r = i / s, c = i - r * s;
       const float2 p = pe[(r >> 1) * sc + (c >> 1)];
       const float2 g = __ldcg(&g1[i]);
-      const float f = __ldg(&iw[i]), q = __ldg(&rr[i]);
-      g1[i] = make_float2(__fmaf_rn(q, p.x, __fmul_rn(g.x, f)), __fmaf_rn(q, p.y, __fmul_rn(g.y, f)));
+      const float f = __ldg(&iw[i]), qq = __ldg(&rr[i]);
+      g1[i] = make_float2(__fmaf_rn(qq, p.x, __fmul_rn(g.x, f)), __fmaf_rn(qq, p.y, __fmul_rn(g.y, f)));
     }
   }
 }
