@@ -76,12 +76,14 @@ struct TcSm {
 // Fills the NL lines from src(l, p) (line l, position p along the line),
 // eight loads in flight per thread.  AXIS 1: consecutive threads take
 // consecutive positions of a line (rows of a window); AXIS 0: consecutive
-// lines at one position (columns).
+// lines at one position (columns).  Returns the largest |re|, |im| this
+// thread stored (for tc_lines' block scale).
 template <int MS, int AXIS, typename Src>
-__device__ __forceinline__ void tc_load(float* Sr, float* Si, Src src) {
+__device__ __forceinline__ float tc_load(float* Sr, float* Si, Src src) {
   using S = TcSm<MS>;
   constexpr int NL = S::NL;
   static_assert((NL * MS) % (128 * 8) == 0, "load batches");
+  float mx = 0.f;
   for (int i0 = threadIdx.x; i0 < NL * MS; i0 += 128 * 8) {
     float2 v[8];
 #pragma unroll
@@ -95,8 +97,10 @@ __device__ __forceinline__ void tc_load(float* Sr, float* Si, Src src) {
       const int l = AXIS == 1 ? i / MS : i % NL, p = AXIS == 1 ? i % MS : i / NL;
       Sr[S::at(l, p)] = v[u].x;
       Si[S::at(l, p)] = v[u].y;
+      mx = fmaxf(mx, fmaxf(fabsf(v[u].x), fabsf(v[u].y)));
     }
   }
+  return mx;
 }
 
 // dst(l, p, value) for every element of the NL lines, in the thread order of
@@ -113,16 +117,11 @@ __device__ __forceinline__ void tc_store(const float* Sr, const float* Si, Dst d
 
 // The power of two s of the FP16 operands (see the top of this file): max
 // |s x| over the block's lines in [2^9, 2^10); 1 for all-zero or non-finite
-// lines.  128 threads; the lines must be in place; one barrier.
-template <int MS>
-__device__ __forceinline__ float tc_scale(const float* Sr, const float* Si) {
-  using S = TcSm<MS>;
+// lines.  Each of the 128 threads passes the largest |re|, |im| it wrote
+// into the lines (so no pass over them is needed); one barrier, which also
+// puts every thread's lines in place.
+__device__ __forceinline__ float tc_scale(float mx) {
   __shared__ float red[4];
-  float mx = 0.f;
-  for (int i = threadIdx.x; i < S::NL * MS; i += 128) {
-    const int l = i / MS, p = i % MS;
-    mx = fmaxf(mx, fmaxf(fabsf(Sr[S::at(l, p)]), fabsf(Si[S::at(l, p)])));
-  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
@@ -139,15 +138,14 @@ __device__ __forceinline__ float tc_scale(const float* Sr, const float* Si) {
 // begins with a barrier (the lines must be in place) and ends with one.
 template <int MS, int INV>
 __device__ __forceinline__ void tc_lines(float* Sr, float* Si, const TcTables* __restrict__ tabs,
-                                         const float2* __restrict__ tw, float scale) {
+                                         const float2* __restrict__ tw, float scale, float mx) {
   using S = TcSm<MS>;
   constexpr int QR = S::QR, NL = S::NL;
   constexpr int K2T = (2 * QR + 15) / 16;  // stage-2 k-tiles
   constexpr int N2T = 2 * QR / 8;          // stage-2 n-tiles
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
-  __syncthreads();  // the lines in place
-  const float sx = tc_scale<MS>(Sr, Si), out_scale = scale / sx;
+  const float sx = tc_scale(mx), out_scale = scale / sx;  // its barrier: the lines in place
 
   // ---- stage-1 operands: the 16-point DFT matrix as A fragments (hi, lo)
   uint32_t ah[2][2][4], al[2][2][4];
@@ -344,14 +342,13 @@ __device__ __forceinline__ void umma_tile(TcUmma& U, uint32_t b_hi, uint32_t b_l
 
 template <int MS, int INV>
 __device__ __forceinline__ void tc_lines_umma(float* Sr, float* Si, const TcTables* __restrict__ tabs,
-                                              const float2* __restrict__ tw, float scale, TcUmma& U) {
+                                              const float2* __restrict__ tw, float scale, float mx, TcUmma& U) {
   using S = TcSm<MS>;
   constexpr int QR = S::QR, NL = S::NL;
   constexpr int Q2 = 2 * QR < 16 ? 16 : 2 * QR;  // stage-2 K and N, padded to 16
   const int tid = threadIdx.x;
   const uint32_t trow = U.tmem + ((uint32_t)(tid & ~31) << 16);  // this warp's TMEM lanes
-  __syncthreads();  // the lines in place
-  const float sx = tc_scale<MS>(Sr, Si), out_scale = scale / sx;
+  const float sx = tc_scale(mx), out_scale = scale / sx;  // its barrier: the lines in place
   // B operands: stage 1 rows r, K c: f16[r][c]; stage 2 rows nn, K kk: fq[kk][nn] (0 in the padding)
   {
     const float* F1 = tabs->f16[INV];
@@ -448,8 +445,9 @@ struct TcPath {
   __device__ __forceinline__ void begin() {}
   __device__ __forceinline__ void end(int*) {}
   template <int MS, int INV>
-  __device__ __forceinline__ void lines(float* Sr, float* Si, const TcTables* tabs, const float2* tw, float sc) {
-    tc_lines<MS, INV>(Sr, Si, tabs, tw, sc);
+  __device__ __forceinline__ void lines(float* Sr, float* Si, const TcTables* tabs, const float2* tw, float sc,
+                                        float mx) {
+    tc_lines<MS, INV>(Sr, Si, tabs, tw, sc, mx);
   }
 };
 template <>
@@ -489,8 +487,9 @@ struct TcPath<1> {
     if (!U.ok && err) atomicOr(err, 16);
   }
   template <int MS, int INV>
-  __device__ __forceinline__ void lines(float* Sr, float* Si, const TcTables* tabs, const float2* tw, float sc) {
-    tc_lines_umma<MS, INV>(Sr, Si, tabs, tw, sc, U);
+  __device__ __forceinline__ void lines(float* Sr, float* Si, const TcTables* tabs, const float2* tw, float sc,
+                                        float mx) {
+    tc_lines_umma<MS, INV>(Sr, Si, tabs, tw, sc, mx, U);
   }
 };
 
@@ -508,10 +507,10 @@ __global__ void __launch_bounds__(128) dft_tc_kernel(float2* __restrict__ data, 
   const int tiles = MS / S::NL;
   const int win = blockIdx.x / tiles, l0 = (blockIdx.x % tiles) * S::NL;
   float2* base = data + (size_t)win * MS * MS;
-  tc_load<MS, AXIS>(Sr, Si, [&](int l, int p) {
+  const float mx = tc_load<MS, AXIS>(Sr, Si, [&](int l, int p) {
     return AXIS == 1 ? base[(size_t)(l0 + l) * MS + p] : base[(size_t)p * MS + l0 + l];
   });
-  T.template lines<MS, INV>(Sr, Si, tabs, tw, scale);
+  T.template lines<MS, INV>(Sr, Si, tabs, tw, scale, mx);
   tc_store<MS, AXIS>(Sr, Si, [&](int l, int p, float2 v) {
     if (AXIS == 1)
       base[(size_t)(l0 + l) * MS + p] = v;
@@ -643,13 +642,13 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) exit_dft_kernel(con
     }
   }
   const float2* zk = A.z + (B.ok ? (size_t)A.pos[2 * B.k] * A.n_cols + A.pos[2 * B.k + 1] : 0);
-  tc_load<MS, 0>(Sr, Si, [&](int l, int p) {
+  const float mx = tc_load<MS, 0>(Sr, Si, [&](int l, int p) {
     if (!B.ok) return make_float2(0.f, 0.f);
     const float2 zz = zk[(size_t)p * A.n_cols + B.l0 + l];
     const float2 qq = __ldg(&A.Q[p * MS + B.l0 + l]);
     return make_float2(qq.x * zz.x - qq.y * zz.y, qq.x * zz.y + qq.y * zz.x);
   });
-  T.template lines<MS, 0>(Sr, Si, tabs, tw, 1.f);
+  T.template lines<MS, 0>(Sr, Si, tabs, tw, 1.f, mx);
   float2* base = A.buf + (size_t)B.w * MS * MS;
   tc_store<MS, 0>(Sr, Si, [&](int l, int p, float2 v) { base[(size_t)p * MS + B.l0 + l] = v; });
   handoff_signal(&A.hand[B.w]);
@@ -679,13 +678,13 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) project_dft_kernel(
     T.end(A.err);
     return;
   }
-  tc_load<MS, 1>(Sr, Si, [&](int l, int p) { return __ldcg(&base[(size_t)(B.l0 + l) * MS + p]); });
-  T.template lines<MS, 0>(Sr, Si, tabs, tw, 1.f);
+  const float mx = tc_load<MS, 1>(Sr, Si, [&](int l, int p) { return __ldcg(&base[(size_t)(B.l0 + l) * MS + p]); });
+  T.template lines<MS, 0>(Sr, Si, tabs, tw, 1.f, mx);
   // Psi <- sqrt(d) Psi / |Psi| / m^2 (sqrt(d) / m^2 where Psi = 0, or the
   // previous visit's phase under the phase rule)
   const float* am = A.amp + (size_t)(B.ok ? B.k : 0) * MS * MS;
   const float inv_m2 = 1.f / (float)(MS * MS);
-  float res = 0.f;
+  float res = 0.f, mx2 = 0.f;  // mx2: the inverse transform's block scale, from the values written
   for (int i0 = threadIdx.x; i0 < S::NL * MS; i0 += 128 * 8) {
     float av[8];  // eight amplitude loads in flight per thread
 #pragma unroll
@@ -710,13 +709,15 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) project_dft_kernel(
       } else if (A.phase && B.ok) {
         ph = A.phase[(size_t)B.k * MS * MS + o];  // Eq. (specification): the previous visit's phase
       }
-      Sr[S::at(l, p)] = a * inv_m2 * ph.x;
-      Si[S::at(l, p)] = a * inv_m2 * ph.y;
+      const float px = a * inv_m2 * ph.x, py = a * inv_m2 * ph.y;
+      Sr[S::at(l, p)] = px;
+      Si[S::at(l, p)] = py;
+      mx2 = fmaxf(mx2, fmaxf(fabsf(px), fabsf(py)));
     }
   }
   const double s = block_sum((double)res, red, threadIdx.x, 128);
   if (threadIdx.x == 0) A.part[((size_t)B.w * A.T + B.tile) * 2] = B.ok ? s : 0.0;
-  T.template lines<MS, 1>(Sr, Si, tabs, tw, 1.f);
+  T.template lines<MS, 1>(Sr, Si, tabs, tw, 1.f, mx2);
   tc_store<MS, 1>(Sr, Si, [&](int l, int p, float2 v) { base[(size_t)(B.l0 + l) * MS + p] = v; });
   handoff_signal(&A.hand[A.count + B.w]);
   T.end(A.err);
@@ -740,8 +741,8 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) grad_dft_kernel(con
     T.end(A.err);
     return;
   }
-  tc_load<MS, 0>(Sr, Si, [&](int l, int p) { return __ldcg(&base[(size_t)p * MS + B.l0 + l]); });
-  T.template lines<MS, 1>(Sr, Si, tabs, tw, 1.f);
+  const float mx = tc_load<MS, 0>(Sr, Si, [&](int l, int p) { return __ldcg(&base[(size_t)p * MS + B.l0 + l]); });
+  T.template lines<MS, 1>(Sr, Si, tabs, tw, 1.f, mx);
   const float2* zk = A.z + (B.ok ? (size_t)A.pos[2 * B.k] * A.n_cols + A.pos[2 * B.k + 1] : 0);
   float2* out = A.contrib + (size_t)B.w * MS * MS;
   float gn = 0.f;
