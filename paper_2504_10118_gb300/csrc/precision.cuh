@@ -807,25 +807,23 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) grad_dft_kernel(con
       A.g1[(size_t)B.w * h * h + br * h + bc] = g1;
     }
     if (A.L >= 3) {
-      // g^2 = W_u^1 . I(g^1) of the block's NL / 4 level-2 columns (the four
-      // g^1 of a bin summed row by row, as the coarse kernel's restrictions),
-      // through shared memory: g^1 as [bin row][NL / 2]
-      __syncthreads();  // every thread is done reading g^0
+      // g^2 = W_u^1 . I(g^1) of the block's NL / 4 level-2 columns: bin i of
+      // g^1 is (row i / (NL / 2), column i % (NL / 2)), so the four g^1 of a
+      // level-2 bin sit in lanes i, i ^ 1, i ^ NL / 2, i ^ (NL / 2 + 1) of one
+      // warp; summed row by row, as the coarse kernel's restrictions
+      static_assert(NL / 2 == 8, "bin row of g^1 = eight lanes");
+      const float* wu1 = A.pyr + lvl_off(MS, 2);
 #pragma unroll
       for (int u = 0; u < NB; ++u) {
         const int i = threadIdx.x + 128 * u;
-        Sr[i] = gv[u].x;
-        Si[i] = gv[u].y;
-      }
-      __syncthreads();
-      constexpr int h2 = h / 2, C2 = NL / 4;
-      const float* wu1 = A.pyr + lvl_off(MS, 2);
-      for (int i = threadIdx.x; i < C2 * h2; i += 128) {
-        const int c2 = i % C2, r2 = i / C2, o = r2 * (MS / 4) + B.l0 / 4 + c2;
-        const int a0 = (2 * r2) * (NL / 2) + 2 * c2, a1 = a0 + NL / 2;
-        const float f = 0.25f * __ldg(&wu1[o]);
-        A.g2[(size_t)B.w * h2 * h2 + o] = make_float2(f * (Sr[a0] + Sr[a0 + 1] + Sr[a1] + Sr[a1 + 1]),
-                                                      f * (Si[a0] + Si[a0 + 1] + Si[a1] + Si[a1 + 1]));
+        const float2 b = shfl_xor2(gv[u], 1), cc = shfl_xor2(gv[u], 8), d = shfl_xor2(gv[u], 9);
+        const int j = i % (NL / 2), br = i / (NL / 2);
+        if (((j | br) & 1) == 0) {
+          const int o = (br / 2) * (MS / 4) + B.l0 / 4 + j / 2;
+          const float f = 0.25f * __ldg(&wu1[o]);
+          A.g2[(size_t)B.w * (h / 2) * (h / 2) + o] =
+              make_float2(f * (gv[u].x + b.x + cc.x + d.x), f * (gv[u].y + b.y + cc.y + d.y));
+        }
       }
     }
   }
