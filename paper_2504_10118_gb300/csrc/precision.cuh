@@ -66,9 +66,13 @@ __device__ __forceinline__ void mma3(float* c, const uint32_t* ah, const uint32_
 template <int MS>
 struct TcSm {
   static constexpr int QR = MS / 16, NL = kTcLines, LD = MS + 68;
-  // resident blocks per SM the fused kernels' registers are bounded for
-  // (m = 256: three 128-thread blocks, which measured faster than two)
-  static constexpr int MIN_BLOCKS = MS == 256 ? 3 : 1;
+  // resident blocks per SM the fused kernels' registers are bounded for at
+  // m = 256: four 128-thread blocks with register-fragment MMAs (128
+  // registers, a few spilled words; 449 k against 422 k patterns/s with
+  // three), three with tcgen05, whose 67 KB of shared memory allow no more
+  // (a bound of four measured slower there: 374 k against 385 k)
+  template <int PATH>
+  static constexpr int min_blocks() { return MS == 256 ? (PATH ? 3 : 4) : 1; }
   static_assert(QR == 4 || QR == 8 || QR == 16, "window side 64, 128 or 256");
   __device__ static __forceinline__ int at(int l, int i) { return l * LD + i + 4 * (i / QR); }
 };
@@ -623,7 +627,7 @@ __device__ __forceinline__ TcBlock tc_block(const PrecArgs& A) {
 }
 
 template <int MS, int PATH>
-__global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) exit_dft_kernel(const PrecArgs A, const TcTables* __restrict__ tabs,
+__global__ void __launch_bounds__(128, TcSm<MS>::template min_blocks<PATH>()) exit_dft_kernel(const PrecArgs A, const TcTables* __restrict__ tabs,
                                                        const float2* __restrict__ tw) {
   using S = TcSm<MS>;
   __shared__ float Sr[S::NL * S::LD];
@@ -656,7 +660,7 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) exit_dft_kernel(con
 }
 
 template <int MS, int PATH>
-__global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) project_dft_kernel(const PrecArgs A, const TcTables* __restrict__ tabs,
+__global__ void __launch_bounds__(128, TcSm<MS>::template min_blocks<PATH>()) project_dft_kernel(const PrecArgs A, const TcTables* __restrict__ tabs,
                                                           const float2* __restrict__ tw) {
   using S = TcSm<MS>;
   __shared__ float Sr[S::NL * S::LD];
@@ -724,7 +728,7 @@ __global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) project_dft_kernel(
 }
 
 template <int MS, int PATH>
-__global__ void __launch_bounds__(128, TcSm<MS>::MIN_BLOCKS) grad_dft_kernel(const PrecArgs A, const TcTables* __restrict__ tabs,
+__global__ void __launch_bounds__(128, TcSm<MS>::template min_blocks<PATH>()) grad_dft_kernel(const PrecArgs A, const TcTables* __restrict__ tabs,
                                                        const float2* __restrict__ tw) {
   using S = TcSm<MS>;
   constexpr int NL = S::NL, h = MS / 2;
