@@ -1208,6 +1208,21 @@ cudaError_t launch_precision_g0(const PrecArgs& a, int count, const TcTables* ta
   return e;
 }
 
+// The precision form's coarse levels (three levels or more), four blocks
+// per window, a programmatic dependent of the gradient kernel.
+cudaError_t launch_coarse_cycle(const PrecArgs& a, int count, int levels, cudaStream_t st) {
+  int o = 0;
+  for (int j = 2; j < levels; ++j) o += (a.MS >> j) * (a.MS >> j);
+  const dim3 grid((unsigned)count, kCoarseSplit);
+  const size_t smem = sizeof(float2) * (size_t)o;
+  switch (a.MS) {
+    case 64: return launch_ex(coarse_cycle_kernel<64>, grid, dim3(1024), smem, st, 1, true, a);
+    case 128: return launch_ex(coarse_cycle_kernel<128>, grid, dim3(1024), smem, st, 1, true, a);
+    case 256: return launch_ex(coarse_cycle_kernel<256>, grid, dim3(1024), smem, st, 1, true, a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 int enqueue_precision_g0(magpie_ctx* c, const PrecArgs& a, int count, cudaStream_t st) {
   switch (a.MS) {
     case 64: CUDA_TRY(launch_precision_g0<64>(a, count, c->tabs, c->tw, st, c->precision == 2)); break;
@@ -1240,13 +1255,7 @@ int enqueue_step(magpie_ctx* c, const int32_t* idx, int count, cudaStream_t st, 
       // gradient kernel): levels 1 .. L-1 on four blocks per window; the
       // finest level is formed by the update kernel as it sums the windows
       const PrecArgs v = precision_args(c, idx, count);
-      if (c->p.levels >= 3) {
-        int o = 0;
-        for (int j = 2; j < c->p.levels; ++j) o += (c->p.m >> j) * (c->p.m >> j);
-        CUDA_TRY(launch_ex(coarse_cycle_kernel, dim3((unsigned)count, kCoarseSplit), dim3(1024),
-                           sizeof(float2) * (size_t)o, st, 1,
-                           true, v));
-      }
+      if (c->p.levels >= 3) CUDA_TRY(launch_coarse_cycle(v, count, c->p.levels, st));
     }
   } else {
     a.grad_only = c->cnn ? 1 : 0;
@@ -2520,13 +2529,7 @@ int magpie_precision_check_waits(magpie_ctx* c, double seconds) {
   a.wait_ns = (unsigned long long)(seconds * 1e9);
   const int rc = enqueue_precision_g0(c, a, count, c->stream);
   if (rc) return rc;
-  if (c->p.levels >= 3 && !c->cnn) {
-    int o = 0;
-    for (int j = 2; j < c->p.levels; ++j) o += (c->p.m >> j) * (c->p.m >> j);
-    CUDA_TRY(launch_ex(coarse_cycle_kernel, dim3((unsigned)count, kCoarseSplit), dim3(1024),
-                       sizeof(float2) * (size_t)o, c->stream,
-                       1, true, a));
-  }
+  if (c->p.levels >= 3 && !c->cnn) CUDA_TRY(launch_coarse_cycle(a, count, c->p.levels, c->stream));
   // no update kernel runs: clear the counts here
   CUDA_TRY(cudaMemsetAsync(c->hand, 0, sizeof(int) * 3 * (size_t)count, c->stream));
   return read_err(c);

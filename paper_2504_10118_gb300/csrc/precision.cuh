@@ -846,10 +846,12 @@ __global__ void __launch_bounds__(128, TcSm<MS>::template min_blocks<PATH>()) gr
 // programmatic dependent of the gradient kernel; each block starts on its
 // window once the gradient kernel has handed it over.
 constexpr int kCoarseSplit = 4;
+template <int MS>
 __global__ void __launch_bounds__(1024) coarse_cycle_kernel(const PrecArgs A) {
   extern __shared__ __align__(16) unsigned char csm[];
   float2* E = reinterpret_cast<float2*>(csm);
-  const int w = blockIdx.x, q = blockIdx.y, tid = threadIdx.x, nt = blockDim.x, MS = A.MS, L = A.L;
+  constexpr int nt = 1024;
+  const int w = blockIdx.x, q = blockIdx.y, tid = threadIdx.x, L = A.L;
   grid_dep_launch();  // the update kernel after it waits for the whole grid
   if ((unsigned)A.idx[w] >= (unsigned)A.n_pos) return;
   if (!handoff_wait(A, &A.hand[2 * A.count + w], MS / kTcLines)) return;  // ran out: skip the window
@@ -859,17 +861,19 @@ __global__ void __launch_bounds__(1024) coarse_cycle_kernel(const PrecArgs A) {
     return o;
   };
   {
-    const int s2 = MS >> 2;
+    constexpr int s2 = MS >> 2;
     const float2* g2 = A.g2 + (size_t)w * s2 * s2;
+#pragma unroll
     for (int i = tid; i < s2 * s2; i += nt) E[i] = __ldcg(&g2[i]);  // off(2) = 0
     __syncthreads();
   }
+  constexpr int LM = MS == 256 ? 8 : MS == 128 ? 7 : 6;  // log2(MS)
   for (int l = 3; l < L; ++l) {
-    const int s = MS >> l, sf = MS >> (l - 1);
+    const int s = MS >> l, sf = MS >> (l - 1), ls = LM - l;
     const float2* src = E + off(l - 1);
     const float* wu = A.pyr + lvl_off(MS, l);
     for (int i = tid; i < s * s; i += nt) {
-      const int r = i / s, c = i - r * s;
+      const int r = i >> ls, c = i & (s - 1);
       const float2 a = src[(2 * r) * sf + 2 * c], b = src[(2 * r) * sf + 2 * c + 1];
       const float2 cc = src[(2 * r + 1) * sf + 2 * c], d = src[(2 * r + 1) * sf + 2 * c + 1];
       const float f = 0.25f * __ldg(&wu[i]);
@@ -888,13 +892,13 @@ __global__ void __launch_bounds__(1024) coarse_cycle_kernel(const PrecArgs A) {
     __syncthreads();
   }
   for (int l = L - 2; l >= 2; --l) {
-    const int s = MS >> l, sc = MS >> (l + 1);
+    const int s = MS >> l, sc = MS >> (l + 1), ls = LM - l;
     const float* iw = A.pyr + lvl_off(MS, l) + s * s;
     const float* rr = iw + s * s;
     float2* a = E + off(l);
     const float2* pe = E + off(l + 1);
     for (int i = tid; i < s * s; i += nt) {
-      const int r = i / s, c = i - r * s;
+      const int r = i >> ls, c = i & (s - 1);
       const float2 p = pe[(r >> 1) * sc + (c >> 1)];
       const float2 g = a[i];
       const float f = __ldg(&iw[i]), q2 = __ldg(&rr[i]);
@@ -904,13 +908,14 @@ __global__ void __launch_bounds__(1024) coarse_cycle_kernel(const PrecArgs A) {
   }
   {
     // level 1 over this block's quarter of the rows of g^1 (in place)
-    const int s = MS >> 1, sc = MS >> 2, rows = s / kCoarseSplit;
+    constexpr int s = MS >> 1, sc = MS >> 2, rows = s / kCoarseSplit;
     float2* g1 = A.g1 + (size_t)w * s * s;
     const float* iw = A.pyr + lvl_off(MS, 1) + s * s;
     const float* rr = iw + s * s;
     const float2* pe = E;  // level 2
+#pragma unroll
     for (int i = q * rows * s + tid; i < (q + 1) * rows * s; i += nt) {
-      const int r = i / s, c = i - r * s;
+      const int r = i >> (LM - 1), c = i & (s - 1);
       const float2 p = pe[(r >> 1) * sc + (c >> 1)];
       const float2 g = __ldcg(&g1[i]);
       const float f = __ldg(&iw[i]), qq = __ldg(&rr[i]);
