@@ -1190,18 +1190,19 @@ template <int MS>
 cudaError_t launch_precision_g0(const PrecArgs& a, int count, const TcTables* tabs, const float2* tw,
                                 cudaStream_t st, int path) {
   const dim3 grid((unsigned)count * (MS / kTcLines));
+  // each a programmatic dependent of the kernel before it: the exit kernel
+  // waits for the previous step to complete, the others take their windows
+  // from the kernel before them one by one (PrecArgs::hand)
   if (path) {
-    const cudaError_t e = prepare_dft_umma<MS>();
-    if (e != cudaSuccess) return e;
-    cudaError_t e2 = launch_ex(exit_dft_kernel<MS, 1>, grid, dim3(128), kUmmaDftSmem, st, 1, true, a, tabs, tw);
-    if (e2 == cudaSuccess)
-      e2 = launch_ex(project_dft_kernel<MS, 1>, grid, dim3(128), kUmmaDftSmem, st, 1, true, a, tabs, tw);
-    if (e2 == cudaSuccess)
-      e2 = launch_ex(grad_dft_kernel<MS, 1>, grid, dim3(128), kUmmaDftSmem, st, 1, true, a, tabs, tw);
-    return e2;
+    cudaError_t e = prepare_dft_umma<MS>();
+    if (e == cudaSuccess)
+      e = launch_ex(exit_dft_kernel<MS, 1>, grid, dim3(128), kUmmaDftSmem, st, 1, true, a, tabs, tw);
+    if (e == cudaSuccess)
+      e = launch_ex(project_dft_kernel<MS, 1>, grid, dim3(128), kUmmaDftSmem, st, 1, true, a, tabs, tw);
+    if (e == cudaSuccess)
+      e = launch_ex(grad_dft_kernel<MS, 1>, grid, dim3(128), kUmmaDftSmem, st, 1, true, a, tabs, tw);
+    return e;
   }
-  // each a programmatic dependent of the kernel before it (its blocks are
-  // set up while that kernel drains)
   cudaError_t e = launch_ex(exit_dft_kernel<MS, 0>, grid, dim3(128), 0, st, 1, true, a, tabs, tw);
   if (e == cudaSuccess) e = launch_ex(project_dft_kernel<MS, 0>, grid, dim3(128), 0, st, 1, true, a, tabs, tw);
   if (e == cudaSuccess) e = launch_ex(grad_dft_kernel<MS, 0>, grid, dim3(128), 0, st, 1, true, a, tabs, tw);

@@ -138,8 +138,9 @@ __device__ __forceinline__ float tc_scale(float mx) {
 }
 
 // The forward (INV = 0) or conjugate (INV = 1) DFT of the block's NL lines,
-// in place in shared memory, the output multiplied by `scale`.  128 threads;
-// begins with a barrier (the lines must be in place) and ends with one.
+// in place in shared memory, the output multiplied by `scale`; `mx` is the
+// largest |re|, |im| this thread wrote into the lines.  128 threads; begins
+// with a barrier (the lines must be in place) and ends with one.
 template <int MS, int INV>
 __device__ __forceinline__ void tc_lines(float* Sr, float* Si, const TcTables* __restrict__ tabs,
                                          const float2* __restrict__ tw, float scale, float mx) {
