@@ -86,17 +86,18 @@ template <int MS, int AXIS, typename Src>
 __device__ __forceinline__ float tc_load(float* Sr, float* Si, Src src) {
   using S = TcSm<MS>;
   constexpr int NL = S::NL;
-  static_assert((NL * MS) % (128 * 8) == 0, "load batches");
+  constexpr int NB = (NL * MS) % (128 * 16) == 0 ? 16 : 8;
+  static_assert((NL * MS) % (128 * NB) == 0, "load batches");
   float mx = 0.f;
-  for (int i0 = threadIdx.x; i0 < NL * MS; i0 += 128 * 8) {
-    float2 v[8];
+  for (int i0 = threadIdx.x; i0 < NL * MS; i0 += 128 * NB) {
+    float2 v[NB];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < NB; ++u) {
       const int i = i0 + 128 * u;
       v[u] = AXIS == 1 ? src(i / MS, i % MS) : src(i % NL, i / NL);
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < NB; ++u) {
       const int i = i0 + 128 * u;
       const int l = AXIS == 1 ? i / MS : i % NL, p = AXIS == 1 ? i % MS : i / NL;
       Sr[S::at(l, p)] = v[u].x;
