@@ -713,9 +713,10 @@ def launches_per_step(args, w) -> int:
     if args.learned:
         return 1 + 1 + 1 + 6 + 4 + 1 + 1  # window, coarse state, cast, 6 convolutions, split-K sums, V-cycle, update
     if args.dft in ("tc", "tcgen05"):
-        # exit wave + column DFTs, row DFTs + projection, inverse column DFTs + g^0,
-        # coarse levels, finest level, update
-        return 3 + (1 if w.levels >= 3 else 0) + (1 if w.levels >= 2 else 0) + 1
+        # exit wave + column DFTs, row DFTs + projection, inverse column DFTs + g^0
+        # (+ g^1, g^2), the coarse levels (three levels or more), the update
+        # (which also forms the finest level)
+        return 3 + (1 if w.levels >= 3 else 0) + 1
     return 2
 
 
