@@ -590,6 +590,91 @@ def check_nrmse_definition(O):
     assert abs(O.nrmse(a, b) - brute) < 1e-9, (O.nrmse(a, b), brute)
 
 
+def check_regulariser_definition(O):
+    """The rPIE regulariser u = alpha (max|Q|^2 - |Q|^2): nonnegative, zero
+    exactly where |Q| is largest, linear in alpha and of degree two in Q for
+    a probe of any scale (the workloads normalise max|Q| to 1, which would
+    hide a missing maximum)."""
+    rng = np.random.default_rng(21)
+    Q = 3.0 * _crand(rng, 8, 8)
+    a2 = np.abs(Q) ** 2
+    u = O.rpie_regulariser(Q, 0.2)
+    assert np.all(u >= -1e-12 * a2.max())
+    assert abs(u.flat[int(np.argmax(a2))]) <= 1e-12 * a2.max()
+    assert _rel(O.rpie_regulariser(2.0 * Q, 0.2), 4.0 * u) < 1e-12
+    assert _rel(O.rpie_regulariser(Q, 0.6), 3.0 * u) < 1e-12
+
+
+def _idft2_brute(x):
+    """Inverse DFT by its defining double sum, (1/m^2) sum X exp(+2 pi i ...)."""
+    m = x.shape[0]
+    k = np.arange(m)
+    w = np.exp(2j * np.pi * np.outer(k, k) / m)
+    return w @ x @ w / (m * m)
+
+
+def check_zero_spectrum_phase(O):
+    """Definition REW with theta(0) = 0: for a window whose exit wave is zero
+    every spectrum entry is exactly 0, so the revised exit wave is the inverse
+    DFT of sqrt(d_k) itself (brute-force inverse DFT here)."""
+    rng = np.random.default_rng(22)
+    m = 8
+    Q = _crand(rng, m, m)
+    d = 4.0 * rng.random((m, m))
+    R = O.revised_exit_wave(np.zeros((m, m), dtype=np.complex128), Q, d)
+    assert _rel(R, _idft2_brute(np.sqrt(d))) < 1e-12
+
+
+def check_disjoint_windows_decouple(O):
+    """Windows that do not overlap do not interact in a minibatch (the weights
+    cancel pixel by pixel), so a sweep over disjoint windows gives each window
+    exactly its own MAGPS step, for any minibatch size: the sweep's last,
+    short minibatch is applied like the others."""
+    rng = np.random.default_rng(23)
+    m, nw = 8, 5
+    z_true = (0.8 + 0.2 * rng.random((m, nw * m))) * np.exp(1j * (rng.random((m, nw * m)) - 0.5))
+    c = (m - 1) / 2.0
+    yy, xx = np.meshgrid(np.arange(m) - c, np.arange(m) - c, indexing="ij")
+    Q = np.exp(-(xx ** 2 + yy ** 2) / (2 * (m / 3.0) ** 2)) * np.exp(0.3j * (xx ** 2 + yy ** 2) / m)
+    pos = np.array([(0, k * m) for k in range(nw)], dtype=np.int64)
+    d = O.forward_intensities(z_true, Q, pos)
+    z = np.ones(z_true.shape, dtype=np.complex128)
+    u = O.rpie_regulariser(Q, 0.1)
+    for B in (1, 2, 3, 5):
+        out = O.sweep(z, Q, pos, d, u, 2, rng.permutation(nw), B)
+        for k in range(nw):
+            zk = z[:, k * m:(k + 1) * m]
+            ref = O.magps(zk, Q, O.revised_exit_wave(zk, Q, d[k]), u, 2)
+            assert _rel(out[:, k * m:(k + 1) * m], ref) < 1e-12, (B, k)
+
+
+def check_dead_bins_stay_finite(O):
+    """A probe with a dead 2 x 2 bin (so dead bins on every coarser level
+    above it): every level weight and every MAGPS output stays finite.  What
+    a dead bin's weight is, is a reading (the division rule); that it is
+    finite is what any rule must give."""
+    z_true, Q, pos, d = _small_problem(O, seed=24)
+    Q = Q.copy()
+    Q[2:4, 2:4] = 0.0
+    d = O.forward_intensities(z_true, Q, pos)
+    u = O.rpie_regulariser(Q, 0.1)
+    Ql = Q
+    for _ in range(3):
+        QH, Wz, WR, Wu = O.coarse_weights(Ql)
+        for a in (QH, Wz, WR, Wu):
+            assert np.all(np.isfinite(a))
+        Ql = QH
+    rng = np.random.default_rng(24)
+    z = z_true + 0.2 * _crand(rng, *z_true.shape)
+    m = Q.shape[0]
+    for k in (0, 3):
+        zk = O.extract(z, pos[k], m)
+        Rk = O.revised_exit_wave(zk, Q, d[k])
+        for L in (2, 3, 4):
+            assert np.all(np.isfinite(O.magps(zk, Q, Rk, u, L))), L
+    assert np.all(np.isfinite(O.minibatch_step(z, Q, pos, d, u, 4, list(range(len(pos))))))
+
+
 ALL_CHECKS = [
     check_dft_defining_sum, check_dft_parseval_inverse, check_dft_closed_forms,
     check_scan_adjoint, check_transfer_operators, check_objective_forms,
@@ -599,5 +684,6 @@ ALL_CHECKS = [
     check_coarse_prox_is_argmin, check_auto_regularisation,
     check_consistency_bounds, check_residual_form, check_special_cases,
     check_probe_step, check_recovery, check_mgopt_variant, check_phase_rule_variant,
-    check_stop_metric_closed_form, check_nrmse_definition,
+    check_stop_metric_closed_form, check_nrmse_definition, check_regulariser_definition,
+    check_zero_spectrum_phase, check_disjoint_windows_decouple, check_dead_bins_stay_finite,
 ]

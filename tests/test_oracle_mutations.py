@@ -202,13 +202,111 @@ def m_nrmse_conjugate_phase(O):
     O.nrmse = nr
 
 
+def m_probe_step_sign(O):
+    orig = O.probe_step
+
+    def ps(z, Q, positions, d, beta, batch):
+        return 2 * np.asarray(Q, dtype=np.complex128) - orig(z, Q, positions, d, beta, batch)
+    O.probe_step = ps
+
+
+def m_probe_regulariser_of_probe(O):
+    def ps(z, Q, positions, d, beta, batch):
+        m = Q.shape[0]
+        num = np.zeros(Q.shape, dtype=np.complex128)
+        den = np.zeros(Q.shape, dtype=np.float64)
+        q2 = np.abs(Q) ** 2
+        for k in batch:
+            zk = O.extract(z, positions[k], m)
+            Rk = O.revised_exit_wave(zk, Q, d[k])
+            a2 = np.abs(zk) ** 2
+            num += np.conj(zk) * (Rk - Q * zk)
+            den += beta * (q2.max() - q2) + a2  # the probe's own intensity in place of the window's
+        out = np.array(Q, dtype=np.complex128, copy=True)
+        lit = den > 0
+        out[lit] += num[lit] / den[lit]
+        return out
+    O.probe_step = ps
+
+
+def m_theta_zero_is_pi(O):
+    def rew(zk, Q, dk, prev_phase=None):
+        psi = O.fft2(O.exit_wave(zk, Q))
+        theta = np.angle(psi)
+        zero = psi == 0
+        theta[zero] = np.pi if prev_phase is None else prev_phase[zero]
+        return O.ifft2(np.sqrt(dk) * np.exp(1j * theta))
+    O.revised_exit_wave = rew
+
+
+def m_proximal_without_u(O):
+    O.proximal_step = lambda zk, Q, Rk, u: zk + O.safe_div(np.conj(Q), np.abs(Q) ** 2) * (Rk - Q * zk)
+
+
+def m_forward_amplitude(O):
+    O.forward_intensities = lambda z, Q, positions: np.stack(
+        [np.abs(O.fft2(O.exit_wave(O.extract(z, p, Q.shape[0]), Q))) for p in positions])
+
+
+def m_sweep_drops_short_minibatch(O):
+    def sw(z, Q, positions, d, u, levels, order, minibatch):
+        n = len(order) - len(order) % minibatch
+        for s in range(0, n, minibatch):
+            z = O.minibatch_step(z, Q, positions, d, u, levels, order[s:s + minibatch])
+        return z
+    O.sweep = sw
+
+
+def m_minibatch_sequential(O):
+    def mb(z, Q, positions, d, u, levels, batch):
+        z = np.array(z, dtype=np.complex128, copy=True)
+        m = Q.shape[0]
+        for k in batch:
+            r, c = positions[k]
+            zk = z[r:r + m, c:c + m]
+            Rk = O.revised_exit_wave(zk, Q, d[k])
+            z[r:r + m, c:c + m] = O.magps(zk, Q, Rk, u, levels)
+        return z
+    O.minibatch_step = mb
+
+
+def m_minibatch_unweighted(O):
+    def mb(z, Q, positions, d, u, levels, batch):
+        z = np.asarray(z, dtype=np.complex128)
+        m = Q.shape[0]
+        num = np.zeros(z.shape, dtype=np.complex128)
+        den = np.zeros(z.shape, dtype=np.float64)
+        for k in batch:
+            r, c = positions[k]
+            zk = z[r:r + m, c:c + m]
+            Rk = O.revised_exit_wave(zk, Q, d[k])
+            num[r:r + m, c:c + m] += O.magps(zk, Q, Rk, u, levels) - zk
+            den[r:r + m, c:c + m] += 1.0
+        out = z.copy()
+        lit = den > 0
+        out[lit] += num[lit] / den[lit]
+        return out
+    O.minibatch_step = mb
+
+
+def m_regulariser_no_max(O):
+    O.rpie_regulariser = lambda Q, alpha: alpha * (1.0 - np.abs(Q) ** 2)
+
+
+def m_safe_div_unguarded(O):
+    O.safe_div = lambda num, den: np.asarray(num) / np.asarray(den)
+
+
 MUTATIONS = [m_restrict_sum, m_prolong_scaled, m_fft_sign, m_fft_unnormalised_inverse,
              m_no_sqrt, m_gradient_no_conj, m_wr_no_conj, m_wz_unnormalised,
              m_uh_unweighted, m_post_smooth_from_z, m_minibatch_count_average,
              m_regulariser_amplitude, m_extract_transposed, m_objective_no_half,
              m_mgopt_shift_sign, m_mgopt_weighted_restriction, m_phase_rule_forgets,
              m_stop_metric_extra_inv_m, m_stop_metric_squared_norms, m_stop_metric_sum_not_mean,
-             m_nrmse_swapped, m_nrmse_no_phase, m_nrmse_conjugate_phase]
+             m_nrmse_swapped, m_nrmse_no_phase, m_nrmse_conjugate_phase,
+             m_probe_step_sign, m_probe_regulariser_of_probe, m_theta_zero_is_pi, m_proximal_without_u,
+             m_forward_amplitude, m_sweep_drops_short_minibatch, m_minibatch_sequential, m_minibatch_unweighted,
+             m_regulariser_no_max, m_safe_div_unguarded]
 
 FAST_CHECKS = [c for c in pins.ALL_CHECKS if c is not pins.check_recovery]
 
