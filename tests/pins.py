@@ -191,6 +191,13 @@ def check_majorization(O):
     eps = 1e-6
     fd = (O.surrogate(zj + eps * h, zj, Q, pos, d) - O.surrogate(zj - eps * h, zj, Q, pos, d)) / (2 * eps)
     assert abs(fd - np.real(np.vdot(g, h))) < 1e-6 * max(1.0, abs(fd))
+    # Eq. (quadratic_surrogate) is a quadratic in z for fixed z^(j): along a
+    # line its second differences are constant and equal 2 * 1/2 sum ||Q . P_k h||^2
+    # per unit step squared; Phi itself is not quadratic (R_k moves with z)
+    vals = [O.surrogate(zj + t * h, zj, Q, pos, d) for t in (-1.0, 0.0, 1.0, 2.0)]
+    curv = sum(float(np.sum(np.abs(Q * O.extract(h, p, Q.shape[0])) ** 2)) for p in pos)
+    assert abs((vals[0] - 2 * vals[1] + vals[2]) - curv) < 1e-9 * curv
+    assert abs((vals[1] - 2 * vals[2] + vals[3]) - curv) < 1e-9 * curv
 
 
 def check_full_batch_monotone(O):

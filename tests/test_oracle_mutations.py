@@ -297,6 +297,99 @@ def m_safe_div_unguarded(O):
     O.safe_div = lambda num, den: np.asarray(num) / np.asarray(den)
 
 
+def m_gradient_scaled_twice(O):
+    orig = O.gradient_k
+    O.gradient_k = lambda zk, Q, dk: 2.0 * orig(zk, Q, dk)
+
+
+def m_amplitude_form_unscaled(O):
+    orig = O.objective_amplitude
+    O.objective_amplitude = lambda z, Q, positions, d: orig(z, Q, positions, d) * Q.shape[0] ** 2
+
+
+def m_magps_no_post_smoothing(O):
+    orig_magps = O.magps
+
+    def magps(zk, Q, Rk, u, levels):
+        if levels == 1:
+            return O.proximal_step(zk, Q, Rk, u)
+        QH, Wz, WR, Wu = O.coarse_weights(Q)
+        zH = O.restrict(Wz * zk)
+        RH = O.restrict(WR * Rk)
+        uH = Wu * O.restrict(u)
+        eH = magps(zH, QH, RH, uH, levels - 1) - zH
+        return zk + O.prolong(eH)
+    O.magps = magps
+
+
+def m_coarse_r_unweighted(O):
+    def magps(zk, Q, Rk, u, levels):
+        if levels == 1:
+            return O.proximal_step(zk, Q, Rk, u)
+        QH, Wz, WR, Wu = O.coarse_weights(Q)
+        zH = O.restrict(Wz * zk)
+        RH = O.restrict(Rk)
+        uH = Wu * O.restrict(u)
+        eH = magps(zH, QH, RH, uH, levels - 1) - zH
+        return O.proximal_step(zk + O.prolong(eH), Q, Rk, u)
+    O.magps = magps
+
+
+def m_coarse_z_unweighted(O):
+    def magps(zk, Q, Rk, u, levels):
+        if levels == 1:
+            return O.proximal_step(zk, Q, Rk, u)
+        QH, Wz, WR, Wu = O.coarse_weights(Q)
+        zH = O.restrict(zk)
+        RH = O.restrict(WR * Rk)
+        uH = Wu * O.restrict(u)
+        eH = magps(zH, QH, RH, uH, levels - 1) - zH
+        return O.proximal_step(zk + O.prolong(eH), Q, Rk, u)
+    O.magps = magps
+
+
+def m_sequential_reversed(O):
+    orig = O.magpie_sequential
+    O.magpie_sequential = lambda z, Q, positions, d, u, levels, order: orig(z, Q, positions, d, u, levels,
+                                                                            list(order)[::-1])
+
+
+def m_probe_ignores_beta(O):
+    orig = O.probe_step
+    O.probe_step = lambda z, Q, positions, d, beta, batch: orig(z, Q, positions, d, 0.0, batch)
+
+
+def m_surrogate_at_new_point(O):
+    def sur(z, zj, Q, positions, d):
+        m = Q.shape[0]
+        tot = 0.0
+        for p, dk in zip(positions, d):
+            Rk = O.revised_exit_wave(O.extract(z, p, m), Q, dk)  # R at z instead of z^(j)
+            tot += 0.5 * float(np.sum(np.abs(O.exit_wave(O.extract(z, p, m), Q) - Rk) ** 2))
+        return tot
+    O.surrogate = sur
+
+
+def m_extract_adjoint_shifted(O):
+    def ea(patch, pos, shape):
+        out = np.zeros(shape, dtype=np.complex128)
+        r, c = pos
+        m = patch.shape[0]
+        r = min(r + 1, shape[0] - m)
+        out[r:r + m, c:c + m] = patch
+        return out
+    O.extract_adjoint = ea
+
+
+def m_wu_not_squared(O):
+    orig = O.coarse_weights
+
+    def cw(Q):
+        QH, Wz, WR, Wu = orig(Q)
+        return QH, Wz, WR, O.safe_div(np.abs(QH), O.restrict(np.abs(Q) ** 2))
+    O.coarse_weights = cw
+
+
 MUTATIONS = [m_restrict_sum, m_prolong_scaled, m_fft_sign, m_fft_unnormalised_inverse,
              m_no_sqrt, m_gradient_no_conj, m_wr_no_conj, m_wz_unnormalised,
              m_uh_unweighted, m_post_smooth_from_z, m_minibatch_count_average,
@@ -306,7 +399,10 @@ MUTATIONS = [m_restrict_sum, m_prolong_scaled, m_fft_sign, m_fft_unnormalised_in
              m_nrmse_swapped, m_nrmse_no_phase, m_nrmse_conjugate_phase,
              m_probe_step_sign, m_probe_regulariser_of_probe, m_theta_zero_is_pi, m_proximal_without_u,
              m_forward_amplitude, m_sweep_drops_short_minibatch, m_minibatch_sequential, m_minibatch_unweighted,
-             m_regulariser_no_max, m_safe_div_unguarded]
+             m_regulariser_no_max, m_safe_div_unguarded,
+             m_gradient_scaled_twice, m_amplitude_form_unscaled, m_magps_no_post_smoothing, m_coarse_r_unweighted,
+             m_coarse_z_unweighted, m_sequential_reversed, m_probe_ignores_beta, m_surrogate_at_new_point,
+             m_extract_adjoint_shifted, m_wu_not_squared]
 
 FAST_CHECKS = [c for c in pins.ALL_CHECKS if c is not pins.check_recovery]
 
