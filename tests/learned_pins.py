@@ -147,6 +147,14 @@ def adam_closed_forms(L):
         th2, m, v = L.adam(th1, g, m, v, t, lr)
         assert np.allclose(th2 - th1, -lr * g / (np.abs(g) + 1e-8), rtol=1e-9, atol=0)
         th1 = th2
+    # a gradient g then 0: the second step's bias-corrected moments are
+    # b1 g / (1 + b1) and b2 g^2 / (1 + b2) (Kingma and Ba, Algorithm 1, two
+    # steps written out), so it moves by -lr (b1/(1+b1)) g / (sqrt(b2/(1+b2)) |g| + eps)
+    b1, b2 = 0.9, 0.999
+    th1, m1, v1 = L.adam(th, g, np.zeros(100), np.zeros(100), 1, lr)
+    th2, _, _ = L.adam(th1, np.zeros(100), m1, v1, 2, lr)
+    expect = -lr * (b1 / (1 + b1)) * g / (np.sqrt(b2 / (1 + b2)) * np.abs(g) + 1e-8)
+    assert np.allclose(th2 - th1, expect, rtol=1e-9, atol=0)
 
 
 def loss_gradient(L):
@@ -225,6 +233,26 @@ def acceptance_rule(L):
         assert np.isclose(L.window_surrogate(a, Q, Rk), lhs)
 
 
+def proposal_in_units_of_the_scale(L):
+    """The network's output is in units of the window's scale s (the RMS of
+    the plain coarse step): a network whose last layer has zero weights and
+    biases (b0, b1) outputs y = b everywhere, and the proposal is then
+    e_plain + s (b0 + i b1); the window's margin is the surrogate of the plain
+    output minus that of the V-cycle built on that proposal."""
+    zk, Q, Rk, u, _, levels = _window()
+    theta = random_theta(L, 18)
+    theta[-(64 * 9 * 2 + 2):] = 0.0
+    theta[-2:] = (0.03, -0.02)
+    _, acc, margin = L.learned_window(zk, Q, Rk, u, levels, theta)
+    _, s, e_plain = L.coarse_state(zk, Q, Rk, u, levels)
+    b = complex(float(np.float32(0.03)), float(np.float32(-0.02)))  # the FP32 output, held in FP64
+    prop = L.magps_coarse_given(zk, Q, Rk, u, levels, e_plain + s * b)
+    plain = L.magps_coarse_given(zk, Q, Rk, u, levels, e_plain)
+    expect = 0.5 * np.sum(np.abs(Q * plain - Rk) ** 2) - 0.5 * np.sum(np.abs(Q * prop - Rk) ** 2)
+    assert s > 0 and abs(margin - expect) <= 1e-9 * max(abs(expect), 1e-300), (margin, expect)
+    assert acc == (expect >= 0)
+
+
 def minibatch_reduces_to_plain(L):
     """With a zero last layer the learned minibatch step is the plain one."""
     w = synth.WORKLOADS["tiny"]
@@ -272,4 +300,4 @@ def targets_definition(L):
 ALL = [bf16_rounding, conv_matches_library, conv_special_cases, network_matches_autograd,
        backward_finite_difference, rounded_network_close, adam_closed_forms, loss_gradient,
        coarse_state_is_residual_chain, plain_coarse_step_is_magps, acceptance_rule,
-       minibatch_reduces_to_plain, stacked_windows_are_independent, targets_definition]
+       minibatch_reduces_to_plain, stacked_windows_are_independent, targets_definition, proposal_in_units_of_the_scale]

@@ -117,8 +117,105 @@ def m_scale_not_rms(L):
     L.coarse_state = cs
 
 
+def m_adam_eps_inside_sqrt(L):
+    def adam(theta, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
+        m = b1 * m + (1.0 - b1) * g
+        v = b2 * v + (1.0 - b2) * g * g
+        mh = m / (1.0 - b1 ** step)
+        vh = v / (1.0 - b2 ** step)
+        return theta - lr * mh / np.sqrt(vh + eps), m, v
+    L.adam = adam
+
+
+def m_adam_betas_swapped(L):
+    orig = L.adam
+    L.adam = lambda theta, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8: orig(theta, g, m, v, step, lr, b2, b1, eps)
+
+
+def m_loss_grad_sum_not_mean(L):
+    def lg(y, t):
+        r = y - t
+        return 0.5 * float(np.mean(r * r)), r
+    L.loss_and_grad = lg
+
+
+def m_upsample_tiled(L):
+    orig = L.conv3x3
+
+    def conv(x, W, b, stride, up):
+        if up > 1:
+            x = np.tile(x, (1, up, up, 1))
+            return orig(x, W, b, stride, 1)
+        return orig(x, W, b, stride, up)
+    L.conv3x3 = conv
+
+
+def m_backward_no_bias_grad(L):
+    orig = L.conv3x3_backward
+
+    def cb(x, W, dy, stride, up):
+        dx, dW, db = orig(x, W, dy, stride, up)
+        return dx, dW, np.zeros_like(db)
+    L.conv3x3_backward = cb
+
+
+def m_acceptance_strict(L):
+    orig = L.learned_window
+
+    def lw(zk, Q, Rk, u, levels, theta, rounding=True):
+        out, acc, margin = orig(zk, Q, Rk, u, levels, theta, rounding)
+        if acc and margin == 0.0:
+            x, s, e_plain = L.coarse_state(zk, Q, Rk, u, levels)
+            return L.magps_coarse_given(zk, Q, Rk, u, levels, e_plain), False, margin
+        return out, acc, margin
+    L.learned_window = lw
+
+
+def m_proposal_unscaled(L):
+    def lw(zk, Q, Rk, u, levels, theta, rounding=True):
+        x, s, e_plain = L.coarse_state(zk, Q, Rk, u, levels)
+        plain = L.magps_coarse_given(zk, Q, Rk, u, levels, e_plain)
+        if not s > L.O.TINY:
+            return plain, False, 0.0
+        y, _ = L.forward(theta, x[None], rounding)
+        e_nn = e_plain + (y[0, ..., 0] + 1j * y[0, ..., 1])  # the scale s dropped
+        learned = L.magps_coarse_given(zk, Q, Rk, u, levels, e_nn)
+        margin = L.window_surrogate(plain, Q, Rk) - L.window_surrogate(learned, Q, Rk)
+        return (learned, True, margin) if margin >= 0 else (plain, False, margin)
+    L.learned_window = lw
+
+
+def m_surrogate_no_half(L):
+    L.window_surrogate = lambda x, Q, Rk: float(np.sum(np.abs(Q * x - Rk) ** 2))
+
+
+def m_relu_on_output(L):
+    orig = L.forward
+
+    def fw(theta, x, rounding=True):
+        out, acts = orig(theta, x, rounding)
+        return np.maximum(out, 0.0), acts
+    L.forward = fw
+
+
+def m_bias_before_weights(L):
+    def unpack(theta):
+        out, o = [], 0
+        for ci, co, _, _, _ in L.LAYERS:
+            b = theta[o:o + co]
+            o += co
+            W = theta[o:o + co * 9 * ci].reshape(co, 3, 3, ci)
+            o += co * 9 * ci
+            out.append((W, b))
+        return out
+    L.unpack = unpack
+
+
 MUTANTS = [m_kernel_transposed, m_no_relu_mask, m_bf16_truncate, m_adam_no_bias_correction, m_plain_restriction,
-           m_acceptance_inverted, m_no_post_smoothing, m_stride_offset, m_target_sign, m_scale_not_rms]
+           m_acceptance_inverted, m_no_post_smoothing, m_stride_offset, m_target_sign, m_scale_not_rms,
+           m_adam_eps_inside_sqrt, m_adam_betas_swapped, m_loss_grad_sum_not_mean, m_upsample_tiled,
+           m_backward_no_bias_grad, m_acceptance_strict, m_proposal_unscaled, m_surrogate_no_half,
+           m_relu_on_output, m_bias_before_weights]
 
 
 @pytest.mark.parametrize("mutant", MUTANTS, ids=lambda f: f.__name__)
