@@ -682,6 +682,29 @@ def check_dead_bins_stay_finite(O):
     assert np.all(np.isfinite(O.minibatch_step(z, Q, pos, d, u, 4, list(range(len(pos))))))
 
 
+def check_metric_helpers(O):
+    """The illuminated mask is the set of pixels whose summed probe intensity
+    sum_k P_k^T |Q|^2 reaches `rel` of its maximum, computed here pixel by
+    pixel from the windows that cover each pixel; the magnitude error of
+    Section 5, || |z| - |z*| ||, ignores every pixel's phase and is ||z*|| for
+    z = 2 z*."""
+    rng = np.random.default_rng(25)
+    m, n = 6, 20
+    Q = _crand(rng, m, m)
+    pos = [(0, 0), (3, 5), (10, 2), (14, 14), (2, 11)]
+    for rel in (1e-3, 0.3, 0.7):
+        cov = np.zeros((n, n))
+        for i in range(n):
+            for j in range(n):
+                for r, c in pos:
+                    if r <= i < r + m and c <= j < c + m:
+                        cov[i, j] += abs(Q[i - r, j - c]) ** 2
+        assert np.array_equal(O.illuminated_mask(Q, pos, (n, n), rel), cov >= rel * cov.max())
+    zt = _crand(rng, n, n)
+    assert O.magnitude_error(zt * np.exp(1j * rng.random((n, n)) * 6.0), zt) < 1e-12 * np.linalg.norm(zt)
+    assert abs(O.magnitude_error(2 * zt, zt) - np.linalg.norm(zt)) < 1e-12 * np.linalg.norm(zt)
+
+
 ALL_CHECKS = [
     check_dft_defining_sum, check_dft_parseval_inverse, check_dft_closed_forms,
     check_scan_adjoint, check_transfer_operators, check_objective_forms,
@@ -693,4 +716,5 @@ ALL_CHECKS = [
     check_probe_step, check_recovery, check_mgopt_variant, check_phase_rule_variant,
     check_stop_metric_closed_form, check_nrmse_definition, check_regulariser_definition,
     check_zero_spectrum_phase, check_disjoint_windows_decouple, check_dead_bins_stay_finite,
+    check_metric_helpers,
 ]

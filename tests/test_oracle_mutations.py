@@ -390,6 +390,45 @@ def m_wu_not_squared(O):
     O.coarse_weights = cw
 
 
+def m_mask_relative_to_sum(O):
+    def im(Q, positions, shape, rel=1e-3):
+        m = Q.shape[0]
+        cov = np.zeros(shape)
+        for r, c in positions:
+            cov[r:r + m, c:c + m] += np.abs(Q) ** 2
+        return cov >= rel * cov.sum()
+    O.illuminated_mask = im
+
+
+def m_mask_amplitude_coverage(O):
+    def im(Q, positions, shape, rel=1e-3):
+        m = Q.shape[0]
+        cov = np.zeros(shape)
+        for r, c in positions:
+            cov[r:r + m, c:c + m] += np.abs(Q)
+        return cov >= rel * cov.max()
+    O.illuminated_mask = im
+
+
+def m_magnitude_error_complex(O):
+    O.magnitude_error = lambda z, z_true: float(np.linalg.norm(z - z_true))
+
+
+def m_objective_skips_last_window(O):
+    orig = O.objective
+    O.objective = lambda z, Q, positions, d: orig(z, Q, positions[:-1], d[:-1])
+
+
+def m_recycled_phase_not_stored(O):
+    def rr(zk, Q, dk, prev_theta):
+        psi = O.fft2(O.exit_wave(zk, Q))
+        theta = np.angle(psi)
+        zero = psi == 0
+        theta[zero] = 0.0
+        return O.ifft2(np.sqrt(dk) * np.exp(1j * theta)), theta
+    O.revised_exit_wave_recycled = rr
+
+
 MUTATIONS = [m_restrict_sum, m_prolong_scaled, m_fft_sign, m_fft_unnormalised_inverse,
              m_no_sqrt, m_gradient_no_conj, m_wr_no_conj, m_wz_unnormalised,
              m_uh_unweighted, m_post_smooth_from_z, m_minibatch_count_average,
@@ -402,7 +441,9 @@ MUTATIONS = [m_restrict_sum, m_prolong_scaled, m_fft_sign, m_fft_unnormalised_in
              m_regulariser_no_max, m_safe_div_unguarded,
              m_gradient_scaled_twice, m_amplitude_form_unscaled, m_magps_no_post_smoothing, m_coarse_r_unweighted,
              m_coarse_z_unweighted, m_sequential_reversed, m_probe_ignores_beta, m_surrogate_at_new_point,
-             m_extract_adjoint_shifted, m_wu_not_squared]
+             m_extract_adjoint_shifted, m_wu_not_squared,
+             m_mask_relative_to_sum, m_mask_amplitude_coverage, m_magnitude_error_complex,
+             m_objective_skips_last_window, m_recycled_phase_not_stored]
 
 FAST_CHECKS = [c for c in pins.ALL_CHECKS if c is not pins.check_recovery]
 
