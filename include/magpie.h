@@ -60,8 +60,9 @@ extern "C" {
 #define MAGPIE_EINDEX (-5)      /* a device-side window index was out of range  */
 #define MAGPIE_ETIMEOUT (-6)    /* a bounded device wait ran out (a tcgen05
                                    convolution or transform stopped waiting for
-                                   its MMAs, or a persistent group step for its
-                                   windows)                                      */
+                                   its MMAs, a persistent group step for its
+                                   windows, or a precision-form kernel for the
+                                   windows handed on by the kernel before it)    */
 
 typedef struct magpie_ctx magpie_ctx;
 
@@ -136,9 +137,10 @@ int magpie_create(magpie_ctx** out, const magpie_params* params, void* object,
 void magpie_destroy(magpie_ctx* ctx);
 
 /*
- * One minibatch step: the windows idx[0..count-1] (DEVICE int32 array) are
- * processed from the current object and their increments applied (the
- * combination rule at the top of this file).  1 <= count <= minibatch.
+ * One minibatch step of Algorithm MAGPIE (every window of the minibatch from
+ * the same object, the combination rule at the top of this file): the windows
+ * idx[0..count-1] (DEVICE int32 array) are processed from the current object
+ * and their increments applied.  1 <= count <= minibatch.
  * Indices outside [0, n_pos) are skipped on the device and reported as
  * MAGPIE_EINDEX by the next synchronous call.
  */
@@ -165,7 +167,8 @@ int magpie_sweep(magpie_ctx* ctx, const int32_t* order);
 int magpie_profile_sweep(magpie_ctx* ctx, const int32_t* order, double* window_ms, double* apply_ms,
                          int32_t* launches);
 
-/* Copy the context's current probe to `probe` (DEVICE complex [m][m]). */
+/* Copy the context's current probe to `probe` (DEVICE complex [m][m]); it
+   differs from the one given only with the probe step (an extension). */
 int magpie_get_probe(magpie_ctx* ctx, void* probe);
 
 /*
@@ -191,8 +194,9 @@ int magpie_set_probe(magpie_ctx* ctx, const void* probe);
 
 /*
  * Per-window values of the last pass over each window (from a sweep, a
- * step or an objective/stop-metric evaluation): phi_k = Phi_k(z_k) and
- * gnorm_k = || grad Phi_k(z_k) ||_2 at the object the window saw.
+ * step or an objective/stop-metric evaluation): phi_k = Phi_k(z_k) (Eq.
+ * exit_misfit) and gnorm_k = || grad Phi_k(z_k) ||_2 (Eq. misfit_derivative)
+ * at the object the window saw.
  * Synchronous: writes HOST arrays phi[n_pos] and gnorm[n_pos] (either may
  * be NULL).
  */
