@@ -156,3 +156,21 @@ def test_learned_and_precision_entry_points_without_a_gpu(L):
     assert L.magpie_set_precision(None, 2) == magpie.EINVAL
     assert L.magpie_precision_check_waits(None, ctypes.c_double(1e-3)) == magpie.EINVAL
     L.magpie_cnn_destroy(None)
+
+
+def test_binding_marshals_only_matching_tensors():
+    """The binding passes raw pointers only for tensors of the declared kind,
+    dtype, layout and size; anything else raises before any library call."""
+    import torch
+    cpu = torch.zeros(16, dtype=torch.int32)
+    with pytest.raises(TypeError):
+        magpie._dev(cpu, torch.int32, 16, "order")              # a host tensor where a device one is due
+    assert magpie._host(cpu, torch.int32, 16, "order") == cpu.data_ptr()
+    with pytest.raises(ValueError):
+        magpie._host(cpu, torch.int64 if cpu.dtype == torch.int32 else torch.int32, 16, "order")
+    with pytest.raises(ValueError):
+        magpie._host(cpu, torch.int32, 15, "order")             # wrong element count
+    with pytest.raises(ValueError):
+        magpie._host(torch.zeros(4, 8, dtype=torch.int32).t(), torch.int32, 32, "order")  # not contiguous
+    with pytest.raises(TypeError):
+        magpie._host([0] * 16, torch.int32, 16, "order")        # not a tensor
